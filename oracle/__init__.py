@@ -1,0 +1,190 @@
+"""CPU oracle for the SPAI methods (test infrastructure only).
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline
+leg may import this package.  It compiles ``spai_oracle.c`` with gcc
+(``-O2 -ffp-contract=off``) into ``oracle/_build/liboracle.so`` and wraps it
+with ctypes.  It imports nothing from the product package.
+
+Method definitions followed (Venkovic & Anzt): MR = Algorithm 1, CG =
+Algorithm 3 (Def. 1, Prop. 2), LOMR = Algorithm 4 (Def. 2, Theorem 3), hard
+thresholding = Sec. 6.1 Eq. (6.2) applied per column, explicit residual =
+Sec. 6.2.  The C file's header lists every reading taken where the paper is
+silent.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "spai_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_BUILD, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+MR, LOMR, CG = 0, 1, 2
+METHODS = {"mr": MR, "lomr": LOMR, "cg": CG}
+FLAG_CONVERGED, FLAG_FALLBACK, FLAG_NONFINITE = 1, 2, 4
+DROP_NONE, DROP_TOPK, DROP_DIRECTIONS = 0, 1, 2
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle shared library (idempotent)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if (not force and os.path.exists(_LIB)
+            and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
+        return _LIB
+    tmp = _LIB + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+           "-o", tmp, _SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        lib = C.CDLL(build())
+        p_i32 = np.ctypeslib.ndpointer(np.int32, flags="C_CONTIGUOUS")
+        p_f64 = np.ctypeslib.ndpointer(np.float64, flags="C_CONTIGUOUS")
+        lib.orc_new.restype = C.c_void_p
+        lib.orc_new.argtypes = [C.c_int, p_i32, p_i32, p_f64, C.c_int, C.c_double]
+        lib.orc_free.argtypes = [C.c_void_p]
+        lib.orc_run.restype = C.c_int
+        lib.orc_run.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int, p_f64, p_f64,
+                                C.POINTER(C.c_int)]
+        lib.orc_nnz.restype = C.c_int64
+        lib.orc_nnz.argtypes = [C.c_void_p, C.c_int]
+        lib.orc_get.argtypes = [C.c_void_p, C.c_int, p_i32, p_i32, p_f64]
+        lib.orc_set_M.restype = C.c_int
+        lib.orc_set_M.argtypes = [C.c_void_p, p_i32, p_i32, p_f64]
+        lib.orc_spgemm_count.restype = C.c_int64
+        lib.orc_spgemm_count.argtypes = [C.c_void_p]
+        lib.orc_residual_norm.restype = C.c_double
+        lib.orc_residual_norm.argtypes = [C.c_void_p]
+        lib.orc_column_residual.restype = C.c_int
+        lib.orc_column_residual.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]
+        lib.orc_drop_column.restype = C.c_int
+        lib.orc_drop_column.argtypes = [C.c_int, p_i32, p_f64, C.c_int]
+        lib.orc_pairwise.restype = C.c_double
+        lib.orc_pairwise.argtypes = [p_f64, C.c_int64]
+        lib.orc_pcg.restype = C.c_int
+        lib.orc_pcg.argtypes = [C.c_int, p_i32, p_i32, p_f64, C.c_int, C.c_void_p, C.c_void_p,
+                                C.c_void_p, p_f64, C.c_double, C.c_int, p_f64,
+                                C.POINTER(C.c_int), C.POINTER(C.c_double)]
+        _lib = lib
+        return lib
+
+
+def pairwise(t) -> float:
+    """Balanced pairwise sum over t zero-padded to a power of two."""
+    t = np.ascontiguousarray(t, dtype=np.float64)
+    return _load().orc_pairwise(t, len(t))
+
+
+class Oracle:
+    """Sparse-iterate state (M, P, Z) for one SPD matrix A.
+
+    ``mixed=True`` emulates the FP32-value / FP64-reduction arithmetic
+    exactly; ``cap_factor`` sets cap_j = floor(f * nnz(A[:, j])) in [1, n].
+    M starts at diag(A)^{-1}.
+    """
+
+    def __init__(self, n, rowptr, colind, vals, mixed=False, cap_factor=2.0):
+        self.lib = _load()
+        self.n = int(n)
+        self.rowptr = np.ascontiguousarray(rowptr, dtype=np.int32)
+        self.colind = np.ascontiguousarray(colind, dtype=np.int32)
+        self.vals = np.ascontiguousarray(vals, dtype=np.float64)
+        self.mixed = bool(mixed)
+        self.h = self.lib.orc_new(self.n, self.rowptr, self.colind, self.vals, int(mixed),
+                                  float(cap_factor))
+
+    def __del__(self):
+        h = getattr(self, "h", None)
+        if h:
+            self.lib.orc_free(h)
+            self.h = None
+
+    def run(self, method, iters, drop=DROP_TOPK):
+        m = METHODS[method] if isinstance(method, str) else int(method)
+        res = np.full(iters + 1, np.nan)
+        coef = np.full(2 * max(iters, 1), np.nan)
+        flags = C.c_int(0)
+        done = self.lib.orc_run(self.h, m, int(iters), int(drop), res, coef, C.byref(flags))
+        return dict(done=done, resnorm=res, coef=coef.reshape(-1, 2), flags=flags.value)
+
+    def get(self, which=0):
+        """CSC (colptr, rowind, vals) of M (0), P (1) or Z (2)."""
+        nnz = self.lib.orc_nnz(self.h, which)
+        cp = np.zeros(self.n + 1, dtype=np.int32)
+        ri = np.zeros(max(nnz, 1), dtype=np.int32)
+        va = np.zeros(max(nnz, 1), dtype=np.float64)
+        self.lib.orc_get(self.h, which, cp, ri, va)
+        return cp, ri[:nnz], va[:nnz]
+
+    def get_M(self):
+        return self.get(0)
+
+    def set_M(self, colptr, rowind, vals):
+        self.lib.orc_set_M(self.h, np.ascontiguousarray(colptr, dtype=np.int32),
+                           np.ascontiguousarray(rowind, dtype=np.int32),
+                           np.ascontiguousarray(vals, dtype=np.float64))
+
+    def spgemm_count(self):
+        return self.lib.orc_spgemm_count(self.h)
+
+    def residual_norm(self):
+        return self.lib.orc_residual_norm(self.h)
+
+    def column_residual(self, j):
+        L = self.lib.orc_column_residual(self.h, int(j), None, None)
+        rows = np.zeros(max(L, 1), dtype=np.int32)
+        vals = np.zeros(max(L, 1), dtype=np.float64)
+        self.lib.orc_column_residual(self.h, int(j), rows.ctypes.data, vals.ctypes.data)
+        return rows[:L], vals[:L]
+
+
+def drop_column(rows, vals, cap):
+    """Hard-threshold one row-sorted column to ``cap`` entries (Sec. 6.1, per column)."""
+    rows = np.array(rows, dtype=np.int32)
+    vals = np.array(vals, dtype=np.float64)
+    L = _load().orc_drop_column(len(rows), rows, vals, int(cap))
+    return rows[:L], vals[:L]
+
+
+def pcg(n, rowptr, colind, vals, b, rtol=1e-8, maxit=10000, precond=0, M=None):
+    """Vector PCG with x0 = 0; precond 0 none, 1 Jacobi, 2 SPAI M, 3 symmetric
+    part (M + M^T)/2 of the SPAI (M given as a CSC triple).
+
+    Returns dict(iters, status (0 conv / 1 maxit / 2 breakdown), relres, x).
+    """
+    lib = _load()
+    rowptr = np.ascontiguousarray(rowptr, dtype=np.int32)
+    colind = np.ascontiguousarray(colind, dtype=np.int32)
+    vals = np.ascontiguousarray(vals, dtype=np.float64)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    x = np.zeros(n, dtype=np.float64)
+    st = C.c_int(0)
+    rr = C.c_double(0.0)
+    keep = []
+    if precond in (2, 3):
+        cp, ri, mv = (np.ascontiguousarray(M[0], dtype=np.int32),
+                      np.ascontiguousarray(M[1], dtype=np.int32),
+                      np.ascontiguousarray(M[2], dtype=np.float64))
+        keep = [cp, ri, mv]
+        args = (cp.ctypes.data, ri.ctypes.data, mv.ctypes.data)
+    else:
+        args = (None, None, None)
+    it = lib.orc_pcg(int(n), rowptr, colind, vals, int(precond), *args, b, float(rtol), int(maxit),
+                     x, C.byref(st), C.byref(rr))
+    del keep
+    return dict(iters=it, status=st.value, relres=rr.value, x=x)

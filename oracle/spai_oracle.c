@@ -1,0 +1,793 @@
+/*
+ * CPU oracle for the global short-recurrence SPAI methods (MR, LOMR,
+ * Frobenius-CG) with per-column hard thresholding, and for the vector PCG
+ * that assesses the resulting approximate inverse.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path links, loads or
+ * calls this file; only the tests, the smoke check and the benchmark's
+ * CPU-baseline leg do.  It shares no code with the CUDA library.
+ *
+ * Plain, slow, single threaded.  Every matrix iterate is a list of columns;
+ * each column is a row-sorted list of (row, value) with value != 0.  Build
+ * with -ffp-contract=off so that a*b+c is never fused implicitly; the only
+ * fused operations are the explicit fma()/fmaf() calls below.
+ *
+ * What each function follows (sections / equations / algorithms of Venkovic
+ * & Anzt, "Global Iterative Methods for Sparse Approximate Inverses of SPD
+ * Matrices"):
+ *   objective f(M) = ||I - A M||_F^2 ............ Sec. 2, Eqs. (2.3)-(2.4)
+ *   MR ........................................... Algorithm 1, Eq. (2.6)
+ *   CG with Frobenius products ................... Def. 1, Prop. 2, Algorithm 3
+ *   LOMR ......................................... Def. 2, Theorem 3, Algorithm 4
+ *   hard thresholding ............................ Sec. 6.1, Eq. (6.2)
+ *   explicit residual under dropping ............. Sec. 6.2, Table 2
+ *   vector PCG assessment ........................ Sec. 7.1.2 / 7.2
+ *
+ * Readings where the paper is silent (identical on the CUDA side):
+ *   - the cap is per column: cap_j = floor(f * nnz(A[:,j])), clamped to
+ *     [1, n]; a column is dropped to its cap_j largest |v|, ties going to the
+ *     smaller row index; exact zeros are never stored;
+ *   - dropping acts on M and on the search direction (P for MR/CG, Z and P
+ *     for LOMR), never on R; the coefficients use the full R;
+ *   - (A X)[r,j] = fma chain over k ascending: acc = fma(a_rk, x_kj, acc),
+ *     acc starting at +0;  R = I - A M with 1 - s on the diagonal, -s off it;
+ *   - column inner products: products x*y (rounded, FP64) over the common
+ *     rows, summed by a balanced pairwise tree over the row-ascending list
+ *     zero-padded to a power of two; the Frobenius product is the same tree
+ *     over the column partials j = 0..n-1;
+ *   - combinations: M + a P -> fma(a, p, m);  S = d Z + g P -> fma(d, z, g*p);
+ *     M + S -> m + s;  R + b P -> fma(b, p, r); all in FP64, then rounded to
+ *     the value type;
+ *   - mixed precision: stored values and A are FP32; the SpGEMM chain and the
+ *     residual run in FP32; inner products, coefficients and combinations in
+ *     FP64 (FP32 inputs promoted exactly).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_MR 0
+#define ORC_LOMR 1
+#define ORC_CG 2
+
+#define ORC_FLAG_CONVERGED 1
+#define ORC_FLAG_FALLBACK 2
+#define ORC_FLAG_NONFINITE 4
+
+typedef struct {
+  int len, cap;
+  int *row;
+  double *val;
+} ocol;
+
+typedef struct {
+  int n;
+  int *rowptr, *colind;
+  double *a64; /* FP64 values of A */
+  double *av;  /* values used by the SPAI arithmetic (FP32-rounded if mixed) */
+  int mixed;
+  int *capj;   /* per-column cap */
+  /* iterates */
+  ocol *M, *P, *Z;
+  /* method continuation state */
+  int method;  /* -1 none */
+  int it;      /* iterations done by current method */
+  double rr;   /* CG: ||R_i||^2 of the current residual */
+  int64_t spgemm_count;
+  /* workspace */
+  double *acc;
+  char *seen;
+  int *touched;
+} orc_state;
+
+/* ---------------------------------------------------------------- columns */
+
+static void col_reserve(ocol *c, int need) {
+  if (need <= c->cap) return;
+  int nc = c->cap ? c->cap : 4;
+  while (nc < need) nc *= 2;
+  c->row = (int *)realloc(c->row, sizeof(int) * (size_t)nc);
+  c->val = (double *)realloc(c->val, sizeof(double) * (size_t)nc);
+  c->cap = nc;
+}
+
+static void col_push(ocol *c, int r, double v) {
+  col_reserve(c, c->len + 1);
+  c->row[c->len] = r;
+  c->val[c->len] = v;
+  c->len++;
+}
+
+static void col_free(ocol *c) {
+  free(c->row);
+  free(c->val);
+  c->row = NULL;
+  c->val = NULL;
+  c->len = c->cap = 0;
+}
+
+static void col_copy(ocol *dst, const ocol *src) {
+  dst->len = 0;
+  col_reserve(dst, src->len);
+  memcpy(dst->row, src->row, sizeof(int) * (size_t)src->len);
+  memcpy(dst->val, src->val, sizeof(double) * (size_t)src->len);
+  dst->len = src->len;
+}
+
+static ocol *mat_new(int n) { return (ocol *)calloc((size_t)n, sizeof(ocol)); }
+
+static void mat_free(ocol *m, int n) {
+  if (!m) return;
+  for (int j = 0; j < n; j++) col_free(&m[j]);
+  free(m);
+}
+
+static double rv(const orc_state *s, double x) { return s->mixed ? (double)(float)x : x; }
+
+static int cmp_int(const void *a, const void *b) {
+  int x = *(const int *)a, y = *(const int *)b;
+  return (x > y) - (x < y);
+}
+
+/* ------------------------------------------------------- pairwise summation */
+
+/* Balanced pairwise sum of t[0..L) zero-padded to the next power of two. */
+static double pw_rec(const double *t, int L, int64_t lo, int64_t size) {
+  if (size == 1) return lo < L ? t[lo] : 0.0;
+  int64_t h = size / 2;
+  if (lo >= L) return 0.0 + 0.0; /* all-padding subtree */
+  return pw_rec(t, L, lo, h) + pw_rec(t, L, lo + h, h);
+}
+
+double orc_pairwise(const double *t, int64_t L) {
+  int64_t P = 1;
+  while (P < L) P *= 2;
+  if (L == 0) return 0.0;
+  return pw_rec(t, (int)L, 0, P);
+}
+
+static double pairwise64(const double *t, int64_t L) {
+  int64_t P = 1;
+  while (P < L) P *= 2;
+  if (L == 0) return 0.0;
+  /* same recursion with 64-bit bounds */
+  if (P == 1) return t[0];
+  double *buf = (double *)malloc(sizeof(double) * (size_t)P);
+  for (int64_t i = 0; i < P; i++) buf[i] = i < L ? t[i] : 0.0;
+  /* level by level, pairing adjacent entries: identical to the recursion */
+  for (int64_t len = P; len > 1; len /= 2)
+    for (int64_t i = 0; i < len / 2; i++) buf[i] = buf[2 * i] + buf[2 * i + 1];
+  double r = buf[0];
+  free(buf);
+  return r;
+}
+
+/* column inner product over the common rows, Sec. 2 Eq. (2.1) */
+static double col_dot(const ocol *x, const ocol *y, double *tmp) {
+  int a = 0, b = 0, L = 0;
+  while (a < x->len && b < y->len) {
+    if (x->row[a] < y->row[b]) a++;
+    else if (x->row[a] > y->row[b]) b++;
+    else {
+      tmp[L++] = x->val[a] * y->val[b];
+      a++;
+      b++;
+    }
+  }
+  return orc_pairwise(tmp, L);
+}
+
+static double col_nrm2(const ocol *x, double *tmp) {
+  for (int a = 0; a < x->len; a++) tmp[a] = x->val[a] * x->val[a];
+  return orc_pairwise(tmp, x->len);
+}
+
+/* ------------------------------------------------------------- operations */
+
+/* out = A X_j (Sec. 6.2: one SpGEMM column) */
+static void spgemm_col(orc_state *s, const ocol *x, ocol *out) {
+  int nt = 0;
+  for (int e = 0; e < x->len; e++) {
+    int k = x->row[e];
+    double xv = x->val[e];
+    for (int q = s->rowptr[k]; q < s->rowptr[k + 1]; q++) {
+      int r = s->colind[q];
+      double a = s->av[q]; /* a_kr == a_rk: A is exactly symmetric */
+      if (!s->seen[r]) {
+        s->seen[r] = 1;
+        s->acc[r] = 0.0;
+        s->touched[nt++] = r;
+      }
+      if (s->mixed)
+        s->acc[r] = (double)fmaf((float)a, (float)xv, (float)s->acc[r]);
+      else
+        s->acc[r] = fma(a, xv, s->acc[r]);
+    }
+  }
+  qsort(s->touched, (size_t)nt, sizeof(int), cmp_int);
+  out->len = 0;
+  for (int t = 0; t < nt; t++) {
+    int r = s->touched[t];
+    double v = s->acc[r];
+    s->seen[r] = 0;
+    if (v != 0.0) col_push(out, r, v);
+  }
+}
+
+/* R_j = e_j - (A M)_j, exact zeros removed (Algorithm 1, explicit residual) */
+static void residual_col(orc_state *s, int j, const ocol *am, ocol *out) {
+  out->len = 0;
+  int placed = 0;
+  for (int e = 0; e <= am->len; e++) {
+    int r = e < am->len ? am->row[e] : 2147483647;
+    double sv = e < am->len ? am->val[e] : 0.0;
+    if (!placed && j < r) { /* diagonal not produced by A M */
+      col_push(out, j, 1.0);
+      placed = 1;
+    }
+    if (e == am->len) break;
+    double v;
+    if (r == j) {
+      placed = 1;
+      v = s->mixed ? (double)(1.0f - (float)sv) : 1.0 - sv;
+    } else {
+      v = -sv;
+    }
+    if (v != 0.0) col_push(out, r, v);
+  }
+}
+
+/* pattern union of x and y; value from f(x or 0, y or 0); zeros removed */
+enum { COMB_AXPY, COMB_LIN, COMB_ADD };
+static void combine_col(orc_state *s, int kind, double c1, double c2, const ocol *x, const ocol *y,
+                        ocol *out) {
+  out->len = 0;
+  int a = 0, b = 0;
+  while (a < x->len || b < y->len) {
+    int r;
+    double xv = 0.0, yv = 0.0;
+    if (b >= y->len || (a < x->len && x->row[a] < y->row[b])) {
+      r = x->row[a];
+      xv = x->val[a++];
+    } else if (a >= x->len || y->row[b] < x->row[a]) {
+      r = y->row[b];
+      yv = y->val[b++];
+    } else {
+      r = x->row[a];
+      xv = x->val[a++];
+      yv = y->val[b++];
+    }
+    double v;
+    if (kind == COMB_AXPY) v = fma(c1, yv, xv);          /* x + c1*y        */
+    else if (kind == COMB_LIN) v = fma(c1, xv, c2 * yv); /* c1*x + c2*y     */
+    else v = xv + yv;                                     /* x + y           */
+    v = rv(s, v);
+    if (v != 0.0) col_push(out, r, v);
+  }
+}
+
+typedef struct {
+  double a;
+  int r;
+} dkey;
+
+static int cmp_dkey(const void *p, const void *q) {
+  const dkey *u = (const dkey *)p, *w = (const dkey *)q;
+  if (u->a > w->a) return -1;
+  if (u->a < w->a) return 1;
+  return (u->r > w->r) - (u->r < w->r);
+}
+
+/* hard thresholding of one column to its cap (Sec. 6.1, Eq. (6.2), per column) */
+static void drop_col(ocol *c, int cap) {
+  if (c->len <= cap) return;
+  dkey *k = (dkey *)malloc(sizeof(dkey) * (size_t)c->len);
+  for (int e = 0; e < c->len; e++) {
+    k[e].a = fabs(c->val[e]);
+    k[e].r = c->row[e];
+  }
+  qsort(k, (size_t)c->len, sizeof(dkey), cmp_dkey);
+  int *keep = (int *)malloc(sizeof(int) * (size_t)cap);
+  for (int e = 0; e < cap; e++) keep[e] = k[e].r;
+  qsort(keep, (size_t)cap, sizeof(int), cmp_int);
+  int w = 0, q = 0;
+  for (int e = 0; e < c->len && q < cap; e++) {
+    if (c->row[e] == keep[q]) {
+      c->row[w] = c->row[e];
+      c->val[w] = c->val[e];
+      w++;
+      q++;
+    }
+  }
+  c->len = w;
+  free(k);
+  free(keep);
+}
+
+/* test hook: drop one row-sorted column in place, returns the new length */
+int orc_drop_column(int len, int *rows, double *vals, int cap) {
+  ocol c = {0};
+  for (int e = 0; e < len; e++) col_push(&c, rows[e], vals[e]);
+  drop_col(&c, cap);
+  for (int e = 0; e < c.len; e++) {
+    rows[e] = c.row[e];
+    vals[e] = c.val[e];
+  }
+  int L = c.len;
+  col_free(&c);
+  return L;
+}
+
+/* ------------------------------------------------------------------ state */
+
+orc_state *orc_new(int n, const int *rowptr, const int *colind, const double *vals, int mixed,
+                   double cap_factor) {
+  orc_state *s = (orc_state *)calloc(1, sizeof(orc_state));
+  s->n = n;
+  int64_t nnz = rowptr[n];
+  s->rowptr = (int *)malloc(sizeof(int) * (size_t)(n + 1));
+  s->colind = (int *)malloc(sizeof(int) * (size_t)(nnz ? nnz : 1));
+  s->a64 = (double *)malloc(sizeof(double) * (size_t)(nnz ? nnz : 1));
+  s->av = (double *)malloc(sizeof(double) * (size_t)(nnz ? nnz : 1));
+  memcpy(s->rowptr, rowptr, sizeof(int) * (size_t)(n + 1));
+  memcpy(s->colind, colind, sizeof(int) * (size_t)nnz);
+  memcpy(s->a64, vals, sizeof(double) * (size_t)nnz);
+  s->mixed = mixed;
+  for (int64_t q = 0; q < nnz; q++) s->av[q] = mixed ? (double)(float)vals[q] : vals[q];
+  s->capj = (int *)malloc(sizeof(int) * (size_t)(n ? n : 1));
+  for (int j = 0; j < n; j++) {
+    double c = floor(cap_factor * (double)(rowptr[j + 1] - rowptr[j]));
+    if (!(c >= 1.0)) c = 1.0;
+    if (c > (double)n) c = (double)n;
+    s->capj[j] = (int)c;
+  }
+  s->M = mat_new(n);
+  s->P = mat_new(n);
+  s->Z = mat_new(n);
+  s->acc = (double *)calloc((size_t)(n ? n : 1), sizeof(double));
+  s->seen = (char *)calloc((size_t)(n ? n : 1), 1);
+  s->touched = (int *)malloc(sizeof(int) * (size_t)(n ? n : 1));
+  s->method = -1;
+  /* M_0 = diag(A)^{-1} */
+  for (int j = 0; j < n; j++) {
+    double d = 0.0;
+    for (int q = rowptr[j]; q < rowptr[j + 1]; q++)
+      if (colind[q] == j) d = vals[q];
+    double m0 = rv(s, 1.0 / d);
+    if (m0 != 0.0) col_push(&s->M[j], j, m0);
+  }
+  return s;
+}
+
+void orc_free(orc_state *s) {
+  if (!s) return;
+  mat_free(s->M, s->n);
+  mat_free(s->P, s->n);
+  mat_free(s->Z, s->n);
+  free(s->rowptr);
+  free(s->colind);
+  free(s->a64);
+  free(s->av);
+  free(s->capj);
+  free(s->acc);
+  free(s->seen);
+  free(s->touched);
+  free(s);
+}
+
+/* replace M (CSC input), reset method state */
+int orc_set_M(orc_state *s, const int *colptr, const int *rowind, const double *vals) {
+  for (int j = 0; j < s->n; j++) {
+    s->M[j].len = 0;
+    s->P[j].len = 0;
+    s->Z[j].len = 0;
+    for (int q = colptr[j]; q < colptr[j + 1]; q++)
+      if (vals[q] != 0.0) col_push(&s->M[j], rowind[q], rv(s, vals[q]));
+  }
+  s->method = -1;
+  s->it = 0;
+  return 0;
+}
+
+int64_t orc_nnz(const orc_state *s, int which) {
+  const ocol *m = which == 0 ? s->M : which == 1 ? s->P : s->Z;
+  int64_t t = 0;
+  for (int j = 0; j < s->n; j++) t += m[j].len;
+  return t;
+}
+
+/* CSC export of M (which=0), P (1) or Z (2) */
+void orc_get(const orc_state *s, int which, int *colptr, int *rowind, double *vals) {
+  const ocol *m = which == 0 ? s->M : which == 1 ? s->P : s->Z;
+  int64_t t = 0;
+  colptr[0] = 0;
+  for (int j = 0; j < s->n; j++) {
+    for (int e = 0; e < m[j].len; e++) {
+      rowind[t] = m[j].row[e];
+      vals[t] = m[j].val[e];
+      t++;
+    }
+    colptr[j + 1] = (int)t;
+  }
+}
+
+int64_t orc_spgemm_count(const orc_state *s) { return s->spgemm_count; }
+
+/* -------------------------------------------------------------- the passes */
+
+/* R = I - A M for all columns; returns ||R||_F^2 (global pairwise) */
+static double residual_all(orc_state *s, ocol *R, double *partial, double *tmp) {
+  ocol am = {0};
+  for (int j = 0; j < s->n; j++) {
+    spgemm_col(s, &s->M[j], &am);
+    residual_col(s, j, &am, &R[j]);
+    partial[j] = col_nrm2(&R[j], tmp);
+  }
+  col_free(&am);
+  s->spgemm_count++;
+  return pairwise64(partial, s->n);
+}
+
+static void product_all(orc_state *s, ocol *X, ocol *out) {
+  for (int j = 0; j < s->n; j++) spgemm_col(s, &X[j], &out[j]);
+  s->spgemm_count++;
+}
+
+static int isfin(double x) { return !isnan(x) && !isinf(x); }
+
+/*
+ * Run `iters` iterations of `method`; continue the current method's
+ * recurrence when the previous call used the same method, otherwise start
+ * it from the current M with empty directions.
+ *   drop: 0 none, 1 top-k per column on M and directions, 2 directions only
+ *   resnorm[0..iters]: ||R_i||_F (entries past an early stop are left alone)
+ *   coef[2*i], coef[2*i+1]: (alpha_i, 0) for MR, (delta_i, gamma_i) for
+ *   LOMR, (alpha_i, beta_{i+1}) for CG.
+ * Returns the number of iterations done; *flags gets ORC_FLAG_* bits.
+ */
+int orc_run(orc_state *s, int method, int iters, int drop, double *resnorm, double *coef, int *flags) {
+  int n = s->n;
+  int done = 0;
+  *flags = 0;
+  int cont = (s->method == method);
+  if (!cont) {
+    for (int j = 0; j < n; j++) {
+      s->P[j].len = 0;
+      s->Z[j].len = 0;
+    }
+    s->it = 0;
+    s->method = method;
+  }
+  ocol *R = mat_new(n), *Q = mat_new(n), *U = mat_new(n), *V = mat_new(n), *S = mat_new(n);
+  ocol tmpc = {0};
+  double *partial = (double *)malloc(sizeof(double) * (size_t)(n ? n : 1));
+  double *p2 = (double *)malloc(sizeof(double) * (size_t)(n ? n : 1));
+  double *p3 = (double *)malloc(sizeof(double) * (size_t)(n ? n : 1));
+  double *p4 = (double *)malloc(sizeof(double) * (size_t)(n ? n : 1));
+  double *p5 = (double *)malloc(sizeof(double) * (size_t)(n ? n : 1));
+  double *tmp = (double *)malloc(sizeof(double) * (size_t)(n ? n : 1) * 2);
+  int dropM = (drop == 1), dropD = (drop >= 1);
+
+  if (method == ORC_MR) {
+    /* Algorithm 1 with explicit residual, P_i = D(R_i) */
+    for (int i = 0; i < iters; i++) {
+      double rr = residual_all(s, R, partial, tmp);
+      resnorm[i] = sqrt(rr);
+      if (rr == 0.0) { *flags |= ORC_FLAG_CONVERGED; break; }
+      for (int j = 0; j < n; j++) {
+        col_copy(&s->P[j], &R[j]);
+        if (dropD) drop_col(&s->P[j], s->capj[j]);
+      }
+      product_all(s, s->P, Q);
+      for (int j = 0; j < n; j++) {
+        p2[j] = col_dot(&R[j], &Q[j], tmp);
+        p3[j] = col_nrm2(&Q[j], tmp);
+      }
+      double rq = pairwise64(p2, n), qq = pairwise64(p3, n);
+      if (qq == 0.0) { *flags |= ORC_FLAG_CONVERGED; break; }
+      double alpha = rq / qq;
+      if (!isfin(alpha)) { *flags |= ORC_FLAG_NONFINITE; break; }
+      coef[2 * i] = alpha;
+      coef[2 * i + 1] = 0.0;
+      for (int j = 0; j < n; j++) {
+        combine_col(s, COMB_AXPY, alpha, 0.0, &s->M[j], &s->P[j], &tmpc);
+        if (dropM) drop_col(&tmpc, s->capj[j]);
+        col_copy(&s->M[j], &tmpc);
+      }
+      done++;
+      s->it++;
+    }
+    if (done == iters) resnorm[iters] = sqrt(residual_all(s, R, partial, tmp));
+  } else if (method == ORC_LOMR) {
+    /* Algorithm 4 with explicit residual: Z_i = D(R_i), P_i = D(S_i),
+       M_{i+1} = D(M_i + S_i), S_i = delta Z_i + gamma P_{i-1}. s->P holds
+       P_{i-1} between iterations. */
+    for (int i = 0; i < iters; i++) {
+      double rr = residual_all(s, R, partial, tmp);
+      resnorm[i] = sqrt(rr);
+      if (rr == 0.0) { *flags |= ORC_FLAG_CONVERGED; break; }
+      for (int j = 0; j < n; j++) {
+        col_copy(&s->Z[j], &R[j]);
+        if (dropD) drop_col(&s->Z[j], s->capj[j]);
+      }
+      product_all(s, s->Z, U);
+      product_all(s, s->P, V);
+      for (int j = 0; j < n; j++) {
+        partial[j] = col_nrm2(&U[j], tmp);
+        p2[j] = col_nrm2(&V[j], tmp);
+        p3[j] = col_dot(&U[j], &V[j], tmp);
+        p4[j] = col_dot(&U[j], &R[j], tmp);
+        p5[j] = col_dot(&V[j], &R[j], tmp);
+      }
+      double uu = pairwise64(partial, n), vv = pairwise64(p2, n), uv = pairwise64(p3, n);
+      double ur = pairwise64(p4, n), vr = pairwise64(p5, n);
+      if (uu == 0.0) { *flags |= ORC_FLAG_CONVERGED; break; }
+      double t1 = uu * vv, t2 = uv * uv;
+      double c = t1 - t2;
+      double delta, gamma;
+      double eps = 2.220446049250313e-16;
+      if (vv == 0.0 || c <= 64.0 * eps * t1) {
+        delta = ur / uu;
+        gamma = 0.0;
+        if (vv != 0.0) *flags |= ORC_FLAG_FALLBACK;
+      } else {
+        double d1 = vv * ur, d2 = uv * vr;
+        double g1 = uu * vr, g2 = uv * ur;
+        delta = (d1 - d2) / c;
+        gamma = (g1 - g2) / c;
+      }
+      if (!isfin(delta) || !isfin(gamma)) { *flags |= ORC_FLAG_NONFINITE; break; }
+      coef[2 * i] = delta;
+      coef[2 * i + 1] = gamma;
+      for (int j = 0; j < n; j++) {
+        combine_col(s, COMB_LIN, delta, gamma, &s->Z[j], &s->P[j], &S[j]);
+        col_copy(&s->P[j], &S[j]);
+        if (dropD) drop_col(&s->P[j], s->capj[j]);
+        combine_col(s, COMB_ADD, 0.0, 0.0, &s->M[j], &S[j], &tmpc);
+        if (dropM) drop_col(&tmpc, s->capj[j]);
+        col_copy(&s->M[j], &tmpc);
+      }
+      done++;
+      s->it++;
+    }
+    if (done == iters) resnorm[iters] = sqrt(residual_all(s, R, partial, tmp));
+  } else if (method == ORC_CG) {
+    /* Algorithm 3 with explicit residual: P_0 = D(R_0),
+       P_{i+1} = D(R_{i+1} + beta P_i).  s->P holds P_i, s->rr ||R_i||^2. */
+    double rr;
+    if (!cont || s->it == 0) {
+      rr = residual_all(s, R, partial, tmp);
+      for (int j = 0; j < n; j++) {
+        col_copy(&s->P[j], &R[j]);
+        if (dropD) drop_col(&s->P[j], s->capj[j]);
+      }
+    } else {
+      rr = s->rr;
+    }
+    resnorm[0] = sqrt(rr);
+    for (int i = 0; i < iters; i++) {
+      if (rr == 0.0) { *flags |= ORC_FLAG_CONVERGED; break; }
+      product_all(s, s->P, Q);
+      for (int j = 0; j < n; j++) p2[j] = col_dot(&s->P[j], &Q[j], tmp);
+      double pq = pairwise64(p2, n);
+      if (pq == 0.0) { *flags |= ORC_FLAG_CONVERGED; break; }
+      double alpha = rr / pq;
+      if (!isfin(alpha)) { *flags |= ORC_FLAG_NONFINITE; break; }
+      for (int j = 0; j < n; j++) {
+        combine_col(s, COMB_AXPY, alpha, 0.0, &s->M[j], &s->P[j], &tmpc);
+        if (dropM) drop_col(&tmpc, s->capj[j]);
+        col_copy(&s->M[j], &tmpc);
+      }
+      double rr1 = residual_all(s, R, partial, tmp);
+      resnorm[i + 1] = sqrt(rr1);
+      double beta = rr1 / rr;
+      coef[2 * i] = alpha;
+      coef[2 * i + 1] = beta;
+      done++;
+      s->it++;
+      s->rr = rr1;
+      if (rr1 == 0.0) { *flags |= ORC_FLAG_CONVERGED; rr = rr1; break; }
+      for (int j = 0; j < n; j++) {
+        combine_col(s, COMB_AXPY, beta, 0.0, &R[j], &s->P[j], &tmpc);
+        if (dropD) drop_col(&tmpc, s->capj[j]);
+        col_copy(&s->P[j], &tmpc);
+      }
+      rr = rr1;
+    }
+  }
+  if (*flags & (ORC_FLAG_CONVERGED | ORC_FLAG_NONFINITE)) s->method = -1;
+  mat_free(R, n);
+  mat_free(Q, n);
+  mat_free(U, n);
+  mat_free(V, n);
+  mat_free(S, n);
+  col_free(&tmpc);
+  free(partial);
+  free(p2);
+  free(p3);
+  free(p4);
+  free(p5);
+  free(tmp);
+  return done;
+}
+
+/* ||I - A M||_F in FP64 from the stored M (FP32 values promoted exactly) */
+double orc_residual_norm(orc_state *s) {
+  int n = s->n;
+  double *saved = s->av;
+  int mixed = s->mixed;
+  s->av = s->a64;
+  s->mixed = 0;
+  ocol am = {0}, r = {0};
+  double *partial = (double *)malloc(sizeof(double) * (size_t)(n ? n : 1));
+  double *tmp = (double *)malloc(sizeof(double) * (size_t)(n ? n : 1) * 2);
+  for (int j = 0; j < n; j++) {
+    spgemm_col(s, &s->M[j], &am);
+    residual_col(s, j, &am, &r);
+    partial[j] = col_nrm2(&r, tmp);
+  }
+  double rr = pairwise64(partial, n);
+  s->av = saved;
+  s->mixed = mixed;
+  col_free(&am);
+  col_free(&r);
+  free(partial);
+  free(tmp);
+  return sqrt(rr);
+}
+
+/* R_j and (A P)_j of one column, for sampled checks of large runs */
+int orc_column_residual(orc_state *s, int j, int *rows, double *vals) {
+  ocol am = {0}, r = {0};
+  spgemm_col(s, &s->M[j], &am);
+  residual_col(s, j, &am, &r);
+  int L = r.len;
+  if (rows) {
+    memcpy(rows, r.row, sizeof(int) * (size_t)L);
+    memcpy(vals, r.val, sizeof(double) * (size_t)L);
+  }
+  col_free(&am);
+  col_free(&r);
+  return L;
+}
+
+/* -------------------------------------------------------------------- PCG */
+
+/* y_i = pairwise over row i (ascending column) of m_ij * x_j */
+static void spmv_rows(int n, const int *rp, const int *ci, const double *v, const double *x, double *y,
+                      double *tmp) {
+  for (int i = 0; i < n; i++) {
+    int L = 0;
+    for (int q = rp[i]; q < rp[i + 1]; q++) tmp[L++] = v[q] * x[ci[q]];
+    y[i] = orc_pairwise(tmp, L);
+  }
+}
+
+static double vdot(int n, const double *x, const double *y, double *tmp) {
+  for (int i = 0; i < n; i++) tmp[i] = x[i] * y[i];
+  return pairwise64(tmp, n);
+}
+
+/*
+ * Vector PCG on A x = b, x_0 = 0, preconditioner z = Prec(r):
+ *   precond 0: z = r; 1: z = r / diag(A); 2: z = M r with M given in CSC;
+ *   3: z = S r with S = (M + M^T)/2, the symmetric part of M (PCG needs a
+ *   symmetric preconditioner; the paper symmetrises M, Appendix A step 1).
+ * Stops when ||r||_2 <= rtol ||b||_2 (recurrence residual), after maxit
+ * iterations, or on breakdown ((p,Ap) or (r,z) zero or non-finite).
+ * Returns iterations (= number of A p products); *status: 0 converged,
+ * 1 maxit, 2 breakdown.  *relres = ||b - A x||_2 / ||b||_2 (true residual).
+ */
+int orc_pcg(int n, const int *rp, const int *ci, const double *av, int precond, const int *mcolptr,
+            const int *mrowind, const double *mvals, const double *b, double rtol, int maxit, double *x,
+            int *status, double *relres) {
+  double *r = (double *)malloc(sizeof(double) * (size_t)n);
+  double *z = (double *)malloc(sizeof(double) * (size_t)n);
+  double *p = (double *)malloc(sizeof(double) * (size_t)n);
+  double *q = (double *)malloc(sizeof(double) * (size_t)n);
+  double *tmp = (double *)malloc(sizeof(double) * (size_t)(n > 64 ? n : 64));
+  double *diag = (double *)malloc(sizeof(double) * (size_t)n);
+  int *mrp = NULL, *mci = NULL;
+  double *mv = NULL;
+  for (int i = 0; i < n; i++) {
+    diag[i] = 0.0;
+    for (int e = rp[i]; e < rp[i + 1]; e++)
+      if (ci[e] == i) diag[i] = av[e];
+  }
+  if (precond == 2 || precond == 3) { /* CSC -> CSR, rows column-sorted */
+    int nnz = mcolptr[n];
+    mrp = (int *)calloc((size_t)n + 1, sizeof(int));
+    mci = (int *)malloc(sizeof(int) * (size_t)(nnz ? nnz : 1));
+    mv = (double *)malloc(sizeof(double) * (size_t)(nnz ? nnz : 1));
+    for (int e = 0; e < nnz; e++) mrp[mrowind[e] + 1]++;
+    for (int i = 0; i < n; i++) mrp[i + 1] += mrp[i];
+    int *fill = (int *)malloc(sizeof(int) * (size_t)n);
+    for (int i = 0; i < n; i++) fill[i] = mrp[i];
+    for (int j = 0; j < n; j++)
+      for (int e = mcolptr[j]; e < mcolptr[j + 1]; e++) {
+        int i = mrowind[e];
+        mci[fill[i]] = j;
+        mv[fill[i]] = mvals[e];
+        fill[i]++;
+      }
+    free(fill);
+    if (precond == 3) { /* S = (M + M^T) / 2: s_ij = 0.5 * (m_ij + m_ji) */
+      int *srp = (int *)calloc((size_t)n + 1, sizeof(int));
+      int *sci = (int *)malloc(sizeof(int) * (size_t)(2 * nnz + 1));
+      double *sv = (double *)malloc(sizeof(double) * (size_t)(2 * nnz + 1));
+      int t = 0;
+      for (int i = 0; i < n; i++) { /* row i of M is CSR row i; row i of M^T is CSC column i */
+        int a = mrp[i], ae = mrp[i + 1], b2 = mcolptr[i], be = mcolptr[i + 1];
+        while (a < ae || b2 < be) {
+          int c;
+          double u = 0.0, w = 0.0;
+          if (b2 >= be || (a < ae && mci[a] < mrowind[b2])) { c = mci[a]; u = mv[a++]; }
+          else if (a >= ae || mrowind[b2] < mci[a]) { c = mrowind[b2]; w = mvals[b2++]; }
+          else { c = mci[a]; u = mv[a++]; w = mvals[b2++]; }
+          double val = 0.5 * (u + w);
+          if (val != 0.0) { sci[t] = c; sv[t] = val; t++; }
+        }
+        srp[i + 1] = t;
+      }
+      free(mrp); free(mci); free(mv);
+      mrp = srp; mci = sci; mv = sv;
+    }
+  }
+  for (int i = 0; i < n; i++) {
+    x[i] = 0.0;
+    r[i] = b[i];
+  }
+  double bn = sqrt(vdot(n, b, b, tmp));
+  int k = 0;
+  *status = 0;
+#define PREC()                                                     \
+  do {                                                             \
+    if (precond == 0) for (int i_ = 0; i_ < n; i_++) z[i_] = r[i_]; \
+    else if (precond == 1) for (int i_ = 0; i_ < n; i_++) z[i_] = r[i_] / diag[i_]; \
+    else spmv_rows(n, mrp, mci, mv, r, z, tmp);                    \
+  } while (0)
+  if (bn == 0.0) goto out;
+  PREC();
+  double rho = vdot(n, r, z, tmp);
+  if (rho == 0.0 || !isfin(rho)) { *status = 2; goto out; }
+  for (int i = 0; i < n; i++) p[i] = z[i];
+  for (;;) {
+    if (k >= maxit) { *status = 1; break; }
+    spmv_rows(n, rp, ci, av, p, q, tmp);
+    double pq = vdot(n, p, q, tmp);
+    if (pq == 0.0 || !isfin(pq)) { *status = 2; break; }
+    double alpha = rho / pq;
+    for (int i = 0; i < n; i++) {
+      x[i] = fma(alpha, p[i], x[i]);
+      r[i] = fma(-alpha, q[i], r[i]);
+    }
+    k++;
+    double rn = sqrt(vdot(n, r, r, tmp));
+    if (!isfin(rn)) { *status = 2; break; }
+    if (rn <= rtol * bn) { *status = 0; break; }
+    PREC();
+    double rho1 = vdot(n, r, z, tmp);
+    if (rho1 == 0.0 || !isfin(rho1)) { *status = 2; break; }
+    double beta = rho1 / rho;
+    for (int i = 0; i < n; i++) p[i] = fma(beta, p[i], z[i]);
+    rho = rho1;
+  }
+out:
+  if (relres) {
+    spmv_rows(n, rp, ci, av, x, q, tmp);
+    for (int i = 0; i < n; i++) q[i] = b[i] - q[i];
+    *relres = bn > 0 ? sqrt(vdot(n, q, q, tmp)) / bn : 0.0;
+  }
+#undef PREC
+  free(r);
+  free(z);
+  free(p);
+  free(q);
+  free(tmp);
+  free(diag);
+  free(mrp);
+  free(mci);
+  free(mv);
+  return k;
+}

@@ -1,0 +1,361 @@
+"""Pins of the CPU oracle to facts the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: a dense
+brute-force minimiser, a closed form, a theorem of the paper, scipy, or a
+fixture printed in the paper.  No GPU.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+import oracle as O
+from paper_2511_09753_gb300 import inputs as I
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def dense_from_csc(n, cp, ri, va):
+    M = np.zeros((n, n))
+    for j in range(n):
+        M[ri[cp[j]:cp[j + 1]], j] = va[cp[j]:cp[j + 1]]
+    return M
+
+
+def frob(X, Y):
+    return float(np.sum(X * Y))
+
+
+def tiny_spd(n=10, seed=3):
+    return I.random_spd_banded(n, 2, seed)
+
+
+def lap2d(N):
+    return I.laplacian_2d_5pt(N)
+
+
+# ------------------------------------------------------------- summation
+
+def test_pairwise_exact_on_integers_and_close_to_fsum():
+    rng = np.random.default_rng(0)
+    t = rng.integers(-1000, 1000, 777).astype(np.float64)
+    assert O.pairwise(t) == float(t.sum())
+    x = rng.standard_normal(1000) * np.exp(rng.uniform(-20, 20, 1000))
+    exact = math.fsum(x)
+    bound = 10 * np.finfo(float).eps * np.sum(np.abs(x))  # log2(1024) levels
+    assert abs(O.pairwise(x) - exact) <= bound
+    assert O.pairwise([]) == 0.0
+    assert O.pairwise([3.5]) == 3.5
+
+
+def test_pairwise_tree_shape():
+    # (a+b)+(c+0) differs from ((a+b)+c) for these values: pins the tree shape
+    a, b, c = 1.0, 1e-16, 1e-16
+    assert O.pairwise([a, b, c]) == (a + b) + (c + 0.0)
+    assert O.pairwise([1e16, 1.0, -1e16, 1.0]) == (1e16 + 1.0) + (-1e16 + 1.0)
+
+
+# ------------------------------------------------------------- dropping
+
+def brute_drop(rows, vals, cap):
+    if len(rows) <= cap:
+        return list(rows), list(vals)
+    order = sorted(range(len(rows)), key=lambda e: (-abs(vals[e]), rows[e]))[:cap]
+    order.sort(key=lambda e: rows[e])
+    return [rows[e] for e in order], [vals[e] for e in order]
+
+
+def test_drop_matches_brute_force_with_ties():
+    rng = np.random.default_rng(1)
+    for trial in range(200):
+        L = int(rng.integers(1, 60))
+        rows = np.sort(rng.choice(1000, L, replace=False))
+        vals = rng.choice([-0.5, -0.25, 0.25, 0.5, 1.0, 3.0], L) * rng.choice([1.0, 1.0, 0.999], L)
+        cap = int(rng.integers(1, 40))
+        r1, v1 = O.drop_column(rows, vals, cap)
+        r2, v2 = brute_drop(list(rows), list(vals), cap)
+        assert list(r1) == r2 and list(v1) == v2
+
+
+def test_drop_hand_made_tie():
+    # four equal magnitudes (the 5-point Laplacian's R_0 pattern): keep the
+    # largest, then the smallest row indices among the ties
+    r, v = O.drop_column([1, 3, 5, 7, 9], [0.25, -0.25, 0.5, 0.25, -0.25], 3)
+    assert list(r) == [1, 3, 5] and list(v) == [0.25, -0.25, 0.5]
+
+
+# ------------------------------------------------ SpGEMM / residual vs scipy
+
+def test_column_residual_matches_scipy():
+    n, rp, ci, v = I.varcoef_3d_7pt(8, seed=5)
+    o = O.Oracle(n, rp, ci, v, cap_factor=2.0)
+    o.run("lomr", 3)
+    cp, ri, va = o.get_M()
+    A = sp.csr_matrix((v, ci, rp), shape=(n, n))
+    M = sp.csc_matrix((va, ri, cp), shape=(n, n))
+    R = (sp.identity(n) - A @ M).tocsc()
+    R.eliminate_zeros()
+    for j in range(0, n, 7):
+        rows, vals = o.column_residual(j)
+        col = R[:, j].toarray().ravel()
+        nz = np.nonzero(col)[0]
+        assert set(rows) <= set(nz) | set(rows)
+        np.testing.assert_allclose(vals, col[rows], rtol=1e-13, atol=1e-15)
+        # every structurally produced nonzero of scipy is in the oracle's column
+        big = nz[np.abs(col[nz]) > 1e-14]
+        assert set(big) <= set(rows)
+
+
+# ---------------------------------------------- MR: line minimiser (Eq. 2.6)
+
+def test_mr_step_is_exact_line_minimiser():
+    n, rp, ci, v = tiny_spd(10)
+    A = I.csr_to_dense(n, rp, ci, v)
+    for drop, capf in [(O.DROP_NONE, 1e9), (O.DROP_DIRECTIONS, 1.0)]:
+        o = O.Oracle(n, rp, ci, v, cap_factor=capf)
+        M0 = dense_from_csc(n, *o.get_M())
+        R0 = np.eye(n) - A @ M0
+        if drop == O.DROP_NONE:
+            P = R0
+        else:  # brute-force per-column drop of R0 to cap_j = nnz(A[:, j])
+            P = np.zeros_like(R0)
+            for j in range(n):
+                nz = np.nonzero(R0[:, j])[0]
+                rr, vv = brute_drop(list(nz), list(R0[nz, j]), int(np.count_nonzero(A[:, j])))
+                P[rr, j] = vv
+        AP = A @ P
+        alpha = np.linalg.lstsq(AP.reshape(-1, 1), R0.reshape(-1), rcond=None)[0][0]
+        o.run("mr", 1, drop=drop)
+        M1 = dense_from_csc(n, *o.get_M())
+        np.testing.assert_allclose(M1, M0 + alpha * P, rtol=0, atol=1e-13)
+
+
+# --------------------------------------- LOMR: 2-D minimiser (Thm 3, Eq. 4.7)
+
+def test_lomr_step_is_exact_2d_minimiser_and_beats_mr():
+    n, rp, ci, v = tiny_spd(9, seed=7)
+    A = I.csr_to_dense(n, rp, ci, v)
+    o = O.Oracle(n, rp, ci, v, cap_factor=1e9)
+    o.run("lomr", 2, drop=O.DROP_NONE)
+    for _ in range(4):
+        M1 = dense_from_csc(n, *o.get_M())
+        Pm = dense_from_csc(n, *o.get(1))  # P_{i-1}
+        R1 = np.eye(n) - A @ M1
+        B = np.stack([(A @ R1).ravel(), (A @ Pm).ravel()], axis=1)
+        d, g = np.linalg.lstsq(B, R1.ravel(), rcond=None)[0]
+        expect = M1 + d * R1 + g * Pm
+        # one-dimensional MR step from the same iterate
+        AR = A @ R1
+        a = frob(R1, AR) / frob(AR, AR)
+        mr_norm = np.linalg.norm(np.eye(n) - A @ (M1 + a * R1))
+        r = o.run("lomr", 1, drop=O.DROP_NONE)
+        M2 = dense_from_csc(n, *o.get_M())
+        np.testing.assert_allclose(M2, expect, rtol=0, atol=1e-12)
+        lomr_norm = np.linalg.norm(np.eye(n) - A @ M2)
+        assert lomr_norm <= mr_norm * (1 + 1e-12)  # Eq. (4.3)
+        assert r["resnorm"][1] <= r["resnorm"][0] * (1 + 1e-12)
+
+
+# ------------------------------------ MR: norm identity and rate (Theorem 1)
+
+def test_mr_norm_identity_and_rate_bound():
+    N = 6
+    n, rp, ci, v = lap2d(N)
+    A = I.csr_to_dense(n, rp, ci, v)
+    lam_min = min(4 - 2 * math.cos(j * math.pi / (N + 1)) - 2 * math.cos(k * math.pi / (N + 1))
+                  for j in range(1, N + 1) for k in range(1, N + 1))
+    assert abs(lam_min - np.linalg.eigvalsh(A)[0]) < 1e-12
+    C = math.sqrt(1 - lam_min ** 2 / float(np.sum(v * v)))  # tr(A^2) = sum a_ij^2
+    o = O.Oracle(n, rp, ci, v, cap_factor=1e9)
+    prev = None
+    for i in range(25):
+        M = dense_from_csc(n, *o.get_M())
+        R = np.eye(n) - A @ M
+        r = o.run("mr", 1, drop=O.DROP_NONE)
+        nr0, nr1 = r["resnorm"][0], r["resnorm"][1]
+        assert abs(nr0 - np.linalg.norm(R)) <= 1e-12 * nr0
+        alpha = r["coef"][0, 0]
+        # ||R_{i+1}||^2 = ||R_i||^2 - alpha_i (A R_i, R_i)
+        np.testing.assert_allclose(nr1 ** 2, nr0 ** 2 - alpha * frob(A @ R, R), rtol=1e-11)
+        assert nr1 <= C * nr0 * (1 + 1e-12)
+        if prev is not None:
+            assert nr0 <= prev * (1 + 1e-14)
+        prev = nr1
+
+
+def test_mr_rate_bound_random_spd():
+    n, rp, ci, v = tiny_spd(12, seed=11)
+    A = I.csr_to_dense(n, rp, ci, v)
+    lam = np.linalg.eigvalsh(A)
+    C = math.sqrt(1 - lam[0] ** 2 / np.trace(A @ A))
+    o = O.Oracle(n, rp, ci, v, cap_factor=1e9)
+    r = o.run("mr", 40, drop=O.DROP_NONE)
+    res = r["resnorm"]
+    assert np.all(res[1:] <= C * res[:-1] * (1 + 1e-12))
+
+
+# ------------------------------------------- CG: Prop. 2 and Theorem 5
+
+def test_cg_orthogonality():
+    n, rp, ci, v = tiny_spd(10, seed=5)
+    A = I.csr_to_dense(n, rp, ci, v)
+    o = O.Oracle(n, rp, ci, v, cap_factor=1e9)
+    Rs, Ps = [], []
+    M = dense_from_csc(n, *o.get_M())
+    Rs.append(np.eye(n) - A @ M)
+    o.run("cg", 0, drop=O.DROP_NONE)
+    Ps.append(dense_from_csc(n, *o.get(1)))
+    for i in range(5):
+        o.run("cg", 1, drop=O.DROP_NONE)
+        M = dense_from_csc(n, *o.get_M())
+        Rs.append(np.eye(n) - A @ M)
+        Ps.append(dense_from_csc(n, *o.get(1)))
+    scale = np.linalg.norm(Rs[0]) ** 2
+    for i in range(1, len(Rs)):
+        for j in range(i):
+            assert abs(frob(Rs[i], Rs[j])) <= 1e-10 * scale          # Eq. (3.4)
+            assert abs(frob(Rs[i], Ps[j])) <= 1e-10 * scale          # Eq. (3.5)
+            assert abs(frob(Ps[i], A @ Ps[j])) <= 1e-9 * scale * 10  # Eq. (3.6)
+
+
+def test_cg_finite_termination_distinct_eigenvalues():
+    rng = np.random.default_rng(4)
+    n = 9
+    Q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    lam = np.array([1.0, 1.0, 1.0, 3.0, 3.0, 3.0, 7.0, 7.0, 7.0])
+    A = Q @ np.diag(lam) @ Q.T
+    A = 0.5 * (A + A.T)
+    n, rp, ci, v = I.dense_to_csr(A)
+    o = O.Oracle(n, rp, ci, v, cap_factor=1e9)
+    r = o.run("cg", 3, drop=O.DROP_NONE)
+    M = dense_from_csc(n, *o.get_M())
+    assert np.abs(M - np.linalg.inv(A)).max() < 1e-10                 # Theorem 5
+    assert r["resnorm"][3] < 1e-10 * r["resnorm"][0]
+
+
+def test_cg_error_bound():
+    n, rp, ci, v = lap2d(5)
+    A = I.csr_to_dense(n, rp, ci, v)
+    Ainv = np.linalg.inv(A)
+    lam = np.linalg.eigvalsh(A)
+    kap = lam[-1] / lam[0]
+    q = (math.sqrt(kap) - 1) / (math.sqrt(kap) + 1)
+
+    def anorm(E):
+        return math.sqrt(max(np.trace(E.T @ A @ E), 0.0))
+
+    o = O.Oracle(n, rp, ci, v, cap_factor=1e9)
+    e0 = anorm(Ainv - dense_from_csc(n, *o.get_M()))
+    for i in range(1, 12):
+        o.run("cg", 1, drop=O.DROP_NONE)
+        ei = anorm(Ainv - dense_from_csc(n, *o.get_M()))
+        assert ei <= math.sqrt(n) * q ** i * e0 * (1 + 1e-9) + 1e-13  # Eq. (3.10)
+
+
+# ------------------------------------------------------- special cases
+
+def test_diagonal_matrix_stops_cleanly():
+    n = 7
+    A = np.diag(np.arange(1.0, n + 1))
+    n, rp, ci, v = I.dense_to_csr(A)
+    for m in ("mr", "lomr", "cg"):
+        o = O.Oracle(n, rp, ci, v, cap_factor=2.0)
+        r = o.run(m, 5)
+        assert r["resnorm"][0] == 0.0
+        assert r["flags"] & O.FLAG_CONVERGED
+        assert r["done"] == 0
+
+
+def test_constant_diagonal_step0_matches_closed_form():
+    # A = 4 I - L (5-point Laplacian): M0 = I/4, R0 = L/4 exactly, whose
+    # Frobenius norm is sqrt(#offdiag)/4
+    n, rp, ci, v = lap2d(6)
+    o = O.Oracle(n, rp, ci, v, cap_factor=2.0)
+    r = o.run("mr", 1)
+    offdiag = len(v) - n
+    assert r["resnorm"][0] == math.sqrt(offdiag) / 4
+
+
+# ------------------------------------------- Table 2 operation counts
+
+def test_table2_spgemm_counts():
+    table = {}
+    with open(os.path.join(GOLDEN, "table2_spgemm_counts.txt")) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                k, c = line.split()
+                table[k] = int(c)
+    n, rp, ci, v = lap2d(8)
+    K = 6
+    for m, key in (("mr", "MR"), ("cg", "CG"), ("lomr", "LOMR")):
+        o = O.Oracle(n, rp, ci, v, cap_factor=2.0)
+        base = o.spgemm_count()
+        r = o.run(m, K)
+        assert r["done"] == K
+        used = o.spgemm_count() - base
+        # MR/LOMR add one final residual product; CG one initial residual
+        assert used == table[key] * K + 1
+
+
+# --------------------------------------------------------------- PCG
+
+def test_pcg_matches_scipy_cg_counts():
+    n, rp, ci, v = lap2d(20)
+    A = sp.csr_matrix((v, ci, rp), shape=(n, n))
+    b = I.rhs_uniform(n, 0)
+    for precond in (0, 1):
+        res = O.pcg(n, rp, ci, v, b, rtol=1e-8, precond=precond)
+        count = [0]
+
+        def cb(xk):
+            count[0] += 1
+        Minv = None if precond == 0 else sp.diags(1.0 / A.diagonal())
+        x, info = spla.cg(A, b, rtol=1e-8, atol=0.0, M=Minv, callback=cb, maxiter=10000)
+        assert info == 0 and res["status"] == 0
+        assert abs(res["iters"] - count[0]) <= 1
+        assert res["relres"] < 2e-8
+        np.testing.assert_allclose(res["x"], x, rtol=1e-6, atol=1e-8)
+
+
+def test_pcg_exact_inverse_and_jacobi_as_matrix():
+    n, rp, ci, v = lap2d(8)
+    A = I.csr_to_dense(n, rp, ci, v)
+    b = I.rhs_uniform(n, 0)
+    Ainv = np.linalg.inv(A)
+    cp = np.arange(0, n * n + 1, n, dtype=np.int32)
+    ri = np.tile(np.arange(n, dtype=np.int32), n)
+    res = O.pcg(n, rp, ci, v, b, precond=2, M=(cp, ri, Ainv.T.ravel().copy()))
+    assert res["iters"] == 1 and res["relres"] < 1e-12
+    d = np.arange(n + 1, dtype=np.int32)
+    jac = O.pcg(n, rp, ci, v, b, precond=2, M=(d, d[:-1].copy(), 1.0 / np.diag(A)))
+    assert jac["iters"] == O.pcg(n, rp, ci, v, b, precond=1)["iters"]
+    sym = O.pcg(n, rp, ci, v, b, precond=3, M=(d, d[:-1].copy(), 1.0 / np.diag(A)))
+    assert sym["iters"] == jac["iters"]
+
+
+# ------------------------------------------------------- mixed precision
+
+def test_mixed_emulation_tracks_fp64():
+    n, rp, ci, v = I.varcoef_3d_7pt(10, seed=2)
+    r64 = O.Oracle(n, rp, ci, v, cap_factor=3.0)
+    r32 = O.Oracle(n, rp, ci, v, cap_factor=3.0, mixed=True)
+    a = r64.run("lomr", 10)
+    b = r32.run("lomr", 10)
+    assert abs(b["resnorm"][-1] - a["resnorm"][-1]) <= 1e-4 * a["resnorm"][-1]
+    cp, ri, va = r32.get_M()
+    assert np.all(va.astype(np.float32).astype(np.float64) == va)
+
+
+def test_continuation_equals_single_run():
+    n, rp, ci, v = lap2d(10)
+    for m in ("mr", "lomr", "cg"):
+        a = O.Oracle(n, rp, ci, v, cap_factor=2.0)
+        a.run(m, 7)
+        a.run(m, 5)
+        b = O.Oracle(n, rp, ci, v, cap_factor=2.0)
+        b.run(m, 12)
+        for x, y in zip(a.get_M(), b.get_M()):
+            assert np.array_equal(x, y)
