@@ -1,0 +1,195 @@
+/*
+ * spai.h -- C ABI of libspai.so: global short-recurrence sparse approximate
+ * inverses (MR, LOMR, Frobenius-CG) of an SPD matrix A on one GB300 GPU,
+ * and the vector PCG that assesses them as preconditioners.
+ *
+ * Problem (Venkovic & Anzt, Sec. 2, Eqs. (2.3)-(2.4)): find a sparse M with
+ * A M ~ I by decreasing f(M) = ||I - A M||_F^2 with global iterations whose
+ * sparse matrix iterates are updated as a whole.
+ *
+ * Conventions for every call:
+ *   - return 0 on success, > 0 for a non-fatal outcome, < 0 for an error;
+ *     spai_status_string() names each code; the library never aborts or
+ *     prints;
+ *   - the handle owns all device memory it allocates; pointers passed in are
+ *     only read or written during the call (or, for device pointers, by work
+ *     the call enqueues on the handle's stream);
+ *   - calls are ordered on the handle's CUDA stream and synchronise that
+ *     stream only where they return host data;
+ *   - a handle is not thread safe; distinct handles are independent;
+ *   - no call falls back to CPU computation: every numeric step runs in the
+ *     library's CUDA kernels.
+ *
+ * Storage of A: CSR, int32 row pointers and column indices (rows sorted by
+ * column, no duplicates), FP64 values; A must be exactly symmetric with a
+ * positive diagonal.  Storage of M on output: CSC (column pointers, row
+ * indices sorted within each column, values).
+ */
+#ifndef SPAI_H
+#define SPAI_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------- status codes */
+#define SPAI_OK 0
+#define SPAI_CONVERGED_EARLY 1   /* ||R_i||_F or a step denominator reached 0 */
+#define SPAI_LOMR_FALLBACK 2     /* LOMR took at least one MR step (c_i ~ 0) */
+#define SPAI_PCG_MAXIT 3         /* PCG stopped at maxit */
+#define SPAI_PCG_BREAKDOWN 4     /* PCG: (p,Ap) or (r,z) zero or non-finite */
+#define SPAI_ERR_ARG -1          /* bad argument (NULL, negative size, ...) */
+#define SPAI_ERR_CSR -2          /* malformed CSR (pointers, order, range) */
+#define SPAI_ERR_NOT_SPD_DIAG -3 /* missing or non-positive diagonal entry */
+#define SPAI_ERR_NOT_SYMMETRIC -4/* A is not exactly symmetric */
+#define SPAI_ERR_NONFINITE -5    /* NaN/Inf in A or in a step coefficient */
+#define SPAI_ERR_CUDA -6         /* a CUDA runtime call failed */
+#define SPAI_ERR_OOM -7          /* device allocation failed */
+#define SPAI_ERR_CAPACITY -8     /* a column outgrew its slab capacity */
+#define SPAI_ERR_UNSUPPORTED -9  /* size outside the kernels' limits */
+#define SPAI_ERR_STATE -10       /* saved state does not match the handle */
+
+/* --------------------------------------------------------------- options */
+enum { SPAI_FP64 = 0, SPAI_MIXED = 1 };           /* MIXED: FP32 values, FP64 reductions */
+enum { SPAI_MR = 0, SPAI_LOMR = 1, SPAI_CG = 2 };
+enum { SPAI_DROP_NONE = 0, SPAI_DROP_TOPK_COL = 1 };
+enum { SPAI_PREC_NONE = 0, SPAI_PREC_JACOBI = 1, SPAI_PREC_SPAI = 2, SPAI_PREC_SPAI_SYM = 3 };
+
+typedef struct spai_ctx *spai_handle;
+
+typedef struct {
+  int prec;          /* SPAI_FP64 or SPAI_MIXED */
+  double cap_factor; /* per-column capacity and drop cap:
+                        cap_j = floor(cap_factor * nnz(A[:,j])), clamped to [1, n] */
+} spai_opts;
+
+typedef struct {
+  double *resnorm;   /* host, [iters+1] or NULL: ||R_i||_F, i = 0..iters */
+  double *coef;      /* host, [2*iters] or NULL: (alpha,0) MR, (delta,gamma) LOMR,
+                        (alpha_i, beta_{i+1}) CG */
+  int iters_done;    /* out: iterations completed */
+  int flags;         /* out: bit0 converged early, bit1 LOMR fallback */
+} spai_history;
+
+typedef struct {
+  int64_t colpass_launches;   /* column-pass kernels launched since create */
+  int64_t colpass_bytes;      /* algorithmic DRAM bytes of those launches */
+  double colpass_ms;          /* their summed device time (timing mode only) */
+  int64_t pcg_launches;       /* PCG kernels launched since create */
+  int64_t other_launches;     /* set-up / transpose / norm kernels */
+  int64_t spgemm_columns;     /* column SpGEMMs performed (Table 2 check) */
+} spai_stats;
+
+/* ------------------------------------------------------------- host only */
+
+/* Validate a CSR matrix on the host without touching the GPU.
+ * Checks n >= 1, rowptr monotone with rowptr[0]=0 and rowptr[n]=nnz, column
+ * indices in [0,n) strictly increasing per row, finite values, a positive
+ * diagonal in every row and, if check_symmetry, exact symmetry.  Returns
+ * SPAI_OK or SPAI_ERR_CSR / SPAI_ERR_NOT_SPD_DIAG / SPAI_ERR_NOT_SYMMETRIC /
+ * SPAI_ERR_NONFINITE / SPAI_ERR_ARG. */
+int spai_validate_csr(int64_t n, int64_t nnz, const int32_t *rowptr, const int32_t *colind,
+                      const double *vals, int check_symmetry);
+
+/* Human-readable name of a status code (static string, never NULL). */
+const char *spai_status_string(int code);
+
+/* ---------------------------------------------------------------- handle */
+
+/* Create a handle for the SPD matrix A (n x n, nnz entries).
+ * rowptr/colind/vals are host pointers (on_device = 0) or device pointers
+ * (on_device = 1); A is validated (symmetry included) and copied, the caller
+ * keeps ownership.  stream: a cudaStream_t, or NULL for a stream the handle
+ * creates.  M is initialised to diag(A)^{-1} (Algorithm 1 with M_0 = D^{-1}).
+ * Column slabs of capacity cap_j are allocated for M and two directions.
+ * Limits: n < 2^31, max row length of A <= 64, cap_j * rowlen <= 65534. */
+int spai_create(spai_handle *out, int64_t n, int64_t nnz, const int32_t *rowptr,
+                const int32_t *colind, const double *vals, int on_device, const spai_opts *opts,
+                void *stream);
+
+/* Free every device and host resource of the handle. */
+int spai_destroy(spai_handle h);
+
+/* Re-initialise M := diag(A)^{-1} and forget the method recurrence. */
+int spai_reset(spai_handle h);
+
+/* Use another CUDA stream for subsequent calls. */
+int spai_set_stream(spai_handle h, void *stream);
+
+/* ---------------------------------------------------------- the methods */
+
+/* Run `iters` iterations of a method from the current M.  A call continues
+ * the recurrence of the previous call when it uses the same method (so
+ * k + l iterations in two calls equal k + l in one); otherwise the method
+ * starts from the current M with empty search directions.
+ *   MR   -- Algorithm 1, explicit residual: P_i = D(R_i),
+ *           alpha_i = (R_i, A P_i)_F / ||A P_i||_F^2 (Eq. 2.6),
+ *           M_{i+1} = D(M_i + alpha_i P_i).
+ *   LOMR -- Algorithm 4 / Theorem 3: Z_i = D(R_i), (delta_i, gamma_i) solve the
+ *           2x2 normal equations for span{A Z_i, A P_{i-1}} (Eqs. 4.7-4.9),
+ *           S_i = delta_i Z_i + gamma_i P_{i-1}, P_i = D(S_i), M_{i+1} = D(M_i + S_i);
+ *           a near-singular 2x2 system (c_i <= 64 eps uu vv) takes an MR step.
+ *   CG   -- Algorithm 3: alpha_i = ||R_i||^2/(P_i, A P_i), M_{i+1} = D(M_i + alpha_i P_i),
+ *           beta_{i+1} = ||R_{i+1}||^2/||R_i||^2, P_{i+1} = D(R_{i+1} + beta_{i+1} P_i).
+ * D is the per-column hard threshold of Sec. 6.1 (keep the cap_j largest |v|,
+ * ties to the smaller row; exact zeros never stored) for SPAI_DROP_TOPK_COL,
+ * or the identity for SPAI_DROP_NONE (a column that outgrows its capacity
+ * then fails the call with SPAI_ERR_CAPACITY).  R is always the explicit
+ * residual I - A M (Sec. 6.2).  hist may be NULL.  Returns SPAI_OK,
+ * SPAI_CONVERGED_EARLY, SPAI_LOMR_FALLBACK or an error. */
+int spai_run(spai_handle h, int method, int iters, int drop_rule, spai_history *hist);
+int spai_mr(spai_handle h, int iters, int drop_rule, spai_history *hist);
+int spai_lomr(spai_handle h, int iters, int drop_rule, spai_history *hist);
+int spai_cg(spai_handle h, int iters, int drop_rule, spai_history *hist);
+
+/* ||I - A M||_F computed in FP64 from the stored M (FP32 values promoted
+ * exactly), Eq. (2.4); written to *out (host). */
+int spai_residual_norm(spai_handle h, double *out);
+
+/* Number of stored nonzeros of M (host *out). */
+int spai_get_nnz(spai_handle h, int64_t *out);
+
+/* Export M in CSC.  Two-call use: with colptr == NULL only *nnz is set.
+ * Otherwise colptr[n+1], rowind[*nnz], vals[*nnz] (FP64) are filled; they are
+ * host arrays (on_device = 0) or device arrays (on_device = 1). */
+int spai_get_M(spai_handle h, int64_t *nnz, int32_t *colptr, int32_t *rowind, double *vals,
+               int on_device);
+
+/* Replace M by a CSC matrix (host or device arrays, rows sorted per column,
+ * column j holding at most cap_j entries) and forget the method recurrence. */
+int spai_set_M(spai_handle h, const int32_t *colptr, const int32_t *rowind, const double *vals,
+               int on_device);
+
+/* y = M x for nrhs right-hand sides stored column-major with leading
+ * dimension ld (>= n); x and y are FP64 device pointers.  Uses the row-wise
+ * (transposed) copy of M built on first use after M changes. */
+int spai_apply(spai_handle h, const double *x, double *y, int nrhs, int64_t ld);
+
+/* Vector PCG on A x = b (Sec. 7 assessment), x_0 = 0, FP64 vectors and
+ * scalars, stop when ||r||_2 <= rtol ||b||_2 (recurrence residual) or after
+ * maxit iterations.  precond: SPAI_PREC_NONE, SPAI_PREC_JACOBI,
+ * SPAI_PREC_SPAI (z = M r) or SPAI_PREC_SPAI_SYM (z = (M + M^T) r / 2).
+ * b, x: n-vectors, host (on_device = 0) or device (on_device = 1); nrhs = 1.
+ * *iters (host) = number of A p products; *relres (host, may be NULL) =
+ * ||b - A x||_2 / ||b||_2.  Returns SPAI_OK, SPAI_PCG_MAXIT,
+ * SPAI_PCG_BREAKDOWN or an error. */
+int pcg_solve(spai_handle h, const double *b, double *x, int nrhs, double rtol, int maxit,
+              int precond, int on_device, int *iters, double *relres);
+
+/* Checkpoint of the iteration state (M, directions, scalars, method and
+ * iteration index).  Two-call: with buf == NULL only *bytes is set. */
+int spai_save_state(spai_handle h, void *buf, size_t *bytes);
+int spai_load_state(spai_handle h, const void *buf, size_t bytes);
+
+/* Launch / byte / time counters; timing (CUDA events around each column
+ * pass, on the handle's stream) is recorded only while enabled. */
+int spai_set_timing(spai_handle h, int enable);
+int spai_get_stats(spai_handle h, spai_stats *out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SPAI_H */

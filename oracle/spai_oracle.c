@@ -38,6 +38,8 @@
  *   - combinations: M + a P -> fma(a, p, m);  S = d Z + g P -> fma(d, z, g*p);
  *     M + S -> m + s;  R + b P -> fma(b, p, r); all in FP64, then rounded to
  *     the value type;
+ *   - PCG: SpMV rows are fma chains over ascending column (as the SpGEMM);
+ *     vector inner products are pairwise trees over the index range;
  *   - mixed precision: stored values and A are FP32; the SpGEMM chain and the
  *     residual run in FP32; inner products, coefficients and combinations in
  *     FP64 (FP32 inputs promoted exactly).
@@ -654,13 +656,14 @@ int orc_column_residual(orc_state *s, int j, int *rows, double *vals) {
 
 /* -------------------------------------------------------------------- PCG */
 
-/* y_i = pairwise over row i (ascending column) of m_ij * x_j */
+/* y_i = fma chain over row i, ascending column: acc = fma(m_ij, x_j, acc) */
 static void spmv_rows(int n, const int *rp, const int *ci, const double *v, const double *x, double *y,
                       double *tmp) {
+  (void)tmp;
   for (int i = 0; i < n; i++) {
-    int L = 0;
-    for (int q = rp[i]; q < rp[i + 1]; q++) tmp[L++] = v[q] * x[ci[q]];
-    y[i] = orc_pairwise(tmp, L);
+    double acc = 0.0;
+    for (int q = rp[i]; q < rp[i + 1]; q++) acc = fma(v[q], x[ci[q]], acc);
+    y[i] = acc;
   }
 }
 

@@ -1,0 +1,1168 @@
+// Host side of libspai.so: the C ABI declared in include/spai.h.
+//
+// A handle owns A (CSR for PCG, ELL for the column passes), three capped
+// column slabs (M and the search directions P, Z), the device scalars and
+// the reduction workspace.  Every numeric step runs in the kernels of
+// colpass_*.cu and vec_kernels.cu; the host only validates input, lays out
+// memory and sequences launches on the handle's stream.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <vector>
+
+#include "spai.h"
+#include "common.cuh"
+#include "vec_kernels.cuh"
+
+using namespace spai;
+
+namespace {
+
+struct PassCfg {
+  WarpLayout lay;
+  int NW, B, grid, nb, ngroups;
+  size_t smem;
+  int part_off, red_off;
+  bool ok;
+};
+
+struct Buf {  // device allocation helper
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+}  // namespace
+
+struct spai_ctx {
+  int n = 0;
+  long long nnz = 0;
+  int prec = SPAI_FP64;
+  double cap_factor = 2.0;
+  int W = 1;
+  uint32_t magicW = 0;
+  int capmax = 1;
+  long long slab_total = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  // A
+  int *d_rowptr = nullptr, *d_colind = nullptr;
+  double *d_vals = nullptr, *d_diag = nullptr;
+  int* d_ell_col = nullptr;
+  float* d_ell32 = nullptr;
+  double* d_ell64 = nullptr;
+  // slabs
+  long long* d_off = nullptr;
+  int* d_cap = nullptr;
+  int *d_Mrow = nullptr, *d_Prow = nullptr, *d_Zrow = nullptr;
+  void *d_Mval = nullptr, *d_Pval = nullptr, *d_Zval = nullptr;
+  int *d_Mlen = nullptr, *d_Plen = nullptr, *d_Zlen = nullptr;
+  // scalars and reduction workspace
+  DevScalars* d_sc = nullptr;
+  double *d_hres = nullptr, *d_hcoef = nullptr;
+  int hist_cap = 0;
+  double *d_bsum = nullptr, *d_gsum = nullptr;
+  unsigned *d_cnt1 = nullptr, *d_cnt2 = nullptr;
+  int red_nb = 0, red_ng = 0;
+  PassCfg cfg[5];
+  // method state (host mirror)
+  int method = -1;
+  int it = 0;
+  // row-wise copies of M for spai_apply / PCG
+  bool mt_valid = false, sym_valid = false;
+  long long* d_ccolptr = nullptr;  // CSC export of M
+  int* d_crow = nullptr;
+  double* d_cval = nullptr;
+  long long* d_mrp = nullptr;
+  int* d_mci = nullptr;
+  double* d_mv = nullptr;
+  long long* d_srp = nullptr;
+  int* d_sci = nullptr;
+  double* d_sv = nullptr;
+  int* d_cnt = nullptr;
+  long long* d_scan = nullptr;
+  int *d_tmpi = nullptr;
+  double* d_tmpv = nullptr;
+  long long mt_cap = 0, sym_cap = 0;
+  // PCG vectors
+  double *d_b = nullptr, *d_x = nullptr, *d_r = nullptr, *d_z = nullptr, *d_p = nullptr,
+         *d_q = nullptr;
+  PcgScalars* d_ps = nullptr;
+  double *d_vbsum = nullptr, *d_vgsum = nullptr;
+  unsigned *d_vcnt1 = nullptr, *d_vcnt2 = nullptr;
+  // stats
+  long long colpass_launches = 0, pcg_launches = 0, other_launches = 0;
+  unsigned long long a_bytes_total = 0;
+  double colpass_ms = 0.0;
+  bool timing = false;
+  std::vector<cudaEvent_t> ev;
+  int ev_used = 0;
+};
+
+namespace {
+
+#define CK(x)                              \
+  do {                                     \
+    cudaError_t e_ = (x);                  \
+    if (e_ != cudaSuccess) {               \
+      (void)cudaGetLastError();            \
+      return e_ == cudaErrorMemoryAllocation ? SPAI_ERR_OOM : SPAI_ERR_CUDA; \
+    }                                      \
+  } while (0)
+
+template <typename T>
+int dalloc(T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  cudaError_t e = cudaMalloc((void**)p, sizeof(T) * count);
+  if (e != cudaSuccess) {
+    (void)cudaGetLastError();
+    *p = nullptr;
+    return SPAI_ERR_OOM;
+  }
+  return SPAI_OK;
+}
+
+template <typename T>
+void dfree(T*& p) {
+  if (p) cudaFree((void*)p);
+  p = nullptr;
+}
+
+int align16(int x) { return (x + 15) & ~15; }
+
+int next_pow2(int x) {
+  int p = 1;
+  while (p < x) p <<= 1;
+  return p;
+}
+
+// Per-warp scratch layout of a pass kind.
+WarpLayout make_layout(int kind, int vc, int CAP, int W) {
+  WarpLayout L;
+  memset(&L, 0, sizeof(L));
+  const int PMAX = CAP * W;
+  const int LMAX = PMAX + 1;
+  int TMAX = 0;
+  if (kind == kMR || kind == kCGA) TMAX = 2 * CAP;
+  if (kind == kLOMR) TMAX = 3 * CAP;
+  if (kind == kCGB) TMAX = LMAX + CAP;
+  const int DMAX = next_pow2(std::max(32, std::max(LMAX, TMAX)));
+  int o = 0;
+  auto take = [&](int bytes) {
+    int at = o;
+    o = align16(o + bytes);
+    return at;
+  };
+  const bool hasP = kind != kRES;
+  const bool lomr = kind == kLOMR;
+  const bool hasQ = kind == kMR || kind == kLOMR || kind == kCGB;
+  L.dtmp = take(8 * DMAX);
+  L.Mr = take(4 * CAP);
+  L.Mv = take(vc * CAP);
+  L.Pr = take(hasP ? 4 * CAP : 0);
+  L.Pv = take(hasP ? vc * CAP : 0);
+  L.Zr = take(lomr ? 4 * CAP : 0);
+  L.Zv = take(lomr ? vc * CAP : 0);
+  L.Sr = take(lomr ? 4 * 2 * CAP : 0);
+  L.Sv = take(lomr ? vc * 2 * CAP : 0);
+  L.Tr = take(4 * TMAX);
+  L.Tv = take(vc * TMAX);
+  L.Rr = take(4 * LMAX);
+  L.Rv = take(vc * LMAX);
+  L.Qr = take(hasQ ? 4 * LMAX : 0);
+  L.Qv = take(hasQ ? vc * LMAX : 0);
+  L.Vr = take(lomr ? 4 * LMAX : 0);
+  L.Vv = take(lomr ? vc * LMAX : 0);
+  L.key0 = take(4 * (PMAX + 1));
+  L.key1 = take(4 * (PMAX + 1));
+  L.idx0 = take(2 * (PMAX + 1));
+  L.idx1 = take(2 * (PMAX + 1));
+  L.aval = take(vc * PMAX);
+  L.hp = take(2 * (LMAX + 1));
+  L.dp = take(2 * (TMAX + 1));
+  L.hist = take(4 * 256);
+  L.bytes = o;
+  return L;
+}
+
+PassCfg make_cfg(int kind, int vc, int n, int CAP, int W, int smem_max) {
+  PassCfg c;
+  memset(&c, 0, sizeof(c));
+  c.lay = make_layout(kind, vc, CAP, W);
+  const int nq = 6;
+  const int extra_fixed = 8 * 1024;  // reduction scratch (1024 doubles)
+  c.ok = false;
+  for (int NW = 8; NW >= 1; NW >>= 1) {
+    // B: columns per CTA, power of two, NW <= B <= 1024, enough CTAs to fill
+    // the GPU, and at most 65536 CTAs so the group tree stays two-level.
+    int B = NW;
+    long long target = (long long)n / (152LL * 8);
+    while ((long long)B * 2 <= target && B * 2 <= 256) B *= 2;
+    while (((long long)n + B - 1) / B > 65536LL && B < 1024) B *= 2;
+    size_t smem = (size_t)NW * c.lay.bytes;
+    int part_off = (int)smem;
+    smem += (size_t)8 * nq * B;
+    int red_off = (int)smem;
+    smem += extra_fixed;
+    bool fits = smem <= (size_t)smem_max;
+    bool good = smem <= (size_t)(smem_max / 2) || NW == 1;
+    if (fits && (good || NW == 1)) {
+      c.NW = NW;
+      c.B = B;
+      c.grid = (int)(((long long)n + B - 1) / B);
+      c.nb = c.grid;
+      c.ngroups = (c.nb + kGroup - 1) / kGroup;
+      c.smem = smem;
+      c.part_off = part_off;
+      c.red_off = red_off;
+      c.ok = c.ngroups <= 1024;
+      return c;
+    }
+  }
+  return c;
+}
+
+int ensure_hist(spai_ctx* h, int iters) {
+  if (iters + 1 <= h->hist_cap) return SPAI_OK;
+  dfree(h->d_hres);
+  dfree(h->d_hcoef);
+  int cap = std::max(iters + 1, 64);
+  int rc = dalloc(&h->d_hres, cap);
+  if (rc) return rc;
+  rc = dalloc(&h->d_hcoef, 2 * cap);
+  if (rc) return rc;
+  h->hist_cap = cap;
+  return SPAI_OK;
+}
+
+cudaError_t timed_launch(spai_ctx* h, const PassParams& p, const PassCfg& c, bool res) {
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (h->timing) {
+    while ((int)h->ev.size() < h->ev_used + 2) {
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) break;
+      h->ev.push_back(e);
+    }
+    if ((int)h->ev.size() >= h->ev_used + 2) {
+      e0 = h->ev[h->ev_used];
+      e1 = h->ev[h->ev_used + 1];
+      h->ev_used += 2;
+      cudaEventRecord(e0, h->stream);
+    }
+  }
+  cudaError_t err;
+  if (res && h->prec == SPAI_MIXED)
+    err = launch_colpass_res_f32(p, c.grid, 32 * c.NW, c.smem, h->stream);
+  else if (res || h->prec == SPAI_FP64)
+    err = launch_colpass_f64(p, c.grid, 32 * c.NW, c.smem, h->stream);
+  else
+    err = launch_colpass_f32(p, c.grid, 32 * c.NW, c.smem, h->stream);
+  if (e1) cudaEventRecord(e1, h->stream);
+  h->colpass_launches++;
+  int vc = (res || h->prec == SPAI_FP64) ? 8 : 4;
+  h->a_bytes_total += (unsigned long long)h->n * h->W * (4 + vc);
+  return err;
+}
+
+void collect_timing(spai_ctx* h) {
+  for (int k = 0; k + 1 < h->ev_used; k += 2) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, h->ev[k], h->ev[k + 1]) == cudaSuccess) h->colpass_ms += ms;
+  }
+  h->ev_used = 0;
+}
+
+PassParams base_params(spai_ctx* h, int kind, bool res) {
+  PassParams p;
+  memset(&p, 0, sizeof(p));
+  const PassCfg& c = h->cfg[kind];
+  p.n = h->n;
+  p.W = h->W;
+  p.magicW = h->magicW;
+  p.B = c.B;
+  p.NW = c.NW;
+  p.capmax = h->capmax;
+  p.kind = kind;
+  p.off = h->d_off;
+  p.cap = h->d_cap;
+  p.Mrow = h->d_Mrow;
+  p.Mval = h->d_Mval;
+  p.Mlen = h->d_Mlen;
+  p.Prow = h->d_Prow;
+  p.Pval = h->d_Pval;
+  p.Plen = h->d_Plen;
+  p.Zrow = h->d_Zrow;
+  p.Zval = h->d_Zval;
+  p.Zlen = h->d_Zlen;
+  p.ell_col = h->d_ell_col;
+  p.ell_val = (res || h->prec == SPAI_FP64) ? (const void*)h->d_ell64 : (const void*)h->d_ell32;
+  p.sc = h->d_sc;
+  p.hist_res = h->d_hres;
+  p.hist_coef = h->d_hcoef;
+  p.bsum = h->d_bsum;
+  p.gsum = h->d_gsum;
+  p.cnt1 = h->d_cnt1;
+  p.cnt2 = h->d_cnt2;
+  p.nb = c.nb;
+  p.ngroups = c.ngroups;
+  p.lay = c.lay;
+  p.part_off = c.part_off;
+  p.red_off = c.red_off;
+  return p;
+}
+
+// reset the per-call device scalars (stop, flags, done)
+int reset_call_scalars(spai_ctx* h) {
+  CK(cudaMemsetAsync((char*)h->d_sc + offsetof(DevScalars, stop), 0, 4 * sizeof(int), h->stream));
+  return SPAI_OK;
+}
+
+void free_all(spai_ctx* h) {
+  dfree(h->d_rowptr);
+  dfree(h->d_colind);
+  dfree(h->d_vals);
+  dfree(h->d_diag);
+  dfree(h->d_ell_col);
+  dfree(h->d_ell32);
+  dfree(h->d_ell64);
+  dfree(h->d_off);
+  dfree(h->d_cap);
+  dfree(h->d_Mrow);
+  dfree(h->d_Prow);
+  dfree(h->d_Zrow);
+  dfree(h->d_Mval);
+  dfree(h->d_Pval);
+  dfree(h->d_Zval);
+  dfree(h->d_Mlen);
+  dfree(h->d_Plen);
+  dfree(h->d_Zlen);
+  dfree(h->d_sc);
+  dfree(h->d_hres);
+  dfree(h->d_hcoef);
+  dfree(h->d_bsum);
+  dfree(h->d_gsum);
+  dfree(h->d_cnt1);
+  dfree(h->d_cnt2);
+  dfree(h->d_ccolptr);
+  dfree(h->d_crow);
+  dfree(h->d_cval);
+  dfree(h->d_mrp);
+  dfree(h->d_mci);
+  dfree(h->d_mv);
+  dfree(h->d_srp);
+  dfree(h->d_sci);
+  dfree(h->d_sv);
+  dfree(h->d_cnt);
+  dfree(h->d_scan);
+  dfree(h->d_tmpi);
+  dfree(h->d_tmpv);
+  dfree(h->d_b);
+  dfree(h->d_x);
+  dfree(h->d_r);
+  dfree(h->d_z);
+  dfree(h->d_p);
+  dfree(h->d_q);
+  dfree(h->d_ps);
+  dfree(h->d_vbsum);
+  dfree(h->d_vgsum);
+  dfree(h->d_vcnt1);
+  dfree(h->d_vcnt2);
+  for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
+  h->ev.clear();
+}
+
+// CSC export of M into h->d_ccolptr / d_crow / d_cval; returns nnz via *nnz
+int export_csc(spai_ctx* h, long long* nnz) {
+  const int n = h->n;
+  if (!h->d_ccolptr) {
+    int rc = dalloc(&h->d_ccolptr, (size_t)n + 1);
+    if (rc) return rc;
+    rc = dalloc(&h->d_scan, 2 * (size_t)((n + 1023) / 1024) + 2);
+    if (rc) return rc;
+  }
+  CK(launch_exclusive_scan(h->d_Mlen, h->d_ccolptr, n, h->d_scan, h->stream));
+  long long tot = 0;
+  CK(cudaMemcpyAsync(&tot, h->d_ccolptr + n, sizeof(long long), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  if (tot > h->mt_cap || !h->d_crow) {
+    dfree(h->d_crow);
+    dfree(h->d_cval);
+    dfree(h->d_mci);
+    dfree(h->d_mv);
+    dfree(h->d_tmpi);
+    dfree(h->d_tmpv);
+    long long cap = std::max(tot, (long long)h->slab_total);
+    int rc = dalloc(&h->d_crow, (size_t)cap);
+    if (!rc) rc = dalloc(&h->d_cval, (size_t)cap);
+    if (!rc) rc = dalloc(&h->d_mci, (size_t)cap);
+    if (!rc) rc = dalloc(&h->d_mv, (size_t)cap);
+    if (!rc) rc = dalloc(&h->d_tmpi, (size_t)cap);
+    if (!rc) rc = dalloc(&h->d_tmpv, (size_t)cap);
+    if (rc) return rc;
+    h->mt_cap = cap;
+  }
+  CK(launch_export_csc(h->prec, n, h->d_off, h->d_Mrow, h->d_Mval, h->d_ccolptr, h->d_crow,
+                       h->d_cval, h->stream));
+  h->other_launches += 4;
+  *nnz = tot;
+  return SPAI_OK;
+}
+
+// row-wise copy of M (and optionally its symmetric part) for apply / PCG
+int ensure_rows(spai_ctx* h, bool sym) {
+  const int n = h->n;
+  if (!h->mt_valid) {
+    long long nnz = 0;
+    int rc = export_csc(h, &nnz);
+    if (rc) return rc;
+    if (!h->d_mrp) {
+      rc = dalloc(&h->d_mrp, (size_t)n + 1);
+      if (!rc) rc = dalloc(&h->d_cnt, (size_t)n + 1);
+      if (rc) return rc;
+    }
+    CK(launch_transpose(n, h->d_ccolptr, h->d_crow, h->d_cval, nnz, h->d_cnt, h->d_mrp, h->d_scan,
+                        h->d_mci, h->d_mv, h->d_tmpi, h->d_tmpv, h->stream));
+    h->other_launches += 7;
+    h->mt_valid = true;
+    h->sym_valid = false;
+  }
+  if (sym && !h->sym_valid) {
+    if (!h->d_srp) {
+      int rc = dalloc(&h->d_srp, (size_t)n + 1);
+      if (rc) return rc;
+    }
+    CK(launch_sym(n, h->d_mrp, h->d_mci, h->d_mv, h->d_ccolptr, h->d_crow, h->d_cval, 0, h->d_cnt,
+                  nullptr, nullptr, nullptr, h->stream));
+    CK(launch_exclusive_scan(h->d_cnt, h->d_srp, n, h->d_scan, h->stream));
+    long long tot = 0;
+    CK(cudaMemcpyAsync(&tot, h->d_srp + n, sizeof(long long), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    if (tot > h->sym_cap || !h->d_sci) {
+      dfree(h->d_sci);
+      dfree(h->d_sv);
+      int rc = dalloc(&h->d_sci, (size_t)tot);
+      if (!rc) rc = dalloc(&h->d_sv, (size_t)tot);
+      if (rc) return rc;
+      h->sym_cap = tot;
+    }
+    CK(launch_sym(n, h->d_mrp, h->d_mci, h->d_mv, h->d_ccolptr, h->d_crow, h->d_cval, 1, h->d_cnt,
+                  h->d_srp, h->d_sci, h->d_sv, h->stream));
+    h->other_launches += 5;
+    h->sym_valid = true;
+  }
+  return SPAI_OK;
+}
+
+void invalidate_rows(spai_ctx* h) {
+  h->mt_valid = false;
+  h->sym_valid = false;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* spai_status_string(int code) {
+  switch (code) {
+    case SPAI_OK: return "ok";
+    case SPAI_CONVERGED_EARLY: return "converged early (residual or step denominator reached zero)";
+    case SPAI_LOMR_FALLBACK: return "LOMR took at least one MR step (near-singular 2x2 system)";
+    case SPAI_PCG_MAXIT: return "PCG reached maxit";
+    case SPAI_PCG_BREAKDOWN: return "PCG breakdown ((p,Ap) or (r,z) zero or non-finite)";
+    case SPAI_ERR_ARG: return "invalid argument";
+    case SPAI_ERR_CSR: return "malformed CSR matrix";
+    case SPAI_ERR_NOT_SPD_DIAG: return "missing or non-positive diagonal entry";
+    case SPAI_ERR_NOT_SYMMETRIC: return "matrix is not exactly symmetric";
+    case SPAI_ERR_NONFINITE: return "non-finite value";
+    case SPAI_ERR_CUDA: return "CUDA runtime error";
+    case SPAI_ERR_OOM: return "device out of memory";
+    case SPAI_ERR_CAPACITY: return "a column outgrew its slab capacity";
+    case SPAI_ERR_UNSUPPORTED: return "size outside the kernels' limits";
+    case SPAI_ERR_STATE: return "saved state does not match this handle";
+    default: return "unknown status";
+  }
+}
+
+int spai_validate_csr(int64_t n, int64_t nnz, const int32_t* rowptr, const int32_t* colind,
+                      const double* vals, int check_symmetry) {
+  if (n < 1 || nnz < 1 || !rowptr || !colind || !vals) return SPAI_ERR_ARG;
+  if (n >= (1LL << 31) || nnz >= (1LL << 31)) return SPAI_ERR_UNSUPPORTED;
+  if (rowptr[0] != 0 || rowptr[n] != nnz) return SPAI_ERR_CSR;
+  for (int64_t i = 0; i < n; i++) {
+    if (rowptr[i + 1] < rowptr[i]) return SPAI_ERR_CSR;
+    bool diag = false;
+    for (int64_t e = rowptr[i]; e < rowptr[i + 1]; e++) {
+      int32_t c = colind[e];
+      if (c < 0 || c >= n) return SPAI_ERR_CSR;
+      if (e > rowptr[i] && colind[e - 1] >= c) return SPAI_ERR_CSR;
+      if (!isfinite(vals[e])) return SPAI_ERR_NONFINITE;
+      if (c == i) {
+        if (!(vals[e] > 0.0)) return SPAI_ERR_NOT_SPD_DIAG;
+        diag = true;
+      }
+    }
+    if (!diag) return SPAI_ERR_NOT_SPD_DIAG;
+  }
+  if (check_symmetry) {
+    for (int64_t i = 0; i < n; i++) {
+      for (int64_t e = rowptr[i]; e < rowptr[i + 1]; e++) {
+        int32_t c = colind[e];
+        // find (c, i)
+        const int32_t* b = colind + rowptr[c];
+        const int32_t* en = colind + rowptr[c + 1];
+        const int32_t* f = std::lower_bound(b, en, (int32_t)i);
+        if (f == en || *f != i) return SPAI_ERR_NOT_SYMMETRIC;
+        if (vals[rowptr[c] + (f - b)] != vals[e]) return SPAI_ERR_NOT_SYMMETRIC;
+      }
+    }
+  }
+  return SPAI_OK;
+}
+
+int spai_create(spai_handle* out, int64_t n, int64_t nnz, const int32_t* rowptr,
+                const int32_t* colind, const double* vals, int on_device, const spai_opts* opts,
+                void* stream) {
+  if (!out) return SPAI_ERR_ARG;
+  *out = nullptr;
+  if (!opts || n < 1 || nnz < 1 || !rowptr || !colind || !vals) return SPAI_ERR_ARG;
+  if (opts->prec != SPAI_FP64 && opts->prec != SPAI_MIXED) return SPAI_ERR_ARG;
+  if (!(opts->cap_factor > 0.0)) return SPAI_ERR_ARG;
+  if (n >= (1LL << 26) || nnz >= (1LL << 31)) return SPAI_ERR_UNSUPPORTED;
+  std::vector<int32_t> hrp, hci;
+  std::vector<double> hv;
+  const int32_t* rp = rowptr;
+  const int32_t* ci = colind;
+  const double* va = vals;
+  if (on_device) {
+    hrp.resize(n + 1);
+    hci.resize(nnz);
+    hv.resize(nnz);
+    if (cudaMemcpy(hrp.data(), rowptr, sizeof(int32_t) * (n + 1), cudaMemcpyDeviceToHost) ||
+        cudaMemcpy(hci.data(), colind, sizeof(int32_t) * nnz, cudaMemcpyDeviceToHost) ||
+        cudaMemcpy(hv.data(), vals, sizeof(double) * nnz, cudaMemcpyDeviceToHost)) {
+      (void)cudaGetLastError();
+      return SPAI_ERR_CUDA;
+    }
+    rp = hrp.data();
+    ci = hci.data();
+    va = hv.data();
+  }
+  int rc = spai_validate_csr(n, nnz, rp, ci, va, 1);
+  if (rc) return rc;
+
+  spai_ctx* h = new (std::nothrow) spai_ctx();
+  if (!h) return SPAI_ERR_OOM;
+  h->n = (int)n;
+  h->nnz = nnz;
+  h->prec = opts->prec;
+  h->cap_factor = opts->cap_factor;
+  if (stream) {
+    h->stream = (cudaStream_t)stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      (void)cudaGetLastError();
+      delete h;
+      return SPAI_ERR_CUDA;
+    }
+    h->own_stream = true;
+  }
+  // ELL layout of A; padding entries point at the row itself with value 0
+  int W = 1;
+  for (int64_t i = 0; i < n; i++) W = std::max(W, (int)(rp[i + 1] - rp[i]));
+  std::vector<int> cap(n);
+  std::vector<long long> off(n + 1);
+  off[0] = 0;
+  int capmax = 1;
+  for (int64_t j = 0; j < n; j++) {
+    double c = floor(opts->cap_factor * (double)(rp[j + 1] - rp[j]));
+    if (!(c >= 1.0)) c = 1.0;
+    if (c > (double)n) c = (double)n;
+    cap[j] = (int)c;
+    capmax = std::max(capmax, cap[j]);
+    off[j + 1] = off[j] + cap[j];
+  }
+  if (W > 64 || (long long)capmax * W + 2 > 65535) {
+    if (h->own_stream) cudaStreamDestroy(h->stream);
+    delete h;
+    return SPAI_ERR_UNSUPPORTED;
+  }
+  h->W = W;
+  h->magicW = (uint32_t)((((uint64_t)1 << 32) + W - 1) / W);
+  h->capmax = capmax;
+  h->slab_total = off[n];
+  int dev = 0;
+  cudaGetDevice(&dev);
+  int smem_max = 0;
+  cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (smem_max <= 0) smem_max = 227 * 1024;
+  const int vc = h->prec == SPAI_MIXED ? 4 : 8;
+  for (int k = 0; k < 5; k++) {
+    h->cfg[k] = make_cfg(k, k == kRES ? 8 : vc, (int)n, capmax, W, smem_max);
+    if (!h->cfg[k].ok) {
+      if (h->own_stream) cudaStreamDestroy(h->stream);
+      delete h;
+      return SPAI_ERR_UNSUPPORTED;
+    }
+    h->red_nb = std::max(h->red_nb, h->cfg[k].nb);
+    h->red_ng = std::max(h->red_ng, h->cfg[k].ngroups);
+  }
+  std::vector<int> ecol((size_t)n * W);
+  std::vector<double> e64((size_t)n * W);
+  std::vector<float> e32;
+  std::vector<double> diag(n);
+  for (int64_t i = 0; i < n; i++) {
+    int t = 0;
+    for (int64_t e = rp[i]; e < rp[i + 1]; e++, t++) {
+      ecol[(size_t)i * W + t] = ci[e];
+      e64[(size_t)i * W + t] = va[e];
+      if (ci[e] == i) diag[i] = va[e];
+    }
+    for (; t < W; t++) {
+      ecol[(size_t)i * W + t] = (int)i;
+      e64[(size_t)i * W + t] = 0.0;
+    }
+  }
+  if (h->prec == SPAI_MIXED) {
+    e32.resize(e64.size());
+    for (size_t k = 0; k < e64.size(); k++) e32[k] = (float)e64[k];
+  }
+  const size_t vs = h->prec == SPAI_MIXED ? 4 : 8;
+  rc = SPAI_OK;
+  rc = rc ? rc : dalloc(&h->d_rowptr, n + 1);
+  rc = rc ? rc : dalloc(&h->d_colind, nnz);
+  rc = rc ? rc : dalloc(&h->d_vals, nnz);
+  rc = rc ? rc : dalloc(&h->d_diag, n);
+  rc = rc ? rc : dalloc(&h->d_ell_col, (size_t)n * W);
+  rc = rc ? rc : dalloc(&h->d_ell64, (size_t)n * W);
+  if (h->prec == SPAI_MIXED) rc = rc ? rc : dalloc(&h->d_ell32, (size_t)n * W);
+  rc = rc ? rc : dalloc(&h->d_off, n + 1);
+  rc = rc ? rc : dalloc(&h->d_cap, n);
+  rc = rc ? rc : dalloc(&h->d_Mrow, h->slab_total);
+  rc = rc ? rc : dalloc(&h->d_Prow, h->slab_total);
+  rc = rc ? rc : dalloc(&h->d_Zrow, h->slab_total);
+  rc = rc ? rc : dalloc((char**)&h->d_Mval, h->slab_total * vs);
+  rc = rc ? rc : dalloc((char**)&h->d_Pval, h->slab_total * vs);
+  rc = rc ? rc : dalloc((char**)&h->d_Zval, h->slab_total * vs);
+  rc = rc ? rc : dalloc(&h->d_Mlen, n);
+  rc = rc ? rc : dalloc(&h->d_Plen, n);
+  rc = rc ? rc : dalloc(&h->d_Zlen, n);
+  rc = rc ? rc : dalloc(&h->d_sc, 1);
+  rc = rc ? rc : dalloc(&h->d_bsum, (size_t)6 * h->red_nb);
+  rc = rc ? rc : dalloc(&h->d_gsum, (size_t)6 * h->red_ng);
+  rc = rc ? rc : dalloc(&h->d_cnt1, h->red_ng);
+  rc = rc ? rc : dalloc(&h->d_cnt2, 1);
+  rc = rc ? rc : ensure_hist(h, 64);
+  if (rc) {
+    free_all(h);
+    if (h->own_stream) cudaStreamDestroy(h->stream);
+    delete h;
+    return rc;
+  }
+  cudaStream_t st = h->stream;
+  bool ok = true;
+  ok &= cudaMemcpyAsync(h->d_rowptr, rp, sizeof(int) * (n + 1), cudaMemcpyHostToDevice, st) == 0;
+  ok &= cudaMemcpyAsync(h->d_colind, ci, sizeof(int) * nnz, cudaMemcpyHostToDevice, st) == 0;
+  ok &= cudaMemcpyAsync(h->d_vals, va, sizeof(double) * nnz, cudaMemcpyHostToDevice, st) == 0;
+  ok &= cudaMemcpyAsync(h->d_diag, diag.data(), sizeof(double) * n, cudaMemcpyHostToDevice, st) == 0;
+  ok &= cudaMemcpyAsync(h->d_ell_col, ecol.data(), sizeof(int) * ecol.size(), cudaMemcpyHostToDevice,
+                        st) == 0;
+  ok &= cudaMemcpyAsync(h->d_ell64, e64.data(), sizeof(double) * e64.size(), cudaMemcpyHostToDevice,
+                        st) == 0;
+  if (h->prec == SPAI_MIXED)
+    ok &= cudaMemcpyAsync(h->d_ell32, e32.data(), sizeof(float) * e32.size(),
+                          cudaMemcpyHostToDevice, st) == 0;
+  ok &= cudaMemcpyAsync(h->d_off, off.data(), sizeof(long long) * (n + 1), cudaMemcpyHostToDevice,
+                        st) == 0;
+  ok &= cudaMemcpyAsync(h->d_cap, cap.data(), sizeof(int) * n, cudaMemcpyHostToDevice, st) == 0;
+  ok &= cudaMemsetAsync(h->d_sc, 0, sizeof(DevScalars), st) == 0;
+  ok &= cudaMemsetAsync(h->d_cnt1, 0, sizeof(unsigned) * h->red_ng, st) == 0;
+  ok &= cudaMemsetAsync(h->d_cnt2, 0, sizeof(unsigned), st) == 0;
+  ok &= launch_init_slab(h->prec, (int)n, h->d_off, h->d_diag, h->d_Mrow, h->d_Mval, h->d_Mlen,
+                         h->d_Plen, h->d_Zlen, st) == 0;
+  ok &= cudaStreamSynchronize(st) == 0;
+  h->other_launches += 1;
+  if (!ok) {
+    (void)cudaGetLastError();
+    free_all(h);
+    if (h->own_stream) cudaStreamDestroy(h->stream);
+    delete h;
+    return SPAI_ERR_CUDA;
+  }
+  *out = h;
+  return SPAI_OK;
+}
+
+int spai_destroy(spai_handle h) {
+  if (!h) return SPAI_ERR_ARG;
+  cudaStreamSynchronize(h->stream);
+  free_all(h);
+  if (h->own_stream) cudaStreamDestroy(h->stream);
+  delete h;
+  return SPAI_OK;
+}
+
+int spai_set_stream(spai_handle h, void* stream) {
+  if (!h) return SPAI_ERR_ARG;
+  CK(cudaStreamSynchronize(h->stream));
+  if (h->own_stream) cudaStreamDestroy(h->stream);
+  h->own_stream = false;
+  if (stream) {
+    h->stream = (cudaStream_t)stream;
+  } else {
+    CK(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
+    h->own_stream = true;
+  }
+  return SPAI_OK;
+}
+
+int spai_reset(spai_handle h) {
+  if (!h) return SPAI_ERR_ARG;
+  CK(launch_init_slab(h->prec, h->n, h->d_off, h->d_diag, h->d_Mrow, h->d_Mval, h->d_Mlen,
+                      h->d_Plen, h->d_Zlen, h->stream));
+  h->other_launches++;
+  h->method = -1;
+  h->it = 0;
+  invalidate_rows(h);
+  CK(cudaStreamSynchronize(h->stream));
+  return SPAI_OK;
+}
+
+int spai_run(spai_handle h, int method, int iters, int drop_rule, spai_history* hist) {
+  if (!h || iters < 0 || (method != SPAI_MR && method != SPAI_LOMR && method != SPAI_CG))
+    return SPAI_ERR_ARG;
+  if (drop_rule != SPAI_DROP_NONE && drop_rule != SPAI_DROP_TOPK_COL) return SPAI_ERR_ARG;
+  int rc = ensure_hist(h, iters);
+  if (rc) return rc;
+  cudaStream_t st = h->stream;
+  const bool fresh = h->method != method;
+  if (fresh) {
+    CK(cudaMemsetAsync(h->d_Plen, 0, sizeof(int) * h->n, st));
+    CK(cudaMemsetAsync(h->d_Zlen, 0, sizeof(int) * h->n, st));
+    CK(cudaMemsetAsync((char*)h->d_sc + offsetof(DevScalars, beta), 0, sizeof(double), st));
+    CK(cudaMemsetAsync((char*)h->d_sc + offsetof(DevScalars, rr), 0, sizeof(double), st));
+  }
+  rc = reset_call_scalars(h);
+  if (rc) return rc;
+  CK(cudaMemsetAsync(h->d_hres, 0xff, sizeof(double) * (iters + 1), st));
+  CK(cudaMemsetAsync(h->d_hcoef, 0xff, sizeof(double) * 2 * std::max(iters, 1), st));
+  invalidate_rows(h);
+  const int drop = drop_rule == SPAI_DROP_TOPK_COL ? 1 : 0;
+  auto pass = [&](int kind, int upd, int dir, int iter, int fresh_b) -> cudaError_t {
+    PassParams p = base_params(h, kind, false);
+    p.do_update = upd;
+    p.do_dir = dir;
+    p.drop = drop;
+    p.iter = iter;
+    p.fresh = fresh_b;
+    return timed_launch(h, p, h->cfg[kind], false);
+  };
+  if (method == SPAI_MR || method == SPAI_LOMR) {
+    const int kind = method == SPAI_MR ? kMR : kLOMR;
+    if (iters == 0) {
+      CK(pass(kind, 0, 0, 0, 0));
+    } else {
+      CK(pass(kind, 0, 1, 0, 0));
+      for (int i = 1; i < iters; i++) CK(pass(kind, 1, 1, i, 0));
+      CK(pass(kind, 1, 0, iters, 0));
+    }
+  } else {
+    if (iters == 0) {
+      CK(pass(kCGB, 0, 1, 0, 1));
+    } else {
+      for (int i = 0; i < iters; i++) {
+        CK(pass(kCGB, 0, 1, i, i == 0));
+        CK(pass(kCGA, 0, 1, i, 0));
+      }
+    }
+  }
+  DevScalars sc;
+  CK(cudaMemcpyAsync(&sc, h->d_sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, st));
+  if (hist && hist->resnorm)
+    CK(cudaMemcpyAsync(hist->resnorm, h->d_hres, sizeof(double) * (iters + 1),
+                       cudaMemcpyDeviceToHost, st));
+  if (hist && hist->coef && iters > 0)
+    CK(cudaMemcpyAsync(hist->coef, h->d_hcoef, sizeof(double) * 2 * iters, cudaMemcpyDeviceToHost,
+                       st));
+  CK(cudaStreamSynchronize(st));
+  if (h->timing) collect_timing(h);
+  if (hist) {
+    hist->iters_done = sc.done;
+    hist->flags = sc.flags & 3;
+  }
+  h->method = method;
+  h->it += sc.done;
+  if (sc.flags & kFlagCapacity) {
+    h->method = -1;
+    return SPAI_ERR_CAPACITY;
+  }
+  if (sc.flags & kFlagNonfinite) {
+    h->method = -1;
+    return SPAI_ERR_NONFINITE;
+  }
+  if (sc.flags & kFlagConverged) {
+    h->method = -1;
+    return SPAI_CONVERGED_EARLY;
+  }
+  if (sc.flags & kFlagFallback) return SPAI_LOMR_FALLBACK;
+  return SPAI_OK;
+}
+
+int spai_mr(spai_handle h, int iters, int drop_rule, spai_history* hist) {
+  return spai_run(h, SPAI_MR, iters, drop_rule, hist);
+}
+int spai_lomr(spai_handle h, int iters, int drop_rule, spai_history* hist) {
+  return spai_run(h, SPAI_LOMR, iters, drop_rule, hist);
+}
+int spai_cg(spai_handle h, int iters, int drop_rule, spai_history* hist) {
+  return spai_run(h, SPAI_CG, iters, drop_rule, hist);
+}
+
+int spai_residual_norm(spai_handle h, double* out) {
+  if (!h || !out) return SPAI_ERR_ARG;
+  int rc = reset_call_scalars(h);
+  if (rc) return rc;
+  PassParams p = base_params(h, kRES, true);
+  p.do_dir = 0;
+  p.hist_res = nullptr;
+  p.hist_coef = nullptr;
+  CK(timed_launch(h, p, h->cfg[kRES], true));
+  DevScalars sc;
+  CK(cudaMemcpyAsync(&sc, h->d_sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  if (h->timing) collect_timing(h);
+  *out = sqrt(sc.result);
+  return SPAI_OK;
+}
+
+int spai_get_nnz(spai_handle h, int64_t* out) {
+  if (!h || !out) return SPAI_ERR_ARG;
+  long long nnz = 0;
+  int rc = export_csc(h, &nnz);
+  if (rc) return rc;
+  *out = nnz;
+  return SPAI_OK;
+}
+
+int spai_get_M(spai_handle h, int64_t* nnz, int32_t* colptr, int32_t* rowind, double* vals,
+               int on_device) {
+  if (!h || !nnz) return SPAI_ERR_ARG;
+  long long tot = 0;
+  int rc = export_csc(h, &tot);
+  if (rc) return rc;
+  *nnz = tot;
+  if (!colptr) return SPAI_OK;
+  if (!rowind || !vals) return SPAI_ERR_ARG;
+  const int n = h->n;
+  cudaStream_t st = h->stream;
+  if (on_device) {
+    CK(launch_ll_to_i32(h->d_ccolptr, colptr, n, st));
+    CK(cudaMemcpyAsync(rowind, h->d_crow, sizeof(int) * tot, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(vals, h->d_cval, sizeof(double) * tot, cudaMemcpyDeviceToDevice, st));
+  } else {
+    std::vector<long long> cp(n + 1);
+    CK(cudaMemcpyAsync(cp.data(), h->d_ccolptr, sizeof(long long) * (n + 1),
+                       cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(rowind, h->d_crow, sizeof(int) * tot, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(vals, h->d_cval, sizeof(double) * tot, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    for (int i = 0; i <= n; i++) colptr[i] = (int32_t)cp[i];
+  }
+  CK(cudaStreamSynchronize(st));
+  return SPAI_OK;
+}
+
+int spai_set_M(spai_handle h, const int32_t* colptr, const int32_t* rowind, const double* vals,
+               int on_device) {
+  if (!h || !colptr || !rowind || !vals) return SPAI_ERR_ARG;
+  const int n = h->n;
+  std::vector<int32_t> cp(n + 1);
+  if (on_device) {
+    CK(cudaMemcpy(cp.data(), colptr, sizeof(int32_t) * (n + 1), cudaMemcpyDeviceToHost));
+  } else {
+    memcpy(cp.data(), colptr, sizeof(int32_t) * (n + 1));
+  }
+  long long nnz = cp[n];
+  if (cp[0] != 0 || nnz < 0) return SPAI_ERR_CSR;
+  std::vector<int32_t> ri(nnz);
+  std::vector<double> va(nnz);
+  if (on_device) {
+    CK(cudaMemcpy(ri.data(), rowind, sizeof(int32_t) * nnz, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(va.data(), vals, sizeof(double) * nnz, cudaMemcpyDeviceToHost));
+  } else {
+    memcpy(ri.data(), rowind, sizeof(int32_t) * nnz);
+    memcpy(va.data(), vals, sizeof(double) * nnz);
+  }
+  std::vector<long long> off(n + 1);
+  std::vector<int> cap(n);
+  CK(cudaMemcpy(off.data(), h->d_off, sizeof(long long) * (n + 1), cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(cap.data(), h->d_cap, sizeof(int) * n, cudaMemcpyDeviceToHost));
+  std::vector<int> srow(h->slab_total, 0), slen(n, 0);
+  std::vector<double> sval(h->slab_total, 0.0);
+  for (int j = 0; j < n; j++) {
+    if (cp[j + 1] < cp[j]) return SPAI_ERR_CSR;
+    int L = 0;
+    for (long long e = cp[j]; e < cp[j + 1]; e++) {
+      if (ri[e] < 0 || ri[e] >= n) return SPAI_ERR_CSR;
+      if (e > cp[j] && ri[e - 1] >= ri[e]) return SPAI_ERR_CSR;
+      if (!isfinite(va[e])) return SPAI_ERR_NONFINITE;
+      double v = h->prec == SPAI_MIXED ? (double)(float)va[e] : va[e];
+      if (v == 0.0) continue;
+      if (L >= cap[j]) return SPAI_ERR_CAPACITY;
+      srow[off[j] + L] = ri[e];
+      sval[off[j] + L] = v;
+      L++;
+    }
+    slen[j] = L;
+  }
+  cudaStream_t st = h->stream;
+  CK(cudaMemcpyAsync(h->d_Mrow, srow.data(), sizeof(int) * h->slab_total, cudaMemcpyHostToDevice, st));
+  if (h->prec == SPAI_MIXED) {
+    std::vector<float> f(h->slab_total);
+    for (long long k = 0; k < h->slab_total; k++) f[k] = (float)sval[k];
+    CK(cudaMemcpyAsync(h->d_Mval, f.data(), sizeof(float) * h->slab_total, cudaMemcpyHostToDevice, st));
+    CK(cudaStreamSynchronize(st));
+  } else {
+    CK(cudaMemcpyAsync(h->d_Mval, sval.data(), sizeof(double) * h->slab_total,
+                       cudaMemcpyHostToDevice, st));
+  }
+  CK(cudaMemcpyAsync(h->d_Mlen, slen.data(), sizeof(int) * n, cudaMemcpyHostToDevice, st));
+  CK(cudaMemsetAsync(h->d_Plen, 0, sizeof(int) * n, st));
+  CK(cudaMemsetAsync(h->d_Zlen, 0, sizeof(int) * n, st));
+  CK(cudaStreamSynchronize(st));
+  h->method = -1;
+  h->it = 0;
+  invalidate_rows(h);
+  return SPAI_OK;
+}
+
+int spai_apply(spai_handle h, const double* x, double* y, int nrhs, int64_t ld) {
+  if (!h || !x || !y || nrhs < 1 || ld < h->n) return SPAI_ERR_ARG;
+  int rc = ensure_rows(h, false);
+  if (rc) return rc;
+  CK(launch_apply(h->n, h->d_mrp, h->d_mci, h->d_mv, x, y, nrhs, ld, h->stream));
+  h->other_launches++;
+  return SPAI_OK;
+}
+
+static int ensure_pcg(spai_ctx* h) {
+  if (h->d_x) return SPAI_OK;
+  const int n = h->n;
+  int nb = (n + 255) / 256;
+  int ng = (nb + kGroup - 1) / kGroup;
+  if (ng > 1024) return SPAI_ERR_UNSUPPORTED;
+  int rc = SPAI_OK;
+  rc = rc ? rc : dalloc(&h->d_b, n);
+  rc = rc ? rc : dalloc(&h->d_x, n);
+  rc = rc ? rc : dalloc(&h->d_r, n);
+  rc = rc ? rc : dalloc(&h->d_z, n);
+  rc = rc ? rc : dalloc(&h->d_p, n);
+  rc = rc ? rc : dalloc(&h->d_q, n);
+  rc = rc ? rc : dalloc(&h->d_ps, 1);
+  rc = rc ? rc : dalloc(&h->d_vbsum, nb);
+  rc = rc ? rc : dalloc(&h->d_vgsum, ng);
+  rc = rc ? rc : dalloc(&h->d_vcnt1, ng);
+  rc = rc ? rc : dalloc(&h->d_vcnt2, 1);
+  if (rc) return rc;
+  CK(cudaMemsetAsync(h->d_vcnt1, 0, sizeof(unsigned) * ng, h->stream));
+  CK(cudaMemsetAsync(h->d_vcnt2, 0, sizeof(unsigned), h->stream));
+  return SPAI_OK;
+}
+
+int pcg_solve(spai_handle h, const double* b, double* x, int nrhs, double rtol, int maxit,
+              int precond, int on_device, int* iters, double* relres) {
+  if (!h || !b || !x || !iters || nrhs != 1 || maxit < 0 || !(rtol >= 0.0)) return SPAI_ERR_ARG;
+  if (precond < SPAI_PREC_NONE || precond > SPAI_PREC_SPAI_SYM) return SPAI_ERR_ARG;
+  int rc = ensure_pcg(h);
+  if (rc) return rc;
+  if (precond == SPAI_PREC_SPAI || precond == SPAI_PREC_SPAI_SYM) {
+    rc = ensure_rows(h, precond == SPAI_PREC_SPAI_SYM);
+    if (rc) return rc;
+  }
+  const int n = h->n;
+  cudaStream_t st = h->stream;
+  if (on_device)
+    CK(cudaMemcpyAsync(h->d_b, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+  else
+    CK(cudaMemcpyAsync(h->d_b, b, sizeof(double) * n, cudaMemcpyHostToDevice, st));
+  PcgScalars ps;
+  memset(&ps, 0, sizeof(ps));
+  ps.rtol = rtol;
+  ps.maxit = maxit;
+  CK(cudaMemcpyAsync(h->d_ps, &ps, sizeof(ps), cudaMemcpyHostToDevice, st));
+  PcgArgs a;
+  memset(&a, 0, sizeof(a));
+  a.n = n;
+  a.arp = h->d_rowptr;
+  a.aci = h->d_colind;
+  a.av = h->d_vals;
+  a.diag = h->d_diag;
+  a.precond = precond;
+  if (precond == SPAI_PREC_SPAI) {
+    a.mrp = h->d_mrp;
+    a.mci = h->d_mci;
+    a.mv = h->d_mv;
+  } else if (precond == SPAI_PREC_SPAI_SYM) {
+    a.mrp = h->d_srp;
+    a.mci = h->d_sci;
+    a.mv = h->d_sv;
+  }
+  a.b = h->d_b;
+  a.x = h->d_x;
+  a.r = h->d_r;
+  a.z = h->d_z;
+  a.p = h->d_p;
+  a.q = h->d_q;
+  a.s = h->d_ps;
+  a.ws.bsum = h->d_vbsum;
+  a.ws.gsum = h->d_vgsum;
+  a.ws.cnt1 = h->d_vcnt1;
+  a.ws.cnt2 = h->d_vcnt2;
+  a.ws.nb = (n + 255) / 256;
+  a.ws.ngroups = (a.ws.nb + kGroup - 1) / kGroup;
+  CK(launch_pcg_init(a, st));
+  h->pcg_launches += 3;
+  const int chunk = 16;
+  for (;;) {
+    for (int c = 0; c < chunk; c++) CK(launch_pcg_iter(a, st));
+    h->pcg_launches += 4 * chunk;
+    CK(cudaMemcpyAsync(&ps, h->d_ps, sizeof(ps), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (ps.done) break;
+  }
+  CK(launch_true_res(a, st));
+  h->pcg_launches += 1;
+  CK(cudaMemcpyAsync(&ps, h->d_ps, sizeof(ps), cudaMemcpyDeviceToHost, st));
+  if (on_device)
+    CK(cudaMemcpyAsync(x, h->d_x, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+  else
+    CK(cudaMemcpyAsync(x, h->d_x, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  *iters = ps.k;
+  if (relres) *relres = ps.bn > 0 ? sqrt(ps.tres) / ps.bn : 0.0;
+  if (ps.status == 1) return SPAI_PCG_MAXIT;
+  if (ps.status == 2) return SPAI_PCG_BREAKDOWN;
+  return SPAI_OK;
+}
+
+// ------------------------------------------------------------ checkpoint
+
+namespace {
+struct StateHeader {
+  char magic[8];
+  int64_t n, slab_total;
+  int32_t prec, capmax, method, it, W, pad;
+  double cap_factor;
+};
+}  // namespace
+
+int spai_save_state(spai_handle h, void* buf, size_t* bytes) {
+  if (!h || !bytes) return SPAI_ERR_ARG;
+  const size_t vs = h->prec == SPAI_MIXED ? 4 : 8;
+  const size_t n = h->n, S = h->slab_total;
+  size_t need = sizeof(StateHeader) + sizeof(DevScalars) + 3 * n * 4 + 3 * S * 4 + 3 * S * vs;
+  if (!buf) {
+    *bytes = need;
+    return SPAI_OK;
+  }
+  if (*bytes < need) return SPAI_ERR_ARG;
+  char* o = (char*)buf;
+  StateHeader hd;
+  memset(&hd, 0, sizeof(hd));
+  memcpy(hd.magic, "SPAIST01", 8);
+  hd.n = h->n;
+  hd.slab_total = h->slab_total;
+  hd.prec = h->prec;
+  hd.capmax = h->capmax;
+  hd.method = h->method;
+  hd.it = h->it;
+  hd.W = h->W;
+  hd.cap_factor = h->cap_factor;
+  memcpy(o, &hd, sizeof(hd));
+  o += sizeof(hd);
+  cudaStream_t st = h->stream;
+  CK(cudaMemcpyAsync(o, h->d_sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, st));
+  o += sizeof(DevScalars);
+  int* lens[3] = {h->d_Mlen, h->d_Plen, h->d_Zlen};
+  int* rows[3] = {h->d_Mrow, h->d_Prow, h->d_Zrow};
+  void* vals[3] = {h->d_Mval, h->d_Pval, h->d_Zval};
+  for (int k = 0; k < 3; k++) {
+    CK(cudaMemcpyAsync(o, lens[k], n * 4, cudaMemcpyDeviceToHost, st));
+    o += n * 4;
+    CK(cudaMemcpyAsync(o, rows[k], S * 4, cudaMemcpyDeviceToHost, st));
+    o += S * 4;
+    CK(cudaMemcpyAsync(o, vals[k], S * vs, cudaMemcpyDeviceToHost, st));
+    o += S * vs;
+  }
+  CK(cudaStreamSynchronize(st));
+  *bytes = need;
+  return SPAI_OK;
+}
+
+int spai_load_state(spai_handle h, const void* buf, size_t bytes) {
+  if (!h || !buf) return SPAI_ERR_ARG;
+  const size_t vs = h->prec == SPAI_MIXED ? 4 : 8;
+  const size_t n = h->n, S = h->slab_total;
+  size_t need = sizeof(StateHeader) + sizeof(DevScalars) + 3 * n * 4 + 3 * S * 4 + 3 * S * vs;
+  if (bytes < need) return SPAI_ERR_STATE;
+  const char* o = (const char*)buf;
+  StateHeader hd;
+  memcpy(&hd, o, sizeof(hd));
+  if (memcmp(hd.magic, "SPAIST01", 8) != 0 || hd.n != h->n || hd.slab_total != h->slab_total ||
+      hd.prec != h->prec || hd.capmax != h->capmax || hd.W != h->W)
+    return SPAI_ERR_STATE;
+  o += sizeof(hd);
+  cudaStream_t st = h->stream;
+  // keep this handle's counters, restore the iteration scalars
+  DevScalars cur, sv;
+  CK(cudaMemcpyAsync(&cur, h->d_sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  memcpy(&sv, o, sizeof(sv));
+  sv.bytes = cur.bytes;
+  sv.spgemm_cols = cur.spgemm_cols;
+  CK(cudaMemcpyAsync(h->d_sc, &sv, sizeof(DevScalars), cudaMemcpyHostToDevice, st));
+  CK(cudaStreamSynchronize(st));
+  o += sizeof(DevScalars);
+  int* lens[3] = {h->d_Mlen, h->d_Plen, h->d_Zlen};
+  int* rows[3] = {h->d_Mrow, h->d_Prow, h->d_Zrow};
+  void* vals[3] = {h->d_Mval, h->d_Pval, h->d_Zval};
+  for (int k = 0; k < 3; k++) {
+    CK(cudaMemcpyAsync(lens[k], o, n * 4, cudaMemcpyHostToDevice, st));
+    o += n * 4;
+    CK(cudaMemcpyAsync(rows[k], o, S * 4, cudaMemcpyHostToDevice, st));
+    o += S * 4;
+    CK(cudaMemcpyAsync(vals[k], o, S * vs, cudaMemcpyHostToDevice, st));
+    o += S * vs;
+  }
+  CK(cudaStreamSynchronize(st));
+  h->method = hd.method;
+  h->it = hd.it;
+  invalidate_rows(h);
+  return SPAI_OK;
+}
+
+int spai_set_timing(spai_handle h, int enable) {
+  if (!h) return SPAI_ERR_ARG;
+  h->timing = enable != 0;
+  return SPAI_OK;
+}
+
+int spai_get_stats(spai_handle h, spai_stats* out) {
+  if (!h || !out) return SPAI_ERR_ARG;
+  DevScalars sc;
+  CK(cudaMemcpyAsync(&sc, h->d_sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  out->colpass_launches = h->colpass_launches;
+  out->colpass_bytes = (int64_t)(sc.bytes + h->a_bytes_total);
+  out->colpass_ms = h->colpass_ms;
+  out->pcg_launches = h->pcg_launches;
+  out->other_launches = h->other_launches;
+  out->spgemm_columns = (int64_t)sc.spgemm_cols;
+  return SPAI_OK;
+}
+
+}  // extern "C"

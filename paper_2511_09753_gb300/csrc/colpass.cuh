@@ -1,0 +1,410 @@
+// The fused column pass: one launch performs, for every column j, the
+// column-local part of one MR / LOMR / CG iteration (pattern-union update,
+// hard thresholding, explicit residual, direction, direction product and the
+// per-column Frobenius partials), then reduces the partials over all
+// columns with a fixed pairwise tree and lets the last-arriving CTA compute
+// the step coefficients for the next pass.  Columns only interact through
+// those few FP64 sums (Sec. 2: the iterations are global only through the
+// Frobenius inner products).
+#pragma once
+#include "common.cuh"
+#include "warp_ops.cuh"
+
+namespace spai {
+
+// Contiguous pairwise tree over v[0..len) (len a power of two <= 1024 or
+// any len with zero padding to 32 minimum), computed by warp 0.  Values are
+// read from global memory with L1 bypass.
+__device__ inline double block_tree_global(const double* v, int len, double* red, int lane, int warp) {
+  // len <= 32*32; lane handles c contiguous entries, c = P2/32
+  int P2 = 32;
+  while (P2 < len) P2 <<= 1;
+  int c = P2 / 32;
+  double s = 0.0;
+  if (warp == 0) {
+    for (int t = 0; t < c; t++) {
+      int i = lane * c + t;
+      red[i] = i < len ? __ldcg(v + i) : 0.0;
+    }
+    __syncwarp();
+    s = warp_pairwise(red, P2, lane);
+  }
+  return s;
+}
+
+template <typename VS, typename VC>
+struct ColCtx {
+  const PassParams& p;
+  char* ws;
+  int lane;
+  int overflow;
+  unsigned long long bytes;
+  unsigned long long spg;
+  __device__ ColCtx(const PassParams& pp, char* w, int l)
+      : p(pp), ws(w), lane(l), overflow(0), bytes(0), spg(0) {}
+  template <typename T> __device__ T* at(int off) const { return (T*)(ws + off); }
+};
+
+template <typename VS, typename VC>
+__device__ int load_col(ColCtx<VS, VC>& c, const int* grow, const void* gval, long long off, int len,
+                        int* sr, VC* sv) {
+  const VS* gv = (const VS*)gval;
+  for (int e = c.lane; e < len; e += 32) {
+    sr[e] = grow[off + e];
+    sv[e] = (VC)gv[off + e];
+  }
+  __syncwarp();
+  c.bytes += (unsigned long long)len * (sizeof(int) + sizeof(VS)) + sizeof(int);
+  return len;
+}
+
+template <typename VS, typename VC>
+__device__ void store_col(ColCtx<VS, VC>& c, int* grow, void* gval, int* glen, int j, long long off,
+                          int len, const int* sr, const VC* sv) {
+  VS* gv = (VS*)gval;
+  for (int e = c.lane; e < len; e += 32) {
+    grow[off + e] = sr[e];
+    gv[off + e] = (VS)sv[e];
+  }
+  if (c.lane == 0) glen[j] = len;
+  c.bytes += (unsigned long long)len * (sizeof(int) + sizeof(VS)) + sizeof(int);
+}
+
+// Column work of one pass.  part[0..nq) receives the column partials.
+template <typename VS, typename VC>
+__device__ void column_work(ColCtx<VS, VC>& c, int j, double* part) {
+  const PassParams& p = c.p;
+  const WarpLayout& L = p.lay;
+  const int lane = c.lane;
+  const long long off = p.off[j];
+  const int cap = p.cap[j];
+  int* Mr = c.template at<int>(L.Mr);
+  VC* Mv = c.template at<VC>(L.Mv);
+  int* Pr = c.template at<int>(L.Pr);
+  VC* Pv = c.template at<VC>(L.Pv);
+  int* Tr = c.template at<int>(L.Tr);
+  VC* Tv = c.template at<VC>(L.Tv);
+  int* Rr = c.template at<int>(L.Rr);
+  VC* Rv = c.template at<VC>(L.Rv);
+  int* Qr = c.template at<int>(L.Qr);
+  VC* Qv = c.template at<VC>(L.Qv);
+  uint16_t* dp = c.template at<uint16_t>(L.dp);
+  uint32_t* hist = c.template at<uint32_t>(L.hist);
+  double* dt = c.template at<double>(L.dtmp);
+  VC* aval = c.template at<VC>(L.aval);
+  SpgemmScratch ss;
+  ss.key0 = c.template at<uint32_t>(L.key0);
+  ss.key1 = c.template at<uint32_t>(L.key1);
+  ss.idx0 = c.template at<uint16_t>(L.idx0);
+  ss.idx1 = c.template at<uint16_t>(L.idx1);
+  ss.hp = c.template at<uint16_t>(L.hp);
+  ss.hist = hist;
+  int* ovf = &c.overflow;
+
+  int Lm = load_col(c, p.Mrow, p.Mval, off, p.Mlen[j], Mr, Mv);
+
+  if (p.kind == kRES) {
+    int LR = warp_spgemm(p, ss, aval, Mr, Mv, Lm, j, Rr, Rv, lane);
+    c.spg++;
+    part[0] = warp_norm2(Rv, LR, dt, lane);
+    return;
+  }
+
+  if (p.kind == kMR) {
+    if (p.do_update) {
+      int Lp = load_col(c, p.Prow, p.Pval, off, p.Plen[j], Pr, Pv);
+      CombAxpy<VC> f{p.sc->alpha};
+      int Lt = warp_union(Mr, Mv, Lm, Pr, Pv, Lp, Tr, Tv, dp, f, lane);
+      Lm = warp_select(Tr, Tv, Lt, cap, Mr, Mv, hist, p.drop, ovf, lane);
+      store_col(c, p.Mrow, p.Mval, p.Mlen, j, off, Lm, Mr, Mv);
+    }
+    int LR = warp_spgemm(p, ss, aval, Mr, Mv, Lm, j, Rr, Rv, lane);
+    c.spg++;
+    part[0] = warp_norm2(Rv, LR, dt, lane);
+    if (!p.do_dir) return;
+    int Lp = warp_select(Rr, Rv, LR, cap, Pr, Pv, hist, p.drop, ovf, lane);
+    store_col(c, p.Prow, p.Pval, p.Plen, j, off, Lp, Pr, Pv);
+    int LQ = warp_spgemm(p, ss, aval, Pr, Pv, Lp, -1, Qr, Qv, lane);
+    c.spg++;
+    part[1] = warp_dot(Rr, Rv, LR, Qr, Qv, LQ, dt, lane);
+    part[2] = warp_norm2(Qv, LQ, dt, lane);
+    return;
+  }
+
+  if (p.kind == kLOMR) {
+    int* Zr = c.template at<int>(L.Zr);
+    VC* Zv = c.template at<VC>(L.Zv);
+    int* Sr = c.template at<int>(L.Sr);
+    VC* Sv = c.template at<VC>(L.Sv);
+    int* Vr = c.template at<int>(L.Vr);
+    VC* Vv = c.template at<VC>(L.Vv);
+    int Lp = load_col(c, p.Prow, p.Pval, off, p.Plen[j], Pr, Pv);
+    if (p.do_update) {
+      int Lz = load_col(c, p.Zrow, p.Zval, off, p.Zlen[j], Zr, Zv);
+      CombLin<VC> fl{p.sc->delta, p.sc->gamma};
+      int Ls = warp_union(Zr, Zv, Lz, Pr, Pv, Lp, Sr, Sv, dp, fl, lane);
+      Lp = warp_select(Sr, Sv, Ls, cap, Pr, Pv, hist, p.drop, ovf, lane);
+      store_col(c, p.Prow, p.Pval, p.Plen, j, off, Lp, Pr, Pv);
+      CombAdd<VC> fa;
+      int Lt = warp_union(Mr, Mv, Lm, Sr, Sv, Ls, Tr, Tv, dp, fa, lane);
+      Lm = warp_select(Tr, Tv, Lt, cap, Mr, Mv, hist, p.drop, ovf, lane);
+      store_col(c, p.Mrow, p.Mval, p.Mlen, j, off, Lm, Mr, Mv);
+    }
+    int LR = warp_spgemm(p, ss, aval, Mr, Mv, Lm, j, Rr, Rv, lane);
+    c.spg++;
+    part[0] = warp_norm2(Rv, LR, dt, lane);
+    if (!p.do_dir) return;
+    int Lz = warp_select(Rr, Rv, LR, cap, Zr, Zv, hist, p.drop, ovf, lane);
+    store_col(c, p.Zrow, p.Zval, p.Zlen, j, off, Lz, Zr, Zv);
+    int LU = warp_spgemm(p, ss, aval, Zr, Zv, Lz, -1, Qr, Qv, lane);
+    int LV = warp_spgemm(p, ss, aval, Pr, Pv, Lp, -1, Vr, Vv, lane);
+    c.spg += 2;
+    part[1] = warp_norm2(Qv, LU, dt, lane);                      // (U,U)
+    part[2] = warp_norm2(Vv, LV, dt, lane);                      // (V,V)
+    part[3] = warp_dot(Qr, Qv, LU, Vr, Vv, LV, dt, lane);        // (U,V)
+    part[4] = warp_dot(Qr, Qv, LU, Rr, Rv, LR, dt, lane);        // (U,R)
+    part[5] = warp_dot(Vr, Vv, LV, Rr, Rv, LR, dt, lane);        // (V,R)
+    return;
+  }
+
+  if (p.kind == kCGA) {
+    int Lp = load_col(c, p.Prow, p.Pval, off, p.Plen[j], Pr, Pv);
+    CombAxpy<VC> f{p.sc->alpha};
+    int Lt = warp_union(Mr, Mv, Lm, Pr, Pv, Lp, Tr, Tv, dp, f, lane);
+    Lm = warp_select(Tr, Tv, Lt, cap, Mr, Mv, hist, p.drop, ovf, lane);
+    store_col(c, p.Mrow, p.Mval, p.Mlen, j, off, Lm, Mr, Mv);
+    int LR = warp_spgemm(p, ss, aval, Mr, Mv, Lm, j, Rr, Rv, lane);
+    c.spg++;
+    part[0] = warp_norm2(Rv, LR, dt, lane);
+    return;
+  }
+
+  // kCGB
+  {
+    int Lp = load_col(c, p.Prow, p.Pval, off, p.Plen[j], Pr, Pv);
+    int LR = warp_spgemm(p, ss, aval, Mr, Mv, Lm, j, Rr, Rv, lane);
+    c.spg++;
+    part[0] = warp_norm2(Rv, LR, dt, lane);
+    CombAxpy<VC> f{p.sc->beta};
+    int Lt = warp_union(Rr, Rv, LR, Pr, Pv, Lp, Tr, Tv, dp, f, lane);
+    Lp = warp_select(Tr, Tv, Lt, cap, Pr, Pv, hist, p.drop, ovf, lane);
+    store_col(c, p.Prow, p.Pval, p.Plen, j, off, Lp, Pr, Pv);
+    int LQ = warp_spgemm(p, ss, aval, Pr, Pv, Lp, -1, Qr, Qv, lane);
+    c.spg++;
+    part[1] = warp_dot(Pr, Pv, Lp, Qr, Qv, LQ, dt, lane);
+  }
+}
+
+__device__ __forceinline__ bool isfin(double x) { return !isnan(x) && !isinf(x); }
+
+// Step coefficients from the global sums t[0..nq); thread 0 of the last CTA.
+__device__ inline void coefficients(const PassParams& p, const double* t) {
+  DevScalars* sc = p.sc;
+  const int it = p.iter;
+  if (p.kind == kRES) {
+    sc->result = t[0];
+    return;
+  }
+  if (p.kind == kMR || p.kind == kLOMR) {
+    double rr = t[0];
+    if (p.do_update) sc->done += 1;
+    if (p.hist_res) p.hist_res[it] = __dsqrt_rn(rr);
+    if (!p.do_dir) return;
+    if (rr == 0.0) {
+      sc->stop = 1;
+      sc->flags |= kFlagConverged;
+      return;
+    }
+    if (p.kind == kMR) {
+      double rq = t[1], qq = t[2];
+      if (qq == 0.0) {
+        sc->stop = 1;
+        sc->flags |= kFlagConverged;
+        return;
+      }
+      double alpha = __ddiv_rn(rq, qq);
+      if (!isfin(alpha)) {
+        sc->stop = 1;
+        sc->flags |= kFlagNonfinite;
+        return;
+      }
+      sc->alpha = alpha;
+      if (p.hist_coef) {
+        p.hist_coef[2 * it] = alpha;
+        p.hist_coef[2 * it + 1] = 0.0;
+      }
+    } else {
+      double uu = t[1], vv = t[2], uv = t[3], ur = t[4], vr = t[5];
+      if (uu == 0.0) {
+        sc->stop = 1;
+        sc->flags |= kFlagConverged;
+        return;
+      }
+      double t1 = __dmul_rn(uu, vv), t2 = __dmul_rn(uv, uv);
+      double cc = __dsub_rn(t1, t2);
+      const double eps = 2.220446049250313e-16;
+      double delta, gamma;
+      if (vv == 0.0 || cc <= __dmul_rn(__dmul_rn(64.0, eps), t1)) {
+        delta = __ddiv_rn(ur, uu);
+        gamma = 0.0;
+        if (vv != 0.0) sc->flags |= kFlagFallback;
+      } else {
+        double d1 = __dmul_rn(vv, ur), d2 = __dmul_rn(uv, vr);
+        double g1 = __dmul_rn(uu, vr), g2 = __dmul_rn(uv, ur);
+        delta = __ddiv_rn(__dsub_rn(d1, d2), cc);
+        gamma = __ddiv_rn(__dsub_rn(g1, g2), cc);
+      }
+      if (!isfin(delta) || !isfin(gamma)) {
+        sc->stop = 1;
+        sc->flags |= kFlagNonfinite;
+        return;
+      }
+      sc->delta = delta;
+      sc->gamma = gamma;
+      if (p.hist_coef) {
+        p.hist_coef[2 * it] = delta;
+        p.hist_coef[2 * it + 1] = gamma;
+      }
+    }
+    return;
+  }
+  if (p.kind == kCGB) {
+    double rr = t[0], pq = t[1];
+    if (p.fresh && p.hist_res) p.hist_res[0] = __dsqrt_rn(rr);
+    if (rr == 0.0 || pq == 0.0) {
+      sc->stop = 1;
+      sc->flags |= kFlagConverged;
+      return;
+    }
+    double alpha = __ddiv_rn(rr, pq);
+    if (!isfin(alpha)) {
+      sc->stop = 1;
+      sc->flags |= kFlagNonfinite;
+      return;
+    }
+    sc->alpha = alpha;
+    sc->rr = rr;
+    return;
+  }
+  // kCGA
+  {
+    double rr1 = t[0];
+    double beta = __ddiv_rn(rr1, sc->rr);
+    if (p.hist_res) p.hist_res[it + 1] = __dsqrt_rn(rr1);
+    if (p.hist_coef) {
+      p.hist_coef[2 * it] = sc->alpha;
+      p.hist_coef[2 * it + 1] = beta;
+    }
+    sc->done += 1;
+    sc->rr = rr1;
+    sc->beta = beta;
+    if (rr1 == 0.0) {
+      sc->stop = 1;
+      sc->flags |= kFlagConverged;
+    }
+  }
+}
+
+template <typename VS, typename VC>
+__global__ void __launch_bounds__(256) colpass_kernel(const PassParams p) {
+  extern __shared__ __align__(16) char smem[];
+  if (p.sc->stop) return;
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  const int nq = p.do_dir ? pass_nq(p.kind) : 1;
+  double* part = (double*)(smem + p.part_off);  // [nq][B]
+  double* red = (double*)(smem + p.red_off);    // reduction scratch (>= 1024 doubles)
+  ColCtx<VS, VC> c(p, smem + warp * p.lay.bytes, lane);
+  const int B = p.B;
+  const long long j0 = (long long)blockIdx.x * B;
+  for (int cc = warp; cc < B; cc += p.NW) {
+    long long j = j0 + cc;
+    double pr[6] = {0, 0, 0, 0, 0, 0};
+    if (j < p.n) column_work<VS, VC>(c, (int)j, pr);
+    if (lane == 0)
+      for (int q = 0; q < nq; q++) part[q * B + cc] = pr[q];
+  }
+  // per-CTA counters
+  __shared__ unsigned long long s_bytes, s_spg;
+  __shared__ int s_ovf, s_last1, s_last2;
+  if (threadIdx.x == 0) {
+    s_bytes = 0;
+    s_spg = 0;
+    s_ovf = 0;
+  }
+  __syncthreads();
+  if (lane == 0) {
+    atomicAdd(&s_bytes, c.bytes);
+    atomicAdd(&s_spg, c.spg);
+    if (c.overflow) atomicOr(&s_ovf, 1);
+  }
+  // CTA tree over the B column partials of each quantity
+  for (int q = 0; q < nq; q++) {
+    const double* v = part + q * B;
+    double s;
+    if (B <= 32) {
+      if (warp == 0) s = warp_tree32(lane < B ? v[lane] : 0.0);
+    } else {
+      int nw = B / 32;  // <= 32
+      if (warp < nw) {
+        double w = warp_tree32(v[warp * 32 + lane]);
+        if (lane == 0) red[warp] = w;
+      }
+      __syncthreads();
+      if (warp == 0) s = warp_tree32(lane < nw ? red[lane] : 0.0);
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) p.bsum[(long long)q * p.nb + blockIdx.x] = s;
+  }
+  __syncthreads();
+  // last-arriver tree: groups of kGroup blocks, then all groups
+  const int g = blockIdx.x / kGroup;
+  if (threadIdx.x == 0) {
+    if (s_ovf) atomicOr(&p.sc->flags, kFlagCapacity);
+    atomicAdd(&p.sc->bytes, s_bytes);
+    atomicAdd(&p.sc->spgemm_cols, s_spg);
+    __threadfence();
+    int gsize = min(kGroup, p.nb - g * kGroup);
+    unsigned old = atomicAdd(&p.cnt1[g], 1u);
+    s_last1 = (old == (unsigned)(gsize - 1));
+  }
+  __syncthreads();
+  if (!s_last1) return;
+  __threadfence();
+  {
+    int gsize = min(kGroup, p.nb - g * kGroup);
+    for (int q = 0; q < nq; q++) {
+      // contiguous tree over the group's 64 blocks (zero padded)
+      double s = 0.0;
+      if (warp == 0) {
+        const double* v = p.bsum + (long long)q * p.nb + (long long)g * kGroup;
+        double a = (2 * lane < gsize) ? __ldcg(v + 2 * lane) : 0.0;
+        double b = (2 * lane + 1 < gsize) ? __ldcg(v + 2 * lane + 1) : 0.0;
+        s = warp_tree32(__dadd_rn(a, b));
+      }
+      if (threadIdx.x == 0) p.gsum[(long long)q * p.ngroups + g] = s;
+    }
+  }
+  if (threadIdx.x == 0) {
+    p.cnt1[g] = 0;
+    __threadfence();
+    unsigned old = atomicAdd(p.cnt2, 1u);
+    s_last2 = (old == (unsigned)(p.ngroups - 1));
+  }
+  __syncthreads();
+  if (!s_last2) return;
+  __threadfence();
+  __shared__ double tot[6];
+  for (int q = 0; q < nq; q++) {
+    double s = block_tree_global(p.gsum + (long long)q * p.ngroups, p.ngroups, red, lane, warp);
+    if (threadIdx.x == 0) tot[q] = s;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    *p.cnt2 = 0;
+    coefficients(p, tot);
+    __threadfence();
+  }
+}
+
+}  // namespace spai

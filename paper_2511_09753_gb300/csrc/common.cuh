@@ -1,0 +1,94 @@
+// Internal types shared by the column-pass kernels, the PCG kernels and the
+// host API of libspai.so.  Not part of the C ABI.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace spai {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+// Device-resident scalars of one handle.  Written only by the last-arriving
+// CTA of a pass (or by the host between calls); read by the next pass.
+struct DevScalars {
+  double alpha, beta, delta, gamma;  // step coefficients for the next pass
+  double rr;                         // CG: ||R_i||_F^2 of the current residual
+  double result;                     // scalar result of a norm pass
+  int stop;                          // nonzero: later passes of this call do nothing
+  int flags;                         // kFlag* bits
+  int done;                          // iterations completed in this call
+  int pad;
+  unsigned long long bytes;          // algorithmic bytes moved by column passes
+  unsigned long long spgemm_cols;    // column SpGEMMs performed
+};
+
+enum : int {
+  kFlagConverged = 1,
+  kFlagFallback = 2,
+  kFlagNonfinite = 4,
+  kFlagCapacity = 8,
+};
+
+// Which column pass a launch performs.
+enum PassKind : int {
+  kMR = 0,     // [update M with alpha] then R, P = D(R), Q = A P; partials rr, rq, qq
+  kLOMR = 1,   // [S, P = D(S), M = D(M+S)] then R, Z = D(R), U = A Z, V = A P; 6 partials
+  kCGA = 2,    // M = D(M + alpha P); R; partial rr
+  kCGB = 3,    // R; P = D(R + beta P); Q = A P; partials rr, pq
+  kRES = 4,    // R = I - A M in FP64; partial rr
+};
+
+// Byte offsets of one warp's scratch inside the CTA's dynamic shared memory.
+struct WarpLayout {
+  int Mr, Mv, Pr, Pv, Zr, Zv;   // capped lists (CAP)
+  int Sr, Sv;                   // LOMR S list (2 CAP)
+  int Tr, Tv;                   // union output before drop (TMAX)
+  int Rr, Rv, Qr, Qv, Vr, Vv;   // SpGEMM outputs (LMAX)
+  int key0, key1;               // u32 [PMAX+1]
+  int idx0, idx1;               // u16 [PMAX+1]
+  int aval;                     // VC  [PMAX]
+  int hp;                       // u16 [LMAX+1]
+  int dp;                       // u16 [TMAX+1]
+  int hist;                     // u32 [256]
+  int dtmp;                     // f64 [DMAX]
+  int bytes;                    // total per warp (multiple of 16)
+};
+
+struct PassParams {
+  int n;
+  int W;             // ELL width of A
+  uint32_t magicW;   // ceil(2^32 / W): q / W == __umulhi(q, magicW) for q < 2^16
+  int B;             // columns per CTA (power of two)
+  int NW;            // warps per CTA
+  int capmax, pmax, lmax, tmax;
+  int kind;
+  int do_update, do_dir, drop;
+  int iter;          // history slot of this pass
+  int fresh;         // CG: first B pass of a call (writes history[0])
+  const long long* off;  // slab offsets (per column)
+  const int* cap;        // per-column cap
+  int* Mrow; void* Mval; int* Mlen;
+  int* Prow; void* Pval; int* Plen;
+  int* Zrow; void* Zval; int* Zlen;
+  const int* ell_col;
+  const void* ell_val;   // VC values of A in ELL layout
+  DevScalars* sc;
+  double* hist_res;      // [iters+1]
+  double* hist_coef;     // [2*iters]
+  double* bsum;          // [NQ][nb]
+  double* gsum;          // [NQ][ngroups]
+  unsigned* cnt1;        // [ngroups]
+  unsigned* cnt2;        // [1]
+  int nb, ngroups;
+  WarpLayout lay;
+  int part_off;          // byte offset of the CTA partials [NQ][B]
+  int red_off;           // byte offset of CTA reduction scratch
+};
+
+constexpr int kGroup = 64;  // blocks per group in the last-arriver reduction tree
+
+__host__ __device__ inline int pass_nq(int kind) {
+  return kind == kMR ? 3 : kind == kLOMR ? 6 : kind == kCGB ? 2 : 1;
+}
+
+}  // namespace spai

@@ -1,0 +1,481 @@
+// Set-up, export, transpose and vector-PCG kernels of libspai.so.
+//
+// PCG (the assessment of Sec. 7): x_0 = 0, FP64 vectors and scalars;
+// SpMV rows are fma chains over ascending column; vector inner products are
+// balanced pairwise trees over the index range (same tree as the Frobenius
+// sums of the column pass); the preconditioner is none, Jacobi, M or the
+// symmetric part (M + M^T)/2.
+#include <stdint.h>
+
+#include "common.cuh"
+#include "vec_kernels.cuh"
+#include "warp_ops.cuh"
+
+namespace spai {
+
+// ------------------------------------------------------------- reduction
+
+// Each thread contributes one term (its element); the CTA (256 threads)
+// reduces by a contiguous tree, then the last-arriving CTA of each group of
+// kGroup CTAs, then the last group, calls finish(total) in its thread 0.
+template <typename F>
+__device__ void reduce_finish(double term, const RedWS& w, F finish) {
+  __shared__ double red[1024];
+  __shared__ int s_last;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nw = blockDim.x >> 5;
+  double s = warp_tree32(term);
+  if (lane == 0) red[warp] = s;
+  __syncthreads();
+  if (warp == 0) s = warp_tree32(lane < nw ? red[lane] : 0.0);
+  const int g = blockIdx.x / kGroup;
+  if (threadIdx.x == 0) {
+    w.bsum[blockIdx.x] = s;
+    __threadfence();
+    int gsize = min(kGroup, w.nb - g * kGroup);
+    unsigned old = atomicAdd(&w.cnt1[g], 1u);
+    s_last = old == (unsigned)(gsize - 1);
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  if (warp == 0) {
+    int gsize = min(kGroup, w.nb - g * kGroup);
+    const double* v = w.bsum + (long long)g * kGroup;
+    double a = (2 * lane < gsize) ? __ldcg(v + 2 * lane) : 0.0;
+    double b = (2 * lane + 1 < gsize) ? __ldcg(v + 2 * lane + 1) : 0.0;
+    s = warp_tree32(__dadd_rn(a, b));
+  }
+  if (threadIdx.x == 0) {
+    w.gsum[g] = s;
+    w.cnt1[g] = 0;
+    __threadfence();
+    unsigned old = atomicAdd(w.cnt2, 1u);
+    s_last = old == (unsigned)(w.ngroups - 1);
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  if (warp == 0) {
+    int P2 = 32;
+    while (P2 < w.ngroups) P2 <<= 1;
+    int c = P2 / 32;
+    for (int t = 0; t < c; t++) {
+      int i = lane * c + t;
+      red[i] = i < w.ngroups ? __ldcg(w.gsum + i) : 0.0;
+    }
+    __syncwarp();
+    s = warp_pairwise(red, P2, lane);
+  }
+  if (threadIdx.x == 0) {
+    *w.cnt2 = 0;
+    finish(s);
+    __threadfence();
+  }
+}
+
+__device__ __forceinline__ bool finite_d(double x) { return !isnan(x) && !isinf(x); }
+
+// y_i = fma chain over row i of a CSR matrix (ascending column)
+template <typename RP, typename V>
+__device__ __forceinline__ double row_chain(const RP* rp, const int* ci, const V* v, const double* x,
+                                            int i) {
+  double acc = 0.0;
+  const RP e1 = rp[i + 1];
+  for (RP e = rp[i]; e < e1; e++) acc = __fma_rn((double)v[e], x[ci[e]], acc);
+  return acc;
+}
+
+// ------------------------------------------------------------ set-up
+
+template <typename VS>
+__global__ void k_init_slab(int n, const long long* off, const double* diag, int* Mrow, VS* Mval,
+                            int* Mlen, int* Plen, int* Zlen) {
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  double m0 = __ddiv_rn(1.0, diag[j]);
+  VS v = (VS)m0;
+  Mrow[off[j]] = j;
+  Mval[off[j]] = v;
+  Mlen[j] = v != VS(0) ? 1 : 0;
+  Plen[j] = 0;
+  Zlen[j] = 0;
+}
+
+cudaError_t launch_init_slab(int prec, int n, const long long* off, const double* diag, int* Mrow,
+                             void* Mval, int* Mlen, int* Plen, int* Zlen, cudaStream_t st) {
+  int g = (n + 255) / 256;
+  if (prec == 1)
+    k_init_slab<float><<<g, 256, 0, st>>>(n, off, diag, Mrow, (float*)Mval, Mlen, Plen, Zlen);
+  else
+    k_init_slab<double><<<g, 256, 0, st>>>(n, off, diag, Mrow, (double*)Mval, Mlen, Plen, Zlen);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------- scan
+
+// exclusive scan of int32 counts into int32/int64 offsets, 1024 per block
+__global__ void k_scan_block(const int* in, long long* out, long long* bsum, int n) {
+  __shared__ long long s[1024];
+  int i = blockIdx.x * 1024 + threadIdx.x;
+  long long v = i < n ? in[i] : 0;
+  s[threadIdx.x] = v;
+  __syncthreads();
+  for (int o = 1; o < 1024; o <<= 1) {
+    long long t = threadIdx.x >= o ? s[threadIdx.x - o] : 0;
+    __syncthreads();
+    s[threadIdx.x] += t;
+    __syncthreads();
+  }
+  if (i < n) out[i] = s[threadIdx.x] - v;
+  if (threadIdx.x == 1023) bsum[blockIdx.x] = s[1023];
+}
+
+__global__ void k_scan_add(long long* out, const long long* boff, int n) {
+  int i = blockIdx.x * 1024 + threadIdx.x;
+  if (i < n) out[i] += boff[blockIdx.x];
+}
+
+__global__ void k_scan_small(const long long* in, long long* out, int n, long long* total) {
+  // single block, sequential over chunks of 1024
+  __shared__ long long s[1024];
+  __shared__ long long carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int base = 0; base < n; base += 1024) {
+    int i = base + threadIdx.x;
+    long long v = i < n ? in[i] : 0;
+    s[threadIdx.x] = v;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {
+      long long t = threadIdx.x >= o ? s[threadIdx.x - o] : 0;
+      __syncthreads();
+      s[threadIdx.x] += t;
+      __syncthreads();
+    }
+    if (i < n) out[i] = carry + s[threadIdx.x] - v;
+    __syncthreads();
+    if (threadIdx.x == 0) carry += s[1023];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0 && total) *total = carry;
+}
+
+// out[0..n) = exclusive scan of in, out[n] = total.  tmp: >= 2*ceil(n/1024)+1
+cudaError_t launch_exclusive_scan(const int* in, long long* out, int n, long long* tmp,
+                                  cudaStream_t st) {
+  int nb = (n + 1023) / 1024;
+  if (nb == 0) nb = 1;
+  k_scan_block<<<nb, 1024, 0, st>>>(in, out, tmp, n);
+  k_scan_small<<<1, 1024, 0, st>>>(tmp, tmp + nb, nb, out + n);
+  k_scan_add<<<nb, 1024, 0, st>>>(out, tmp + nb, n);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------- export / transpose
+
+template <typename VS>
+__global__ void k_export_csc(int n, const long long* off, const int* Mrow, const VS* Mval,
+                             const long long* colptr, int* rowind, double* vals) {
+  int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (j >= n) return;
+  long long src = off[j], dst = colptr[j];
+  int len = (int)(colptr[j + 1] - dst);
+  for (int e = lane; e < len; e += 32) {
+    rowind[dst + e] = Mrow[src + e];
+    vals[dst + e] = (double)Mval[src + e];
+  }
+}
+
+__global__ void k_ll_to_i32(const long long* a, int* b, int n) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i <= n) b[i] = (int)a[i];
+}
+
+cudaError_t launch_export_csc(int prec, int n, const long long* off, const int* Mrow,
+                              const void* Mval, const long long* colptr, int* rowind, double* vals,
+                              cudaStream_t st) {
+  int g = (int)(((long long)n * 32 + 255) / 256);
+  if (prec == 1)
+    k_export_csc<float><<<g, 256, 0, st>>>(n, off, Mrow, (const float*)Mval, colptr, rowind, vals);
+  else
+    k_export_csc<double><<<g, 256, 0, st>>>(n, off, Mrow, (const double*)Mval, colptr, rowind, vals);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ll_to_i32(const long long* a, int* b, int n, cudaStream_t st) {
+  k_ll_to_i32<<<(n + 1 + 255) / 256, 256, 0, st>>>(a, b, n);
+  return cudaGetLastError();
+}
+
+__global__ void k_count_rows(int n, const long long* colptr, const int* rowind, int* cnt) {
+  long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= colptr[n]) return;
+  atomicAdd(&cnt[rowind[e]], 1);
+}
+
+// scatter CSC entries into row buckets (unordered within a row)
+__global__ void k_fill_rows(int n, const long long* colptr, const int* rowind, const double* vals,
+                            const long long* rowptr, int* cursor, int* ci, double* cv) {
+  int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (j >= n) return;
+  for (long long e = colptr[j] + lane; e < colptr[j + 1]; e += 32) {
+    int r = rowind[e];
+    int pos = atomicAdd(&cursor[r], 1);
+    ci[rowptr[r] + pos] = j;
+    cv[rowptr[r] + pos] = vals[e];
+  }
+}
+
+// sort each row by column (keys unique): rank by counting, warp per row
+__global__ void k_sort_rows(int n, const long long* rowptr, int* ci, double* cv, int* tmpi,
+                            double* tmpv) {
+  int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (i >= n) return;
+  long long b = rowptr[i], e = rowptr[i + 1];
+  int L = (int)(e - b);
+  for (int a = lane; a < L; a += 32) {
+    int key = ci[b + a];
+    int rank = 0;
+    for (int t = 0; t < L; t++) rank += ci[b + t] < key;
+    tmpi[b + rank] = key;
+    tmpv[b + rank] = cv[b + a];
+  }
+  __syncwarp();
+  for (int a = lane; a < L; a += 32) {
+    ci[b + a] = tmpi[b + a];
+    cv[b + a] = tmpv[b + a];
+  }
+}
+
+// symmetric part S = (M + M^T)/2: row i of S merges CSR row i of M and CSC
+// column i of M; s = 0.5 * (m_ij + m_ji); exact zeros dropped.
+// pass 0 counts, pass 1 fills.
+__global__ void k_sym_rows(int n, const long long* rp, const int* rci, const double* rv,
+                           const long long* cp, const int* cri, const double* cvv, int pass,
+                           int* cnt, const long long* srp, int* sci, double* sv) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  long long a = rp[i], ae = rp[i + 1], b = cp[i], be = cp[i + 1];
+  long long t = pass ? srp[i] : 0;
+  int c = 0;
+  while (a < ae || b < be) {
+    int col;
+    double u = 0.0, w = 0.0;
+    if (b >= be || (a < ae && rci[a] < cri[b])) {
+      col = rci[a];
+      u = rv[a++];
+    } else if (a >= ae || cri[b] < rci[a]) {
+      col = cri[b];
+      w = cvv[b++];
+    } else {
+      col = rci[a];
+      u = rv[a++];
+      w = cvv[b++];
+    }
+    double val = __dmul_rn(0.5, __dadd_rn(u, w));
+    if (val != 0.0) {
+      if (pass) {
+        sci[t + c] = col;
+        sv[t + c] = val;
+      }
+      c++;
+    }
+  }
+  if (!pass) cnt[i] = c;
+}
+
+cudaError_t launch_transpose(int n, const long long* colptr, const int* rowind, const double* vals,
+                             long long nnz, int* cnt, long long* rowptr, long long* scan_tmp,
+                             int* ci, double* cv, int* tmpi, double* tmpv, cudaStream_t st) {
+  cudaMemsetAsync(cnt, 0, sizeof(int) * (size_t)n, st);
+  if (nnz > 0) k_count_rows<<<(int)((nnz + 255) / 256), 256, 0, st>>>(n, colptr, rowind, cnt);
+  launch_exclusive_scan(cnt, rowptr, n, scan_tmp, st);
+  cudaMemsetAsync(cnt, 0, sizeof(int) * (size_t)n, st);
+  int g = (int)(((long long)n * 32 + 255) / 256);
+  k_fill_rows<<<g, 256, 0, st>>>(n, colptr, rowind, vals, rowptr, cnt, ci, cv);
+  k_sort_rows<<<g, 256, 0, st>>>(n, rowptr, ci, cv, tmpi, tmpv);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sym(int n, const long long* rp, const int* rci, const double* rv,
+                       const long long* cp, const int* cri, const double* cvv, int pass, int* cnt,
+                       const long long* srp, int* sci, double* sv, cudaStream_t st) {
+  k_sym_rows<<<(n + 255) / 256, 256, 0, st>>>(n, rp, rci, rv, cp, cri, cvv, pass, cnt, srp, sci, sv);
+  return cudaGetLastError();
+}
+
+// -------------------------------------------------------- y = M x (apply)
+
+__global__ void k_spmv_multi(int n, const long long* rp, const int* ci, const double* v,
+                             const double* x, double* y, int nrhs, long long ld) {
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)n * nrhs) return;
+  int k = (int)(t / n), i = (int)(t % n);
+  const double* xk = x + (long long)k * ld;
+  double acc = 0.0;
+  for (long long e = rp[i]; e < rp[i + 1]; e++) acc = __fma_rn(v[e], xk[ci[e]], acc);
+  y[(long long)k * ld + i] = acc;
+}
+
+cudaError_t launch_apply(int n, const long long* rp, const int* ci, const double* v, const double* x,
+                         double* y, int nrhs, long long ld, cudaStream_t st) {
+  long long tot = (long long)n * nrhs;
+  k_spmv_multi<<<(int)((tot + 255) / 256), 256, 0, st>>>(n, rp, ci, v, x, y, nrhs, ld);
+  return cudaGetLastError();
+}
+
+// --------------------------------------------------------------- residual
+// FP64 ||b - A x|| helper terms: t_i = (b_i - (A x)_i)^2
+__global__ void k_true_res(PcgArgs a) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  double term = 0.0;
+  if (i < a.n) {
+    double y = row_chain(a.arp, a.aci, a.av, a.x, i);
+    double d = __dsub_rn(a.b[i], y);
+    term = __dmul_rn(d, d);
+  }
+  PcgScalars* s = a.s;
+  reduce_finish(term, a.ws, [s](double tot) { s->tres = tot; });
+}
+
+// ------------------------------------------------------------------- PCG
+
+__device__ __forceinline__ double precond_apply(const PcgArgs& a, int i) {
+  if (a.precond == 0) return a.r[i];
+  if (a.precond == 1) return __ddiv_rn(a.r[i], a.diag[i]);
+  return row_chain(a.mrp, a.mci, a.mv, a.r, i);
+}
+
+// init: x = 0, r = b, terms b_i^2 -> bn
+__global__ void k_pcg_init(PcgArgs a) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  double term = 0.0;
+  if (i < a.n) {
+    double bi = a.b[i];
+    a.x[i] = 0.0;
+    a.r[i] = bi;
+    term = __dmul_rn(bi, bi);
+  }
+  PcgScalars* s = a.s;
+  reduce_finish(term, a.ws, [s](double tot) {
+    s->bn = __dsqrt_rn(tot);
+    s->k = 0;
+    s->status = 0;
+    s->done = (tot == 0.0) ? 1 : 0;
+  });
+}
+
+// z = Prec(r), terms r_i z_i -> rho (first = 1: initial rho, p = z follows)
+__global__ void k_pcg_prec(PcgArgs a, int first) {
+  if (a.s->done) return;
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  double term = 0.0;
+  if (i < a.n) {
+    double z = precond_apply(a, i);
+    a.z[i] = z;
+    term = __dmul_rn(a.r[i], z);
+  }
+  PcgScalars* s = a.s;
+  reduce_finish(term, a.ws, [s, first](double rho1) {
+    if (rho1 == 0.0 || !finite_d(rho1)) {
+      s->done = 1;
+      s->status = 2;
+      return;
+    }
+    if (first) {
+      s->rho = rho1;
+      s->beta = 0.0;
+    } else {
+      s->beta = __ddiv_rn(rho1, s->rho);
+      s->rho = rho1;
+    }
+  });
+}
+
+// p = z (first) or p = fma(beta, p, z)
+__global__ void k_pcg_dir(PcgArgs a, int first) {
+  if (a.s->done) return;
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.n) return;
+  a.p[i] = first ? a.z[i] : __fma_rn(a.s->beta, a.p[i], a.z[i]);
+}
+
+// q = A p, terms p_i q_i -> alpha
+__global__ void k_pcg_spmv(PcgArgs a) {
+  if (a.s->done) return;
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  double term = 0.0;
+  if (i < a.n) {
+    double q = row_chain(a.arp, a.aci, a.av, a.p, i);
+    a.q[i] = q;
+    term = __dmul_rn(a.p[i], q);
+  }
+  PcgScalars* s = a.s;
+  reduce_finish(term, a.ws, [s](double pq) {
+    if (s->k >= s->maxit) {
+      s->done = 1;
+      s->status = 1;
+      return;
+    }
+    if (pq == 0.0 || !finite_d(pq)) {
+      s->done = 1;
+      s->status = 2;
+      return;
+    }
+    s->alpha = __ddiv_rn(s->rho, pq);
+  });
+}
+
+// x += alpha p, r -= alpha q, terms r_i^2 -> convergence test
+__global__ void k_pcg_update(PcgArgs a) {
+  if (a.s->done) return;
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  double term = 0.0;
+  if (i < a.n) {
+    double al = a.s->alpha;
+    a.x[i] = __fma_rn(al, a.p[i], a.x[i]);
+    double r = __fma_rn(-al, a.q[i], a.r[i]);
+    a.r[i] = r;
+    term = __dmul_rn(r, r);
+  }
+  PcgScalars* s = a.s;
+  reduce_finish(term, a.ws, [s](double rr) {
+    s->k += 1;
+    double rn = __dsqrt_rn(rr);
+    if (!finite_d(rn)) {
+      s->done = 1;
+      s->status = 2;
+    } else if (rn <= __dmul_rn(s->rtol, s->bn)) {
+      s->done = 1;
+      s->status = 0;
+    }
+  });
+}
+
+cudaError_t launch_pcg_init(const PcgArgs& a, cudaStream_t st) {
+  int g = (a.n + 255) / 256;
+  k_pcg_init<<<g, 256, 0, st>>>(a);
+  k_pcg_prec<<<g, 256, 0, st>>>(a, 1);
+  k_pcg_dir<<<g, 256, 0, st>>>(a, 1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pcg_iter(const PcgArgs& a, cudaStream_t st) {
+  int g = (a.n + 255) / 256;
+  k_pcg_spmv<<<g, 256, 0, st>>>(a);
+  k_pcg_update<<<g, 256, 0, st>>>(a);
+  k_pcg_prec<<<g, 256, 0, st>>>(a, 0);
+  k_pcg_dir<<<g, 256, 0, st>>>(a, 0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_true_res(const PcgArgs& a, cudaStream_t st) {
+  k_true_res<<<(a.n + 255) / 256, 256, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace spai

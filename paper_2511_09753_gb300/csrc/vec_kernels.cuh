@@ -1,0 +1,63 @@
+// Declarations of the set-up, transpose and PCG kernels (vec_kernels.cu).
+#pragma once
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace spai {
+
+struct RedWS {  // last-arriver reduction workspace
+  double* bsum;
+  double* gsum;
+  unsigned* cnt1;
+  unsigned* cnt2;
+  int nb, ngroups;
+};
+
+struct PcgScalars {
+  double rho, alpha, beta, bn, rtol, tres;
+  int k, maxit, done, status;
+};
+
+struct PcgArgs {
+  int n;
+  const int* arp;    // CSR of A (int32 row pointers for A)
+  const int* aci;
+  const double* av;
+  const double* diag;
+  int precond;       // 0 none, 1 Jacobi, 2/3 CSR in mrp/mci/mv
+  const long long* mrp;
+  const int* mci;
+  const double* mv;
+  const double* b;
+  double *x, *r, *z, *p, *q;
+  PcgScalars* s;
+  RedWS ws;
+};
+
+cudaError_t launch_init_slab(int prec, int n, const long long* off, const double* diag, int* Mrow,
+                             void* Mval, int* Mlen, int* Plen, int* Zlen, cudaStream_t st);
+cudaError_t launch_exclusive_scan(const int* in, long long* out, int n, long long* tmp,
+                                  cudaStream_t st);
+cudaError_t launch_export_csc(int prec, int n, const long long* off, const int* Mrow,
+                              const void* Mval, const long long* colptr, int* rowind, double* vals,
+                              cudaStream_t st);
+cudaError_t launch_ll_to_i32(const long long* a, int* b, int n, cudaStream_t st);
+cudaError_t launch_transpose(int n, const long long* colptr, const int* rowind, const double* vals,
+                             long long nnz, int* cnt, long long* rowptr, long long* scan_tmp,
+                             int* ci, double* cv, int* tmpi, double* tmpv, cudaStream_t st);
+cudaError_t launch_sym(int n, const long long* rp, const int* rci, const double* rv,
+                       const long long* cp, const int* cri, const double* cvv, int pass, int* cnt,
+                       const long long* srp, int* sci, double* sv, cudaStream_t st);
+cudaError_t launch_apply(int n, const long long* rp, const int* ci, const double* v, const double* x,
+                         double* y, int nrhs, long long ld, cudaStream_t st);
+cudaError_t launch_pcg_init(const PcgArgs& a, cudaStream_t st);
+cudaError_t launch_pcg_iter(const PcgArgs& a, cudaStream_t st);
+cudaError_t launch_true_res(const PcgArgs& a, cudaStream_t st);
+
+cudaError_t launch_colpass_f32(const PassParams& p, int grid, int block, size_t smem, cudaStream_t st);
+cudaError_t launch_colpass_f64(const PassParams& p, int grid, int block, size_t smem, cudaStream_t st);
+cudaError_t launch_colpass_res_f32(const PassParams& p, int grid, int block, size_t smem,
+                                   cudaStream_t st);
+
+}  // namespace spai

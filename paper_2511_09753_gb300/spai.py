@@ -1,0 +1,273 @@
+"""Python binding of libspai.so (ctypes; argument marshalling only).
+
+Every numeric step runs in the library's CUDA kernels; this module converts
+numpy arrays / torch CUDA tensors to pointers and codes to exceptions.  If
+the shared library is missing the import of a handle fails loudly: there is
+no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libspai.so")
+
+SPAI_FP64, SPAI_MIXED = 0, 1
+SPAI_MR, SPAI_LOMR, SPAI_CG = 0, 1, 2
+SPAI_DROP_NONE, SPAI_DROP_TOPK_COL = 0, 1
+PREC_NONE, PREC_JACOBI, PREC_SPAI, PREC_SPAI_SYM = 0, 1, 2, 3
+METHODS = {"mr": SPAI_MR, "lomr": SPAI_LOMR, "cg": SPAI_CG}
+
+OK, CONVERGED_EARLY, LOMR_FALLBACK, PCG_MAXIT, PCG_BREAKDOWN = 0, 1, 2, 3, 4
+ERR_CAPACITY = -8
+
+EXPORTED = ["spai_validate_csr", "spai_status_string", "spai_create", "spai_destroy", "spai_reset",
+            "spai_set_stream", "spai_run", "spai_mr", "spai_lomr", "spai_cg",
+            "spai_residual_norm", "spai_get_nnz", "spai_get_M", "spai_set_M", "spai_apply",
+            "pcg_solve", "spai_save_state", "spai_load_state", "spai_set_timing",
+            "spai_get_stats"]
+
+
+class SpaiError(RuntimeError):
+    def __init__(self, code, where):
+        self.code = code
+        super().__init__(f"{where}: {status_string(code)} ({code})")
+
+
+class _Opts(C.Structure):
+    _fields_ = [("prec", C.c_int), ("cap_factor", C.c_double)]
+
+
+class _Hist(C.Structure):
+    _fields_ = [("resnorm", C.c_void_p), ("coef", C.c_void_p), ("iters_done", C.c_int),
+                ("flags", C.c_int)]
+
+
+class _Stats(C.Structure):
+    _fields_ = [("colpass_launches", C.c_int64), ("colpass_bytes", C.c_int64),
+                ("colpass_ms", C.c_double), ("pcg_launches", C.c_int64),
+                ("other_launches", C.c_int64), ("spgemm_columns", C.c_int64)]
+
+
+_lib = None
+
+
+def load():
+    """Load libspai.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"libspai.so not built ({LIB_PATH}); run paper_2511_09753_gb300.build")
+    lib = C.CDLL(LIB_PATH)
+    vp, i64, i32, dbl = C.c_void_p, C.c_int64, C.c_int, C.c_double
+    sig = {
+        "spai_validate_csr": (i32, [i64, i64, vp, vp, vp, i32]),
+        "spai_status_string": (C.c_char_p, [i32]),
+        "spai_create": (i32, [C.POINTER(vp), i64, i64, vp, vp, vp, i32, C.POINTER(_Opts), vp]),
+        "spai_destroy": (i32, [vp]),
+        "spai_reset": (i32, [vp]),
+        "spai_set_stream": (i32, [vp, vp]),
+        "spai_run": (i32, [vp, i32, i32, i32, C.POINTER(_Hist)]),
+        "spai_mr": (i32, [vp, i32, i32, C.POINTER(_Hist)]),
+        "spai_lomr": (i32, [vp, i32, i32, C.POINTER(_Hist)]),
+        "spai_cg": (i32, [vp, i32, i32, C.POINTER(_Hist)]),
+        "spai_residual_norm": (i32, [vp, C.POINTER(dbl)]),
+        "spai_get_nnz": (i32, [vp, C.POINTER(i64)]),
+        "spai_get_M": (i32, [vp, C.POINTER(i64), vp, vp, vp, i32]),
+        "spai_set_M": (i32, [vp, vp, vp, vp, i32]),
+        "spai_apply": (i32, [vp, vp, vp, i32, i64]),
+        "pcg_solve": (i32, [vp, vp, vp, i32, dbl, i32, i32, i32, C.POINTER(i32), C.POINTER(dbl)]),
+        "spai_save_state": (i32, [vp, vp, C.POINTER(C.c_size_t)]),
+        "spai_load_state": (i32, [vp, vp, C.c_size_t]),
+        "spai_set_timing": (i32, [vp, i32]),
+        "spai_get_stats": (i32, [vp, C.POINTER(_Stats)]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def status_string(code: int) -> str:
+    return load().spai_status_string(int(code)).decode()
+
+
+def _np(a, dtype):
+    return np.ascontiguousarray(np.asarray(a), dtype=dtype)
+
+
+def _ptr(a):
+    """(pointer, on_device, keepalive) for a numpy array or torch tensor."""
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr(), (1 if a.is_cuda else 0), a
+    return a.ctypes.data, 0, a
+
+
+def validate_csr(n, rowptr, colind, vals, check_symmetry=True) -> int:
+    rp, ci, va = _np(rowptr, np.int32), _np(colind, np.int32), _np(vals, np.float64)
+    return load().spai_validate_csr(int(n), int(len(va)), rp.ctypes.data, ci.ctypes.data,
+                                    va.ctypes.data, int(check_symmetry))
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return torch.cuda.current_stream().cuda_stream
+        except Exception:
+            pass
+        return None
+    return getattr(stream, "cuda_stream", stream)
+
+
+class Spai:
+    """Handle for one SPD matrix A (CSR, exactly symmetric).
+
+    prec: "fp64" or "mixed" (FP32 values, FP64 reductions and coefficients).
+    cap_factor: column capacity and drop cap, cap_j = floor(f * nnz(A[:, j])).
+    Arrays may be numpy (host) or torch CUDA tensors (device).
+    """
+
+    def __init__(self, n, rowptr, colind, vals, prec="fp64", cap_factor=2.0, stream=None):
+        self.lib = load()
+        self.n = int(n)
+        if hasattr(vals, "data_ptr"):
+            rp, ci, va = rowptr, colind, vals
+        else:
+            rp, ci, va = _np(rowptr, np.int32), _np(colind, np.int32), _np(vals, np.float64)
+        self.nnz = int(va.numel() if hasattr(va, "numel") else len(va))
+        p_rp, dev, k1 = _ptr(rp)
+        p_ci, _, k2 = _ptr(ci)
+        p_va, _, k3 = _ptr(va)
+        opts = _Opts(SPAI_MIXED if prec == "mixed" else SPAI_FP64, float(cap_factor))
+        h = C.c_void_p()
+        rc = self.lib.spai_create(C.byref(h), self.n, self.nnz, p_rp, p_ci, p_va, dev,
+                                  C.byref(opts), _stream_ptr(stream))
+        if rc != 0:
+            raise SpaiError(rc, "spai_create")
+        self.h = h
+        self.prec = prec
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.spai_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc, where, ok=(OK,)):
+        if rc not in ok and rc < 0:
+            raise SpaiError(rc, where)
+        return rc
+
+    def run(self, method, iters, drop=True):
+        m = METHODS[method] if isinstance(method, str) else int(method)
+        res = np.full(iters + 1, np.nan)
+        coef = np.full(2 * max(iters, 1), np.nan)
+        hist = _Hist(res.ctypes.data, coef.ctypes.data, 0, 0)
+        rc = self.lib.spai_run(self.h, m, int(iters), SPAI_DROP_TOPK_COL if drop else SPAI_DROP_NONE,
+                               C.byref(hist))
+        self._check(rc, "spai_run")
+        return dict(status=rc, done=hist.iters_done, flags=hist.flags, resnorm=res,
+                    coef=coef.reshape(-1, 2))
+
+    def mr(self, iters, drop=True):
+        return self.run("mr", iters, drop)
+
+    def lomr(self, iters, drop=True):
+        return self.run("lomr", iters, drop)
+
+    def cg(self, iters, drop=True):
+        return self.run("cg", iters, drop)
+
+    def reset(self):
+        self._check(self.lib.spai_reset(self.h), "spai_reset")
+
+    def residual_norm(self) -> float:
+        out = C.c_double()
+        self._check(self.lib.spai_residual_norm(self.h, C.byref(out)), "spai_residual_norm")
+        return out.value
+
+    def nnz_M(self) -> int:
+        out = C.c_int64()
+        self._check(self.lib.spai_get_nnz(self.h, C.byref(out)), "spai_get_nnz")
+        return out.value
+
+    def get_M(self):
+        """CSC triple (colptr int32[n+1], rowind int32[nnz], vals float64[nnz]) on the host."""
+        nnz = C.c_int64()
+        self._check(self.lib.spai_get_M(self.h, C.byref(nnz), None, None, None, 0), "spai_get_M")
+        cp = np.zeros(self.n + 1, dtype=np.int32)
+        ri = np.zeros(max(nnz.value, 1), dtype=np.int32)
+        va = np.zeros(max(nnz.value, 1), dtype=np.float64)
+        self._check(self.lib.spai_get_M(self.h, C.byref(nnz), cp.ctypes.data, ri.ctypes.data,
+                                        va.ctypes.data, 0), "spai_get_M")
+        return cp, ri[:nnz.value], va[:nnz.value]
+
+    def get_M_device(self, colptr, rowind, vals):
+        """Fill device tensors (int32, int32, float64) with the CSC of M; returns nnz."""
+        nnz = C.c_int64()
+        self._check(self.lib.spai_get_M(self.h, C.byref(nnz), colptr.data_ptr(), rowind.data_ptr(),
+                                        vals.data_ptr(), 1), "spai_get_M")
+        return nnz.value
+
+    def set_M(self, colptr, rowind, vals):
+        cp, ri, va = _np(colptr, np.int32), _np(rowind, np.int32), _np(vals, np.float64)
+        self._check(self.lib.spai_set_M(self.h, cp.ctypes.data, ri.ctypes.data, va.ctypes.data, 0),
+                    "spai_set_M")
+
+    def apply(self, x, y):
+        """y = M x for FP64 CUDA tensors x, y of shape (n,) or (nrhs, n)."""
+        nrhs = 1 if x.dim() == 1 else x.shape[0]
+        self._check(self.lib.spai_apply(self.h, x.data_ptr(), y.data_ptr(), nrhs, self.n),
+                    "spai_apply")
+        return y
+
+    def pcg(self, b, x=None, rtol=1e-8, maxit=10000, precond=PREC_SPAI_SYM):
+        """Vector PCG with x0 = 0; b/x numpy (host) or FP64 CUDA tensors (device)."""
+        dev = hasattr(b, "data_ptr")
+        if dev:
+            if x is None:
+                import torch
+                x = torch.empty_like(b)
+            pb, px = b.data_ptr(), x.data_ptr()
+        else:
+            b = _np(b, np.float64)
+            x = np.zeros(self.n) if x is None else x
+            pb, px = b.ctypes.data, x.ctypes.data
+        it = C.c_int()
+        rr = C.c_double()
+        rc = self.lib.pcg_solve(self.h, pb, px, 1, float(rtol), int(maxit), int(precond),
+                                1 if dev else 0, C.byref(it), C.byref(rr))
+        self._check(rc, "pcg_solve")
+        return dict(status=rc, iters=it.value, relres=rr.value, x=x)
+
+    def save_state(self) -> bytes:
+        n = C.c_size_t()
+        self._check(self.lib.spai_save_state(self.h, None, C.byref(n)), "spai_save_state")
+        buf = C.create_string_buffer(n.value)
+        self._check(self.lib.spai_save_state(self.h, buf, C.byref(n)), "spai_save_state")
+        return buf.raw[:n.value]
+
+    def load_state(self, data: bytes):
+        buf = C.create_string_buffer(data, len(data))
+        self._check(self.lib.spai_load_state(self.h, buf, len(data)), "spai_load_state")
+
+    def set_timing(self, on=True):
+        self._check(self.lib.spai_set_timing(self.h, int(bool(on))), "spai_set_timing")
+
+    def stats(self):
+        s = _Stats()
+        self._check(self.lib.spai_get_stats(self.h, C.byref(s)), "spai_get_stats")
+        return {k: getattr(s, k) for k, _ in _Stats._fields_}

@@ -1,0 +1,81 @@
+"""The C-ABI library loads, exports every symbol of include/spai.h, and its
+host-only entry points (CSR validation, status strings) behave; no GPU."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2511_09753_gb300 import inputs as I
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "spai.h")
+
+
+def _lib():
+    from paper_2511_09753_gb300 import build, spai
+    if not os.path.exists(spai.LIB_PATH):
+        build.build()
+    return spai
+
+
+def header_functions():
+    txt = open(HEADER).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(\w+)\s*\(", txt, flags=re.M)
+    return sorted(set(n for n in names if n not in ("if", "while")))
+
+
+def test_library_exports_every_declared_function():
+    spai = _lib()
+    import ctypes
+    lib = ctypes.CDLL(spai.LIB_PATH)
+    decl = header_functions()
+    assert len(decl) >= 20
+    for name in decl:
+        assert hasattr(lib, name), name
+    assert sorted(decl) == sorted(spai.EXPORTED)
+
+
+def test_status_strings():
+    spai = _lib()
+    for code in (0, 1, 2, 3, 4, -1, -2, -3, -4, -5, -6, -7, -8, -9, -10):
+        s = spai.status_string(code)
+        assert s and s != "unknown status"
+    assert spai.status_string(12345) == "unknown status"
+
+
+def test_validate_csr_accepts_generators():
+    spai = _lib()
+    for f, a in ((I.laplacian_2d_5pt, (8,)), (I.varcoef_3d_7pt, (5,)), (I.aniso_2d_9pt, (7,))):
+        n, rp, ci, v = f(*a)
+        assert spai.validate_csr(n, rp, ci, v) == 0
+
+
+def test_validate_csr_rejects_bad_input():
+    spai = _lib()
+    n, rp, ci, v = I.laplacian_2d_5pt(4)
+    bad = v.copy(); bad[0] = np.nan
+    assert spai.validate_csr(n, rp, ci, bad) == -5            # non-finite
+    nd = v.copy(); nd[rp[3]:rp[4]][ci[rp[3]:rp[4]] == 3] = -1.0
+    assert spai.validate_csr(n, rp, ci, nd) == -3             # non-positive diagonal
+    asym = v.copy(); asym[1] = -0.5
+    assert spai.validate_csr(n, rp, ci, asym) == -4           # not symmetric
+    assert spai.validate_csr(n, rp, ci, asym, check_symmetry=False) == 0
+    unsorted = ci.copy(); unsorted[0], unsorted[1] = unsorted[1], unsorted[0]
+    assert spai.validate_csr(n, rp, unsorted, v) == -2        # unsorted row
+    oob = ci.copy(); oob[-1] = n
+    assert spai.validate_csr(n, rp, oob, v) == -2             # column out of range
+    rp2 = rp.copy(); rp2[-1] += 1
+    assert spai.validate_csr(n, rp2, ci, v) == -2             # rowptr[n] != nnz
+
+
+def test_handle_calls_reject_null():
+    spai = _lib()
+    import ctypes
+    lib = spai.load()
+    assert lib.spai_destroy(None) == -1
+    assert lib.spai_run(None, 0, 1, 1, None) == -1
+    out = ctypes.c_void_p()
+    opts = spai._Opts(0, 2.0)
+    assert lib.spai_create(ctypes.byref(out), 0, 1, None, None, None, 0, ctypes.byref(opts), None) == -1
