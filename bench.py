@@ -1,0 +1,366 @@
+"""Benchmark: global SPAI iterations (MR, LOMR, CG) plus PCG assessment on one GB300.
+
+Workload (one step): the 3-D 7-point variable-coefficient diffusion operator
+on a 64^3 grid (n = 262,144; kappa = exp(g), g Gaussian, sigma 1.5,
+correlation length 8 cells, harmonic-mean faces, seed 0); FP32 values with
+FP64 reductions; per-column cap 3 nnz(A[:,j]); from M_0 = diag(A)^{-1}:
+50 MR iterations, then PCG, 50 LOMR iterations, then PCG, 50 CG iterations,
+then PCG (b ~ U(-1,1) seed 0, rtol 1e-8, symmetric part of M as
+preconditioner).  Metric: SPAI iterations per second over the whole step
+(150 iterations / step time, PCG and set-up included).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the CPU oracle (the plain single-threaded C
+implementation used by the tests) on a bounded sample of the same workload.
+N > 1 runs N independent replicas (one per GPU, weak scaling): the method
+shards by columns, but this build has no multi-GPU data path.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+ITERS = 50
+CAP = 3.0
+PCG_MAXIT = 1000
+METHODS = ("mr", "lomr", "cg")
+WORKLOAD = "varcoef3d_64"
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class Clocks:
+    """Samples nvidia-smi SM clocks and throttle reasons in the background."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 7:
+                continue
+            try:
+                sm.append(float(p[0]))
+                smax = float(p[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[3:7]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_2511_09753_gb300 import inputs as I
+    from paper_2511_09753_gb300.spai import PREC_SPAI_SYM, Spai
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    n, rp, ci, v = I.varcoef_3d_7pt(64, sigma=1.5, ell=8.0, seed=0)
+    b = I.rhs_uniform(n, 0)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    # device-resident inputs: A copied once, handle created outside the timed region
+    g = Spai(n, rp, ci, v, prec="mixed", cap_factor=CAP)
+    b_dev = torch.tensor(b, dtype=torch.float64, device="cuda")
+    x_dev = torch.empty_like(b_dev)
+
+    def step(h):
+        out = {}
+        for m in METHODS:
+            h.reset()
+            r = h.run(m, ITERS)
+            p = h.pcg(b_dev, x_dev, rtol=1e-8, maxit=PCG_MAXIT, precond=PREC_SPAI_SYM)
+            out[m] = (r, p)
+        return out
+
+    for _ in range(args.warmup):
+        step(g)
+    torch.cuda.synchronize()
+    g.set_timing(True)
+    s0 = g.stats()
+    clocks = Clocks(local)
+    clocks.start()
+    times = []
+    last = None
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    for _ in range(args.steps):
+        flush.fill_(1.0)  # evict L2 between steps (outside the events)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        last = step(g)
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    clk = clocks.stop()
+    s1 = g.stats()
+    g.set_timing(False)
+    ms_step = sum(times) / len(times)
+    if dist:
+        t = torch.tensor([ms_step], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step = float(t.item())
+    total_iters = ITERS * len(METHODS)
+    value = ws * total_iters / (ms_step * 1e-3)
+
+    # dominant kernel: the column pass (timed per launch inside the library)
+    launches = s1["colpass_launches"] - s0["colpass_launches"]
+    cp_ms = s1["colpass_ms"] - s0["colpass_ms"]
+    cp_bytes = s1["colpass_bytes"] - s0["colpass_bytes"]
+    peak, peak_kind = _peaks()
+    per_launch_bytes = cp_bytes / max(launches, 1)
+    per_launch_ms = cp_ms / max(launches, 1)
+    achieved = per_launch_bytes / (per_launch_ms * 1e-3) / 1e9 if per_launch_ms > 0 else 0.0
+    gpu_launches = ((s1["colpass_launches"] - s0["colpass_launches"])
+                    + (s1["pcg_launches"] - s0["pcg_launches"])
+                    + (s1["other_launches"] - s0["other_launches"]))
+
+    # end to end through the C ABI with host buffers: create (H2D of A), run,
+    # PCG with host b and x, export M (D2H) -- every step
+    def e2e_step():
+        h = Spai(n, rp, ci, v, prec="mixed", cap_factor=CAP)
+        h2d = rp.nbytes + ci.nbytes + v.nbytes
+        d2h = 0
+        for m in METHODS:
+            h.reset()
+            h.run(m, ITERS)
+            p = h.pcg(b, rtol=1e-8, maxit=PCG_MAXIT, precond=PREC_SPAI_SYM)
+            h2d += b.nbytes
+            d2h += p["x"].nbytes
+            cp, ri, va = h.get_M()
+            d2h += cp.nbytes + ri.nbytes + va.nbytes
+        h.close()
+        return h2d, d2h
+
+    e2e_steps = max(1, min(args.steps, 3))
+    e2e_step()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        h2d, d2h = e2e_step()
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    if dist:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+
+    # FP64 path, same workload, one step (reported beside the mixed path)
+    g64 = Spai(n, rp, ci, v, prec="fp64", cap_factor=CAP)
+    step(g64)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    r64 = step(g64)
+    e1.record(stream)
+    e1.synchronize()
+    fp64_ms = e0.elapsed_time(e1)
+
+    results = {m: {"resnorm": float(last[m][0]["resnorm"][-1]),
+                   "residual_fp64": None,
+                   "pcg_iters": int(last[m][1]["iters"]),
+                   "pcg_relres": float(last[m][1]["relres"]),
+                   "pcg_status": int(last[m][1]["status"])} for m in METHODS}
+    for m in METHODS:
+        results[m]["fp64_resnorm"] = float(r64[m][0]["resnorm"][-1])
+        results[m]["fp64_pcg_iters"] = int(r64[m][1]["iters"])
+        rel = abs(results[m]["resnorm"] - results[m]["fp64_resnorm"]) / results[m]["fp64_resnorm"]
+        results[m]["mixed_vs_fp64_rel"] = rel
+
+    cpu = cpu_baseline() if (rank == 0 and ws == 1 and not args.no_cpu) else None
+    if rank == 0:
+        line = {
+            "metric": "SPAI iterations/s (MR+LOMR+CG, 50 each, with PCG assessment)",
+            "value": value,
+            "unit": "SPAI iterations/s",
+            "n_gpus": ws,
+            "steps": args.steps,
+            "warmup": args.warmup,
+            "ms_per_step": ms_step,
+            "higher_is_better": True,
+            "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": "f32 values / f64 reductions",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": n, "nnz": int(len(v)), "cap_factor": CAP,
+                       "iters_per_method": ITERS, "methods": list(METHODS),
+                       "pcg": "symmetric part of M, rtol 1e-8, maxit 1000",
+                       "l2": "flushed between steps (256 MB write)", "parallelism": "replicas"},
+            "e2e": {"value": ws * total_iters / e2e_s, "unit": "SPAI iterations/s",
+                    "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+            "roofline": {"bound": "hbm", "kernel": "colpass_kernel", "achieved": achieved,
+                         "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "peak_source": peak_kind, "traffic": None,
+                         "algorithmic_bytes_per_launch": per_launch_bytes,
+                         "launch_ms": per_launch_ms, "launches": launches},
+            "cpu_baseline": cpu,
+            "gpu_launches": int(gpu_launches),
+            "clocks": clk,
+            "fp64_path": {"ms_per_step": fp64_ms,
+                          "value": total_iters / (fp64_ms * 1e-3), "unit": "SPAI iterations/s"},
+            "results": results,
+            "wall_s": wall,
+        }
+        print(json.dumps(line))
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def profile_case(method, prec):
+    """Small launch sequence for ncu captures: one handle on the workload,
+    3 iterations of `method` (4 column passes for MR/LOMR, 6 for CG)."""
+    import torch
+
+    from paper_2511_09753_gb300 import inputs as I
+    from paper_2511_09753_gb300.spai import Spai
+    n, rp, ci, v = I.varcoef_3d_7pt(64, sigma=1.5, ell=8.0, seed=0)
+    g = Spai(n, rp, ci, v, prec=prec, cap_factor=CAP)
+    r = g.run(method, 3)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile": method, "prec": prec, "resnorm": float(r["resnorm"][-1])}))
+
+
+def cpu_baseline(sample_iters=1):
+    """The CPU oracle (single thread) on a bounded sample of the workload:
+    `sample_iters` MR iterations on the full operator (mixed arithmetic)."""
+    import oracle as O
+    from paper_2511_09753_gb300 import inputs as I
+    n, rp, ci, v = I.varcoef_3d_7pt(64, sigma=1.5, ell=8.0, seed=0)
+    o = O.Oracle(n, rp, ci, v, mixed=True, cap_factor=CAP)
+    t0 = time.perf_counter()
+    o.run("mr", sample_iters)
+    dt = time.perf_counter() - t0
+    return {"value": sample_iters / dt, "unit": "SPAI iterations/s", "cores": 1, "kind": "oracle",
+            "sample": f"{sample_iters} MR iteration(s) (+ final residual) on the full "
+                      f"n={n} operator, mixed arithmetic, single thread", "seconds": dt}
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    k = max(1, args.steps)
+    vals = []
+    for _ in range(max(0, min(args.warmup, 1))):
+        cpu_baseline(1)
+    for _ in range(k):
+        vals.append(cpu_baseline(1))
+    secs = sum(c["seconds"] for c in vals) / k
+    value = 1.0 / secs
+    line = {
+        "impl": "reference",
+        "metric": "SPAI iterations/s (MR+LOMR+CG, 50 each, with PCG assessment)",
+        "value": value,
+        "unit": "SPAI iterations/s",
+        "n_gpus": ws,
+        "steps": k,
+        "warmup": args.warmup,
+        "ms_per_step": secs * 1e3,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32 values / f64 reductions",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "cap_factor": CAP, "parallelism": "cpu, single thread"},
+        "cpu_baseline": {"value": value, "unit": "SPAI iterations/s", "cores": 1, "kind": "oracle",
+                         "sample": vals[0]["sample"]},
+        "e2e": {"value": value, "unit": "SPAI iterations/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline sample")
+    ap.add_argument("--profile", choices=list(METHODS), default=None,
+                    help="profiling case for ncu: 3 iterations of one method on the workload")
+    ap.add_argument("--prec", choices=["mixed", "fp64"], default="mixed")
+    args = ap.parse_args()
+    if args.profile:
+        profile_case(args.profile, args.prec)
+    elif args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()
