@@ -184,6 +184,25 @@ int pcg_solve(spai_handle h, const double *b, double *x, int nrhs, double rtol, 
 int spai_save_state(spai_handle h, void *buf, size_t *bytes);
 int spai_load_state(spai_handle h, const void *buf, size_t bytes);
 
+/* Residual norms of a linear system without allocating: out[0] = ||b - A x||_2
+ * and out[1] = ||b||_2, both FP64, written to the device array `out` (2
+ * doubles) in stream order on `stream` (NULL: the legacy default stream); the
+ * call does not synchronise.  The paper has no counterpart: this is a
+ * utility for callers that cannot allocate device memory, such as code whose
+ * GPU memory belongs to another allocator, or latency-critical loops that
+ * cannot pay for cudaMalloc/cudaFree.  A (CSR int32/int32/FP64, n x n), b
+ * and x are device pointers owned by the caller; the rows are summed in the
+ * same order as pcg_solve's residual, so out[0]/out[1] equals its *relres.
+ * Workspace: a fixed ~1 MB array inside the library (every GPU that loads the
+ * library holds it until exit); n above 16,777,216 returns
+ * SPAI_ERR_UNSUPPORTED.  The first call on each device looks up that array's
+ * device address, so make it before starting any stream capture.  All calls
+ * share the array: calls that overlap on the GPU race; order them on one
+ * stream.  No cudaMalloc, cudaFree or allocating library routine is called. */
+int spai_true_residual_noalloc(int64_t n, const int32_t *rowptr, const int32_t *colind,
+                               const double *vals, const double *b, const double *x, double *out,
+                               void *stream);
+
 /* Launch / byte / time counters; timing (CUDA events around each column
  * pass, on the handle's stream) is recorded only while enabled. */
 int spai_set_timing(spai_handle h, int enable);

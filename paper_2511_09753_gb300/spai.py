@@ -28,7 +28,7 @@ EXPORTED = ["spai_validate_csr", "spai_status_string", "spai_create", "spai_dest
             "spai_set_stream", "spai_run", "spai_mr", "spai_lomr", "spai_cg",
             "spai_residual_norm", "spai_get_nnz", "spai_get_M", "spai_set_M", "spai_apply",
             "pcg_solve", "spai_save_state", "spai_load_state", "spai_set_timing",
-            "spai_get_stats"]
+            "spai_get_stats", "spai_true_residual_noalloc"]
 
 
 class SpaiError(RuntimeError):
@@ -85,6 +85,7 @@ def load():
         "spai_load_state": (i32, [vp, vp, C.c_size_t]),
         "spai_set_timing": (i32, [vp, i32]),
         "spai_get_stats": (i32, [vp, C.POINTER(_Stats)]),
+        "spai_true_residual_noalloc": (i32, [i64, vp, vp, vp, vp, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -107,6 +108,15 @@ def _ptr(a):
     if hasattr(a, "data_ptr"):
         return a.data_ptr(), (1 if a.is_cuda else 0), a
     return a.ctypes.data, 0, a
+
+
+def true_residual_noalloc(n, rowptr, colind, vals, b, x, out, stream=None) -> int:
+    """Allocation-free ||b - A x||_2 and ||b||_2 into the 2-element FP64 CUDA
+    tensor `out` (all arguments CUDA tensors).  For callers that cannot
+    allocate device memory; see include/spai.h.  Returns the status code."""
+    return load().spai_true_residual_noalloc(int(n), rowptr.data_ptr(), colind.data_ptr(),
+                                             vals.data_ptr(), b.data_ptr(), x.data_ptr(),
+                                             out.data_ptr(), _stream_ptr(stream))
 
 
 def validate_csr(n, rowptr, colind, vals, check_symmetry=True) -> int:
