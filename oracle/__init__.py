@@ -74,6 +74,8 @@ def _load():
         lib.orc_column_residual.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]
         lib.orc_drop_column.restype = C.c_int
         lib.orc_drop_column.argtypes = [C.c_int, p_i32, p_f64, C.c_int]
+        lib.orc_fixsum.restype = C.c_double
+        lib.orc_fixsum.argtypes = [p_f64, C.c_int64]
         lib.orc_pairwise.restype = C.c_double
         lib.orc_pairwise.argtypes = [p_f64, C.c_int64]
         lib.orc_pcg.restype = C.c_int
@@ -88,6 +90,13 @@ def pairwise(t) -> float:
     """Balanced pairwise sum over t zero-padded to a power of two."""
     t = np.ascontiguousarray(t, dtype=np.float64)
     return _load().orc_pairwise(t, len(t))
+
+
+def fixsum(t) -> float:
+    """Order-free sum used for column inner products (128-bit fixed point
+    anchored at the largest term, rounded once)."""
+    t = np.ascontiguousarray(t, dtype=np.float64)
+    return _load().orc_fixsum(t, len(t))
 
 
 class Oracle:

@@ -32,9 +32,12 @@
  *   - (A X)[r,j] = fma chain over k ascending: acc = fma(a_rk, x_kj, acc),
  *     acc starting at +0;  R = I - A M with 1 - s on the diagonal, -s off it;
  *   - column inner products: products x*y (rounded, FP64) over the common
- *     rows, summed by a balanced pairwise tree over the row-ascending list
- *     zero-padded to a power of two; the Frobenius product is the same tree
- *     over the column partials j = 0..n-1;
+ *     rows, summed exactly in a 128-bit fixed point whose unit is 2^(E-110),
+ *     E the largest binary exponent among the terms (each term truncated
+ *     toward zero to that unit), then rounded once to FP64 (nearest, ties to
+ *     even) -- a sum that does not depend on the order of the terms; the
+ *     Frobenius product is a balanced pairwise tree over the column partials
+ *     j = 0..n-1 zero-padded to a power of two;
  *   - combinations: M + a P -> fma(a, p, m);  S = d Z + g P -> fma(d, z, g*p);
  *     M + S -> m + s;  R + b P -> fma(b, p, r); all in FP64, then rounded to
  *     the value type;
@@ -165,6 +168,58 @@ static double pairwise64(const double *t, int64_t L) {
   return r;
 }
 
+/* Order-free sum of finite FP64 terms (see the header): exact 128-bit fixed
+ * point with unit 2^(E-110), E = largest exponent, terms truncated toward
+ * zero, one final rounding to nearest-even. */
+double orc_fixsum(const double *t, int64_t L) {
+  int eb = 0;
+  for (int64_t i = 0; i < L; i++) {
+    uint64_t bits;
+    memcpy(&bits, &t[i], 8);
+    int b = (int)((bits >> 52) & 0x7ff);
+    uint64_t m = bits & ((1ull << 52) - 1);
+    if (b == 0 && m == 0) continue;
+    if (b == 0) b = 1;
+    if (b > eb) eb = b;
+  }
+  if (eb == 0) return 0.0;
+  __int128 S = 0;
+  for (int64_t i = 0; i < L; i++) {
+    uint64_t bits;
+    memcpy(&bits, &t[i], 8);
+    int b = (int)((bits >> 52) & 0x7ff);
+    uint64_t m = bits & ((1ull << 52) - 1);
+    if (b == 0) b = 1;
+    else m |= 1ull << 52;
+    if (m == 0) continue;
+    int sh = b - eb + 58; /* t = m 2^(b-1075); unit = 2^(eb-1133) */
+    unsigned __int128 q;
+    if (sh >= 0) q = (unsigned __int128)m << sh;
+    else if (sh > -64) q = (unsigned __int128)(m >> (-sh));
+    else q = 0;
+    if (bits >> 63) S -= (__int128)q;
+    else S += (__int128)q;
+  }
+  if (S == 0) return 0.0;
+  int neg = S < 0;
+  unsigned __int128 U = neg ? (unsigned __int128)(-S) : (unsigned __int128)S;
+  int bl = 0;
+  for (unsigned __int128 v = U; v; v >>= 1) bl++;
+  uint64_t mant;
+  int shift = 0;
+  if (bl <= 53) {
+    mant = (uint64_t)U;
+  } else {
+    shift = bl - 53;
+    mant = (uint64_t)(U >> shift);
+    unsigned __int128 rem = U & (((unsigned __int128)1 << shift) - 1);
+    unsigned __int128 half = (unsigned __int128)1 << (shift - 1);
+    if (rem > half || (rem == half && (mant & 1))) mant++;
+  }
+  double r = ldexp((double)mant, shift + eb - 1133);
+  return neg ? -r : r;
+}
+
 /* column inner product over the common rows, Sec. 2 Eq. (2.1) */
 static double col_dot(const ocol *x, const ocol *y, double *tmp) {
   int a = 0, b = 0, L = 0;
@@ -177,12 +232,12 @@ static double col_dot(const ocol *x, const ocol *y, double *tmp) {
       b++;
     }
   }
-  return orc_pairwise(tmp, L);
+  return orc_fixsum(tmp, L);
 }
 
 static double col_nrm2(const ocol *x, double *tmp) {
   for (int a = 0; a < x->len; a++) tmp[a] = x->val[a] * x->val[a];
-  return orc_pairwise(tmp, x->len);
+  return orc_fixsum(tmp, x->len);
 }
 
 /* ------------------------------------------------------------- operations */

@@ -55,6 +55,11 @@ struct spai_ctx {
   int* d_ell_col = nullptr;
   float* d_ell32 = nullptr;
   double* d_ell64 = nullptr;
+  bool dia = false;  // A also stored by diagonal slots
+  int D = 0, Dp = 0;
+  int dia_off[32];
+  float* d_dia32 = nullptr;
+  double* d_dia64 = nullptr;
   // slabs
   long long* d_off = nullptr;
   int* d_cap = nullptr;
@@ -142,16 +147,17 @@ int next_pow2(int x) {
 }
 
 // Per-warp scratch layout of a pass kind.
-WarpLayout make_layout(int kind, int vc, int CAP, int W) {
+WarpLayout make_layout(int kind, int vc, int CAP, int W, bool dia) {
   WarpLayout L;
   memset(&L, 0, sizeof(L));
   const int PMAX = CAP * W;
   const int LMAX = PMAX + 1;
-  int TMAX = 0;
-  if (kind == kMR || kind == kCGA) TMAX = 2 * CAP;
+  int TMAX = 2 * CAP;  // union output, also the general path's input-sort scratch
   if (kind == kLOMR) TMAX = 3 * CAP;
   if (kind == kCGB) TMAX = LMAX + CAP;
-  const int DMAX = next_pow2(std::max(32, std::max(LMAX, TMAX)));
+  const int H = std::max(32, next_pow2((4 * LMAX + 2) / 3 + 1));
+  const int HU = std::max(32, next_pow2((4 * TMAX + 2) / 3 + 1));
+  const int LIST = std::max(LMAX, TMAX);
   int o = 0;
   auto take = [&](int bytes) {
     int at = o;
@@ -160,8 +166,33 @@ WarpLayout make_layout(int kind, int vc, int CAP, int W) {
   };
   const bool hasP = kind != kRES;
   const bool lomr = kind == kLOMR;
-  const bool hasQ = kind == kMR || kind == kLOMR || kind == kCGB;
-  L.dtmp = take(8 * DMAX);
+  (void)dia;
+  L.H = H;
+  L.HU = HU;
+  L.hk = take(4 * H);
+  L.hv = take(vc * H);
+  L.ho = take(2 * H);
+  L.gk = take(lomr ? 4 * H : 0);
+  L.gv = take(lomr ? vc * H : 0);
+  L.go = take(lomr ? 2 * H : 0);
+  // union table, looked-up values and tie scratch share one region
+  {
+    int base = o;
+    int u = 0;
+    auto sub = [&](int bytes) {
+      int at = base + u;
+      u = align16(u + bytes);
+      return at;
+    };
+    L.uk = sub(4 * HU);
+    L.ua = sub(vc * HU);
+    L.ub = sub(vc * HU);
+    L.uo = sub(2 * HU);
+    int region = std::max(u, std::max(4 * LIST, align16(vc * LMAX) + vc * LMAX));
+    L.yc = base;
+    L.tie = base;
+    o = align16(base + region);
+  }
   L.Mr = take(4 * CAP);
   L.Mv = take(vc * CAP);
   L.Pr = take(hasP ? 4 * CAP : 0);
@@ -174,43 +205,51 @@ WarpLayout make_layout(int kind, int vc, int CAP, int W) {
   L.Tv = take(vc * TMAX);
   L.Rr = take(4 * LMAX);
   L.Rv = take(vc * LMAX);
-  L.Qr = take(hasQ ? 4 * LMAX : 0);
-  L.Qv = take(hasQ ? vc * LMAX : 0);
-  L.Vr = take(lomr ? 4 * LMAX : 0);
-  L.Vv = take(lomr ? vc * LMAX : 0);
-  L.key0 = take(4 * (PMAX + 1));
-  L.key1 = take(4 * (PMAX + 1));
-  L.idx0 = take(2 * (PMAX + 1));
-  L.idx1 = take(2 * (PMAX + 1));
-  L.aval = take(vc * PMAX);
-  L.hp = take(2 * (LMAX + 1));
-  L.dp = take(2 * (TMAX + 1));
-  L.hist = take(4 * 256);
+  L.Ur = take(lomr ? 4 * LMAX : 0);
+  L.Uv = take(lomr ? vc * LMAX : 0);
+  L.hist = take(4 * 128);  // 256 packed 16-bit bins
   L.bytes = o;
   return L;
 }
 
-PassCfg make_cfg(int kind, int vc, int n, int CAP, int W, int smem_max) {
+// Launch shape of the column pass.  Results do not depend on it (the
+// reduction tree is fixed by the column index), so it is a pure tuning knob:
+// occ = CTAs per SM the shared memory should allow, cpw = columns per warp.
+// SPAI_COLPASS_OCC / SPAI_COLPASS_CPW override the defaults.
+static int env_int(const char* name, int dflt) {
+  const char* v = getenv(name);
+  if (!v || !*v) return dflt;
+  int x = atoi(v);
+  return x > 0 ? x : dflt;
+}
+
+PassCfg make_cfg(int kind, int vc, int n, int CAP, int W, bool dia, int smem_max) {
   PassCfg c;
   memset(&c, 0, sizeof(c));
-  c.lay = make_layout(kind, vc, CAP, W);
+  c.lay = make_layout(kind, vc, CAP, W, dia);
   const int nq = 6;
   const int extra_fixed = 8 * 1024;  // reduction scratch (1024 doubles)
+  // defaults measured on GB300 (64^3 operator, cap 3): LOMR's large scratch
+  // prefers 8-warp CTAs at two per SM, the CG passes four CTAs per SM
+  const int occ_default = kind == kLOMR ? 2 : (kind == kMR ? 3 : 4);
+  const int occ = env_int("SPAI_COLPASS_OCC", occ_default);
+  const int cpw = env_int("SPAI_COLPASS_CPW", 4);
   c.ok = false;
   for (int NW = 8; NW >= 1; NW >>= 1) {
-    // B: columns per CTA, power of two, NW <= B <= 1024, enough CTAs to fill
-    // the GPU, and at most 65536 CTAs so the group tree stays two-level.
+    // B: columns per CTA, a power of two: cpw per warp, fewer when n is
+    // small, more when needed to keep at most 65536 CTAs (two-level tree).
     int B = NW;
     long long target = (long long)n / (152LL * 8);
-    while ((long long)B * 2 <= target && B * 2 <= 256) B *= 2;
+    while ((long long)B * 2 <= target && B * 2 <= cpw * NW) B *= 2;
     while (((long long)n + B - 1) / B > 65536LL && B < 1024) B *= 2;
-    size_t smem = (size_t)NW * c.lay.bytes;
+    // the CTA reduction buffer (1024 doubles) reuses the warps' scratch,
+    // which is free once every column of the block is done
+    size_t smem = std::max((size_t)NW * c.lay.bytes, (size_t)extra_fixed);
     int part_off = (int)smem;
     smem += (size_t)8 * nq * B;
-    int red_off = (int)smem;
-    smem += extra_fixed;
+    int red_off = 0;
     bool fits = smem <= (size_t)smem_max;
-    bool good = smem <= (size_t)(smem_max / 2) || NW == 1;
+    bool good = smem <= (size_t)(smem_max / occ) || NW == 1;
     if (fits && (good || NW == 1)) {
       c.NW = NW;
       c.B = B;
@@ -301,6 +340,11 @@ PassParams base_params(spai_ctx* h, int kind, bool res) {
   p.Zlen = h->d_Zlen;
   p.ell_col = h->d_ell_col;
   p.ell_val = (res || h->prec == SPAI_FP64) ? (const void*)h->d_ell64 : (const void*)h->d_ell32;
+  p.dia = h->dia ? 1 : 0;
+  p.D = h->D;
+  p.Dp = h->Dp;
+  for (int s2 = 0; s2 < 32; s2++) p.dia_off[s2] = h->dia ? h->dia_off[s2 < h->D ? s2 : 0] : 0;
+  p.dia_val = (res || h->prec == SPAI_FP64) ? (const void*)h->d_dia64 : (const void*)h->d_dia32;
   p.sc = h->d_sc;
   p.hist_res = h->d_hres;
   p.hist_coef = h->d_hcoef;
@@ -330,6 +374,8 @@ void free_all(spai_ctx* h) {
   dfree(h->d_ell_col);
   dfree(h->d_ell32);
   dfree(h->d_ell64);
+  dfree(h->d_dia32);
+  dfree(h->d_dia64);
   dfree(h->d_off);
   dfree(h->d_cap);
   dfree(h->d_Mrow);
@@ -595,22 +641,6 @@ int spai_create(spai_handle* out, int64_t n, int64_t nnz, const int32_t* rowptr,
   h->magicW = (uint32_t)((((uint64_t)1 << 32) + W - 1) / W);
   h->capmax = capmax;
   h->slab_total = off[n];
-  int dev = 0;
-  cudaGetDevice(&dev);
-  int smem_max = 0;
-  cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  if (smem_max <= 0) smem_max = 227 * 1024;
-  const int vc = h->prec == SPAI_MIXED ? 4 : 8;
-  for (int k = 0; k < 5; k++) {
-    h->cfg[k] = make_cfg(k, k == kRES ? 8 : vc, (int)n, capmax, W, smem_max);
-    if (!h->cfg[k].ok) {
-      if (h->own_stream) cudaStreamDestroy(h->stream);
-      delete h;
-      return SPAI_ERR_UNSUPPORTED;
-    }
-    h->red_nb = std::max(h->red_nb, h->cfg[k].nb);
-    h->red_ng = std::max(h->red_ng, h->cfg[k].ngroups);
-  }
   std::vector<int> ecol((size_t)n * W);
   std::vector<double> e64((size_t)n * W);
   std::vector<float> e32;
@@ -623,13 +653,65 @@ int spai_create(spai_handle* out, int64_t n, int64_t nnz, const int32_t* rowptr,
       if (ci[e] == i) diag[i] = va[e];
     }
     for (; t < W; t++) {
-      ecol[(size_t)i * W + t] = (int)i;
+      ecol[(size_t)i * W + t] = -1;
       e64[(size_t)i * W + t] = 0.0;
     }
   }
   if (h->prec == SPAI_MIXED) {
     e32.resize(e64.size());
     for (size_t k = 0; k < e64.size(); k++) e32[k] = (float)e64[k];
+  }
+  // diagonal-slot layout when A has at most 32 distinct offsets col - row
+  std::vector<double> d64;
+  std::vector<float> d32;
+  {
+    std::vector<long long> offs;
+    bool ok = true;
+    for (int64_t i = 0; i < n && ok; i++)
+      for (int64_t e = rp[i]; e < rp[i + 1]; e++) {
+        long long o = (long long)ci[e] - i;
+        if (std::find(offs.begin(), offs.end(), o) == offs.end()) {
+          offs.push_back(o);
+          if (offs.size() > 32) {
+            ok = false;
+            break;
+          }
+        }
+      }
+    if (ok) {
+      std::sort(offs.begin(), offs.end());
+      h->dia = true;
+      h->D = (int)offs.size();
+      h->Dp = h->D;
+      for (int s2 = 0; s2 < h->D; s2++) h->dia_off[s2] = (int)offs[s2];
+      d64.assign((size_t)n * h->Dp, 0.0);
+      for (int64_t i = 0; i < n; i++)
+        for (int64_t e = rp[i]; e < rp[i + 1]; e++) {
+          long long o = (long long)ci[e] - i;
+          int s2 = (int)(std::lower_bound(offs.begin(), offs.end(), o) - offs.begin());
+          d64[(size_t)i * h->Dp + s2] = va[e];
+        }
+      if (h->prec == SPAI_MIXED) {
+        d32.resize(d64.size());
+        for (size_t k = 0; k < d64.size(); k++) d32[k] = (float)d64[k];
+      }
+    }
+  }
+  int dev = 0;
+  cudaGetDevice(&dev);
+  int smem_max = 0;
+  cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (smem_max <= 0) smem_max = 227 * 1024;
+  const int vc = h->prec == SPAI_MIXED ? 4 : 8;
+  for (int k = 0; k < 5; k++) {
+    h->cfg[k] = make_cfg(k, k == kRES ? 8 : vc, (int)n, capmax, W, h->dia, smem_max);
+    if (!h->cfg[k].ok) {
+      if (h->own_stream) cudaStreamDestroy(h->stream);
+      delete h;
+      return SPAI_ERR_UNSUPPORTED;
+    }
+    h->red_nb = std::max(h->red_nb, h->cfg[k].nb);
+    h->red_ng = std::max(h->red_ng, h->cfg[k].ngroups);
   }
   const size_t vs = h->prec == SPAI_MIXED ? 4 : 8;
   rc = SPAI_OK;
@@ -640,6 +722,10 @@ int spai_create(spai_handle* out, int64_t n, int64_t nnz, const int32_t* rowptr,
   rc = rc ? rc : dalloc(&h->d_ell_col, (size_t)n * W);
   rc = rc ? rc : dalloc(&h->d_ell64, (size_t)n * W);
   if (h->prec == SPAI_MIXED) rc = rc ? rc : dalloc(&h->d_ell32, (size_t)n * W);
+  if (h->dia) {
+    rc = rc ? rc : dalloc(&h->d_dia64, (size_t)n * h->Dp);
+    if (h->prec == SPAI_MIXED) rc = rc ? rc : dalloc(&h->d_dia32, (size_t)n * h->Dp);
+  }
   rc = rc ? rc : dalloc(&h->d_off, n + 1);
   rc = rc ? rc : dalloc(&h->d_cap, n);
   rc = rc ? rc : dalloc(&h->d_Mrow, h->slab_total);
@@ -676,6 +762,13 @@ int spai_create(spai_handle* out, int64_t n, int64_t nnz, const int32_t* rowptr,
   if (h->prec == SPAI_MIXED)
     ok &= cudaMemcpyAsync(h->d_ell32, e32.data(), sizeof(float) * e32.size(),
                           cudaMemcpyHostToDevice, st) == 0;
+  if (h->dia) {
+    ok &= cudaMemcpyAsync(h->d_dia64, d64.data(), sizeof(double) * d64.size(),
+                          cudaMemcpyHostToDevice, st) == 0;
+    if (h->prec == SPAI_MIXED)
+      ok &= cudaMemcpyAsync(h->d_dia32, d32.data(), sizeof(float) * d32.size(),
+                            cudaMemcpyHostToDevice, st) == 0;
+  }
   ok &= cudaMemcpyAsync(h->d_off, off.data(), sizeof(long long) * (n + 1), cudaMemcpyHostToDevice,
                         st) == 0;
   ok &= cudaMemcpyAsync(h->d_cap, cap.data(), sizeof(int) * n, cudaMemcpyHostToDevice, st) == 0;
@@ -1115,6 +1208,29 @@ int spai_load_state(spai_handle h, const void* buf, size_t bytes) {
   if (memcmp(hd.magic, "SPAIST01", 8) != 0 || hd.n != h->n || hd.slab_total != h->slab_total ||
       hd.prec != h->prec || hd.capmax != h->capmax || hd.W != h->W)
     return SPAI_ERR_STATE;
+  {
+    // every slab column must hold at most cap_j distinct rows in [0, n):
+    // the kernels rely on it, so a damaged checkpoint is refused here
+    std::vector<long long> offv(n + 1);
+    std::vector<int> capv(n);
+    CK(cudaMemcpy(offv.data(), h->d_off, sizeof(long long) * (n + 1), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(capv.data(), h->d_cap, sizeof(int) * n, cudaMemcpyDeviceToHost));
+    const char* q = o + sizeof(hd) + sizeof(DevScalars);
+    std::vector<int> tmp;
+    for (int k = 0; k < 3; k++) {
+      const int* lens = (const int*)q;
+      const int* rows = (const int*)(q + n * 4);
+      for (size_t jj = 0; jj < n; jj++) {
+        int len = lens[jj];
+        if (len < 0 || len > capv[jj]) return SPAI_ERR_STATE;
+        tmp.assign(rows + offv[jj], rows + offv[jj] + len);
+        std::sort(tmp.begin(), tmp.end());
+        for (int e = 0; e < len; e++)
+          if (tmp[e] < 0 || tmp[e] >= (int)n || (e > 0 && tmp[e] == tmp[e - 1])) return SPAI_ERR_STATE;
+      }
+      q += n * 4 + S * 4 + S * vs;
+    }
+  }
   o += sizeof(hd);
   cudaStream_t st = h->stream;
   // keep this handle's counters, restore the iteration scalars

@@ -70,6 +70,16 @@ __device__ void store_col(ColCtx<VS, VC>& c, int* grow, void* gval, int* glen, i
   c.bytes += (unsigned long long)len * (sizeof(int) + sizeof(VS)) + sizeof(int);
 }
 
+__device__ __forceinline__ int L_lmax(const PassParams& p) { return p.capmax * p.W + 1; }
+
+template <typename VC>
+__device__ __forceinline__ int spgemm(const PassParams& p, const HashT& h, int* xr, VC* xv, int L,
+                                      int diag, int* sr, VC* sv, int lane) {
+  if (p.dia) return spgemm_dia(p, h, xr, xv, L, diag, lane);
+  sort_rows_small(xr, xv, L, sr, sv, lane);
+  return spgemm_ell(p, h, xr, xv, L, diag, lane);
+}
+
 // Column work of one pass.  part[0..nq) receives the column partials.
 template <typename VS, typename VC>
 __device__ void column_work(ColCtx<VS, VC>& c, int j, double* part) {
@@ -86,27 +96,31 @@ __device__ void column_work(ColCtx<VS, VC>& c, int j, double* part) {
   VC* Tv = c.template at<VC>(L.Tv);
   int* Rr = c.template at<int>(L.Rr);
   VC* Rv = c.template at<VC>(L.Rv);
-  int* Qr = c.template at<int>(L.Qr);
-  VC* Qv = c.template at<VC>(L.Qv);
-  uint16_t* dp = c.template at<uint16_t>(L.dp);
   uint32_t* hist = c.template at<uint32_t>(L.hist);
-  double* dt = c.template at<double>(L.dtmp);
-  VC* aval = c.template at<VC>(L.aval);
-  SpgemmScratch ss;
-  ss.key0 = c.template at<uint32_t>(L.key0);
-  ss.key1 = c.template at<uint32_t>(L.key1);
-  ss.idx0 = c.template at<uint16_t>(L.idx0);
-  ss.idx1 = c.template at<uint16_t>(L.idx1);
-  ss.hp = c.template at<uint16_t>(L.hp);
-  ss.hist = hist;
+  VC* yc = c.template at<VC>(L.yc);
+  VC* yc2 = c.template at<VC>(L.yc + ((int)sizeof(VC) * L_lmax(p) + 15) / 16 * 16);
+  int* tie = c.template at<int>(L.tie);
+  HashT ha;
+  ha.key = c.template at<int>(L.hk);
+  ha.val = c.template at<VC>(L.hv);
+  ha.occ = c.template at<uint16_t>(L.ho);
+  ha.H = L.H;
+  UnionT un;
+  un.key = c.template at<int>(L.uk);
+  un.va = c.template at<VC>(L.ua);
+  un.vb = c.template at<VC>(L.ub);
+  un.occ = c.template at<uint16_t>(L.uo);
+  un.H = L.HU;
   int* ovf = &c.overflow;
 
   int Lm = load_col(c, p.Mrow, p.Mval, off, p.Mlen[j], Mr, Mv);
 
   if (p.kind == kRES) {
-    int LR = warp_spgemm(p, ss, aval, Mr, Mv, Lm, j, Rr, Rv, lane);
+    int cnt = spgemm(p, ha, Mr, Mv, Lm, j, Tr, Tv, lane);
+    int LR = table_to_list(ha, cnt, j, Rr, Rv, lane);
+    hash_clear(ha, cnt, lane);
     c.spg++;
-    part[0] = warp_norm2(Rv, LR, dt, lane);
+    fixsum<1>(part, lane, TermSq<VC>{Rv}, LR);
     return;
   }
 
@@ -114,20 +128,28 @@ __device__ void column_work(ColCtx<VS, VC>& c, int j, double* part) {
     if (p.do_update) {
       int Lp = load_col(c, p.Prow, p.Pval, off, p.Plen[j], Pr, Pv);
       CombAxpy<VC> f{p.sc->alpha};
-      int Lt = warp_union(Mr, Mv, Lm, Pr, Pv, Lp, Tr, Tv, dp, f, lane);
-      Lm = warp_select(Tr, Tv, Lt, cap, Mr, Mv, hist, p.drop, ovf, lane);
+      int Lt = warp_union(un, Mr, Mv, Lm, Pr, Pv, Lp, Tr, Tv, f, lane);
+      Lm = warp_select(Tr, Tv, Lt, cap, Mr, Mv, hist, tie, p.drop, ovf, lane);
       store_col(c, p.Mrow, p.Mval, p.Mlen, j, off, Lm, Mr, Mv);
     }
-    int LR = warp_spgemm(p, ss, aval, Mr, Mv, Lm, j, Rr, Rv, lane);
+    int cnt = spgemm(p, ha, Mr, Mv, Lm, j, Tr, Tv, lane);
+    int LR = table_to_list(ha, cnt, j, Rr, Rv, lane);
+    hash_clear(ha, cnt, lane);
     c.spg++;
-    part[0] = warp_norm2(Rv, LR, dt, lane);
-    if (!p.do_dir) return;
-    int Lp = warp_select(Rr, Rv, LR, cap, Pr, Pv, hist, p.drop, ovf, lane);
+    if (!p.do_dir) {
+      fixsum<1>(part, lane, TermSq<VC>{Rv}, LR);
+      return;
+    }
+    int Lp = warp_select(Rr, Rv, LR, cap, Pr, Pv, hist, tie, p.drop, ovf, lane);
     store_col(c, p.Prow, p.Pval, p.Plen, j, off, Lp, Pr, Pv);
-    int LQ = warp_spgemm(p, ss, aval, Pr, Pv, Lp, -1, Qr, Qv, lane);
+    int cq = spgemm(p, ha, Pr, Pv, Lp, -1, Tr, Tv, lane);  // table holds Q = A P
     c.spg++;
-    part[1] = warp_dot(Rr, Rv, LR, Qr, Qv, LQ, dt, lane);
-    part[2] = warp_norm2(Qv, LQ, dt, lane);
+    lookup_list(Rr, LR, ha, yc, lane);                      // Q at the rows of R
+    __syncwarp();
+    // (R,R), (R,Q), (Q,Q)
+    fixsum<3>(part, lane, TermSq<VC>{Rv}, LR, TermProd<VC>{Rv, yc}, LR,
+              TermSqTable<VC>{(const VC*)ha.val, ha.occ}, cq);
+    hash_clear(ha, cq, lane);
     return;
   }
 
@@ -136,62 +158,95 @@ __device__ void column_work(ColCtx<VS, VC>& c, int j, double* part) {
     VC* Zv = c.template at<VC>(L.Zv);
     int* Sr = c.template at<int>(L.Sr);
     VC* Sv = c.template at<VC>(L.Sv);
-    int* Vr = c.template at<int>(L.Vr);
-    VC* Vv = c.template at<VC>(L.Vv);
+    int* Ur = c.template at<int>(L.Ur);
+    VC* Uv = c.template at<VC>(L.Uv);
+    HashT hb;
+    hb.key = c.template at<int>(L.gk);
+    hb.val = c.template at<VC>(L.gv);
+    hb.occ = c.template at<uint16_t>(L.go);
+    hb.H = L.H;
     int Lp = load_col(c, p.Prow, p.Pval, off, p.Plen[j], Pr, Pv);
     if (p.do_update) {
       int Lz = load_col(c, p.Zrow, p.Zval, off, p.Zlen[j], Zr, Zv);
       CombLin<VC> fl{p.sc->delta, p.sc->gamma};
-      int Ls = warp_union(Zr, Zv, Lz, Pr, Pv, Lp, Sr, Sv, dp, fl, lane);
-      Lp = warp_select(Sr, Sv, Ls, cap, Pr, Pv, hist, p.drop, ovf, lane);
+      int Ls = warp_union(un, Zr, Zv, Lz, Pr, Pv, Lp, Sr, Sv, fl, lane);
+      Lp = warp_select(Sr, Sv, Ls, cap, Pr, Pv, hist, tie, p.drop, ovf, lane);
       store_col(c, p.Prow, p.Pval, p.Plen, j, off, Lp, Pr, Pv);
       CombAdd<VC> fa;
-      int Lt = warp_union(Mr, Mv, Lm, Sr, Sv, Ls, Tr, Tv, dp, fa, lane);
-      Lm = warp_select(Tr, Tv, Lt, cap, Mr, Mv, hist, p.drop, ovf, lane);
+      int Lt = warp_union(un, Mr, Mv, Lm, Sr, Sv, Ls, Tr, Tv, fa, lane);
+      Lm = warp_select(Tr, Tv, Lt, cap, Mr, Mv, hist, tie, p.drop, ovf, lane);
       store_col(c, p.Mrow, p.Mval, p.Mlen, j, off, Lm, Mr, Mv);
     }
-    int LR = warp_spgemm(p, ss, aval, Mr, Mv, Lm, j, Rr, Rv, lane);
+    int cr = spgemm(p, ha, Mr, Mv, Lm, j, Tr, Tv, lane);
+    int LR = table_to_list(ha, cr, j, Rr, Rv, lane);  // table A now holds R
     c.spg++;
-    part[0] = warp_norm2(Rv, LR, dt, lane);
-    if (!p.do_dir) return;
-    int Lz = warp_select(Rr, Rv, LR, cap, Zr, Zv, hist, p.drop, ovf, lane);
+    if (!p.do_dir) {
+      fixsum<1>(part, lane, TermSq<VC>{Rv}, LR);
+      hash_clear(ha, cr, lane);
+      return;
+    }
+    int Lz = warp_select(Rr, Rv, LR, cap, Zr, Zv, hist, tie, p.drop, ovf, lane);
     store_col(c, p.Zrow, p.Zval, p.Zlen, j, off, Lz, Zr, Zv);
-    int LU = warp_spgemm(p, ss, aval, Zr, Zv, Lz, -1, Qr, Qv, lane);
-    int LV = warp_spgemm(p, ss, aval, Pr, Pv, Lp, -1, Vr, Vv, lane);
+    int cu = spgemm(p, hb, Zr, Zv, Lz, -1, Tr, Tv, lane);   // table B: U = A Z
+    lookup_table(hb, cu, ha, yc, lane);                     // R at the rows of U
+    __syncwarp();
+    double t3[3];
+    // (R,R), (U,U), (U,R)
+    fixsum<3>(t3, lane, TermSq<VC>{Rv}, LR, TermSqTable<VC>{(const VC*)hb.val, hb.occ}, cu,
+              TermProdTable<VC>{(const VC*)hb.val, hb.occ, yc}, cu);
+    part[0] = t3[0];
+    part[1] = t3[1];
+    part[4] = t3[2];
+    int LU = table_to_list(hb, cu, -1, Ur, Uv, lane);
+    hash_clear(hb, cu, lane);
+    int cv = spgemm(p, hb, Pr, Pv, Lp, -1, Tr, Tv, lane);   // table B: V = A P
     c.spg += 2;
-    part[1] = warp_norm2(Qv, LU, dt, lane);                      // (U,U)
-    part[2] = warp_norm2(Vv, LV, dt, lane);                      // (V,V)
-    part[3] = warp_dot(Qr, Qv, LU, Vr, Vv, LV, dt, lane);        // (U,V)
-    part[4] = warp_dot(Qr, Qv, LU, Rr, Rv, LR, dt, lane);        // (U,R)
-    part[5] = warp_dot(Vr, Vv, LV, Rr, Rv, LR, dt, lane);        // (V,R)
+    lookup_list(Ur, LU, hb, yc, lane);                      // V at the rows of U
+    lookup_table(hb, cv, ha, yc2, lane);                    // R at the rows of V
+    __syncwarp();
+    // (V,V), (U,V), (V,R)
+    fixsum<3>(t3, lane, TermSqTable<VC>{(const VC*)hb.val, hb.occ}, cv, TermProd<VC>{Uv, yc}, LU,
+              TermProdTable<VC>{(const VC*)hb.val, hb.occ, yc2}, cv);
+    part[2] = t3[0];
+    part[3] = t3[1];
+    part[5] = t3[2];
+    hash_clear(hb, cv, lane);
+    hash_clear(ha, cr, lane);
     return;
   }
 
   if (p.kind == kCGA) {
     int Lp = load_col(c, p.Prow, p.Pval, off, p.Plen[j], Pr, Pv);
     CombAxpy<VC> f{p.sc->alpha};
-    int Lt = warp_union(Mr, Mv, Lm, Pr, Pv, Lp, Tr, Tv, dp, f, lane);
-    Lm = warp_select(Tr, Tv, Lt, cap, Mr, Mv, hist, p.drop, ovf, lane);
+    int Lt = warp_union(un, Mr, Mv, Lm, Pr, Pv, Lp, Tr, Tv, f, lane);
+    Lm = warp_select(Tr, Tv, Lt, cap, Mr, Mv, hist, tie, p.drop, ovf, lane);
     store_col(c, p.Mrow, p.Mval, p.Mlen, j, off, Lm, Mr, Mv);
-    int LR = warp_spgemm(p, ss, aval, Mr, Mv, Lm, j, Rr, Rv, lane);
+    int cr = spgemm(p, ha, Mr, Mv, Lm, j, Tr, Tv, lane);
+    int LR = table_to_list(ha, cr, j, Rr, Rv, lane);
+    hash_clear(ha, cr, lane);
     c.spg++;
-    part[0] = warp_norm2(Rv, LR, dt, lane);
+    fixsum<1>(part, lane, TermSq<VC>{Rv}, LR);
     return;
   }
 
   // kCGB
   {
     int Lp = load_col(c, p.Prow, p.Pval, off, p.Plen[j], Pr, Pv);
-    int LR = warp_spgemm(p, ss, aval, Mr, Mv, Lm, j, Rr, Rv, lane);
+    int cr = spgemm(p, ha, Mr, Mv, Lm, j, Tr, Tv, lane);
+    int LR = table_to_list(ha, cr, j, Rr, Rv, lane);
+    hash_clear(ha, cr, lane);
     c.spg++;
-    part[0] = warp_norm2(Rv, LR, dt, lane);
     CombAxpy<VC> f{p.sc->beta};
-    int Lt = warp_union(Rr, Rv, LR, Pr, Pv, Lp, Tr, Tv, dp, f, lane);
-    Lp = warp_select(Tr, Tv, Lt, cap, Pr, Pv, hist, p.drop, ovf, lane);
+    int Lt = warp_union(un, Rr, Rv, LR, Pr, Pv, Lp, Tr, Tv, f, lane);
+    Lp = warp_select(Tr, Tv, Lt, cap, Pr, Pv, hist, tie, p.drop, ovf, lane);
     store_col(c, p.Prow, p.Pval, p.Plen, j, off, Lp, Pr, Pv);
-    int LQ = warp_spgemm(p, ss, aval, Pr, Pv, Lp, -1, Qr, Qv, lane);
+    int cq = spgemm(p, ha, Pr, Pv, Lp, -1, Tr, Tv, lane);  // table holds Q = A P
     c.spg++;
-    part[1] = warp_dot(Pr, Pv, Lp, Qr, Qv, LQ, dt, lane);
+    lookup_list(Pr, Lp, ha, yc, lane);                     // Q at the rows of P
+    __syncwarp();
+    // (R,R), (P,Q)
+    fixsum<2>(part, lane, TermSq<VC>{Rv}, LR, TermProd<VC>{Pv, yc}, Lp);
+    hash_clear(ha, cq, lane);
   }
 }
 
@@ -306,7 +361,7 @@ __device__ inline void coefficients(const PassParams& p, const double* t) {
 }
 
 template <typename VS, typename VC>
-__global__ void __launch_bounds__(256) colpass_kernel(const PassParams p) {
+__global__ void __launch_bounds__(256, 3) colpass_kernel(const PassParams p) {
   extern __shared__ __align__(16) char smem[];
   if (p.sc->stop) return;
   const int lane = threadIdx.x & 31;
@@ -315,6 +370,21 @@ __global__ void __launch_bounds__(256) colpass_kernel(const PassParams p) {
   double* part = (double*)(smem + p.part_off);  // [nq][B]
   double* red = (double*)(smem + p.red_off);    // reduction scratch (>= 1024 doubles)
   ColCtx<VS, VC> c(p, smem + warp * p.lay.bytes, lane);
+  {
+    HashT h0;
+    h0.key = c.template at<int>(p.lay.hk);
+    h0.H = p.lay.H;
+    hash_clear_all(h0, lane);
+    if (p.kind == kLOMR) {
+      h0.key = c.template at<int>(p.lay.gk);
+      hash_clear_all(h0, lane);
+    }
+    if (p.kind != kRES) {
+      h0.key = c.template at<int>(p.lay.uk);
+      h0.H = p.lay.HU;
+      hash_clear_all(h0, lane);
+    }
+  }
   const int B = p.B;
   const long long j0 = (long long)blockIdx.x * B;
   for (int cc = warp; cc < B; cc += p.NW) {

@@ -43,14 +43,14 @@ struct WarpLayout {
   int Mr, Mv, Pr, Pv, Zr, Zv;   // capped lists (CAP)
   int Sr, Sv;                   // LOMR S list (2 CAP)
   int Tr, Tv;                   // union output before drop (TMAX)
-  int Rr, Rv, Qr, Qv, Vr, Vv;   // SpGEMM outputs (LMAX)
-  int key0, key1;               // u32 [PMAX+1]
-  int idx0, idx1;               // u16 [PMAX+1]
-  int aval;                     // VC  [PMAX]
-  int hp;                       // u16 [LMAX+1]
-  int dp;                       // u16 [TMAX+1]
-  int hist;                     // u32 [256]
-  int dtmp;                     // f64 [DMAX]
+  int Rr, Rv, Ur, Uv;           // SpGEMM output lists (LMAX)
+  int hk, hv, ho;               // hash table A: keys, values, occupied slots (H)
+  int gk, gv, go;               // hash table B (LOMR)
+  int uk, ua, ub, uo;           // union table (HU); shares its bytes with yc / tie
+  int yc;                       // looked-up values for inner products (2 x LMAX)
+  int tie;                      // int scratch of the threshold tie-break
+  int hist;                     // 256 packed 16-bit bins (128 words)
+  int H, HU;                    // table capacities (powers of two)
   int bytes;                    // total per warp (multiple of 16)
 };
 
@@ -71,7 +71,11 @@ struct PassParams {
   int* Prow; void* Pval; int* Plen;
   int* Zrow; void* Zval; int* Zlen;
   const int* ell_col;
-  const void* ell_val;   // VC values of A in ELL layout
+  const void* ell_val;   // VC values of A in ELL layout (padding column -1)
+  int dia;               // nonzero: A is also stored by diagonal slots
+  int D, Dp;             // number of distinct offsets, padded slot stride
+  int dia_off[32];       // the offsets, ascending
+  const void* dia_val;   // VC values [n][Dp], 0 where row k has no entry k+off
   DevScalars* sc;
   double* hist_res;      // [iters+1]
   double* hist_coef;     // [2*iters]

@@ -174,6 +174,8 @@ cudaError_t launch_exclusive_scan(const int* in, long long* out, int n, long lon
 
 // ------------------------------------------------- export / transpose
 
+// Slab columns are stored in no particular order; the CSC export sorts each
+// column by row (rank by counting: rows within a column are distinct).
 template <typename VS>
 __global__ void k_export_csc(int n, const long long* off, const int* Mrow, const VS* Mval,
                              const long long* colptr, int* rowind, double* vals) {
@@ -183,8 +185,11 @@ __global__ void k_export_csc(int n, const long long* off, const int* Mrow, const
   long long src = off[j], dst = colptr[j];
   int len = (int)(colptr[j + 1] - dst);
   for (int e = lane; e < len; e += 32) {
-    rowind[dst + e] = Mrow[src + e];
-    vals[dst + e] = (double)Mval[src + e];
+    int r = Mrow[src + e];
+    int rank = 0;
+    for (int q = 0; q < len; q++) rank += Mrow[src + q] < r;
+    rowind[dst + rank] = r;
+    vals[dst + rank] = (double)Mval[src + e];
   }
 }
 

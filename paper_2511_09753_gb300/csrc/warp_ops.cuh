@@ -1,14 +1,14 @@
 // Warp-level building blocks of the column pass.  One warp owns one column
-// at a time; every list lives in that warp's shared-memory scratch as a
-// row-sorted array of (row, value) with value != 0.  All functions are
-// called by the 32 lanes of the warp together.
+// at a time; every list lives in that warp's shared-memory scratch as an
+// array of (row, value) with distinct rows and value != 0, in no particular
+// order.  All functions are called by the 32 lanes of the warp together.
 //
-// Arithmetic order is fixed so that results do not depend on the launch
-// shape:
+// The arithmetic does not depend on list order or launch shape:
 //   (A X)[r]      fma chain over k ascending, acc = fma(a_rk, x_k, acc)
-//   column dot    x*y in FP64 over the common rows, balanced pairwise tree over
-//                 the row-ascending term list padded with zeros
+//   column dot    FP64 products over the common rows, summed exactly in a
+//                 128-bit fixed point anchored at the largest term, rounded once
 //   combination   computed in FP64, rounded once to the value type
+//   hard threshold keeps the cap largest |v|, ties to the smaller row
 #pragma once
 #include <stdint.h>
 
@@ -44,98 +44,220 @@ __device__ __forceinline__ double warp_tree32(double v) {
   return v;
 }
 
-__device__ __forceinline__ int lower_bound(const int* a, int L, int x) {
-  int lo = 0, hi = L;
-  while (lo < hi) {
-    int mid = (lo + hi) >> 1;
-    if (a[mid] < x) lo = mid + 1;
-    else hi = mid;
-  }
-  return lo;
-}
-
-// Pairwise sum of t[0..L) padded to max(32, next power of two); t must have
-// room for that many doubles.  Levels above 32 pair adjacent entries in place.
+// Pairwise sum of t[0..L) zero-padded to max(32, next power of two); levels
+// above 32 pair adjacent entries in place (t needs only L entries).
 __device__ inline double warp_pairwise(double* t, int L, int lane) {
   int P2 = 32;
   while (P2 < L) P2 <<= 1;
-  for (int i = L + lane; i < P2; i += 32) t[i] = 0.0;
-  __syncwarp();
+  int cur = L;
   for (int len = P2; len > 32; len >>= 1) {
-    int half = len >> 1;
-    for (int base = 0; base < half; base += 32) {
+    const int next = (cur + 1) >> 1;
+    for (int base = 0; base < next; base += 32) {
       int i = base + lane;
-      double a = t[2 * i], b = t[2 * i + 1];
+      double a = (2 * i < cur) ? t[2 * i] : 0.0;
+      double b = (2 * i + 1 < cur) ? t[2 * i + 1] : 0.0;
       __syncwarp();
-      t[i] = __dadd_rn(a, b);
+      if (i < next) t[i] = __dadd_rn(a, b);
       __syncwarp();
     }
+    cur = next;
   }
-  double v = t[lane];
+  double v = lane < cur ? t[lane] : 0.0;
   __syncwarp();
   return warp_tree32(v);
 }
 
-template <typename V>
-__device__ double warp_norm2(const V* v, int L, double* t, int lane) {
-  for (int i = lane; i < L; i += 32) {
-    double x = (double)v[i];
-    t[i] = __dmul_rn(x, x);
-  }
-  __syncwarp();
-  return warp_pairwise(t, L, lane);
+// ------------------------------------------------------ order-free dot sum
+// A column inner product is the exact two's-complement sum of its FP64 terms
+// in a 128-bit fixed point with unit 2^(E-110), E the largest exponent among
+// the terms (each term truncated toward zero to the unit), rounded once to
+// the nearest double (ties to even).  Integer addition is associative, so
+// neither the term order nor the reduction order matters.  Terms come from
+// functors f(i), i < L, each lane taking i = lane, lane + 32, ...; up to
+// three sums are reduced together so their latencies overlap.
+
+__device__ __forceinline__ int term_exp(double t) {
+  uint64_t bits = (uint64_t)__double_as_longlong(t);
+  int b = (int)((bits >> 52) & 0x7ff);
+  if (b == 0 && (bits & ((1ull << 52) - 1)) == 0) return 0;
+  return b == 0 ? 1 : b;
 }
 
-// Inner product over the common rows of two row-sorted lists.
-template <typename V>
-__device__ double warp_dot(const int* xr, const V* xv, int Lx, const int* yr, const V* yv, int Ly,
-                           double* t, int lane) {
-  int L = 0;
-  for (int base = 0; base < Lx; base += 32) {
-    int i = base + lane;
-    bool hit = false;
-    double term = 0.0;
-    if (i < Lx) {
-      int r = xr[i];
-      int lb = lower_bound(yr, Ly, r);
-      if (lb < Ly && yr[lb] == r) {
-        hit = true;
-        term = __dmul_rn((double)xv[i], (double)yv[lb]);
-      }
-    }
-    unsigned b = __ballot_sync(kFull, hit);
-    if (hit) t[L + __popc(b & lanemask_lt())] = term;
-    L += __popc(b);
+// 128-bit two's-complement accumulator held as (hi, lo) 64-bit limbs.
+struct Fix128 {
+  unsigned long long lo;
+  long long hi;
+};
+
+__device__ __forceinline__ void term_add(Fix128& S, double t, int eb) {
+  unsigned long long bits = (unsigned long long)__double_as_longlong(t);
+  int b = (int)((bits >> 52) & 0x7ff);
+  unsigned long long m = bits & ((1ull << 52) - 1);
+  if (b == 0) b = 1;
+  else m |= 1ull << 52;
+  const int sh = b - eb + 58;  // <= 58: the term fits in 111 bits
+  unsigned long long lo, hi;
+  if (sh >= 0) {
+    lo = m << sh;
+    hi = sh ? (m >> (64 - sh)) : 0ull;
+  } else {
+    lo = (sh > -64) ? (m >> (-sh)) : 0ull;
+    hi = 0ull;
   }
-  __syncwarp();
-  return warp_pairwise(t, L, lane);
+  if (bits >> 63) {
+    unsigned long long borrow = S.lo < lo ? 1ull : 0ull;
+    S.lo -= lo;
+    S.hi -= (long long)(hi + borrow);
+  } else {
+    unsigned long long s2 = S.lo + lo;
+    unsigned long long carry = s2 < lo ? 1ull : 0ull;
+    S.lo = s2;
+    S.hi += (long long)(hi + carry);
+  }
 }
 
-// In-place removal of exact zeros, order kept.
-template <typename V>
-__device__ int compact_nonzero(int* r, V* v, int L, int lane) {
-  int outn = 0;
-  for (int base = 0; base < L; base += 32) {
-    int i = base + lane;
-    int rr = 0;
-    V vv = V(0);
-    bool nz = false;
-    if (i < L) {
-      rr = r[i];
-      vv = v[i];
-      nz = vv != V(0);
-    }
-    unsigned b = __ballot_sync(kFull, nz);
-    __syncwarp();
-    if (nz) {
-      int pos = outn + __popc(b & lanemask_lt());
-      r[pos] = rr;
-      v[pos] = vv;
-    }
-    outn += __popc(b);
-    __syncwarp();
+__device__ __forceinline__ void fix_allreduce(Fix128& S) {
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1) {
+    unsigned long long lo2 = __shfl_xor_sync(kFull, S.lo, o);
+    long long hi2 = __shfl_xor_sync(kFull, S.hi, o);
+    unsigned long long sum = S.lo + lo2;
+    S.hi = S.hi + hi2 + (sum < lo2 ? 1 : 0);
+    S.lo = sum;
   }
-  return outn;
+}
+
+// round S * 2^(eb-1133) to the nearest double (ties to even)
+__device__ __forceinline__ double fix_to_double(Fix128 S, int eb) {
+  if ((S.lo | (unsigned long long)S.hi) == 0ull || eb == 0) return 0.0;
+  const bool neg = S.hi < 0;
+  unsigned long long ulo = S.lo, uhi = (unsigned long long)S.hi;
+  if (neg) {
+    ulo = ~ulo + 1ull;
+    uhi = ~uhi + (ulo == 0ull ? 1ull : 0ull);
+  }
+  const int bl = uhi ? 128 - __clzll((long long)uhi) : 64 - __clzll((long long)ulo);
+  unsigned long long mant;
+  int shift = 0;
+  if (bl <= 53) {
+    mant = ulo;
+  } else {
+    shift = bl - 53;  // 1 .. 74
+    bool up;
+    if (shift < 64) {
+      mant = (ulo >> shift) | (uhi << (64 - shift));
+      unsigned long long rem = ulo & ((1ull << shift) - 1ull);
+      unsigned long long half = 1ull << (shift - 1);
+      up = rem > half || (rem == half && (mant & 1ull));
+    } else if (shift == 64) {
+      mant = uhi;
+      unsigned long long half = 1ull << 63;
+      up = ulo > half || (ulo == half && (mant & 1ull));
+    } else {
+      const int s2 = shift - 64;  // 1 .. 10
+      mant = uhi >> s2;
+      unsigned long long rhi = uhi & ((1ull << s2) - 1ull);
+      unsigned long long hhi = 1ull << (s2 - 1);
+      up = rhi > hhi || (rhi == hhi && (ulo != 0ull || (mant & 1ull)));
+    }
+    if (up) mant++;
+  }
+  double r = ldexp(__ull2double_rn(mant), shift + eb - 1133);
+  return neg ? -r : r;
+}
+
+struct NoTerms {
+  __device__ double operator()(int) const { return 0.0; }
+};
+
+template <int K, typename F0, typename F1 = NoTerms, typename F2 = NoTerms>
+__device__ void fixsum(double* out, int lane, const F0& f0, int L0, const F1& f1 = F1(), int L1 = 0,
+                       const F2& f2 = F2(), int L2 = 0) {
+  int e0 = 0, e1 = 0, e2 = 0;
+  for (int i = lane; i < L0; i += 32) e0 = max(e0, term_exp(f0(i)));
+  if (K > 1) for (int i = lane; i < L1; i += 32) e1 = max(e1, term_exp(f1(i)));
+  if (K > 2) for (int i = lane; i < L2; i += 32) e2 = max(e2, term_exp(f2(i)));
+  e0 = __reduce_max_sync(kFull, e0);
+  if (K > 1) e1 = __reduce_max_sync(kFull, e1);
+  if (K > 2) e2 = __reduce_max_sync(kFull, e2);
+  Fix128 S0 = {0ull, 0ll}, S1 = {0ull, 0ll}, S2 = {0ull, 0ll};
+  if (e0) for (int i = lane; i < L0; i += 32) term_add(S0, f0(i), e0);
+  if (K > 1 && e1) for (int i = lane; i < L1; i += 32) term_add(S1, f1(i), e1);
+  if (K > 2 && e2) for (int i = lane; i < L2; i += 32) term_add(S2, f2(i), e2);
+  fix_allreduce(S0);
+  if (K > 1) fix_allreduce(S1);
+  if (K > 2) fix_allreduce(S2);
+  out[0] = fix_to_double(S0, e0);
+  if (K > 1) out[1] = fix_to_double(S1, e1);
+  if (K > 2) out[2] = fix_to_double(S2, e2);
+}
+
+// ------------------------------------------------------------- hash table
+// Open addressing with linear probing in shared memory: keys (row, -1 =
+// empty), values, and the list of occupied slots in insertion order.  The
+// capacity is a power of two above the largest possible number of distinct
+// rows, so probing always terminates.
+
+struct HashT {
+  int* key;
+  void* val;
+  uint16_t* occ;
+  int H;
+};
+
+__device__ __forceinline__ int hslot(int r, int H) {
+  return (int)(((unsigned)r * 0x9E3779B1u) >> (33 - __ffs(H))) & (H - 1);
+}
+
+// insert r; a new slot gets value 0 and *isnew = true
+template <typename V>
+__device__ __forceinline__ int hash_insert(const HashT& h, int r, bool* isnew) {
+  V* hv = (V*)h.val;
+  int s = hslot(r, h.H);
+  for (;;) {
+    int k = atomicCAS(&h.key[s], -1, r);
+    if (k == -1) {
+      hv[s] = V(0);
+      *isnew = true;
+      return s;
+    }
+    if (k == r) return s;
+    s = (s + 1) & (h.H - 1);
+  }
+}
+
+// value of row r, or 0 if absent
+template <typename V>
+__device__ __forceinline__ V hash_find(const HashT& h, int r) {
+  const V* hv = (const V*)h.val;
+  int s = hslot(r, h.H);
+  for (;;) {
+    int k = h.key[s];
+    if (k == r) return hv[s];
+    if (k == -1) return V(0);
+    s = (s + 1) & (h.H - 1);
+  }
+}
+
+// append the slots that lanes inserted as new to the occupied list
+__device__ __forceinline__ void occ_append(const HashT& h, int& cnt, bool isnew, int slot) {
+  unsigned b = __ballot_sync(kFull, isnew);
+  if (isnew) h.occ[cnt + __popc(b & lanemask_lt())] = (uint16_t)slot;
+  cnt += __popc(b);
+}
+
+__device__ __forceinline__ void hash_clear_all(const HashT& h, int lane) {
+  int4* k4 = (int4*)h.key;
+  const int4 e = make_int4(-1, -1, -1, -1);
+  for (int i = lane; i < h.H / 4; i += 32) k4[i] = e;
+  __syncwarp();
+}
+
+// empty the table again (only the occupied slots are touched)
+__device__ __forceinline__ void hash_clear(const HashT& h, int cnt, int lane) {
+  __syncwarp();
+  for (int i = lane; i < cnt; i += 32) h.key[h.occ[i]] = -1;
+  __syncwarp();
 }
 
 // Combination functors: computed in FP64, rounded once to V.
@@ -153,56 +275,109 @@ template <typename V> struct CombAdd {   // x + y
   __device__ V operator()(V x, V y) const { return (V)__dadd_rn((double)x, (double)y); }
 };
 
-// out = pattern union of A and B with value f(a or 0, b or 0); zeros removed.
-// dp needs Lb + 1 u16 entries.  Returns the output length.
+// Union table: keys, the A value and the B value of each row.
+struct UnionT {
+  int* key;
+  void* va;
+  void* vb;
+  uint16_t* occ;
+  int H;
+};
+
+// out = pattern union of A and B with value f(a or 0, b or 0); exact zeros
+// removed.  Returns the output length.
 template <typename V, typename F>
-__device__ int warp_union(const int* ar, const V* av, int La, const int* br, const V* bv, int Lb,
-                          int* outr, V* outv, uint16_t* dp, F f, int lane) {
-  int run = 0;
+__device__ int warp_union(const UnionT& u, const int* ar, const V* av, int La, const int* br,
+                          const V* bv, int Lb, int* outr, V* outv, F f, int lane) {
+  HashT h;
+  h.key = u.key;
+  h.val = u.va;
+  h.occ = u.occ;
+  h.H = u.H;
+  V* va = (V*)u.va;
+  V* vb = (V*)u.vb;
+  hash_clear_all(h, lane);  // the table's bytes are shared with other scratch
+  int cnt = 0;
+  for (int base = 0; base < La; base += 32) {
+    int i = base + lane;
+    bool isnew = false;
+    int s = -1;
+    if (i < La) {
+      s = hash_insert<V>(h, ar[i], &isnew);
+      va[s] = av[i];
+      vb[s] = V(0);
+    }
+    occ_append(h, cnt, isnew, s);
+  }
+  __syncwarp();
   for (int base = 0; base < Lb; base += 32) {
     int i = base + lane;
-    bool dup = false;
+    bool isnew = false;
+    int s = -1;
     if (i < Lb) {
-      int r = br[i];
-      int lb = lower_bound(ar, La, r);
-      dup = lb < La && ar[lb] == r;
+      s = hash_insert<V>(h, br[i], &isnew);
+      if (isnew) va[s] = V(0);
+      vb[s] = bv[i];
     }
-    unsigned b = __ballot_sync(kFull, dup);
-    if (i < Lb) dp[i] = (uint16_t)(run + __popc(b & lanemask_lt()));
-    run += __popc(b);
+    occ_append(h, cnt, isnew, s);
   }
-  if (lane == 0) dp[Lb] = (uint16_t)run;
   __syncwarp();
-  int U = La + Lb - run;
-  for (int i = lane; i < La; i += 32) {
-    int r = ar[i];
-    int lb = lower_bound(br, Lb, r);
-    bool has = lb < Lb && br[lb] == r;
-    int pos = i + lb - (int)dp[lb];
-    outr[pos] = r;
-    outv[pos] = f(av[i], has ? bv[lb] : V(0));
-  }
-  for (int i = lane; i < Lb; i += 32) {
-    int r = br[i];
-    int lb = lower_bound(ar, La, r);
-    if (!(lb < La && ar[lb] == r)) {
-      int pos = i - (int)dp[i] + lb;
+  int outn = 0;
+  for (int base = 0; base < cnt; base += 32) {
+    int i = base + lane;
+    bool nz = false;
+    int r = 0;
+    V v = V(0);
+    if (i < cnt) {
+      int s = u.occ[i];
+      r = u.key[s];
+      v = f(va[s], vb[s]);
+      nz = v != V(0);
+    }
+    unsigned b = __ballot_sync(kFull, nz);
+    if (nz) {
+      int pos = outn + __popc(b & lanemask_lt());
       outr[pos] = r;
-      outv[pos] = f(V(0), bv[i]);
+      outv[pos] = v;
     }
+    outn += __popc(b);
   }
   __syncwarp();
-  return compact_nonzero(outr, outv, U, lane);
+  return outn;
 }
 
-// Hard thresholding (Sec. 6.1, per column): copy the `cap` entries of the
-// row-sorted list src with the largest |v| (ties: smaller row) to dst, in row
-// order.  If L <= cap the list is copied unchanged.  When `drop` is 0 the
-// list is not thresholded; a list longer than cap then raises *overflow and
-// is truncated so that no buffer is overrun.
+// ------------------------------------------------------ 256-bin histograms
+// 16-bit counts packed two per word (128 words): lane l owns bins [8l, 8l+8)
+// = words [4l, 4l+4), read and cleared with one 16-byte access.
+
+__device__ __forceinline__ void hist_clear(uint32_t* hist, int lane) {
+  ((uint4*)hist)[lane] = make_uint4(0u, 0u, 0u, 0u);
+}
+
+__device__ __forceinline__ void hist_load(const uint32_t* hist, int lane, unsigned c[8]) {
+  uint4 a = ((const uint4*)hist)[lane];
+  c[0] = a.x & 0xffffu; c[1] = a.x >> 16; c[2] = a.y & 0xffffu; c[3] = a.y >> 16;
+  c[4] = a.z & 0xffffu; c[5] = a.z >> 16; c[6] = a.w & 0xffffu; c[7] = a.w >> 16;
+}
+
+// one count per active lane in bin d, one atomic per distinct digit
+__device__ __forceinline__ void hist_add(uint32_t* hist, bool act, unsigned d) {
+  unsigned am = __ballot_sync(kFull, act);
+  if (act) {
+    unsigned peers = __match_any_sync(am, d);
+    if ((peers & lanemask_lt()) == 0)
+      atomicAdd(&hist[d >> 1], (unsigned)__popc(peers) << ((d & 1u) * 16u));
+  }
+}
+
+// Hard thresholding (Sec. 6.1, per column): copy the `cap` entries of list
+// src with the largest |v| to dst (ties: smaller row), keeping src order.
+// With L <= cap the list is copied.  When `drop` is 0 the list is not
+// thresholded; a list longer than cap then raises *overflow and is truncated
+// so that no buffer is overrun.  tie: scratch of L ints.
 template <typename V>
 __device__ int warp_select(const int* sr, const V* sv, int L, int cap, int* dr, V* dv,
-                           uint32_t* hist, int drop, int* overflow, int lane) {
+                           uint32_t* hist, int* tie, int drop, int* overflow, int lane) {
   typedef typename KeyOf<V>::T K;
   if (L <= cap || !drop) {
     if (L > cap) {
@@ -221,20 +396,25 @@ __device__ int warp_select(const int* sr, const V* sv, int L, int cap, int* dr, 
   bool exact = false;
   for (int d = (int)sizeof(K) - 1; d >= 0; d--) {
     const int shift = 8 * d;
-    for (int b = lane; b < 256; b += 32) hist[b] = 0;
+    hist_clear(hist, lane);
     __syncwarp();
-    for (int i = lane; i < L; i += 32) {
-      K k = absbits(sv[i]);
-      if ((k & pmask) == prefix) atomicAdd(&hist[(unsigned)(k >> shift) & 255u], 1u);
+    for (int base = 0; base < L; base += 32) {
+      int i = base + lane;
+      bool act = false;
+      unsigned dig = 0;
+      if (i < L) {
+        K k = absbits(sv[i]);
+        act = (k & pmask) == prefix;
+        dig = (unsigned)(k >> shift) & 255u;
+      }
+      hist_add(hist, act, dig);
     }
     __syncwarp();
     unsigned c[8];
+    hist_load(hist, lane, c);
     int tot = 0;
 #pragma unroll
-    for (int t = 0; t < 8; t++) {
-      c[t] = hist[8 * lane + t];
-      tot += (int)c[t];
-    }
+    for (int t = 0; t < 8; t++) tot += (int)c[t];
     int suf = tot;  // inclusive suffix over lanes >= lane
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -266,10 +446,24 @@ __device__ int warp_select(const int* sr, const V* sv, int L, int cap, int* dr, 
       break;
     }
   }
-  int outn = 0, ties = 0;
+  // exact: every entry whose masked key equals the prefix is kept.
+  // Otherwise the full key equals the threshold for more than `need`
+  // entries: keep the `need` of them with the smallest rows.
+  int ntie = 0;
+  if (!exact) {
+    for (int base = 0; base < L; base += 32) {
+      int i = base + lane;
+      bool t = i < L && absbits(sv[i]) == prefix;
+      unsigned b = __ballot_sync(kFull, t);
+      if (t) tie[ntie + __popc(b & lanemask_lt())] = sr[i];
+      ntie += __popc(b);
+    }
+    __syncwarp();
+  }
+  int outn = 0;
   for (int base = 0; base < L; base += 32) {
     int i = base + lane;
-    bool keep = false, tie = false;
+    bool keep = false;
     int rr = 0;
     V vv = V(0);
     if (i < L) {
@@ -277,15 +471,15 @@ __device__ int warp_select(const int* sr, const V* sv, int L, int cap, int* dr, 
       vv = sv[i];
       K k = absbits(vv) & pmask;
       keep = k > prefix;
-      tie = k == prefix;
-    }
-    if (exact) {
-      keep = keep || tie;
-    } else {
-      unsigned tb = __ballot_sync(kFull, tie);
-      int trank = ties + __popc(tb & lanemask_lt());
-      keep = keep || (tie && trank < need);
-      ties += __popc(tb);
+      if (k == prefix) {
+        if (exact) {
+          keep = true;
+        } else {
+          int rank = 0;
+          for (int q = 0; q < ntie; q++) rank += tie[q] < rr;
+          keep = rank < need;
+        }
+      }
     }
     unsigned kb = __ballot_sync(kFull, keep);
     if (keep) {
@@ -299,139 +493,144 @@ __device__ int warp_select(const int* sr, const V* sv, int L, int cap, int* dr, 
   return outn;
 }
 
-// One stable LSD radix pass over 8 bits of the keys.
-__device__ inline void radix_pass(const uint32_t* kin, const uint16_t* iin, uint32_t* kout,
-                           uint16_t* iout, int N, int shift, uint32_t* hist, int lane) {
-  for (int b = lane; b < 256; b += 32) hist[b] = 0;
-  __syncwarp();
-  for (int q = lane; q < N; q += 32) atomicAdd(&hist[(kin[q] >> shift) & 255u], 1u);
-  __syncwarp();
-  unsigned c[8];
-  unsigned tot = 0;
-#pragma unroll
-  for (int t = 0; t < 8; t++) {
-    c[t] = hist[8 * lane + t];
-    tot += c[t];
-  }
-  unsigned inc = tot;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    unsigned x = __shfl_up_sync(kFull, inc, o);
-    if (lane >= o) inc += x;
-  }
-  unsigned run = inc - tot;
-#pragma unroll
-  for (int t = 0; t < 8; t++) {
-    hist[8 * lane + t] = run;
-    run += c[t];
-  }
-  __syncwarp();
-  for (int base = 0; base < N; base += 32) {
-    int q = base + lane;
-    bool act = q < N;
-    unsigned am = __ballot_sync(kFull, act);
-    if (act) {
-      uint32_t k = kin[q];
-      unsigned d = (k >> shift) & 255u;
-      unsigned peers = __match_any_sync(am, d);
-      int rank = __popc(peers & lanemask_lt());
-      unsigned pos = hist[d] + rank;
-      kout[pos] = k;
-      iout[pos] = iin[q];
-      __syncwarp(am);
-      if (rank == 0) hist[d] += __popc(peers);
+// ---------------------------------------------------------------- SpGEMM
+// Accumulate A X (one column X, rows xr, values xv, length L, any order) in
+// the hash table: after the call the table holds, for every row r reached,
+// the fma chain over k ascending; returns the number of occupied slots (the
+// occupied list holds them).  If diag >= 0, row diag is inserted as well.
+//
+// DIA layout (A stored by diagonal slots, offsets ascending): the product of
+// x_k with slot s lands on r = k + off_s.  Slots are processed in descending
+// offset, which for any fixed r is ascending k = r - off_s, so every chain
+// has the canonical order; inside one slot distinct k give distinct r, so no
+// two lanes touch the same accumulator.
+template <typename VC>
+__device__ int spgemm_dia(const PassParams& p, const HashT& h, const int* xr, const VC* xv, int L,
+                          int diag, int lane) {
+  const VC* dv = (const VC*)p.dia_val;
+  VC* hv = (VC*)h.val;
+  const int D = p.D, Dp = p.Dp;
+  int cnt = 0;
+  for (int s = D - 1; s >= 0; s--) {
+    const int o = p.dia_off[s];
+    for (int base = 0; base < L; base += 32) {
+      int i = base + lane;
+      bool isnew = false;
+      int slot = -1;
+      if (i < L) {
+        int k = xr[i];
+        VC a = __ldg(dv + (long long)k * Dp + s);
+        if (a != VC(0)) {
+          slot = hash_insert<VC>(h, k + o, &isnew);
+          hv[slot] = vfma(a, xv[i], hv[slot]);
+        }
+      }
+      occ_append(h, cnt, isnew, slot);
     }
     __syncwarp();
   }
+  if (diag >= 0) {
+    bool isnew = false;
+    int slot = -1;
+    if (lane == 0) slot = hash_insert<VC>(h, diag, &isnew);
+    occ_append(h, cnt, isnew, slot);
+    __syncwarp();
+  }
+  return cnt;
 }
 
-struct SpgemmScratch {
-  uint32_t* key0;
-  uint32_t* key1;
-  uint16_t* idx0;
-  uint16_t* idx1;
-  uint16_t* hp;
-  uint32_t* hist;
-};
-
-// out = A X (diag < 0) or e_diag - A X (diag >= 0) for one column X; exact
-// zeros removed; output row-sorted.  Expansion-sort-compress: every product
-// (k, r) of the column is expanded, stably sorted by r (so k stays ascending
-// inside each r), and each r is accumulated by an fma chain.
+// General ELL layout (A rows padded with column -1).  X must be row-sorted:
+// products are generated k-major and lanes of one chunk that hit the same r
+// apply their fma in lane order, so each r sees the chain over ascending k.
 template <typename VC>
-__device__ int warp_spgemm(const PassParams& p, const SpgemmScratch& s, VC* aval, const int* xr,
-                           const VC* xv, int L, int diag, int* outr, VC* outv, int lane) {
+__device__ int spgemm_ell(const PassParams& p, const HashT& h, const int* xr, const VC* xv, int L,
+                          int diag, int lane) {
   const int W = p.W;
   const int P = L * W;
-  const int Ptot = P + (diag >= 0 ? 1 : 0);
-  if (Ptot == 0) return 0;
   const VC* ev = (const VC*)p.ell_val;
-  unsigned rmin = 0xffffffffu, rmax = 0u;
-  for (int q = lane; q < P; q += 32) {
-    int i = (int)__umulhi((unsigned)q, p.magicW);
-    int t = q - i * W;
-    long long e = (long long)xr[i] * W + t;
-    int col = __ldg(p.ell_col + e);
-    VC a = __ldg(ev + e);
-    s.key0[q] = (uint32_t)col;
-    aval[q] = a;
-    rmin = min(rmin, (unsigned)col);
-    rmax = max(rmax, (unsigned)col);
+  VC* hv = (VC*)h.val;
+  int cnt = 0;
+  for (int base = 0; base < P; base += 32) {
+    int q = base + lane;
+    bool act = false, isnew = false;
+    int slot = -1;
+    VC a = VC(0), x = VC(0);
+    if (q < P) {
+      int i = (int)__umulhi((unsigned)q, p.magicW);
+      int t = q - i * W;
+      long long e = (long long)xr[i] * W + t;
+      int col = __ldg(p.ell_col + e);
+      if (col >= 0) {
+        act = true;
+        a = __ldg(ev + e);
+        x = xv[i];
+        slot = hash_insert<VC>(h, col, &isnew);
+      }
+    }
+    occ_append(h, cnt, isnew, slot);
+    __syncwarp();
+    unsigned am = __ballot_sync(kFull, act);
+    int rank = 0;
+    if (act) {
+      unsigned peers = __match_any_sync(am, slot);
+      rank = __popc(peers & lanemask_lt());
+    }
+    int maxr = __reduce_max_sync(kFull, rank);
+    for (int rho = 0; rho <= maxr; rho++) {
+      if (act && rank == rho) hv[slot] = vfma(a, x, hv[slot]);
+      __syncwarp();
+    }
   }
   if (diag >= 0) {
-    if (lane == 0) s.key0[P] = (uint32_t)diag;
-    rmin = min(rmin, (unsigned)diag);
-    rmax = max(rmax, (unsigned)diag);
+    bool isnew = false;
+    int slot = -1;
+    if (lane == 0) slot = hash_insert<VC>(h, diag, &isnew);
+    occ_append(h, cnt, isnew, slot);
+    __syncwarp();
   }
-  rmin = __reduce_min_sync(kFull, rmin);
-  rmax = __reduce_max_sync(kFull, rmax);
+  return cnt;
+}
+
+// sort a short list by row in place (rank by counting; rows distinct)
+template <typename V>
+__device__ void sort_rows_small(int* r, V* v, int L, int* tr, V* tv, int lane) {
+  for (int i = lane; i < L; i += 32) {
+    int x = r[i], rank = 0;
+    for (int q = 0; q < L; q++) rank += r[q] < x;
+    tr[rank] = x;
+    tv[rank] = v[i];
+  }
   __syncwarp();
-  for (int q = lane; q < Ptot; q += 32) {
-    s.key0[q] -= rmin;
-    s.idx0[q] = (uint16_t)q;
+  for (int i = lane; i < L; i += 32) {
+    r[i] = tr[i];
+    v[i] = tv[i];
   }
   __syncwarp();
-  unsigned range = rmax - rmin;
-  int bits = range ? 32 - __clz(range) : 0;
-  int passes = (bits + 7) >> 3;
-  uint32_t* kin = s.key0;
-  uint16_t* iin = s.idx0;
-  uint32_t* kout = s.key1;
-  uint16_t* iout = s.idx1;
-  for (int ps = 0; ps < passes; ps++) {
-    radix_pass(kin, iin, kout, iout, Ptot, 8 * ps, s.hist, lane);
-    uint32_t* tk = kin; kin = kout; kout = tk;
-    uint16_t* ti = iin; iin = iout; iout = ti;
-  }
-  int U = 0;
-  for (int base = 0; base < Ptot; base += 32) {
-    int q = base + lane;
-    bool head = q < Ptot && (q == 0 || kin[q] != kin[q - 1]);
-    unsigned b = __ballot_sync(kFull, head);
-    if (head) s.hp[U + __popc(b & lanemask_lt())] = (uint16_t)q;
-    U += __popc(b);
-  }
-  if (lane == 0) s.hp[U] = (uint16_t)Ptot;
-  __syncwarp();
+}
+
+// Move the table's rows to a list: value = acc (diag < 0) or the residual
+// 1 - acc on the diagonal / -acc elsewhere (diag >= 0); the transformed
+// value is also written back to the table so later lookups see R itself.
+// Exact zeros are left out of the list.
+template <typename VC>
+__device__ int table_to_list(const HashT& h, int cnt, int diag, int* outr, VC* outv, int lane) {
+  VC* hv = (VC*)h.val;
   int outn = 0;
-  for (int base = 0; base < U; base += 32) {
-    int u = base + lane;
-    VC val = VC(0);
-    int r = 0;
+  for (int base = 0; base < cnt; base += 32) {
+    int i = base + lane;
     bool nz = false;
-    if (u < U) {
-      int s0 = s.hp[u], s1 = s.hp[u + 1];
-      VC acc = VC(0);
-      for (int q = s0; q < s1; q++) {
-        int pi = iin[q];
-        if (pi < P) {
-          int i = (int)__umulhi((unsigned)pi, p.magicW);
-          acc = vfma(aval[pi], xv[i], acc);
-        }
+    int r = 0;
+    VC val = VC(0);
+    if (i < cnt) {
+      int s = h.occ[i];
+      r = h.key[s];
+      VC acc = hv[s];
+      if (diag >= 0) {
+        val = (r == diag) ? (VC(1) - acc) : -acc;
+        hv[s] = val;
+      } else {
+        val = acc;
       }
-      r = (int)(kin[s0] + rmin);
-      if (diag >= 0) val = (r == diag) ? (VC(1) - acc) : -acc;
-      else val = acc;
       nz = val != VC(0);
     }
     unsigned b = __ballot_sync(kFull, nz);
@@ -444,6 +643,49 @@ __device__ int warp_spgemm(const PassParams& p, const SpgemmScratch& s, VC* aval
   }
   __syncwarp();
   return outn;
+}
+
+// ----------------------------------------------------- term functors
+
+template <typename V> struct TermSq {        // x_i^2 of a list
+  const V* v;
+  __device__ double operator()(int i) const {
+    double x = (double)v[i];
+    return __dmul_rn(x, x);
+  }
+};
+template <typename V> struct TermSqTable {   // x^2 of the occupied slots of a table
+  const V* v;
+  const uint16_t* occ;
+  __device__ double operator()(int i) const {
+    double x = (double)v[occ[i]];
+    return __dmul_rn(x, x);
+  }
+};
+template <typename V> struct TermProd {      // x_i * y_i of two aligned arrays
+  const V* x;
+  const V* y;
+  __device__ double operator()(int i) const { return __dmul_rn((double)x[i], (double)y[i]); }
+};
+template <typename V> struct TermProdTable { // a[occ[i]] * y_i
+  const V* a;
+  const uint16_t* occ;
+  const V* y;
+  __device__ double operator()(int i) const {
+    return __dmul_rn((double)a[occ[i]], (double)y[i]);
+  }
+};
+
+// y_i = value of row xr[i] in table h (0 if absent)
+template <typename V>
+__device__ void lookup_list(const int* xr, int L, const HashT& h, V* y, int lane) {
+  for (int i = lane; i < L; i += 32) y[i] = hash_find<V>(h, xr[i]);
+}
+
+// y_i = value in table b of the row of the i-th occupied slot of table a
+template <typename V>
+__device__ void lookup_table(const HashT& a, int cnt, const HashT& b, V* y, int lane) {
+  for (int i = lane; i < cnt; i += 32) y[i] = hash_find<V>(b, a.key[a.occ[i]]);
 }
 
 }  // namespace spai

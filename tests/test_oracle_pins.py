@@ -58,6 +58,24 @@ def test_pairwise_tree_shape():
     assert O.pairwise([1e16, 1.0, -1e16, 1.0]) == (1e16 + 1.0) + (-1e16 + 1.0)
 
 
+def test_fixsum_is_the_correctly_rounded_exact_sum():
+    # within 2^58 of the largest term nothing is truncated, so the result is
+    # the exact sum rounded once -- which math.fsum also computes
+    rng = np.random.default_rng(2)
+    for trial in range(300):
+        L = int(rng.integers(1, 400))
+        x = rng.standard_normal(L) * np.exp2(rng.integers(-50, 0, L))
+        if trial % 3 == 0:
+            x = np.concatenate([x, -x[: L // 2]])  # heavy cancellation
+        assert O.fixsum(x) == math.fsum(x)
+        assert O.fixsum(rng.permutation(x)) == O.fixsum(x)     # order free
+    assert O.fixsum([]) == 0.0
+    assert O.fixsum([1.0, -1.0]) == 0.0
+    assert O.fixsum([2.0 ** 1000, 1.0]) == 2.0 ** 1000          # tiny term truncated
+    big = [1e300, -1e300, 3.0]
+    assert O.fixsum(big) == 0.0                                  # 3 is below 2^(E-110)
+
+
 # ------------------------------------------------------------- dropping
 
 def brute_drop(rows, vals, cap):
