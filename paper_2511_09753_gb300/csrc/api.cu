@@ -93,6 +93,11 @@ struct spai_ctx {
   int *d_tmpi = nullptr;
   double* d_tmpv = nullptr;
   long long mt_cap = 0, sym_cap = 0;
+  // sliced-ELL copies for PCG: A (built on first use), and M or S
+  long long* d_asp = nullptr;
+  int *d_acol = nullptr, *d_w32 = nullptr;
+  double* d_aval = nullptr;
+  long long a_cap = 0;
   // PCG vectors
   double *d_b = nullptr, *d_x = nullptr, *d_r = nullptr, *d_z = nullptr, *d_p = nullptr,
          *d_q = nullptr;
@@ -407,6 +412,10 @@ void free_all(spai_ctx* h) {
   dfree(h->d_scan);
   dfree(h->d_tmpi);
   dfree(h->d_tmpv);
+  dfree(h->d_asp);
+  dfree(h->d_acol);
+  dfree(h->d_w32);
+  dfree(h->d_aval);
   dfree(h->d_b);
   dfree(h->d_x);
   dfree(h->d_r);
@@ -1060,7 +1069,15 @@ static int ensure_pcg(spai_ctx* h) {
   rc = rc ? rc : dalloc(&h->d_vgsum, ng);
   rc = rc ? rc : dalloc(&h->d_vcnt1, ng);
   rc = rc ? rc : dalloc(&h->d_vcnt2, 1);
+  const int ns = (n + 31) / 32;
+  rc = rc ? rc : dalloc(&h->d_asp, (size_t)ns + 1);
+  rc = rc ? rc : dalloc(&h->d_w32, (size_t)ns + 1);
+  if (!h->d_scan) rc = rc ? rc : dalloc(&h->d_scan, 2 * (size_t)((n + 1023) / 1024) + 2);
   if (rc) return rc;
+  long long tot = 0;
+  CK(launch_sell_build_i32(n, h->d_rowptr, h->d_colind, h->d_vals, h->d_w32, h->d_asp, h->d_scan,
+                           &h->d_acol, &h->d_aval, &h->a_cap, &tot, h->stream));
+  h->other_launches += 5;
   CK(cudaMemsetAsync(h->d_vcnt1, 0, sizeof(unsigned) * ng, h->stream));
   CK(cudaMemsetAsync(h->d_vcnt2, 0, sizeof(unsigned), h->stream));
   return SPAI_OK;
@@ -1090,9 +1107,9 @@ int pcg_solve(spai_handle h, const double* b, double* x, int nrhs, double rtol, 
   PcgArgs a;
   memset(&a, 0, sizeof(a));
   a.n = n;
-  a.arp = h->d_rowptr;
-  a.aci = h->d_colind;
-  a.av = h->d_vals;
+  a.A.sptr = h->d_asp;
+  a.A.col = h->d_acol;
+  a.A.val = h->d_aval;
   a.diag = h->d_diag;
   a.precond = precond;
   if (precond == SPAI_PREC_SPAI) {

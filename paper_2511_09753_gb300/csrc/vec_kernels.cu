@@ -86,6 +86,94 @@ __device__ __forceinline__ double row_chain(const RP* rp, const int* ci, const V
   return acc;
 }
 
+// Sliced ELL (32 rows per slice, column-major inside a slice, padded with
+// zero values): thread i reads entry t of its row at base + 32 t + lane, so
+// a warp's loads are coalesced; entries keep ascending column order, so the
+// fma chain of every row is the same as in CSR.
+__device__ __forceinline__ double sell_chain(const SellM& m, const double* x, int i) {
+  const int s = i >> 5, lane = i & 31;
+  const long long b = m.sptr[s];
+  const int w = (int)((m.sptr[s + 1] - b) >> 5);
+  double acc = 0.0;
+  for (int t = 0; t < w; t++) {
+    long long e = b + 32LL * t + lane;
+    acc = __fma_rn(m.val[e], x[m.col[e]], acc);
+  }
+  return acc;
+}
+
+template <typename RP>
+__global__ void k_sell_width(int n, const RP* rp, int* w32) {
+  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  int ns = (n + 31) / 32;
+  if (s >= ns) return;
+  int w = 0;
+  for (int i = 32 * s; i < min(n, 32 * s + 32); i++) w = max(w, (int)(rp[i + 1] - rp[i]));
+  w32[s] = 32 * w;
+}
+
+template <typename RP>
+__global__ void k_sell_fill(int n, const RP* rp, const int* ci, const double* v,
+                            const long long* sptr, int* scol, double* sval) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  int ns = (n + 31) / 32;
+  if (i >= 32 * ns) return;
+  const int s = i >> 5, lane = i & 31;
+  const long long b = sptr[s];
+  const int w = (int)((sptr[s + 1] - b) >> 5);
+  long long e0 = i < n ? (long long)rp[i] : 0, e1 = i < n ? (long long)rp[i + 1] : 0;
+  for (int t = 0; t < w; t++) {
+    long long e = e0 + t;
+    long long d = b + 32LL * t + lane;
+    if (e < e1) {
+      scol[d] = ci[e];
+      sval[d] = v[e];
+    } else {
+      scol[d] = 0;
+      sval[d] = 0.0;
+    }
+  }
+}
+
+template <typename RP>
+static cudaError_t sell_build_t(int n, const RP* rp, const int* ci, const double* v, int* w32,
+                                long long* sptr, long long* scan_tmp, int** scol, double** sval,
+                                long long* cap, long long* total, cudaStream_t st) {
+  int ns = (n + 31) / 32;
+  k_sell_width<RP><<<(ns + 255) / 256, 256, 0, st>>>(n, rp, w32);
+  cudaError_t e = launch_exclusive_scan(w32, sptr, ns, scan_tmp, st);
+  if (e != cudaSuccess) return e;
+  long long tot = 0;
+  e = cudaMemcpyAsync(&tot, sptr + ns, sizeof(long long), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return e;
+  if (tot > *cap || !*scol) {
+    if (*scol) cudaFree(*scol);
+    if (*sval) cudaFree(*sval);
+    *scol = nullptr;
+    *sval = nullptr;
+    e = cudaMalloc((void**)scol, sizeof(int) * (size_t)(tot ? tot : 1));
+    if (e == cudaSuccess) e = cudaMalloc((void**)sval, sizeof(double) * (size_t)(tot ? tot : 1));
+    if (e != cudaSuccess) return e;
+    *cap = tot;
+  }
+  k_sell_fill<RP><<<(32 * ns + 255) / 256, 256, 0, st>>>(n, rp, ci, v, sptr, *scol, *sval);
+  *total = tot;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sell_build_i32(int n, const int* rp, const int* ci, const double* v, int* w32,
+                                  long long* sptr, long long* scan_tmp, int** scol, double** sval,
+                                  long long* cap, long long* total, cudaStream_t st) {
+  return sell_build_t<int>(n, rp, ci, v, w32, sptr, scan_tmp, scol, sval, cap, total, st);
+}
+
+cudaError_t launch_sell_build_i64(int n, const long long* rp, const int* ci, const double* v,
+                                  int* w32, long long* sptr, long long* scan_tmp, int** scol,
+                                  double** sval, long long* cap, long long* total, cudaStream_t st) {
+  return sell_build_t<long long>(n, rp, ci, v, w32, sptr, scan_tmp, scol, sval, cap, total, st);
+}
+
 // ------------------------------------------------------------ set-up
 
 template <typename VS>
@@ -339,7 +427,7 @@ __global__ void k_true_res(PcgArgs a) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   double term = 0.0;
   if (i < a.n) {
-    double y = row_chain(a.arp, a.aci, a.av, a.x, i);
+    double y = sell_chain(a.A, a.x, i);
     double d = __dsub_rn(a.b[i], y);
     term = __dmul_rn(d, d);
   }
@@ -415,7 +503,7 @@ __global__ void k_pcg_spmv(PcgArgs a) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   double term = 0.0;
   if (i < a.n) {
-    double q = row_chain(a.arp, a.aci, a.av, a.p, i);
+    double q = sell_chain(a.A, a.p, i);
     a.q[i] = q;
     term = __dmul_rn(a.p[i], q);
   }

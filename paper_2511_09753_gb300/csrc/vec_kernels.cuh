@@ -14,6 +14,12 @@ struct RedWS {  // last-arriver reduction workspace
   int nb, ngroups;
 };
 
+struct SellM {  // sliced ELL: slice s holds entries [sptr[s], sptr[s+1])
+  const long long* sptr;
+  const int* col;
+  const double* val;
+};
+
 struct PcgScalars {
   double rho, alpha, beta, bn, rtol, tres;
   int k, maxit, done, status;
@@ -21,11 +27,9 @@ struct PcgScalars {
 
 struct PcgArgs {
   int n;
-  const int* arp;    // CSR of A (int32 row pointers for A)
-  const int* aci;
-  const double* av;
+  SellM A;           // A in sliced ELL
   const double* diag;
-  int precond;       // 0 none, 1 Jacobi, 2/3 CSR in mrp/mci/mv
+  int precond;       // 0 none, 1 Jacobi, 2/3 CSR rows of M or of (M + M^T)/2
   const long long* mrp;
   const int* mci;
   const double* mv;
@@ -51,6 +55,12 @@ cudaError_t launch_sym(int n, const long long* rp, const int* rci, const double*
                        const long long* srp, int* sci, double* sv, cudaStream_t st);
 cudaError_t launch_apply(int n, const long long* rp, const int* ci, const double* v, const double* x,
                          double* y, int nrhs, long long ld, cudaStream_t st);
+cudaError_t launch_sell_build_i32(int n, const int* rp, const int* ci, const double* v, int* w32,
+                                  long long* sptr, long long* scan_tmp, int** scol, double** sval,
+                                  long long* cap, long long* total, cudaStream_t st);
+cudaError_t launch_sell_build_i64(int n, const long long* rp, const int* ci, const double* v,
+                                  int* w32, long long* sptr, long long* scan_tmp, int** scol,
+                                  double** sval, long long* cap, long long* total, cudaStream_t st);
 cudaError_t launch_pcg_init(const PcgArgs& a, cudaStream_t st);
 cudaError_t launch_pcg_iter(const PcgArgs& a, cudaStream_t st);
 cudaError_t launch_true_res(const PcgArgs& a, cudaStream_t st);
