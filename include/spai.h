@@ -110,6 +110,35 @@ int spai_create(spai_handle *out, int64_t n, int64_t nnz, const int32_t *rowptr,
                 const int32_t *colind, const double *vals, int on_device, const spai_opts *opts,
                 void *stream);
 
+/* Batched handle (no counterpart in the paper: many independent SPAIs at
+ * once).  nmat SPD matrices, each given as its own CSR (host arrays, each
+ * validated as in spai_create), are laid block-diagonally, each padded with
+ * identity rows to a multiple of 256; every spai_run / PCG step then treats
+ * all of them in the same launches, with per-matrix step coefficients, stops
+ * and histories, so that each matrix's iterates equal those of a
+ * single-matrix handle.  Limits: every matrix n <= 262,144 and has at most 32
+ * distinct diagonals for the fast path; the padded total n < 2^26.
+ * spai_get_M / spai_apply / pcg_solve see the padded block-diagonal matrix;
+ * a call after one matrix converged early restarts every recurrence. */
+int spai_create_batched(spai_handle *out, int nmat, const int64_t *n, const int64_t *nnz,
+                        const int32_t *const *rowptr, const int32_t *const *colind,
+                        const double *const *vals, const spai_opts *opts, void *stream);
+
+/* Number of matrices of a handle (1 for a single-matrix handle) and, if
+ * n_each != NULL, their sizes. */
+int spai_batch_info(spai_handle h, int *nmat, int64_t *n_each);
+
+/* Per-matrix results of the last spai_run (host arrays, may be NULL):
+ * resnorm[m*(iters+1) + i] = ||R_i||_F of matrix m, iters_done[m], flags[m]. */
+int spai_batch_history(spai_handle h, double *resnorm, int *iters_done, int *flags);
+
+/* ||I - A_m M_m||_F in FP64 for every matrix m (host out[nmat]). */
+int spai_batch_residual_norms(spai_handle h, double *out);
+
+/* CSC of matrix m's M on the host, two-call like spai_get_M. */
+int spai_batch_get_M(spai_handle h, int m, int64_t *nnz, int32_t *colptr, int32_t *rowind,
+                     double *vals);
+
 /* Free every device and host resource of the handle. */
 int spai_destroy(spai_handle h);
 

@@ -31,9 +31,13 @@ struct PassCfg {
   bool ok;
 };
 
-struct Buf {  // device allocation helper
-  void* p = nullptr;
-  size_t bytes = 0;
+constexpr int kSegAlign = 256;  // batched segments start at multiples of this
+
+struct BatchDesc {
+  int nseg;
+  const long long* col0;   // first global column of each matrix
+  const long long* nreal;  // its size
+  const long long* npad;   // its padded size (multiple of kSegAlign)
 };
 
 }  // namespace
@@ -74,6 +78,15 @@ struct spai_ctx {
   unsigned *d_cnt1 = nullptr, *d_cnt2 = nullptr;
   int red_nb = 0, red_ng = 0;
   PassCfg cfg[5];
+  // batched mode: nseg matrices laid block-diagonally, each padded with
+  // identity rows/columns to a multiple of kSegAlign
+  int nseg = 0;
+  std::vector<long long> seg_col0, seg_n, seg_npad;
+  int *d_seg_of_col = nullptr, *d_seg_col0 = nullptr, *d_seg_npad = nullptr;
+  int *d_seg_D = nullptr, *d_seg_doff = nullptr;
+  DevScalars* d_segsc = nullptr;
+  unsigned* d_seg_cnt = nullptr;
+  int last_iters = 0;
   // method state (host mirror)
   int method = -1;
   int it = 0;
@@ -228,7 +241,8 @@ static int env_int(const char* name, int dflt) {
   return x > 0 ? x : dflt;
 }
 
-PassCfg make_cfg(int kind, int vc, int n, int CAP, int W, bool dia, int smem_max) {
+PassCfg make_cfg(int kind, int vc, int n, int CAP, int W, bool dia, int smem_max, int Bmin = 1,
+                 int Bmax = 1024) {
   PassCfg c;
   memset(&c, 0, sizeof(c));
   c.lay = make_layout(kind, vc, CAP, W, dia);
@@ -247,6 +261,8 @@ PassCfg make_cfg(int kind, int vc, int n, int CAP, int W, bool dia, int smem_max
     long long target = (long long)n / (152LL * 8);
     while ((long long)B * 2 <= target && B * 2 <= cpw * NW) B *= 2;
     while (((long long)n + B - 1) / B > 65536LL && B < 1024) B *= 2;
+    while (B < Bmin) B *= 2;
+    if (B > Bmax) return c;  // batched: a CTA must not straddle two matrices
     // the CTA reduction buffer (1024 doubles) reuses the warps' scratch,
     // which is free once every column of the block is done
     size_t smem = std::max((size_t)NW * c.lay.bytes, (size_t)extra_fixed);
@@ -350,6 +366,15 @@ PassParams base_params(spai_ctx* h, int kind, bool res) {
   p.Dp = h->Dp;
   for (int s2 = 0; s2 < 32; s2++) p.dia_off[s2] = h->dia ? h->dia_off[s2 < h->D ? s2 : 0] : 0;
   p.dia_val = (res || h->prec == SPAI_FP64) ? (const void*)h->d_dia64 : (const void*)h->d_dia32;
+  p.nseg = h->nseg;
+  p.seg_of_col = h->d_seg_of_col;
+  p.seg_col0 = h->d_seg_col0;
+  p.seg_npad = h->d_seg_npad;
+  p.segsc = h->d_segsc;
+  p.seg_D = h->d_seg_D;
+  p.seg_doff = h->d_seg_doff;
+  p.seg_cnt = h->d_seg_cnt;
+  p.hist_stride = h->last_iters + 1;
   p.sc = h->d_sc;
   p.hist_res = h->d_hres;
   p.hist_coef = h->d_hcoef;
@@ -393,6 +418,13 @@ void free_all(spai_ctx* h) {
   dfree(h->d_Plen);
   dfree(h->d_Zlen);
   dfree(h->d_sc);
+  dfree(h->d_seg_of_col);
+  dfree(h->d_seg_col0);
+  dfree(h->d_seg_npad);
+  dfree(h->d_seg_D);
+  dfree(h->d_seg_doff);
+  dfree(h->d_segsc);
+  dfree(h->d_seg_cnt);
   dfree(h->d_hres);
   dfree(h->d_hcoef);
   dfree(h->d_bsum);
@@ -579,37 +611,15 @@ int spai_validate_csr(int64_t n, int64_t nnz, const int32_t* rowptr, const int32
   return SPAI_OK;
 }
 
-int spai_create(spai_handle* out, int64_t n, int64_t nnz, const int32_t* rowptr,
-                const int32_t* colind, const double* vals, int on_device, const spai_opts* opts,
-                void* stream) {
-  if (!out) return SPAI_ERR_ARG;
-  *out = nullptr;
-  if (!opts || n < 1 || nnz < 1 || !rowptr || !colind || !vals) return SPAI_ERR_ARG;
-  if (opts->prec != SPAI_FP64 && opts->prec != SPAI_MIXED) return SPAI_ERR_ARG;
-  if (!(opts->cap_factor > 0.0)) return SPAI_ERR_ARG;
-  if (n >= (1LL << 26) || nnz >= (1LL << 31)) return SPAI_ERR_UNSUPPORTED;
-  std::vector<int32_t> hrp, hci;
-  std::vector<double> hv;
-  const int32_t* rp = rowptr;
-  const int32_t* ci = colind;
-  const double* va = vals;
-  if (on_device) {
-    hrp.resize(n + 1);
-    hci.resize(nnz);
-    hv.resize(nnz);
-    if (cudaMemcpy(hrp.data(), rowptr, sizeof(int32_t) * (n + 1), cudaMemcpyDeviceToHost) ||
-        cudaMemcpy(hci.data(), colind, sizeof(int32_t) * nnz, cudaMemcpyDeviceToHost) ||
-        cudaMemcpy(hv.data(), vals, sizeof(double) * nnz, cudaMemcpyDeviceToHost)) {
-      (void)cudaGetLastError();
-      return SPAI_ERR_CUDA;
-    }
-    rp = hrp.data();
-    ci = hci.data();
-    va = hv.data();
-  }
-  int rc = spai_validate_csr(n, nnz, rp, ci, va, 1);
-  if (rc) return rc;
+}  // extern "C"
 
+namespace {
+
+// Build a handle from a validated host CSR.  bd != nullptr: the CSR is the
+// block-diagonal, padded concatenation of bd->nseg matrices.
+int create_impl(spai_handle* out, int64_t n, int64_t nnz, const int32_t* rp, const int32_t* ci,
+                const double* va, const spai_opts* opts, void* stream, const BatchDesc* bd) {
+  int rc = SPAI_OK;
   spai_ctx* h = new (std::nothrow) spai_ctx();
   if (!h) return SPAI_ERR_OOM;
   h->n = (int)n;
@@ -633,10 +643,18 @@ int spai_create(spai_handle* out, int64_t n, int64_t nnz, const int32_t* rowptr,
   std::vector<long long> off(n + 1);
   off[0] = 0;
   int capmax = 1;
+  std::vector<int> seg_of_col;
+  if (bd) {
+    seg_of_col.assign(n, 0);
+    for (int m = 0; m < bd->nseg; m++)
+      for (long long q = 0; q < bd->npad[m]; q++) seg_of_col[bd->col0[m] + q] = m;
+  }
   for (int64_t j = 0; j < n; j++) {
     double c = floor(opts->cap_factor * (double)(rp[j + 1] - rp[j]));
+    const double lim = bd ? (double)bd->nreal[seg_of_col[j]] : (double)n;
     if (!(c >= 1.0)) c = 1.0;
-    if (c > (double)n) c = (double)n;
+    if (c > lim) c = lim;
+    if (c < 1.0) c = 1.0;
     cap[j] = (int)c;
     capmax = std::max(capmax, cap[j]);
     off[j + 1] = off[j] + cap[j];
@@ -673,7 +691,56 @@ int spai_create(spai_handle* out, int64_t n, int64_t nnz, const int32_t* rowptr,
   // diagonal-slot layout when A has at most 32 distinct offsets col - row
   std::vector<double> d64;
   std::vector<float> d32;
-  {
+  std::vector<int> seg_D, seg_doff;
+  if (bd) {
+    // per-matrix diagonal slots; every matrix must have at most 32
+    bool ok = true;
+    seg_D.assign(bd->nseg, 0);
+    seg_doff.assign((size_t)bd->nseg * 32, 0);
+    int Dmax = 0;
+    for (int m = 0; m < bd->nseg && ok; m++) {
+      std::vector<long long> offs;
+      for (long long i = bd->col0[m]; i < bd->col0[m] + bd->npad[m] && ok; i++)
+        for (int64_t e = rp[i]; e < rp[i + 1]; e++) {
+          long long o = (long long)ci[e] - i;
+          if (std::find(offs.begin(), offs.end(), o) == offs.end()) {
+            offs.push_back(o);
+            if (offs.size() > 32) {
+              ok = false;
+              break;
+            }
+          }
+        }
+      if (!ok) break;
+      std::sort(offs.begin(), offs.end());
+      seg_D[m] = (int)offs.size();
+      for (size_t s2 = 0; s2 < offs.size(); s2++) seg_doff[(size_t)m * 32 + s2] = (int)offs[s2];
+      Dmax = std::max(Dmax, seg_D[m]);
+    }
+    if (ok) {
+      h->dia = true;
+      h->D = Dmax;
+      h->Dp = Dmax;
+      for (int s2 = 0; s2 < 32; s2++) h->dia_off[s2] = 0;
+      d64.assign((size_t)n * h->Dp, 0.0);
+      for (int64_t i = 0; i < n; i++) {
+        const int m = seg_of_col[i];
+        const int* so = &seg_doff[(size_t)m * 32];
+        for (int64_t e = rp[i]; e < rp[i + 1]; e++) {
+          long long o = (long long)ci[e] - i;
+          int s2 = (int)(std::lower_bound(so, so + seg_D[m], (int)o) - so);
+          d64[(size_t)i * h->Dp + s2] = va[e];
+        }
+      }
+      if (h->prec == SPAI_MIXED) {
+        d32.resize(d64.size());
+        for (size_t k = 0; k < d64.size(); k++) d32[k] = (float)d64[k];
+      }
+    } else {
+      seg_D.clear();
+      seg_doff.clear();
+    }
+  } else {
     std::vector<long long> offs;
     bool ok = true;
     for (int64_t i = 0; i < n && ok; i++)
@@ -713,7 +780,14 @@ int spai_create(spai_handle* out, int64_t n, int64_t nnz, const int32_t* rowptr,
   if (smem_max <= 0) smem_max = 227 * 1024;
   const int vc = h->prec == SPAI_MIXED ? 4 : 8;
   for (int k = 0; k < 5; k++) {
-    h->cfg[k] = make_cfg(k, k == kRES ? 8 : vc, (int)n, capmax, W, h->dia, smem_max);
+    int Bmin = 1, Bmax = 1024;
+    if (bd) {
+      long long npmax = 0;
+      for (int m = 0; m < bd->nseg; m++) npmax = std::max(npmax, bd->npad[m]);
+      while ((long long)Bmin * 1024 < npmax) Bmin *= 2;  // <= 1024 CTAs per matrix
+      Bmax = kSegAlign;
+    }
+    h->cfg[k] = make_cfg(k, k == kRES ? 8 : vc, (int)n, capmax, W, h->dia, smem_max, Bmin, Bmax);
     if (!h->cfg[k].ok) {
       if (h->own_stream) cudaStreamDestroy(h->stream);
       delete h;
@@ -752,6 +826,20 @@ int spai_create(spai_handle* out, int64_t n, int64_t nnz, const int32_t* rowptr,
   rc = rc ? rc : dalloc(&h->d_cnt1, h->red_ng);
   rc = rc ? rc : dalloc(&h->d_cnt2, 1);
   rc = rc ? rc : ensure_hist(h, 64);
+  if (bd) {
+    h->nseg = bd->nseg;
+    h->seg_col0.assign(bd->col0, bd->col0 + bd->nseg);
+    h->seg_n.assign(bd->nreal, bd->nreal + bd->nseg);
+    h->seg_npad.assign(bd->npad, bd->npad + bd->nseg);
+    rc = rc ? rc : dalloc(&h->d_seg_of_col, n);
+    rc = rc ? rc : dalloc(&h->d_seg_col0, bd->nseg);
+    rc = rc ? rc : dalloc(&h->d_seg_npad, bd->nseg);
+    rc = rc ? rc : dalloc(&h->d_seg_D, bd->nseg);
+    rc = rc ? rc : dalloc(&h->d_seg_doff, (size_t)bd->nseg * 32);
+    rc = rc ? rc : dalloc(&h->d_segsc, bd->nseg);
+    rc = rc ? rc : dalloc(&h->d_seg_cnt, bd->nseg);
+    rc = rc ? rc : ensure_hist(h, 64 * bd->nseg);
+  }
   if (rc) {
     free_all(h);
     if (h->own_stream) cudaStreamDestroy(h->stream);
@@ -782,6 +870,31 @@ int spai_create(spai_handle* out, int64_t n, int64_t nnz, const int32_t* rowptr,
                         st) == 0;
   ok &= cudaMemcpyAsync(h->d_cap, cap.data(), sizeof(int) * n, cudaMemcpyHostToDevice, st) == 0;
   ok &= cudaMemsetAsync(h->d_sc, 0, sizeof(DevScalars), st) == 0;
+  if (bd) {
+    std::vector<int> c0(bd->nseg), np(bd->nseg);
+    for (int m = 0; m < bd->nseg; m++) {
+      c0[m] = (int)bd->col0[m];
+      np[m] = (int)bd->npad[m];
+    }
+    if (seg_D.empty()) {
+      seg_D.assign(bd->nseg, 0);
+      seg_doff.assign((size_t)bd->nseg * 32, 0);
+    }
+    ok &= cudaMemcpyAsync(h->d_seg_of_col, seg_of_col.data(), sizeof(int) * n,
+                          cudaMemcpyHostToDevice, st) == 0;
+    ok &= cudaMemcpyAsync(h->d_seg_col0, c0.data(), sizeof(int) * bd->nseg, cudaMemcpyHostToDevice,
+                          st) == 0;
+    ok &= cudaMemcpyAsync(h->d_seg_npad, np.data(), sizeof(int) * bd->nseg, cudaMemcpyHostToDevice,
+                          st) == 0;
+    ok &= cudaMemcpyAsync(h->d_seg_D, seg_D.data(), sizeof(int) * bd->nseg, cudaMemcpyHostToDevice,
+                          st) == 0;
+    ok &= cudaMemcpyAsync(h->d_seg_doff, seg_doff.data(), sizeof(int) * seg_doff.size(),
+                          cudaMemcpyHostToDevice, st) == 0;
+    ok &= cudaMemsetAsync(h->d_segsc, 0, sizeof(DevScalars) * bd->nseg, st) == 0;
+    ok &= cudaMemsetAsync(h->d_seg_cnt, 0, sizeof(unsigned) * bd->nseg, st) == 0;
+    // keep the host copies alive until the copies have run
+    ok &= cudaStreamSynchronize(st) == 0;
+  }
   ok &= cudaMemsetAsync(h->d_cnt1, 0, sizeof(unsigned) * h->red_ng, st) == 0;
   ok &= cudaMemsetAsync(h->d_cnt2, 0, sizeof(unsigned), st) == 0;
   ok &= launch_init_slab(h->prec, (int)n, h->d_off, h->d_diag, h->d_Mrow, h->d_Mval, h->d_Mlen,
@@ -797,6 +910,89 @@ int spai_create(spai_handle* out, int64_t n, int64_t nnz, const int32_t* rowptr,
   }
   *out = h;
   return SPAI_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int spai_create(spai_handle* out, int64_t n, int64_t nnz, const int32_t* rowptr,
+                const int32_t* colind, const double* vals, int on_device, const spai_opts* opts,
+                void* stream) {
+  if (!out) return SPAI_ERR_ARG;
+  *out = nullptr;
+  if (!opts || n < 1 || nnz < 1 || !rowptr || !colind || !vals) return SPAI_ERR_ARG;
+  if (opts->prec != SPAI_FP64 && opts->prec != SPAI_MIXED) return SPAI_ERR_ARG;
+  if (!(opts->cap_factor > 0.0)) return SPAI_ERR_ARG;
+  if (n >= (1LL << 26) || nnz >= (1LL << 31)) return SPAI_ERR_UNSUPPORTED;
+  std::vector<int32_t> hrp, hci;
+  std::vector<double> hv;
+  const int32_t* rp = rowptr;
+  const int32_t* ci = colind;
+  const double* va = vals;
+  if (on_device) {
+    hrp.resize(n + 1);
+    hci.resize(nnz);
+    hv.resize(nnz);
+    if (cudaMemcpy(hrp.data(), rowptr, sizeof(int32_t) * (n + 1), cudaMemcpyDeviceToHost) ||
+        cudaMemcpy(hci.data(), colind, sizeof(int32_t) * nnz, cudaMemcpyDeviceToHost) ||
+        cudaMemcpy(hv.data(), vals, sizeof(double) * nnz, cudaMemcpyDeviceToHost)) {
+      (void)cudaGetLastError();
+      return SPAI_ERR_CUDA;
+    }
+    rp = hrp.data();
+    ci = hci.data();
+    va = hv.data();
+  }
+  int rc = spai_validate_csr(n, nnz, rp, ci, va, 1);
+  if (rc) return rc;
+  return create_impl(out, n, nnz, rp, ci, va, opts, stream, nullptr);
+}
+
+int spai_create_batched(spai_handle* out, int nmat, const int64_t* n, const int64_t* nnz,
+                        const int32_t* const* rowptr, const int32_t* const* colind,
+                        const double* const* vals, const spai_opts* opts, void* stream) {
+  if (!out) return SPAI_ERR_ARG;
+  *out = nullptr;
+  if (!opts || nmat < 1 || !n || !nnz || !rowptr || !colind || !vals) return SPAI_ERR_ARG;
+  if (opts->prec != SPAI_FP64 && opts->prec != SPAI_MIXED) return SPAI_ERR_ARG;
+  if (!(opts->cap_factor > 0.0)) return SPAI_ERR_ARG;
+  std::vector<long long> col0(nmat), nreal(nmat), npad(nmat);
+  long long N = 0, NNZ = 0;
+  for (int m = 0; m < nmat; m++) {
+    if (!rowptr[m] || !colind[m] || !vals[m]) return SPAI_ERR_ARG;
+    int rc = spai_validate_csr(n[m], nnz[m], rowptr[m], colind[m], vals[m], 1);
+    if (rc) return rc;
+    nreal[m] = n[m];
+    npad[m] = (n[m] + kSegAlign - 1) / kSegAlign * kSegAlign;
+    if (npad[m] > 1024LL * kSegAlign) return SPAI_ERR_UNSUPPORTED;
+    col0[m] = N;
+    N += npad[m];
+    NNZ += nnz[m] + (npad[m] - n[m]);
+  }
+  if (N >= (1LL << 26) || NNZ >= (1LL << 31)) return SPAI_ERR_UNSUPPORTED;
+  // block-diagonal concatenation; padding rows are identity rows
+  std::vector<int32_t> grp(N + 1), gci(NNZ);
+  std::vector<double> gv(NNZ);
+  long long e = 0, row = 0;
+  grp[0] = 0;
+  for (int m = 0; m < nmat; m++) {
+    for (long long i = 0; i < n[m]; i++, row++) {
+      for (int32_t q = rowptr[m][i]; q < rowptr[m][i + 1]; q++, e++) {
+        gci[e] = (int32_t)(colind[m][q] + col0[m]);
+        gv[e] = vals[m][q];
+      }
+      grp[row + 1] = (int32_t)e;
+    }
+    for (long long i = n[m]; i < npad[m]; i++, row++) {
+      gci[e] = (int32_t)row;
+      gv[e] = 1.0;
+      e++;
+      grp[row + 1] = (int32_t)e;
+    }
+  }
+  BatchDesc bd{nmat, col0.data(), nreal.data(), npad.data()};
+  return create_impl(out, N, NNZ, grp.data(), gci.data(), gv.data(), opts, stream, &bd);
 }
 
 int spai_destroy(spai_handle h) {
@@ -838,8 +1034,10 @@ int spai_run(spai_handle h, int method, int iters, int drop_rule, spai_history* 
   if (!h || iters < 0 || (method != SPAI_MR && method != SPAI_LOMR && method != SPAI_CG))
     return SPAI_ERR_ARG;
   if (drop_rule != SPAI_DROP_NONE && drop_rule != SPAI_DROP_TOPK_COL) return SPAI_ERR_ARG;
-  int rc = ensure_hist(h, iters);
+  const int nh = std::max(h->nseg, 1);
+  int rc = ensure_hist(h, (iters + 1) * nh);
   if (rc) return rc;
+  h->last_iters = iters;
   cudaStream_t st = h->stream;
   const bool fresh = h->method != method;
   if (fresh) {
@@ -850,8 +1048,9 @@ int spai_run(spai_handle h, int method, int iters, int drop_rule, spai_history* 
   }
   rc = reset_call_scalars(h);
   if (rc) return rc;
-  CK(cudaMemsetAsync(h->d_hres, 0xff, sizeof(double) * (iters + 1), st));
-  CK(cudaMemsetAsync(h->d_hcoef, 0xff, sizeof(double) * 2 * std::max(iters, 1), st));
+  if (h->nseg) CK(launch_seg_reset(h->d_segsc, h->nseg, fresh ? 1 : 0, st));
+  CK(cudaMemsetAsync(h->d_hres, 0xff, sizeof(double) * (iters + 1) * nh, st));
+  CK(cudaMemsetAsync(h->d_hcoef, 0xff, sizeof(double) * 2 * std::max(iters, 1) * nh, st));
   invalidate_rows(h);
   const int drop = drop_rule == SPAI_DROP_TOPK_COL ? 1 : 0;
   auto pass = [&](int kind, int upd, int dir, int iter, int fresh_b) -> cudaError_t {
@@ -890,8 +1089,24 @@ int spai_run(spai_handle h, int method, int iters, int drop_rule, spai_history* 
   if (hist && hist->coef && iters > 0)
     CK(cudaMemcpyAsync(hist->coef, h->d_hcoef, sizeof(double) * 2 * iters, cudaMemcpyDeviceToHost,
                        st));
+  std::vector<DevScalars> ssc;
+  if (h->nseg) {
+    ssc.resize(h->nseg);
+    CK(cudaMemcpyAsync(ssc.data(), h->d_segsc, sizeof(DevScalars) * h->nseg,
+                       cudaMemcpyDeviceToHost, st));
+  }
   CK(cudaStreamSynchronize(st));
   if (h->timing) collect_timing(h);
+  if (h->nseg) {
+    // batched: combine the matrices' outcomes (fewest iterations done, all flags)
+    int done = iters, flags = 0;
+    for (const DevScalars& x : ssc) {
+      done = std::min(done, x.done);
+      flags |= x.flags;
+    }
+    sc.done = done;
+    sc.flags |= flags;
+  }
   if (hist) {
     hist->iters_done = sc.done;
     hist->flags = sc.flags & 3;
@@ -914,6 +1129,37 @@ int spai_run(spai_handle h, int method, int iters, int drop_rule, spai_history* 
   return SPAI_OK;
 }
 
+int spai_batch_info(spai_handle h, int* nmat, int64_t* n_each) {
+  if (!h || !nmat) return SPAI_ERR_ARG;
+  *nmat = h->nseg ? h->nseg : 1;
+  if (n_each) {
+    if (h->nseg)
+      for (int m = 0; m < h->nseg; m++) n_each[m] = h->seg_n[m];
+    else
+      n_each[0] = h->n;
+  }
+  return SPAI_OK;
+}
+
+int spai_batch_history(spai_handle h, double* resnorm, int* iters_done, int* flags) {
+  if (!h) return SPAI_ERR_ARG;
+  const int nh = std::max(h->nseg, 1);
+  const int stride = h->last_iters + 1;
+  cudaStream_t st = h->stream;
+  if (resnorm)
+    CK(cudaMemcpyAsync(resnorm, h->d_hres, sizeof(double) * stride * nh, cudaMemcpyDeviceToHost,
+                       st));
+  std::vector<DevScalars> ssc(nh);
+  CK(cudaMemcpyAsync(ssc.data(), h->nseg ? h->d_segsc : h->d_sc, sizeof(DevScalars) * nh,
+                     cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  for (int m = 0; m < nh; m++) {
+    if (iters_done) iters_done[m] = ssc[m].done;
+    if (flags) flags[m] = ssc[m].flags & 3;
+  }
+  return SPAI_OK;
+}
+
 int spai_mr(spai_handle h, int iters, int drop_rule, spai_history* hist) {
   return spai_run(h, SPAI_MR, iters, drop_rule, hist);
 }
@@ -926,6 +1172,15 @@ int spai_cg(spai_handle h, int iters, int drop_rule, spai_history* hist) {
 
 int spai_residual_norm(spai_handle h, double* out) {
   if (!h || !out) return SPAI_ERR_ARG;
+  if (h->nseg) {
+    std::vector<double> r(h->nseg);
+    int rc = spai_batch_residual_norms(h, r.data());
+    if (rc) return rc;
+    double s2 = 0.0;
+    for (double x : r) s2 += x * x;
+    *out = sqrt(s2);
+    return SPAI_OK;
+  }
   int rc = reset_call_scalars(h);
   if (rc) return rc;
   PassParams p = base_params(h, kRES, true);
@@ -938,6 +1193,53 @@ int spai_residual_norm(spai_handle h, double* out) {
   CK(cudaStreamSynchronize(h->stream));
   if (h->timing) collect_timing(h);
   *out = sqrt(sc.result);
+  return SPAI_OK;
+}
+
+int spai_batch_residual_norms(spai_handle h, double* out) {
+  if (!h || !out) return SPAI_ERR_ARG;
+  if (!h->nseg) return spai_residual_norm(h, out);
+  int rc = reset_call_scalars(h);
+  if (rc) return rc;
+  CK(launch_seg_reset(h->d_segsc, h->nseg, 0, h->stream));
+  PassParams p = base_params(h, kRES, true);
+  p.do_dir = 0;
+  p.hist_res = nullptr;
+  p.hist_coef = nullptr;
+  CK(timed_launch(h, p, h->cfg[kRES], true));
+  std::vector<DevScalars> ssc(h->nseg);
+  CK(cudaMemcpyAsync(ssc.data(), h->d_segsc, sizeof(DevScalars) * h->nseg, cudaMemcpyDeviceToHost,
+                     h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  if (h->timing) collect_timing(h);
+  for (int m = 0; m < h->nseg; m++) out[m] = sqrt(ssc[m].result);
+  return SPAI_OK;
+}
+
+int spai_batch_get_M(spai_handle h, int m, int64_t* nnz, int32_t* colptr, int32_t* rowind,
+                     double* vals) {
+  if (!h || !nnz) return SPAI_ERR_ARG;
+  const int nh = h->nseg ? h->nseg : 1;
+  if (m < 0 || m >= nh) return SPAI_ERR_ARG;
+  if (!h->nseg) return spai_get_M(h, nnz, colptr, rowind, vals, 0);
+  long long tot = 0;
+  int rc = export_csc(h, &tot);
+  if (rc) return rc;
+  const long long c0 = h->seg_col0[m], nm = h->seg_n[m];
+  std::vector<long long> cp(nm + 1);
+  CK(cudaMemcpyAsync(cp.data(), h->d_ccolptr + c0, sizeof(long long) * (nm + 1),
+                     cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  *nnz = cp[nm] - cp[0];
+  if (!colptr) return SPAI_OK;
+  if (!rowind || !vals) return SPAI_ERR_ARG;
+  CK(cudaMemcpyAsync(rowind, h->d_crow + cp[0], sizeof(int) * (size_t)*nnz, cudaMemcpyDeviceToHost,
+                     h->stream));
+  CK(cudaMemcpyAsync(vals, h->d_cval + cp[0], sizeof(double) * (size_t)*nnz,
+                     cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  for (long long q = 0; q <= nm; q++) colptr[q] = (int32_t)(cp[q] - cp[0]);
+  for (long long e = 0; e < *nnz; e++) rowind[e] -= (int32_t)c0;
   return SPAI_OK;
 }
 

@@ -40,8 +40,10 @@ struct ColCtx {
   int overflow;
   unsigned long long bytes;
   unsigned long long spg;
-  __device__ ColCtx(const PassParams& pp, char* w, int l)
-      : p(pp), ws(w), lane(l), overflow(0), bytes(0), spg(0) {}
+  const DevScalars* sc;  // the coefficients of this column's matrix
+  int seg;               // its segment in batched mode, else -1
+  __device__ ColCtx(const PassParams& pp, char* w, int l, const DevScalars* s, int sg)
+      : p(pp), ws(w), lane(l), overflow(0), bytes(0), spg(0), sc(s), seg(sg) {}
   template <typename T> __device__ T* at(int off) const { return (T*)(ws + off); }
 };
 
@@ -74,8 +76,8 @@ __device__ __forceinline__ int L_lmax(const PassParams& p) { return p.capmax * p
 
 template <typename VC>
 __device__ __forceinline__ int spgemm(const PassParams& p, const HashT& h, int* xr, VC* xv, int L,
-                                      int diag, int* sr, VC* sv, int lane) {
-  if (p.dia) return spgemm_dia(p, h, xr, xv, L, diag, lane);
+                                      int diag, int* sr, VC* sv, int lane, int seg) {
+  if (p.dia) return spgemm_dia(p, h, xr, xv, L, diag, seg, lane);
   sort_rows_small(xr, xv, L, sr, sv, lane);
   return spgemm_ell(p, h, xr, xv, L, diag, lane);
 }
@@ -116,7 +118,7 @@ __device__ void column_work(ColCtx<VS, VC>& c, int j, double* part) {
   int Lm = load_col(c, p.Mrow, p.Mval, off, p.Mlen[j], Mr, Mv);
 
   if (p.kind == kRES) {
-    int cnt = spgemm(p, ha, Mr, Mv, Lm, j, Tr, Tv, lane);
+    int cnt = spgemm(p, ha, Mr, Mv, Lm, j, Tr, Tv, lane, c.seg);
     int LR = table_to_list(ha, cnt, j, Rr, Rv, lane);
     hash_clear(ha, cnt, lane);
     c.spg++;
@@ -127,12 +129,12 @@ __device__ void column_work(ColCtx<VS, VC>& c, int j, double* part) {
   if (p.kind == kMR) {
     if (p.do_update) {
       int Lp = load_col(c, p.Prow, p.Pval, off, p.Plen[j], Pr, Pv);
-      CombAxpy<VC> f{p.sc->alpha};
+      CombAxpy<VC> f{c.sc->alpha};
       int Lt = warp_union(un, Mr, Mv, Lm, Pr, Pv, Lp, Tr, Tv, f, lane);
       Lm = warp_select(Tr, Tv, Lt, cap, Mr, Mv, hist, tie, p.drop, ovf, lane);
       store_col(c, p.Mrow, p.Mval, p.Mlen, j, off, Lm, Mr, Mv);
     }
-    int cnt = spgemm(p, ha, Mr, Mv, Lm, j, Tr, Tv, lane);
+    int cnt = spgemm(p, ha, Mr, Mv, Lm, j, Tr, Tv, lane, c.seg);
     int LR = table_to_list(ha, cnt, j, Rr, Rv, lane);
     hash_clear(ha, cnt, lane);
     c.spg++;
@@ -142,7 +144,7 @@ __device__ void column_work(ColCtx<VS, VC>& c, int j, double* part) {
     }
     int Lp = warp_select(Rr, Rv, LR, cap, Pr, Pv, hist, tie, p.drop, ovf, lane);
     store_col(c, p.Prow, p.Pval, p.Plen, j, off, Lp, Pr, Pv);
-    int cq = spgemm(p, ha, Pr, Pv, Lp, -1, Tr, Tv, lane);  // table holds Q = A P
+    int cq = spgemm(p, ha, Pr, Pv, Lp, -1, Tr, Tv, lane, c.seg);  // table holds Q = A P
     c.spg++;
     lookup_list(Rr, LR, ha, yc, lane);                      // Q at the rows of R
     __syncwarp();
@@ -168,7 +170,7 @@ __device__ void column_work(ColCtx<VS, VC>& c, int j, double* part) {
     int Lp = load_col(c, p.Prow, p.Pval, off, p.Plen[j], Pr, Pv);
     if (p.do_update) {
       int Lz = load_col(c, p.Zrow, p.Zval, off, p.Zlen[j], Zr, Zv);
-      CombLin<VC> fl{p.sc->delta, p.sc->gamma};
+      CombLin<VC> fl{c.sc->delta, c.sc->gamma};
       int Ls = warp_union(un, Zr, Zv, Lz, Pr, Pv, Lp, Sr, Sv, fl, lane);
       Lp = warp_select(Sr, Sv, Ls, cap, Pr, Pv, hist, tie, p.drop, ovf, lane);
       store_col(c, p.Prow, p.Pval, p.Plen, j, off, Lp, Pr, Pv);
@@ -177,7 +179,7 @@ __device__ void column_work(ColCtx<VS, VC>& c, int j, double* part) {
       Lm = warp_select(Tr, Tv, Lt, cap, Mr, Mv, hist, tie, p.drop, ovf, lane);
       store_col(c, p.Mrow, p.Mval, p.Mlen, j, off, Lm, Mr, Mv);
     }
-    int cr = spgemm(p, ha, Mr, Mv, Lm, j, Tr, Tv, lane);
+    int cr = spgemm(p, ha, Mr, Mv, Lm, j, Tr, Tv, lane, c.seg);
     int LR = table_to_list(ha, cr, j, Rr, Rv, lane);  // table A now holds R
     c.spg++;
     if (!p.do_dir) {
@@ -187,7 +189,7 @@ __device__ void column_work(ColCtx<VS, VC>& c, int j, double* part) {
     }
     int Lz = warp_select(Rr, Rv, LR, cap, Zr, Zv, hist, tie, p.drop, ovf, lane);
     store_col(c, p.Zrow, p.Zval, p.Zlen, j, off, Lz, Zr, Zv);
-    int cu = spgemm(p, hb, Zr, Zv, Lz, -1, Tr, Tv, lane);   // table B: U = A Z
+    int cu = spgemm(p, hb, Zr, Zv, Lz, -1, Tr, Tv, lane, c.seg);   // table B: U = A Z
     lookup_table(hb, cu, ha, yc, lane);                     // R at the rows of U
     __syncwarp();
     double t3[3];
@@ -199,7 +201,7 @@ __device__ void column_work(ColCtx<VS, VC>& c, int j, double* part) {
     part[4] = t3[2];
     int LU = table_to_list(hb, cu, -1, Ur, Uv, lane);
     hash_clear(hb, cu, lane);
-    int cv = spgemm(p, hb, Pr, Pv, Lp, -1, Tr, Tv, lane);   // table B: V = A P
+    int cv = spgemm(p, hb, Pr, Pv, Lp, -1, Tr, Tv, lane, c.seg);   // table B: V = A P
     c.spg += 2;
     lookup_list(Ur, LU, hb, yc, lane);                      // V at the rows of U
     lookup_table(hb, cv, ha, yc2, lane);                    // R at the rows of V
@@ -217,11 +219,11 @@ __device__ void column_work(ColCtx<VS, VC>& c, int j, double* part) {
 
   if (p.kind == kCGA) {
     int Lp = load_col(c, p.Prow, p.Pval, off, p.Plen[j], Pr, Pv);
-    CombAxpy<VC> f{p.sc->alpha};
+    CombAxpy<VC> f{c.sc->alpha};
     int Lt = warp_union(un, Mr, Mv, Lm, Pr, Pv, Lp, Tr, Tv, f, lane);
     Lm = warp_select(Tr, Tv, Lt, cap, Mr, Mv, hist, tie, p.drop, ovf, lane);
     store_col(c, p.Mrow, p.Mval, p.Mlen, j, off, Lm, Mr, Mv);
-    int cr = spgemm(p, ha, Mr, Mv, Lm, j, Tr, Tv, lane);
+    int cr = spgemm(p, ha, Mr, Mv, Lm, j, Tr, Tv, lane, c.seg);
     int LR = table_to_list(ha, cr, j, Rr, Rv, lane);
     hash_clear(ha, cr, lane);
     c.spg++;
@@ -232,15 +234,15 @@ __device__ void column_work(ColCtx<VS, VC>& c, int j, double* part) {
   // kCGB
   {
     int Lp = load_col(c, p.Prow, p.Pval, off, p.Plen[j], Pr, Pv);
-    int cr = spgemm(p, ha, Mr, Mv, Lm, j, Tr, Tv, lane);
+    int cr = spgemm(p, ha, Mr, Mv, Lm, j, Tr, Tv, lane, c.seg);
     int LR = table_to_list(ha, cr, j, Rr, Rv, lane);
     hash_clear(ha, cr, lane);
     c.spg++;
-    CombAxpy<VC> f{p.sc->beta};
+    CombAxpy<VC> f{c.sc->beta};
     int Lt = warp_union(un, Rr, Rv, LR, Pr, Pv, Lp, Tr, Tv, f, lane);
     Lp = warp_select(Tr, Tv, Lt, cap, Pr, Pv, hist, tie, p.drop, ovf, lane);
     store_col(c, p.Prow, p.Pval, p.Plen, j, off, Lp, Pr, Pv);
-    int cq = spgemm(p, ha, Pr, Pv, Lp, -1, Tr, Tv, lane);  // table holds Q = A P
+    int cq = spgemm(p, ha, Pr, Pv, Lp, -1, Tr, Tv, lane, c.seg);  // table holds Q = A P
     c.spg++;
     lookup_list(Pr, Lp, ha, yc, lane);                     // Q at the rows of P
     __syncwarp();
@@ -252,9 +254,10 @@ __device__ void column_work(ColCtx<VS, VC>& c, int j, double* part) {
 
 __device__ __forceinline__ bool isfin(double x) { return !isnan(x) && !isinf(x); }
 
-// Step coefficients from the global sums t[0..nq); thread 0 of the last CTA.
-__device__ inline void coefficients(const PassParams& p, const double* t) {
-  DevScalars* sc = p.sc;
+// Step coefficients from the global sums t[0..nq) of one matrix; thread 0 of
+// the last CTA of that matrix.  hist_res / hist_coef point at its histories.
+__device__ inline void coefficients(const PassParams& p, DevScalars* sc, double* hist_res,
+                                    double* hist_coef, const double* t) {
   const int it = p.iter;
   if (p.kind == kRES) {
     sc->result = t[0];
@@ -263,7 +266,7 @@ __device__ inline void coefficients(const PassParams& p, const double* t) {
   if (p.kind == kMR || p.kind == kLOMR) {
     double rr = t[0];
     if (p.do_update) sc->done += 1;
-    if (p.hist_res) p.hist_res[it] = __dsqrt_rn(rr);
+    if (hist_res) hist_res[it] = __dsqrt_rn(rr);
     if (!p.do_dir) return;
     if (rr == 0.0) {
       sc->stop = 1;
@@ -284,9 +287,9 @@ __device__ inline void coefficients(const PassParams& p, const double* t) {
         return;
       }
       sc->alpha = alpha;
-      if (p.hist_coef) {
-        p.hist_coef[2 * it] = alpha;
-        p.hist_coef[2 * it + 1] = 0.0;
+      if (hist_coef) {
+        hist_coef[2 * it] = alpha;
+        hist_coef[2 * it + 1] = 0.0;
       }
     } else {
       double uu = t[1], vv = t[2], uv = t[3], ur = t[4], vr = t[5];
@@ -316,16 +319,16 @@ __device__ inline void coefficients(const PassParams& p, const double* t) {
       }
       sc->delta = delta;
       sc->gamma = gamma;
-      if (p.hist_coef) {
-        p.hist_coef[2 * it] = delta;
-        p.hist_coef[2 * it + 1] = gamma;
+      if (hist_coef) {
+        hist_coef[2 * it] = delta;
+        hist_coef[2 * it + 1] = gamma;
       }
     }
     return;
   }
   if (p.kind == kCGB) {
     double rr = t[0], pq = t[1];
-    if (p.fresh && p.hist_res) p.hist_res[0] = __dsqrt_rn(rr);
+    if (p.fresh && hist_res) hist_res[0] = __dsqrt_rn(rr);
     if (rr == 0.0 || pq == 0.0) {
       sc->stop = 1;
       sc->flags |= kFlagConverged;
@@ -345,10 +348,10 @@ __device__ inline void coefficients(const PassParams& p, const double* t) {
   {
     double rr1 = t[0];
     double beta = __ddiv_rn(rr1, sc->rr);
-    if (p.hist_res) p.hist_res[it + 1] = __dsqrt_rn(rr1);
-    if (p.hist_coef) {
-      p.hist_coef[2 * it] = sc->alpha;
-      p.hist_coef[2 * it + 1] = beta;
+    if (hist_res) hist_res[it + 1] = __dsqrt_rn(rr1);
+    if (hist_coef) {
+      hist_coef[2 * it] = sc->alpha;
+      hist_coef[2 * it + 1] = beta;
     }
     sc->done += 1;
     sc->rr = rr1;
@@ -363,13 +366,15 @@ __device__ inline void coefficients(const PassParams& p, const double* t) {
 template <typename VS, typename VC>
 __global__ void __launch_bounds__(256, 3) colpass_kernel(const PassParams p) {
   extern __shared__ __align__(16) char smem[];
-  if (p.sc->stop) return;
+  const int seg = p.nseg ? p.seg_of_col[(long long)blockIdx.x * p.B] : -1;
+  DevScalars* sc = seg >= 0 ? p.segsc + seg : p.sc;
+  if (sc->stop) return;  // set by an earlier pass for this matrix
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
   const int nq = p.do_dir ? pass_nq(p.kind) : 1;
   double* part = (double*)(smem + p.part_off);  // [nq][B]
   double* red = (double*)(smem + p.red_off);    // reduction scratch (>= 1024 doubles)
-  ColCtx<VS, VC> c(p, smem + warp * p.lay.bytes, lane);
+  ColCtx<VS, VC> c(p, smem + warp * p.lay.bytes, lane, sc, seg);
   {
     HashT h0;
     h0.key = c.template at<int>(p.lay.hk);
@@ -411,7 +416,7 @@ __global__ void __launch_bounds__(256, 3) colpass_kernel(const PassParams p) {
   // CTA tree over the B column partials of each quantity
   for (int q = 0; q < nq; q++) {
     const double* v = part + q * B;
-    double s;
+    double s = 0.0;
     if (B <= 32) {
       if (warp == 0) s = warp_tree32(lane < B ? v[lane] : 0.0);
     } else {
@@ -427,6 +432,36 @@ __global__ void __launch_bounds__(256, 3) colpass_kernel(const PassParams p) {
     if (threadIdx.x == 0) p.bsum[(long long)q * p.nb + blockIdx.x] = s;
   }
   __syncthreads();
+  __shared__ double tot[6];
+  if (seg >= 0) {
+    // batched: the last CTA of this matrix reduces its CTAs' sums (aligned,
+    // so this is the matrix's own pairwise tree) and sets its coefficients
+    if (threadIdx.x == 0) {
+      if (s_ovf) atomicOr(&sc->flags, kFlagCapacity);
+      atomicAdd(&p.sc->bytes, s_bytes);
+      atomicAdd(&p.sc->spgemm_cols, s_spg);
+      __threadfence();
+      unsigned old = atomicAdd(&p.seg_cnt[seg], 1u);
+      s_last1 = (old == (unsigned)(p.seg_npad[seg] / p.B - 1));
+    }
+    __syncthreads();
+    if (!s_last1) return;
+    __threadfence();
+    for (int q = 0; q < nq; q++) {
+      double s = block_tree_global(p.bsum + (long long)q * p.nb + p.seg_col0[seg] / p.B,
+                                   p.seg_npad[seg] / p.B, red, lane, warp);
+      if (threadIdx.x == 0) tot[q] = s;
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+      p.seg_cnt[seg] = 0;
+      coefficients(p, sc, p.hist_res ? p.hist_res + (long long)seg * p.hist_stride : nullptr,
+                   p.hist_coef ? p.hist_coef + (long long)seg * 2 * (p.hist_stride - 1) : nullptr,
+                   tot);
+      __threadfence();
+    }
+    return;
+  }
   // last-arriver tree: groups of kGroup blocks, then all groups
   const int g = blockIdx.x / kGroup;
   if (threadIdx.x == 0) {
@@ -464,7 +499,6 @@ __global__ void __launch_bounds__(256, 3) colpass_kernel(const PassParams p) {
   __syncthreads();
   if (!s_last2) return;
   __threadfence();
-  __shared__ double tot[6];
   for (int q = 0; q < nq; q++) {
     double s = block_tree_global(p.gsum + (long long)q * p.ngroups, p.ngroups, red, lane, warp);
     if (threadIdx.x == 0) tot[q] = s;
@@ -472,7 +506,7 @@ __global__ void __launch_bounds__(256, 3) colpass_kernel(const PassParams p) {
   }
   if (threadIdx.x == 0) {
     *p.cnt2 = 0;
-    coefficients(p, tot);
+    coefficients(p, p.sc, p.hist_res, p.hist_coef, tot);
     __threadfence();
   }
 }

@@ -84,6 +84,17 @@ struct PassParams {
   unsigned* cnt1;        // [ngroups]
   unsigned* cnt2;        // [1]
   int nb, ngroups;
+  // batched mode (nseg > 0): independent matrices laid block-diagonally, each
+  // padded to whole CTAs; every CTA belongs to one matrix (segment)
+  int nseg;
+  const int* seg_of_col;   // [n] segment of each column
+  const int* seg_col0;     // [nseg] first column of each segment
+  const int* seg_npad;     // [nseg] padded size (a multiple of B)
+  DevScalars* segsc;       // [nseg] per-segment scalars
+  const int* seg_D;        // [nseg] diagonal slots of each segment
+  const int* seg_doff;     // [nseg][32] their offsets, ascending
+  unsigned* seg_cnt;       // [nseg] arrival counters
+  int hist_stride;         // per-segment history stride (iters + 1)
   WarpLayout lay;
   int part_off;          // byte offset of the CTA partials [NQ][B]
   int red_off;           // byte offset of CTA reduction scratch

@@ -200,6 +200,24 @@ cudaError_t launch_init_slab(int prec, int n, const long long* off, const double
   return cudaGetLastError();
 }
 
+// per-matrix scalars of a batched handle at the start of a call
+__global__ void k_seg_reset(DevScalars* sc, int nseg, int fresh) {
+  int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= nseg) return;
+  sc[m].stop = 0;
+  sc[m].flags = 0;
+  sc[m].done = 0;
+  if (fresh) {
+    sc[m].beta = 0.0;
+    sc[m].rr = 0.0;
+  }
+}
+
+cudaError_t launch_seg_reset(DevScalars* sc, int nseg, int fresh, cudaStream_t st) {
+  k_seg_reset<<<(nseg + 127) / 128, 128, 0, st>>>(sc, nseg, fresh);
+  return cudaGetLastError();
+}
+
 // ------------------------------------------------------------- scan
 
 // exclusive scan of int32 counts into int32/int64 offsets, 1024 per block

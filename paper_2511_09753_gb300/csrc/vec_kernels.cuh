@@ -39,6 +39,7 @@ struct PcgArgs {
   RedWS ws;
 };
 
+cudaError_t launch_seg_reset(DevScalars* sc, int nseg, int fresh, cudaStream_t st);
 cudaError_t launch_init_slab(int prec, int n, const long long* off, const double* diag, int* Mrow,
                              void* Mval, int* Mlen, int* Plen, int* Zlen, cudaStream_t st);
 cudaError_t launch_exclusive_scan(const int* in, long long* out, int n, long long* tmp,

@@ -506,13 +506,13 @@ __device__ int warp_select(const int* sr, const V* sv, int L, int cap, int* dr, 
 // two lanes touch the same accumulator.
 template <typename VC>
 __device__ int spgemm_dia(const PassParams& p, const HashT& h, const int* xr, const VC* xv, int L,
-                          int diag, int lane) {
+                          int diag, int seg, int lane) {
   const VC* dv = (const VC*)p.dia_val;
   VC* hv = (VC*)h.val;
-  const int D = p.D, Dp = p.Dp;
+  const int D = seg >= 0 ? p.seg_D[seg] : p.D, Dp = p.Dp;
   int cnt = 0;
   for (int s = D - 1; s >= 0; s--) {
-    const int o = p.dia_off[s];
+    const int o = seg >= 0 ? p.seg_doff[seg * 32 + s] : p.dia_off[s];
     for (int base = 0; base < L; base += 32) {
       int i = base + lane;
       bool isnew = false;

@@ -155,6 +155,59 @@ def varcoef_2d_5pt(N: int, sigma: float = 1.5, ell: float = 8.0, seed: int = 0):
     return n, rp, ci, v
 
 
+def varcoef_grid(dims, sigma: float = 1.5, ell: float = 8.0, seed: int = 0):
+    """Variable-coefficient diffusion on a rectangular 2-D (ny, nx) or 3-D
+    (nz, ny, nx) grid, same construction as varcoef_3d_7pt / varcoef_2d_5pt."""
+    dims = tuple(int(d) for d in dims)
+    d = len(dims)
+    kap = np.exp(gaussian_field(tuple(m + 2 for m in dims), sigma, ell, seed))
+    inner = tuple(slice(1, -1) for _ in range(d))
+    c = kap[inner]
+    n = int(np.prod(dims))
+    idx = np.arange(n).reshape(dims)
+    strides = [int(np.prod(dims[a + 1:])) for a in range(d)]
+    nan = np.full(n, np.nan)
+    cols_m, cols_p, diag = [], [], np.zeros(dims)
+    for a in range(d):
+        sl_p = list(inner)
+        sl_m = list(inner)
+        sl_p[a] = slice(2, None)
+        sl_m[a] = slice(None, -2)
+        ep = _harm(c, kap[tuple(sl_p)])
+        em = _harm(c, kap[tuple(sl_m)])
+        diag = diag + ep + em
+        coord = (idx // strides[a]) % dims[a]
+        cols_m.append(np.where(coord.ravel() > 0, -em.ravel(), nan))
+        cols_p.append(np.where(coord.ravel() < dims[a] - 1, -ep.ravel(), nan))
+    offsets = [-strides[a] for a in range(d)] + [0] + [strides[a] for a in reversed(range(d))]
+    cols = cols_m + [diag.ravel()] + list(reversed(cols_p))
+    order = np.argsort(offsets)
+    rp, ci, v = _assemble(n, [offsets[k] for k in order], [cols[k] for k in order])
+    return n, rp, ci, v
+
+
+def batch_uneven(count: int = 64, nmin: float = 1e3, nmax: float = 6.4e4, seed: int = 0,
+                 sigma: float = 1.5, ell: float = 8.0):
+    """Batch of variable-coefficient operators with n log-uniform in
+    [nmin, nmax] (drawn from default_rng(seed)), alternating 2-D 5-point and
+    3-D 7-point grids, matrix k using field seed 1000 + k."""
+    rng = np.random.default_rng(seed)
+    targets = np.exp(rng.uniform(math.log(nmin), math.log(nmax), count))
+    mats = []
+    for k, t in enumerate(targets):
+        if k % 2 == 0:
+            nx = max(2, int(round(math.sqrt(t))))
+            ny = max(2, int(round(t / nx)))
+            dims = (ny, nx)
+        else:
+            nx = max(2, int(round(t ** (1.0 / 3.0))))
+            ny = nx
+            nz = max(2, int(round(t / (nx * ny))))
+            dims = (nz, ny, nx)
+        mats.append(varcoef_grid(dims, sigma, ell, 1000 + k))
+    return mats
+
+
 def aniso_2d_9pt(N: int, eps: float = 1e-3, theta: float = math.pi / 6):
     cs, sn = math.cos(theta), math.sin(theta)
     a = cs * cs + eps * sn * sn

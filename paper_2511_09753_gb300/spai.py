@@ -28,7 +28,9 @@ EXPORTED = ["spai_validate_csr", "spai_status_string", "spai_create", "spai_dest
             "spai_set_stream", "spai_run", "spai_mr", "spai_lomr", "spai_cg",
             "spai_residual_norm", "spai_get_nnz", "spai_get_M", "spai_set_M", "spai_apply",
             "pcg_solve", "spai_save_state", "spai_load_state", "spai_set_timing",
-            "spai_get_stats", "spai_true_residual_noalloc"]
+            "spai_get_stats", "spai_true_residual_noalloc", "spai_create_batched",
+            "spai_batch_info", "spai_batch_history", "spai_batch_residual_norms",
+            "spai_batch_get_M"]
 
 
 class SpaiError(RuntimeError):
@@ -86,6 +88,12 @@ def load():
         "spai_set_timing": (i32, [vp, i32]),
         "spai_get_stats": (i32, [vp, C.POINTER(_Stats)]),
         "spai_true_residual_noalloc": (i32, [i64, vp, vp, vp, vp, vp, vp, vp]),
+        "spai_create_batched": (i32, [C.POINTER(vp), i32, vp, vp, vp, vp, vp, C.POINTER(_Opts),
+                                      vp]),
+        "spai_batch_info": (i32, [vp, C.POINTER(i32), vp]),
+        "spai_batch_history": (i32, [vp, vp, vp, vp]),
+        "spai_batch_residual_norms": (i32, [vp, vp]),
+        "spai_batch_get_M": (i32, [vp, i32, C.POINTER(i64), vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -281,3 +289,73 @@ class Spai:
         s = _Stats()
         self._check(self.lib.spai_get_stats(self.h, C.byref(s)), "spai_get_stats")
         return {k: getattr(s, k) for k, _ in _Stats._fields_}
+
+
+class SpaiBatch(Spai):
+    """Many SPD matrices solved together (block-diagonal, per-matrix coefficients).
+
+    mats: list of (n, rowptr, colind, vals) host CSR triples.
+    """
+
+    def __init__(self, mats, prec="fp64", cap_factor=2.0, stream=None):
+        self.lib = load()
+        k = len(mats)
+        self.nmat = k
+        ns = np.array([m[0] for m in mats], dtype=np.int64)
+        arrs = [(_np(m[1], np.int32), _np(m[2], np.int32), _np(m[3], np.float64)) for m in mats]
+        nnz = np.array([len(a[2]) for a in arrs], dtype=np.int64)
+        rps = (C.c_void_p * k)(*[a[0].ctypes.data for a in arrs])
+        cis = (C.c_void_p * k)(*[a[1].ctypes.data for a in arrs])
+        vas = (C.c_void_p * k)(*[a[2].ctypes.data for a in arrs])
+        opts = _Opts(SPAI_MIXED if prec == "mixed" else SPAI_FP64, float(cap_factor))
+        h = C.c_void_p()
+        rc = self.lib.spai_create_batched(C.byref(h), k, ns.ctypes.data, nnz.ctypes.data, rps, cis,
+                                          vas, C.byref(opts), _stream_ptr(stream))
+        if rc != 0:
+            raise SpaiError(rc, "spai_create_batched")
+        self.h = h
+        self.prec = prec
+        self.ns = ns
+        self.n = int(self._total_n())
+
+    def _total_n(self):
+        # padded block-diagonal size: each matrix rounded up to 256
+        return int(sum((int(x) + 255) // 256 * 256 for x in self.ns))
+
+    def run(self, method, iters, drop=True):
+        r = super().run(method, iters, drop)
+        res = np.full(self.nmat * (iters + 1), np.nan)
+        done = np.zeros(self.nmat, dtype=np.int32)
+        flags = np.zeros(self.nmat, dtype=np.int32)
+        self._check(self.lib.spai_batch_history(self.h, res.ctypes.data, done.ctypes.data,
+                                                flags.ctypes.data), "spai_batch_history")
+        r["resnorm_each"] = res.reshape(self.nmat, iters + 1)
+        r["done_each"] = done
+        r["flags_each"] = flags
+        return r
+
+    def batch_info(self):
+        """Sizes of the matrices of the batch (without padding)."""
+        nm = C.c_int()
+        ns = np.zeros(self.nmat, dtype=np.int64)
+        self._check(self.lib.spai_batch_info(self.h, C.byref(nm), ns.ctypes.data),
+                    "spai_batch_info")
+        return [int(x) for x in ns[:nm.value]]
+
+    def residual_norms(self):
+        out = np.zeros(self.nmat)
+        self._check(self.lib.spai_batch_residual_norms(self.h, out.ctypes.data),
+                    "spai_batch_residual_norms")
+        return out
+
+    def get_M_of(self, m):
+        nnz = C.c_int64()
+        self._check(self.lib.spai_batch_get_M(self.h, int(m), C.byref(nnz), None, None, None),
+                    "spai_batch_get_M")
+        n = int(self.ns[m])
+        cp = np.zeros(n + 1, dtype=np.int32)
+        ri = np.zeros(max(nnz.value, 1), dtype=np.int32)
+        va = np.zeros(max(nnz.value, 1), dtype=np.float64)
+        self._check(self.lib.spai_batch_get_M(self.h, int(m), C.byref(nnz), cp.ctypes.data,
+                                              ri.ctypes.data, va.ctypes.data), "spai_batch_get_M")
+        return cp, ri[:nnz.value], va[:nnz.value]

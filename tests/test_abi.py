@@ -79,3 +79,20 @@ def test_handle_calls_reject_null():
     out = ctypes.c_void_p()
     opts = spai._Opts(0, 2.0)
     assert lib.spai_create(ctypes.byref(out), 0, 1, None, None, None, 0, ctypes.byref(opts), None) == -1
+
+
+def test_create_batched_rejects_bad_input_before_any_device_call():
+    spai = _lib()
+    good = I.laplacian_2d_5pt(8)
+    with pytest.raises(spai.SpaiError) as e:
+        spai.SpaiBatch([], prec="fp64")
+    assert e.value.code == -1
+    n, rp, ci, v = I.laplacian_2d_5pt(8)
+    v = v.copy()
+    v[1] += 0.5  # breaks symmetry of one off-diagonal pair
+    with pytest.raises(spai.SpaiError) as e:
+        spai.SpaiBatch([good, (n, rp, ci, v)], prec="fp64")
+    assert e.value.code == -4
+    with pytest.raises(spai.SpaiError) as e:
+        spai.SpaiBatch([good], prec="fp64", cap_factor=0.0)
+    assert e.value.code == -1
