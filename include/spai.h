@@ -208,6 +208,27 @@ int spai_apply(spai_handle h, const double *x, double *y, int nrhs, int64_t ld);
 int pcg_solve(spai_handle h, const double *b, double *x, int nrhs, double rtol, int maxit,
               int precond, int on_device, int *iters, double *relres);
 
+/* Block PCG (Sec. 7's assessment applied to many right-hand sides; the paper
+ * solves one at a time): nrhs (1..32) independent PCG recurrences per matrix
+ * of the handle, each one exactly the recurrence pcg_solve runs on that
+ * matrix and vector (same stopping rule, same preconditioner choices), all
+ * sharing each product with A and with M.  A single-matrix handle counts as
+ * one matrix.
+ * b, x: host (on_device = 0) or device (on_device = 1) FP64 arrays holding,
+ * matrix after matrix, that matrix's nrhs vectors one after another:
+ * element i of vector j of matrix m is at off_m + j n_m + i, where
+ * off_m = nrhs (n_0 + ... + n_{m-1}) and n_m is the matrix's own size.
+ * iters, status (host, [nmat * nrhs], index m nrhs + j): A p products done and
+ * SPAI_OK / SPAI_PCG_MAXIT / SPAI_PCG_BREAKDOWN per recurrence; relres (host,
+ * may be NULL) = ||b - A x||_2 / ||b||_2 per recurrence.  Returns
+ * SPAI_PCG_BREAKDOWN if any recurrence broke down, else SPAI_PCG_MAXIT if any
+ * hit maxit, else SPAI_OK; or an error (SPAI_ERR_UNSUPPORTED for a matrix of
+ * more than 4,194,304 rows).  The iterations are replayed from a captured
+ * CUDA graph of 8 iterations on the handle's stream (launched directly if
+ * that stream cannot be captured). */
+int pcg_solve_block(spai_handle h, int nrhs, const double *b, double *x, double rtol, int maxit,
+                    int precond, int on_device, int *iters, int *status, double *relres);
+
 /* Checkpoint of the iteration state (M, directions, scalars, method and
  * iteration index).  Two-call: with buf == NULL only *bytes is set. */
 int spai_save_state(spai_handle h, void *buf, size_t *bytes);

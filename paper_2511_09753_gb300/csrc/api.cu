@@ -18,6 +18,7 @@
 #include "spai.h"
 #include "common.cuh"
 #include "vec_kernels.cuh"
+#include "bpcg.cuh"
 
 using namespace spai;
 
@@ -117,6 +118,20 @@ struct spai_ctx {
   PcgScalars* d_ps = nullptr;
   double *d_vbsum = nullptr, *d_vgsum = nullptr;
   unsigned *d_vcnt1 = nullptr, *d_vcnt2 = nullptr;
+  // block PCG: vectors [n][32], per (matrix, rhs) state, segment maps
+  double *d_bb = nullptr, *d_bx = nullptr, *d_br = nullptr, *d_bz = nullptr, *d_bp = nullptr,
+         *d_bq = nullptr, *d_bstage = nullptr;
+  long long bstage_cap = 0;
+  double* d_bstate = nullptr;  // rho, alpha, beta, bn, tres: 5 x [nseg][32]
+  int* d_bistate = nullptr;    // k, done, status: 3 x [nseg][32]
+  int *d_bseg_live = nullptr, *d_blive = nullptr;
+  double* d_bbsum = nullptr;
+  unsigned* d_bcnt = nullptr;
+  int *d_bseg_of_cta = nullptr, *d_bseg_cta0 = nullptr, *d_bseg_ncta = nullptr,
+      *d_bseg_row0 = nullptr, *d_bseg_n = nullptr;
+  long long* d_bseg_boff = nullptr;
+  cudaGraphExec_t bp_graph = nullptr;
+  unsigned char bp_graph_key[sizeof(spai::BpcgArgs)];
   // stats
   long long colpass_launches = 0, pcg_launches = 0, other_launches = 0;
   unsigned long long a_bytes_total = 0;
@@ -459,6 +474,27 @@ void free_all(spai_ctx* h) {
   dfree(h->d_vgsum);
   dfree(h->d_vcnt1);
   dfree(h->d_vcnt2);
+  dfree(h->d_bb);
+  dfree(h->d_bx);
+  dfree(h->d_br);
+  dfree(h->d_bz);
+  dfree(h->d_bp);
+  dfree(h->d_bq);
+  dfree(h->d_bstage);
+  dfree(h->d_bstate);
+  dfree(h->d_bistate);
+  dfree(h->d_bseg_live);
+  dfree(h->d_blive);
+  dfree(h->d_bbsum);
+  dfree(h->d_bcnt);
+  dfree(h->d_bseg_of_cta);
+  dfree(h->d_bseg_cta0);
+  dfree(h->d_bseg_ncta);
+  dfree(h->d_bseg_row0);
+  dfree(h->d_bseg_n);
+  dfree(h->d_bseg_boff);
+  if (h->bp_graph) cudaGraphExecDestroy(h->bp_graph);
+  h->bp_graph = nullptr;
   for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
   h->ev.clear();
 }
@@ -1459,6 +1495,246 @@ int pcg_solve(spai_handle h, const double* b, double* x, int nrhs, double rtol, 
   if (ps.status == 1) return SPAI_PCG_MAXIT;
   if (ps.status == 2) return SPAI_PCG_BREAKDOWN;
   return SPAI_OK;
+}
+
+// ------------------------------------------------------------ block PCG
+
+static void free_bpcg(spai_ctx* h) {
+  dfree(h->d_bb);
+  dfree(h->d_bx);
+  dfree(h->d_br);
+  dfree(h->d_bz);
+  dfree(h->d_bp);
+  dfree(h->d_bq);
+  dfree(h->d_bstate);
+  dfree(h->d_bistate);
+  dfree(h->d_bseg_live);
+  dfree(h->d_blive);
+  dfree(h->d_bbsum);
+  dfree(h->d_bcnt);
+  dfree(h->d_bseg_of_cta);
+  dfree(h->d_bseg_cta0);
+  dfree(h->d_bseg_ncta);
+  dfree(h->d_bseg_row0);
+  dfree(h->d_bseg_n);
+  dfree(h->d_bseg_boff);
+}
+
+// Block vectors [n][32], per-(matrix, rhs) state and the segment maps, on
+// first use.  A single-matrix handle is one segment of ceil(n / 256) CTAs.
+static int ensure_bpcg(spai_ctx* h) {
+  if (h->d_bb) return SPAI_OK;
+  const long long n = h->n;
+  const int nseg = std::max(h->nseg, 1);
+  const int ncta = (int)((n + kBpRows - 1) / kBpRows);
+  std::vector<int> soc(ncta, 0), c0(nseg), nc(nseg), r0(nseg), nn(nseg);
+  if (h->nseg) {
+    for (int m = 0; m < nseg; m++) {
+      c0[m] = (int)(h->seg_col0[m] / kBpRows);
+      nc[m] = (int)(h->seg_npad[m] / kBpRows);
+      r0[m] = (int)h->seg_col0[m];
+      nn[m] = (int)h->seg_n[m];
+      for (int c = 0; c < nc[m]; c++) soc[c0[m] + c] = m;
+    }
+  } else {
+    c0[0] = 0;
+    nc[0] = ncta;
+    r0[0] = 0;
+    nn[0] = (int)n;
+  }
+  // the last-arriving CTA sums at most 8 x 2048 CTA partials per segment
+  for (int m = 0; m < nseg; m++)
+    if (nc[m] > 16384) return SPAI_ERR_UNSUPPORTED;
+  const size_t V = (size_t)n * kBpLd, S = (size_t)nseg * kBpLd;
+  int rc = SPAI_OK;
+  rc = rc ? rc : dalloc(&h->d_bb, V);
+  rc = rc ? rc : dalloc(&h->d_bx, V);
+  rc = rc ? rc : dalloc(&h->d_br, V);
+  rc = rc ? rc : dalloc(&h->d_bz, V);
+  rc = rc ? rc : dalloc(&h->d_bp, V);
+  rc = rc ? rc : dalloc(&h->d_bq, V);
+  rc = rc ? rc : dalloc(&h->d_bstate, 5 * S);
+  rc = rc ? rc : dalloc(&h->d_bistate, 3 * S);
+  rc = rc ? rc : dalloc(&h->d_bseg_live, nseg);
+  rc = rc ? rc : dalloc(&h->d_blive, 1);
+  rc = rc ? rc : dalloc(&h->d_bbsum, (size_t)ncta * kBpLd);
+  rc = rc ? rc : dalloc(&h->d_bcnt, nseg);
+  rc = rc ? rc : dalloc(&h->d_bseg_of_cta, ncta);
+  rc = rc ? rc : dalloc(&h->d_bseg_cta0, nseg);
+  rc = rc ? rc : dalloc(&h->d_bseg_ncta, nseg);
+  rc = rc ? rc : dalloc(&h->d_bseg_row0, nseg);
+  rc = rc ? rc : dalloc(&h->d_bseg_n, nseg);
+  rc = rc ? rc : dalloc(&h->d_bseg_boff, nseg);
+  if (rc) {
+    free_bpcg(h);
+    return rc;
+  }
+  cudaStream_t st = h->stream;
+  bool ok = true;
+  ok &= cudaMemcpyAsync(h->d_bseg_of_cta, soc.data(), sizeof(int) * ncta, cudaMemcpyHostToDevice,
+                        st) == cudaSuccess;
+  ok &= cudaMemcpyAsync(h->d_bseg_cta0, c0.data(), sizeof(int) * nseg, cudaMemcpyHostToDevice,
+                        st) == cudaSuccess;
+  ok &= cudaMemcpyAsync(h->d_bseg_ncta, nc.data(), sizeof(int) * nseg, cudaMemcpyHostToDevice,
+                        st) == cudaSuccess;
+  ok &= cudaMemcpyAsync(h->d_bseg_row0, r0.data(), sizeof(int) * nseg, cudaMemcpyHostToDevice,
+                        st) == cudaSuccess;
+  ok &= cudaMemcpyAsync(h->d_bseg_n, nn.data(), sizeof(int) * nseg, cudaMemcpyHostToDevice,
+                        st) == cudaSuccess;
+  ok &= cudaStreamSynchronize(st) == cudaSuccess;
+  if (!ok) {
+    (void)cudaGetLastError();
+    free_bpcg(h);
+    return SPAI_ERR_CUDA;
+  }
+  return SPAI_OK;
+}
+
+int pcg_solve_block(spai_handle h, int nrhs, const double* b, double* x, double rtol, int maxit,
+                    int precond, int on_device, int* iters, int* status, double* relres) {
+  if (!h || !b || !x || !iters || !status || nrhs < 1 || nrhs > kBpLd || maxit < 0 ||
+      !(rtol >= 0.0))
+    return SPAI_ERR_ARG;
+  if (precond < SPAI_PREC_NONE || precond > SPAI_PREC_SPAI_SYM) return SPAI_ERR_ARG;
+  int rc = ensure_bpcg(h);
+  if (rc) return rc;
+  if (precond == SPAI_PREC_SPAI || precond == SPAI_PREC_SPAI_SYM) {
+    rc = ensure_rows(h, precond == SPAI_PREC_SPAI_SYM);
+    if (rc) return rc;
+  }
+  const int nseg = std::max(h->nseg, 1);
+  std::vector<long long> boff(nseg);
+  long long tot = 0;
+  for (int m = 0; m < nseg; m++) {
+    boff[m] = tot;
+    tot += (long long)nrhs * (h->nseg ? h->seg_n[m] : h->n);
+  }
+  cudaStream_t st = h->stream;
+  CK(cudaMemcpyAsync(h->d_bseg_boff, boff.data(), sizeof(long long) * nseg, cudaMemcpyHostToDevice,
+                     st));
+  const double* ub = b;
+  double* ux = x;
+  if (!on_device) {
+    if (tot > h->bstage_cap) {
+      dfree(h->d_bstage);
+      h->bstage_cap = 0;
+      rc = dalloc(&h->d_bstage, (size_t)tot);
+      if (rc) return rc;
+      h->bstage_cap = tot;
+    }
+    CK(cudaMemcpyAsync(h->d_bstage, b, sizeof(double) * tot, cudaMemcpyHostToDevice, st));
+    ub = h->d_bstage;
+    ux = h->d_bstage;  // reused for the result once b is gathered
+  }
+  const int n = h->n;
+  CK(launch_bp_gather(ub, h->d_bb, n, nrhs, h->d_bseg_of_cta, h->d_bseg_row0, h->d_bseg_n,
+                      h->d_bseg_boff, st));
+  BpcgArgs a;
+  memset(&a, 0, sizeof(a));
+  a.n = n;
+  a.R = nrhs;
+  a.W = h->W;
+  a.ell_col = h->d_ell_col;
+  a.ell_val = h->d_ell64;
+  a.diag = h->d_diag;
+  a.precond = precond;
+  if (precond == SPAI_PREC_SPAI) {
+    a.mrp = h->d_mrp;
+    a.mci = h->d_mci;
+    a.mv = h->d_mv;
+  } else if (precond == SPAI_PREC_SPAI_SYM) {
+    a.mrp = h->d_srp;
+    a.mci = h->d_sci;
+    a.mv = h->d_sv;
+  }
+  a.rtol = rtol;
+  a.maxit = maxit;
+  a.b = h->d_bb;
+  a.x = h->d_bx;
+  a.r = h->d_br;
+  a.z = h->d_bz;
+  a.p = h->d_bp;
+  a.q = h->d_bq;
+  a.seg_of_cta = h->d_bseg_of_cta;
+  a.seg_cta0 = h->d_bseg_cta0;
+  a.seg_ncta = h->d_bseg_ncta;
+  const size_t S = (size_t)nseg * kBpLd;
+  a.rho = h->d_bstate;
+  a.alpha = h->d_bstate + S;
+  a.beta = h->d_bstate + 2 * S;
+  a.bn = h->d_bstate + 3 * S;
+  a.tres = h->d_bstate + 4 * S;
+  a.k = h->d_bistate;
+  a.done = h->d_bistate + S;
+  a.status = h->d_bistate + 2 * S;
+  a.seg_live = h->d_bseg_live;
+  a.live = h->d_blive;
+  a.bsum = h->d_bbsum;
+  a.cnt = h->d_bcnt;
+  CK(launch_bp_setup(a, nseg, st));
+  CK(launch_bp_init(a, st));
+  h->other_launches += 2;
+  h->pcg_launches += 3;
+  // the iterations run as replays of a captured graph of `chunk` iterations;
+  // the host polls the number of running recurrences between replays
+  const int chunk = 8;
+  if (!h->bp_graph || memcmp(h->bp_graph_key, &a, sizeof(a)) != 0) {
+    if (h->bp_graph) cudaGraphExecDestroy(h->bp_graph);
+    h->bp_graph = nullptr;
+    cudaGraph_t g = nullptr;
+    if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+      cudaError_t e = cudaSuccess;
+      for (int c = 0; c < chunk && e == cudaSuccess; c++) e = launch_bp_iter(a, st);
+      cudaError_t e2 = cudaStreamEndCapture(st, &g);
+      if (e == cudaSuccess && e2 == cudaSuccess && g)
+        if (cudaGraphInstantiate(&h->bp_graph, g, 0) != cudaSuccess) h->bp_graph = nullptr;
+      if (g) cudaGraphDestroy(g);
+    }
+    (void)cudaGetLastError();
+    if (h->bp_graph) memcpy(h->bp_graph_key, &a, sizeof(a));
+  }
+  const int reps = maxit / chunk + 2;
+  int live = 0;
+  for (int rep = 0; rep < reps; rep++) {
+    if (h->bp_graph) {
+      CK(cudaGraphLaunch(h->bp_graph, st));
+    } else {
+      for (int c = 0; c < chunk; c++) CK(launch_bp_iter(a, st));
+    }
+    h->pcg_launches += 4 * chunk;
+    CK(cudaMemcpyAsync(&live, h->d_blive, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (live == 0) break;
+  }
+  CK(launch_bp_tres(a, st));
+  h->pcg_launches += 1;
+  CK(launch_bp_scatter(h->d_bx, ux, n, nrhs, h->d_bseg_of_cta, h->d_bseg_row0, h->d_bseg_n,
+                       h->d_bseg_boff, st));
+  h->other_launches += 2;
+  if (!on_device)
+    CK(cudaMemcpyAsync(x, h->d_bstage, sizeof(double) * tot, cudaMemcpyDeviceToHost, st));
+  std::vector<double> dst(5 * S);
+  std::vector<int> ist(3 * S);
+  CK(cudaMemcpyAsync(dst.data(), h->d_bstate, sizeof(double) * 5 * S, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(ist.data(), h->d_bistate, sizeof(int) * 3 * S, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (live != 0) return SPAI_ERR_STATE;  // cannot happen: every recurrence stops by maxit
+  bool brk = false, lim = false;
+  for (int m = 0; m < nseg; m++)
+    for (int j = 0; j < nrhs; j++) {
+      const size_t s = (size_t)m * kBpLd + j;
+      const int o = m * nrhs + j;
+      iters[o] = ist[s];
+      const int code = ist[2 * S + s];
+      status[o] = code == 0 ? SPAI_OK : code == 1 ? SPAI_PCG_MAXIT : SPAI_PCG_BREAKDOWN;
+      brk |= code == 2;
+      lim |= code == 1;
+      if (relres) {
+        const double bn = dst[3 * S + s];
+        relres[o] = bn > 0 ? sqrt(dst[4 * S + s]) / bn : 0.0;
+      }
+    }
+  return brk ? SPAI_PCG_BREAKDOWN : lim ? SPAI_PCG_MAXIT : SPAI_OK;
 }
 
 // ------------------------------------------------------------ checkpoint

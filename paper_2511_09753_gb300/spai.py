@@ -30,7 +30,7 @@ EXPORTED = ["spai_validate_csr", "spai_status_string", "spai_create", "spai_dest
             "pcg_solve", "spai_save_state", "spai_load_state", "spai_set_timing",
             "spai_get_stats", "spai_true_residual_noalloc", "spai_create_batched",
             "spai_batch_info", "spai_batch_history", "spai_batch_residual_norms",
-            "spai_batch_get_M"]
+            "spai_batch_get_M", "pcg_solve_block"]
 
 
 class SpaiError(RuntimeError):
@@ -83,6 +83,7 @@ def load():
         "spai_set_M": (i32, [vp, vp, vp, vp, i32]),
         "spai_apply": (i32, [vp, vp, vp, i32, i64]),
         "pcg_solve": (i32, [vp, vp, vp, i32, dbl, i32, i32, i32, C.POINTER(i32), C.POINTER(dbl)]),
+        "pcg_solve_block": (i32, [vp, i32, vp, vp, dbl, i32, i32, i32, vp, vp, vp]),
         "spai_save_state": (i32, [vp, vp, C.POINTER(C.c_size_t)]),
         "spai_load_state": (i32, [vp, vp, C.c_size_t]),
         "spai_set_timing": (i32, [vp, i32]),
@@ -271,6 +272,47 @@ class Spai:
         self._check(rc, "pcg_solve")
         return dict(status=rc, iters=it.value, relres=rr.value, x=x)
 
+    def _sizes(self):
+        return [int(self.n)]
+
+    def pcg_block(self, B, rtol=1e-8, maxit=10000, precond=PREC_SPAI_SYM, nrhs=None, x=None):
+        """Block PCG: up to 32 independent recurrences per matrix of the handle.
+
+        B: a list with one (nrhs, n_m) host array per matrix, or one flat FP64
+        CUDA tensor in the library layout (matrix after matrix, vector after
+        vector; give nrhs).  Returns dict(status, iters, statuses, relres, x),
+        the per-recurrence arrays shaped (nmat, nrhs); x in the form of B.
+        """
+        sizes = self._sizes()
+        dev = hasattr(B, "data_ptr")
+        if dev:
+            R = int(nrhs)
+            if x is None:
+                import torch
+                x = torch.empty_like(B)
+            pb, px = B.data_ptr(), x.data_ptr()
+        else:
+            R = int(np.asarray(B[0]).shape[0])
+            flat = np.concatenate([_np(np.asarray(b).reshape(R, n), np.float64).ravel()
+                                   for b, n in zip(B, sizes)])
+            xf = np.zeros_like(flat)
+            pb, px = flat.ctypes.data, xf.ctypes.data
+        k = len(sizes)
+        it = np.zeros(k * R, dtype=np.int32)
+        st = np.zeros(k * R, dtype=np.int32)
+        rr = np.zeros(k * R)
+        rc = self.lib.pcg_solve_block(self.h, R, pb, px, float(rtol), int(maxit), int(precond),
+                                      1 if dev else 0, it.ctypes.data, st.ctypes.data,
+                                      rr.ctypes.data)
+        self._check(rc, "pcg_solve_block")
+        if not dev:
+            x, o = [], 0
+            for n in sizes:
+                x.append(xf[o:o + R * n].reshape(R, n))
+                o += R * n
+        return dict(status=rc, iters=it.reshape(k, R), statuses=st.reshape(k, R),
+                    relres=rr.reshape(k, R), x=x)
+
     def save_state(self) -> bytes:
         n = C.c_size_t()
         self._check(self.lib.spai_save_state(self.h, None, C.byref(n)), "spai_save_state")
@@ -333,6 +375,9 @@ class SpaiBatch(Spai):
         r["done_each"] = done
         r["flags_each"] = flags
         return r
+
+    def _sizes(self):
+        return [int(x) for x in self.ns]
 
     def batch_info(self):
         """Sizes of the matrices of the batch (without padding)."""
