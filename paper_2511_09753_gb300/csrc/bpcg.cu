@@ -27,22 +27,23 @@ namespace {
 
 __device__ __forceinline__ bool bp_finite(double x) { return !isnan(x) && !isinf(x); }
 
-// Pairwise sum over the 32 rows of a warp, row t's term from f(t): groups
-// of four rows ((f0 + f1) + (f2 + f3)), then a three-level binary counter
-// over the eight groups held in named registers.
-template <typename F>
-__device__ __forceinline__ double rows32(F f) {
+// Pairwise sum over the 32 rows of a warp.  g(t, o) computes rows t .. t+3
+// together (so their loads are in flight at once) and leaves their terms in
+// o[0..3]; each group gives ((o0 + o1) + (o2 + o3)), and a three-level binary
+// counter in named registers combines the eight groups.
+template <typename G>
+__device__ __forceinline__ double rows32(G g) {
   double s0 = 0.0, s1 = 0.0, s2 = 0.0, tot = 0.0;
 #pragma unroll 1
-  for (int g = 0; g < 8; g++) {
-    const int t = 4 * g;
-    const double f0 = f(t), f1 = f(t + 1), f2 = f(t + 2), f3 = f(t + 3);
-    double v = __dadd_rn(__dadd_rn(f0, f1), __dadd_rn(f2, f3));
-    if (g & 1) {
+  for (int k = 0; k < 8; k++) {
+    double o[4];
+    g(4 * k, o);
+    double v = __dadd_rn(__dadd_rn(o[0], o[1]), __dadd_rn(o[2], o[3]));
+    if (k & 1) {
       v = __dadd_rn(s0, v);
-      if (g & 2) {
+      if (k & 2) {
         v = __dadd_rn(s1, v);
-        if (g & 4)
+        if (k & 4)
           tot = __dadd_rn(s2, v);
         else
           s2 = v;
@@ -129,50 +130,136 @@ __device__ __forceinline__ void bp_retire(const BpcgArgs& a, int sl, int status)
   atomicSub(a.live, 1);
 }
 
-// (A v)_i for right-hand side lane: A's row from the ELL layout, entries
-// broadcast with shuffles (all lanes take part; act selects the lanes whose
-// product is formed)
-__device__ __forceinline__ double a_row(const BpcgArgs& a, int i, const double* v, int lane,
-                                        bool act) {
-  double acc = 0.0;
-  for (int t0 = 0; t0 < a.W; t0 += 32) {
-    int c = -1;
-    double av = 0.0;
-    if (t0 + lane < a.W) {
-      c = a.ell_col[(long long)i * a.W + t0 + lane];
-      av = a.ell_val[(long long)i * a.W + t0 + lane];
-    }
-    const int m = min(32, a.W - t0);
-    for (int t = 0; t < m; t++) {
-      const int cc = __shfl_sync(kFull, c, t);
-      const double vv = __shfl_sync(kFull, av, t);
-      if (cc < 0) break;  // padding sits at the end of a row
-      if (act) acc = __fma_rn(vv, v[(long long)cc * kBpLd + lane], acc);
-    }
+// Rows of A with at most 8 entries are handled four at a time: lane 8r + e
+// holds entry e of row i0 + r (column -1 where the row has fewer), loaded in
+// one coalesced access; AGroup keeps the entries of the current group and
+// prefetches those of the next while the current group's operands are read.
+struct AGroup {
+  int c, cn;
+  double v, vn;
+};
+
+__device__ __forceinline__ void a_group_load(const BpcgArgs& a, long long i0, int lane, int& c,
+                                             double& v) {
+  const long long i = i0 + (lane >> 3);
+  const int e = lane & 7;
+  c = -1;
+  v = 0.0;
+  if (i < a.n && e < a.W) {
+    c = __ldg(a.ell_col + i * a.W + e);
+    v = __ldg(a.ell_val + i * a.W + e);
   }
-  return acc;
 }
 
-// (M v)_i over the CSR rows of the preconditioner
-__device__ __forceinline__ double m_row(const BpcgArgs& a, int i, const double* v, int lane,
-                                        bool act) {
-  const long long e0 = a.mrp[i], e1 = a.mrp[i + 1];
-  double acc = 0.0;
-  for (long long eb = e0; eb < e1; eb += 32) {
-    int c = 0;
-    double mv = 0.0;
-    if (eb + lane < e1) {
-      c = a.mci[eb + lane];
-      mv = a.mv[eb + lane];
-    }
-    const int m = (int)min(32LL, e1 - eb);
-    for (int t = 0; t < m; t++) {
-      const int cc = __shfl_sync(kFull, c, t);
-      const double vv = __shfl_sync(kFull, mv, t);
-      if (act) acc = __fma_rn(vv, v[(long long)cc * kBpLd + lane], acc);
-    }
+// (A v)_i, i = i0 .. i0+3, for right-hand side lane into y[0..3], and
+// d[r] = v_i (the operand of the diagonal entry) for the inner-product term.
+// Every operand of the four rows is fetched before the fma chains run (32
+// gathers in flight per warp); padding (column -1) ends a row.
+__device__ __forceinline__ void a_rows4_small(const BpcgArgs& a, AGroup& g, long long i0,
+                                              bool more, const double* v, int lane, bool act,
+                                              double* y, double* d) {
+  const int c = g.cn;
+  const double av = g.vn;
+  if (more) a_group_load(a, i0 + 4, lane, g.cn, g.vn);
+  double pv[32];
+#pragma unroll
+  for (int s = 0; s < 32; s++) {
+    const int cc = __shfl_sync(kFull, c, s);
+    pv[s] = (act && cc >= 0) ? __ldg(v + (long long)cc * kBpLd + lane) : 0.0;
   }
-  return acc;
+#pragma unroll
+  for (int r = 0; r < 4; r++) {
+    double acc = 0.0, dd = 0.0;
+#pragma unroll
+    for (int e = 0; e < 8; e++) {
+      const int cc = __shfl_sync(kFull, c, 8 * r + e);
+      const double vv = __shfl_sync(kFull, av, 8 * r + e);
+      if (cc >= 0) acc = __fma_rn(vv, pv[8 * r + e], acc);
+      if (cc == i0 + r) dd = pv[8 * r + e];
+    }
+    y[r] = acc;
+    d[r] = dd;
+  }
+}
+
+// General rows (more than 8 entries): entry by entry, 32 per load
+__device__ __forceinline__ void a_rows4_wide(const BpcgArgs& a, long long i0, const double* v,
+                                             int lane, bool act, double* y, double* d) {
+  for (int r = 0; r < 4; r++) {
+    const long long i = i0 + r;
+    double acc = 0.0;
+    if (i < a.n) {
+      for (int t0 = 0; t0 < a.W; t0 += 32) {
+        int c = -1;
+        double av = 0.0;
+        if (t0 + lane < a.W) {
+          c = __ldg(a.ell_col + i * a.W + t0 + lane);
+          av = __ldg(a.ell_val + i * a.W + t0 + lane);
+        }
+        const int m = min(32, a.W - t0);
+        for (int t = 0; t < m; t++) {
+          const int cc = __shfl_sync(kFull, c, t);
+          const double vv = __shfl_sync(kFull, av, t);
+          if (cc < 0) break;
+          if (act) acc = __fma_rn(vv, __ldg(v + (long long)cc * kBpLd + lane), acc);
+        }
+      }
+    }
+    y[r] = acc;
+    d[r] = (act && i < a.n) ? __ldg(v + i * kBpLd + lane) : 0.0;
+  }
+}
+
+// (M v)_i, i = i0 .. i0+3, over the CSR rows of the preconditioner: lanes
+// 8r .. 8r+7 walk row r eight entries at a time (the next eight prefetched),
+// and the 32 operands of a step are fetched before their fmas.  Entries stay
+// in ascending column order within each row's chain.
+__device__ __forceinline__ void m_rows4(const BpcgArgs& a, long long i0, const double* v, int lane,
+                                        bool act, double* y) {
+  const int e = lane & 7;
+  const long long i = i0 + (lane >> 3);
+  long long b0 = 0, b1 = 0;
+  if (i < a.n) {
+    b0 = __ldg(a.mrp + i);
+    b1 = __ldg(a.mrp + i + 1);
+  }
+  int nch = (int)((b1 - b0 + 7) >> 3);
+  nch = max(nch, __shfl_xor_sync(kFull, nch, 8));
+  nch = max(nch, __shfl_xor_sync(kFull, nch, 16));
+  int c = -1;
+  double mv = 0.0;
+  if (b0 + e < b1) {
+    c = __ldg(a.mci + b0 + e);
+    mv = __ldg(a.mv + b0 + e);
+  }
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int t = 0; t < nch; t++) {
+    int cn = -1;
+    double mn = 0.0;
+    const long long en = b0 + 8LL * (t + 1) + e;
+    if (en < b1) {
+      cn = __ldg(a.mci + en);
+      mn = __ldg(a.mv + en);
+    }
+    double pv[32];
+#pragma unroll
+    for (int s = 0; s < 32; s++) {
+      const int cc = __shfl_sync(kFull, c, s);
+      pv[s] = (act && cc >= 0) ? __ldg(v + (long long)cc * kBpLd + lane) : 0.0;
+    }
+#pragma unroll
+    for (int r = 0; r < 4; r++)
+#pragma unroll
+      for (int e2 = 0; e2 < 8; e2++) {
+        const int cc = __shfl_sync(kFull, c, 8 * r + e2);
+        const double mm = __shfl_sync(kFull, mv, 8 * r + e2);
+        if (cc >= 0) acc[r] = __fma_rn(mm, pv[8 * r + e2], acc[r]);
+      }
+    c = cn;
+    mv = mn;
+  }
+#pragma unroll
+  for (int r = 0; r < 4; r++) y[r] = acc[r];
 }
 
 __global__ void k_bp_setup(BpcgArgs a, int nseg) {
@@ -196,13 +283,23 @@ __global__ void __launch_bounds__(256) k_bp_init(BpcgArgs a) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const bool act = lane < a.R;
   const long long row0 = (long long)blockIdx.x * kBpRows + warp * 32;
-  const double s = rows32([&](int t) {
-    const long long i = row0 + t;
-    if (i >= a.n || !act) return 0.0;
-    const double bi = a.b[i * kBpLd + lane];
-    a.x[i * kBpLd + lane] = 0.0;
-    a.r[i * kBpLd + lane] = bi;
-    return __dmul_rn(bi, bi);
+  const double s = rows32([&](int t, double* o) {
+    double bv[4];
+#pragma unroll
+    for (int r = 0; r < 4; r++) {
+      const long long i = row0 + t + r;
+      bv[r] = (act && i < a.n) ? __ldg(a.b + i * kBpLd + lane) : 0.0;
+    }
+#pragma unroll
+    for (int r = 0; r < 4; r++) {
+      const long long i = row0 + t + r;
+      o[r] = 0.0;
+      if (act && i < a.n) {
+        a.x[i * kBpLd + lane] = 0.0;
+        a.r[i * kBpLd + lane] = bv[r];
+        o[r] = __dmul_rn(bv[r], bv[r]);
+      }
+    }
   });
   bp_reduce(a, seg, s, [&](int sl, double tot) {
     a.bn[sl] = __dsqrt_rn(tot);
@@ -218,20 +315,35 @@ __global__ void __launch_bounds__(256) k_bp_prec(BpcgArgs a, int first) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const bool act = lane < a.R && !a.done[seg * kBpLd + lane];
   const long long row0 = (long long)blockIdx.x * kBpRows + warp * 32;
-  const double s = rows32([&](int t) {
-    const long long i = row0 + t;
-    if (i >= a.n) return 0.0;
-    double z;
-    if (a.precond == 0) {
-      z = act ? a.r[i * kBpLd + lane] : 0.0;
-    } else if (a.precond == 1) {
-      z = act ? __ddiv_rn(a.r[i * kBpLd + lane], a.diag[i]) : 0.0;
-    } else {
-      z = m_row(a, (int)i, a.r, lane, act);
+  const double* __restrict__ rv = a.r;
+  const double s = rows32([&](int t, double* o) {
+    double rr[4], z[4];
+#pragma unroll
+    for (int r = 0; r < 4; r++) {
+      const long long i = row0 + t + r;
+      rr[r] = (act && i < a.n) ? __ldg(rv + i * kBpLd + lane) : 0.0;
     }
-    if (!act) return 0.0;
-    a.z[i * kBpLd + lane] = z;
-    return __dmul_rn(a.r[i * kBpLd + lane], z);
+    if (a.precond == 0) {
+#pragma unroll
+      for (int r = 0; r < 4; r++) z[r] = rr[r];
+    } else if (a.precond == 1) {
+#pragma unroll
+      for (int r = 0; r < 4; r++) {
+        const long long i = row0 + t + r;
+        z[r] = (act && i < a.n) ? __ddiv_rn(rr[r], __ldg(a.diag + i)) : 0.0;
+      }
+    } else {
+      m_rows4(a, row0 + t, rv, lane, act, z);
+    }
+#pragma unroll
+    for (int r = 0; r < 4; r++) {
+      const long long i = row0 + t + r;
+      o[r] = 0.0;
+      if (act && i < a.n) {
+        a.z[i * kBpLd + lane] = z[r];
+        o[r] = __dmul_rn(rr[r], z[r]);
+      }
+    }
   });
   bp_reduce(a, seg, s, [&](int sl, double rho1) {
     if (a.done[sl]) return;
@@ -258,11 +370,21 @@ __global__ void __launch_bounds__(256) k_bp_dir(BpcgArgs a, int first) {
   if (lane >= a.R || a.done[sl]) return;
   const double be = a.beta[sl];
   const long long row0 = (long long)blockIdx.x * kBpRows + warp * 32;
-  for (int t = 0; t < 32; t++) {
-    const long long i = row0 + t;
-    if (i >= a.n) break;
-    const long long e = i * kBpLd + lane;
-    a.p[e] = first ? a.z[e] : __fma_rn(be, a.p[e], a.z[e]);
+  const double* __restrict__ zv = a.z;
+  double* __restrict__ pv = a.p;
+  for (int t = 0; t < 32; t += 8) {
+    double zz[8], pp[8];
+#pragma unroll
+    for (int r = 0; r < 8; r++) {
+      const long long i = row0 + t + r;
+      zz[r] = i < a.n ? __ldg(zv + i * kBpLd + lane) : 0.0;
+      pp[r] = (!first && i < a.n) ? pv[i * kBpLd + lane] : 0.0;
+    }
+#pragma unroll
+    for (int r = 0; r < 8; r++) {
+      const long long i = row0 + t + r;
+      if (i < a.n) pv[i * kBpLd + lane] = first ? zz[r] : __fma_rn(be, pp[r], zz[r]);
+    }
   }
 }
 
@@ -274,13 +396,23 @@ __global__ void __launch_bounds__(256) k_bp_spmm(BpcgArgs a) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const bool act = lane < a.R && !a.done[seg * kBpLd + lane];
   const long long row0 = (long long)blockIdx.x * kBpRows + warp * 32;
-  const double s = rows32([&](int t) {
-    const long long i = row0 + t;
-    if (i >= a.n) return 0.0;
-    const double q = a_row(a, (int)i, a.p, lane, act);
-    if (!act) return 0.0;
-    a.q[i * kBpLd + lane] = q;
-    return __dmul_rn(a.p[i * kBpLd + lane], q);
+  AGroup g;
+  if (a.W <= 8) a_group_load(a, row0, lane, g.cn, g.vn);
+  const double s = rows32([&](int t, double* o) {
+    double q[4], pd[4];
+    if (a.W <= 8)
+      a_rows4_small(a, g, row0 + t, t + 4 < 32, a.p, lane, act, q, pd);
+    else
+      a_rows4_wide(a, row0 + t, a.p, lane, act, q, pd);
+#pragma unroll
+    for (int r = 0; r < 4; r++) {
+      const long long i = row0 + t + r;
+      o[r] = 0.0;
+      if (act && i < a.n) {
+        a.q[i * kBpLd + lane] = q[r];
+        o[r] = __dmul_rn(pd[r], q[r]);
+      }
+    }
   });
   bp_reduce(a, seg, s, [&](int sl, double pq) {
     if (a.done[sl]) return;
@@ -305,14 +437,34 @@ __global__ void __launch_bounds__(256) k_bp_update(BpcgArgs a) {
   const bool act = lane < a.R && !a.done[sl0];
   const double al = act ? a.alpha[sl0] : 0.0;
   const long long row0 = (long long)blockIdx.x * kBpRows + warp * 32;
-  const double s = rows32([&](int t) {
-    const long long i = row0 + t;
-    if (i >= a.n || !act) return 0.0;
-    const long long e = i * kBpLd + lane;
-    a.x[e] = __fma_rn(al, a.p[e], a.x[e]);
-    const double r = __fma_rn(-al, a.q[e], a.r[e]);
-    a.r[e] = r;
-    return __dmul_rn(r, r);
+  double* __restrict__ xv = a.x;
+  double* __restrict__ rv = a.r;
+  const double* __restrict__ pv = a.p;
+  const double* __restrict__ qv = a.q;
+  const double s = rows32([&](int t, double* o) {
+    double xx[4], pp[4], qq[4], rr[4];
+#pragma unroll
+    for (int r = 0; r < 4; r++) {
+      const long long i = row0 + t + r;
+      const bool ok = act && i < a.n;
+      const long long e = i * kBpLd + lane;
+      xx[r] = ok ? xv[e] : 0.0;
+      pp[r] = ok ? __ldg(pv + e) : 0.0;
+      qq[r] = ok ? __ldg(qv + e) : 0.0;
+      rr[r] = ok ? rv[e] : 0.0;
+    }
+#pragma unroll
+    for (int r = 0; r < 4; r++) {
+      const long long i = row0 + t + r;
+      o[r] = 0.0;
+      if (act && i < a.n) {
+        const long long e = i * kBpLd + lane;
+        xv[e] = __fma_rn(al, pp[r], xx[r]);
+        const double rn = __fma_rn(-al, qq[r], rr[r]);
+        rv[e] = rn;
+        o[r] = __dmul_rn(rn, rn);
+      }
+    }
   });
   bp_reduce(a, seg, s, [&](int sl, double rr) {
     if (a.done[sl]) return;
@@ -331,13 +483,23 @@ __global__ void __launch_bounds__(256) k_bp_tres(BpcgArgs a) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const bool act = lane < a.R;
   const long long row0 = (long long)blockIdx.x * kBpRows + warp * 32;
-  const double s = rows32([&](int t) {
-    const long long i = row0 + t;
-    if (i >= a.n) return 0.0;
-    const double y = a_row(a, (int)i, a.x, lane, act);
-    if (!act) return 0.0;
-    const double d = __dsub_rn(a.b[i * kBpLd + lane], y);
-    return __dmul_rn(d, d);
+  AGroup g;
+  if (a.W <= 8) a_group_load(a, row0, lane, g.cn, g.vn);
+  const double s = rows32([&](int t, double* o) {
+    double y[4], pd[4];
+    if (a.W <= 8)
+      a_rows4_small(a, g, row0 + t, t + 4 < 32, a.x, lane, act, y, pd);
+    else
+      a_rows4_wide(a, row0 + t, a.x, lane, act, y, pd);
+#pragma unroll
+    for (int r = 0; r < 4; r++) {
+      const long long i = row0 + t + r;
+      o[r] = 0.0;
+      if (act && i < a.n) {
+        const double d = __dsub_rn(__ldg(a.b + i * kBpLd + lane), y[r]);
+        o[r] = __dmul_rn(d, d);
+      }
+    }
   });
   bp_reduce(a, seg, s, [&](int sl, double tot) { a.tres[sl] = tot; });
 }
