@@ -208,6 +208,19 @@ int spai_apply(spai_handle h, const double *x, double *y, int nrhs, int64_t ld);
 int pcg_solve(spai_handle h, const double *b, double *x, int nrhs, double rtol, int maxit,
               int precond, int on_device, int *iters, double *relres);
 
+/* Arithmetic of the products inside pcg_solve and pcg_solve_block.
+ * SPAI_FP64 (the default): A p and M r (or S r) in FP64.  SPAI_MIXED: those
+ * products use FP32 values (A rounded once to FP32; M's values, and S's
+ * computed in FP64 and then rounded) and an FP32 copy of the operand vector,
+ * accumulated by an FP32 fma chain over ascending column and widened to
+ * FP64; the vectors x, r, p, z, all inner products, the step scalars and the
+ * reported true residual stay FP64 (the mixed path of Sec. 7's assessment:
+ * FP32 values, FP64 recurrences).  On GB300 the FP32 products avoid the
+ * small FP64 pipe.  The recurrence residual still reaches rtol; the true
+ * residual of a mixed solve levels off near FP32 rounding times the
+ * conditioning, so report relres beside the iteration count. */
+int spai_set_pcg_prec(spai_handle h, int prec);
+
 /* Block PCG (Sec. 7's assessment applied to many right-hand sides; the paper
  * solves one at a time): nrhs (1..32) independent PCG recurrences per matrix
  * of the handle, each one exactly the recurrence pcg_solve runs on that

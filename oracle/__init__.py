@@ -81,7 +81,7 @@ def _load():
         lib.orc_pcg.restype = C.c_int
         lib.orc_pcg.argtypes = [C.c_int, p_i32, p_i32, p_f64, C.c_int, C.c_void_p, C.c_void_p,
                                 C.c_void_p, p_f64, C.c_double, C.c_int, p_f64,
-                                C.POINTER(C.c_int), C.POINTER(C.c_double)]
+                                C.POINTER(C.c_int), C.POINTER(C.c_double), C.c_int]
         _lib = lib
         return lib
 
@@ -170,9 +170,11 @@ def drop_column(rows, vals, cap):
     return rows[:L], vals[:L]
 
 
-def pcg(n, rowptr, colind, vals, b, rtol=1e-8, maxit=10000, precond=0, M=None):
+def pcg(n, rowptr, colind, vals, b, rtol=1e-8, maxit=10000, precond=0, M=None, mixed=False):
     """Vector PCG with x0 = 0; precond 0 none, 1 Jacobi, 2 SPAI M, 3 symmetric
-    part (M + M^T)/2 of the SPAI (M given as a CSC triple).
+    part (M + M^T)/2 of the SPAI (M given as a CSC triple).  mixed: products
+    with A and with M (or its symmetric part) in FP32 values (FP32 operand
+    copy, FP32 fma chain); vectors, inner products and scalars in FP64.
 
     Returns dict(iters, status (0 conv / 1 maxit / 2 breakdown), relres, x).
     """
@@ -194,6 +196,6 @@ def pcg(n, rowptr, colind, vals, b, rtol=1e-8, maxit=10000, precond=0, M=None):
     else:
         args = (None, None, None)
     it = lib.orc_pcg(int(n), rowptr, colind, vals, int(precond), *args, b, float(rtol), int(maxit),
-                     x, C.byref(st), C.byref(rr))
+                     x, C.byref(st), C.byref(rr), 1 if mixed else 0)
     del keep
     return dict(iters=it, status=st.value, relres=rr.value, x=x)

@@ -722,6 +722,19 @@ static void spmv_rows(int n, const int *rp, const int *ci, const double *v, cons
   }
 }
 
+/* The FP32-values SpMV of the mixed PCG: the operand is rounded to FP32,
+ * each row is an FP32 fma chain over ascending column with FP32 values, and
+ * the row result is widened to FP64. */
+static void spmv_rows_f32(int n, const int *rp, const int *ci, const float *v, const double *x,
+                          double *y, float *x32) {
+  for (int i = 0; i < n; i++) x32[i] = (float)x[i];
+  for (int i = 0; i < n; i++) {
+    float acc = 0.0f;
+    for (int q = rp[i]; q < rp[i + 1]; q++) acc = fmaf(v[q], x32[ci[q]], acc);
+    y[i] = (double)acc;
+  }
+}
+
 static double vdot(int n, const double *x, const double *y, double *tmp) {
   for (int i = 0; i < n; i++) tmp[i] = x[i] * y[i];
   return pairwise64(tmp, n);
@@ -736,10 +749,13 @@ static double vdot(int n, const double *x, const double *y, double *tmp) {
  * iterations, or on breakdown ((p,Ap) or (r,z) zero or non-finite).
  * Returns iterations (= number of A p products); *status: 0 converged,
  * 1 maxit, 2 breakdown.  *relres = ||b - A x||_2 / ||b||_2 (true residual).
+ * mixed != 0: the products with A and with M (or S) use FP32 values and an
+ * FP32 copy of the operand (spmv_rows_f32); vectors, inner products and the
+ * scalars stay FP64, and so does the final true residual.
  */
 int orc_pcg(int n, const int *rp, const int *ci, const double *av, int precond, const int *mcolptr,
             const int *mrowind, const double *mvals, const double *b, double rtol, int maxit, double *x,
-            int *status, double *relres) {
+            int *status, double *relres, int mixed) {
   double *r = (double *)malloc(sizeof(double) * (size_t)n);
   double *z = (double *)malloc(sizeof(double) * (size_t)n);
   double *p = (double *)malloc(sizeof(double) * (size_t)n);
@@ -792,6 +808,18 @@ int orc_pcg(int n, const int *rp, const int *ci, const double *av, int precond, 
       mrp = srp; mci = sci; mv = sv;
     }
   }
+  float *av32 = NULL, *mv32 = NULL, *x32 = NULL;
+  if (mixed) {
+    int nnz = rp[n];
+    av32 = (float *)malloc(sizeof(float) * (size_t)(nnz ? nnz : 1));
+    for (int e = 0; e < nnz; e++) av32[e] = (float)av[e];
+    x32 = (float *)malloc(sizeof(float) * (size_t)(n ? n : 1));
+    if (mrp) {
+      int mnz = mrp[n];
+      mv32 = (float *)malloc(sizeof(float) * (size_t)(mnz ? mnz : 1));
+      for (int e = 0; e < mnz; e++) mv32[e] = (float)mv[e];
+    }
+  }
   for (int i = 0; i < n; i++) {
     x[i] = 0.0;
     r[i] = b[i];
@@ -803,6 +831,7 @@ int orc_pcg(int n, const int *rp, const int *ci, const double *av, int precond, 
   do {                                                             \
     if (precond == 0) for (int i_ = 0; i_ < n; i_++) z[i_] = r[i_]; \
     else if (precond == 1) for (int i_ = 0; i_ < n; i_++) z[i_] = r[i_] / diag[i_]; \
+    else if (mixed) spmv_rows_f32(n, mrp, mci, mv32, r, z, x32);   \
     else spmv_rows(n, mrp, mci, mv, r, z, tmp);                    \
   } while (0)
   if (bn == 0.0) goto out;
@@ -812,7 +841,8 @@ int orc_pcg(int n, const int *rp, const int *ci, const double *av, int precond, 
   for (int i = 0; i < n; i++) p[i] = z[i];
   for (;;) {
     if (k >= maxit) { *status = 1; break; }
-    spmv_rows(n, rp, ci, av, p, q, tmp);
+    if (mixed) spmv_rows_f32(n, rp, ci, av32, p, q, x32);
+    else spmv_rows(n, rp, ci, av, p, q, tmp);
     double pq = vdot(n, p, q, tmp);
     if (pq == 0.0 || !isfin(pq)) { *status = 2; break; }
     double alpha = rho / pq;
@@ -847,5 +877,8 @@ out:
   free(mrp);
   free(mci);
   free(mv);
+  free(av32);
+  free(mv32);
+  free(x32);
   return k;
 }

@@ -118,6 +118,14 @@ struct spai_ctx {
   PcgScalars* d_ps = nullptr;
   double *d_vbsum = nullptr, *d_vgsum = nullptr;
   unsigned *d_vcnt1 = nullptr, *d_vcnt2 = nullptr;
+  // PCG arithmetic (SPAI_FP64, or SPAI_MIXED: FP32-values products) and the
+  // FP32 copies it uses: A's sliced-ELL values, M's and S's row values, the
+  // operand vectors
+  int pcg_prec = SPAI_FP64;
+  float *d_aval32 = nullptr, *d_mv32 = nullptr, *d_sv32 = nullptr, *d_p32 = nullptr,
+        *d_r32 = nullptr, *d_bp32 = nullptr, *d_br32 = nullptr;
+  long long mt_nnz = 0, sym_nnz = 0, mv32_cap = 0, sv32_cap = 0;
+  bool m32_valid = false, s32_valid = false;
   // block PCG: vectors [n][32], per (matrix, rhs) state, segment maps
   double *d_bb = nullptr, *d_bx = nullptr, *d_br = nullptr, *d_bz = nullptr, *d_bp = nullptr,
          *d_bq = nullptr, *d_bstage = nullptr;
@@ -481,6 +489,13 @@ void free_all(spai_ctx* h) {
   dfree(h->d_bp);
   dfree(h->d_bq);
   dfree(h->d_bstage);
+  dfree(h->d_aval32);
+  dfree(h->d_mv32);
+  dfree(h->d_sv32);
+  dfree(h->d_p32);
+  dfree(h->d_r32);
+  dfree(h->d_bp32);
+  dfree(h->d_br32);
   dfree(h->d_bstate);
   dfree(h->d_bistate);
   dfree(h->d_bseg_live);
@@ -550,6 +565,7 @@ int ensure_rows(spai_ctx* h, bool sym) {
     }
     CK(launch_transpose(n, h->d_ccolptr, h->d_crow, h->d_cval, nnz, h->d_cnt, h->d_mrp, h->d_scan,
                         h->d_mci, h->d_mv, h->d_tmpi, h->d_tmpv, h->stream));
+    h->mt_nnz = nnz;
     h->other_launches += 7;
     h->mt_valid = true;
     h->sym_valid = false;
@@ -575,6 +591,7 @@ int ensure_rows(spai_ctx* h, bool sym) {
     }
     CK(launch_sym(n, h->d_mrp, h->d_mci, h->d_mv, h->d_ccolptr, h->d_crow, h->d_cval, 1, h->d_cnt,
                   h->d_srp, h->d_sci, h->d_sv, h->stream));
+    h->sym_nnz = tot;
     h->other_launches += 5;
     h->sym_valid = true;
   }
@@ -584,6 +601,8 @@ int ensure_rows(spai_ctx* h, bool sym) {
 void invalidate_rows(spai_ctx* h) {
   h->mt_valid = false;
   h->sym_valid = false;
+  h->m32_valid = false;
+  h->s32_valid = false;
 }
 
 }  // namespace
@@ -1421,6 +1440,70 @@ static int ensure_pcg(spai_ctx* h) {
   return SPAI_OK;
 }
 
+// FP32 copies for the mixed PCG products (made on first use; M's and S's
+// again after M changes).  block: the ELL values of A and [n][32] operand
+// copies instead of the sliced-ELL values and n-vectors.
+static int ensure_pcg32(spai_ctx* h, int precond, bool block) {
+  cudaStream_t st = h->stream;
+  int rc = SPAI_OK;
+  if (!block) {
+    if (!h->d_aval32) {
+      rc = dalloc(&h->d_aval32, (size_t)h->a_cap);
+      if (rc) return rc;
+      CK(launch_to_f32(h->d_aval, h->d_aval32, h->a_cap, st));
+      h->other_launches++;
+    }
+    if (!h->d_p32) {
+      rc = dalloc(&h->d_p32, (size_t)h->n);
+      if (!rc) rc = dalloc(&h->d_r32, (size_t)h->n);
+      if (rc) return rc;
+    }
+  } else {
+    if (!h->d_ell32) {
+      rc = dalloc(&h->d_ell32, (size_t)h->n * h->W);
+      if (rc) return rc;
+      CK(launch_to_f32(h->d_ell64, h->d_ell32, (long long)h->n * h->W, st));
+      h->other_launches++;
+    }
+    if (!h->d_bp32) {
+      rc = dalloc(&h->d_bp32, (size_t)h->n * kBpLd);
+      if (!rc) rc = dalloc(&h->d_br32, (size_t)h->n * kBpLd);
+      if (rc) return rc;
+    }
+  }
+  if (precond == SPAI_PREC_SPAI && !h->m32_valid) {
+    if (h->mt_nnz > h->mv32_cap || !h->d_mv32) {
+      dfree(h->d_mv32);
+      h->mv32_cap = 0;
+      rc = dalloc(&h->d_mv32, (size_t)std::max(h->mt_nnz, 1LL));
+      if (rc) return rc;
+      h->mv32_cap = std::max(h->mt_nnz, 1LL);
+    }
+    CK(launch_to_f32(h->d_mv, h->d_mv32, h->mt_nnz, st));
+    h->other_launches++;
+    h->m32_valid = true;
+  }
+  if (precond == SPAI_PREC_SPAI_SYM && !h->s32_valid) {
+    if (h->sym_nnz > h->sv32_cap || !h->d_sv32) {
+      dfree(h->d_sv32);
+      h->sv32_cap = 0;
+      rc = dalloc(&h->d_sv32, (size_t)std::max(h->sym_nnz, 1LL));
+      if (rc) return rc;
+      h->sv32_cap = std::max(h->sym_nnz, 1LL);
+    }
+    CK(launch_to_f32(h->d_sv, h->d_sv32, h->sym_nnz, st));
+    h->other_launches++;
+    h->s32_valid = true;
+  }
+  return SPAI_OK;
+}
+
+int spai_set_pcg_prec(spai_handle h, int prec) {
+  if (!h || (prec != SPAI_FP64 && prec != SPAI_MIXED)) return SPAI_ERR_ARG;
+  h->pcg_prec = prec;
+  return SPAI_OK;
+}
+
 int pcg_solve(spai_handle h, const double* b, double* x, int nrhs, double rtol, int maxit,
               int precond, int on_device, int* iters, double* relres) {
   if (!h || !b || !x || !iters || nrhs != 1 || maxit < 0 || !(rtol >= 0.0)) return SPAI_ERR_ARG;
@@ -1466,6 +1549,15 @@ int pcg_solve(spai_handle h, const double* b, double* x, int nrhs, double rtol, 
   a.p = h->d_p;
   a.q = h->d_q;
   a.s = h->d_ps;
+  if (h->pcg_prec == SPAI_MIXED) {
+    rc = ensure_pcg32(h, precond, false);
+    if (rc) return rc;
+    a.mixed = 1;
+    a.aval32 = h->d_aval32;
+    a.mv32 = precond == SPAI_PREC_SPAI ? h->d_mv32 : precond == SPAI_PREC_SPAI_SYM ? h->d_sv32 : nullptr;
+    a.p32 = h->d_p32;
+    a.r32 = h->d_r32;
+  }
   a.ws.bsum = h->d_vbsum;
   a.ws.gsum = h->d_vgsum;
   a.ws.cnt1 = h->d_vcnt1;
@@ -1671,6 +1763,15 @@ int pcg_solve_block(spai_handle h, int nrhs, const double* b, double* x, double 
   a.live = h->d_blive;
   a.bsum = h->d_bbsum;
   a.cnt = h->d_bcnt;
+  if (h->pcg_prec == SPAI_MIXED) {
+    rc = ensure_pcg32(h, precond, true);
+    if (rc) return rc;
+    a.mixed = 1;
+    a.ell_val32 = h->d_ell32;
+    a.mv32 = precond == SPAI_PREC_SPAI ? h->d_mv32 : precond == SPAI_PREC_SPAI_SYM ? h->d_sv32 : nullptr;
+    a.p32 = h->d_bp32;
+    a.r32 = h->d_br32;
+  }
   CK(launch_bp_setup(a, nseg, st));
   CK(launch_bp_init(a, st));
   h->other_launches += 2;

@@ -130,92 +130,108 @@ __device__ __forceinline__ void bp_retire(const BpcgArgs& a, int sl, int status)
   atomicSub(a.live, 1);
 }
 
+__device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+
 // Rows of A with at most 8 entries are handled four at a time: lane 8r + e
 // holds entry e of row i0 + r (column -1 where the row has fewer), loaded in
 // one coalesced access; AGroup keeps the entries of the current group and
 // prefetches those of the next while the current group's operands are read.
+// VT is the value type of the products: double, or float on the mixed path.
+template <typename VT>
 struct AGroup {
-  int c, cn;
-  double v, vn;
+  int cn;
+  VT vn;
 };
 
-__device__ __forceinline__ void a_group_load(const BpcgArgs& a, long long i0, int lane, int& c,
-                                             double& v) {
+template <typename VT>
+__device__ __forceinline__ void a_group_load(const BpcgArgs& a, const VT* vals, long long i0,
+                                             int lane, int& c, VT& v) {
   const long long i = i0 + (lane >> 3);
   const int e = lane & 7;
   c = -1;
-  v = 0.0;
+  v = VT(0);
   if (i < a.n && e < a.W) {
     c = __ldg(a.ell_col + i * a.W + e);
-    v = __ldg(a.ell_val + i * a.W + e);
+    v = __ldg(vals + i * a.W + e);
   }
 }
 
-// (A v)_i, i = i0 .. i0+3, for right-hand side lane into y[0..3], and
-// d[r] = v_i (the operand of the diagonal entry) for the inner-product term.
-// Every operand of the four rows is fetched before the fma chains run (32
-// gathers in flight per warp); padding (column -1) ends a row.
-__device__ __forceinline__ void a_rows4_small(const BpcgArgs& a, AGroup& g, long long i0,
-                                              bool more, const double* v, int lane, bool act,
-                                              double* y, double* d) {
+// (A x)_i, i = i0 .. i0+3, for right-hand side lane into y[0..3] (an fma
+// chain in VT over ascending column, widened to FP64).  Every operand of the
+// four rows is fetched before the chains run (32 gathers in flight per
+// warp); padding (column -1) ends a row.
+template <typename VT>
+__device__ __forceinline__ void a_rows4_small(const BpcgArgs& a, const VT* vals, AGroup<VT>& g,
+                                              long long i0, bool more, const VT* x, int lane,
+                                              bool act, double* y) {
   const int c = g.cn;
-  const double av = g.vn;
-  if (more) a_group_load(a, i0 + 4, lane, g.cn, g.vn);
-  double pv[32];
+  const VT av = g.vn;
+  if (more) a_group_load(a, vals, i0 + 4, lane, g.cn, g.vn);
+  VT pv[32];
 #pragma unroll
   for (int s = 0; s < 32; s++) {
     const int cc = __shfl_sync(kFull, c, s);
-    pv[s] = (act && cc >= 0) ? __ldg(v + (long long)cc * kBpLd + lane) : 0.0;
+    pv[s] = (act && cc >= 0) ? __ldg(x + (long long)cc * kBpLd + lane) : VT(0);
   }
 #pragma unroll
   for (int r = 0; r < 4; r++) {
-    double acc = 0.0, dd = 0.0;
+    VT acc = VT(0);
 #pragma unroll
     for (int e = 0; e < 8; e++) {
       const int cc = __shfl_sync(kFull, c, 8 * r + e);
-      const double vv = __shfl_sync(kFull, av, 8 * r + e);
-      if (cc >= 0) acc = __fma_rn(vv, pv[8 * r + e], acc);
-      if (cc == i0 + r) dd = pv[8 * r + e];
+      const VT vv = __shfl_sync(kFull, av, 8 * r + e);
+      if (cc >= 0) acc = fma_rn(vv, pv[8 * r + e], acc);
     }
-    y[r] = acc;
-    d[r] = dd;
+    y[r] = (double)acc;
   }
 }
 
 // General rows (more than 8 entries): entry by entry, 32 per load
-__device__ __forceinline__ void a_rows4_wide(const BpcgArgs& a, long long i0, const double* v,
-                                             int lane, bool act, double* y, double* d) {
+template <typename VT>
+__device__ __forceinline__ void a_rows4_wide(const BpcgArgs& a, const VT* vals, long long i0,
+                                             const VT* x, int lane, bool act, double* y) {
   for (int r = 0; r < 4; r++) {
     const long long i = i0 + r;
-    double acc = 0.0;
+    VT acc = VT(0);
     if (i < a.n) {
       for (int t0 = 0; t0 < a.W; t0 += 32) {
         int c = -1;
-        double av = 0.0;
+        VT av = VT(0);
         if (t0 + lane < a.W) {
           c = __ldg(a.ell_col + i * a.W + t0 + lane);
-          av = __ldg(a.ell_val + i * a.W + t0 + lane);
+          av = __ldg(vals + i * a.W + t0 + lane);
         }
         const int m = min(32, a.W - t0);
         for (int t = 0; t < m; t++) {
           const int cc = __shfl_sync(kFull, c, t);
-          const double vv = __shfl_sync(kFull, av, t);
+          const VT vv = __shfl_sync(kFull, av, t);
           if (cc < 0) break;
-          if (act) acc = __fma_rn(vv, __ldg(v + (long long)cc * kBpLd + lane), acc);
+          if (act) acc = fma_rn(vv, __ldg(x + (long long)cc * kBpLd + lane), acc);
         }
       }
     }
-    y[r] = acc;
-    d[r] = (act && i < a.n) ? __ldg(v + i * kBpLd + lane) : 0.0;
+    y[r] = (double)acc;
   }
 }
 
-// (M v)_i, i = i0 .. i0+3, over the CSR rows of the preconditioner: lanes
+template <typename VT>
+__device__ __forceinline__ void a_rows4(const BpcgArgs& a, const VT* vals, AGroup<VT>& g,
+                                        long long i0, bool more, const VT* x, int lane, bool act,
+                                        double* y) {
+  if (a.W <= 8)
+    a_rows4_small(a, vals, g, i0, more, x, lane, act, y);
+  else
+    a_rows4_wide(a, vals, i0, x, lane, act, y);
+}
+
+// (M x)_i, i = i0 .. i0+3, over the CSR rows of the preconditioner: lanes
 // 8r .. 8r+7 walk row r eight entries at a time (the next eight prefetched),
 // and the 32 operands of a step are fetched before their fmas.  Entries stay
 // in ascending column order within each row's chain.
-__device__ __forceinline__ void m_rows4(const BpcgArgs& a, long long i0, const double* v, int lane,
-                                        bool act, double* y) {
+template <typename VT>
+__device__ __forceinline__ void m_rows4(const BpcgArgs& a, const VT* mvals, long long i0,
+                                        const VT* x, int lane, bool act, double* y) {
   const int e = lane & 7;
   const long long i = i0 + (lane >> 3);
   long long b0 = 0, b1 = 0;
@@ -227,39 +243,39 @@ __device__ __forceinline__ void m_rows4(const BpcgArgs& a, long long i0, const d
   nch = max(nch, __shfl_xor_sync(kFull, nch, 8));
   nch = max(nch, __shfl_xor_sync(kFull, nch, 16));
   int c = -1;
-  double mv = 0.0;
+  VT mv = VT(0);
   if (b0 + e < b1) {
     c = __ldg(a.mci + b0 + e);
-    mv = __ldg(a.mv + b0 + e);
+    mv = __ldg(mvals + b0 + e);
   }
-  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  VT acc[4] = {VT(0), VT(0), VT(0), VT(0)};
   for (int t = 0; t < nch; t++) {
     int cn = -1;
-    double mn = 0.0;
+    VT mn = VT(0);
     const long long en = b0 + 8LL * (t + 1) + e;
     if (en < b1) {
       cn = __ldg(a.mci + en);
-      mn = __ldg(a.mv + en);
+      mn = __ldg(mvals + en);
     }
-    double pv[32];
+    VT pv[32];
 #pragma unroll
     for (int s = 0; s < 32; s++) {
       const int cc = __shfl_sync(kFull, c, s);
-      pv[s] = (act && cc >= 0) ? __ldg(v + (long long)cc * kBpLd + lane) : 0.0;
+      pv[s] = (act && cc >= 0) ? __ldg(x + (long long)cc * kBpLd + lane) : VT(0);
     }
 #pragma unroll
     for (int r = 0; r < 4; r++)
 #pragma unroll
       for (int e2 = 0; e2 < 8; e2++) {
         const int cc = __shfl_sync(kFull, c, 8 * r + e2);
-        const double mm = __shfl_sync(kFull, mv, 8 * r + e2);
-        if (cc >= 0) acc[r] = __fma_rn(mm, pv[8 * r + e2], acc[r]);
+        const VT mm = __shfl_sync(kFull, mv, 8 * r + e2);
+        if (cc >= 0) acc[r] = fma_rn(mm, pv[8 * r + e2], acc[r]);
       }
     c = cn;
     mv = mn;
   }
 #pragma unroll
-  for (int r = 0; r < 4; r++) y[r] = acc[r];
+  for (int r = 0; r < 4; r++) y[r] = (double)acc[r];
 }
 
 __global__ void k_bp_setup(BpcgArgs a, int nseg) {
@@ -297,6 +313,7 @@ __global__ void __launch_bounds__(256) k_bp_init(BpcgArgs a) {
       if (act && i < a.n) {
         a.x[i * kBpLd + lane] = 0.0;
         a.r[i * kBpLd + lane] = bv[r];
+        if (a.mixed) a.r32[i * kBpLd + lane] = __double2float_rn(bv[r]);
         o[r] = __dmul_rn(bv[r], bv[r]);
       }
     }
@@ -332,8 +349,10 @@ __global__ void __launch_bounds__(256) k_bp_prec(BpcgArgs a, int first) {
         const long long i = row0 + t + r;
         z[r] = (act && i < a.n) ? __ddiv_rn(rr[r], __ldg(a.diag + i)) : 0.0;
       }
+    } else if (a.mixed) {
+      m_rows4(a, a.mv32, row0 + t, (const float*)a.r32, lane, act, z);
     } else {
-      m_rows4(a, row0 + t, rv, lane, act, z);
+      m_rows4(a, a.mv, row0 + t, rv, lane, act, z);
     }
 #pragma unroll
     for (int r = 0; r < 4; r++) {
@@ -383,7 +402,11 @@ __global__ void __launch_bounds__(256) k_bp_dir(BpcgArgs a, int first) {
 #pragma unroll
     for (int r = 0; r < 8; r++) {
       const long long i = row0 + t + r;
-      if (i < a.n) pv[i * kBpLd + lane] = first ? zz[r] : __fma_rn(be, pp[r], zz[r]);
+      if (i < a.n) {
+        const double pn = first ? zz[r] : __fma_rn(be, pp[r], zz[r]);
+        pv[i * kBpLd + lane] = pn;
+        if (a.mixed) a.p32[i * kBpLd + lane] = __double2float_rn(pn);
+      }
     }
   }
 }
@@ -396,21 +419,27 @@ __global__ void __launch_bounds__(256) k_bp_spmm(BpcgArgs a) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const bool act = lane < a.R && !a.done[seg * kBpLd + lane];
   const long long row0 = (long long)blockIdx.x * kBpRows + warp * 32;
-  AGroup g;
-  if (a.W <= 8) a_group_load(a, row0, lane, g.cn, g.vn);
-  const double s = rows32([&](int t, double* o) {
-    double q[4], pd[4];
-    if (a.W <= 8)
-      a_rows4_small(a, g, row0 + t, t + 4 < 32, a.p, lane, act, q, pd);
+  AGroup<double> g;
+  AGroup<float> g32;
+  if (a.W <= 8) {
+    if (a.mixed)
+      a_group_load(a, a.ell_val32, row0, lane, g32.cn, g32.vn);
     else
-      a_rows4_wide(a, row0 + t, a.p, lane, act, q, pd);
+      a_group_load(a, a.ell_val, row0, lane, g.cn, g.vn);
+  }
+  const double s = rows32([&](int t, double* o) {
+    double q[4];
+    if (a.mixed)
+      a_rows4(a, a.ell_val32, g32, row0 + t, t + 4 < 32, (const float*)a.p32, lane, act, q);
+    else
+      a_rows4(a, a.ell_val, g, row0 + t, t + 4 < 32, (const double*)a.p, lane, act, q);
 #pragma unroll
     for (int r = 0; r < 4; r++) {
       const long long i = row0 + t + r;
       o[r] = 0.0;
       if (act && i < a.n) {
         a.q[i * kBpLd + lane] = q[r];
-        o[r] = __dmul_rn(pd[r], q[r]);
+        o[r] = __dmul_rn(__ldg(a.p + i * kBpLd + lane), q[r]);
       }
     }
   });
@@ -462,6 +491,7 @@ __global__ void __launch_bounds__(256) k_bp_update(BpcgArgs a) {
         xv[e] = __fma_rn(al, pp[r], xx[r]);
         const double rn = __fma_rn(-al, qq[r], rr[r]);
         rv[e] = rn;
+        if (a.mixed) a.r32[e] = __double2float_rn(rn);
         o[r] = __dmul_rn(rn, rn);
       }
     }
@@ -483,14 +513,11 @@ __global__ void __launch_bounds__(256) k_bp_tres(BpcgArgs a) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const bool act = lane < a.R;
   const long long row0 = (long long)blockIdx.x * kBpRows + warp * 32;
-  AGroup g;
-  if (a.W <= 8) a_group_load(a, row0, lane, g.cn, g.vn);
+  AGroup<double> g;
+  if (a.W <= 8) a_group_load(a, a.ell_val, row0, lane, g.cn, g.vn);
   const double s = rows32([&](int t, double* o) {
-    double y[4], pd[4];
-    if (a.W <= 8)
-      a_rows4_small(a, g, row0 + t, t + 4 < 32, a.x, lane, act, y, pd);
-    else
-      a_rows4_wide(a, row0 + t, a.x, lane, act, y, pd);
+    double y[4];
+    a_rows4(a, a.ell_val, g, row0 + t, t + 4 < 32, (const double*)a.x, lane, act, y);
 #pragma unroll
     for (int r = 0; r < 4; r++) {
       const long long i = row0 + t + r;

@@ -34,6 +34,12 @@ struct BpcgArgs {
   int* live;                       // [1] recurrences still running
   double* bsum;                    // [ncta][kBpLd] CTA partials
   unsigned* cnt;                   // [nseg] arrival counters
+  // mixed (FP32-values) products: A's ELL values and M's (or S's) row values
+  // in FP32, FP32 copies of p and r ([n][kBpLd]) as their operands
+  int mixed;
+  const float* ell_val32;
+  const float* mv32;
+  float *p32, *r32;
 };
 
 cudaError_t launch_bp_setup(const BpcgArgs& a, int nseg, cudaStream_t st);

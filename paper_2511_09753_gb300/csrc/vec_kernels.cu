@@ -102,6 +102,41 @@ __device__ __forceinline__ double sell_chain(const SellM& m, const double* x, in
   return acc;
 }
 
+// FP32-values variants for the mixed PCG: FP32 values and operand, an FP32
+// fma chain in the same entry order, the row result widened to FP64
+__device__ __forceinline__ double sell_chain_f32(const SellM& m, const float* v32, const float* x,
+                                                 int i) {
+  const int s = i >> 5, lane = i & 31;
+  const long long b = m.sptr[s];
+  const int w = (int)((m.sptr[s + 1] - b) >> 5);
+  float acc = 0.0f;
+  for (int t = 0; t < w; t++) {
+    long long e = b + 32LL * t + lane;
+    acc = __fmaf_rn(v32[e], x[m.col[e]], acc);
+  }
+  return (double)acc;
+}
+
+template <typename RP>
+__device__ __forceinline__ double row_chain_f32(const RP* rp, const int* ci, const float* v,
+                                                const float* x, int i) {
+  float acc = 0.0f;
+  const RP e1 = rp[i + 1];
+  for (RP e = rp[i]; e < e1; e++) acc = __fmaf_rn(v[e], x[ci[e]], acc);
+  return (double)acc;
+}
+
+__global__ void k_to_f32(const double* in, float* out, long long count) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < count) out[i] = __double2float_rn(in[i]);
+}
+
+cudaError_t launch_to_f32(const double* in, float* out, long long count, cudaStream_t st) {
+  if (count <= 0) return cudaSuccess;
+  k_to_f32<<<(unsigned)((count + 255) / 256), 256, 0, st>>>(in, out, count);
+  return cudaGetLastError();
+}
+
 template <typename RP>
 __global__ void k_sell_width(int n, const RP* rp, int* w32) {
   int s = blockIdx.x * blockDim.x + threadIdx.x;
@@ -458,6 +493,7 @@ __global__ void k_true_res(PcgArgs a) {
 __device__ __forceinline__ double precond_apply(const PcgArgs& a, int i) {
   if (a.precond == 0) return a.r[i];
   if (a.precond == 1) return __ddiv_rn(a.r[i], a.diag[i]);
+  if (a.mixed) return row_chain_f32(a.mrp, a.mci, a.mv32, a.r32, i);
   return row_chain(a.mrp, a.mci, a.mv, a.r, i);
 }
 
@@ -469,6 +505,7 @@ __global__ void k_pcg_init(PcgArgs a) {
     double bi = a.b[i];
     a.x[i] = 0.0;
     a.r[i] = bi;
+    if (a.mixed) a.r32[i] = __double2float_rn(bi);
     term = __dmul_rn(bi, bi);
   }
   PcgScalars* s = a.s;
@@ -512,7 +549,9 @@ __global__ void k_pcg_dir(PcgArgs a, int first) {
   if (a.s->done) return;
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= a.n) return;
-  a.p[i] = first ? a.z[i] : __fma_rn(a.s->beta, a.p[i], a.z[i]);
+  const double p = first ? a.z[i] : __fma_rn(a.s->beta, a.p[i], a.z[i]);
+  a.p[i] = p;
+  if (a.mixed) a.p32[i] = __double2float_rn(p);
 }
 
 // q = A p, terms p_i q_i -> alpha
@@ -521,7 +560,7 @@ __global__ void k_pcg_spmv(PcgArgs a) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   double term = 0.0;
   if (i < a.n) {
-    double q = sell_chain(a.A, a.p, i);
+    double q = a.mixed ? sell_chain_f32(a.A, a.aval32, a.p32, i) : sell_chain(a.A, a.p, i);
     a.q[i] = q;
     term = __dmul_rn(a.p[i], q);
   }
@@ -551,6 +590,7 @@ __global__ void k_pcg_update(PcgArgs a) {
     a.x[i] = __fma_rn(al, a.p[i], a.x[i]);
     double r = __fma_rn(-al, a.q[i], a.r[i]);
     a.r[i] = r;
+    if (a.mixed) a.r32[i] = __double2float_rn(r);
     term = __dmul_rn(r, r);
   }
   PcgScalars* s = a.s;

@@ -37,6 +37,12 @@ struct PcgArgs {
   double *x, *r, *z, *p, *q;
   PcgScalars* s;
   RedWS ws;
+  // mixed (FP32-values) products: A's sliced-ELL values and M's (or S's)
+  // row values in FP32, and FP32 copies of p and r as their operands
+  int mixed;
+  const float* aval32;
+  const float* mv32;
+  float *p32, *r32;
 };
 
 cudaError_t launch_seg_reset(DevScalars* sc, int nseg, int fresh, cudaStream_t st);
@@ -62,6 +68,7 @@ cudaError_t launch_sell_build_i32(int n, const int* rp, const int* ci, const dou
 cudaError_t launch_sell_build_i64(int n, const long long* rp, const int* ci, const double* v,
                                   int* w32, long long* sptr, long long* scan_tmp, int** scol,
                                   double** sval, long long* cap, long long* total, cudaStream_t st);
+cudaError_t launch_to_f32(const double* in, float* out, long long count, cudaStream_t st);
 cudaError_t launch_pcg_init(const PcgArgs& a, cudaStream_t st);
 cudaError_t launch_pcg_iter(const PcgArgs& a, cudaStream_t st);
 cudaError_t launch_true_res(const PcgArgs& a, cudaStream_t st);

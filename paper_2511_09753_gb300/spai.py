@@ -30,7 +30,7 @@ EXPORTED = ["spai_validate_csr", "spai_status_string", "spai_create", "spai_dest
             "pcg_solve", "spai_save_state", "spai_load_state", "spai_set_timing",
             "spai_get_stats", "spai_true_residual_noalloc", "spai_create_batched",
             "spai_batch_info", "spai_batch_history", "spai_batch_residual_norms",
-            "spai_batch_get_M", "pcg_solve_block"]
+            "spai_batch_get_M", "pcg_solve_block", "spai_set_pcg_prec"]
 
 
 class SpaiError(RuntimeError):
@@ -84,6 +84,7 @@ def load():
         "spai_apply": (i32, [vp, vp, vp, i32, i64]),
         "pcg_solve": (i32, [vp, vp, vp, i32, dbl, i32, i32, i32, C.POINTER(i32), C.POINTER(dbl)]),
         "pcg_solve_block": (i32, [vp, i32, vp, vp, dbl, i32, i32, i32, vp, vp, vp]),
+        "spai_set_pcg_prec": (i32, [vp, i32]),
         "spai_save_state": (i32, [vp, vp, C.POINTER(C.c_size_t)]),
         "spai_load_state": (i32, [vp, vp, C.c_size_t]),
         "spai_set_timing": (i32, [vp, i32]),
@@ -274,6 +275,12 @@ class Spai:
 
     def _sizes(self):
         return [int(self.n)]
+
+    def set_pcg_prec(self, prec):
+        """Products inside PCG in "fp64" (default) or "mixed" (FP32 values,
+        FP32 operand copies; FP64 vectors, dots and scalars)."""
+        self._check(self.lib.spai_set_pcg_prec(self.h, SPAI_MIXED if prec == "mixed" else SPAI_FP64),
+                    "spai_set_pcg_prec")
 
     def pcg_block(self, B, rtol=1e-8, maxit=10000, precond=PREC_SPAI_SYM, nrhs=None, x=None):
         """Block PCG: up to 32 independent recurrences per matrix of the handle.

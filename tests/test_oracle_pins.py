@@ -354,6 +354,40 @@ def test_pcg_exact_inverse_and_jacobi_as_matrix():
     assert sym["iters"] == jac["iters"]
 
 
+def test_mixed_pcg_first_step_is_exact_on_integer_data():
+    """With values and operands exact in FP32 and every FP32 product and sum
+    exact (small integers), the FP32-values products equal the FP64 ones, so
+    one mixed iteration reproduces one FP64 iteration bit for bit."""
+    n, rp, ci, v = I.laplacian_1d(40)          # entries 2 and -1
+    b = np.arange(1.0, n + 1.0) % 7.0 - 3.0      # small integers
+    d = np.arange(n + 1, dtype=np.int32)
+    half = (d, d[:-1].copy(), np.full(n, 0.5))  # M = I / 2, exact in FP32
+    for precond, M in ((0, None), (2, half), (3, half)):
+        a = O.pcg(n, rp, ci, v, b, maxit=1, precond=precond, M=M, mixed=True)
+        f = O.pcg(n, rp, ci, v, b, maxit=1, precond=precond, M=M)
+        assert a["iters"] == f["iters"] == 1 and a["status"] == f["status"] == 1
+        assert np.array_equal(a["x"], f["x"])
+
+
+def test_mixed_pcg_tracks_fp64_pcg():
+    """FP32-values products perturb each product by FP32 rounding only: the
+    iteration count stays within 2 % of the FP64 solve and x within FP32
+    accuracy of it, while the results do differ (the rounding is applied)."""
+    n, rp, ci, v = lap2d(32)
+    b = I.rhs_uniform(n, 0)
+    o = O.Oracle(n, rp, ci, v, cap_factor=2.0)
+    o.run("mr", 20)
+    M = o.get_M()
+    for precond in (1, 3):
+        f = O.pcg(n, rp, ci, v, b, rtol=1e-8, precond=precond, M=M)
+        a = O.pcg(n, rp, ci, v, b, rtol=1e-8, precond=precond, M=M, mixed=True)
+        assert f["status"] == a["status"] == 0
+        assert abs(a["iters"] - f["iters"]) <= max(1, 0.02 * f["iters"])
+        assert not np.array_equal(a["x"], f["x"])
+        assert np.linalg.norm(a["x"] - f["x"]) <= 1e-5 * np.linalg.norm(f["x"])
+        assert a["relres"] < 1e-5
+
+
 # ------------------------------------------------------- mixed precision
 
 def test_mixed_emulation_tracks_fp64():
