@@ -6,8 +6,10 @@ correlation length 8 cells, harmonic-mean faces, seed 0); FP32 values with
 FP64 reductions; per-column cap 3 nnz(A[:,j]); from M_0 = diag(A)^{-1}:
 50 MR iterations, then PCG, 50 LOMR iterations, then PCG, 50 CG iterations,
 then PCG (b ~ U(-1,1) seed 0, rtol 1e-8, symmetric part of M as
-preconditioner).  Metric: SPAI iterations per second over the whole step
-(150 iterations / step time, PCG and set-up included).
+preconditioner; FP32-values products, FP64 vectors and scalars).  Metric:
+SPAI iterations per second over the whole step (150 iterations / step time,
+PCG and set-up included).  The FP64 path (FP64 values, FP64 PCG) is timed
+on the same workload and reported beside it.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
   python bench.py --workload batch64     # batched SPAIs + block PCG (below)
@@ -17,7 +19,8 @@ preconditioner).  Metric: SPAI iterations per second over the whole step
 953,176 rows in all) in one batched handle; one step = 30 LOMR iterations of
 every matrix (mixed, cap 3 nnz(A[:,j])) from M_0 = diag(A)^{-1}, then block
 PCG with 32 right-hand sides per matrix (U(-1,1), seed 2000+k), symmetric
-part of M, rtol 1e-8.  Metric: matrix-iterations per second (64 x 30 / step
+part of M, rtol 1e-8, FP64 products (FP32-values products leave some of
+the ill-conditioned 2-D systems unconverged at 1000 iterations).  Metric: matrix-iterations per second (64 x 30 / step
 time); the PCG share and iteration counts are reported beside it.
 
 --impl reference times the CPU oracle (the plain single-threaded C
@@ -136,6 +139,7 @@ def run_ours(args):
 
     # device-resident inputs: A copied once, handle created outside the timed region
     g = Spai(n, rp, ci, v, prec="mixed", cap_factor=CAP)
+    g.set_pcg_prec("mixed")
     b_dev = torch.tensor(b, dtype=torch.float64, device="cuda")
     x_dev = torch.empty_like(b_dev)
 
@@ -199,6 +203,7 @@ def run_ours(args):
     # PCG with host b and x, export M (D2H) -- every step
     def e2e_step():
         h = Spai(n, rp, ci, v, prec="mixed", cap_factor=CAP)
+        h.set_pcg_prec("mixed")
         h2d = rp.nbytes + ci.nbytes + v.nbytes
         d2h = 0
         for m in METHODS:
@@ -245,6 +250,8 @@ def run_ours(args):
     for m in METHODS:
         results[m]["fp64_resnorm"] = float(r64[m][0]["resnorm"][-1])
         results[m]["fp64_pcg_iters"] = int(r64[m][1]["iters"])
+        results[m]["pcg_iters_rel_diff"] = (abs(results[m]["pcg_iters"] - results[m]["fp64_pcg_iters"])
+                                            / max(1, results[m]["fp64_pcg_iters"]))
         rel = abs(results[m]["resnorm"] - results[m]["fp64_resnorm"]) / results[m]["fp64_resnorm"]
         results[m]["mixed_vs_fp64_rel"] = rel
 
@@ -265,7 +272,7 @@ def run_ours(args):
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "n": n, "nnz": int(len(v)), "cap_factor": CAP,
                        "iters_per_method": ITERS, "methods": list(METHODS),
-                       "pcg": "symmetric part of M, rtol 1e-8, maxit 1000",
+                       "pcg": "symmetric part of M, rtol 1e-8, maxit 1000, FP32-values products",
                        "l2": "flushed between steps (256 MB write)", "parallelism": "replicas"},
             "e2e": {"value": ws * total_iters / e2e_s, "unit": "SPAI iterations/s",
                     "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
@@ -410,7 +417,7 @@ def run_batch(args):
             "config": {"workload": "batch64_uneven", "nmat": len(mats), "n_total": int(sum(ns)),
                        "n_min": int(min(ns)), "n_max": int(max(ns)), "cap_factor": CAP,
                        "lomr_iters": BATCH_ITERS, "rhs_per_matrix": BATCH_RHS,
-                       "pcg": "symmetric part of M, rtol 1e-8, maxit 1000",
+                       "pcg": "symmetric part of M, rtol 1e-8, maxit 1000, FP64 products",
                        "l2": "flushed between steps (256 MB write)", "parallelism": "replicas"},
             "e2e": {"value": ws * units / e2e_s, "unit": "matrix SPAI iterations/s",
                     "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
@@ -446,6 +453,25 @@ def profile_case(method, prec):
     r = g.run(method, 3)
     torch.cuda.synchronize()
     print(json.dumps({"profile": method, "prec": prec, "resnorm": float(r["resnorm"][-1])}))
+
+
+def profile_bpcg(prec):
+    """Launch sequence for ncu captures of the block PCG kernels: the 64-matrix
+    batch, 30 LOMR iterations, one block solve (products in `prec`)."""
+    import numpy as np
+    import torch
+
+    from paper_2511_09753_gb300 import inputs as I
+    from paper_2511_09753_gb300.spai import PREC_SPAI_SYM, SpaiBatch
+    mats = I.batch_uneven(count=64)
+    B = [np.random.default_rng(2000 + k).uniform(-1.0, 1.0, size=(BATCH_RHS, m[0]))
+         for k, m in enumerate(mats)]
+    g = SpaiBatch(mats, prec="mixed", cap_factor=CAP)
+    g.set_pcg_prec(prec)
+    g.run("lomr", BATCH_ITERS)
+    p = g.pcg_block(B, rtol=1e-8, maxit=PCG_MAXIT, precond=PREC_SPAI_SYM)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile": "bpcg", "prec": prec, "iters_max": int(p["iters"].max())}))
 
 
 def cpu_baseline(sample_iters=1):
@@ -505,12 +531,15 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline sample")
-    ap.add_argument("--profile", choices=list(METHODS), default=None,
-                    help="profiling case for ncu: 3 iterations of one method on the workload")
+    ap.add_argument("--profile", choices=list(METHODS) + ["bpcg"], default=None,
+                    help="profiling case for ncu: 3 iterations of one method on the workload, "
+                         "or (bpcg) one block PCG solve of the 64-matrix batch")
     ap.add_argument("--prec", choices=["mixed", "fp64"], default="mixed")
     ap.add_argument("--workload", choices=[WORKLOAD, "batch64"], default=WORKLOAD)
     args = ap.parse_args()
-    if args.profile:
+    if args.profile == "bpcg":
+        profile_bpcg(args.prec)
+    elif args.profile:
         profile_case(args.profile, args.prec)
     elif args.workload == "batch64" and args.impl == "ours":
         run_batch(args)

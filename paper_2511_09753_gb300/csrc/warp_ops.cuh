@@ -76,12 +76,61 @@ __device__ inline double warp_pairwise(double* t, int L, int lane) {
 // functors f(i), i < L, each lane taking i = lane, lane + 32, ...; up to
 // three sums are reduced together so their latencies overlap.
 
-__device__ __forceinline__ int term_exp(double t) {
-  uint64_t bits = (uint64_t)__double_as_longlong(t);
-  int b = (int)((bits >> 52) & 0x7ff);
-  if (b == 0 && (bits & ((1ull << 52) - 1)) == 0) return 0;
-  return b == 0 ? 1 : b;
+// A term held exactly as sign, biased FP64 exponent (0 for a zero, 1 for a
+// subnormal) and 53-bit significand (hidden bit included): the fields of the
+// FP64 number it equals.
+struct Term {
+  unsigned long long m;
+  int e;
+  int neg;
+};
+
+__device__ __forceinline__ Term term_of(double t) {
+  const unsigned long long bits = (unsigned long long)__double_as_longlong(t);
+  Term r;
+  const int b = (int)((bits >> 52) & 0x7ff);
+  r.m = bits & ((1ull << 52) - 1);
+  r.neg = (int)(bits >> 63);
+  if (b == 0) {
+    r.e = r.m ? 1 : 0;
+  } else {
+    r.e = b;
+    r.m |= 1ull << 52;
+  }
+  return r;
 }
+
+// The product of two FP32 numbers is exact in FP64 (48 significant bits), so
+// its FP64 fields follow from the integer product of the significands: the
+// same Term as term_of((double)a * (double)b), without FP64 instructions
+// (GB300's FP64 pipe is narrow).  Inf or NaN operands give an exponent of
+// 2047, so the sum comes out non-finite as in FP64.
+__device__ __forceinline__ Term term_prod(float a, float b) {
+  const uint32_t ua = __float_as_uint(a), ub = __float_as_uint(b);
+  int ea = (int)((ua >> 23) & 0xff), eb = (int)((ub >> 23) & 0xff);
+  uint32_t ma = ua & 0x7fffffu, mb = ub & 0x7fffffu;
+  Term r;
+  r.neg = (int)((ua ^ ub) >> 31);
+  if (ea == 255 || eb == 255) {
+    r.e = 2047;
+    r.m = 1ull << 52;
+    return r;
+  }
+  if (ea) ma |= 0x800000u; else ea = 1;
+  if (eb) mb |= 0x800000u; else eb = 1;
+  const unsigned long long mm = (unsigned long long)ma * mb;
+  if (mm == 0ull) {
+    r.e = 0;
+    r.m = 0ull;
+    return r;
+  }
+  const int top = 63 - __clzll((long long)mm);  // <= 47
+  r.e = top + ea + eb - 300 + 1023;              // >= 1: no FP64 subnormal arises
+  r.m = mm << (52 - top);
+  return r;
+}
+
+__device__ __forceinline__ Term term_prod(double a, double b) { return term_of(__dmul_rn(a, b)); }
 
 // 128-bit two's-complement accumulator held as (hi, lo) 64-bit limbs.
 struct Fix128 {
@@ -89,13 +138,9 @@ struct Fix128 {
   long long hi;
 };
 
-__device__ __forceinline__ void term_add(Fix128& S, double t, int eb) {
-  unsigned long long bits = (unsigned long long)__double_as_longlong(t);
-  int b = (int)((bits >> 52) & 0x7ff);
-  unsigned long long m = bits & ((1ull << 52) - 1);
-  if (b == 0) b = 1;
-  else m |= 1ull << 52;
-  const int sh = b - eb + 58;  // <= 58: the term fits in 111 bits
+__device__ __forceinline__ void term_add(Fix128& S, const Term& t, int eb) {
+  const unsigned long long m = t.m;
+  const int sh = (t.e ? t.e : 1) - eb + 58;  // <= 58: the term fits in 111 bits
   unsigned long long lo, hi;
   if (sh >= 0) {
     lo = m << sh;
@@ -104,7 +149,7 @@ __device__ __forceinline__ void term_add(Fix128& S, double t, int eb) {
     lo = (sh > -64) ? (m >> (-sh)) : 0ull;
     hi = 0ull;
   }
-  if (bits >> 63) {
+  if (t.neg) {
     unsigned long long borrow = S.lo < lo ? 1ull : 0ull;
     S.lo -= lo;
     S.hi -= (long long)(hi + borrow);
@@ -167,16 +212,16 @@ __device__ __forceinline__ double fix_to_double(Fix128 S, int eb) {
 }
 
 struct NoTerms {
-  __device__ double operator()(int) const { return 0.0; }
+  __device__ Term operator()(int) const { return Term{0ull, 0, 0}; }
 };
 
 template <int K, typename F0, typename F1 = NoTerms, typename F2 = NoTerms>
 __device__ void fixsum(double* out, int lane, const F0& f0, int L0, const F1& f1 = F1(), int L1 = 0,
                        const F2& f2 = F2(), int L2 = 0) {
   int e0 = 0, e1 = 0, e2 = 0;
-  for (int i = lane; i < L0; i += 32) e0 = max(e0, term_exp(f0(i)));
-  if (K > 1) for (int i = lane; i < L1; i += 32) e1 = max(e1, term_exp(f1(i)));
-  if (K > 2) for (int i = lane; i < L2; i += 32) e2 = max(e2, term_exp(f2(i)));
+  for (int i = lane; i < L0; i += 32) e0 = max(e0, f0(i).e);
+  if (K > 1) for (int i = lane; i < L1; i += 32) e1 = max(e1, f1(i).e);
+  if (K > 2) for (int i = lane; i < L2; i += 32) e2 = max(e2, f2(i).e);
   e0 = __reduce_max_sync(kFull, e0);
   if (K > 1) e1 = __reduce_max_sync(kFull, e1);
   if (K > 2) e2 = __reduce_max_sync(kFull, e2);
@@ -649,31 +694,26 @@ __device__ int table_to_list(const HashT& h, int cnt, int diag, int* outr, VC* o
 
 template <typename V> struct TermSq {        // x_i^2 of a list
   const V* v;
-  __device__ double operator()(int i) const {
-    double x = (double)v[i];
-    return __dmul_rn(x, x);
-  }
+  __device__ Term operator()(int i) const { return term_prod(v[i], v[i]); }
 };
 template <typename V> struct TermSqTable {   // x^2 of the occupied slots of a table
   const V* v;
   const uint16_t* occ;
-  __device__ double operator()(int i) const {
-    double x = (double)v[occ[i]];
-    return __dmul_rn(x, x);
+  __device__ Term operator()(int i) const {
+    const V x = v[occ[i]];
+    return term_prod(x, x);
   }
 };
 template <typename V> struct TermProd {      // x_i * y_i of two aligned arrays
   const V* x;
   const V* y;
-  __device__ double operator()(int i) const { return __dmul_rn((double)x[i], (double)y[i]); }
+  __device__ Term operator()(int i) const { return term_prod(x[i], y[i]); }
 };
 template <typename V> struct TermProdTable { // a[occ[i]] * y_i
   const V* a;
   const uint16_t* occ;
   const V* y;
-  __device__ double operator()(int i) const {
-    return __dmul_rn((double)a[occ[i]], (double)y[i]);
-  }
+  __device__ Term operator()(int i) const { return term_prod(a[occ[i]], y[i]); }
 };
 
 // y_i = value of row xr[i] in table h (0 if absent)
