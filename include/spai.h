@@ -54,7 +54,7 @@ extern "C" {
 
 /* --------------------------------------------------------------- options */
 enum { SPAI_FP64 = 0, SPAI_MIXED = 1 };           /* MIXED: FP32 values, FP64 reductions */
-enum { SPAI_MR = 0, SPAI_LOMR = 1, SPAI_CG = 2 };
+enum { SPAI_MR = 0, SPAI_LOMR = 1, SPAI_CG = 2, SPAI_MR_PI = 3, SPAI_LOMR_PI = 4, SPAI_CG_PI = 5 };
 enum { SPAI_DROP_NONE = 0, SPAI_DROP_TOPK_COL = 1 };
 enum { SPAI_PREC_NONE = 0, SPAI_PREC_JACOBI = 1, SPAI_PREC_SPAI = 2, SPAI_PREC_SPAI_SYM = 3 };
 
@@ -163,6 +163,16 @@ int spai_set_stream(spai_handle h, void *stream);
  *           a near-singular 2x2 system (c_i <= 64 eps uu vv) takes an MR step.
  *   CG   -- Algorithm 3: alpha_i = ||R_i||^2/(P_i, A P_i), M_{i+1} = D(M_i + alpha_i P_i),
  *           beta_{i+1} = ||R_{i+1}||^2/||R_i||^2, P_{i+1} = D(R_{i+1} + beta_{i+1} P_i).
+ *   MR_PI, LOMR_PI, CG_PI -- the left-preconditioned forms of Sec. 5 with
+ *           Pi = diag(A)^{-1} (MR_SPD Algorithm 5, LOMR_SPD Algorithm 8, CG
+ *           Algorithm 7): the direction is built from Z = Pi R (z_k = r_k / a_kk
+ *           as pi_k r_k, pi_k = 1/a_kk in FP64, rounded to the value type) and
+ *           every coefficient inner product is weighted, (X, Pi Y)_F with terms
+ *           fl(fl(x y) pi_k); CG's (P, A P) stays unweighted.  MR_PI: alpha =
+ *           (Pi R, A P)/(A P, Pi A P), P = D(Pi R).  LOMR_PI: the 2x2 system in
+ *           the Pi-weighted products, Z = D(Pi R).  CG_PI: alpha =
+ *           (R, Pi R)/(P, A P), beta = (R+, Pi R+)/(R, Pi R), P = D(Pi R + beta P).
+ *           The history still records ||R_i||_F.
  * D is the per-column hard threshold of Sec. 6.1 (keep the cap_j largest |v|,
  * ties to the smaller row; exact zeros never stored) for SPAI_DROP_TOPK_COL,
  * or the identity for SPAI_DROP_NONE (a column that outgrows its capacity

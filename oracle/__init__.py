@@ -28,7 +28,8 @@ _lock = threading.Lock()
 _lib = None
 
 MR, LOMR, CG = 0, 1, 2
-METHODS = {"mr": MR, "lomr": LOMR, "cg": CG}
+MR_PI, LOMR_PI, CG_PI = 3, 4, 5  # Section 5's forms with Pi = diag(A)^{-1} (Algorithms 5, 8, 7)
+METHODS = {"mr": MR, "lomr": LOMR, "cg": CG, "mr_pi": MR_PI, "lomr_pi": LOMR_PI, "cg_pi": CG_PI}
 FLAG_CONVERGED, FLAG_FALLBACK, FLAG_NONFINITE = 1, 2, 4
 DROP_NONE, DROP_TOPK, DROP_DIRECTIONS = 0, 1, 2
 

@@ -55,6 +55,11 @@
 #define ORC_MR 0
 #define ORC_LOMR 1
 #define ORC_CG 2
+/* Section 5's left-preconditioned variants with Pi = diag(A)^{-1}:
+   MR_SPD (Algorithm 5), LOMR_SPD (Algorithm 8), CG (Algorithm 7) */
+#define ORC_MR_PI 3
+#define ORC_LOMR_PI 4
+#define ORC_CG_PI 5
 
 #define ORC_FLAG_CONVERGED 1
 #define ORC_FLAG_FALLBACK 2
@@ -71,6 +76,7 @@ typedef struct {
   int *rowptr, *colind;
   double *a64; /* FP64 values of A */
   double *av;  /* values used by the SPAI arithmetic (FP32-rounded if mixed) */
+  double *pi;  /* pi_k = 1 / a_kk in FP64: the diagonal of Pi = diag(A)^{-1} */
   int mixed;
   int *capj;   /* per-column cap */
   /* iterates */
@@ -78,7 +84,8 @@ typedef struct {
   /* method continuation state */
   int method;  /* -1 none */
   int it;      /* iterations done by current method */
-  double rr;   /* CG: ||R_i||^2 of the current residual */
+  double rr;   /* CG: numerator of alpha for the current residual, (R,R) or (R,Pi R) */
+  double rr_hist; /* CG: ||R_i||^2 of the current residual */
   int64_t spgemm_count;
   /* workspace */
   double *acc;
@@ -240,6 +247,28 @@ static double col_nrm2(const ocol *x, double *tmp) {
   return orc_fixsum(tmp, x->len);
 }
 
+/* Pi-weighted column inner product (X, Pi Y) of Section 5: each term is the
+ * product of the two values (exact for FP32 values) times pi_k, rounded in
+ * FP64, and the terms are summed exactly like col_dot's. */
+static double col_wdot(const ocol *x, const ocol *y, const double *pi, double *tmp) {
+  int a = 0, b = 0, L = 0;
+  while (a < x->len && b < y->len) {
+    if (x->row[a] < y->row[b]) a++;
+    else if (x->row[a] > y->row[b]) b++;
+    else {
+      tmp[L++] = (x->val[a] * y->val[b]) * pi[x->row[a]];
+      a++;
+      b++;
+    }
+  }
+  return orc_fixsum(tmp, L);
+}
+
+static double col_wnrm2(const ocol *x, const double *pi, double *tmp) {
+  for (int a = 0; a < x->len; a++) tmp[a] = (x->val[a] * x->val[a]) * pi[x->row[a]];
+  return orc_fixsum(tmp, x->len);
+}
+
 /* ------------------------------------------------------------- operations */
 
 /* out = A X_j (Sec. 6.2: one SpGEMM column) */
@@ -292,6 +321,16 @@ static void residual_col(orc_state *s, int j, const ocol *am, ocol *out) {
       v = -sv;
     }
     if (v != 0.0) col_push(out, r, v);
+  }
+}
+
+/* Z_j = (Pi R)_j: z_k = pi_k r_k in FP64, rounded to the value type, exact
+ * zeros removed (Algorithms 5, 7, 8: Z := Pi R) */
+static void pi_col(orc_state *s, const ocol *r, ocol *out) {
+  out->len = 0;
+  for (int e = 0; e < r->len; e++) {
+    double z = rv(s, s->pi[r->row[e]] * r->val[e]);
+    if (z != 0.0) col_push(out, r->row[e], z);
   }
 }
 
@@ -392,7 +431,7 @@ orc_state *orc_new(int n, const int *rowptr, const int *colind, const double *va
   memcpy(s->a64, vals, sizeof(double) * (size_t)nnz);
   s->mixed = mixed;
   for (int64_t q = 0; q < nnz; q++) s->av[q] = mixed ? (double)(float)vals[q] : vals[q];
-  s->capj = (int *)malloc(sizeof(int) * (size_t)(n ? n : 1));
+  s->capj = (int *)malloc(sizeof(int) * (size_t)(n > 0 ? n : 1));
   for (int j = 0; j < n; j++) {
     double c = floor(cap_factor * (double)(rowptr[j + 1] - rowptr[j]));
     if (!(c >= 1.0)) c = 1.0;
@@ -402,10 +441,17 @@ orc_state *orc_new(int n, const int *rowptr, const int *colind, const double *va
   s->M = mat_new(n);
   s->P = mat_new(n);
   s->Z = mat_new(n);
-  s->acc = (double *)calloc((size_t)(n ? n : 1), sizeof(double));
-  s->seen = (char *)calloc((size_t)(n ? n : 1), 1);
-  s->touched = (int *)malloc(sizeof(int) * (size_t)(n ? n : 1));
+  s->acc = (double *)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
+  s->seen = (char *)calloc((size_t)(n > 0 ? n : 1), 1);
+  s->touched = (int *)malloc(sizeof(int) * (size_t)(n > 0 ? n : 1));
   s->method = -1;
+  s->pi = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+  for (int j = 0; j < n; j++) {
+    double d = 0.0;
+    for (int q = rowptr[j]; q < rowptr[j + 1]; q++)
+      if (colind[q] == j) d = vals[q];
+    s->pi[j] = 1.0 / d;
+  }
   /* M_0 = diag(A)^{-1} */
   for (int j = 0; j < n; j++) {
     double d = 0.0;
@@ -426,6 +472,7 @@ void orc_free(orc_state *s) {
   free(s->colind);
   free(s->a64);
   free(s->av);
+  free(s->pi);
   free(s->capj);
   free(s->acc);
   free(s->seen);
@@ -501,10 +548,17 @@ static int isfin(double x) { return !isnan(x) && !isinf(x); }
  *   resnorm[0..iters]: ||R_i||_F (entries past an early stop are left alone)
  *   coef[2*i], coef[2*i+1]: (alpha_i, 0) for MR, (delta_i, gamma_i) for
  *   LOMR, (alpha_i, beta_{i+1}) for CG.
+ * ORC_MR_PI / ORC_LOMR_PI / ORC_CG_PI run the Pi-preconditioned forms
+ * (Algorithms 5, 8, 7 with Pi = diag(A)^{-1}): the direction is built from
+ * Z = Pi R instead of R, and every coefficient inner product is the
+ * Pi-weighted one; (P, A P) of CG stays unweighted, and resnorm still
+ * records ||R_i||_F.
  * Returns the number of iterations done; *flags gets ORC_FLAG_* bits.
  */
 int orc_run(orc_state *s, int method, int iters, int drop, double *resnorm, double *coef, int *flags) {
   int n = s->n;
+  const int use_pi = method >= ORC_MR_PI;
+  const int base = use_pi ? method - ORC_MR_PI : method;
   int done = 0;
   *flags = 0;
   int cont = (s->method == method);
@@ -518,28 +572,30 @@ int orc_run(orc_state *s, int method, int iters, int drop, double *resnorm, doub
   }
   ocol *R = mat_new(n), *Q = mat_new(n), *U = mat_new(n), *V = mat_new(n), *S = mat_new(n);
   ocol tmpc = {0};
-  double *partial = (double *)malloc(sizeof(double) * (size_t)(n ? n : 1));
-  double *p2 = (double *)malloc(sizeof(double) * (size_t)(n ? n : 1));
-  double *p3 = (double *)malloc(sizeof(double) * (size_t)(n ? n : 1));
-  double *p4 = (double *)malloc(sizeof(double) * (size_t)(n ? n : 1));
-  double *p5 = (double *)malloc(sizeof(double) * (size_t)(n ? n : 1));
-  double *tmp = (double *)malloc(sizeof(double) * (size_t)(n ? n : 1) * 2);
+  double *partial = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+  double *p2 = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+  double *p3 = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+  double *p4 = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+  double *p5 = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+  double *tmp = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1) * 2);
   int dropM = (drop == 1), dropD = (drop >= 1);
 
-  if (method == ORC_MR) {
-    /* Algorithm 1 with explicit residual, P_i = D(R_i) */
+  if (base == ORC_MR) {
+    /* Algorithm 1 with explicit residual, P_i = D(R_i); with Pi
+       (Algorithm 5): P_i = D(Pi R_i), alpha = (Pi R, A P) / (A P, Pi A P) */
     for (int i = 0; i < iters; i++) {
       double rr = residual_all(s, R, partial, tmp);
       resnorm[i] = sqrt(rr);
       if (rr == 0.0) { *flags |= ORC_FLAG_CONVERGED; break; }
       for (int j = 0; j < n; j++) {
-        col_copy(&s->P[j], &R[j]);
+        if (use_pi) pi_col(s, &R[j], &s->P[j]);
+        else col_copy(&s->P[j], &R[j]);
         if (dropD) drop_col(&s->P[j], s->capj[j]);
       }
       product_all(s, s->P, Q);
       for (int j = 0; j < n; j++) {
-        p2[j] = col_dot(&R[j], &Q[j], tmp);
-        p3[j] = col_nrm2(&Q[j], tmp);
+        p2[j] = use_pi ? col_wdot(&R[j], &Q[j], s->pi, tmp) : col_dot(&R[j], &Q[j], tmp);
+        p3[j] = use_pi ? col_wnrm2(&Q[j], s->pi, tmp) : col_nrm2(&Q[j], tmp);
       }
       double rq = pairwise64(p2, n), qq = pairwise64(p3, n);
       if (qq == 0.0) { *flags |= ORC_FLAG_CONVERGED; break; }
@@ -556,7 +612,7 @@ int orc_run(orc_state *s, int method, int iters, int drop, double *resnorm, doub
       s->it++;
     }
     if (done == iters) resnorm[iters] = sqrt(residual_all(s, R, partial, tmp));
-  } else if (method == ORC_LOMR) {
+  } else if (base == ORC_LOMR) {
     /* Algorithm 4 with explicit residual: Z_i = D(R_i), P_i = D(S_i),
        M_{i+1} = D(M_i + S_i), S_i = delta Z_i + gamma P_{i-1}. s->P holds
        P_{i-1} between iterations. */
@@ -565,17 +621,26 @@ int orc_run(orc_state *s, int method, int iters, int drop, double *resnorm, doub
       resnorm[i] = sqrt(rr);
       if (rr == 0.0) { *flags |= ORC_FLAG_CONVERGED; break; }
       for (int j = 0; j < n; j++) {
-        col_copy(&s->Z[j], &R[j]);
+        if (use_pi) pi_col(s, &R[j], &s->Z[j]);
+        else col_copy(&s->Z[j], &R[j]);
         if (dropD) drop_col(&s->Z[j], s->capj[j]);
       }
       product_all(s, s->Z, U);
       product_all(s, s->P, V);
       for (int j = 0; j < n; j++) {
-        partial[j] = col_nrm2(&U[j], tmp);
-        p2[j] = col_nrm2(&V[j], tmp);
-        p3[j] = col_dot(&U[j], &V[j], tmp);
-        p4[j] = col_dot(&U[j], &R[j], tmp);
-        p5[j] = col_dot(&V[j], &R[j], tmp);
+        if (use_pi) { /* Algorithm 8: (AZ, Pi AZ), ..., (Pi R, AZ), (Pi R, AP) */
+          partial[j] = col_wnrm2(&U[j], s->pi, tmp);
+          p2[j] = col_wnrm2(&V[j], s->pi, tmp);
+          p3[j] = col_wdot(&U[j], &V[j], s->pi, tmp);
+          p4[j] = col_wdot(&U[j], &R[j], s->pi, tmp);
+          p5[j] = col_wdot(&V[j], &R[j], s->pi, tmp);
+        } else {
+          partial[j] = col_nrm2(&U[j], tmp);
+          p2[j] = col_nrm2(&V[j], tmp);
+          p3[j] = col_dot(&U[j], &V[j], tmp);
+          p4[j] = col_dot(&U[j], &R[j], tmp);
+          p5[j] = col_dot(&V[j], &R[j], tmp);
+        }
       }
       double uu = pairwise64(partial, n), vv = pairwise64(p2, n), uv = pairwise64(p3, n);
       double ur = pairwise64(p4, n), vr = pairwise64(p5, n);
@@ -609,27 +674,38 @@ int orc_run(orc_state *s, int method, int iters, int drop, double *resnorm, doub
       s->it++;
     }
     if (done == iters) resnorm[iters] = sqrt(residual_all(s, R, partial, tmp));
-  } else if (method == ORC_CG) {
+  } else if (base == ORC_CG) {
     /* Algorithm 3 with explicit residual: P_0 = D(R_0),
-       P_{i+1} = D(R_{i+1} + beta P_i).  s->P holds P_i, s->rr ||R_i||^2. */
-    double rr;
+       P_{i+1} = D(R_{i+1} + beta P_i).  With Pi (Algorithm 7): Z = Pi R,
+       P_0 = D(Z_0), P_{i+1} = D(Z_{i+1} + beta P_i), alpha = (R, Z)/(P, AP),
+       beta = (R_{i+1}, Z_{i+1}) / (R_i, Z_i).  s->P holds P_i, s->rr the
+       numerator (R_i, R_i) or (R_i, Pi R_i). */
+    double rz;
     if (!cont || s->it == 0) {
-      rr = residual_all(s, R, partial, tmp);
+      double rr0 = residual_all(s, R, partial, tmp);
+      resnorm[0] = sqrt(rr0);
+      if (use_pi) {
+        for (int j = 0; j < n; j++) partial[j] = col_wnrm2(&R[j], s->pi, tmp);
+        rz = pairwise64(partial, n);
+      } else {
+        rz = rr0;
+      }
       for (int j = 0; j < n; j++) {
-        col_copy(&s->P[j], &R[j]);
+        if (use_pi) pi_col(s, &R[j], &s->P[j]);
+        else col_copy(&s->P[j], &R[j]);
         if (dropD) drop_col(&s->P[j], s->capj[j]);
       }
     } else {
-      rr = s->rr;
+      rz = s->rr;
+      resnorm[0] = sqrt(s->rr_hist);
     }
-    resnorm[0] = sqrt(rr);
     for (int i = 0; i < iters; i++) {
-      if (rr == 0.0) { *flags |= ORC_FLAG_CONVERGED; break; }
+      if (rz == 0.0) { *flags |= ORC_FLAG_CONVERGED; break; }
       product_all(s, s->P, Q);
       for (int j = 0; j < n; j++) p2[j] = col_dot(&s->P[j], &Q[j], tmp);
       double pq = pairwise64(p2, n);
       if (pq == 0.0) { *flags |= ORC_FLAG_CONVERGED; break; }
-      double alpha = rr / pq;
+      double alpha = rz / pq;
       if (!isfin(alpha)) { *flags |= ORC_FLAG_NONFINITE; break; }
       for (int j = 0; j < n; j++) {
         combine_col(s, COMB_AXPY, alpha, 0.0, &s->M[j], &s->P[j], &tmpc);
@@ -638,19 +714,30 @@ int orc_run(orc_state *s, int method, int iters, int drop, double *resnorm, doub
       }
       double rr1 = residual_all(s, R, partial, tmp);
       resnorm[i + 1] = sqrt(rr1);
-      double beta = rr1 / rr;
+      double rz1 = rr1;
+      if (use_pi) {
+        for (int j = 0; j < n; j++) partial[j] = col_wnrm2(&R[j], s->pi, tmp);
+        rz1 = pairwise64(partial, n);
+      }
+      double beta = rz1 / rz;
       coef[2 * i] = alpha;
       coef[2 * i + 1] = beta;
       done++;
       s->it++;
-      s->rr = rr1;
-      if (rr1 == 0.0) { *flags |= ORC_FLAG_CONVERGED; rr = rr1; break; }
+      s->rr = rz1;
+      s->rr_hist = rr1;
+      if (rz1 == 0.0) { *flags |= ORC_FLAG_CONVERGED; rz = rz1; break; }
       for (int j = 0; j < n; j++) {
-        combine_col(s, COMB_AXPY, beta, 0.0, &R[j], &s->P[j], &tmpc);
+        if (use_pi) {
+          pi_col(s, &R[j], &S[j]);
+          combine_col(s, COMB_AXPY, beta, 0.0, &S[j], &s->P[j], &tmpc);
+        } else {
+          combine_col(s, COMB_AXPY, beta, 0.0, &R[j], &s->P[j], &tmpc);
+        }
         if (dropD) drop_col(&tmpc, s->capj[j]);
         col_copy(&s->P[j], &tmpc);
       }
-      rr = rr1;
+      rz = rz1;
     }
   }
   if (*flags & (ORC_FLAG_CONVERGED | ORC_FLAG_NONFINITE)) s->method = -1;
@@ -677,8 +764,8 @@ double orc_residual_norm(orc_state *s) {
   s->av = s->a64;
   s->mixed = 0;
   ocol am = {0}, r = {0};
-  double *partial = (double *)malloc(sizeof(double) * (size_t)(n ? n : 1));
-  double *tmp = (double *)malloc(sizeof(double) * (size_t)(n ? n : 1) * 2);
+  double *partial = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+  double *tmp = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1) * 2);
   for (int j = 0; j < n; j++) {
     spgemm_col(s, &s->M[j], &am);
     residual_col(s, j, &am, &r);
@@ -813,7 +900,7 @@ int orc_pcg(int n, const int *rp, const int *ci, const double *av, int precond, 
     int nnz = rp[n];
     av32 = (float *)malloc(sizeof(float) * (size_t)(nnz ? nnz : 1));
     for (int e = 0; e < nnz; e++) av32[e] = (float)av[e];
-    x32 = (float *)malloc(sizeof(float) * (size_t)(n ? n : 1));
+    x32 = (float *)malloc(sizeof(float) * (size_t)(n > 0 ? n : 1));
     if (mrp) {
       int mnz = mrp[n];
       mv32 = (float *)malloc(sizeof(float) * (size_t)(mnz ? mnz : 1));

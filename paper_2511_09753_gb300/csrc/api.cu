@@ -79,6 +79,11 @@ struct spai_ctx {
   unsigned *d_cnt1 = nullptr, *d_cnt2 = nullptr;
   int red_nb = 0, red_ng = 0;
   PassCfg cfg[5];
+  // Pi-preconditioned forms: pi_k = 1 / a_kk, and the pass shapes of their
+  // (larger) per-warp layouts for MR, LOMR, CG-A, CG-B
+  double* d_pi = nullptr;
+  PassCfg cfg_pi[4];
+  bool pi_ok = false;
   // batched mode: nseg matrices laid block-diagonally, each padded with
   // identity rows/columns to a multiple of kSegAlign
   int nseg = 0;
@@ -188,7 +193,7 @@ int next_pow2(int x) {
 }
 
 // Per-warp scratch layout of a pass kind.
-WarpLayout make_layout(int kind, int vc, int CAP, int W, bool dia) {
+WarpLayout make_layout(int kind, int vc, int CAP, int W, bool dia, bool pi = false) {
   WarpLayout L;
   memset(&L, 0, sizeof(L));
   const int PMAX = CAP * W;
@@ -249,6 +254,8 @@ WarpLayout make_layout(int kind, int vc, int CAP, int W, bool dia) {
   L.Ur = take(lomr ? 4 * LMAX : 0);
   L.Uv = take(lomr ? vc * LMAX : 0);
   L.hist = take(4 * 128);  // 256 packed 16-bit bins
+  L.zr = take(pi ? 4 * LMAX : 0);
+  L.zv = take(pi ? vc * LMAX : 0);
   L.bytes = o;
   return L;
 }
@@ -265,10 +272,10 @@ static int env_int(const char* name, int dflt) {
 }
 
 PassCfg make_cfg(int kind, int vc, int n, int CAP, int W, bool dia, int smem_max, int Bmin = 1,
-                 int Bmax = 1024) {
+                 int Bmax = 1024, bool pi = false) {
   PassCfg c;
   memset(&c, 0, sizeof(c));
-  c.lay = make_layout(kind, vc, CAP, W, dia);
+  c.lay = make_layout(kind, vc, CAP, W, dia, pi);
   const int nq = 6;
   const int extra_fixed = 8 * 1024;  // reduction scratch (1024 doubles)
   // defaults measured on GB300 (64^3 operator, cap 3): LOMR's large scratch
@@ -339,7 +346,10 @@ cudaError_t timed_launch(spai_ctx* h, const PassParams& p, const PassCfg& c, boo
     }
   }
   cudaError_t err;
-  if (res && h->prec == SPAI_MIXED)
+  if (p.pi)
+    err = h->prec == SPAI_MIXED ? launch_colpass_pi_f32(p, c.grid, 32 * c.NW, c.smem, h->stream)
+                                : launch_colpass_pi_f64(p, c.grid, 32 * c.NW, c.smem, h->stream);
+  else if (res && h->prec == SPAI_MIXED)
     err = launch_colpass_res_f32(p, c.grid, 32 * c.NW, c.smem, h->stream);
   else if (res || h->prec == SPAI_FP64)
     err = launch_colpass_f64(p, c.grid, 32 * c.NW, c.smem, h->stream);
@@ -360,10 +370,11 @@ void collect_timing(spai_ctx* h) {
   h->ev_used = 0;
 }
 
-PassParams base_params(spai_ctx* h, int kind, bool res) {
+PassParams base_params(spai_ctx* h, int kind, bool res, bool pi = false) {
   PassParams p;
   memset(&p, 0, sizeof(p));
-  const PassCfg& c = h->cfg[kind];
+  const PassCfg& c = pi ? h->cfg_pi[kind] : h->cfg[kind];
+  p.pi = pi ? h->d_pi : nullptr;
   p.n = h->n;
   p.W = h->W;
   p.magicW = h->magicW;
@@ -424,6 +435,7 @@ void free_all(spai_ctx* h) {
   dfree(h->d_colind);
   dfree(h->d_vals);
   dfree(h->d_diag);
+  dfree(h->d_pi);
   dfree(h->d_ell_col);
   dfree(h->d_ell32);
   dfree(h->d_ell64);
@@ -851,12 +863,30 @@ int create_impl(spai_handle* out, int64_t n, int64_t nnz, const int32_t* rp, con
     h->red_nb = std::max(h->red_nb, h->cfg[k].nb);
     h->red_ng = std::max(h->red_ng, h->cfg[k].ngroups);
   }
+  h->pi_ok = true;
+  for (int k = 0; k < 4; k++) {
+    int Bmin = 1, Bmax = 1024;
+    if (bd) {
+      long long npmax = 0;
+      for (int m = 0; m < bd->nseg; m++) npmax = std::max(npmax, bd->npad[m]);
+      while ((long long)Bmin * 1024 < npmax) Bmin *= 2;
+      Bmax = kSegAlign;
+    }
+    h->cfg_pi[k] = make_cfg(k, vc, (int)n, capmax, W, h->dia, smem_max, Bmin, Bmax, true);
+    if (!h->cfg_pi[k].ok) {
+      h->pi_ok = false;
+      continue;
+    }
+    h->red_nb = std::max(h->red_nb, h->cfg_pi[k].nb);
+    h->red_ng = std::max(h->red_ng, h->cfg_pi[k].ngroups);
+  }
   const size_t vs = h->prec == SPAI_MIXED ? 4 : 8;
   rc = SPAI_OK;
   rc = rc ? rc : dalloc(&h->d_rowptr, n + 1);
   rc = rc ? rc : dalloc(&h->d_colind, nnz);
   rc = rc ? rc : dalloc(&h->d_vals, nnz);
   rc = rc ? rc : dalloc(&h->d_diag, n);
+  rc = rc ? rc : dalloc(&h->d_pi, n);
   rc = rc ? rc : dalloc(&h->d_ell_col, (size_t)n * W);
   rc = rc ? rc : dalloc(&h->d_ell64, (size_t)n * W);
   if (h->prec == SPAI_MIXED) rc = rc ? rc : dalloc(&h->d_ell32, (size_t)n * W);
@@ -907,6 +937,9 @@ int create_impl(spai_handle* out, int64_t n, int64_t nnz, const int32_t* rp, con
   ok &= cudaMemcpyAsync(h->d_colind, ci, sizeof(int) * nnz, cudaMemcpyHostToDevice, st) == 0;
   ok &= cudaMemcpyAsync(h->d_vals, va, sizeof(double) * nnz, cudaMemcpyHostToDevice, st) == 0;
   ok &= cudaMemcpyAsync(h->d_diag, diag.data(), sizeof(double) * n, cudaMemcpyHostToDevice, st) == 0;
+  std::vector<double> piv(n);
+  for (int64_t i = 0; i < n; i++) piv[i] = 1.0 / diag[i];
+  ok &= cudaMemcpyAsync(h->d_pi, piv.data(), sizeof(double) * n, cudaMemcpyHostToDevice, st) == 0;
   ok &= cudaMemcpyAsync(h->d_ell_col, ecol.data(), sizeof(int) * ecol.size(), cudaMemcpyHostToDevice,
                         st) == 0;
   ok &= cudaMemcpyAsync(h->d_ell64, e64.data(), sizeof(double) * e64.size(), cudaMemcpyHostToDevice,
@@ -1086,8 +1119,10 @@ int spai_reset(spai_handle h) {
 }
 
 int spai_run(spai_handle h, int method, int iters, int drop_rule, spai_history* hist) {
-  if (!h || iters < 0 || (method != SPAI_MR && method != SPAI_LOMR && method != SPAI_CG))
-    return SPAI_ERR_ARG;
+  if (!h || iters < 0 || method < SPAI_MR || method > SPAI_CG_PI) return SPAI_ERR_ARG;
+  const bool pim = method >= SPAI_MR_PI;  // Section 5's forms with Pi = diag(A)^{-1}
+  if (pim && !h->pi_ok) return SPAI_ERR_UNSUPPORTED;
+  const int base = pim ? method - SPAI_MR_PI : method;
   if (drop_rule != SPAI_DROP_NONE && drop_rule != SPAI_DROP_TOPK_COL) return SPAI_ERR_ARG;
   const int nh = std::max(h->nseg, 1);
   int rc = ensure_hist(h, (iters + 1) * nh);
@@ -1109,16 +1144,16 @@ int spai_run(spai_handle h, int method, int iters, int drop_rule, spai_history* 
   invalidate_rows(h);
   const int drop = drop_rule == SPAI_DROP_TOPK_COL ? 1 : 0;
   auto pass = [&](int kind, int upd, int dir, int iter, int fresh_b) -> cudaError_t {
-    PassParams p = base_params(h, kind, false);
+    PassParams p = base_params(h, kind, false, pim);
     p.do_update = upd;
     p.do_dir = dir;
     p.drop = drop;
     p.iter = iter;
     p.fresh = fresh_b;
-    return timed_launch(h, p, h->cfg[kind], false);
+    return timed_launch(h, p, pim ? h->cfg_pi[kind] : h->cfg[kind], false);
   };
-  if (method == SPAI_MR || method == SPAI_LOMR) {
-    const int kind = method == SPAI_MR ? kMR : kLOMR;
+  if (base == SPAI_MR || base == SPAI_LOMR) {
+    const int kind = base == SPAI_MR ? kMR : kLOMR;
     if (iters == 0) {
       CK(pass(kind, 0, 0, 0, 0));
     } else {

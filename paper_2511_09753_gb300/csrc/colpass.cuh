@@ -83,7 +83,9 @@ __device__ __forceinline__ int spgemm(const PassParams& p, const HashT& h, int* 
 }
 
 // Column work of one pass.  part[0..nq) receives the column partials.
-template <typename VS, typename VC>
+// PI: the Pi-preconditioned forms (Algorithms 5, 7, 8 with Pi = diag(A)^{-1}):
+// directions from Z = Pi R, Pi-weighted coefficient inner products.
+template <typename VS, typename VC, bool PI>
 __device__ void column_work(ColCtx<VS, VC>& c, int j, double* part) {
   const PassParams& p = c.p;
   const WarpLayout& L = p.lay;
@@ -142,15 +144,26 @@ __device__ void column_work(ColCtx<VS, VC>& c, int j, double* part) {
       fixsum<1>(part, lane, TermSq<VC>{Rv}, LR);
       return;
     }
-    int Lp = warp_select(Rr, Rv, LR, cap, Pr, Pv, hist, tie, p.drop, ovf, lane);
+    int Lp;
+    if (PI) {  // P = D(Pi R) (Algorithm 5)
+      int* Zr = c.template at<int>(L.zr);
+      VC* Zv = c.template at<VC>(L.zv);
+      int Lz = list_scale_pi(Rr, Rv, LR, p.pi, Zr, Zv, lane);
+      Lp = warp_select(Zr, Zv, Lz, cap, Pr, Pv, hist, tie, p.drop, ovf, lane);
+    } else {
+      Lp = warp_select(Rr, Rv, LR, cap, Pr, Pv, hist, tie, p.drop, ovf, lane);
+    }
     store_col(c, p.Prow, p.Pval, p.Plen, j, off, Lp, Pr, Pv);
     int cq = spgemm(p, ha, Pr, Pv, Lp, -1, Tr, Tv, lane, c.seg);  // table holds Q = A P
     c.spg++;
     lookup_list(Rr, LR, ha, yc, lane);                      // Q at the rows of R
     __syncwarp();
-    // (R,R), (R,Q), (Q,Q)
-    fixsum<3>(part, lane, TermSq<VC>{Rv}, LR, TermProd<VC>{Rv, yc}, LR,
-              TermSqTable<VC>{(const VC*)ha.val, ha.occ}, cq);
+    if (PI)  // (R,R), (R,Pi Q), (Q,Pi Q)
+      fixsum<3>(part, lane, TermSq<VC>{Rv}, LR, TermWProd<VC>{Rr, Rv, yc, p.pi}, LR,
+                TermWSqTable<VC>{ha.key, (const VC*)ha.val, ha.occ, p.pi}, cq);
+    else     // (R,R), (R,Q), (Q,Q)
+      fixsum<3>(part, lane, TermSq<VC>{Rv}, LR, TermProd<VC>{Rv, yc}, LR,
+                TermSqTable<VC>{(const VC*)ha.val, ha.occ}, cq);
     hash_clear(ha, cq, lane);
     return;
   }
@@ -187,15 +200,27 @@ __device__ void column_work(ColCtx<VS, VC>& c, int j, double* part) {
       hash_clear(ha, cr, lane);
       return;
     }
-    int Lz = warp_select(Rr, Rv, LR, cap, Zr, Zv, hist, tie, p.drop, ovf, lane);
+    int Lz;
+    if (PI) {  // Z = D(Pi R) (Algorithm 8)
+      int* Xr = c.template at<int>(L.zr);
+      VC* Xv = c.template at<VC>(L.zv);
+      int Lx = list_scale_pi(Rr, Rv, LR, p.pi, Xr, Xv, lane);
+      Lz = warp_select(Xr, Xv, Lx, cap, Zr, Zv, hist, tie, p.drop, ovf, lane);
+    } else {
+      Lz = warp_select(Rr, Rv, LR, cap, Zr, Zv, hist, tie, p.drop, ovf, lane);
+    }
     store_col(c, p.Zrow, p.Zval, p.Zlen, j, off, Lz, Zr, Zv);
     int cu = spgemm(p, hb, Zr, Zv, Lz, -1, Tr, Tv, lane, c.seg);   // table B: U = A Z
     lookup_table(hb, cu, ha, yc, lane);                     // R at the rows of U
     __syncwarp();
     double t3[3];
-    // (R,R), (U,U), (U,R)
-    fixsum<3>(t3, lane, TermSq<VC>{Rv}, LR, TermSqTable<VC>{(const VC*)hb.val, hb.occ}, cu,
-              TermProdTable<VC>{(const VC*)hb.val, hb.occ, yc}, cu);
+    if (PI)  // (R,R), (U,Pi U), (U,Pi R)
+      fixsum<3>(t3, lane, TermSq<VC>{Rv}, LR,
+                TermWSqTable<VC>{hb.key, (const VC*)hb.val, hb.occ, p.pi}, cu,
+                TermWProdTable<VC>{hb.key, (const VC*)hb.val, hb.occ, yc, p.pi}, cu);
+    else     // (R,R), (U,U), (U,R)
+      fixsum<3>(t3, lane, TermSq<VC>{Rv}, LR, TermSqTable<VC>{(const VC*)hb.val, hb.occ}, cu,
+                TermProdTable<VC>{(const VC*)hb.val, hb.occ, yc}, cu);
     part[0] = t3[0];
     part[1] = t3[1];
     part[4] = t3[2];
@@ -206,9 +231,13 @@ __device__ void column_work(ColCtx<VS, VC>& c, int j, double* part) {
     lookup_list(Ur, LU, hb, yc, lane);                      // V at the rows of U
     lookup_table(hb, cv, ha, yc2, lane);                    // R at the rows of V
     __syncwarp();
-    // (V,V), (U,V), (V,R)
-    fixsum<3>(t3, lane, TermSqTable<VC>{(const VC*)hb.val, hb.occ}, cv, TermProd<VC>{Uv, yc}, LU,
-              TermProdTable<VC>{(const VC*)hb.val, hb.occ, yc2}, cv);
+    if (PI)  // (V,Pi V), (U,Pi V), (V,Pi R)
+      fixsum<3>(t3, lane, TermWSqTable<VC>{hb.key, (const VC*)hb.val, hb.occ, p.pi}, cv,
+                TermWProd<VC>{Ur, Uv, yc, p.pi}, LU,
+                TermWProdTable<VC>{hb.key, (const VC*)hb.val, hb.occ, yc2, p.pi}, cv);
+    else     // (V,V), (U,V), (V,R)
+      fixsum<3>(t3, lane, TermSqTable<VC>{(const VC*)hb.val, hb.occ}, cv, TermProd<VC>{Uv, yc}, LU,
+                TermProdTable<VC>{(const VC*)hb.val, hb.occ, yc2}, cv);
     part[2] = t3[0];
     part[3] = t3[1];
     part[5] = t3[2];
@@ -227,7 +256,10 @@ __device__ void column_work(ColCtx<VS, VC>& c, int j, double* part) {
     int LR = table_to_list(ha, cr, j, Rr, Rv, lane);
     hash_clear(ha, cr, lane);
     c.spg++;
-    fixsum<1>(part, lane, TermSq<VC>{Rv}, LR);
+    if (PI)  // (R,R), (R,Pi R)
+      fixsum<2>(part, lane, TermSq<VC>{Rv}, LR, TermWSq<VC>{Rr, Rv, p.pi}, LR);
+    else
+      fixsum<1>(part, lane, TermSq<VC>{Rv}, LR);
     return;
   }
 
@@ -239,15 +271,26 @@ __device__ void column_work(ColCtx<VS, VC>& c, int j, double* part) {
     hash_clear(ha, cr, lane);
     c.spg++;
     CombAxpy<VC> f{c.sc->beta};
-    int Lt = warp_union(un, Rr, Rv, LR, Pr, Pv, Lp, Tr, Tv, f, lane);
+    int Lt;
+    if (PI) {  // P = D(Pi R + beta P) (Algorithm 7)
+      int* Zr = c.template at<int>(L.zr);
+      VC* Zv = c.template at<VC>(L.zv);
+      int Lz = list_scale_pi(Rr, Rv, LR, p.pi, Zr, Zv, lane);
+      Lt = warp_union(un, Zr, Zv, Lz, Pr, Pv, Lp, Tr, Tv, f, lane);
+    } else {
+      Lt = warp_union(un, Rr, Rv, LR, Pr, Pv, Lp, Tr, Tv, f, lane);
+    }
     Lp = warp_select(Tr, Tv, Lt, cap, Pr, Pv, hist, tie, p.drop, ovf, lane);
     store_col(c, p.Prow, p.Pval, p.Plen, j, off, Lp, Pr, Pv);
     int cq = spgemm(p, ha, Pr, Pv, Lp, -1, Tr, Tv, lane, c.seg);  // table holds Q = A P
     c.spg++;
     lookup_list(Pr, Lp, ha, yc, lane);                     // Q at the rows of P
     __syncwarp();
-    // (R,R), (P,Q)
-    fixsum<2>(part, lane, TermSq<VC>{Rv}, LR, TermProd<VC>{Pv, yc}, Lp);
+    if (PI)  // (R,R), (P,Q), (R,Pi R)
+      fixsum<3>(part, lane, TermSq<VC>{Rv}, LR, TermProd<VC>{Pv, yc}, Lp,
+                TermWSq<VC>{Rr, Rv, p.pi}, LR);
+    else     // (R,R), (P,Q)
+      fixsum<2>(part, lane, TermSq<VC>{Rv}, LR, TermProd<VC>{Pv, yc}, Lp);
     hash_clear(ha, cq, lane);
   }
 }
@@ -327,8 +370,9 @@ __device__ inline void coefficients(const PassParams& p, DevScalars* sc, double*
     return;
   }
   if (p.kind == kCGB) {
-    double rr = t[0], pq = t[1];
-    if (p.fresh && hist_res) hist_res[0] = __dsqrt_rn(rr);
+    // alpha = (R, R) / (P, AP), or (R, Pi R) / (P, AP) with Pi
+    double rr = p.pi ? t[2] : t[0], pq = t[1];
+    if (p.fresh && hist_res) hist_res[0] = __dsqrt_rn(t[0]);
     if (rr == 0.0 || pq == 0.0) {
       sc->stop = 1;
       sc->flags |= kFlagConverged;
@@ -344,11 +388,11 @@ __device__ inline void coefficients(const PassParams& p, DevScalars* sc, double*
     sc->rr = rr;
     return;
   }
-  // kCGA
+  // kCGA: beta = (R+, R+) / (R, R), or the Pi-weighted ratio with Pi
   {
-    double rr1 = t[0];
+    double rr1 = p.pi ? t[1] : t[0];
     double beta = __ddiv_rn(rr1, sc->rr);
-    if (hist_res) hist_res[it + 1] = __dsqrt_rn(rr1);
+    if (hist_res) hist_res[it + 1] = __dsqrt_rn(t[0]);
     if (hist_coef) {
       hist_coef[2 * it] = sc->alpha;
       hist_coef[2 * it + 1] = beta;
@@ -363,7 +407,7 @@ __device__ inline void coefficients(const PassParams& p, DevScalars* sc, double*
   }
 }
 
-template <typename VS, typename VC>
+template <typename VS, typename VC, bool PI>
 __global__ void __launch_bounds__(256, 3) colpass_kernel(const PassParams p) {
   extern __shared__ __align__(16) char smem[];
   const int seg = p.nseg ? p.seg_of_col[(long long)blockIdx.x * p.B] : -1;
@@ -371,7 +415,7 @@ __global__ void __launch_bounds__(256, 3) colpass_kernel(const PassParams p) {
   if (sc->stop) return;  // set by an earlier pass for this matrix
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
-  const int nq = p.do_dir ? pass_nq(p.kind) : 1;
+  const int nq = p.do_dir ? pass_nq(p.kind, PI) : 1;
   double* part = (double*)(smem + p.part_off);  // [nq][B]
   double* red = (double*)(smem + p.red_off);    // reduction scratch (>= 1024 doubles)
   ColCtx<VS, VC> c(p, smem + warp * p.lay.bytes, lane, sc, seg);
@@ -395,7 +439,7 @@ __global__ void __launch_bounds__(256, 3) colpass_kernel(const PassParams p) {
   for (int cc = warp; cc < B; cc += p.NW) {
     long long j = j0 + cc;
     double pr[6] = {0, 0, 0, 0, 0, 0};
-    if (j < p.n) column_work<VS, VC>(c, (int)j, pr);
+    if (j < p.n) column_work<VS, VC, PI>(c, (int)j, pr);
     if (lane == 0)
       for (int q = 0; q < nq; q++) part[q * B + cc] = pr[q];
   }

@@ -49,6 +49,7 @@ struct WarpLayout {
   int uk, ua, ub, uo;           // union table (HU); shares its bytes with yc / tie
   int yc;                       // looked-up values for inner products (2 x LMAX)
   int tie;                      // int scratch of the threshold tie-break
+  int zr, zv;                   // Pi-preconditioned forms: the list Pi R (LMAX)
   int hist;                     // 256 packed 16-bit bins (128 words)
   int H, HU;                    // table capacities (powers of two)
   int bytes;                    // total per warp (multiple of 16)
@@ -76,6 +77,7 @@ struct PassParams {
   int D, Dp;             // number of distinct offsets, padded slot stride
   int dia_off[32];       // the offsets, ascending
   const void* dia_val;   // VC values [n][Dp], 0 where row k has no entry k+off
+  const double* pi;      // Pi = diag(A)^{-1} per row (Pi-preconditioned forms), else null
   DevScalars* sc;
   double* hist_res;      // [iters+1]
   double* hist_coef;     // [2*iters]
@@ -102,8 +104,10 @@ struct PassParams {
 
 constexpr int kGroup = 64;  // blocks per group in the last-arriver reduction tree
 
-__host__ __device__ inline int pass_nq(int kind) {
-  return kind == kMR ? 3 : kind == kLOMR ? 6 : kind == kCGB ? 2 : 1;
+// partials per column: MR (R,R) (R,Q) (Q,Q); LOMR (R,R) (U,U) (V,V) (U,V)
+// (U,R) (V,R); CG pass B (R,R) (P,Q) [+ (R,Pi R)]; CG pass A (R,R) [+ (R,Pi R)]
+__host__ __device__ inline int pass_nq(int kind, bool pi = false) {
+  return kind == kMR ? 3 : kind == kLOMR ? 6 : kind == kCGB ? (pi ? 3 : 2) : kind == kCGA ? (pi ? 2 : 1) : 1;
 }
 
 }  // namespace spai

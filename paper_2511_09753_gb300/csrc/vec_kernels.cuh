@@ -77,5 +77,9 @@ cudaError_t launch_colpass_f32(const PassParams& p, int grid, int block, size_t 
 cudaError_t launch_colpass_f64(const PassParams& p, int grid, int block, size_t smem, cudaStream_t st);
 cudaError_t launch_colpass_res_f32(const PassParams& p, int grid, int block, size_t smem,
                                    cudaStream_t st);
+cudaError_t launch_colpass_pi_f32(const PassParams& p, int grid, int block, size_t smem,
+                                  cudaStream_t st);
+cudaError_t launch_colpass_pi_f64(const PassParams& p, int grid, int block, size_t smem,
+                                  cudaStream_t st);
 
 }  // namespace spai

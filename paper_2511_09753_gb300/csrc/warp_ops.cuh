@@ -716,6 +716,75 @@ template <typename V> struct TermProdTable { // a[occ[i]] * y_i
   __device__ Term operator()(int i) const { return term_prod(a[occ[i]], y[i]); }
 };
 
+// Pi-weighted terms of Section 5's inner products: fl(fl(x y) pi_k), the
+// product of the two values (exact for FP32 values) times the row weight,
+// each rounded in FP64.
+template <typename V>
+__device__ __forceinline__ Term term_wprod(V x, V y, double w) {
+  return term_of(__dmul_rn(__dmul_rn((double)x, (double)y), w));
+}
+template <typename V> struct TermWSq {       // pi_k x_k^2 of a list
+  const int* r;
+  const V* v;
+  const double* pi;
+  __device__ Term operator()(int i) const { return term_wprod(v[i], v[i], pi[r[i]]); }
+};
+template <typename V> struct TermWProd {     // pi_k x_k y_k of two aligned arrays
+  const int* r;
+  const V* x;
+  const V* y;
+  const double* pi;
+  __device__ Term operator()(int i) const { return term_wprod(x[i], y[i], pi[r[i]]); }
+};
+template <typename V> struct TermWSqTable {  // pi_k x_k^2 of the occupied slots of a table
+  const int* key;
+  const V* v;
+  const uint16_t* occ;
+  const double* pi;
+  __device__ Term operator()(int i) const {
+    const int s = occ[i];
+    return term_wprod(v[s], v[s], pi[key[s]]);
+  }
+};
+template <typename V> struct TermWProdTable {  // pi_k a[occ[i]] y_i
+  const int* key;
+  const V* a;
+  const uint16_t* occ;
+  const V* y;
+  const double* pi;
+  __device__ Term operator()(int i) const {
+    const int s = occ[i];
+    return term_wprod(a[s], y[i], pi[key[s]]);
+  }
+};
+
+// (Pi R)_j of a list: z_k = pi_k r_k in FP64 rounded to the value type,
+// exact zeros removed (Algorithms 5, 7, 8: Z := Pi R).  Returns the length.
+template <typename V>
+__device__ int list_scale_pi(const int* rr, const V* rv, int L, const double* pi, int* zr, V* zv,
+                             int lane) {
+  int out = 0;
+  for (int base = 0; base < L; base += 32) {
+    const int i = base + lane;
+    int r = 0;
+    V z = V(0);
+    if (i < L) {
+      r = rr[i];
+      z = (V)__dmul_rn(pi[r], (double)rv[i]);
+    }
+    const bool keep = i < L && z != V(0);
+    const unsigned b = __ballot_sync(kFull, keep);
+    if (keep) {
+      const int pos = out + __popc(b & lanemask_lt());
+      zr[pos] = r;
+      zv[pos] = z;
+    }
+    out += __popc(b);
+  }
+  __syncwarp();
+  return out;
+}
+
 // y_i = value of row xr[i] in table h (0 if absent)
 template <typename V>
 __device__ void lookup_list(const int* xr, int L, const HashT& h, V* y, int lane) {

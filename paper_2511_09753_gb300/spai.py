@@ -19,7 +19,8 @@ SPAI_FP64, SPAI_MIXED = 0, 1
 SPAI_MR, SPAI_LOMR, SPAI_CG = 0, 1, 2
 SPAI_DROP_NONE, SPAI_DROP_TOPK_COL = 0, 1
 PREC_NONE, PREC_JACOBI, PREC_SPAI, PREC_SPAI_SYM = 0, 1, 2, 3
-METHODS = {"mr": SPAI_MR, "lomr": SPAI_LOMR, "cg": SPAI_CG}
+METHODS = {"mr": SPAI_MR, "lomr": SPAI_LOMR, "cg": SPAI_CG,
+           "mr_pi": 3, "lomr_pi": 4, "cg_pi": 5}  # Section 5's forms with Pi = diag(A)^{-1}
 
 OK, CONVERGED_EARLY, LOMR_FALLBACK, PCG_MAXIT, PCG_BREAKDOWN = 0, 1, 2, 3, 4
 ERR_CAPACITY = -8

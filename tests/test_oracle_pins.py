@@ -215,6 +215,101 @@ def test_mr_rate_bound_random_spd():
     assert np.all(res[1:] <= C * res[:-1] * (1 + 1e-12))
 
 
+# ----------------------------- Pi-preconditioned forms (Algorithms 5, 7, 8)
+
+@pytest.mark.parametrize("mixed", [False, True])
+@pytest.mark.parametrize("method", ["mr", "lomr", "cg"])
+def test_pi_forms_reduce_to_plain_forms_on_power_of_two_diagonals(method, mixed):
+    """With Pi = diag(A)^{-1} = I / 2^k every Pi scaling is exact, so Z = Pi R
+    ranks, drops and combines like R, the weighted inner products are the
+    plain ones scaled by powers of two, and the iterates are bitwise those of
+    the plain method; step coefficients carry the factor 2^k where the
+    algebra says (MR and CG alpha, LOMR delta)."""
+    for (n, rp, ci, v), scale in ((lap2d(12), 4.0), (I.laplacian_1d(50), 2.0)):
+        plain = O.Oracle(n, rp, ci, v, mixed=mixed, cap_factor=2.0)
+        pre = O.Oracle(n, rp, ci, v, mixed=mixed, cap_factor=2.0)
+        a = plain.run(method, 7)
+        b = pre.run(method + "_pi", 7)
+        assert a["done"] == b["done"] == 7
+        assert np.array_equal(a["resnorm"], b["resnorm"])
+        for x, y in zip(plain.get_M(), pre.get_M()):
+            assert np.array_equal(x, y)
+        np.testing.assert_array_equal(b["coef"][:, 0], scale * a["coef"][:, 0])
+        np.testing.assert_array_equal(b["coef"][:, 1], a["coef"][:, 1])
+
+
+def _pi_dense(A):
+    return np.diag(1.0 / np.diag(A))
+
+
+def test_pi_mr_step_is_the_weighted_line_minimiser():
+    """Algorithm 5, no dropping: alpha minimises (R - a A Z, Pi (R - a A Z))
+    over a, with Z = Pi R; the Pi-weighted residual never grows."""
+    n, rp, ci, v = I.varcoef_grid((4, 5), seed=9)
+    A = I.csr_to_dense(n, rp, ci, v)
+    Pi = _pi_dense(A)
+    o = O.Oracle(n, rp, ci, v, cap_factor=1e9)
+    prev = None
+    for _ in range(6):
+        M = dense_from_csc(n, *o.get_M())
+        R = np.eye(n) - A @ M
+        Z = Pi @ R
+        AZ = A @ Z
+        alpha = frob(AZ, Pi @ R) / frob(AZ, Pi @ AZ)
+        o.run("mr_pi", 1, drop=O.DROP_NONE)
+        M1 = dense_from_csc(n, *o.get_M())
+        np.testing.assert_allclose(M1, M + alpha * Z, rtol=0, atol=1e-13)
+        R1 = np.eye(n) - A @ M1
+        w = frob(R1, Pi @ R1)
+        if prev is not None:
+            assert w <= prev * (1 + 1e-12)
+        prev = w
+
+
+def test_pi_lomr_step_is_the_weighted_2d_minimiser():
+    """Algorithm 8, no dropping: (delta, gamma) minimise the Pi-weighted
+    norm of R - d A Z - g A P_{i-1} (its 2x2 normal equations)."""
+    n, rp, ci, v = I.varcoef_grid((3, 4), seed=5)
+    A = I.csr_to_dense(n, rp, ci, v)
+    Pi = _pi_dense(A)
+    W = np.sqrt(np.diag(Pi))[:, None]
+    o = O.Oracle(n, rp, ci, v, cap_factor=1e9)
+    o.run("lomr_pi", 2, drop=O.DROP_NONE)
+    for _ in range(4):
+        M1 = dense_from_csc(n, *o.get_M())
+        Pm = dense_from_csc(n, *o.get(1))
+        R1 = np.eye(n) - A @ M1
+        Z = Pi @ R1
+        B = np.stack([(W * (A @ Z)).ravel(), (W * (A @ Pm)).ravel()], axis=1)
+        d, g = np.linalg.lstsq(B, (W * R1).ravel(), rcond=None)[0]
+        o.run("lomr_pi", 1, drop=O.DROP_NONE)
+        M2 = dense_from_csc(n, *o.get_M())
+        np.testing.assert_allclose(M2, M1 + d * Z + g * Pm, rtol=0, atol=1e-12)
+
+
+def test_pi_cg_orthogonality():
+    """Algorithm 7, no dropping: (R_i, Pi R_j) = 0 and (P_i, A P_j) = 0 for
+    i != j (the preconditioned counterparts of Eqs. 3.4 and 3.6)."""
+    n, rp, ci, v = I.varcoef_grid((3, 4), seed=2)
+    A = I.csr_to_dense(n, rp, ci, v)
+    Pi = _pi_dense(A)
+    o = O.Oracle(n, rp, ci, v, cap_factor=1e9)
+    Rs, Ps = [], []
+    Rs.append(np.eye(n) - A @ dense_from_csc(n, *o.get_M()))
+    o.run("cg_pi", 0, drop=O.DROP_NONE)
+    Ps.append(dense_from_csc(n, *o.get(1)))
+    np.testing.assert_allclose(Ps[0], Pi @ Rs[0], rtol=0, atol=1e-15)
+    for _ in range(5):
+        o.run("cg_pi", 1, drop=O.DROP_NONE)
+        Rs.append(np.eye(n) - A @ dense_from_csc(n, *o.get_M()))
+        Ps.append(dense_from_csc(n, *o.get(1)))
+    scale = frob(Rs[0], Pi @ Rs[0])
+    for i in range(1, len(Rs)):
+        for j in range(i):
+            assert abs(frob(Rs[i], Pi @ Rs[j])) <= 1e-10 * scale
+            assert abs(frob(Ps[i], A @ Ps[j])) <= 1e-9 * scale * 10
+
+
 # ------------------------------------------- CG: Prop. 2 and Theorem 5
 
 def test_cg_orthogonality():
