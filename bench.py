@@ -278,7 +278,7 @@ def run_ours(args):
                     "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
             "roofline": {"bound": "hbm", "kernel": "colpass_kernel", "achieved": achieved,
                          "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                         "peak_source": peak_kind, "traffic": None,
+                         "peak_source": peak_kind, "traffic": COLPASS_TRAFFIC_BYTES,
                          "algorithmic_bytes_per_launch": per_launch_bytes,
                          "launch_ms": per_launch_ms, "launches": launches},
             "cpu_baseline": cpu,
@@ -294,6 +294,11 @@ def run_ours(args):
         dist.barrier()
         dist.destroy_process_group()
 
+
+# DRAM bytes (read + write) per column-pass launch, from ncu captures of the
+# --profile mr|lomr|cg cases on this workload, weighted by the launch mix of
+# one step (51 MR, 51 LOMR, 50 + 50 CG passes).
+COLPASS_TRAFFIC_BYTES = 139.5e6
 
 BATCH_ITERS = 30
 BATCH_RHS = 32
