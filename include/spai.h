@@ -252,6 +252,23 @@ int spai_set_pcg_prec(spai_handle h, int prec);
 int pcg_solve_block(spai_handle h, int nrhs, const double *b, double *x, double rtol, int maxit,
                     int precond, int on_device, int *iters, int *status, double *relres);
 
+/* Definiteness diagnostic (the paper's motivation: an SPAI of an SPD matrix
+ * should keep a positive-definite symmetric part; the spectra of Tables 4-6):
+ * `steps` steps of the Lanczos three-term recurrence on S = (M + M^T)/2 (no
+ * reorthogonalisation, FP64) from the host start vector v0[n] (nonzero,
+ * finite; the caller draws it).  S v is an fma chain over ascending column
+ * per row, inner products and norms the pairwise trees of the PCG,
+ * w = fma(-beta_{j-1}, v_{j-1}, fma(-alpha_j, v_j, w)), v_{j+1} = w / beta_j;
+ * the recurrence stops early when beta_j is 0 or not finite.  Host outputs:
+ * alpha[steps], beta[steps] (may be NULL), *steps_done, and *lmin / *lmax
+ * (may be NULL): the extremal eigenvalues of the tridiagonal T of the done
+ * steps (bisection on its Sturm sequence), which approach lambda_min(S) and
+ * lambda_max(S) from inside as the steps grow; lmin < 0 shows an indefinite
+ * symmetric part.  Single-matrix handles only (SPAI_ERR_UNSUPPORTED for a
+ * batch). */
+int spai_sym_lanczos(spai_handle h, int steps, const double *v0, double *alpha, double *beta,
+                     int *steps_done, double *lmin, double *lmax);
+
 /* Checkpoint of the iteration state (M, directions, scalars, method and
  * iteration index).  Two-call: with buf == NULL only *bytes is set. */
 int spai_save_state(spai_handle h, void *buf, size_t *bytes);

@@ -83,6 +83,8 @@ def _load():
         lib.orc_pcg.argtypes = [C.c_int, p_i32, p_i32, p_f64, C.c_int, C.c_void_p, C.c_void_p,
                                 C.c_void_p, p_f64, C.c_double, C.c_int, p_f64,
                                 C.POINTER(C.c_int), C.POINTER(C.c_double), C.c_int]
+        lib.orc_lanczos.restype = C.c_int
+        lib.orc_lanczos.argtypes = [C.c_int, p_i32, p_i32, p_f64, p_f64, C.c_int, p_f64, p_f64]
         _lib = lib
         return lib
 
@@ -200,3 +202,19 @@ def pcg(n, rowptr, colind, vals, b, rtol=1e-8, maxit=10000, precond=0, M=None, m
                      x, C.byref(st), C.byref(rr), 1 if mixed else 0)
     del keep
     return dict(iters=it, status=st.value, relres=rr.value, x=x)
+
+
+def lanczos(n, M, v0, steps):
+    """Lanczos on the symmetric part (M + M^T)/2 of M (CSC triple) from v0:
+    returns dict(alpha, beta, steps, lmin, lmax), the extremal eigenvalues of
+    the tridiagonal T from scipy's tridiagonal eigensolver."""
+    from scipy.linalg import eigvalsh_tridiagonal
+    lib = _load()
+    cp, ri, mv = (np.ascontiguousarray(M[0], dtype=np.int32), np.ascontiguousarray(M[1], dtype=np.int32),
+                  np.ascontiguousarray(M[2], dtype=np.float64))
+    v0 = np.ascontiguousarray(v0, dtype=np.float64)
+    a = np.zeros(max(steps, 1))
+    b = np.zeros(max(steps, 1))
+    k = lib.orc_lanczos(int(n), cp, ri, mv, v0, int(steps), a, b)
+    ev = eigvalsh_tridiagonal(a[:k], b[:k - 1]) if k > 1 else a[:k]
+    return dict(alpha=a[:k], beta=b[:k], steps=k, lmin=float(ev[0]), lmax=float(ev[-1]))

@@ -827,6 +827,53 @@ static double vdot(int n, const double *x, const double *y, double *tmp) {
   return pairwise64(tmp, n);
 }
 
+/* Rows of M (CSC input) as CSR with column-sorted rows, or (sym != 0) the
+ * rows of its symmetric part S = (M + M^T)/2, s_ij = 0.5 (m_ij + m_ji) in
+ * FP64 with exact zeros dropped (the paper symmetrises M, Appendix A step 1). */
+static void build_rows(int n, const int *mcolptr, const int *mrowind, const double *mvals, int sym,
+                       int **rp_out, int **ci_out, double **v_out) {
+  int nnz = mcolptr[n];
+  int *mrp = (int *)calloc((size_t)n + 1, sizeof(int));
+  int *mci = (int *)malloc(sizeof(int) * (size_t)(nnz ? nnz : 1));
+  double *mv = (double *)malloc(sizeof(double) * (size_t)(nnz ? nnz : 1));
+  for (int e = 0; e < nnz; e++) mrp[mrowind[e] + 1]++;
+  for (int i = 0; i < n; i++) mrp[i + 1] += mrp[i];
+  int *fill = (int *)malloc(sizeof(int) * (size_t)(n > 0 ? n : 1));
+  for (int i = 0; i < n; i++) fill[i] = mrp[i];
+  for (int j = 0; j < n; j++)
+    for (int e = mcolptr[j]; e < mcolptr[j + 1]; e++) {
+      int i = mrowind[e];
+      mci[fill[i]] = j;
+      mv[fill[i]] = mvals[e];
+      fill[i]++;
+    }
+  free(fill);
+  if (sym) {
+    int *srp = (int *)calloc((size_t)n + 1, sizeof(int));
+    int *sci = (int *)malloc(sizeof(int) * (size_t)(2 * nnz + 1));
+    double *sv = (double *)malloc(sizeof(double) * (size_t)(2 * nnz + 1));
+    int t = 0;
+    for (int i = 0; i < n; i++) { /* row i of M is CSR row i; row i of M^T is CSC column i */
+      int a = mrp[i], ae = mrp[i + 1], b2 = mcolptr[i], be = mcolptr[i + 1];
+      while (a < ae || b2 < be) {
+        int c;
+        double u = 0.0, w = 0.0;
+        if (b2 >= be || (a < ae && mci[a] < mrowind[b2])) { c = mci[a]; u = mv[a++]; }
+        else if (a >= ae || mrowind[b2] < mci[a]) { c = mrowind[b2]; w = mvals[b2++]; }
+        else { c = mci[a]; u = mv[a++]; w = mvals[b2++]; }
+        double val = 0.5 * (u + w);
+        if (val != 0.0) { sci[t] = c; sv[t] = val; t++; }
+      }
+      srp[i + 1] = t;
+    }
+    free(mrp); free(mci); free(mv);
+    mrp = srp; mci = sci; mv = sv;
+  }
+  *rp_out = mrp;
+  *ci_out = mci;
+  *v_out = mv;
+}
+
 /*
  * Vector PCG on A x = b, x_0 = 0, preconditioner z = Prec(r):
  *   precond 0: z = r; 1: z = r / diag(A); 2: z = M r with M given in CSC;
@@ -856,45 +903,7 @@ int orc_pcg(int n, const int *rp, const int *ci, const double *av, int precond, 
     for (int e = rp[i]; e < rp[i + 1]; e++)
       if (ci[e] == i) diag[i] = av[e];
   }
-  if (precond == 2 || precond == 3) { /* CSC -> CSR, rows column-sorted */
-    int nnz = mcolptr[n];
-    mrp = (int *)calloc((size_t)n + 1, sizeof(int));
-    mci = (int *)malloc(sizeof(int) * (size_t)(nnz ? nnz : 1));
-    mv = (double *)malloc(sizeof(double) * (size_t)(nnz ? nnz : 1));
-    for (int e = 0; e < nnz; e++) mrp[mrowind[e] + 1]++;
-    for (int i = 0; i < n; i++) mrp[i + 1] += mrp[i];
-    int *fill = (int *)malloc(sizeof(int) * (size_t)n);
-    for (int i = 0; i < n; i++) fill[i] = mrp[i];
-    for (int j = 0; j < n; j++)
-      for (int e = mcolptr[j]; e < mcolptr[j + 1]; e++) {
-        int i = mrowind[e];
-        mci[fill[i]] = j;
-        mv[fill[i]] = mvals[e];
-        fill[i]++;
-      }
-    free(fill);
-    if (precond == 3) { /* S = (M + M^T) / 2: s_ij = 0.5 * (m_ij + m_ji) */
-      int *srp = (int *)calloc((size_t)n + 1, sizeof(int));
-      int *sci = (int *)malloc(sizeof(int) * (size_t)(2 * nnz + 1));
-      double *sv = (double *)malloc(sizeof(double) * (size_t)(2 * nnz + 1));
-      int t = 0;
-      for (int i = 0; i < n; i++) { /* row i of M is CSR row i; row i of M^T is CSC column i */
-        int a = mrp[i], ae = mrp[i + 1], b2 = mcolptr[i], be = mcolptr[i + 1];
-        while (a < ae || b2 < be) {
-          int c;
-          double u = 0.0, w = 0.0;
-          if (b2 >= be || (a < ae && mci[a] < mrowind[b2])) { c = mci[a]; u = mv[a++]; }
-          else if (a >= ae || mrowind[b2] < mci[a]) { c = mrowind[b2]; w = mvals[b2++]; }
-          else { c = mci[a]; u = mv[a++]; w = mvals[b2++]; }
-          double val = 0.5 * (u + w);
-          if (val != 0.0) { sci[t] = c; sv[t] = val; t++; }
-        }
-        srp[i + 1] = t;
-      }
-      free(mrp); free(mci); free(mv);
-      mrp = srp; mci = sci; mv = sv;
-    }
-  }
+  if (precond == 2 || precond == 3) build_rows(n, mcolptr, mrowind, mvals, precond == 3, &mrp, &mci, &mv);
   float *av32 = NULL, *mv32 = NULL, *x32 = NULL;
   if (mixed) {
     int nnz = rp[n];
@@ -967,5 +976,51 @@ out:
   free(av32);
   free(mv32);
   free(x32);
+  return k;
+}
+
+/*
+ * Lanczos on the symmetric part S = (M + M^T)/2 of M (definiteness
+ * diagnostics: the extremal eigenvalues of the tridiagonal T approach
+ * lambda_min(S) and lambda_max(S)), plain three-term recurrence without
+ * reorthogonalisation, FP64:
+ *   v_1 = v0 / ||v0||, v_0 = 0, beta_0 = 0; for j = 1..m:
+ *   w = S v_j (fma chain per row, ascending column); alpha_j = (w, v_j);
+ *   w = fma(-beta_{j-1}, v_{j-1}, fma(-alpha_j, v_j, w)); beta_j = ||w||;
+ *   stop if beta_j is 0 or not finite; v_{j+1} = w / beta_j.
+ * Inner products and norms are the pairwise trees of the PCG.  Writes
+ * alpha[0..k), beta[0..k) and returns k, the steps done.
+ */
+int orc_lanczos(int n, const int *mcolptr, const int *mrowind, const double *mvals, const double *v0,
+                int steps, double *alpha, double *beta) {
+  int *srp, *sci;
+  double *sv;
+  build_rows(n, mcolptr, mrowind, mvals, 1, &srp, &sci, &sv);
+  size_t nn = (size_t)(n > 0 ? n : 1);
+  double *vp = (double *)calloc(nn, sizeof(double));
+  double *vc = (double *)malloc(sizeof(double) * nn);
+  double *w = (double *)malloc(sizeof(double) * nn);
+  double *tmp = (double *)malloc(sizeof(double) * (nn > 64 ? nn : 64));
+  double nrm = sqrt(vdot(n, v0, v0, tmp));
+  for (int i = 0; i < n; i++) vc[i] = v0[i] / nrm;
+  int k = 0;
+  double bprev = 0.0;
+  for (int j = 0; j < steps; j++) {
+    spmv_rows(n, srp, sci, sv, vc, w, tmp);
+    double a = vdot(n, w, vc, tmp);
+    for (int i = 0; i < n; i++) w[i] = fma(-bprev, vp[i], fma(-a, vc[i], w[i]));
+    double b = sqrt(vdot(n, w, w, tmp));
+    alpha[j] = a;
+    beta[j] = b;
+    k = j + 1;
+    if (b == 0.0 || !isfin(b)) break;
+    for (int i = 0; i < n; i++) {
+      vp[i] = vc[i];
+      vc[i] = w[i] / b;
+    }
+    bprev = b;
+  }
+  free(srp); free(sci); free(sv);
+  free(vp); free(vc); free(w); free(tmp);
   return k;
 }

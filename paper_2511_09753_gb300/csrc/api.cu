@@ -12,6 +12,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <new>
 #include <vector>
 
@@ -1621,6 +1622,114 @@ int pcg_solve(spai_handle h, const double* b, double* x, int nrhs, double rtol, 
   if (relres) *relres = ps.bn > 0 ? sqrt(ps.tres) / ps.bn : 0.0;
   if (ps.status == 1) return SPAI_PCG_MAXIT;
   if (ps.status == 2) return SPAI_PCG_BREAKDOWN;
+  return SPAI_OK;
+}
+
+// ------------------------------------------------------- diagnostics
+
+// Number of eigenvalues below x of the symmetric tridiagonal matrix with
+// diagonal a[0..k) and off-diagonal b[0..k-1) (Sturm sequence of the LDL^T
+// pivots; a zero pivot is replaced by a tiny negative one).
+static int sturm_count(const double* a, const double* b, int k, double x) {
+  int c = 0;
+  double q = 1.0;
+  for (int i = 0; i < k; i++) {
+    q = (a[i] - x) - (i ? (b[i - 1] * b[i - 1]) / q : 0.0);
+    if (q == 0.0) q = -1e-300;
+    if (q < 0.0) c++;
+  }
+  return c;
+}
+
+// Smallest and largest eigenvalue of that tridiagonal matrix by bisection
+// inside its Gershgorin interval, to the last bit.
+static void tri_extremes(const double* a, const double* b, int k, double* lmin, double* lmax) {
+  double lo = a[0], hi = a[0];
+  for (int i = 0; i < k; i++) {
+    double r = (i ? fabs(b[i - 1]) : 0.0) + (i + 1 < k ? fabs(b[i]) : 0.0);
+    lo = std::min(lo, a[i] - r);
+    hi = std::max(hi, a[i] + r);
+  }
+  for (int which = 0; which < 2; which++) {
+    double l = lo, u = hi;
+    const int need = which == 0 ? 1 : k;  // count(x) >= need means x is past the eigenvalue
+    for (int it = 0; it < 2100; it++) {
+      double m = 0.5 * (l + u);
+      if (m <= l || m >= u) break;
+      if (sturm_count(a, b, k, m) >= need) u = m;
+      else l = m;
+    }
+    (which == 0 ? *lmin : *lmax) = 0.5 * (l + u);
+  }
+}
+
+int spai_sym_lanczos(spai_handle h, int steps, const double* v0, double* alpha, double* beta,
+                     int* steps_done, double* lmin, double* lmax) {
+  if (!h || steps < 1 || !v0 || !steps_done) return SPAI_ERR_ARG;
+  if (h->nseg) return SPAI_ERR_UNSUPPORTED;
+  const int n = h->n;
+  bool nonzero = false;
+  for (int i = 0; i < n; i++) {
+    if (!std::isfinite(v0[i])) return SPAI_ERR_ARG;
+    nonzero |= v0[i] != 0.0;
+  }
+  if (!nonzero) return SPAI_ERR_ARG;
+  int rc = ensure_pcg(h);
+  if (rc) return rc;
+  rc = ensure_rows(h, true);
+  if (rc) return rc;
+  double* d_ab = nullptr;
+  int* d_st = nullptr;
+  rc = dalloc(&d_ab, 2 * (size_t)steps + 1);
+  if (!rc) rc = dalloc(&d_st, 2);
+  if (rc) {
+    dfree(d_ab);
+    return rc;
+  }
+  cudaStream_t st = h->stream;
+  LzArgs a;
+  memset(&a, 0, sizeof(a));
+  a.n = n;
+  a.rp = h->d_srp;
+  a.ci = h->d_sci;
+  a.v = h->d_sv;
+  a.vp = h->d_x;
+  a.vc = h->d_r;
+  a.w = h->d_z;
+  a.alpha = d_ab;
+  a.beta = d_ab + steps;
+  a.nrm0 = d_ab + 2 * steps;
+  a.state = d_st;
+  a.ws.bsum = h->d_vbsum;
+  a.ws.gsum = h->d_vgsum;
+  a.ws.cnt1 = h->d_vcnt1;
+  a.ws.cnt2 = h->d_vcnt2;
+  a.ws.nb = (n + 255) / 256;
+  a.ws.ngroups = (a.ws.nb + kGroup - 1) / kGroup;
+  std::vector<double> ab(2 * (size_t)steps);
+  int stt[2] = {0, 0};
+  cudaError_t e = cudaMemcpyAsync(h->d_r, v0, sizeof(double) * n, cudaMemcpyHostToDevice, st);
+  if (!e) e = launch_lz_start(a, st);
+  for (int j = 0; j < steps && !e; j++) e = launch_lz_step(a, j, st);
+  h->other_launches += 2 + 3LL * steps;
+  if (!e) e = cudaMemcpyAsync(ab.data(), d_ab, sizeof(double) * 2 * steps, cudaMemcpyDeviceToHost, st);
+  if (!e) e = cudaMemcpyAsync(stt, d_st, sizeof(stt), cudaMemcpyDeviceToHost, st);
+  if (!e) e = cudaStreamSynchronize(st);
+  dfree(d_ab);
+  dfree(d_st);
+  if (e) {
+    (void)cudaGetLastError();
+    return SPAI_ERR_CUDA;
+  }
+  const int k = stt[0];
+  *steps_done = k;
+  if (alpha) for (int j = 0; j < k; j++) alpha[j] = ab[j];
+  if (beta) for (int j = 0; j < k; j++) beta[j] = ab[steps + j];
+  if (k == 0) return SPAI_ERR_NONFINITE;
+  double l0 = 0.0, l1 = 0.0;
+  tri_extremes(ab.data(), ab.data() + steps, k, &l0, &l1);
+  if (lmin) *lmin = l0;
+  if (lmax) *lmax = l1;
   return SPAI_OK;
 }
 

@@ -607,6 +607,97 @@ __global__ void k_pcg_update(PcgArgs a) {
   });
 }
 
+// ---------------------------------------------------------------- Lanczos
+// Three-term recurrence on S (no reorthogonalisation), FP64: S v rows are
+// fma chains over ascending column, inner products and norms the pairwise
+// tree of reduce_finish; the coefficients stay on the device.
+
+// ||v0|| with v0 in vc
+__global__ void k_lz_norm0(LzArgs a) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  double term = 0.0;
+  if (i < a.n) {
+    double x = a.vc[i];
+    term = __dmul_rn(x, x);
+  }
+  double* nrm = a.nrm0;
+  int* stt = a.state;
+  reduce_finish(term, a.ws, [nrm, stt](double tot) {
+    *nrm = __dsqrt_rn(tot);
+    stt[0] = 0;
+    stt[1] = (tot == 0.0 || !finite_d(tot)) ? 1 : 0;
+  });
+}
+
+// v_1 = v0 / ||v0||, v_0 = 0
+__global__ void k_lz_scale0(LzArgs a) {
+  if (a.state[1]) return;
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.n) return;
+  a.vc[i] = __ddiv_rn(a.vc[i], *a.nrm0);
+  a.vp[i] = 0.0;
+}
+
+// w = S v_j, alpha_j = (w, v_j)
+__global__ void k_lz_av(LzArgs a, int j) {
+  if (a.state[1]) return;
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  double term = 0.0;
+  if (i < a.n) {
+    double wi = row_chain(a.rp, a.ci, a.v, a.vc, i);
+    a.w[i] = wi;
+    term = __dmul_rn(wi, a.vc[i]);
+  }
+  double* al = a.alpha;
+  reduce_finish(term, a.ws, [al, j](double tot) { al[j] = tot; });
+}
+
+// w = fma(-beta_{j-1}, v_{j-1}, fma(-alpha_j, v_j, w)), beta_j = ||w||
+__global__ void k_lz_orth(LzArgs a, int j) {
+  if (a.state[1]) return;
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  double term = 0.0;
+  if (i < a.n) {
+    const double al = a.alpha[j], bp = j ? a.beta[j - 1] : 0.0;
+    double wi = __fma_rn(-bp, a.vp[i], __fma_rn(-al, a.vc[i], a.w[i]));
+    a.w[i] = wi;
+    term = __dmul_rn(wi, wi);
+  }
+  double* be = a.beta;
+  int* stt = a.state;
+  reduce_finish(term, a.ws, [be, stt, j](double tot) {
+    double b = __dsqrt_rn(tot);
+    be[j] = b;
+    stt[0] = j + 1;
+    if (b == 0.0 || !finite_d(b)) stt[1] = 1;
+  });
+}
+
+// v_{j-1} = v_j, v_{j+1} = w / beta_j
+__global__ void k_lz_next(LzArgs a, int j) {
+  if (a.state[1]) return;
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.n) return;
+  const double b = a.beta[j];
+  a.vp[i] = a.vc[i];
+  a.vc[i] = __ddiv_rn(a.w[i], b);
+}
+
+cudaError_t launch_lz_start(const LzArgs& a, cudaStream_t st) {
+  int g = (a.n + 255) / 256;
+  k_lz_norm0<<<g, 256, 0, st>>>(a);
+  k_lz_scale0<<<g, 256, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lz_step(const LzArgs& a, int j, cudaStream_t st) {
+  int g = (a.n + 255) / 256;
+  k_lz_av<<<g, 256, 0, st>>>(a, j);
+  k_lz_orth<<<g, 256, 0, st>>>(a, j);
+  k_lz_next<<<g, 256, 0, st>>>(a, j);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_pcg_init(const PcgArgs& a, cudaStream_t st) {
   int g = (a.n + 255) / 256;
   k_pcg_init<<<g, 256, 0, st>>>(a);

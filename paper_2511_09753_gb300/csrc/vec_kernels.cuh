@@ -69,6 +69,21 @@ cudaError_t launch_sell_build_i64(int n, const long long* rp, const int* ci, con
                                   int* w32, long long* sptr, long long* scan_tmp, int** scol,
                                   double** sval, long long* cap, long long* total, cudaStream_t st);
 cudaError_t launch_to_f32(const double* in, float* out, long long count, cudaStream_t st);
+
+// Lanczos on the rows of a symmetric matrix S (definiteness diagnostics)
+struct LzArgs {
+  int n;
+  const long long* rp;  // CSR rows of S, column-sorted
+  const int* ci;
+  const double* v;
+  double *vp, *vc, *w;  // v_{j-1}, v_j (v0 on entry), work
+  double *alpha, *beta; // [steps]
+  int* state;           // [0] steps done, [1] stopped
+  double* nrm0;
+  RedWS ws;
+};
+cudaError_t launch_lz_start(const LzArgs& a, cudaStream_t st);
+cudaError_t launch_lz_step(const LzArgs& a, int j, cudaStream_t st);
 cudaError_t launch_pcg_init(const PcgArgs& a, cudaStream_t st);
 cudaError_t launch_pcg_iter(const PcgArgs& a, cudaStream_t st);
 cudaError_t launch_true_res(const PcgArgs& a, cudaStream_t st);

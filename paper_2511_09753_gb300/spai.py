@@ -31,7 +31,7 @@ EXPORTED = ["spai_validate_csr", "spai_status_string", "spai_create", "spai_dest
             "pcg_solve", "spai_save_state", "spai_load_state", "spai_set_timing",
             "spai_get_stats", "spai_true_residual_noalloc", "spai_create_batched",
             "spai_batch_info", "spai_batch_history", "spai_batch_residual_norms",
-            "spai_batch_get_M", "pcg_solve_block", "spai_set_pcg_prec"]
+            "spai_batch_get_M", "pcg_solve_block", "spai_set_pcg_prec", "spai_sym_lanczos"]
 
 
 class SpaiError(RuntimeError):
@@ -86,6 +86,8 @@ def load():
         "pcg_solve": (i32, [vp, vp, vp, i32, dbl, i32, i32, i32, C.POINTER(i32), C.POINTER(dbl)]),
         "pcg_solve_block": (i32, [vp, i32, vp, vp, dbl, i32, i32, i32, vp, vp, vp]),
         "spai_set_pcg_prec": (i32, [vp, i32]),
+        "spai_sym_lanczos": (i32, [vp, i32, vp, vp, vp, C.POINTER(i32), C.POINTER(dbl),
+                                   C.POINTER(dbl)]),
         "spai_save_state": (i32, [vp, vp, C.POINTER(C.c_size_t)]),
         "spai_load_state": (i32, [vp, vp, C.c_size_t]),
         "spai_set_timing": (i32, [vp, i32]),
@@ -320,6 +322,23 @@ class Spai:
                 o += R * n
         return dict(status=rc, iters=it.reshape(k, R), statuses=st.reshape(k, R),
                     relres=rr.reshape(k, R), x=x)
+
+    def sym_spectrum(self, steps=200, v0=None, seed=0):
+        """Lanczos on (M + M^T)/2 from v0 (default: standard normal draws from
+        default_rng(seed)); returns dict(lmin, lmax, alpha, beta, steps)."""
+        if v0 is None:
+            v0 = np.random.default_rng(seed).standard_normal(int(self.n))
+        v0 = _np(v0, np.float64)
+        a = np.zeros(steps)
+        b = np.zeros(steps)
+        k = C.c_int()
+        lo = C.c_double()
+        hi = C.c_double()
+        self._check(self.lib.spai_sym_lanczos(self.h, int(steps), v0.ctypes.data, a.ctypes.data,
+                                              b.ctypes.data, C.byref(k), C.byref(lo), C.byref(hi)),
+                    "spai_sym_lanczos")
+        return dict(lmin=lo.value, lmax=hi.value, alpha=a[:k.value], beta=b[:k.value],
+                    steps=k.value)
 
     def save_state(self) -> bytes:
         n = C.c_size_t()

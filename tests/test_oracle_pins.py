@@ -506,3 +506,54 @@ def test_continuation_equals_single_run():
         b.run(m, 12)
         for x, y in zip(a.get_M(), b.get_M()):
             assert np.array_equal(x, y)
+
+
+# ------------------------------------------------- definiteness diagnostics
+
+def test_lanczos_extremes_match_dense_eigenvalues_of_sym_part():
+    """After enough steps the extremal Ritz values are the extremal
+    eigenvalues of S = (M + M^T)/2 (dense eigvalsh), and the recurrence
+    tridiagonalises S: V^T S V = T for the Lanczos basis of a short run."""
+    n, rp, ci, v = I.varcoef_grid((6, 7), seed=4)
+    o = O.Oracle(n, rp, ci, v, cap_factor=2.0)
+    o.run("mr", 6)
+    cp, ri, mv = o.get_M()
+    M = dense_from_csc(n, cp, ri, mv)
+    S = 0.5 * (M + M.T)
+    ev = np.linalg.eigvalsh(S)
+    v0 = np.random.default_rng(0).standard_normal(n)
+    r = O.lanczos(n, (cp, ri, mv), v0, 3 * n)
+    assert abs(r["lmin"] - ev[0]) <= 1e-10 * abs(ev).max()
+    assert abs(r["lmax"] - ev[-1]) <= 1e-10 * abs(ev).max()
+    # three-term recurrence, rebuilt densely from the oracle's coefficients
+    k = 8
+    r8 = O.lanczos(n, (cp, ri, mv), v0, k)
+    V = np.zeros((n, k + 1))
+    V[:, 0] = v0 / np.linalg.norm(v0)
+    for j in range(k):
+        w = S @ V[:, j] - r8["alpha"][j] * V[:, j] - (r8["beta"][j - 1] * V[:, j - 1] if j else 0)
+        V[:, j + 1] = w / r8["beta"][j]
+    T = np.diag(r8["alpha"]) + np.diag(r8["beta"][:-1], 1) + np.diag(r8["beta"][:-1], -1)
+    np.testing.assert_allclose(V[:, :k].T @ S @ V[:, :k], T, atol=1e-10)
+
+
+def test_lanczos_on_diagonal_and_indefinite_sym_parts():
+    """Diagonal M: T's eigenvalues are M's distinct entries (one per
+    Krylov dimension); a symmetric part with a negative eigenvalue is seen
+    as lmin < 0."""
+    n = 6
+    d = np.array([3.0, -1.0, 2.0, 5.0, 0.5, 4.0])
+    cp = np.arange(n + 1, dtype=np.int32)
+    ri = np.arange(n, dtype=np.int32)
+    r = O.lanczos(n, (cp, ri, d), np.ones(n), n)
+    assert r["steps"] == n
+    np.testing.assert_allclose(sorted(np.linalg.eigvalsh(
+        np.diag(r["alpha"]) + np.diag(r["beta"][:-1], 1) + np.diag(r["beta"][:-1], -1))),
+        sorted(d), rtol=0, atol=1e-12)
+    assert r["lmin"] < 0 and abs(r["lmin"] + 1.0) < 1e-12 and abs(r["lmax"] - 5.0) < 1e-12
+    # a nonsymmetric M: only its symmetric part counts
+    A = np.array([[2.0, 1.0], [-1.0, 2.0]])   # sym part = 2 I
+    r2 = O.lanczos(2, (np.array([0, 2, 4], np.int32), np.array([0, 1, 0, 1], np.int32),
+                       A.T.ravel().copy()), np.array([1.0, 0.3]), 2)
+    assert abs(r2["alpha"][0] - 2.0) <= 1e-15 and r2["beta"][0] <= 1e-15
+    assert abs(r2["lmin"] - 2.0) <= 1e-14 and abs(r2["lmax"] - 2.0) <= 1e-14
