@@ -269,6 +269,20 @@ int pcg_solve_block(spai_handle h, int nrhs, const double *b, double *x, double 
 int spai_sym_lanczos(spai_handle h, int steps, const double *v0, double *alpha, double *beta,
                      int *steps_done, double *lmin, double *lmax);
 
+/* The best approximate inverse on the fixed pattern supp(A^k) (the paper's
+ * Exp. 09 and Figs. 1-2, the classic Frobenius-norm SPAI it contrasts with):
+ * replaces M by the matrix whose column j minimises ||e_j - A m_j||_2 over
+ * supp(m_j) = supp(A^k e_j) (k >= 0; k = 0 is the diagonal), and forgets the
+ * method recurrence.  Column j solves its normal equations
+ * (A^2)[J,J] m = A[J,j] in FP64 (Cholesky); M is stored in the handle's
+ * precision, so spai_residual_norm, spai_get_M, spai_sym_lanczos and the PCG
+ * apply to it.  Errors: SPAI_ERR_CAPACITY if some |supp(A^k e_j)| exceeds
+ * cap_j (create the handle with a larger cap_factor), SPAI_ERR_UNSUPPORTED
+ * if the largest pattern does not fit a warp's shared memory (about 160
+ * rows), SPAI_ERR_NONFINITE if a Gram matrix was not numerically positive
+ * definite. */
+int spai_fixed_pattern(spai_handle h, int k);
+
 /* Checkpoint of the iteration state (M, directions, scalars, method and
  * iteration index).  Two-call: with buf == NULL only *bytes is set. */
 int spai_save_state(spai_handle h, void *buf, size_t *bytes);

@@ -218,3 +218,45 @@ def lanczos(n, M, v0, steps):
     k = lib.orc_lanczos(int(n), cp, ri, mv, v0, int(steps), a, b)
     ev = eigvalsh_tridiagonal(a[:k], b[:k - 1]) if k > 1 else a[:k]
     return dict(alpha=a[:k], beta=b[:k], steps=k, lmin=float(ev[0]), lmax=float(ev[-1]))
+
+
+def pattern_power(n, rowptr, colind, k):
+    """supp(A^k e_j) for every column j (sorted row lists); A's pattern is
+    symmetric, so column j's neighbours are row j's columns."""
+    pats = []
+    for j in range(n):
+        seen = {j}
+        front = [j]
+        for _ in range(k):
+            nxt = []
+            for u in front:
+                for c in colind[rowptr[u]:rowptr[u + 1]]:
+                    c = int(c)
+                    if c not in seen:
+                        seen.add(c)
+                        nxt.append(c)
+            front = nxt
+        pats.append(sorted(seen))
+    return pats
+
+
+def fixed_pattern_spai(n, rowptr, colind, vals, k):
+    """The best approximate inverse on a prescribed pattern (the paper's
+    Exp. 09 / Figs. 1-2): column j of M minimises ||e_j - A m_j||_2 over
+    supp(m_j) = supp(A^k e_j), solved as a dense least-squares problem on
+    the rows A touches.  Returns M as a CSC triple."""
+    A = np.zeros((n, n))
+    for i in range(n):
+        A[i, colind[rowptr[i]:rowptr[i + 1]]] = vals[rowptr[i]:rowptr[i + 1]]
+    pats = pattern_power(n, rowptr, colind, k)
+    cp = [0]
+    ri, va = [], []
+    for j, J in enumerate(pats):
+        B = A[:, J]
+        rows = np.nonzero(np.any(B != 0.0, axis=1))[0]
+        e = (rows == j).astype(np.float64)
+        m = np.linalg.lstsq(B[rows], e, rcond=None)[0]
+        ri.extend(J)
+        va.extend(m.tolist())
+        cp.append(len(ri))
+    return (np.array(cp, dtype=np.int32), np.array(ri, dtype=np.int32), np.array(va))

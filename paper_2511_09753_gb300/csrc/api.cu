@@ -20,6 +20,7 @@
 #include "common.cuh"
 #include "vec_kernels.cuh"
 #include "bpcg.cuh"
+#include "fixed_pattern.cuh"
 
 using namespace spai;
 
@@ -1731,6 +1732,100 @@ int spai_sym_lanczos(spai_handle h, int steps, const double* v0, double* alpha, 
   if (lmin) *lmin = l0;
   if (lmax) *lmax = l1;
   return SPAI_OK;
+}
+
+int spai_fixed_pattern(spai_handle h, int k) {
+  if (!h || k < 0) return SPAI_ERR_ARG;
+  const int n = h->n;
+  cudaStream_t st = h->stream;
+  // pattern supp(A^k e_j) by breadth-first search on A's (symmetric) graph
+  std::vector<int> rp(n + 1), ci(h->nnz), cap(n);
+  CK(cudaMemcpyAsync(rp.data(), h->d_rowptr, sizeof(int) * (n + 1), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(ci.data(), h->d_colind, sizeof(int) * h->nnz, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(cap.data(), h->d_cap, sizeof(int) * n, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  std::vector<long long> pptr(n + 1, 0);
+  std::vector<int> prow;
+  std::vector<int> mark(n, -1), front, next;
+  int Lmax = 1;
+  for (int j = 0; j < n; j++) {
+    const size_t start = prow.size();
+    prow.push_back(j);
+    mark[j] = j;
+    front.assign(1, j);
+    for (int lev = 0; lev < k && !front.empty(); lev++) {
+      next.clear();
+      for (int u : front)
+        for (int e = rp[u]; e < rp[u + 1]; e++) {
+          const int c = ci[e];
+          if (mark[c] != j) {
+            mark[c] = j;
+            next.push_back(c);
+            prow.push_back(c);
+          }
+        }
+      front.swap(next);
+    }
+    std::sort(prow.begin() + start, prow.end());
+    const int L = (int)(prow.size() - start);
+    if (L > cap[j]) return SPAI_ERR_CAPACITY;
+    Lmax = std::max(Lmax, L);
+    pptr[j + 1] = (long long)prow.size();
+  }
+  int dev = 0, smem_max = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (smem_max <= 0) smem_max = 227 * 1024;
+  const int wb = align16(8 * Lmax * Lmax + 8 * Lmax + 4 * Lmax);
+  const int nw = std::min(8, smem_max / wb);
+  if (nw < 1) return SPAI_ERR_UNSUPPORTED;
+  long long* d_pptr = nullptr;
+  int *d_prow = nullptr, *d_err = nullptr;
+  int rc = dalloc(&d_pptr, (size_t)n + 1);
+  if (!rc) rc = dalloc(&d_prow, prow.size());
+  if (!rc) rc = dalloc(&d_err, 1);
+  if (rc) {
+    dfree(d_pptr);
+    dfree(d_prow);
+    return rc;
+  }
+  FpArgs a;
+  memset(&a, 0, sizeof(a));
+  a.n = n;
+  a.W = h->W;
+  a.ell_col = h->d_ell_col;
+  a.ell_val = h->d_ell64;
+  a.pptr = d_pptr;
+  a.prow = d_prow;
+  a.off = h->d_off;
+  a.Mrow = h->d_Mrow;
+  a.Mval = h->d_Mval;
+  a.Mlen = h->d_Mlen;
+  a.Lmax = Lmax;
+  a.warp_bytes = wb;
+  a.err = d_err;
+  int err = 0;
+  cudaError_t e = cudaMemcpyAsync(d_pptr, pptr.data(), sizeof(long long) * (n + 1),
+                                  cudaMemcpyHostToDevice, st);
+  if (!e) e = cudaMemcpyAsync(d_prow, prow.data(), sizeof(int) * prow.size(), cudaMemcpyHostToDevice, st);
+  if (!e) e = cudaMemsetAsync(d_err, 0, sizeof(int), st);
+  if (!e) e = launch_fixed_pattern(a, h->prec == SPAI_MIXED ? 4 : 8, nw, st);
+  if (!e) e = cudaMemsetAsync(h->d_Plen, 0, sizeof(int) * n, st);
+  if (!e) e = cudaMemsetAsync(h->d_Zlen, 0, sizeof(int) * n, st);
+  if (!e) e = cudaMemcpyAsync(&err, d_err, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (!e) e = cudaStreamSynchronize(st);
+  h->other_launches += 1;
+  dfree(d_pptr);
+  dfree(d_prow);
+  dfree(d_err);
+  if (e) {
+    (void)cudaGetLastError();
+    return SPAI_ERR_CUDA;
+  }
+  h->method = -1;
+  h->it = 0;
+  invalidate_rows(h);
+  return err ? SPAI_ERR_NONFINITE : SPAI_OK;
 }
 
 // ------------------------------------------------------------ block PCG

@@ -31,7 +31,8 @@ EXPORTED = ["spai_validate_csr", "spai_status_string", "spai_create", "spai_dest
             "pcg_solve", "spai_save_state", "spai_load_state", "spai_set_timing",
             "spai_get_stats", "spai_true_residual_noalloc", "spai_create_batched",
             "spai_batch_info", "spai_batch_history", "spai_batch_residual_norms",
-            "spai_batch_get_M", "pcg_solve_block", "spai_set_pcg_prec", "spai_sym_lanczos"]
+            "spai_batch_get_M", "pcg_solve_block", "spai_set_pcg_prec", "spai_sym_lanczos",
+            "spai_fixed_pattern"]
 
 
 class SpaiError(RuntimeError):
@@ -86,6 +87,7 @@ def load():
         "pcg_solve": (i32, [vp, vp, vp, i32, dbl, i32, i32, i32, C.POINTER(i32), C.POINTER(dbl)]),
         "pcg_solve_block": (i32, [vp, i32, vp, vp, dbl, i32, i32, i32, vp, vp, vp]),
         "spai_set_pcg_prec": (i32, [vp, i32]),
+        "spai_fixed_pattern": (i32, [vp, i32]),
         "spai_sym_lanczos": (i32, [vp, i32, vp, vp, vp, C.POINTER(i32), C.POINTER(dbl),
                                    C.POINTER(dbl)]),
         "spai_save_state": (i32, [vp, vp, C.POINTER(C.c_size_t)]),
@@ -322,6 +324,10 @@ class Spai:
                 o += R * n
         return dict(status=rc, iters=it.reshape(k, R), statuses=st.reshape(k, R),
                     relres=rr.reshape(k, R), x=x)
+
+    def fixed_pattern(self, k):
+        """M := the best approximate inverse on supp(A^k) (column least squares)."""
+        self._check(self.lib.spai_fixed_pattern(self.h, int(k)), "spai_fixed_pattern")
 
     def sym_spectrum(self, steps=200, v0=None, seed=0):
         """Lanczos on (M + M^T)/2 from v0 (default: standard normal draws from

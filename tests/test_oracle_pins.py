@@ -557,3 +557,29 @@ def test_lanczos_on_diagonal_and_indefinite_sym_parts():
                        A.T.ravel().copy()), np.array([1.0, 0.3]), 2)
     assert abs(r2["alpha"][0] - 2.0) <= 1e-15 and r2["beta"][0] <= 1e-15
     assert abs(r2["lmin"] - 2.0) <= 1e-14 and abs(r2["lmax"] - 2.0) <= 1e-14
+
+
+def test_fixed_pattern_spai_pins():
+    """k = 0 gives m_jj = a_jj / ||A e_j||^2; a pattern that covers every
+    row gives A^{-1}; each column's residual is orthogonal to A's columns on
+    its pattern (the normal equations)."""
+    n, rp, ci, v = I.varcoef_grid((4, 5), seed=3)
+    A = I.csr_to_dense(n, rp, ci, v)
+    cp, ri, va = O.fixed_pattern_spai(n, rp, ci, v, 0)
+    assert np.array_equal(ri, np.arange(n))
+    np.testing.assert_allclose(va, np.diag(A) / np.sum(A * A, axis=0), rtol=1e-14)
+    cp, ri, va = O.fixed_pattern_spai(n, rp, ci, v, n)
+    np.testing.assert_allclose(dense_from_csc(n, cp, ri, va), np.linalg.inv(A), rtol=0, atol=1e-12)
+    for k in (1, 2, 3):
+        cp, ri, va = O.fixed_pattern_spai(n, rp, ci, v, k)
+        M = dense_from_csc(n, cp, ri, va)
+        pats = O.pattern_power(n, rp, ci, k)
+        for j in range(n):
+            J = pats[j]
+            assert list(ri[cp[j]:cp[j + 1]]) == J
+            res = np.eye(n)[:, j] - A @ M[:, j]
+            np.testing.assert_allclose(A[:, J].T @ res, 0.0, atol=1e-13)
+    # A^k patterns: the 5-point stencil reaches 1, 5, 13, 25 rows in the interior
+    n2, rp2, ci2, v2 = I.laplacian_2d_5pt(12)
+    sizes = [len(O.pattern_power(n2, rp2, ci2, k)[5 * 12 + 5]) for k in range(4)]
+    assert sizes == [1, 5, 13, 25]
