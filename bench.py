@@ -13,6 +13,7 @@ on the same workload and reported beside it.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
   python bench.py --workload batch64     # batched SPAIs + block PCG (below)
+  python bench.py --workload aniso1024   # rotated anisotropic 9-point, 1024^2
 
 --workload batch64: 64 variable-coefficient operators (alternating 2-D
 5-point and 3-D 7-point, n log-uniform in [1e3, 6.4e4], field seed 1000+k,
@@ -460,6 +461,68 @@ def profile_case(method, prec):
     print(json.dumps({"profile": method, "prec": prec, "resnorm": float(r["resnorm"][-1])}))
 
 
+def run_aniso(args):
+    """Rotated anisotropic 9-point operator, 1024^2 (eps 1e-3, theta pi/6):
+    LOMR and CG, 100 iterations each at caps 2, 4 and 8 nnz(A[:,j]) (mixed),
+    each followed by the Lanczos extremes of sym(M); then the best
+    approximate inverses on supp(A^k), k = 1..4 (FP64), with theirs.  The
+    metric is SPAI iterations/s over the six runs."""
+    import numpy as np
+    import torch
+
+    from paper_2511_09753_gb300 import inputs as I
+    from paper_2511_09753_gb300.spai import Spai
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    n, rp, ci, v = I.aniso_2d_9pt(1024)
+    v0 = np.random.default_rng(0).standard_normal(n)
+    stream = torch.cuda.current_stream()
+    iters = int(os.environ.get("ANISO_ITERS", "100"))
+    runs, tot_ms, tot_it = [], 0.0, 0
+    for capf in (2.0, 4.0, 8.0):
+        h = Spai(n, rp, ci, v, prec="mixed", cap_factor=capf)
+        for m in ("lomr", "cg"):
+            h.reset()
+            h.run(m, 2)
+            h.reset()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            r = h.run(m, iters)
+            e1.record(stream)
+            e1.synchronize()
+            ms = e0.elapsed_time(e1)
+            tot_ms += ms
+            tot_it += iters
+            sp = h.sym_spectrum(steps=300, v0=v0)
+            runs.append({"method": m, "cap_factor": capf, "ms": ms,
+                         "resnorm_first_last": [float(r["resnorm"][0]), float(r["resnorm"][-1])],
+                         "sym_lmin": sp["lmin"], "sym_lmax": sp["lmax"]})
+        h.close()
+    fixed = []
+    for k in (1, 2, 3, 4):
+        h = Spai(n, rp, ci, v, prec="fp64", cap_factor=10.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        h.fixed_pattern(k)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        sp = h.sym_spectrum(steps=300, v0=v0)
+        fixed.append({"k": k, "s": dt, "residual_fro": h.residual_norm(), "sym_lmin": sp["lmin"],
+                      "sym_lmax": sp["lmax"], "nnz": h.nnz_M()})
+        h.close()
+    if rank == 0:
+        print(json.dumps({
+            "metric": "SPAI iterations/s (LOMR and CG, 100 each at caps 2/4/8)",
+            "value": ws * tot_it / (tot_ms * 1e-3), "unit": "SPAI iterations/s", "n_gpus": ws,
+            "higher_is_better": True, "dtype": "f32 values / f64 reductions", "data": "synthetic",
+            "config": {"workload": "aniso9_1024", "n": n, "nnz": int(len(v)), "eps": 1e-3,
+                       "theta": "pi/6", "iters": iters, "lanczos_steps": 300},
+            "runs": runs, "fixed_pattern": fixed}))
+
+
 def profile_bpcg(prec):
     """Launch sequence for ncu captures of the block PCG kernels: the 64-matrix
     batch, 30 LOMR iterations, one block solve (products in `prec`)."""
@@ -540,7 +603,7 @@ def main():
                     help="profiling case for ncu: 3 iterations of one method on the workload, "
                          "or (bpcg) one block PCG solve of the 64-matrix batch")
     ap.add_argument("--prec", choices=["mixed", "fp64"], default="mixed")
-    ap.add_argument("--workload", choices=[WORKLOAD, "batch64"], default=WORKLOAD)
+    ap.add_argument("--workload", choices=[WORKLOAD, "batch64", "aniso1024"], default=WORKLOAD)
     args = ap.parse_args()
     if args.profile == "bpcg":
         profile_bpcg(args.prec)
@@ -548,6 +611,8 @@ def main():
         profile_case(args.profile, args.prec)
     elif args.workload == "batch64" and args.impl == "ours":
         run_batch(args)
+    elif args.workload == "aniso1024" and args.impl == "ours":
+        run_aniso(args)
     elif args.impl == "reference":
         run_reference(args)
     else:
