@@ -283,6 +283,35 @@ int spai_sym_lanczos(spai_handle h, int steps, const double *v0, double *alpha, 
  * definite. */
 int spai_fixed_pattern(spai_handle h, int k);
 
+/* ------------------------------------------------ differentiation */
+
+/* Gradient of fixed-pattern MR (no counterpart in the paper, which gives the
+ * objective of Sec. 2 and its gradient -2 A^T R in Sec. 3): K steps
+ *   M_0 = diag(A)^{-1}, R_i = I - A M_i, P_i = mask_S(R_i), Q_i = A P_i,
+ *   alpha_i = (R_i, Q_i)_F / (Q_i, Q_i)_F, M_{i+1} = M_i + alpha_i P_i,
+ * S = supp(A), loss L = ||I - A M_K||_F^2, differentiated with respect to the
+ * stored values of A taken as independent entries (through M_0, alpha_i,
+ * R_i, P_i and Q_i).  spai_fpmr_create takes A's pattern (host CSR, rows
+ * strictly ascending, symmetric, full diagonal; else SPAI_ERR_CSR /
+ * SPAI_ERR_NOT_SYMMETRIC / SPAI_ERR_NOT_SPD_DIAG) and builds, once, the
+ * patterns S and T = supp(A S) + I and the product lists of the forward and
+ * adjoint passes.  spai_fpmr_forward takes A's values (nnz FP64, CSR order,
+ * host or device) and returns L on the host, keeping M_0..M_K on the device
+ * (one checkpoint per step; R, P, Q are recomputed in the backward pass);
+ * SPAI_ERR_NONFINITE if some (Q_i, Q_i) is zero.  spai_fpmr_backward writes
+ * dloss * dL/dvals (nnz, CSR order, host or device) for the values of the
+ * last forward call (SPAI_ERR_STATE without one).  FP64 throughout.  The
+ * handle owns its device memory: about (K + 6) nnz(A) + 5 nnz(T) doubles and
+ * 6 int32 per product-list entry. */
+typedef struct spai_fpmr_ctx *spai_fpmr_handle;
+int spai_fpmr_create(spai_fpmr_handle *out, int64_t n, int64_t nnz, const int32_t *rowptr,
+                     const int32_t *colind, int K, void *stream);
+int spai_fpmr_forward(spai_fpmr_handle h, const double *vals, int on_device, double *loss);
+int spai_fpmr_backward(spai_fpmr_handle h, double dloss, double *dvals, int on_device);
+/* nnz(T), product-list entries and kernel launches so far (any may be NULL). */
+int spai_fpmr_info(spai_fpmr_handle h, int64_t *nnz_t, int64_t *list_entries, int64_t *launches);
+int spai_fpmr_destroy(spai_fpmr_handle h);
+
 /* Checkpoint of the iteration state (M, directions, scalars, method and
  * iteration index).  Two-call: with buf == NULL only *bytes is set. */
 int spai_save_state(spai_handle h, void *buf, size_t *bytes);

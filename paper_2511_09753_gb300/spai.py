@@ -32,7 +32,8 @@ EXPORTED = ["spai_validate_csr", "spai_status_string", "spai_create", "spai_dest
             "spai_get_stats", "spai_true_residual_noalloc", "spai_create_batched",
             "spai_batch_info", "spai_batch_history", "spai_batch_residual_norms",
             "spai_batch_get_M", "pcg_solve_block", "spai_set_pcg_prec", "spai_sym_lanczos",
-            "spai_fixed_pattern"]
+            "spai_fixed_pattern", "spai_fpmr_create", "spai_fpmr_forward", "spai_fpmr_backward",
+            "spai_fpmr_info", "spai_fpmr_destroy"]
 
 
 class SpaiError(RuntimeError):
@@ -88,6 +89,11 @@ def load():
         "pcg_solve_block": (i32, [vp, i32, vp, vp, dbl, i32, i32, i32, vp, vp, vp]),
         "spai_set_pcg_prec": (i32, [vp, i32]),
         "spai_fixed_pattern": (i32, [vp, i32]),
+        "spai_fpmr_create": (i32, [C.POINTER(vp), i64, i64, vp, vp, i32, vp]),
+        "spai_fpmr_forward": (i32, [vp, vp, i32, C.POINTER(dbl)]),
+        "spai_fpmr_backward": (i32, [vp, dbl, vp, i32]),
+        "spai_fpmr_info": (i32, [vp, C.POINTER(i64), C.POINTER(i64), C.POINTER(i64)]),
+        "spai_fpmr_destroy": (i32, [vp]),
         "spai_sym_lanczos": (i32, [vp, i32, vp, vp, vp, C.POINTER(i32), C.POINTER(dbl),
                                    C.POINTER(dbl)]),
         "spai_save_state": (i32, [vp, vp, C.POINTER(C.c_size_t)]),
@@ -437,3 +443,78 @@ class SpaiBatch(Spai):
         self._check(self.lib.spai_batch_get_M(self.h, int(m), C.byref(nnz), cp.ctypes.data,
                                               ri.ctypes.data, va.ctypes.data), "spai_batch_get_M")
         return cp, ri[:nnz.value], va[:nnz.value]
+
+
+class FixedPatternMR:
+    """K fixed-pattern MR steps on supp(A) and the gradient of ||I - A M_K||_F^2
+    with respect to A's stored values (see spai_fpmr_* in include/spai.h)."""
+
+    def __init__(self, n, rowptr, colind, K, stream=None):
+        self.lib = load()
+        rp, ci = _np(rowptr, np.int32), _np(colind, np.int32)
+        h = C.c_void_p()
+        rc = self.lib.spai_fpmr_create(C.byref(h), int(n), len(ci), rp.ctypes.data, ci.ctypes.data,
+                                       int(K), _stream_ptr(stream))
+        if rc != 0:
+            raise SpaiError(rc, "spai_fpmr_create")
+        self.h, self.n, self.nnz, self.K = h, int(n), len(ci), int(K)
+
+    def _ptr(self, a):
+        if hasattr(a, "data_ptr"):
+            return a.data_ptr(), 1 if a.is_cuda else 0
+        return a.ctypes.data, 0
+
+    def forward(self, vals) -> float:
+        if not hasattr(vals, "data_ptr"):
+            vals = _np(vals, np.float64)
+        p, dev = self._ptr(vals)
+        loss = C.c_double()
+        rc = self.lib.spai_fpmr_forward(self.h, p, dev, C.byref(loss))
+        if rc != 0:
+            raise SpaiError(rc, "spai_fpmr_forward")
+        return loss.value
+
+    def backward(self, dloss=1.0, out=None):
+        if out is None:
+            out = np.zeros(self.nnz)
+        p, dev = self._ptr(out)
+        rc = self.lib.spai_fpmr_backward(self.h, float(dloss), p, dev)
+        if rc != 0:
+            raise SpaiError(rc, "spai_fpmr_backward")
+        return out
+
+    def info(self):
+        a, b, c = C.c_int64(), C.c_int64(), C.c_int64()
+        self.lib.spai_fpmr_info(self.h, C.byref(a), C.byref(b), C.byref(c))
+        return dict(nnz_t=a.value, list_entries=b.value, launches=c.value)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.spai_fpmr_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def fpmr_loss(vals, fpmr):
+    """||I - A M_K||_F^2 as a differentiable function of A's values (an FP64
+    CUDA tensor in CSR order) through torch.autograd."""
+    import torch
+
+    class _F(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, v):
+            loss = fpmr.forward(v.detach().contiguous())
+            return torch.tensor(loss, dtype=torch.float64, device=v.device)
+
+        @staticmethod
+        def backward(ctx, g):
+            out = torch.empty(fpmr.nnz, dtype=torch.float64, device=g.device)
+            fpmr.backward(float(g.item()), out)
+            return out
+
+    return _F.apply(vals)

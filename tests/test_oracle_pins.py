@@ -583,3 +583,39 @@ def test_fixed_pattern_spai_pins():
     n2, rp2, ci2, v2 = I.laplacian_2d_5pt(12)
     sizes = [len(O.pattern_power(n2, rp2, ci2, k)[5 * 12 + 5]) for k in range(4)]
     assert sizes == [1, 5, 13, 25]
+
+
+# ------------------------------------------ differentiation (fixed pattern)
+
+def test_fpmr_gradient_k0_closed_form():
+    """K = 0: L = sum_{r != s} (a_rs / a_ss)^2, so dL/da_rs = 2 a_rs / a_ss^2
+    off the diagonal and dL/da_ss = -2 sum_{r != s} a_rs^2 / a_ss^3."""
+    from oracle import fpmr
+    n, rp, ci, v = I.varcoef_grid((4, 5), seed=2)
+    loss, g = fpmr.gradient(n, rp, ci, v, 0)
+    A = I.csr_to_dense(n, rp, ci, v)
+    d = np.diag(A)
+    off = A - np.diag(d)
+    assert abs(loss - float(np.sum((off / d[None, :]) ** 2))) <= 1e-12 * loss
+    for i in range(n):
+        for e in range(rp[i], rp[i + 1]):
+            s = ci[e]
+            want = 2 * v[e] / d[s] ** 2 if i != s else -2 * np.sum(off[:, s] ** 2) / d[s] ** 3
+            assert abs(g[e] - want) <= 1e-12 * max(1.0, abs(want))
+
+
+@pytest.mark.parametrize("K", [1, 3, 10])
+def test_fpmr_gradient_matches_central_differences(K):
+    """Central differences (h = 1e-6, relative to each entry) on 50 entries
+    of A treated as independent values."""
+    from oracle import fpmr
+    n, rp, ci, v = I.varcoef_3d_7pt(6, seed=4)
+    loss, g = fpmr.gradient(n, rp, ci, v, K)
+    rng = np.random.default_rng(K)
+    for e in rng.choice(len(v), 50, replace=False):
+        h = 1e-6 * abs(v[e])
+        vp, vm = v.copy(), v.copy()
+        vp[e] += h
+        vm[e] -= h
+        fd = (fpmr.forward(n, rp, ci, vp, K) - fpmr.forward(n, rp, ci, vm, K)) / (2 * h)
+        assert abs(fd - g[e]) <= 1e-6 * max(abs(g).max(), 1e-300), (e, fd, g[e])
