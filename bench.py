@@ -14,6 +14,7 @@ on the same workload and reported beside it.
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
   python bench.py --workload batch64     # batched SPAIs + block PCG (below)
   python bench.py --workload aniso1024   # rotated anisotropic 9-point, 1024^2
+  python bench.py --workload fpmr        # gradient through 10 fixed-pattern MR steps
 
 --workload batch64: 64 variable-coefficient operators (alternating 2-D
 5-point and 3-D 7-point, n log-uniform in [1e3, 6.4e4], field seed 1000+k,
@@ -523,6 +524,52 @@ def run_aniso(args):
             "runs": runs, "fixed_pattern": fixed}))
 
 
+def run_fpmr(args):
+    """Gradient of ||I - A M_K||_F^2 through K = 10 fixed-pattern MR steps with
+    respect to A's values: the 32^3 and 128^3 variable-coefficient operators
+    (seed 0), FP64, one checkpoint of M per step.  Metric: gradients per
+    second at 128^3 (forward + backward, inputs resident)."""
+    import numpy as np
+    import torch
+
+    from paper_2511_09753_gb300 import inputs as I
+    from paper_2511_09753_gb300.spai import FixedPatternMR
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    out = {}
+    for N in (32, 128):
+        n, rp, ci, v = I.varcoef_3d_7pt(N, sigma=1.5, ell=8.0, seed=0)
+        t0 = time.perf_counter()
+        f = FixedPatternMR(n, rp, ci, 10)
+        setup = time.perf_counter() - t0
+        vd = torch.tensor(v, dtype=torch.float64, device="cuda")
+        gd = torch.empty_like(vd)
+        for _ in range(max(1, args.warmup)):
+            f.forward(vd)
+            f.backward(1.0, gd)
+        torch.cuda.synchronize()
+        times = []
+        for _ in range(max(1, args.steps)):
+            t0 = time.perf_counter()
+            loss = f.forward(vd)
+            f.backward(1.0, gd)
+            torch.cuda.synchronize()
+            times.append(time.perf_counter() - t0)
+        info = f.info()
+        out[N] = {"n": n, "nnz": int(len(v)), "setup_s": setup, "s_per_gradient": min(times),
+                  "median_s": statistics.median(times), "loss": loss,
+                  "grad_norm": float(torch.linalg.vector_norm(gd).item()), **info}
+        f.close()
+    if rank == 0:
+        print(json.dumps({
+            "metric": "gradients/s of ||I - A M_10||_F^2 w.r.t. A's values (128^3)",
+            "value": ws / out[128]["median_s"], "unit": "gradients/s", "n_gpus": ws,
+            "higher_is_better": True, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "fpmr_varcoef3d", "K": 10, "checkpoints": "M per step"},
+            "cases": out}))
+
+
 def profile_bpcg(prec):
     """Launch sequence for ncu captures of the block PCG kernels: the 64-matrix
     batch, 30 LOMR iterations, one block solve (products in `prec`)."""
@@ -603,7 +650,8 @@ def main():
                     help="profiling case for ncu: 3 iterations of one method on the workload, "
                          "or (bpcg) one block PCG solve of the 64-matrix batch")
     ap.add_argument("--prec", choices=["mixed", "fp64"], default="mixed")
-    ap.add_argument("--workload", choices=[WORKLOAD, "batch64", "aniso1024"], default=WORKLOAD)
+    ap.add_argument("--workload", choices=[WORKLOAD, "batch64", "aniso1024", "fpmr"],
+                    default=WORKLOAD)
     args = ap.parse_args()
     if args.profile == "bpcg":
         profile_bpcg(args.prec)
@@ -613,6 +661,8 @@ def main():
         run_batch(args)
     elif args.workload == "aniso1024" and args.impl == "ours":
         run_aniso(args)
+    elif args.workload == "fpmr" and args.impl == "ours":
+        run_fpmr(args)
     elif args.impl == "reference":
         run_reference(args)
     else:
