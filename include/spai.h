@@ -180,6 +180,16 @@ int spai_set_stream(spai_handle h, void *stream);
  * residual I - A M (Sec. 6.2).  hist may be NULL.  Returns SPAI_OK,
  * SPAI_CONVERGED_EARLY, SPAI_LOMR_FALLBACK or an error. */
 int spai_run(spai_handle h, int method, int iters, int drop_rule, spai_history *hist);
+
+/* Launch-shape autotuner (no counterpart in the paper).  For the column
+ * passes that `method` uses, times `iters` iterations from M_0 with each
+ * candidate shape (1..4 CTAs per SM x 1, 2, 4 or 8 columns per warp) and
+ * keeps the fastest for later calls.  Results do not depend on the shape
+ * (column sums are order-free and the Frobenius tree runs over column
+ * indices), so only the time changes.  Leaves M = diag(A)^{-1} and no
+ * recurrence.  *best_ms (may be NULL): the chosen shape's time per
+ * iteration. */
+int spai_autotune(spai_handle h, int method, int iters, double *best_ms);
 int spai_mr(spai_handle h, int iters, int drop_rule, spai_history *hist);
 int spai_lomr(spai_handle h, int iters, int drop_rule, spai_history *hist);
 int spai_cg(spai_handle h, int iters, int drop_rule, spai_history *hist);

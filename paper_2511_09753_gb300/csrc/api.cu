@@ -86,6 +86,8 @@ struct spai_ctx {
   double* d_pi = nullptr;
   PassCfg cfg_pi[4];
   bool pi_ok = false;
+  // inputs of make_cfg kept for the launch-shape autotuner
+  int smem_max = 0, Bmin = 1, Bmax = 1024;
   // batched mode: nseg matrices laid block-diagonally, each padded with
   // identity rows/columns to a multiple of kSegAlign
   int nseg = 0;
@@ -274,7 +276,7 @@ static int env_int(const char* name, int dflt) {
 }
 
 PassCfg make_cfg(int kind, int vc, int n, int CAP, int W, bool dia, int smem_max, int Bmin = 1,
-                 int Bmax = 1024, bool pi = false) {
+                 int Bmax = 1024, bool pi = false, int occ_req = 0, int cpw_req = 0) {
   PassCfg c;
   memset(&c, 0, sizeof(c));
   c.lay = make_layout(kind, vc, CAP, W, dia, pi);
@@ -283,8 +285,8 @@ PassCfg make_cfg(int kind, int vc, int n, int CAP, int W, bool dia, int smem_max
   // defaults measured on GB300 (64^3 operator, cap 3): LOMR's large scratch
   // prefers 8-warp CTAs at two per SM, the CG passes four CTAs per SM
   const int occ_default = kind == kLOMR ? 2 : (kind == kMR ? 3 : 4);
-  const int occ = env_int("SPAI_COLPASS_OCC", occ_default);
-  const int cpw = env_int("SPAI_COLPASS_CPW", 4);
+  const int occ = occ_req > 0 ? occ_req : env_int("SPAI_COLPASS_OCC", occ_default);
+  const int cpw = cpw_req > 0 ? cpw_req : env_int("SPAI_COLPASS_CPW", 4);
   c.ok = false;
   for (int NW = 8; NW >= 1; NW >>= 1) {
     // B: columns per CTA, a power of two: cpw per warp, fewer when n is
@@ -865,6 +867,18 @@ int create_impl(spai_handle* out, int64_t n, int64_t nnz, const int32_t* rp, con
     h->red_nb = std::max(h->red_nb, h->cfg[k].nb);
     h->red_ng = std::max(h->red_ng, h->cfg[k].ngroups);
   }
+  h->smem_max = smem_max;
+  {
+    int Bmin = 1, Bmax = 1024;
+    if (bd) {
+      long long npmax = 0;
+      for (int m = 0; m < bd->nseg; m++) npmax = std::max(npmax, bd->npad[m]);
+      while ((long long)Bmin * 1024 < npmax) Bmin *= 2;
+      Bmax = kSegAlign;
+    }
+    h->Bmin = Bmin;
+    h->Bmax = Bmax;
+  }
   h->pi_ok = true;
   for (int k = 0; k < 4; k++) {
     int Bmin = 1, Bmax = 1024;
@@ -1219,6 +1233,72 @@ int spai_run(spai_handle h, int method, int iters, int drop_rule, spai_history* 
   }
   if (sc.flags & kFlagFallback) return SPAI_LOMR_FALLBACK;
   return SPAI_OK;
+}
+
+int spai_autotune(spai_handle h, int method, int iters, double* best_ms) {
+  if (!h || iters < 1 || method < SPAI_MR || method > SPAI_CG_PI) return SPAI_ERR_ARG;
+  const bool pim = method >= SPAI_MR_PI;
+  if (pim && !h->pi_ok) return SPAI_ERR_UNSUPPORTED;
+  const int base = pim ? method - SPAI_MR_PI : method;
+  int kinds[2] = {base == SPAI_MR ? kMR : base == SPAI_LOMR ? kLOMR : kCGA, kCGB};
+  const int nk = base == SPAI_CG ? 2 : 1;
+  PassCfg* cfgs = pim ? h->cfg_pi : h->cfg;
+  const int vc = h->prec == SPAI_MIXED ? 4 : 8;
+  PassCfg keep[2] = {cfgs[kinds[0]], cfgs[kinds[1]]};
+  double best = 1e300;
+  PassCfg bestc[2] = {keep[0], keep[1]};
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CK(cudaEventCreate(&e0));
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    (void)cudaGetLastError();
+    return SPAI_ERR_CUDA;
+  }
+  int rc = SPAI_OK;
+  for (int occ = 1; occ <= 4 && !rc; occ++)
+    for (int cpw = 1; cpw <= 8 && !rc; cpw *= 2) {
+      PassCfg c[2];
+      bool ok = true;
+      for (int q = 0; q < nk; q++) {
+        c[q] = make_cfg(kinds[q], vc, h->n, h->capmax, h->W, h->dia, h->smem_max, h->Bmin, h->Bmax,
+                        pim, occ, cpw);
+        ok &= c[q].ok && c[q].nb <= h->red_nb && c[q].ngroups <= h->red_ng;
+      }
+      if (!ok) continue;
+      for (int q = 0; q < nk; q++) cfgs[kinds[q]] = c[q];
+      rc = spai_reset(h);
+      if (!rc) {
+        int r1 = spai_run(h, method, 1, SPAI_DROP_TOPK_COL, nullptr);  // warm-up
+        if (r1 < 0) rc = r1;
+      }
+      if (!rc) rc = spai_reset(h);
+      if (rc) break;
+      cudaEventRecord(e0, h->stream);
+      int r2 = spai_run(h, method, iters, SPAI_DROP_TOPK_COL, nullptr);
+      cudaEventRecord(e1, h->stream);
+      if (r2 < 0) {
+        rc = r2;
+        break;
+      }
+      float ms = 0.f;
+      if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+        rc = SPAI_ERR_CUDA;
+        break;
+      }
+      const double per = (double)ms / iters;
+      if (per < best) {
+        best = per;
+        bestc[0] = c[0];
+        bestc[1] = c[1];
+      }
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  for (int q = 0; q < nk; q++) cfgs[kinds[q]] = rc ? keep[q] : bestc[q];
+  int r3 = spai_reset(h);
+  if (rc) return rc;
+  if (best_ms) *best_ms = best;
+  return r3;
 }
 
 int spai_batch_info(spai_handle h, int* nmat, int64_t* n_each) {

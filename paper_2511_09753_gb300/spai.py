@@ -33,7 +33,7 @@ EXPORTED = ["spai_validate_csr", "spai_status_string", "spai_create", "spai_dest
             "spai_batch_info", "spai_batch_history", "spai_batch_residual_norms",
             "spai_batch_get_M", "pcg_solve_block", "spai_set_pcg_prec", "spai_sym_lanczos",
             "spai_fixed_pattern", "spai_fpmr_create", "spai_fpmr_forward", "spai_fpmr_backward",
-            "spai_fpmr_info", "spai_fpmr_destroy"]
+            "spai_fpmr_info", "spai_fpmr_destroy", "spai_autotune"]
 
 
 class SpaiError(RuntimeError):
@@ -94,6 +94,7 @@ def load():
         "spai_fpmr_backward": (i32, [vp, dbl, vp, i32]),
         "spai_fpmr_info": (i32, [vp, C.POINTER(i64), C.POINTER(i64), C.POINTER(i64)]),
         "spai_fpmr_destroy": (i32, [vp]),
+        "spai_autotune": (i32, [vp, i32, i32, C.POINTER(dbl)]),
         "spai_sym_lanczos": (i32, [vp, i32, vp, vp, vp, C.POINTER(i32), C.POINTER(dbl),
                                    C.POINTER(dbl)]),
         "spai_save_state": (i32, [vp, vp, C.POINTER(C.c_size_t)]),
@@ -330,6 +331,13 @@ class Spai:
                 o += R * n
         return dict(status=rc, iters=it.reshape(k, R), statuses=st.reshape(k, R),
                     relres=rr.reshape(k, R), x=x)
+
+    def autotune(self, method, iters=3):
+        """Pick the fastest launch shape for `method` (resets M); returns ms per iteration."""
+        m = METHODS[method] if isinstance(method, str) else int(method)
+        out = C.c_double()
+        self._check(self.lib.spai_autotune(self.h, m, int(iters), C.byref(out)), "spai_autotune")
+        return out.value
 
     def fixed_pattern(self, k):
         """M := the best approximate inverse on supp(A^k) (column least squares)."""

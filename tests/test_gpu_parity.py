@@ -174,3 +174,18 @@ def test_table2_spgemm_counts_on_gpu():
         g.run(m, K)
         used = g.stats()["spgemm_columns"] - s0
         assert used == n * (per * K + extra), (m, used)
+
+
+@pytest.mark.parametrize("method", ["mr", "lomr", "cg", "lomr_pi"])
+def test_autotune_keeps_results_bitwise(method):
+    """Any launch shape the autotuner picks gives the same iterates."""
+    spai = _spai()
+    n, rp, ci, v = I.varcoef_3d_7pt(16, seed=3)
+    a = spai.Spai(n, rp, ci, v, prec="mixed", cap_factor=3.0)
+    ra = a.run(method, 6)
+    b = spai.Spai(n, rp, ci, v, prec="mixed", cap_factor=3.0)
+    ms = b.autotune(method, 2)
+    assert ms > 0
+    rb = b.run(method, 6)
+    np.testing.assert_array_equal(ra["resnorm"], rb["resnorm"])
+    assert _same(a.get_M(), b.get_M())
