@@ -293,6 +293,30 @@ int spai_sym_lanczos(spai_handle h, int steps, const double *v0, double *alpha, 
  * definite. */
 int spai_fixed_pattern(spai_handle h, int k);
 
+/* ------------------------------------------------ global dropping */
+
+/* Hard thresholding with a global density cap (Sec. 6.1, Eq. 6.2): if the
+ * stored M (which = 0) or direction P (which = 1) holds more than m entries,
+ * keep the m of largest |v| (ties: smaller column, then smaller row) and
+ * drop the rest, in place.  The per-column dropping of spai_run caps each
+ * column instead; this is the paper's global form, applied between calls.
+ * Forgets the method recurrence.  Single-matrix handles only. */
+int spai_drop_global(spai_handle h, int which, int64_t m);
+
+/* The dropping heuristic for the main iterate (Appendix A), in place:
+ * (1) M := (M + M^T)/2 (s_kl = 0.5 (m_kl + m_lk) in FP64, rounded to the
+ * value type); (2) off-diagonal entries with |m_kl| < u dropped, u the unit
+ * round-off of the value type (2^-53 FP64, 2^-24 FP32); (3) if more than m
+ * entries remain, the off-diagonal entries of smallest score
+ * s_kl = m_kl^2 ||A e_k||^2 + 2 m_kl (A R)_kl (Eq. 435 with the m^2 of
+ * Eq. 430: the change of ||R||_F^2 when that entry alone is dropped;
+ * R = I - A M after steps 1-2, in the method's arithmetic; ||A e_k||^2 and
+ * (A R)_kl FP64 fma chains over row k of A; s = fma(2m, ar, (m m) nrm)) are
+ * dropped until m remain (the diagonal is always kept; ties: smaller column,
+ * then smaller row).  SPAI_ERR_CAPACITY if a symmetrised column exceeds
+ * cap_j.  Forgets the method recurrence.  Single-matrix handles only. */
+int spai_drop_heuristic(spai_handle h, int64_t m);
+
 /* ------------------------------------------------ differentiation */
 
 /* Gradient of fixed-pattern MR (no counterpart in the paper, which gives the

@@ -1,0 +1,121 @@
+"""Oracle for the paper's global dropping operators (test infrastructure).
+
+Hard thresholding with a global density cap (Sec. 6.1, Eq. 6.2 / 445):
+when |supp(X)| > m, keep the m entries of largest |x|; ties go to the
+smaller (column, row) position.
+
+The dropping heuristic for the main iterate (Appendix A):
+  1. M := (M + M^T) / 2  (s_kl = 0.5 (m_kl + m_lk) in FP64, rounded to the
+     value type; exact zeros dropped);
+  2. drop the off-diagonal entries with |m_kl| < u, u the unit round-off of
+     the value type (2^-53 for FP64, 2^-24 for FP32 values);
+  3. if |supp(M)| > m, drop the |supp(M)| - m off-diagonal entries of
+     smallest score s_kl = m_kl^2 ||A e_k||^2 + 2 m_kl (A R)_kl, R = I - A M
+     (Eq. 435 with the m^2 reading of Eq. 430: the change of ||R||_F^2 when
+     that entry alone is dropped); ties go to the smaller (column, row)
+     position, the diagonal is always kept.
+Arithmetic of the scores (shared with the kernels by definition): R's
+columns as the method computes them (an fma chain over ascending k in the
+value type, R = 1 - s on the diagonal, -s elsewhere), ||A e_k||^2 and
+(A R)_kl as FP64 fma chains over ascending column of row k of A, and
+s = fma(2 m, ar, (m m) nrm) in FP64.
+"""
+import numpy as np
+
+
+def _csc_cols(cp, ri, va):
+    return [(ri[cp[j]:cp[j + 1]].astype(np.int64), va[cp[j]:cp[j + 1]].astype(np.float64))
+            for j in range(len(cp) - 1)]
+
+
+def _to_csc(n, cols):
+    cp = [0]
+    ri, va = [], []
+    for j in range(n):
+        r, v = cols[j]
+        o = np.argsort(r, kind="stable")
+        ri.extend(r[o].tolist())
+        va.extend(v[o].tolist())
+        cp.append(len(ri))
+    return np.array(cp, np.int32), np.array(ri, np.int32), np.array(va, np.float64)
+
+
+def hard_threshold(n, M, m):
+    """Keep the m entries of largest |x| (ties: smaller (column, row))."""
+    cols = _csc_cols(*M)
+    ent = [(-abs(v), j, r) for j, (rr, vv) in enumerate(cols) for r, v in zip(rr, vv)]
+    if len(ent) <= m:
+        return M
+    ent.sort()
+    keep = set((j, r) for _, j, r in ent[:m])
+    out = []
+    for j, (rr, vv) in enumerate(cols):
+        sel = np.array([(j, int(r)) in keep for r in rr], dtype=bool)
+        out.append((rr[sel], vv[sel]))
+    return _to_csc(n, out)
+
+
+def _fma(a, b, c):
+    """Correctly rounded FP64 fma via exact rationals."""
+    from fractions import Fraction
+    return float(Fraction(a) * Fraction(b) + Fraction(c))
+
+
+def heuristic(n, rowptr, colind, vals, M, m, mixed=False):
+    """Appendix A's three steps on M (CSC triple); returns the new M."""
+    av = np.array([float(np.float32(x)) for x in vals]) if mixed else np.asarray(vals, np.float64)
+    u = 2.0 ** -24 if mixed else 2.0 ** -53
+    cols = _csc_cols(*M)
+    dense = {}
+    for j, (rr, vv) in enumerate(cols):
+        for r, v in zip(rr, vv):
+            dense[(int(r), j)] = float(v)
+    keys = set(dense) | set((j, r) for (r, j) in dense)
+    sym = {}
+    for (r, j) in keys:
+        s = 0.5 * (dense.get((r, j), 0.0) + dense.get((j, r), 0.0))
+        if mixed:
+            s = float(np.float32(s))
+        if s != 0.0 and (r == j or abs(s) >= u):
+            sym[(r, j)] = s
+    newcols = [[] for _ in range(n)]
+    for (r, j), s in sym.items():
+        newcols[j].append((r, s))
+    cols2 = []
+    for j in range(n):
+        lst = sorted(newcols[j])
+        cols2.append((np.array([a for a, _ in lst], np.int64), np.array([b for _, b in lst])))
+    if len(sym) <= m:
+        return _to_csc(n, cols2)
+    nrm = np.zeros(n)
+    for k in range(n):
+        acc = 0.0
+        for q in range(rowptr[k], rowptr[k + 1]):
+            acc = _fma(av[q], av[q], acc)
+        nrm[k] = acc
+    from oracle import Oracle
+    o = Oracle(n, rowptr, colind, vals, mixed=mixed, cap_factor=float(n))
+    o.set_M(*_to_csc(n, cols2))
+    scores = []
+    for j in range(n):
+        rr, rv = o.column_residual(j)
+        R = dict(zip(rr.tolist(), rv.tolist()))
+        for r, x in zip(*cols2[j]):
+            r = int(r)
+            if r == j:
+                continue
+            ar = 0.0
+            for q in range(rowptr[r], rowptr[r + 1]):
+                ar = _fma(av[q], R.get(int(colind[q]), 0.0), ar)
+            s = _fma(2.0 * x, ar, (x * x) * nrm[r])
+            scores.append((s, j, r))
+    ndiag = sum(1 for (r, j) in sym if r == j)
+    ndrop = len(sym) - max(m, ndiag)
+    scores.sort()
+    drop = set((j, r) for _, j, r in scores[:ndrop])
+    out = []
+    for j in range(n):
+        rr, vv = cols2[j]
+        sel = np.array([(j, int(r)) not in drop for r in rr], dtype=bool)
+        out.append((rr[sel], vv[sel]))
+    return _to_csc(n, out)

@@ -21,6 +21,7 @@
 #include "vec_kernels.cuh"
 #include "bpcg.cuh"
 #include "fixed_pattern.cuh"
+#include "dropping.cuh"
 
 using namespace spai;
 
@@ -86,6 +87,9 @@ struct spai_ctx {
   double* d_pi = nullptr;
   PassCfg cfg_pi[4];
   bool pi_ok = false;
+  // global dropping: ||A e_k||^2 per row and a score per slab entry of M
+  double *d_anrm = nullptr, *d_score = nullptr;
+  unsigned* d_hist = nullptr;
   // inputs of make_cfg kept for the launch-shape autotuner
   int smem_max = 0, Bmin = 1, Bmax = 1024;
   // batched mode: nseg matrices laid block-diagonally, each padded with
@@ -505,6 +509,9 @@ void free_all(spai_ctx* h) {
   dfree(h->d_bp);
   dfree(h->d_bq);
   dfree(h->d_bstage);
+  dfree(h->d_anrm);
+  dfree(h->d_score);
+  dfree(h->d_hist);
   dfree(h->d_aval32);
   dfree(h->d_mv32);
   dfree(h->d_sv32);
@@ -1906,6 +1913,203 @@ int spai_fixed_pattern(spai_handle h, int k) {
   h->it = 0;
   invalidate_rows(h);
   return err ? SPAI_ERR_NONFINITE : SPAI_OK;
+}
+
+// ------------------------------------------------------ global dropping
+
+// Histogram of one 16-bit digit of the selection keys (see dropping.cu)
+static int sel_hist(spai_ctx* h, SelArgs& a, std::vector<unsigned>& hh) {
+  CK(cudaMemsetAsync(h->d_hist, 0, sizeof(unsigned) * 65536, h->stream));
+  CK(launch_sel_hist(a, h->stream));
+  h->other_launches++;
+  CK(cudaMemcpyAsync(hh.data(), h->d_hist, sizeof(unsigned) * 65536, cudaMemcpyDeviceToHost,
+                     h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return SPAI_OK;
+}
+
+// t-th smallest (1-based) key of the current stage; *less = keys below it
+static int sel_select(spai_ctx* h, SelArgs& a, long long t, unsigned long long* key,
+                      long long* less) {
+  std::vector<unsigned> hh(65536);
+  a.prefix = 0;
+  a.mask = 0;
+  long long rem = t, below = 0;
+  for (int d = 0; d < 4; d++) {
+    a.shift = 48 - 16 * d;
+    int rc = sel_hist(h, a, hh);
+    if (rc) return rc;
+    long long acc = 0;
+    int bucket = -1;
+    for (int b = 0; b < 65536; b++) {
+      if (acc + hh[b] >= rem) {
+        bucket = b;
+        break;
+      }
+      acc += hh[b];
+    }
+    if (bucket < 0) return SPAI_ERR_STATE;
+    rem -= acc;
+    below += acc;
+    a.prefix |= (unsigned long long)bucket << a.shift;
+    a.mask |= 0xffffull << a.shift;
+  }
+  *key = a.prefix;
+  *less = below;
+  return SPAI_OK;
+}
+
+// Select the t first entries by (key, position) and keep (keep_selected) or
+// drop them, in place
+static int select_and_compact(spai_ctx* h, SelArgs& a, long long t, int keep_selected) {
+  if (!h->d_hist) {
+    int rc = dalloc(&h->d_hist, 65536);
+    if (rc) return rc;
+  }
+  unsigned long long ustar = 0, pstar = 0;
+  long long less = 0, less2 = 0;
+  a.stage = 0;
+  int rc = sel_select(h, a, t, &ustar, &less);
+  if (rc) return rc;
+  a.stage = 1;
+  a.ustar = ustar;
+  rc = sel_select(h, a, t - less, &pstar, &less2);
+  if (rc) return rc;
+  a.pstar = pstar;
+  a.keep_selected = keep_selected;
+  CK(launch_sel_compact(a, h->stream));
+  h->other_launches++;
+  CK(cudaStreamSynchronize(h->stream));
+  return SPAI_OK;
+}
+
+static long long count_entries(spai_ctx* h, const int* d_len) {
+  std::vector<int> l(h->n);
+  if (cudaMemcpyAsync(l.data(), d_len, sizeof(int) * h->n, cudaMemcpyDeviceToHost, h->stream) ||
+      cudaStreamSynchronize(h->stream)) {
+    (void)cudaGetLastError();
+    return -1;
+  }
+  long long s = 0;
+  for (int x : l) s += x;
+  return s;
+}
+
+int spai_drop_global(spai_handle h, int which, int64_t m) {
+  if (!h || (which != 0 && which != 1) || m < 0) return SPAI_ERR_ARG;
+  if (h->nseg) return SPAI_ERR_UNSUPPORTED;
+  int* len = which == 0 ? h->d_Mlen : h->d_Plen;
+  const long long N = count_entries(h, len);
+  if (N < 0) return SPAI_ERR_CUDA;
+  if (N > m) {
+    SelArgs a;
+    memset(&a, 0, sizeof(a));
+    a.n = h->n;
+    a.off = h->d_off;
+    a.len = len;
+    a.rows = which == 0 ? h->d_Mrow : h->d_Prow;
+    a.vals = which == 0 ? h->d_Mval : h->d_Pval;
+    a.vs = h->prec == SPAI_MIXED ? 4 : 8;
+    a.mode = 0;
+    a.hist = nullptr;
+    if (!h->d_hist) {
+      int rc = dalloc(&h->d_hist, 65536);
+      if (rc) return rc;
+    }
+    a.hist = h->d_hist;
+    if (m == 0) {
+      CK(cudaMemsetAsync(len, 0, sizeof(int) * h->n, h->stream));
+    } else {
+      int rc = select_and_compact(h, a, m, 1);
+      if (rc) return rc;
+    }
+  }
+  h->method = -1;
+  invalidate_rows(h);
+  return SPAI_OK;
+}
+
+int spai_drop_heuristic(spai_handle h, int64_t m) {
+  if (!h || m < 0) return SPAI_ERR_ARG;
+  if (h->nseg) return SPAI_ERR_UNSUPPORTED;
+  cudaStream_t st = h->stream;
+  const int vs = h->prec == SPAI_MIXED ? 4 : 8;
+  // 1-2: M := (M + M^T)/2 in FP64, rounded to the value type; off-diagonal
+  // entries below the unit round-off dropped
+  int rc = ensure_rows(h, true);
+  if (rc) return rc;
+  int* d_ovf = nullptr;
+  rc = dalloc(&d_ovf, 1);
+  if (rc) return rc;
+  int ovf = 0;
+  cudaError_t e = cudaMemsetAsync(d_ovf, 0, sizeof(int), st);
+  if (!e) e = launch_sym_to_slab(h->n, h->d_srp, h->d_sci, h->d_sv, h->d_off, h->d_cap, h->d_Mrow,
+                                 h->d_Mval, h->d_Mlen, vs, vs == 4 ? 0x1p-24 : 0x1p-53, d_ovf, st);
+  if (!e) e = cudaMemcpyAsync(&ovf, d_ovf, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (!e) e = cudaStreamSynchronize(st);
+  dfree(d_ovf);
+  h->other_launches++;
+  h->method = -1;
+  invalidate_rows(h);
+  if (e) {
+    (void)cudaGetLastError();
+    return SPAI_ERR_CUDA;
+  }
+  if (ovf) return SPAI_ERR_CAPACITY;
+  const long long N = count_entries(h, h->d_Mlen);
+  if (N < 0) return SPAI_ERR_CUDA;
+  if (N <= m) return SPAI_OK;
+  // 3: scores m^2 ||A e_k||^2 + 2 m (A R)_kl of the off-diagonal entries
+  if (!h->d_anrm) {
+    rc = dalloc(&h->d_anrm, h->n);
+    if (!rc) rc = dalloc(&h->d_score, (size_t)h->slab_total);
+    if (rc) return rc;
+    CK(launch_anrm(h->n, h->W, h->d_ell_col, vs == 4 ? (const void*)h->d_ell32 : (const void*)h->d_ell64,
+                   vs, h->d_anrm, st));
+    h->other_launches++;
+  }
+  rc = reset_call_scalars(h);
+  if (rc) return rc;
+  PassParams p = base_params(h, kRES, false);
+  p.kind = kSCORE;
+  p.do_dir = 0;
+  p.hist_res = nullptr;
+  p.hist_coef = nullptr;
+  p.score = h->d_score;
+  p.anrm = h->d_anrm;
+  CK(timed_launch(h, p, h->cfg[kRES], false));
+  SelArgs a;
+  memset(&a, 0, sizeof(a));
+  a.n = h->n;
+  a.off = h->d_off;
+  a.len = h->d_Mlen;
+  a.rows = h->d_Mrow;
+  a.vals = h->d_Mval;
+  a.vs = vs;
+  a.score = h->d_score;
+  a.mode = 1;
+  if (!h->d_hist) {
+    rc = dalloc(&h->d_hist, 65536);
+    if (rc) return rc;
+  }
+  a.hist = h->d_hist;
+  // eligible (off-diagonal) entries: the first digit's histogram total
+  std::vector<unsigned> hh(65536);
+  a.stage = 0;
+  a.prefix = 0;
+  a.mask = 0;
+  a.shift = 48;
+  rc = sel_hist(h, a, hh);
+  if (rc) return rc;
+  long long E = 0;
+  for (unsigned x : hh) E += x;
+  const long long D = std::min(N - (long long)m, E);
+  if (D > 0) {
+    rc = select_and_compact(h, a, D, 0);
+    if (rc) return rc;
+  }
+  invalidate_rows(h);
+  return SPAI_OK;
 }
 
 // ------------------------------------------------------------ block PCG

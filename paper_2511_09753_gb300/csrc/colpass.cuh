@@ -119,6 +119,36 @@ __device__ void column_work(ColCtx<VS, VC>& c, int j, double* part) {
 
   int Lm = load_col(c, p.Mrow, p.Mval, off, p.Mlen[j], Mr, Mv);
 
+  if (p.kind == kSCORE) {
+    // Appendix A, Eq. 430: dropping m_kj alone changes ||R||_F^2 by
+    // m^2 ||A e_k||^2 + 2 m (A R)_kj; (A R)_kj from row k of A and the R table
+    int cnt = spgemm(p, ha, Mr, Mv, Lm, j, Tr, Tv, lane, c.seg);
+    table_to_list(ha, cnt, j, Rr, Rv, lane);  // the table now holds R
+    c.spg++;
+    const VC* av = (const VC*)p.ell_val;
+    for (int e = lane; e < Lm; e += 32) {
+      const int k = Mr[e];
+      double s;
+      if (k == j) {
+        s = __longlong_as_double(0x7ff0000000000000ll);  // the diagonal is kept
+      } else {
+        const double m = (double)Mv[e];
+        double ar = 0.0;
+        for (int t = 0; t < p.W; t++) {
+          const int col = p.ell_col[(long long)k * p.W + t];
+          if (col < 0) break;
+          ar = __fma_rn((double)av[(long long)k * p.W + t], (double)hash_find<VC>(ha, col), ar);
+        }
+        s = __fma_rn(__dmul_rn(2.0, m), ar, __dmul_rn(__dmul_rn(m, m), p.anrm[k]));
+      }
+      p.score[off + e] = s;
+    }
+    __syncwarp();
+    hash_clear(ha, cnt, lane);
+    part[0] = 0.0;
+    return;
+  }
+
   if (p.kind == kRES) {
     int cnt = spgemm(p, ha, Mr, Mv, Lm, j, Tr, Tv, lane, c.seg);
     int LR = table_to_list(ha, cnt, j, Rr, Rv, lane);
@@ -302,7 +332,7 @@ __device__ __forceinline__ bool isfin(double x) { return !isnan(x) && !isinf(x);
 __device__ inline void coefficients(const PassParams& p, DevScalars* sc, double* hist_res,
                                     double* hist_coef, const double* t) {
   const int it = p.iter;
-  if (p.kind == kRES) {
+  if (p.kind == kRES || p.kind == kSCORE) {
     sc->result = t[0];
     return;
   }
@@ -428,7 +458,7 @@ __global__ void __launch_bounds__(256, 3) colpass_kernel(const PassParams p) {
       h0.key = c.template at<int>(p.lay.gk);
       hash_clear_all(h0, lane);
     }
-    if (p.kind != kRES) {
+    if (p.kind != kRES && p.kind != kSCORE) {
       h0.key = c.template at<int>(p.lay.uk);
       h0.H = p.lay.HU;
       hash_clear_all(h0, lane);

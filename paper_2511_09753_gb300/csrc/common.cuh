@@ -36,6 +36,7 @@ enum PassKind : int {
   kCGA = 2,    // M = D(M + alpha P); R; partial rr
   kCGB = 3,    // R; P = D(R + beta P); Q = A P; partials rr, pq
   kRES = 4,    // R = I - A M in FP64; partial rr
+  kSCORE = 5,  // R = I - A M, then the Appendix A drop score of every entry of M
 };
 
 // Byte offsets of one warp's scratch inside the CTA's dynamic shared memory.
@@ -78,6 +79,8 @@ struct PassParams {
   int dia_off[32];       // the offsets, ascending
   const void* dia_val;   // VC values [n][Dp], 0 where row k has no entry k+off
   const double* pi;      // Pi = diag(A)^{-1} per row (Pi-preconditioned forms), else null
+  double* score;         // kSCORE: drop score per slab entry of M (+inf on the diagonal)
+  const double* anrm;    // kSCORE: ||A e_k||^2 per row k
   DevScalars* sc;
   double* hist_res;      // [iters+1]
   double* hist_coef;     // [2*iters]

@@ -33,7 +33,8 @@ EXPORTED = ["spai_validate_csr", "spai_status_string", "spai_create", "spai_dest
             "spai_batch_info", "spai_batch_history", "spai_batch_residual_norms",
             "spai_batch_get_M", "pcg_solve_block", "spai_set_pcg_prec", "spai_sym_lanczos",
             "spai_fixed_pattern", "spai_fpmr_create", "spai_fpmr_forward", "spai_fpmr_backward",
-            "spai_fpmr_info", "spai_fpmr_destroy", "spai_autotune"]
+            "spai_fpmr_info", "spai_fpmr_destroy", "spai_autotune", "spai_drop_global",
+            "spai_drop_heuristic"]
 
 
 class SpaiError(RuntimeError):
@@ -95,6 +96,8 @@ def load():
         "spai_fpmr_info": (i32, [vp, C.POINTER(i64), C.POINTER(i64), C.POINTER(i64)]),
         "spai_fpmr_destroy": (i32, [vp]),
         "spai_autotune": (i32, [vp, i32, i32, C.POINTER(dbl)]),
+        "spai_drop_global": (i32, [vp, i32, i64]),
+        "spai_drop_heuristic": (i32, [vp, i64]),
         "spai_sym_lanczos": (i32, [vp, i32, vp, vp, vp, C.POINTER(i32), C.POINTER(dbl),
                                    C.POINTER(dbl)]),
         "spai_save_state": (i32, [vp, vp, C.POINTER(C.c_size_t)]),
@@ -338,6 +341,15 @@ class Spai:
         out = C.c_double()
         self._check(self.lib.spai_autotune(self.h, m, int(iters), C.byref(out)), "spai_autotune")
         return out.value
+
+    def drop_global(self, m, which="M"):
+        """Keep the m largest-|v| entries of M (or of P) over the whole matrix."""
+        self._check(self.lib.spai_drop_global(self.h, 0 if which == "M" else 1, int(m)),
+                    "spai_drop_global")
+
+    def drop_heuristic(self, m):
+        """Appendix A: symmetrise M, drop round-off entries, then by score to m entries."""
+        self._check(self.lib.spai_drop_heuristic(self.h, int(m)), "spai_drop_heuristic")
 
     def fixed_pattern(self, k):
         """M := the best approximate inverse on supp(A^k) (column least squares)."""

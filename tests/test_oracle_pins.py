@@ -619,3 +619,55 @@ def test_fpmr_gradient_matches_central_differences(K):
         vm[e] -= h
         fd = (fpmr.forward(n, rp, ci, vp, K) - fpmr.forward(n, rp, ci, vm, K)) / (2 * h)
         assert abs(fd - g[e]) <= 1e-6 * max(abs(g).max(), 1e-300), (e, fd, g[e])
+
+
+# ------------------------------------------ global dropping (Sec. 6.1, App. A)
+
+def test_hard_threshold_global_cap_brute_force():
+    from oracle import dropping as D
+    n, rp, ci, v = lap2d(6)
+    o = O.Oracle(n, rp, ci, v, cap_factor=3.0)
+    o.run("mr", 3)
+    cp, ri, va = o.get_M()
+    for m in (n, 2 * n, len(va) - 3, len(va) + 5):
+        k = D.hard_threshold(n, (cp, ri, va), m)
+        ent = sorted((-abs(va[e]), j, ri[e]) for j in range(n) for e in range(cp[j], cp[j + 1]))
+        want = sorted((j, r) for _, j, r in ent[:m])
+        got = sorted((j, int(k[1][e])) for j in range(n) for e in range(k[0][j], k[0][j + 1]))
+        assert got == want
+
+
+def test_heuristic_scores_are_the_exact_single_drop_change():
+    """Eq. 430: dropping one entry m_kl changes ||R||_F^2 by
+    m_kl^2 ||A e_k||^2 + 2 m_kl (A R)_kl; the heuristic drops the entries
+    of smallest change and keeps the diagonal."""
+    from oracle import dropping as D
+    n, rp, ci, v = I.varcoef_grid((5, 6), seed=1)
+    A = I.csr_to_dense(n, rp, ci, v)
+    o = O.Oracle(n, rp, ci, v, cap_factor=3.0)
+    o.run("lomr", 4)
+    Mc = o.get_M()
+    M = dense_from_csc(n, *Mc)
+    S = 0.5 * (M + M.T)
+    S[np.abs(S) < 2.0 ** -53] = 0.0
+    R = np.eye(n) - A @ S
+    base = np.sum(R * R)
+    nz = [(k, l) for k in range(n) for l in range(n) if S[k, l] != 0 and k != l]
+    change = {}
+    for (k, l) in nz:
+        S2 = S.copy()
+        S2[k, l] = 0.0
+        R2 = np.eye(n) - A @ S2
+        change[(k, l)] = np.sum(R2 * R2) - base
+        pred = S[k, l] ** 2 * np.sum(A[:, k] ** 2) + 2 * S[k, l] * (A @ R)[k, l]
+        assert abs(change[(k, l)] - pred) <= 1e-10 * max(1.0, base)
+    m = len(nz) + n - 25
+    out = D.heuristic(n, rp, ci, v, Mc, m)
+    Mo = dense_from_csc(n, *out)
+    assert np.all(np.diag(Mo) == np.diag(S))               # diagonal kept
+    order = sorted(change, key=lambda kl: (change[kl], kl[1], kl[0]))
+    assert change[order[25]] - change[order[24]] > 1e-9 * max(1.0, base)  # no near-tie at the cut
+    assert set((k, l) for (k, l) in nz if Mo[k, l] == 0) == set(order[:25])
+    # entries that stay keep the symmetrised values
+    keep = Mo != 0
+    assert np.array_equal(Mo[keep], S[keep])
