@@ -59,6 +59,22 @@ def _dist():
     return ws, rank, local
 
 
+def max_over_ranks(x, dist, device="cuda"):
+    """The largest value of x over all ranks (x itself without a process group)."""
+    if not dist:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world, units_per_rank, seconds):
+    """Whole-job throughput of independent replicas: every rank processes
+    units_per_rank in the slowest rank's time."""
+    return world * units_per_rank / seconds
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -182,13 +198,9 @@ def run_ours(args):
     clk = clocks.stop()
     s1 = g.stats()
     g.set_timing(False)
-    ms_step = sum(times) / len(times)
-    if dist:
-        t = torch.tensor([ms_step], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step = float(t.item())
+    ms_step = max_over_ranks(sum(times) / len(times), dist)
     total_iters = ITERS * len(METHODS)
-    value = ws * total_iters / (ms_step * 1e-3)
+    value = job_throughput(ws, total_iters, ms_step * 1e-3)
 
     # dominant kernel: the column pass (timed per launch inside the library)
     launches = s1["colpass_launches"] - s0["colpass_launches"]
@@ -227,11 +239,7 @@ def run_ours(args):
     for _ in range(e2e_steps):
         h2d, d2h = e2e_step()
     torch.cuda.synchronize()
-    e2e_s = (time.perf_counter() - t0) / e2e_steps
-    if dist:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks((time.perf_counter() - t0) / e2e_steps, dist)
 
     # FP64 path, same workload, one step (reported beside the mixed path)
     g64 = Spai(n, rp, ci, v, prec="fp64", cap_factor=CAP)
@@ -372,13 +380,9 @@ def run_batch(args):
     clk = clocks.stop()
     s1 = g.stats()
     g.set_timing(False)
-    ms_step = sum(times) / len(times)
-    if dist:
-        t = torch.tensor([ms_step], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step = float(t.item())
+    ms_step = max_over_ranks(sum(times) / len(times), dist)
     units = len(mats) * BATCH_ITERS
-    value = ws * units / (ms_step * 1e-3)
+    value = job_throughput(ws, units, ms_step * 1e-3)
     launches = s1["colpass_launches"] - s0["colpass_launches"]
     cp_ms = s1["colpass_ms"] - s0["colpass_ms"]
     cp_bytes = s1["colpass_bytes"] - s0["colpass_bytes"]
