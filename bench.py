@@ -545,10 +545,10 @@ def run_fpmr(args):
     ws, rank, local = _dist()
     torch.cuda.set_device(local)
     out = {}
-    for N in (32, 128):
+    for N, prec in ((32, "fp64"), (128, "fp64"), (128, "mixed")):
         n, rp, ci, v = I.varcoef_3d_7pt(N, sigma=1.5, ell=8.0, seed=0)
         t0 = time.perf_counter()
-        f = FixedPatternMR(n, rp, ci, 10)
+        f = FixedPatternMR(n, rp, ci, 10, prec=prec)
         setup = time.perf_counter() - t0
         vd = torch.tensor(v, dtype=torch.float64, device="cuda")
         gd = torch.empty_like(vd)
@@ -564,14 +564,14 @@ def run_fpmr(args):
             torch.cuda.synchronize()
             times.append(time.perf_counter() - t0)
         info = f.info()
-        out[N] = {"n": n, "nnz": int(len(v)), "setup_s": setup, "s_per_gradient": min(times),
+        out[f"{N}_{prec}"] = {"n": n, "nnz": int(len(v)), "setup_s": setup, "s_per_gradient": min(times),
                   "median_s": statistics.median(times), "loss": loss,
                   "grad_norm": float(torch.linalg.vector_norm(gd).item()), **info}
         f.close()
     if rank == 0:
         print(json.dumps({
             "metric": "gradients/s of ||I - A M_10||_F^2 w.r.t. A's values (128^3)",
-            "value": ws / out[128]["median_s"], "unit": "gradients/s", "n_gpus": ws,
+            "value": ws / out["128_fp64"]["median_s"], "unit": "gradients/s", "n_gpus": ws,
             "higher_is_better": True, "dtype": "f64", "data": "synthetic",
             "config": {"workload": "fpmr_varcoef3d", "K": 10, "checkpoints": "M per step"},
             "cases": out}))

@@ -334,12 +334,14 @@ int spai_drop_heuristic(spai_handle h, int64_t m);
  * (one checkpoint per step; R, P, Q are recomputed in the backward pass);
  * SPAI_ERR_NONFINITE if some (Q_i, Q_i) is zero.  spai_fpmr_backward writes
  * dloss * dL/dvals (nnz, CSR order, host or device) for the values of the
- * last forward call (SPAI_ERR_STATE without one).  FP64 throughout.  The
- * handle owns its device memory: about (K + 6) nnz(A) + 5 nnz(T) doubles and
- * 6 int32 per product-list entry. */
+ * last forward call (SPAI_ERR_STATE without one).  prec: SPAI_FP64, or
+ * SPAI_MIXED (values and the products' fma chains in FP32; inner products,
+ * step scalars and the axpy/accumulation arithmetic in FP64, each stored
+ * value rounded once to FP32).  The handle owns its device memory: about
+ * (K + 6) nnz(A) + 5 nnz(T) values and 6 int32 per product-list entry. */
 typedef struct spai_fpmr_ctx *spai_fpmr_handle;
 int spai_fpmr_create(spai_fpmr_handle *out, int64_t n, int64_t nnz, const int32_t *rowptr,
-                     const int32_t *colind, int K, void *stream);
+                     const int32_t *colind, int K, int prec, void *stream);
 int spai_fpmr_forward(spai_fpmr_handle h, const double *vals, int on_device, double *loss);
 int spai_fpmr_backward(spai_fpmr_handle h, double dloss, double *dvals, int on_device);
 /* nnz(T), product-list entries and kernel launches so far (any may be NULL). */

@@ -15,7 +15,9 @@
 // the host in the order of the fma chain (ascending inner index) by merging
 // sorted rows, so the GPU side is a gather-fma per output entry.  The
 // backward pass recomputes R_i, P_i, Q_i from the stored M_i (one checkpoint
-// per step).  FP64 throughout.
+// per step).  Values are FP64, or FP32 on the mixed path (FP32 products and
+// stored values; inner products, step scalars and the axpy arithmetic in
+// FP64, each stored value rounded once).
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -48,10 +50,11 @@ struct spai_fpmr_ctx {
   int* d_diagT = nullptr;  // [n] position of (j,j) in T
   int* d_s2t = nullptr;    // [nS] position of S's entry in T
   ProdList Y, X, D;        // the three products (see above)
-  double *d_A = nullptr, *d_Mck = nullptr, *d_P = nullptr, *d_dM = nullptr, *d_dP = nullptr,
-         *d_dA = nullptr;
-  double *d_R = nullptr, *d_Q = nullptr, *d_dR = nullptr, *d_dQ = nullptr;
-  double *d_part = nullptr, *d_res = nullptr;
+  int vs = 8;               // bytes per stored value (8 FP64, 4 FP32)
+  void *d_A = nullptr, *d_Mck = nullptr, *d_P = nullptr, *d_dM = nullptr, *d_dP = nullptr,
+       *d_dA = nullptr;
+  void *d_R = nullptr, *d_Q = nullptr, *d_dR = nullptr, *d_dQ = nullptr;
+  double *d_part = nullptr, *d_res = nullptr, *d_stage = nullptr;
   std::vector<double> alpha, num, den;
   std::vector<double> diag;  // a_jj of the last forward values
   bool have_forward = false;
@@ -87,66 +90,108 @@ void ffree(T*& p) {
   p = nullptr;
 }
 
+int valloc(void** p, size_t count, int vs) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  if (cudaMalloc(p, (size_t)vs * count) != cudaSuccess) {
+    (void)cudaGetLastError();
+    *p = nullptr;
+    return SPAI_ERR_OOM;
+  }
+  return SPAI_OK;
+}
+
 constexpr int kDotChunk = 16;     // elements per thread in the dot partials
 constexpr int kDotBlock = 256;
 
+__device__ __forceinline__ double fma_t(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float fma_t(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+
 // out[s] (=|+=) scale * sum_t a[ia[t]] b[ib[t]] over t in [ptr[s], ptr[s+1]),
-// an fma chain in list order
+// an fma chain in list order in the value type; scale and accumulation in
+// FP64, rounded once
+template <typename T>
 __global__ void k_seg_prod(long long nout, const long long* ptr, const int* ia, const int* ib,
-                           const double* a, const double* b, double* out, double scale, int acc) {
+                           const T* a, const T* b, T* out, double scale, int acc) {
   const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= nout) return;
-  double v = 0.0;
-  for (long long t = ptr[s]; t < ptr[s + 1]; t++) v = __fma_rn(a[ia[t]], b[ib[t]], v);
-  v = __dmul_rn(scale, v);
-  out[s] = acc ? __dadd_rn(out[s], v) : v;
+  T v = T(0);
+  for (long long t = ptr[s]; t < ptr[s + 1]; t++) v = fma_t(a[ia[t]], b[ib[t]], v);
+  double w = __dmul_rn(scale, (double)v);
+  out[s] = (T)(acc ? __dadd_rn((double)out[s], w) : w);
 }
 
-__global__ void k_add_diag(int n, const int* diag, double* x, double v) {
+template <typename T>
+__global__ void k_add_diag(int n, const int* diag, T* x, double v) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j < n) x[diag[j]] = __dadd_rn(x[diag[j]], v);
+  if (j < n) x[diag[j]] = (T)__dadd_rn((double)x[diag[j]], v);
 }
 
-__global__ void k_gather(long long m, const int* idx, const double* src, double* dst) {
+template <typename T>
+__global__ void k_gather(long long m, const int* idx, const T* src, T* dst) {
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (e < m) dst[e] = src[idx[e]];
 }
 
-__global__ void k_scatter_add(long long m, const int* idx, const double* src, double* dst) {
+template <typename T>
+__global__ void k_scatter_add(long long m, const int* idx, const T* src, T* dst) {
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e < m) dst[idx[e]] = __dadd_rn(dst[idx[e]], src[e]);
+  if (e < m) dst[idx[e]] = (T)__dadd_rn((double)dst[idx[e]], (double)src[e]);
 }
 
-// y = a x + b y  (b == 0: y = a x)
-__global__ void k_axby(long long m, double a, const double* x, double b, double* y) {
+// y = a x + b y in FP64 (b == 0: y = a x), rounded to the value type
+template <typename T>
+__global__ void k_axby(long long m, double a, const T* x, double b, T* y) {
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e < m) y[e] = b == 0.0 ? __dmul_rn(a, x[e]) : __fma_rn(a, x[e], __dmul_rn(b, y[e]));
+  if (e < m)
+    y[e] = (T)(b == 0.0 ? __dmul_rn(a, (double)x[e])
+                        : __fma_rn(a, (double)x[e], __dmul_rn(b, (double)y[e])));
 }
 
-// z = a x + b y
-__global__ void k_lin2(long long m, double a, const double* x, double b, const double* y,
-                       double* z) {
+// z = a x + b y in FP64, rounded to the value type
+template <typename T>
+__global__ void k_lin2(long long m, double a, const T* x, double b, const T* y, T* z) {
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e < m) z[e] = __fma_rn(a, x[e], __dmul_rn(b, y[e]));
+  if (e < m) z[e] = (T)__fma_rn(a, (double)x[e], __dmul_rn(b, (double)y[e]));
+}
+
+template <typename T>
+__global__ void k_copy(long long m, const T* x, T* y) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < m) y[e] = x[e];
+}
+
+template <typename T>
+__global__ void k_from_f64(long long m, const double* x, T* y) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < m) y[e] = (T)x[e];
+}
+
+template <typename T>
+__global__ void k_to_f64(long long m, const T* x, double* y) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < m) y[e] = (double)x[e];
 }
 
 // M0 = diag(A)^{-1} on S: zero everywhere (k_m0), then the diagonal
-__global__ void k_m0(long long nS, double* M) {
+template <typename T>
+__global__ void k_m0(long long nS, T* M) {
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e < nS) M[e] = 0.0;
+  if (e < nS) M[e] = T(0);
 }
-__global__ void k_m0_diag(int n, const int* diag, const double* A, double* M) {
+template <typename T>
+__global__ void k_m0_diag(int n, const int* diag, const T* A, T* M) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j < n) M[diag[j]] = __ddiv_rn(1.0, A[diag[j]]);
+  if (j < n) M[diag[j]] = (T)__ddiv_rn(1.0, (double)A[diag[j]]);
 }
 
 // dA[(j,j)] -= dM[(j,j)] / a_jj^2  (through M_0 = diag(A)^{-1})
-__global__ void k_m0_adjoint(int n, const int* diag, const double* A, const double* dM,
-                             double* dA) {
+template <typename T>
+__global__ void k_m0_adjoint(int n, const int* diag, const T* A, const T* dM, T* dA) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= n) return;
-  const double a = A[diag[j]];
-  dA[diag[j]] = __dsub_rn(dA[diag[j]], __ddiv_rn(dM[diag[j]], __dmul_rn(a, a)));
+  const double a = (double)A[diag[j]];
+  dA[diag[j]] = (T)__dsub_rn((double)dA[diag[j]], __ddiv_rn((double)dM[diag[j]], __dmul_rn(a, a)));
 }
 
 __device__ __forceinline__ double warp_sum32(double v) {
@@ -155,15 +200,16 @@ __device__ __forceinline__ double warp_sum32(double v) {
   return v;
 }
 
-// per block: kDotBlock * kDotChunk consecutive products x_e y_e summed in a
-// fixed order (sequential per thread, then a tree)
-__global__ void k_dot_part(long long m, const double* x, const double* y, double* part) {
+// per block: kDotBlock * kDotChunk consecutive products x_e y_e (promoted to
+// FP64) summed in a fixed order (sequential per thread, then a tree)
+template <typename T>
+__global__ void k_dot_part(long long m, const T* x, const T* y, double* part) {
   __shared__ double red[kDotBlock / 32];
   const long long base = (long long)blockIdx.x * kDotBlock * kDotChunk + threadIdx.x * kDotChunk;
   double s = 0.0;
   for (int t = 0; t < kDotChunk; t++) {
     const long long e = base + t;
-    if (e < m) s = __fma_rn(x[e], y[e], s);
+    if (e < m) s = __fma_rn((double)x[e], (double)y[e], s);
   }
   s = warp_sum32(s);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
@@ -191,23 +237,54 @@ __global__ void k_dot_final(long long nb, const double* part, double* out) {
 
 inline unsigned nblk(long long m) { return (unsigned)((m + 255) / 256); }
 
-int seg_prod(spai_fpmr_ctx* h, const ProdList& L, const double* a, const double* b, double* out,
+// the kernels above for the handle's value type
+template <typename T>
+struct Ops {
+  static int seg_prod(spai_fpmr_ctx* h, const ProdList& L, const void* a, const void* b, void* out,
+                      double scale, int acc) {
+    k_seg_prod<T><<<nblk(L.nout), 256, 0, h->stream>>>(L.nout, L.ptr, L.ia, L.ib, (const T*)a,
+                                                        (const T*)b, (T*)out, scale, acc);
+    h->launches++;
+    FCK(cudaGetLastError());
+    return SPAI_OK;
+  }
+  static int dot(spai_fpmr_ctx* h, long long m, const void* x, const void* y, int slot) {
+    const long long nb = (m + (long long)kDotBlock * kDotChunk - 1) / ((long long)kDotBlock * kDotChunk);
+    k_dot_part<T><<<(unsigned)std::max(nb, 1LL), kDotBlock, 0, h->stream>>>(m, (const T*)x, (const T*)y,
+                                                                            h->d_part);
+    k_dot_final<<<1, 1024, 0, h->stream>>>(std::max(nb, 1LL), h->d_part, h->d_res + slot);
+    h->launches += 2;
+    FCK(cudaGetLastError());
+    return SPAI_OK;
+  }
+};
+
+int seg_prod(spai_fpmr_ctx* h, const ProdList& L, const void* a, const void* b, void* out,
              double scale, int acc) {
-  k_seg_prod<<<nblk(L.nout), 256, 0, h->stream>>>(L.nout, L.ptr, L.ia, L.ib, a, b, out, scale, acc);
-  h->launches++;
-  FCK(cudaGetLastError());
-  return SPAI_OK;
+  return h->vs == 4 ? Ops<float>::seg_prod(h, L, a, b, out, scale, acc)
+                    : Ops<double>::seg_prod(h, L, a, b, out, scale, acc);
 }
 
 // (x, y) over m entries, into h->d_res[slot] (device)
-int dot(spai_fpmr_ctx* h, long long m, const double* x, const double* y, int slot) {
-  const long long nb = (m + (long long)kDotBlock * kDotChunk - 1) / ((long long)kDotBlock * kDotChunk);
-  k_dot_part<<<(unsigned)std::max(nb, 1LL), kDotBlock, 0, h->stream>>>(m, x, y, h->d_part);
-  k_dot_final<<<1, 1024, 0, h->stream>>>(std::max(nb, 1LL), h->d_part, h->d_res + slot);
-  h->launches += 2;
-  FCK(cudaGetLastError());
-  return SPAI_OK;
+int dot(spai_fpmr_ctx* h, long long m, const void* x, const void* y, int slot) {
+  return h->vs == 4 ? Ops<float>::dot(h, m, x, y, slot) : Ops<double>::dot(h, m, x, y, slot);
 }
+
+inline void* at(void* base, int vs, long long idx) { return (char*)base + (size_t)vs * idx; }
+
+// launch KERNEL<T_> with T_ the handle's value type (T_ may appear in the
+// arguments)
+#define FP_DISPATCH(h, KERNEL, GRID, ...)                                          \
+  do {                                                                             \
+    if ((h)->vs == 4) {                                                            \
+      using T_ = float;                                                            \
+      KERNEL<T_><<<(GRID), 256, 0, (h)->stream>>>(__VA_ARGS__);                    \
+    } else {                                                                       \
+      using T_ = double;                                                           \
+      KERNEL<T_><<<(GRID), 256, 0, (h)->stream>>>(__VA_ARGS__);                    \
+    }                                                                              \
+    (h)->launches++;                                                               \
+  } while (0)
 
 int read_res(spai_fpmr_ctx* h, double* out, int count) {
   FCK(cudaMemcpyAsync(out, h->d_res, sizeof(double) * count, cudaMemcpyDeviceToHost, h->stream));
@@ -216,11 +293,18 @@ int read_res(spai_fpmr_ctx* h, double* out, int count) {
 }
 
 // R = I - A M (on T), P = mask_S(R), Q = A P
-int step_products(spai_fpmr_ctx* h, const double* M, bool want_q) {
+int step_products(spai_fpmr_ctx* h, const void* M, bool want_q) {
   int rc = seg_prod(h, h->Y, h->d_A, M, h->d_R, -1.0, 0);
   if (rc) return rc;
-  k_add_diag<<<nblk(h->n), 256, 0, h->stream>>>(h->n, h->d_diagT, h->d_R, 1.0);
-  k_gather<<<nblk(h->nS), 256, 0, h->stream>>>(h->nS, h->d_s2t, h->d_R, h->d_P);
+  if (h->vs == 4) {
+    k_add_diag<float><<<nblk(h->n), 256, 0, h->stream>>>(h->n, h->d_diagT, (float*)h->d_R, 1.0);
+    k_gather<float><<<nblk(h->nS), 256, 0, h->stream>>>(h->nS, h->d_s2t, (const float*)h->d_R,
+                                                        (float*)h->d_P);
+  } else {
+    k_add_diag<double><<<nblk(h->n), 256, 0, h->stream>>>(h->n, h->d_diagT, (double*)h->d_R, 1.0);
+    k_gather<double><<<nblk(h->nS), 256, 0, h->stream>>>(h->nS, h->d_s2t, (const double*)h->d_R,
+                                                         (double*)h->d_P);
+  }
   h->launches += 2;
   FCK(cudaGetLastError());
   if (want_q) return seg_prod(h, h->Y, h->d_A, h->d_P, h->d_Q, 1.0, 0);
@@ -252,6 +336,7 @@ void free_fpmr(spai_fpmr_ctx* h) {
   ffree(h->d_dQ);
   ffree(h->d_part);
   ffree(h->d_res);
+  ffree(h->d_stage);
 }
 
 int upload_list(ProdList& L, const std::vector<long long>& ptr, const std::vector<int>& ia,
@@ -284,10 +369,11 @@ inline long long find_pos(const std::vector<long long>& ptr, const std::vector<i
 extern "C" {
 
 int spai_fpmr_create(spai_fpmr_handle* out, int64_t n, int64_t nnz, const int32_t* rowptr,
-                     const int32_t* colind, int K, void* stream) {
+                     const int32_t* colind, int K, int prec, void* stream) {
   if (!out) return SPAI_ERR_ARG;
   *out = nullptr;
   if (n < 1 || nnz < 1 || !rowptr || !colind || K < 0 || K > 1000) return SPAI_ERR_ARG;
+  if (prec != SPAI_FP64 && prec != SPAI_MIXED) return SPAI_ERR_ARG;
   if (n >= (1LL << 31) || nnz >= (1LL << 31)) return SPAI_ERR_UNSUPPORTED;
   // S: A's pattern, rows strictly ascending, symmetric, full diagonal
   std::vector<long long> sp(n + 1);
@@ -399,6 +485,7 @@ int spai_fpmr_create(spai_fpmr_handle* out, int64_t n, int64_t nnz, const int32_
   if (!h) return SPAI_ERR_OOM;
   h->n = (int)n;
   h->K = K;
+  h->vs = prec == SPAI_MIXED ? 4 : 8;
   h->nS = nS;
   h->nT = nT;
   if (stream) {
@@ -417,16 +504,18 @@ int spai_fpmr_create(spai_fpmr_handle* out, int64_t n, int64_t nnz, const int32_
   rc = rc ? rc : falloc(&h->d_diagS, n);
   rc = rc ? rc : falloc(&h->d_diagT, n);
   rc = rc ? rc : falloc(&h->d_s2t, nS);
-  rc = rc ? rc : falloc(&h->d_A, nS);
-  rc = rc ? rc : falloc(&h->d_Mck, (size_t)(K + 1) * nS);
-  rc = rc ? rc : falloc(&h->d_P, nS);
-  rc = rc ? rc : falloc(&h->d_dM, nS);
-  rc = rc ? rc : falloc(&h->d_dP, nS);
-  rc = rc ? rc : falloc(&h->d_dA, nS);
-  rc = rc ? rc : falloc(&h->d_R, nT);
-  rc = rc ? rc : falloc(&h->d_Q, nT);
-  rc = rc ? rc : falloc(&h->d_dR, nT);
-  rc = rc ? rc : falloc(&h->d_dQ, nT);
+  const int vs = h->vs;
+  rc = rc ? rc : valloc(&h->d_A, nS, vs);
+  rc = rc ? rc : valloc(&h->d_Mck, (size_t)(K + 1) * nS, vs);
+  rc = rc ? rc : valloc(&h->d_P, nS, vs);
+  rc = rc ? rc : valloc(&h->d_dM, nS, vs);
+  rc = rc ? rc : valloc(&h->d_dP, nS, vs);
+  rc = rc ? rc : valloc(&h->d_dA, nS, vs);
+  rc = rc ? rc : valloc(&h->d_R, nT, vs);
+  rc = rc ? rc : valloc(&h->d_Q, nT, vs);
+  rc = rc ? rc : valloc(&h->d_dR, nT, vs);
+  rc = rc ? rc : valloc(&h->d_dQ, nT, vs);
+  rc = rc ? rc : falloc(&h->d_stage, nS);
   rc = rc ? rc : falloc(&h->d_part, std::max(nbmax, 1LL));
   rc = rc ? rc : falloc(&h->d_res, 8);
   rc = rc ? rc : upload_list(h->Y, yp, ya, yb, st);
@@ -463,17 +552,19 @@ int spai_fpmr_forward(spai_fpmr_handle h, const double* vals, int on_device, dou
   if (!h || !vals || !loss) return SPAI_ERR_ARG;
   cudaStream_t st = h->stream;
   const long long nS = h->nS, nT = h->nT;
-  FCK(cudaMemcpyAsync(h->d_A, vals, sizeof(double) * nS,
+  const int vs = h->vs;
+  FCK(cudaMemcpyAsync(h->d_stage, vals, sizeof(double) * nS,
                       on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
-  k_m0<<<nblk(nS), 256, 0, st>>>(nS, h->d_Mck);
-  k_m0_diag<<<nblk(h->n), 256, 0, st>>>(h->n, h->d_diagS, h->d_A, h->d_Mck);
-  h->launches += 2;
+  FP_DISPATCH(h, k_from_f64, nblk(nS), nS, h->d_stage, (T_*)h->d_A);
+  FP_DISPATCH(h, k_m0, nblk(nS), nS, (T_*)h->d_Mck);
+  FP_DISPATCH(h, k_m0_diag, nblk(h->n), h->n, h->d_diagS, (const T_*)h->d_A, (T_*)h->d_Mck);
   FCK(cudaGetLastError());
   h->alpha.assign(h->K, 0.0);
   h->num.assign(h->K, 0.0);
   h->den.assign(h->K, 0.0);
   for (int i = 0; i < h->K; i++) {
-    double* M = h->d_Mck + (size_t)i * nS;
+    void* M = at(h->d_Mck, vs, (long long)i * nS);
+    void* Mn = at(h->d_Mck, vs, (long long)(i + 1) * nS);
     int rc = step_products(h, M, true);
     if (!rc) rc = dot(h, nT, h->d_R, h->d_Q, 0);
     if (!rc) rc = dot(h, nT, h->d_Q, h->d_Q, 1);
@@ -485,12 +576,11 @@ int spai_fpmr_forward(spai_fpmr_handle h, const double* vals, int on_device, dou
     h->num[i] = nd[0];
     h->den[i] = nd[1];
     h->alpha[i] = a;
-    FCK(cudaMemcpyAsync(M + nS, M, sizeof(double) * nS, cudaMemcpyDeviceToDevice, st));
-    k_axby<<<nblk(nS), 256, 0, st>>>(nS, a, h->d_P, 1.0, M + nS);
-    h->launches++;
+    FP_DISPATCH(h, k_copy, nblk(nS), nS, (const T_*)M, (T_*)Mn);
+    FP_DISPATCH(h, k_axby, nblk(nS), nS, a, (const T_*)h->d_P, 1.0, (T_*)Mn);
     FCK(cudaGetLastError());
   }
-  int rc = step_products(h, h->d_Mck + (size_t)h->K * nS, false);
+  int rc = step_products(h, at(h->d_Mck, vs, (long long)h->K * nS), false);
   if (!rc) rc = dot(h, nT, h->d_R, h->d_R, 0);
   double l;
   if (!rc) rc = read_res(h, &l, 1);
@@ -505,18 +595,18 @@ int spai_fpmr_backward(spai_fpmr_handle h, double dloss, double* dvals, int on_d
   if (!h->have_forward) return SPAI_ERR_STATE;
   cudaStream_t st = h->stream;
   const long long nS = h->nS, nT = h->nT;
-  const int K = h->K;
+  const int K = h->K, vs = h->vs;
   // dR_K = 2 dL R_K;  dA = -mask_S(dR M_K^T);  dM = -mask_S(A^T dR)
-  int rc = step_products(h, h->d_Mck + (size_t)K * nS, false);
+  void* MK = at(h->d_Mck, vs, (long long)K * nS);
+  int rc = step_products(h, MK, false);
   if (rc) return rc;
-  k_axby<<<nblk(nT), 256, 0, st>>>(nT, 2.0 * dloss, h->d_R, 0.0, h->d_dR);
-  h->launches++;
+  FP_DISPATCH(h, k_axby, nblk(nT), nT, 2.0 * dloss, (const T_*)h->d_R, 0.0, (T_*)h->d_dR);
   FCK(cudaGetLastError());
-  rc = seg_prod(h, h->D, h->d_dR, h->d_Mck + (size_t)K * nS, h->d_dA, -1.0, 0);
+  rc = seg_prod(h, h->D, h->d_dR, MK, h->d_dA, -1.0, 0);
   if (!rc) rc = seg_prod(h, h->X, h->d_A, h->d_dR, h->d_dM, -1.0, 0);
   if (rc) return rc;
   for (int i = K - 1; i >= 0; i--) {
-    const double* M = h->d_Mck + (size_t)i * nS;
+    const void* M = at(h->d_Mck, vs, (long long)i * nS);
     const double a = h->alpha[i], den = h->den[i];
     rc = step_products(h, M, true);  // R_i, P_i, Q_i
     if (!rc) rc = dot(h, nS, h->d_dM, h->d_P, 0);
@@ -525,18 +615,17 @@ int spai_fpmr_backward(spai_fpmr_handle h, double dloss, double* dvals, int on_d
     if (rc) return rc;
     const double dnum = da / den, dden = -da * a / den;
     // dP = alpha dM;  dR = dnum Q;  dQ = dnum R + 2 dden Q
-    k_axby<<<nblk(nS), 256, 0, st>>>(nS, a, h->d_dM, 0.0, h->d_dP);
-    k_axby<<<nblk(nT), 256, 0, st>>>(nT, dnum, h->d_Q, 0.0, h->d_dR);
-    k_lin2<<<nblk(nT), 256, 0, st>>>(nT, dnum, h->d_R, 2.0 * dden, h->d_Q, h->d_dQ);
-    h->launches += 3;
+    FP_DISPATCH(h, k_axby, nblk(nS), nS, a, (const T_*)h->d_dM, 0.0, (T_*)h->d_dP);
+    FP_DISPATCH(h, k_axby, nblk(nT), nT, dnum, (const T_*)h->d_Q, 0.0, (T_*)h->d_dR);
+    FP_DISPATCH(h, k_lin2, nblk(nT), nT, dnum, (const T_*)h->d_R, 2.0 * dden, (const T_*)h->d_Q,
+                (T_*)h->d_dQ);
     FCK(cudaGetLastError());
     // Q = A P:  dA += mask_S(dQ P^T);  dP += mask_S(A^T dQ)
     rc = seg_prod(h, h->D, h->d_dQ, h->d_P, h->d_dA, 1.0, 1);
     if (!rc) rc = seg_prod(h, h->X, h->d_A, h->d_dQ, h->d_dP, 1.0, 1);
     if (rc) return rc;
     // P = mask_S(R):  dR += dP on S's positions of T
-    k_scatter_add<<<nblk(nS), 256, 0, st>>>(nS, h->d_s2t, h->d_dP, h->d_dR);
-    h->launches++;
+    FP_DISPATCH(h, k_scatter_add, nblk(nS), nS, h->d_s2t, (const T_*)h->d_dP, (T_*)h->d_dR);
     FCK(cudaGetLastError());
     // R = I - A M:  dA -= mask_S(dR M^T);  dM -= mask_S(A^T dR)
     rc = seg_prod(h, h->D, h->d_dR, M, h->d_dA, -1.0, 1);
@@ -544,10 +633,11 @@ int spai_fpmr_backward(spai_fpmr_handle h, double dloss, double* dvals, int on_d
     if (rc) return rc;
   }
   // M_0 = diag(A)^{-1}
-  k_m0_adjoint<<<nblk(h->n), 256, 0, st>>>(h->n, h->d_diagS, h->d_A, h->d_dM, h->d_dA);
-  h->launches++;
+  FP_DISPATCH(h, k_m0_adjoint, nblk(h->n), h->n, h->d_diagS, (const T_*)h->d_A, (const T_*)h->d_dM,
+              (T_*)h->d_dA);
+  FP_DISPATCH(h, k_to_f64, nblk(nS), nS, (const T_*)h->d_dA, h->d_stage);
   FCK(cudaGetLastError());
-  FCK(cudaMemcpyAsync(dvals, h->d_dA, sizeof(double) * nS,
+  FCK(cudaMemcpyAsync(dvals, h->d_stage, sizeof(double) * nS,
                       on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
   FCK(cudaStreamSynchronize(st));
   return SPAI_OK;

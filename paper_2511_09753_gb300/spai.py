@@ -90,7 +90,7 @@ def load():
         "pcg_solve_block": (i32, [vp, i32, vp, vp, dbl, i32, i32, i32, vp, vp, vp]),
         "spai_set_pcg_prec": (i32, [vp, i32]),
         "spai_fixed_pattern": (i32, [vp, i32]),
-        "spai_fpmr_create": (i32, [C.POINTER(vp), i64, i64, vp, vp, i32, vp]),
+        "spai_fpmr_create": (i32, [C.POINTER(vp), i64, i64, vp, vp, i32, i32, vp]),
         "spai_fpmr_forward": (i32, [vp, vp, i32, C.POINTER(dbl)]),
         "spai_fpmr_backward": (i32, [vp, dbl, vp, i32]),
         "spai_fpmr_info": (i32, [vp, C.POINTER(i64), C.POINTER(i64), C.POINTER(i64)]),
@@ -469,12 +469,13 @@ class FixedPatternMR:
     """K fixed-pattern MR steps on supp(A) and the gradient of ||I - A M_K||_F^2
     with respect to A's stored values (see spai_fpmr_* in include/spai.h)."""
 
-    def __init__(self, n, rowptr, colind, K, stream=None):
+    def __init__(self, n, rowptr, colind, K, prec="fp64", stream=None):
         self.lib = load()
         rp, ci = _np(rowptr, np.int32), _np(colind, np.int32)
         h = C.c_void_p()
         rc = self.lib.spai_fpmr_create(C.byref(h), int(n), len(ci), rp.ctypes.data, ci.ctypes.data,
-                                       int(K), _stream_ptr(stream))
+                                       int(K), SPAI_MIXED if prec == "mixed" else SPAI_FP64,
+                                       _stream_ptr(stream))
         if rc != 0:
             raise SpaiError(rc, "spai_fpmr_create")
         self.h, self.n, self.nnz, self.K = h, int(n), len(ci), int(K)

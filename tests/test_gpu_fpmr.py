@@ -60,3 +60,18 @@ def test_fpmr_through_torch_autograd():
     lo, go = OF.gradient(n, rp, ci, v, 5)
     np.testing.assert_allclose(x.grad.cpu().numpy(), 3.0 * go, rtol=1e-9, atol=1e-12 * np.abs(go).max())
     f.close()
+
+
+def test_fpmr_mixed_tracks_fp64():
+    """FP32 values and products with FP64 inner products and scalars: loss
+    and gradient within FP32 accuracy of the FP64 oracle."""
+    from paper_2511_09753_gb300 import spai
+    n, rp, ci, v = I.varcoef_3d_7pt(12, seed=6)
+    f = spai.FixedPatternMR(n, rp, ci, 10, prec="mixed")
+    loss = f.forward(v)
+    g = f.backward()
+    lo, go = OF.gradient(n, rp, ci, v, 10)
+    assert abs(loss - lo) <= 1e-5 * lo
+    assert np.max(np.abs(g - go)) <= 1e-4 * np.abs(go).max()
+    assert not np.array_equal(g, go)
+    f.close()
