@@ -310,7 +310,7 @@ def run_ours(args):
 # DRAM bytes (read + write) per column-pass launch, from ncu captures of the
 # --profile mr|lomr|cg cases on this workload, weighted by the launch mix of
 # one step (51 MR, 51 LOMR, 50 + 50 CG passes).
-COLPASS_TRAFFIC_BYTES = 139.5e6
+COLPASS_TRAFFIC_BYTES = 139.0e6
 
 BATCH_ITERS = 30
 BATCH_RHS = 32
