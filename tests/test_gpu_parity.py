@@ -63,7 +63,7 @@ def test_mixed_within_tolerance_of_fp64_oracle(method):
     assert abs(a - b) <= 1e-5 * b, (a, b)
 
 
-def test_c1_mr_then_pcg_matches_oracle():
+def test_laplacian32_mr_then_pcg_matches_oracle():
     """Plain MR, FP64, 32x32 Laplacian, 20 iterations, cap 2 nnz, then PCG to 1e-8."""
     spai = _spai()
     n, rp, ci, v = I.laplacian_2d_5pt(32)
