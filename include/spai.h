@@ -317,6 +317,22 @@ int spai_drop_global(spai_handle h, int which, int64_t m);
  * cap_j.  Forgets the method recurrence.  Single-matrix handles only. */
 int spai_drop_heuristic(spai_handle h, int64_t m);
 
+/* MR (Algorithm 1, method SPAI_MR) or MR_SPD (Algorithm 5, SPAI_MR_PI) with
+ * the paper's global dropping inside every iteration, where its dropping
+ * experiments place it (Sec. 7.2): R_i = I - A M_i explicitly; every
+ * direction candidate (Pi) R_i kept, then the m_dir entries of largest |v|
+ * over the whole matrix kept (Sec. 6.1, Eq. 6.2); alpha_i from that
+ * direction, with spai_run's arithmetic; M_i + alpha_i P_i kept whole, then
+ * Appendix A's heuristic with density cap m_M (see spai_drop_heuristic).
+ * Each iteration takes three column passes and the two global selections.
+ * The column capacities cap_j (from cap_factor) must hold the whole
+ * candidate columns, else SPAI_ERR_CAPACITY.  hist as for spai_run:
+ * resnorm[i] = ||R_i||_F of the dropped iterates, coef[2i] = alpha_i.
+ * Returns SPAI_OK, SPAI_CONVERGED_EARLY or an error; forgets any method
+ * recurrence.  Single-matrix handles only. */
+int spai_run_global(spai_handle h, int method, int iters, int64_t m_dir, int64_t m_M,
+                    spai_history *hist);
+
 /* ------------------------------------------------ differentiation */
 
 /* Gradient of fixed-pattern MR (no counterpart in the paper, which gives the

@@ -73,6 +73,9 @@ def _load():
         lib.orc_residual_norm.argtypes = [C.c_void_p]
         lib.orc_column_residual.restype = C.c_int
         lib.orc_column_residual.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]
+        lib.orc_product_column.restype = C.c_int
+        lib.orc_product_column.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
+                                           C.c_void_p]
         lib.orc_drop_column.restype = C.c_int
         lib.orc_drop_column.argtypes = [C.c_int, p_i32, p_f64, C.c_int]
         lib.orc_fixsum.restype = C.c_double
@@ -156,6 +159,18 @@ class Oracle:
 
     def residual_norm(self):
         return self.lib.orc_residual_norm(self.h)
+
+    def product_column(self, rows, vals):
+        """A x for one column x (sorted rows) with the method's arithmetic."""
+        rows = np.ascontiguousarray(rows, dtype=np.int32)
+        vals = np.ascontiguousarray(vals, dtype=np.float64)
+        L = self.lib.orc_product_column(self.h, len(rows), rows.ctypes.data, vals.ctypes.data,
+                                        None, None)
+        orow = np.zeros(max(L, 1), dtype=np.int32)
+        oval = np.zeros(max(L, 1), dtype=np.float64)
+        self.lib.orc_product_column(self.h, len(rows), rows.ctypes.data, vals.ctypes.data,
+                                    orow.ctypes.data, oval.ctypes.data)
+        return orow[:L], oval[:L]
 
     def column_residual(self, j):
         L = self.lib.orc_column_residual(self.h, int(j), None, None)

@@ -119,3 +119,83 @@ def heuristic(n, rowptr, colind, vals, M, m, mixed=False):
         sel = np.array([(j, int(r)) not in drop for r in rr], dtype=bool)
         out.append((rr[sel], vv[sel]))
     return _to_csc(n, out)
+
+
+def _rv(x, mixed):
+    return float(np.float32(x)) if mixed else float(x)
+
+
+def run_global_mr(n, rowptr, colind, vals, iters, m_dir, m_M, mixed=False, use_pi=False):
+    """MR (Algorithm 1) or MR_SPD (Algorithm 5, Pi = diag(A)^{-1}) with the
+    paper's global dropping placed as in its Experiment 05: every iteration
+    takes R_i = I - A M_i, the direction P_i = (Pi) R_i hard-thresholded to the
+    m_dir largest entries over the whole matrix, alpha_i from that P_i (the
+    coefficient arithmetic of the column pass), M_i + alpha_i P_i (union, FP64
+    fma rounded once), then the Appendix A heuristic with density cap m_M.
+    Returns dict(M, resnorm, coef, done)."""
+    import math
+    from oracle import Oracle, fixsum, pairwise
+    o = Oracle(n, rowptr, colind, vals, mixed=mixed, cap_factor=float(n))
+    M = o.get_M()
+    diag = np.zeros(n)
+    for i in range(n):
+        for q in range(rowptr[i], rowptr[i + 1]):
+            if colind[q] == i:
+                diag[i] = vals[q]
+    pi = 1.0 / diag
+    res, coef = [], []
+    done = 0
+
+    def residuals(Mc):
+        o.set_M(*Mc)
+        R = [o.column_residual(j) for j in range(n)]
+        rr = pairwise([fixsum(np.asarray(v) * np.asarray(v)) for _, v in R])
+        return R, rr
+
+    for _ in range(iters):
+        R, rr = residuals(M)
+        res.append(math.sqrt(rr))
+        if rr == 0.0:
+            break
+        cols = []
+        for j, (rr_, rv_) in enumerate(R):
+            if use_pi:
+                z = [(int(r), _rv(pi[r] * v, mixed)) for r, v in zip(rr_, rv_)]
+                z = [(r, v) for r, v in z if v != 0.0]
+                cols.append((np.array([r for r, _ in z], np.int64), np.array([v for _, v in z])))
+            else:
+                cols.append((np.asarray(rr_, np.int64), np.asarray(rv_, np.float64)))
+        P = hard_threshold(n, _to_csc(n, cols), m_dir)
+        rq_p, qq_p = [], []
+        for j in range(n):
+            pr = P[1][P[0][j]:P[0][j + 1]]
+            pv = P[2][P[0][j]:P[0][j + 1]]
+            qr, qv = o.product_column(pr, pv)
+            Rj = dict(zip(R[j][0].tolist(), R[j][1].tolist()))
+            if use_pi:
+                t1 = [(Rj[r] * q) * pi[r] for r, q in zip(qr.tolist(), qv.tolist()) if r in Rj]
+                t2 = [(q * q) * pi[r] for r, q in zip(qr.tolist(), qv.tolist())]
+            else:
+                t1 = [Rj[r] * q for r, q in zip(qr.tolist(), qv.tolist()) if r in Rj]
+                t2 = [q * q for q in qv.tolist()]
+            rq_p.append(fixsum(np.array(t1)))
+            qq_p.append(fixsum(np.array(t2)))
+        rq, qq = pairwise(rq_p), pairwise(qq_p)
+        if qq == 0.0:
+            break
+        alpha = rq / qq
+        coef.append(alpha)
+        newcols = []
+        for j in range(n):
+            a = dict(zip(M[1][M[0][j]:M[0][j + 1]].tolist(), M[2][M[0][j]:M[0][j + 1]].tolist()))
+            b = dict(zip(P[1][P[0][j]:P[0][j + 1]].tolist(), P[2][P[0][j]:P[0][j + 1]].tolist()))
+            rows = sorted(set(a) | set(b))
+            vv = [_rv(_fma(alpha, b.get(r, 0.0), a.get(r, 0.0)), mixed) for r in rows]
+            keep = [(r, v) for r, v in zip(rows, vv) if v != 0.0]
+            newcols.append((np.array([r for r, _ in keep], np.int64), np.array([v for _, v in keep])))
+        M = heuristic(n, rowptr, colind, vals, _to_csc(n, newcols), m_M, mixed=mixed)
+        done += 1
+    if done == iters:
+        _, rr = residuals(M)
+        res.append(math.sqrt(rr))
+    return dict(M=M, resnorm=np.array(res), coef=np.array(coef), done=done)

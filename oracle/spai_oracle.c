@@ -796,6 +796,24 @@ int orc_column_residual(orc_state *s, int j, int *rows, double *vals) {
   return L;
 }
 
+/* A x for one column x (rows sorted, len entries) with the method's
+ * arithmetic (spgemm_col: fma chains over ascending k in the value type,
+ * exact zeros removed); out_rows/out_vals may be NULL to get the length. */
+int orc_product_column(orc_state *s, int len, const int *rows, const double *vals, int *out_rows,
+                       double *out_vals) {
+  ocol x = {0}, y = {0};
+  for (int e = 0; e < len; e++) col_push(&x, rows[e], vals[e]);
+  spgemm_col(s, &x, &y);
+  int L = y.len;
+  if (out_rows) {
+    memcpy(out_rows, y.row, sizeof(int) * (size_t)L);
+    memcpy(out_vals, y.val, sizeof(double) * (size_t)L);
+  }
+  col_free(&x);
+  col_free(&y);
+  return L;
+}
+
 /* -------------------------------------------------------------------- PCG */
 
 /* y_i = fma chain over row i, ascending column: acc = fma(m_ij, x_j, acc) */

@@ -1995,9 +1995,7 @@ static long long count_entries(spai_ctx* h, const int* d_len) {
   return s;
 }
 
-int spai_drop_global(spai_handle h, int which, int64_t m) {
-  if (!h || (which != 0 && which != 1) || m < 0) return SPAI_ERR_ARG;
-  if (h->nseg) return SPAI_ERR_UNSUPPORTED;
+static int drop_global_impl(spai_ctx* h, int which, int64_t m) {
   int* len = which == 0 ? h->d_Mlen : h->d_Plen;
   const long long N = count_entries(h, len);
   if (N < 0) return SPAI_ERR_CUDA;
@@ -2024,14 +2022,18 @@ int spai_drop_global(spai_handle h, int which, int64_t m) {
       if (rc) return rc;
     }
   }
-  h->method = -1;
   invalidate_rows(h);
   return SPAI_OK;
 }
 
-int spai_drop_heuristic(spai_handle h, int64_t m) {
-  if (!h || m < 0) return SPAI_ERR_ARG;
+int spai_drop_global(spai_handle h, int which, int64_t m) {
+  if (!h || (which != 0 && which != 1) || m < 0) return SPAI_ERR_ARG;
   if (h->nseg) return SPAI_ERR_UNSUPPORTED;
+  h->method = -1;
+  return drop_global_impl(h, which, m);
+}
+
+static int drop_heuristic_impl(spai_ctx* h, int64_t m) {
   cudaStream_t st = h->stream;
   const int vs = h->prec == SPAI_MIXED ? 4 : 8;
   // 1-2: M := (M + M^T)/2 in FP64, rounded to the value type; off-diagonal
@@ -2109,6 +2111,88 @@ int spai_drop_heuristic(spai_handle h, int64_t m) {
     if (rc) return rc;
   }
   invalidate_rows(h);
+  return SPAI_OK;
+}
+
+int spai_drop_heuristic(spai_handle h, int64_t m) {
+  if (!h || m < 0) return SPAI_ERR_ARG;
+  if (h->nseg) return SPAI_ERR_UNSUPPORTED;
+  h->method = -1;
+  return drop_heuristic_impl(h, m);
+}
+
+int spai_run_global(spai_handle h, int method, int iters, int64_t m_dir, int64_t m_M,
+                    spai_history* hist) {
+  if (!h || iters < 0 || m_dir < 0 || m_M < 0) return SPAI_ERR_ARG;
+  if (method != SPAI_MR && method != SPAI_MR_PI) return SPAI_ERR_ARG;
+  if (h->nseg) return SPAI_ERR_UNSUPPORTED;
+  const bool pim = method == SPAI_MR_PI;
+  if (pim && !h->pi_ok) return SPAI_ERR_UNSUPPORTED;
+  int rc = ensure_hist(h, iters + 1);
+  if (rc) return rc;
+  h->last_iters = iters;
+  cudaStream_t st = h->stream;
+  CK(cudaMemsetAsync(h->d_Plen, 0, sizeof(int) * h->n, st));
+  CK(cudaMemsetAsync(h->d_Zlen, 0, sizeof(int) * h->n, st));
+  rc = reset_call_scalars(h);
+  if (rc) return rc;
+  CK(cudaMemsetAsync(h->d_hres, 0xff, sizeof(double) * (iters + 1), st));
+  CK(cudaMemsetAsync(h->d_hcoef, 0xff, sizeof(double) * 2 * std::max(iters, 1), st));
+  h->method = -1;
+  invalidate_rows(h);
+  auto pass = [&](int upd, int dir, int iter, int from_slab) -> int {
+    PassParams p = base_params(h, kMR, false, pim);
+    p.do_update = upd;
+    p.do_dir = dir;
+    p.drop = 0;
+    p.iter = iter;
+    p.dir_from_slab = from_slab;
+    CK(timed_launch(h, p, pim ? h->cfg_pi[kMR] : h->cfg[kMR], false));
+    invalidate_rows(h);
+    return SPAI_OK;
+  };
+  DevScalars sc;
+  auto read_sc = [&]() -> int {
+    CK(cudaMemcpyAsync(&sc, h->d_sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    return SPAI_OK;
+  };
+  int i = 0;
+  for (; i < iters; i++) {
+    // R_i and every direction candidate (Pi) R_i, kept whole
+    if ((rc = pass(0, 1, i, 0)) || (rc = read_sc())) return rc;
+    if (sc.flags & (kFlagCapacity | kFlagNonfinite) || sc.stop) break;
+    // P_i: the m_dir largest entries over the whole matrix (Sec. 6.1)
+    if ((rc = drop_global_impl(h, 1, m_dir))) return rc;
+    // alpha_i from that P_i
+    if ((rc = pass(0, 1, i, 1)) || (rc = read_sc())) return rc;
+    if (sc.flags & (kFlagCapacity | kFlagNonfinite) || sc.stop) break;
+    // M_i + alpha_i P_i, whole, then the Appendix A heuristic with cap m_M
+    if ((rc = pass(1, 0, i + 1, 0)) || (rc = read_sc())) return rc;
+    if (sc.flags & kFlagCapacity) break;
+    if ((rc = drop_heuristic_impl(h, m_M))) return rc;
+  }
+  if (i == iters && !(sc.flags & kFlagCapacity)) {
+    rc = reset_call_scalars(h);  // keep done; clear stop for the final norm
+    if (rc) return rc;
+    if ((rc = pass(0, 0, iters, 0)) || (rc = read_sc())) return rc;
+  }
+  if (hist && hist->resnorm)
+    CK(cudaMemcpyAsync(hist->resnorm, h->d_hres, sizeof(double) * (iters + 1),
+                       cudaMemcpyDeviceToHost, st));
+  if (hist && hist->coef && iters > 0)
+    CK(cudaMemcpyAsync(hist->coef, h->d_hcoef, sizeof(double) * 2 * iters, cudaMemcpyDeviceToHost,
+                       st));
+  CK(cudaStreamSynchronize(st));
+  if (hist) {
+    hist->iters_done = i;
+    hist->flags = sc.flags & 3;
+  }
+  invalidate_rows(h);
+  h->method = -1;
+  if (sc.flags & kFlagCapacity) return SPAI_ERR_CAPACITY;
+  if (sc.flags & kFlagNonfinite) return SPAI_ERR_NONFINITE;
+  if (sc.flags & kFlagConverged) return SPAI_CONVERGED_EARLY;
   return SPAI_OK;
 }
 

@@ -175,15 +175,19 @@ __device__ void column_work(ColCtx<VS, VC>& c, int j, double* part) {
       return;
     }
     int Lp;
-    if (PI) {  // P = D(Pi R) (Algorithm 5)
-      int* Zr = c.template at<int>(L.zr);
-      VC* Zv = c.template at<VC>(L.zv);
-      int Lz = list_scale_pi(Rr, Rv, LR, p.pi, Zr, Zv, lane);
-      Lp = warp_select(Zr, Zv, Lz, cap, Pr, Pv, hist, tie, p.drop, ovf, lane);
+    if (p.dir_from_slab) {  // a direction chosen outside the pass (global dropping)
+      Lp = load_col(c, p.Prow, p.Pval, off, p.Plen[j], Pr, Pv);
     } else {
-      Lp = warp_select(Rr, Rv, LR, cap, Pr, Pv, hist, tie, p.drop, ovf, lane);
+      if (PI) {  // P = D(Pi R) (Algorithm 5)
+        int* Zr = c.template at<int>(L.zr);
+        VC* Zv = c.template at<VC>(L.zv);
+        int Lz = list_scale_pi(Rr, Rv, LR, p.pi, Zr, Zv, lane);
+        Lp = warp_select(Zr, Zv, Lz, cap, Pr, Pv, hist, tie, p.drop, ovf, lane);
+      } else {
+        Lp = warp_select(Rr, Rv, LR, cap, Pr, Pv, hist, tie, p.drop, ovf, lane);
+      }
+      store_col(c, p.Prow, p.Pval, p.Plen, j, off, Lp, Pr, Pv);
     }
-    store_col(c, p.Prow, p.Pval, p.Plen, j, off, Lp, Pr, Pv);
     int cq = spgemm(p, ha, Pr, Pv, Lp, -1, Tr, Tv, lane, c.seg);  // table holds Q = A P
     c.spg++;
     lookup_list(Rr, LR, ha, yc, lane);                      // Q at the rows of R

@@ -65,6 +65,7 @@ struct PassParams {
   int capmax, pmax, lmax, tmax;
   int kind;
   int do_update, do_dir, drop;
+  int dir_from_slab;     // MR: take the direction P stored in its slab instead of selecting it from R
   int iter;          // history slot of this pass
   int fresh;         // CG: first B pass of a call (writes history[0])
   const long long* off;  // slab offsets (per column)

@@ -34,7 +34,7 @@ EXPORTED = ["spai_validate_csr", "spai_status_string", "spai_create", "spai_dest
             "spai_batch_get_M", "pcg_solve_block", "spai_set_pcg_prec", "spai_sym_lanczos",
             "spai_fixed_pattern", "spai_fpmr_create", "spai_fpmr_forward", "spai_fpmr_backward",
             "spai_fpmr_info", "spai_fpmr_destroy", "spai_autotune", "spai_drop_global",
-            "spai_drop_heuristic"]
+            "spai_drop_heuristic", "spai_run_global"]
 
 
 class SpaiError(RuntimeError):
@@ -98,6 +98,7 @@ def load():
         "spai_autotune": (i32, [vp, i32, i32, C.POINTER(dbl)]),
         "spai_drop_global": (i32, [vp, i32, i64]),
         "spai_drop_heuristic": (i32, [vp, i64]),
+        "spai_run_global": (i32, [vp, i32, i32, i64, i64, C.POINTER(_Hist)]),
         "spai_sym_lanczos": (i32, [vp, i32, vp, vp, vp, C.POINTER(i32), C.POINTER(dbl),
                                    C.POINTER(dbl)]),
         "spai_save_state": (i32, [vp, vp, C.POINTER(C.c_size_t)]),
@@ -346,6 +347,17 @@ class Spai:
         """Keep the m largest-|v| entries of M (or of P) over the whole matrix."""
         self._check(self.lib.spai_drop_global(self.h, 0 if which == "M" else 1, int(m)),
                     "spai_drop_global")
+
+    def run_global(self, method, iters, m_dir, m_M):
+        """MR or MR_SPD with global dropping inside every iteration (see spai_run_global)."""
+        m = METHODS[method] if isinstance(method, str) else int(method)
+        res = np.full(iters + 1, np.nan)
+        coef = np.full(2 * max(iters, 1), np.nan)
+        hist = _Hist(res.ctypes.data, coef.ctypes.data, 0, 0)
+        rc = self.lib.spai_run_global(self.h, m, int(iters), int(m_dir), int(m_M), C.byref(hist))
+        self._check(rc, "spai_run_global")
+        return dict(status=rc, done=hist.iters_done, flags=hist.flags, resnorm=res,
+                    coef=coef.reshape(-1, 2))
 
     def drop_heuristic(self, m):
         """Appendix A: symmetrise M, drop round-off entries, then by score to m entries."""

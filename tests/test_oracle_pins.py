@@ -671,3 +671,31 @@ def test_heuristic_scores_are_the_exact_single_drop_change():
     # entries that stay keep the symmetrised values
     keep = Mo != 0
     assert np.array_equal(Mo[keep], S[keep])
+
+
+def test_global_mr_flow_step_is_the_line_minimiser_of_the_thresholded_direction():
+    """One iteration of MR with global dropping: alpha_0 minimises
+    ||R_0 - a A P_0||_F for P_0 the brute-force top-m_dir of R_0 (MR) or of
+    Pi R_0 (MR_SPD, weighted norm), and the final history entry is the
+    dense ||I - A M_1||_F of the returned M."""
+    from oracle import dropping as D
+    n, rp, ci, v = I.varcoef_grid((5, 6), seed=4)
+    A = I.csr_to_dense(n, rp, ci, v)
+    d = np.diag(A)
+    R0 = np.eye(n) - A @ np.diag(1.0 / d)
+    for use_pi in (False, True):
+        X = np.diag(1.0 / d) @ R0 if use_pi else R0
+        ent = sorted((-abs(X[r, j]), j, r) for j in range(n) for r in range(n) if X[r, j] != 0)
+        m_dir = len(ent) // 3
+        P = np.zeros_like(X)
+        for _, j, r in ent[:m_dir]:
+            P[r, j] = X[r, j]
+        AP = A @ P
+        W = np.diag(1.0 / d) if use_pi else np.eye(n)
+        alpha = np.sum(R0 * (W @ AP)) / np.sum(AP * (W @ AP))
+        out = D.run_global_mr(n, rp, ci, v, 1, m_dir, 10 ** 9, use_pi=use_pi)
+        assert out["done"] == 1
+        assert abs(out["coef"][0] - alpha) <= 1e-12 * abs(alpha)
+        M1 = dense_from_csc(n, *out["M"])
+        np.testing.assert_allclose(out["resnorm"][-1], np.linalg.norm(np.eye(n) - A @ M1),
+                                   rtol=1e-12)
