@@ -60,6 +60,49 @@ __device__ int load_col(ColCtx<VS, VC>& c, const int* grow, const void* gval, lo
   return len;
 }
 
+// Load the M column and, when asked, the P and Z columns of the same slab
+// offset: every global load of a lane is issued before its shared-memory
+// stores, so the three latencies overlap.
+template <typename VS, typename VC>
+__device__ void load_cols(ColCtx<VS, VC>& c, long long off, int Lm, int* Mr, VC* Mv, int Lp, int* Pr,
+                          VC* Pv, int Lz, int* Zr, VC* Zv) {
+  const PassParams& p = c.p;
+  const VS* mv = (const VS*)p.Mval;
+  const VS* pv = (const VS*)p.Pval;
+  const VS* zv = (const VS*)p.Zval;
+  const int Lx = max(Lm, max(Lp, Lz));
+  for (int e = c.lane; e < Lx; e += 32) {
+    const bool am = e < Lm, ap = e < Lp, az = e < Lz;
+    int rm = 0, rp = 0, rz = 0;
+    VS xm = VS(0), xp = VS(0), xz = VS(0);
+    if (am) {
+      rm = p.Mrow[off + e];
+      xm = mv[off + e];
+    }
+    if (ap) {
+      rp = p.Prow[off + e];
+      xp = pv[off + e];
+    }
+    if (az) {
+      rz = p.Zrow[off + e];
+      xz = zv[off + e];
+    }
+    if (am) {
+      Mr[e] = rm;
+      Mv[e] = (VC)xm;
+    }
+    if (ap) {
+      Pr[e] = rp;
+      Pv[e] = (VC)xp;
+    }
+    if (az) {
+      Zr[e] = rz;
+      Zv[e] = (VC)xz;
+    }
+  }
+  __syncwarp();
+}
+
 template <typename VS, typename VC>
 __device__ void store_col(ColCtx<VS, VC>& c, int* grow, void* gval, int* glen, int j, long long off,
                           int len, const int* sr, const VC* sv) {
@@ -117,7 +160,16 @@ __device__ void column_work(ColCtx<VS, VC>& c, int j, double* part) {
   un.H = L.HU;
   int* ovf = &c.overflow;
 
-  int Lm = load_col(c, p.Mrow, p.Mval, off, p.Mlen[j], Mr, Mv);
+  // the columns this pass reads from the slabs, loaded together
+  const bool needP = (p.kind == kMR && p.do_update) || p.kind == kLOMR || p.kind == kCGA ||
+                     p.kind == kCGB;
+  const bool needZ = p.kind == kLOMR && p.do_update;
+  int Lm = p.Mlen[j];
+  int Lp = needP ? p.Plen[j] : 0;
+  const int Lz0 = needZ ? p.Zlen[j] : 0;
+  load_cols(c, off, Lm, Mr, Mv, Lp, Pr, Pv, Lz0, c.template at<int>(L.Zr), c.template at<VC>(L.Zv));
+  c.bytes += (unsigned long long)(Lm + Lp + Lz0) * (sizeof(int) + sizeof(VS)) +
+             (1 + (int)needP + (int)needZ) * sizeof(int);
 
   if (p.kind == kSCORE) {
     // Appendix A, Eq. 430: dropping m_kj alone changes ||R||_F^2 by
@@ -160,7 +212,6 @@ __device__ void column_work(ColCtx<VS, VC>& c, int j, double* part) {
 
   if (p.kind == kMR) {
     if (p.do_update) {
-      int Lp = load_col(c, p.Prow, p.Pval, off, p.Plen[j], Pr, Pv);
       CombAxpy<VC> f{c.sc->alpha};
       int Lt = warp_union(un, Mr, Mv, Lm, Pr, Pv, Lp, Tr, Tv, f, lane);
       Lm = warp_select(Tr, Tv, Lt, cap, Mr, Mv, hist, tie, p.drop, ovf, lane);
@@ -174,7 +225,6 @@ __device__ void column_work(ColCtx<VS, VC>& c, int j, double* part) {
       fixsum<1>(part, lane, TermSq<VC>{Rv}, LR);
       return;
     }
-    int Lp;
     if (p.dir_from_slab) {  // a direction chosen outside the pass (global dropping)
       Lp = load_col(c, p.Prow, p.Pval, off, p.Plen[j], Pr, Pv);
     } else {
@@ -214,11 +264,9 @@ __device__ void column_work(ColCtx<VS, VC>& c, int j, double* part) {
     hb.val = c.template at<VC>(L.gv);
     hb.occ = c.template at<uint16_t>(L.go);
     hb.H = L.H;
-    int Lp = load_col(c, p.Prow, p.Pval, off, p.Plen[j], Pr, Pv);
     if (p.do_update) {
-      int Lz = load_col(c, p.Zrow, p.Zval, off, p.Zlen[j], Zr, Zv);
       CombLin<VC> fl{c.sc->delta, c.sc->gamma};
-      int Ls = warp_union(un, Zr, Zv, Lz, Pr, Pv, Lp, Sr, Sv, fl, lane);
+      int Ls = warp_union(un, Zr, Zv, Lz0, Pr, Pv, Lp, Sr, Sv, fl, lane);
       Lp = warp_select(Sr, Sv, Ls, cap, Pr, Pv, hist, tie, p.drop, ovf, lane);
       store_col(c, p.Prow, p.Pval, p.Plen, j, off, Lp, Pr, Pv);
       CombAdd<VC> fa;
@@ -281,7 +329,6 @@ __device__ void column_work(ColCtx<VS, VC>& c, int j, double* part) {
   }
 
   if (p.kind == kCGA) {
-    int Lp = load_col(c, p.Prow, p.Pval, off, p.Plen[j], Pr, Pv);
     CombAxpy<VC> f{c.sc->alpha};
     int Lt = warp_union(un, Mr, Mv, Lm, Pr, Pv, Lp, Tr, Tv, f, lane);
     Lm = warp_select(Tr, Tv, Lt, cap, Mr, Mv, hist, tie, p.drop, ovf, lane);
@@ -299,7 +346,6 @@ __device__ void column_work(ColCtx<VS, VC>& c, int j, double* part) {
 
   // kCGB
   {
-    int Lp = load_col(c, p.Prow, p.Pval, off, p.Plen[j], Pr, Pv);
     int cr = spgemm(p, ha, Mr, Mv, Lm, j, Tr, Tv, lane, c.seg);
     int LR = table_to_list(ha, cr, j, Rr, Rv, lane);
     hash_clear(ha, cr, lane);
@@ -442,7 +488,7 @@ __device__ inline void coefficients(const PassParams& p, DevScalars* sc, double*
 }
 
 template <typename VS, typename VC, bool PI>
-__global__ void __launch_bounds__(256, 3) colpass_kernel(const PassParams p) {
+__global__ void __launch_bounds__(256, sizeof(VC) == 4 ? 4 : 3) colpass_kernel(const PassParams p) {
   extern __shared__ __align__(16) char smem[];
   const int seg = p.nseg ? p.seg_of_col[(long long)blockIdx.x * p.B] : -1;
   DevScalars* sc = seg >= 0 ? p.segsc + seg : p.sc;

@@ -215,20 +215,49 @@ struct NoTerms {
   __device__ Term operator()(int) const { return Term{0ull, 0, 0}; }
 };
 
+template <typename F>
+__device__ __forceinline__ Term term_at(const F& f, int i, int L) {
+  return i < L ? f(i) : Term{0ull, 0, 0};
+}
+
+// The first two terms of each lane stay in registers between the exponent
+// pass and the accumulation pass; only the terms past 64 are evaluated twice.
 template <int K, typename F0, typename F1 = NoTerms, typename F2 = NoTerms>
 __device__ void fixsum(double* out, int lane, const F0& f0, int L0, const F1& f1 = F1(), int L1 = 0,
                        const F2& f2 = F2(), int L2 = 0) {
-  int e0 = 0, e1 = 0, e2 = 0;
-  for (int i = lane; i < L0; i += 32) e0 = max(e0, f0(i).e);
-  if (K > 1) for (int i = lane; i < L1; i += 32) e1 = max(e1, f1(i).e);
-  if (K > 2) for (int i = lane; i < L2; i += 32) e2 = max(e2, f2(i).e);
+  const Term a0 = term_at(f0, lane, L0), b0 = term_at(f0, lane + 32, L0);
+  Term a1 = {0ull, 0, 0}, b1 = {0ull, 0, 0}, a2 = {0ull, 0, 0}, b2 = {0ull, 0, 0};
+  if (K > 1) {
+    a1 = term_at(f1, lane, L1);
+    b1 = term_at(f1, lane + 32, L1);
+  }
+  if (K > 2) {
+    a2 = term_at(f2, lane, L2);
+    b2 = term_at(f2, lane + 32, L2);
+  }
+  int e0 = max(a0.e, b0.e), e1 = max(a1.e, b1.e), e2 = max(a2.e, b2.e);
+  for (int i = lane + 64; i < L0; i += 32) e0 = max(e0, f0(i).e);
+  if (K > 1) for (int i = lane + 64; i < L1; i += 32) e1 = max(e1, f1(i).e);
+  if (K > 2) for (int i = lane + 64; i < L2; i += 32) e2 = max(e2, f2(i).e);
   e0 = __reduce_max_sync(kFull, e0);
   if (K > 1) e1 = __reduce_max_sync(kFull, e1);
   if (K > 2) e2 = __reduce_max_sync(kFull, e2);
   Fix128 S0 = {0ull, 0ll}, S1 = {0ull, 0ll}, S2 = {0ull, 0ll};
-  if (e0) for (int i = lane; i < L0; i += 32) term_add(S0, f0(i), e0);
-  if (K > 1 && e1) for (int i = lane; i < L1; i += 32) term_add(S1, f1(i), e1);
-  if (K > 2 && e2) for (int i = lane; i < L2; i += 32) term_add(S2, f2(i), e2);
+  if (e0) {
+    if (lane < L0) term_add(S0, a0, e0);
+    if (lane + 32 < L0) term_add(S0, b0, e0);
+    for (int i = lane + 64; i < L0; i += 32) term_add(S0, f0(i), e0);
+  }
+  if (K > 1 && e1) {
+    if (lane < L1) term_add(S1, a1, e1);
+    if (lane + 32 < L1) term_add(S1, b1, e1);
+    for (int i = lane + 64; i < L1; i += 32) term_add(S1, f1(i), e1);
+  }
+  if (K > 2 && e2) {
+    if (lane < L2) term_add(S2, a2, e2);
+    if (lane + 32 < L2) term_add(S2, b2, e2);
+    for (int i = lane + 64; i < L2; i += 32) term_add(S2, f2(i), e2);
+  }
   fix_allreduce(S0);
   if (K > 1) fix_allreduce(S1);
   if (K > 2) fix_allreduce(S2);
