@@ -229,8 +229,32 @@ WarpLayout make_layout(int kind, int vc, int CAP, int W, bool dia, bool pi = fal
   L.gk = take(lomr ? 4 * H : 0);
   L.gv = take(lomr ? vc * H : 0);
   L.go = take(lomr ? 2 * H : 0);
+  // LOMR: the union table and the select scratch (tie rows, histogram) live
+  // in table B's bytes, which they use only while table B is empty (the
+  // pass clears it before its first product); the inner products look R
+  // and V up in the tables directly, so no looked-up-values region is needed
+  bool in_b = false;
+  if (lomr) {
+    int u = 0;
+    auto sub = [&](int bytes) {
+      int at = L.gk + u;
+      u = align16(u + bytes);
+      return at;
+    };
+    L.uk = sub(4 * HU);
+    L.ua = sub(vc * HU);
+    L.ub = sub(vc * HU);
+    L.uo = sub(2 * HU);
+    const int hist_at = align16(std::max(u, 4 * LIST));
+    if (hist_at + 4 * 128 <= o - L.gk) {
+      L.tie = L.gk;
+      L.hist = L.gk + hist_at;
+      L.yc = 0;
+      in_b = true;
+    }
+  }
   // union table, looked-up values and tie scratch share one region
-  {
+  if (!in_b) {
     int base = o;
     int u = 0;
     auto sub = [&](int bytes) {
@@ -261,7 +285,7 @@ WarpLayout make_layout(int kind, int vc, int CAP, int W, bool dia, bool pi = fal
   L.Rv = take(vc * LMAX);
   L.Ur = take(lomr ? 4 * LMAX : 0);
   L.Uv = take(lomr ? vc * LMAX : 0);
-  L.hist = take(4 * 128);  // 256 packed 16-bit bins
+  if (!in_b) L.hist = take(4 * 128);  // 256 packed 16-bit bins
   L.zr = take(pi ? 4 * LMAX : 0);
   L.zv = take(pi ? vc * LMAX : 0);
   L.bytes = o;
@@ -286,9 +310,9 @@ PassCfg make_cfg(int kind, int vc, int n, int CAP, int W, bool dia, int smem_max
   c.lay = make_layout(kind, vc, CAP, W, dia, pi);
   const int nq = 6;
   const int extra_fixed = 8 * 1024;  // reduction scratch (1024 doubles)
-  // defaults measured on GB300 (64^3 operator, cap 3): LOMR's large scratch
-  // prefers 8-warp CTAs at two per SM, the CG passes four CTAs per SM
-  const int occ_default = kind == kLOMR ? 2 : (kind == kMR ? 3 : 4);
+  // defaults measured on GB300 (64^3 operator, cap 3): LOMR's larger scratch
+  // fits three 8-warp CTAs per SM, MR and the CG passes four
+  const int occ_default = kind == kLOMR ? 3 : 4;
   const int occ = occ_req > 0 ? occ_req : env_int("SPAI_COLPASS_OCC", occ_default);
   const int cpw = cpw_req > 0 ? cpw_req : env_int("SPAI_COLPASS_CPW", 4);
   c.ok = false;

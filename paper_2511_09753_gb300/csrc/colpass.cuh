@@ -115,8 +115,6 @@ __device__ void store_col(ColCtx<VS, VC>& c, int* grow, void* gval, int* glen, i
   c.bytes += (unsigned long long)len * (sizeof(int) + sizeof(VS)) + sizeof(int);
 }
 
-__device__ __forceinline__ int L_lmax(const PassParams& p) { return p.capmax * p.W + 1; }
-
 template <typename VC>
 __device__ __forceinline__ int spgemm(const PassParams& p, const HashT& h, int* xr, VC* xv, int L,
                                       int diag, int* sr, VC* sv, int lane, int seg) {
@@ -145,7 +143,6 @@ __device__ void column_work(ColCtx<VS, VC>& c, int j, double* part) {
   VC* Rv = c.template at<VC>(L.Rv);
   uint32_t* hist = c.template at<uint32_t>(L.hist);
   VC* yc = c.template at<VC>(L.yc);
-  VC* yc2 = c.template at<VC>(L.yc + ((int)sizeof(VC) * L_lmax(p) + 15) / 16 * 16);
   int* tie = c.template at<int>(L.tie);
   HashT ha;
   ha.key = c.template at<int>(L.hk);
@@ -292,17 +289,17 @@ __device__ void column_work(ColCtx<VS, VC>& c, int j, double* part) {
       Lz = warp_select(Rr, Rv, LR, cap, Zr, Zv, hist, tie, p.drop, ovf, lane);
     }
     store_col(c, p.Zrow, p.Zval, p.Zlen, j, off, Lz, Zr, Zv);
+    hash_clear_all(hb, lane);  // its bytes also held the union table and the select scratch
     int cu = spgemm(p, hb, Zr, Zv, Lz, -1, Tr, Tv, lane, c.seg);   // table B: U = A Z
-    lookup_table(hb, cu, ha, yc, lane);                     // R at the rows of U
     __syncwarp();
     double t3[3];
     if (PI)  // (R,R), (U,Pi U), (U,Pi R)
       fixsum<3>(t3, lane, TermSq<VC>{Rv}, LR,
                 TermWSqTable<VC>{hb.key, (const VC*)hb.val, hb.occ, p.pi}, cu,
-                TermWProdTable<VC>{hb.key, (const VC*)hb.val, hb.occ, yc, p.pi}, cu);
+                TermWProdTableFind<VC>{hb.key, (const VC*)hb.val, hb.occ, ha, p.pi}, cu);
     else     // (R,R), (U,U), (U,R)
       fixsum<3>(t3, lane, TermSq<VC>{Rv}, LR, TermSqTable<VC>{(const VC*)hb.val, hb.occ}, cu,
-                TermProdTable<VC>{(const VC*)hb.val, hb.occ, yc}, cu);
+                TermProdTableFind<VC>{hb.key, (const VC*)hb.val, hb.occ, ha}, cu);
     part[0] = t3[0];
     part[1] = t3[1];
     part[4] = t3[2];
@@ -310,20 +307,18 @@ __device__ void column_work(ColCtx<VS, VC>& c, int j, double* part) {
     hash_clear(hb, cu, lane);
     int cv = spgemm(p, hb, Pr, Pv, Lp, -1, Tr, Tv, lane, c.seg);   // table B: V = A P
     c.spg += 2;
-    lookup_list(Ur, LU, hb, yc, lane);                      // V at the rows of U
-    lookup_table(hb, cv, ha, yc2, lane);                    // R at the rows of V
     __syncwarp();
     if (PI)  // (V,Pi V), (U,Pi V), (V,Pi R)
       fixsum<3>(t3, lane, TermWSqTable<VC>{hb.key, (const VC*)hb.val, hb.occ, p.pi}, cv,
-                TermWProd<VC>{Ur, Uv, yc, p.pi}, LU,
-                TermWProdTable<VC>{hb.key, (const VC*)hb.val, hb.occ, yc2, p.pi}, cv);
+                TermWProdFind<VC>{Ur, Uv, hb, p.pi}, LU,
+                TermWProdTableFind<VC>{hb.key, (const VC*)hb.val, hb.occ, ha, p.pi}, cv);
     else     // (V,V), (U,V), (V,R)
-      fixsum<3>(t3, lane, TermSqTable<VC>{(const VC*)hb.val, hb.occ}, cv, TermProd<VC>{Uv, yc}, LU,
-                TermProdTable<VC>{(const VC*)hb.val, hb.occ, yc2}, cv);
+      fixsum<3>(t3, lane, TermSqTable<VC>{(const VC*)hb.val, hb.occ}, cv,
+                TermProdFind<VC>{Ur, Uv, hb}, LU,
+                TermProdTableFind<VC>{hb.key, (const VC*)hb.val, hb.occ, ha}, cv);
     part[2] = t3[0];
     part[3] = t3[1];
     part[5] = t3[2];
-    hash_clear(hb, cv, lane);
     hash_clear(ha, cr, lane);
     return;
   }

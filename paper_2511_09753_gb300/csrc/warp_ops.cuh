@@ -787,6 +787,47 @@ template <typename V> struct TermWProdTable {  // pi_k a[occ[i]] y_i
   }
 };
 
+// The same products with the second factor found in a hash table (0 when
+// its row is absent), for inner products over rows of two different columns.
+template <typename V> struct TermProdFind {        // x_i * b(r_i)
+  const int* r;
+  const V* x;
+  HashT b;
+  __device__ Term operator()(int i) const { return term_prod(x[i], hash_find<V>(b, r[i])); }
+};
+template <typename V> struct TermProdTableFind {   // a[s] * b(key[s]), s = occ[i]
+  const int* key;
+  const V* a;
+  const uint16_t* occ;
+  HashT b;
+  __device__ Term operator()(int i) const {
+    const int s = occ[i];
+    return term_prod(a[s], hash_find<V>(b, key[s]));
+  }
+};
+template <typename V> struct TermWProdFind {       // pi_k x_i b(k), k = r_i
+  const int* r;
+  const V* x;
+  HashT b;
+  const double* pi;
+  __device__ Term operator()(int i) const {
+    const int k = r[i];
+    return term_wprod(x[i], hash_find<V>(b, k), pi[k]);
+  }
+};
+template <typename V> struct TermWProdTableFind {  // pi_k a[s] b(k), s = occ[i], k = key[s]
+  const int* key;
+  const V* a;
+  const uint16_t* occ;
+  HashT b;
+  const double* pi;
+  __device__ Term operator()(int i) const {
+    const int s = occ[i];
+    const int k = key[s];
+    return term_wprod(a[s], hash_find<V>(b, k), pi[k]);
+  }
+};
+
 // (Pi R)_j of a list: z_k = pi_k r_k in FP64 rounded to the value type,
 // exact zeros removed (Algorithms 5, 7, 8: Z := Pi R).  Returns the length.
 template <typename V>
