@@ -74,6 +74,9 @@ struct spai_ctx {
   int *d_Mrow = nullptr, *d_Prow = nullptr, *d_Zrow = nullptr;
   void *d_Mval = nullptr, *d_Pval = nullptr, *d_Zval = nullptr;
   int *d_Mlen = nullptr, *d_Plen = nullptr, *d_Zlen = nullptr;
+  // CG: the residual of pass A kept for the next pass B ([n][capmax*W+1])
+  int *d_Rrow = nullptr, *d_Rlen = nullptr;
+  void* d_Rval = nullptr;
   // scalars and reduction workspace
   DevScalars* d_sc = nullptr;
   double *d_hres = nullptr, *d_hcoef = nullptr;
@@ -231,8 +234,7 @@ WarpLayout make_layout(int kind, int vc, int CAP, int W, bool dia, bool pi = fal
   L.go = take(lomr ? 2 * H : 0);
   // LOMR: the union table and the select scratch (tie rows, histogram) live
   // in table B's bytes, which they use only while table B is empty (the
-  // pass clears it before its first product); the inner products look R
-  // and V up in the tables directly, so no looked-up-values region is needed
+  // pass clears it before its first product)
   bool in_b = false;
   if (lomr) {
     int u = 0;
@@ -249,11 +251,10 @@ WarpLayout make_layout(int kind, int vc, int CAP, int W, bool dia, bool pi = fal
     if (hist_at + 4 * 128 <= o - L.gk) {
       L.tie = L.gk;
       L.hist = L.gk + hist_at;
-      L.yc = 0;
       in_b = true;
     }
   }
-  // union table, looked-up values and tie scratch share one region
+  // union table and tie scratch share one region
   if (!in_b) {
     int base = o;
     int u = 0;
@@ -266,8 +267,7 @@ WarpLayout make_layout(int kind, int vc, int CAP, int W, bool dia, bool pi = fal
     L.ua = sub(vc * HU);
     L.ub = sub(vc * HU);
     L.uo = sub(2 * HU);
-    int region = std::max(u, std::max(4 * LIST, align16(vc * LMAX) + vc * LMAX));
-    L.yc = base;
+    int region = std::max(u, 4 * LIST);
     L.tie = base;
     o = align16(base + region);
   }
@@ -425,6 +425,9 @@ PassParams base_params(spai_ctx* h, int kind, bool res, bool pi = false) {
   p.Zrow = h->d_Zrow;
   p.Zval = h->d_Zval;
   p.Zlen = h->d_Zlen;
+  p.Rrow = h->d_Rrow;
+  p.Rval = h->d_Rval;
+  p.Rlen = h->d_Rlen;
   p.ell_col = h->d_ell_col;
   p.ell_val = (res || h->prec == SPAI_FP64) ? (const void*)h->d_ell64 : (const void*)h->d_ell32;
   p.dia = h->dia ? 1 : 0;
@@ -484,6 +487,9 @@ void free_all(spai_ctx* h) {
   dfree(h->d_Mlen);
   dfree(h->d_Plen);
   dfree(h->d_Zlen);
+  dfree(h->d_Rrow);
+  dfree(h->d_Rval);
+  dfree(h->d_Rlen);
   dfree(h->d_sc);
   dfree(h->d_seg_of_col);
   dfree(h->d_seg_col0);
@@ -1190,13 +1196,32 @@ int spai_run(spai_handle h, int method, int iters, int drop_rule, spai_history* 
   CK(cudaMemsetAsync(h->d_hcoef, 0xff, sizeof(double) * 2 * std::max(iters, 1) * nh, st));
   invalidate_rows(h);
   const int drop = drop_rule == SPAI_DROP_TOPK_COL ? 1 : 0;
-  auto pass = [&](int kind, int upd, int dir, int iter, int fresh_b) -> cudaError_t {
+  // CG: pass A keeps R_{i+1} for pass B of the next iteration, which then
+  // reads it instead of repeating the product (the same values)
+  const bool keep_r = base == SPAI_CG && iters > 1;
+  if (keep_r && !h->d_Rrow) {
+    const size_t cnt = (size_t)h->n * ((size_t)h->capmax * h->W + 1);
+    const size_t vb = h->prec == SPAI_FP64 ? 8 : 4;
+    rc = dalloc(&h->d_Rrow, cnt);
+    if (!rc) rc = dalloc((char**)&h->d_Rval, cnt * vb);
+    if (!rc) rc = dalloc(&h->d_Rlen, (size_t)h->n);
+    if (rc) {
+      dfree(h->d_Rrow);
+      dfree(h->d_Rval);
+      dfree(h->d_Rlen);
+      return rc;
+    }
+  }
+  auto pass = [&](int kind, int upd, int dir, int iter, int fresh_b, int r_in = 0,
+                  int r_out = 0) -> cudaError_t {
     PassParams p = base_params(h, kind, false, pim);
     p.do_update = upd;
     p.do_dir = dir;
     p.drop = drop;
     p.iter = iter;
     p.fresh = fresh_b;
+    p.r_in = r_in;
+    p.r_out = r_out;
     return timed_launch(h, p, pim ? h->cfg_pi[kind] : h->cfg[kind], false);
   };
   if (base == SPAI_MR || base == SPAI_LOMR) {
@@ -1213,8 +1238,8 @@ int spai_run(spai_handle h, int method, int iters, int drop_rule, spai_history* 
       CK(pass(kCGB, 0, 1, 0, 1));
     } else {
       for (int i = 0; i < iters; i++) {
-        CK(pass(kCGB, 0, 1, i, i == 0));
-        CK(pass(kCGA, 0, 1, i, 0));
+        CK(pass(kCGB, 0, 1, i, i == 0, keep_r && i > 0));
+        CK(pass(kCGA, 0, 1, i, 0, 0, keep_r && i + 1 < iters));
       }
     }
   }

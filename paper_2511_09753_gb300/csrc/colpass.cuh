@@ -103,6 +103,37 @@ __device__ void load_cols(ColCtx<VS, VC>& c, long long off, int Lm, int* Mr, VC*
   __syncwarp();
 }
 
+// CG: the R list of column j kept between pass A and the next pass B
+template <typename VS, typename VC>
+__device__ void store_r(ColCtx<VS, VC>& c, int j, int LR, const int* Rr, const VC* Rv) {
+  const PassParams& p = c.p;
+  const long long o = (long long)j * (p.capmax * p.W + 1);
+  VC* gv = (VC*)p.Rval;
+  for (int e = c.lane; e < LR; e += 32) {
+    p.Rrow[o + e] = Rr[e];
+    gv[o + e] = Rv[e];
+  }
+  if (c.lane == 0) p.Rlen[j] = LR;
+  c.bytes += (unsigned long long)LR * (sizeof(int) + sizeof(VC)) + sizeof(int);
+}
+
+template <typename VS, typename VC>
+__device__ int load_r(ColCtx<VS, VC>& c, int j, int* Rr, VC* Rv) {
+  const PassParams& p = c.p;
+  const long long o = (long long)j * (p.capmax * p.W + 1);
+  const VC* gv = (const VC*)p.Rval;
+  const int LR = p.Rlen[j];
+  for (int e = c.lane; e < LR; e += 32) {
+    const int r = p.Rrow[o + e];
+    const VC v = gv[o + e];
+    Rr[e] = r;
+    Rv[e] = v;
+  }
+  __syncwarp();
+  c.bytes += (unsigned long long)LR * (sizeof(int) + sizeof(VC)) + sizeof(int);
+  return LR;
+}
+
 template <typename VS, typename VC>
 __device__ void store_col(ColCtx<VS, VC>& c, int* grow, void* gval, int* glen, int j, long long off,
                           int len, const int* sr, const VC* sv) {
@@ -142,7 +173,6 @@ __device__ void column_work(ColCtx<VS, VC>& c, int j, double* part) {
   int* Rr = c.template at<int>(L.Rr);
   VC* Rv = c.template at<VC>(L.Rv);
   uint32_t* hist = c.template at<uint32_t>(L.hist);
-  VC* yc = c.template at<VC>(L.yc);
   int* tie = c.template at<int>(L.tie);
   HashT ha;
   ha.key = c.template at<int>(L.hk);
@@ -161,12 +191,13 @@ __device__ void column_work(ColCtx<VS, VC>& c, int j, double* part) {
   const bool needP = (p.kind == kMR && p.do_update) || p.kind == kLOMR || p.kind == kCGA ||
                      p.kind == kCGB;
   const bool needZ = p.kind == kLOMR && p.do_update;
-  int Lm = p.Mlen[j];
+  const bool needM = !(p.kind == kCGB && p.r_in);  // M only feeds R there
+  int Lm = needM ? p.Mlen[j] : 0;
   int Lp = needP ? p.Plen[j] : 0;
   const int Lz0 = needZ ? p.Zlen[j] : 0;
   load_cols(c, off, Lm, Mr, Mv, Lp, Pr, Pv, Lz0, c.template at<int>(L.Zr), c.template at<VC>(L.Zv));
   c.bytes += (unsigned long long)(Lm + Lp + Lz0) * (sizeof(int) + sizeof(VS)) +
-             (1 + (int)needP + (int)needZ) * sizeof(int);
+             ((int)needM + (int)needP + (int)needZ) * sizeof(int);
 
   if (p.kind == kSCORE) {
     // Appendix A, Eq. 430: dropping m_kj alone changes ||R||_F^2 by
@@ -237,13 +268,11 @@ __device__ void column_work(ColCtx<VS, VC>& c, int j, double* part) {
     }
     int cq = spgemm(p, ha, Pr, Pv, Lp, -1, Tr, Tv, lane, c.seg);  // table holds Q = A P
     c.spg++;
-    lookup_list(Rr, LR, ha, yc, lane);                      // Q at the rows of R
-    __syncwarp();
     if (PI)  // (R,R), (R,Pi Q), (Q,Pi Q)
-      fixsum<3>(part, lane, TermSq<VC>{Rv}, LR, TermWProd<VC>{Rr, Rv, yc, p.pi}, LR,
+      fixsum<3>(part, lane, TermSq<VC>{Rv}, LR, TermWProdFind<VC>{Rr, Rv, ha, p.pi}, LR,
                 TermWSqTable<VC>{ha.key, (const VC*)ha.val, ha.occ, p.pi}, cq);
     else     // (R,R), (R,Q), (Q,Q)
-      fixsum<3>(part, lane, TermSq<VC>{Rv}, LR, TermProd<VC>{Rv, yc}, LR,
+      fixsum<3>(part, lane, TermSq<VC>{Rv}, LR, TermProdFind<VC>{Rr, Rv, ha}, LR,
                 TermSqTable<VC>{(const VC*)ha.val, ha.occ}, cq);
     hash_clear(ha, cq, lane);
     return;
@@ -332,6 +361,7 @@ __device__ void column_work(ColCtx<VS, VC>& c, int j, double* part) {
     int LR = table_to_list(ha, cr, j, Rr, Rv, lane);
     hash_clear(ha, cr, lane);
     c.spg++;
+    if (p.r_out) store_r(c, j, LR, Rr, Rv);
     if (PI)  // (R,R), (R,Pi R)
       fixsum<2>(part, lane, TermSq<VC>{Rv}, LR, TermWSq<VC>{Rr, Rv, p.pi}, LR);
     else
@@ -341,10 +371,15 @@ __device__ void column_work(ColCtx<VS, VC>& c, int j, double* part) {
 
   // kCGB
   {
-    int cr = spgemm(p, ha, Mr, Mv, Lm, j, Tr, Tv, lane, c.seg);
-    int LR = table_to_list(ha, cr, j, Rr, Rv, lane);
-    hash_clear(ha, cr, lane);
-    c.spg++;
+    int LR;
+    if (p.r_in) {  // R as the previous pass A computed it
+      LR = load_r(c, j, Rr, Rv);
+    } else {
+      int cr = spgemm(p, ha, Mr, Mv, Lm, j, Tr, Tv, lane, c.seg);
+      LR = table_to_list(ha, cr, j, Rr, Rv, lane);
+      hash_clear(ha, cr, lane);
+      c.spg++;
+    }
     CombAxpy<VC> f{c.sc->beta};
     int Lt;
     if (PI) {  // P = D(Pi R + beta P) (Algorithm 7)
@@ -359,13 +394,11 @@ __device__ void column_work(ColCtx<VS, VC>& c, int j, double* part) {
     store_col(c, p.Prow, p.Pval, p.Plen, j, off, Lp, Pr, Pv);
     int cq = spgemm(p, ha, Pr, Pv, Lp, -1, Tr, Tv, lane, c.seg);  // table holds Q = A P
     c.spg++;
-    lookup_list(Pr, Lp, ha, yc, lane);                     // Q at the rows of P
-    __syncwarp();
     if (PI)  // (R,R), (P,Q), (R,Pi R)
-      fixsum<3>(part, lane, TermSq<VC>{Rv}, LR, TermProd<VC>{Pv, yc}, Lp,
+      fixsum<3>(part, lane, TermSq<VC>{Rv}, LR, TermProdFind<VC>{Pr, Pv, ha}, Lp,
                 TermWSq<VC>{Rr, Rv, p.pi}, LR);
     else     // (R,R), (P,Q)
-      fixsum<2>(part, lane, TermSq<VC>{Rv}, LR, TermProd<VC>{Pv, yc}, Lp);
+      fixsum<2>(part, lane, TermSq<VC>{Rv}, LR, TermProdFind<VC>{Pr, Pv, ha}, Lp);
     hash_clear(ha, cq, lane);
   }
 }

@@ -47,8 +47,7 @@ struct WarpLayout {
   int Rr, Rv, Ur, Uv;           // SpGEMM output lists (LMAX)
   int hk, hv, ho;               // hash table A: keys, values, occupied slots (H)
   int gk, gv, go;               // hash table B (LOMR)
-  int uk, ua, ub, uo;           // union table (HU); shares its bytes with yc / tie
-  int yc;                       // looked-up values for inner products (2 x LMAX)
+  int uk, ua, ub, uo;           // union table (HU); shares its bytes with tie
   int tie;                      // int scratch of the threshold tie-break
   int zr, zv;                   // Pi-preconditioned forms: the list Pi R (LMAX)
   int hist;                     // 256 packed 16-bit bins (128 words)
@@ -73,6 +72,10 @@ struct PassParams {
   int* Mrow; void* Mval; int* Mlen;
   int* Prow; void* Pval; int* Plen;
   int* Zrow; void* Zval; int* Zlen;
+  // CG: R of pass A kept for the next pass B, VC values, [n][capmax*W+1]
+  int* Rrow; void* Rval; int* Rlen;
+  int r_out;             // pass A: store R there
+  int r_in;              // pass B: read R there instead of recomputing it
   const int* ell_col;
   const void* ell_val;   // VC values of A in ELL layout (padding column -1)
   int dia;               // nonzero: A is also stored by diagonal slots

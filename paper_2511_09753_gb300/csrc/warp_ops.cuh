@@ -733,17 +733,6 @@ template <typename V> struct TermSqTable {   // x^2 of the occupied slots of a t
     return term_prod(x, x);
   }
 };
-template <typename V> struct TermProd {      // x_i * y_i of two aligned arrays
-  const V* x;
-  const V* y;
-  __device__ Term operator()(int i) const { return term_prod(x[i], y[i]); }
-};
-template <typename V> struct TermProdTable { // a[occ[i]] * y_i
-  const V* a;
-  const uint16_t* occ;
-  const V* y;
-  __device__ Term operator()(int i) const { return term_prod(a[occ[i]], y[i]); }
-};
 
 // Pi-weighted terms of Section 5's inner products: fl(fl(x y) pi_k), the
 // product of the two values (exact for FP32 values) times the row weight,
@@ -758,13 +747,6 @@ template <typename V> struct TermWSq {       // pi_k x_k^2 of a list
   const double* pi;
   __device__ Term operator()(int i) const { return term_wprod(v[i], v[i], pi[r[i]]); }
 };
-template <typename V> struct TermWProd {     // pi_k x_k y_k of two aligned arrays
-  const int* r;
-  const V* x;
-  const V* y;
-  const double* pi;
-  __device__ Term operator()(int i) const { return term_wprod(x[i], y[i], pi[r[i]]); }
-};
 template <typename V> struct TermWSqTable {  // pi_k x_k^2 of the occupied slots of a table
   const int* key;
   const V* v;
@@ -773,17 +755,6 @@ template <typename V> struct TermWSqTable {  // pi_k x_k^2 of the occupied slots
   __device__ Term operator()(int i) const {
     const int s = occ[i];
     return term_wprod(v[s], v[s], pi[key[s]]);
-  }
-};
-template <typename V> struct TermWProdTable {  // pi_k a[occ[i]] y_i
-  const int* key;
-  const V* a;
-  const uint16_t* occ;
-  const V* y;
-  const double* pi;
-  __device__ Term operator()(int i) const {
-    const int s = occ[i];
-    return term_wprod(a[s], y[i], pi[key[s]]);
   }
 };
 
@@ -853,18 +824,6 @@ __device__ int list_scale_pi(const int* rr, const V* rv, int L, const double* pi
   }
   __syncwarp();
   return out;
-}
-
-// y_i = value of row xr[i] in table h (0 if absent)
-template <typename V>
-__device__ void lookup_list(const int* xr, int L, const HashT& h, V* y, int lane) {
-  for (int i = lane; i < L; i += 32) y[i] = hash_find<V>(h, xr[i]);
-}
-
-// y_i = value in table b of the row of the i-th occupied slot of table a
-template <typename V>
-__device__ void lookup_table(const HashT& a, int cnt, const HashT& b, V* y, int lane) {
-  for (int i = lane; i < cnt; i += 32) y[i] = hash_find<V>(b, a.key[a.occ[i]]);
 }
 
 }  // namespace spai

@@ -166,9 +166,10 @@ def test_table2_spgemm_counts_on_gpu():
     spai = _spai()
     n, rp, ci, v = I.laplacian_2d_5pt(16)
     K = 5
-    # column SpGEMMs per iteration: MR 2, LOMR 3 (Table 2); the GPU CG pass
-    # recomputes R instead of storing it (3 instead of 2)
-    for m, per, extra in (("mr", 2, 1), ("lomr", 3, 1), ("cg", 3, 0)):
+    # column SpGEMMs per iteration: MR 2, LOMR 3, CG 2 (Table 2), plus the
+    # final (MR, LOMR) or initial (CG) residual; CG's pass B reads the R that
+    # the previous pass A computed
+    for m, per, extra in (("mr", 2, 1), ("lomr", 3, 1), ("cg", 2, 1)):
         g = spai.Spai(n, rp, ci, v, cap_factor=2.0)
         s0 = g.stats()["spgemm_columns"]
         g.run(m, K)
