@@ -158,7 +158,7 @@ def run_ours(args):
     # device-resident inputs: A copied once, handle created outside the timed region
     g = Spai(n, rp, ci, v, prec="mixed", cap_factor=CAP)
     g.set_pcg_prec("mixed")
-    tuned = {m: g.autotune(m, 3) for m in METHODS}  # launch shapes (results unchanged)
+    tuned = {m: g.autotune(m, 10) for m in METHODS}  # launch shapes (results unchanged)
     b_dev = torch.tensor(b, dtype=torch.float64, device="cuda")
     x_dev = torch.empty_like(b_dev)
 
@@ -337,7 +337,7 @@ def run_batch(args):
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     g = SpaiBatch(mats, prec="mixed", cap_factor=CAP)
-    g.autotune("lomr", 3)
+    g.autotune("lomr", 5)
     b_dev = torch.tensor(flatB, dtype=torch.float64, device="cuda")
     x_dev = torch.empty_like(b_dev)
     pcg_ms = []

@@ -182,9 +182,11 @@ int spai_set_stream(spai_handle h, void *stream);
 int spai_run(spai_handle h, int method, int iters, int drop_rule, spai_history *hist);
 
 /* Launch-shape autotuner (no counterpart in the paper).  For the column
- * passes that `method` uses, times `iters` iterations from M_0 with each
- * candidate shape (1..4 CTAs per SM x 1, 2, 4 or 8 columns per warp) and
- * keeps the fastest for later calls.  Results do not depend on the shape
+ * passes that `method` uses, runs `iters` iterations from M_0 and then
+ * times `iters` more (continuing from that state) with each
+ * distinct candidate shape (the CTA size that lets 1..8 CTAs share an
+ * SM's shared memory x 1, 2, 4 or 8 columns per warp) and keeps the
+ * fastest for later calls.  Results do not depend on the shape
  * (column sums are order-free and the Frobenius tree runs over column
  * indices), so only the time changes.  Leaves M = diag(A)^{-1} and no
  * recurrence.  *best_ms (may be NULL): the chosen shape's time per

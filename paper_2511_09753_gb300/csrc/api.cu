@@ -283,8 +283,6 @@ WarpLayout make_layout(int kind, int vc, int CAP, int W, bool dia, bool pi = fal
   L.Tv = take(vc * TMAX);
   L.Rr = take(4 * LMAX);
   L.Rv = take(vc * LMAX);
-  L.Ur = take(lomr ? 4 * LMAX : 0);
-  L.Uv = take(lomr ? vc * LMAX : 0);
   if (!in_b) L.hist = take(4 * 128);  // 256 packed 16-bit bins
   L.zr = take(pi ? 4 * LMAX : 0);
   L.zv = take(pi ? vc * LMAX : 0);
@@ -310,11 +308,12 @@ PassCfg make_cfg(int kind, int vc, int n, int CAP, int W, bool dia, int smem_max
   c.lay = make_layout(kind, vc, CAP, W, dia, pi);
   const int nq = 6;
   const int extra_fixed = 8 * 1024;  // reduction scratch (1024 doubles)
-  // defaults measured on GB300 (64^3 operator, cap 3): LOMR's larger scratch
-  // fits three 8-warp CTAs per SM, MR and the CG passes four
-  const int occ_default = kind == kLOMR ? 3 : 4;
-  const int occ = occ_req > 0 ? occ_req : env_int("SPAI_COLPASS_OCC", occ_default);
-  const int cpw = cpw_req > 0 ? cpw_req : env_int("SPAI_COLPASS_CPW", 4);
+  // defaults measured on GB300 (64^3 operator, cap 3, 50 iterations from
+  // M_0): 8-warp CTAs everywhere (smaller CTAs that pack more warps leave
+  // too little L1 for the gathers of A), LOMR with one column per warp,
+  // MR and the CG passes with eight
+  const int occ = occ_req > 0 ? occ_req : env_int("SPAI_COLPASS_OCC", kind == kLOMR ? 3 : 4);
+  const int cpw = cpw_req > 0 ? cpw_req : env_int("SPAI_COLPASS_CPW", kind == kLOMR ? 1 : 8);
   c.ok = false;
   for (int NW = 8; NW >= 1; NW >>= 1) {
     // B: columns per CTA, a power of two: cpw per warp, fewer when n is
@@ -1311,23 +1310,28 @@ int spai_autotune(spai_handle h, int method, int iters, double* best_ms) {
     return SPAI_ERR_CUDA;
   }
   int rc = SPAI_OK;
-  for (int occ = 1; occ <= 4 && !rc; occ++)
+  std::vector<long long> tried;  // (NW, B) of each kind, packed
+  for (int occ = 1; occ <= 8 && !rc; occ++)
     for (int cpw = 1; cpw <= 8 && !rc; cpw *= 2) {
       PassCfg c[2];
       bool ok = true;
+      long long key = 0;
       for (int q = 0; q < nk; q++) {
         c[q] = make_cfg(kinds[q], vc, h->n, h->capmax, h->W, h->dia, h->smem_max, h->Bmin, h->Bmax,
                         pim, occ, cpw);
         ok &= c[q].ok && c[q].nb <= h->red_nb && c[q].ngroups <= h->red_ng;
+        key = key * 65536 + (long long)c[q].NW * 2048 + c[q].B;
       }
-      if (!ok) continue;
+      if (!ok || std::find(tried.begin(), tried.end(), key) != tried.end()) continue;
+      tried.push_back(key);
       for (int q = 0; q < nk; q++) cfgs[kinds[q]] = c[q];
+      // untimed: `iters` iterations from M_0, so that the columns have
+      // filled towards their caps before the timed iterations
       rc = spai_reset(h);
       if (!rc) {
-        int r1 = spai_run(h, method, 1, SPAI_DROP_TOPK_COL, nullptr);  // warm-up
+        int r1 = spai_run(h, method, iters, SPAI_DROP_TOPK_COL, nullptr);
         if (r1 < 0) rc = r1;
       }
-      if (!rc) rc = spai_reset(h);
       if (rc) break;
       cudaEventRecord(e0, h->stream);
       int r2 = spai_run(h, method, iters, SPAI_DROP_TOPK_COL, nullptr);

@@ -283,8 +283,6 @@ __device__ void column_work(ColCtx<VS, VC>& c, int j, double* part) {
     VC* Zv = c.template at<VC>(L.Zv);
     int* Sr = c.template at<int>(L.Sr);
     VC* Sv = c.template at<VC>(L.Sv);
-    int* Ur = c.template at<int>(L.Ur);
-    VC* Uv = c.template at<VC>(L.Uv);
     HashT hb;
     hb.key = c.template at<int>(L.gk);
     hb.val = c.template at<VC>(L.gv);
@@ -301,11 +299,11 @@ __device__ void column_work(ColCtx<VS, VC>& c, int j, double* part) {
       store_col(c, p.Mrow, p.Mval, p.Mlen, j, off, Lm, Mr, Mv);
     }
     int cr = spgemm(p, ha, Mr, Mv, Lm, j, Tr, Tv, lane, c.seg);
-    int LR = table_to_list(ha, cr, j, Rr, Rv, lane);  // table A now holds R
+    int LR = table_to_list(ha, cr, j, Rr, Rv, lane);
+    hash_clear(ha, cr, lane);
     c.spg++;
     if (!p.do_dir) {
       fixsum<1>(part, lane, TermSq<VC>{Rv}, LR);
-      hash_clear(ha, cr, lane);
       return;
     }
     int Lz;
@@ -318,37 +316,33 @@ __device__ void column_work(ColCtx<VS, VC>& c, int j, double* part) {
       Lz = warp_select(Rr, Rv, LR, cap, Zr, Zv, hist, tie, p.drop, ovf, lane);
     }
     store_col(c, p.Zrow, p.Zval, p.Zlen, j, off, Lz, Zr, Zv);
-    hash_clear_all(hb, lane);  // its bytes also held the union table and the select scratch
-    int cu = spgemm(p, hb, Zr, Zv, Lz, -1, Tr, Tv, lane, c.seg);   // table B: U = A Z
-    __syncwarp();
+    int cu = spgemm(p, ha, Zr, Zv, Lz, -1, Tr, Tv, lane, c.seg);   // table A: U = A Z
     double t3[3];
     if (PI)  // (R,R), (U,Pi U), (U,Pi R)
       fixsum<3>(t3, lane, TermSq<VC>{Rv}, LR,
-                TermWSqTable<VC>{hb.key, (const VC*)hb.val, hb.occ, p.pi}, cu,
-                TermWProdTableFind<VC>{hb.key, (const VC*)hb.val, hb.occ, ha, p.pi}, cu);
+                TermWSqTable<VC>{ha.key, (const VC*)ha.val, ha.occ, p.pi}, cu,
+                TermWProdFind<VC>{Rr, Rv, ha, p.pi}, LR);
     else     // (R,R), (U,U), (U,R)
-      fixsum<3>(t3, lane, TermSq<VC>{Rv}, LR, TermSqTable<VC>{(const VC*)hb.val, hb.occ}, cu,
-                TermProdTableFind<VC>{hb.key, (const VC*)hb.val, hb.occ, ha}, cu);
+      fixsum<3>(t3, lane, TermSq<VC>{Rv}, LR, TermSqTable<VC>{(const VC*)ha.val, ha.occ}, cu,
+                TermProdFind<VC>{Rr, Rv, ha}, LR);
     part[0] = t3[0];
     part[1] = t3[1];
     part[4] = t3[2];
-    int LU = table_to_list(hb, cu, -1, Ur, Uv, lane);
-    hash_clear(hb, cu, lane);
+    hash_clear_all(hb, lane);  // its bytes also held the union table and the select scratch
     int cv = spgemm(p, hb, Pr, Pv, Lp, -1, Tr, Tv, lane, c.seg);   // table B: V = A P
     c.spg += 2;
-    __syncwarp();
     if (PI)  // (V,Pi V), (U,Pi V), (V,Pi R)
       fixsum<3>(t3, lane, TermWSqTable<VC>{hb.key, (const VC*)hb.val, hb.occ, p.pi}, cv,
-                TermWProdFind<VC>{Ur, Uv, hb, p.pi}, LU,
-                TermWProdTableFind<VC>{hb.key, (const VC*)hb.val, hb.occ, ha, p.pi}, cv);
+                TermWProdTableFind<VC>{ha.key, (const VC*)ha.val, ha.occ, hb, p.pi}, cu,
+                TermWProdFind<VC>{Rr, Rv, hb, p.pi}, LR);
     else     // (V,V), (U,V), (V,R)
       fixsum<3>(t3, lane, TermSqTable<VC>{(const VC*)hb.val, hb.occ}, cv,
-                TermProdFind<VC>{Ur, Uv, hb}, LU,
-                TermProdTableFind<VC>{hb.key, (const VC*)hb.val, hb.occ, ha}, cv);
+                TermProdTableFind<VC>{ha.key, (const VC*)ha.val, ha.occ, hb}, cu,
+                TermProdFind<VC>{Rr, Rv, hb}, LR);
     part[2] = t3[0];
     part[3] = t3[1];
     part[5] = t3[2];
-    hash_clear(ha, cr, lane);
+    hash_clear(ha, cu, lane);
     return;
   }
 

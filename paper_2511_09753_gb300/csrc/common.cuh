@@ -44,7 +44,7 @@ struct WarpLayout {
   int Mr, Mv, Pr, Pv, Zr, Zv;   // capped lists (CAP)
   int Sr, Sv;                   // LOMR S list (2 CAP)
   int Tr, Tv;                   // union output before drop (TMAX)
-  int Rr, Rv, Ur, Uv;           // SpGEMM output lists (LMAX)
+  int Rr, Rv;                   // SpGEMM output list (LMAX)
   int hk, hv, ho;               // hash table A: keys, values, occupied slots (H)
   int gk, gv, go;               // hash table B (LOMR)
   int uk, ua, ub, uo;           // union table (HU); shares its bytes with tie

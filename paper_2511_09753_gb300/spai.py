@@ -336,8 +336,9 @@ class Spai:
         return dict(status=rc, iters=it.reshape(k, R), statuses=st.reshape(k, R),
                     relres=rr.reshape(k, R), x=x)
 
-    def autotune(self, method, iters=3):
-        """Pick the fastest launch shape for `method` (resets M); returns ms per iteration."""
+    def autotune(self, method, iters=10):
+        """Pick the fastest launch shape for `method` (times `iters` iterations after
+        `iters` untimed ones; resets M); returns ms per iteration."""
         m = METHODS[method] if isinstance(method, str) else int(method)
         out = C.c_double()
         self._check(self.lib.spai_autotune(self.h, m, int(iters), C.byref(out)), "spai_autotune")
