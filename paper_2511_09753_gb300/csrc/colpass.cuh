@@ -149,7 +149,11 @@ __device__ void store_col(ColCtx<VS, VC>& c, int* grow, void* gval, int* glen, i
 template <typename VC>
 __device__ __forceinline__ int spgemm(const PassParams& p, const HashT& h, int* xr, VC* xv, int L,
                                       int diag, int* sr, VC* sv, int lane, int seg) {
-  if (p.dia) return spgemm_dia(p, h, xr, xv, L, diag, seg, lane);
+  if (p.dia) {
+    if (L <= 32 && (seg >= 0 ? p.seg_D[seg] : p.D) <= 8)
+      return spgemm_dia32(p, h, xr, xv, L, diag, seg, lane);
+    return spgemm_dia(p, h, xr, xv, L, diag, seg, lane);
+  }
   sort_rows_small(xr, xv, L, sr, sv, lane);
   return spgemm_ell(p, h, xr, xv, L, diag, lane);
 }

@@ -613,6 +613,82 @@ __device__ int spgemm_dia(const PassParams& p, const HashT& h, const int* xr, co
   return cnt;
 }
 
+// Short inputs (L <= 32, D <= 8): lane i owns entry i and gathers its row's
+// slot values at once.  The rows of all products are claimed in the table
+// first (order-free: the first attempts at the home slots are issued
+// together, collisions probe on as in hash_insert), then the products are
+// added slot by slot in descending offset -- the same chains as above, each
+// round now a read-modify-write of slots already known.
+template <typename VC>
+__device__ int spgemm_dia32(const PassParams& p, const HashT& h, const int* xr, const VC* xv, int L,
+                            int diag, int seg, int lane) {
+  const VC* dv = (const VC*)p.dia_val;
+  VC* hv = (VC*)h.val;
+  const int D = seg >= 0 ? p.seg_D[seg] : p.D;
+  const bool act = lane < L;
+  int k = 0;
+  VC x = VC(0);
+  if (act) {
+    k = xr[lane];
+    x = xv[lane];
+  }
+  VC a[8];
+  int sl[8];
+#pragma unroll
+  for (int s = 0; s < 8; s++) {
+    a[s] = VC(0);
+    if (act && s < D) a[s] = __ldg(dv + (long long)k * p.Dp + s);
+  }
+  // first attempts: sl = the key found at the home slot (-1: claimed), or
+  // -2 when there is no product
+#pragma unroll
+  for (int s = 0; s < 8; s++) {
+    sl[s] = -2;
+    if (s < D && a[s] != VC(0)) {
+      const int r = k + (seg >= 0 ? p.seg_doff[seg * 32 + s] : p.dia_off[s]);
+      sl[s] = atomicCAS(&h.key[hslot(r, h.H)], -1, r);
+    }
+  }
+  int cnt = 0;
+#pragma unroll
+  for (int s = 7; s >= 0; s--) {
+    if (s < D) {
+      bool isnew = false;
+      int slot = -1;
+      if (sl[s] != -2) {
+        const int r = k + (seg >= 0 ? p.seg_doff[seg * 32 + s] : p.dia_off[s]);
+        int q = hslot(r, h.H);
+        int got = sl[s];
+        while (got != -1 && got != r) {
+          q = (q + 1) & (h.H - 1);
+          got = atomicCAS(&h.key[q], -1, r);
+        }
+        isnew = got == -1;
+        slot = q;
+        if (isnew) hv[q] = VC(0);
+      }
+      sl[s] = slot;
+      occ_append(h, cnt, isnew, slot);
+    }
+  }
+  __syncwarp();
+#pragma unroll
+  for (int s = 7; s >= 0; s--) {
+    if (s < D) {
+      if (sl[s] >= 0) hv[sl[s]] = vfma(a[s], x, hv[sl[s]]);
+      __syncwarp();
+    }
+  }
+  if (diag >= 0) {
+    bool isnew = false;
+    int slot = -1;
+    if (lane == 0) slot = hash_insert<VC>(h, diag, &isnew);
+    occ_append(h, cnt, isnew, slot);
+    __syncwarp();
+  }
+  return cnt;
+}
+
 // General ELL layout (A rows padded with column -1).  X must be row-sorted:
 // products are generated k-major and lanes of one chunk that hit the same r
 // apply their fma in lane order, so each r sees the chain over ascending k.
