@@ -703,15 +703,16 @@ int spai_validate_csr(int64_t n, int64_t nnz, const int32_t* rowptr, const int32
     if (!diag) return SPAI_ERR_NOT_SPD_DIAG;
   }
   if (check_symmetry) {
+    // rows are sorted, so scanning rows i in ascending order meets the
+    // entries (c, i) of each row c in its own order: a cursor per row
+    // points at the entry the next (i, c) must mirror
+    std::vector<int32_t> nxt(rowptr, rowptr + n);
     for (int64_t i = 0; i < n; i++) {
       for (int64_t e = rowptr[i]; e < rowptr[i + 1]; e++) {
-        int32_t c = colind[e];
-        // find (c, i)
-        const int32_t* b = colind + rowptr[c];
-        const int32_t* en = colind + rowptr[c + 1];
-        const int32_t* f = std::lower_bound(b, en, (int32_t)i);
-        if (f == en || *f != i) return SPAI_ERR_NOT_SYMMETRIC;
-        if (vals[rowptr[c] + (f - b)] != vals[e]) return SPAI_ERR_NOT_SYMMETRIC;
+        const int32_t c = colind[e];
+        const int32_t q = nxt[c];
+        if (q >= rowptr[c + 1] || colind[q] != i || vals[q] != vals[e]) return SPAI_ERR_NOT_SYMMETRIC;
+        nxt[c] = q + 1;
       }
     }
   }
@@ -807,16 +808,23 @@ int create_impl(spai_handle* out, int64_t n, int64_t nnz, const int32_t* rp, con
     int Dmax = 0;
     for (int m = 0; m < bd->nseg && ok; m++) {
       std::vector<long long> offs;
+      std::vector<int> hint;  // as for a single matrix below
       for (long long i = bd->col0[m]; i < bd->col0[m] + bd->npad[m] && ok; i++)
         for (int64_t e = rp[i]; e < rp[i + 1]; e++) {
-          long long o = (long long)ci[e] - i;
-          if (std::find(offs.begin(), offs.end(), o) == offs.end()) {
+          const long long o = (long long)ci[e] - i;
+          const size_t t = (size_t)(e - rp[i]);
+          if (t < hint.size() && offs[hint[t]] == o) continue;
+          auto f = std::find(offs.begin(), offs.end(), o);
+          if (f == offs.end()) {
             offs.push_back(o);
             if (offs.size() > 32) {
               ok = false;
               break;
             }
+            f = offs.end() - 1;
           }
+          if (t >= hint.size()) hint.resize(t + 1, 0);
+          hint[t] = (int)(f - offs.begin());
         }
       if (!ok) break;
       std::sort(offs.begin(), offs.end());
@@ -833,9 +841,10 @@ int create_impl(spai_handle* out, int64_t n, int64_t nnz, const int32_t* rp, con
       for (int64_t i = 0; i < n; i++) {
         const int m = seg_of_col[i];
         const int* so = &seg_doff[(size_t)m * 32];
-        for (int64_t e = rp[i]; e < rp[i + 1]; e++) {
-          long long o = (long long)ci[e] - i;
-          int s2 = (int)(std::lower_bound(so, so + seg_D[m], (int)o) - so);
+        int s2 = 0;
+        for (int64_t e = rp[i]; e < rp[i + 1]; e++) {  // columns, hence slots, ascend
+          const int o = (int)((long long)ci[e] - i);
+          while (so[s2] < o) s2++;
           d64[(size_t)i * h->Dp + s2] = va[e];
         }
       }
@@ -849,17 +858,24 @@ int create_impl(spai_handle* out, int64_t n, int64_t nnz, const int32_t* rp, con
     }
   } else {
     std::vector<long long> offs;
+    std::vector<int> hint;  // index in offs of the t-th entry's offset in the previous row
     bool ok = true;
     for (int64_t i = 0; i < n && ok; i++)
       for (int64_t e = rp[i]; e < rp[i + 1]; e++) {
-        long long o = (long long)ci[e] - i;
-        if (std::find(offs.begin(), offs.end(), o) == offs.end()) {
+        const long long o = (long long)ci[e] - i;
+        const size_t t = (size_t)(e - rp[i]);
+        if (t < hint.size() && offs[hint[t]] == o) continue;
+        auto f = std::find(offs.begin(), offs.end(), o);
+        if (f == offs.end()) {
           offs.push_back(o);
           if (offs.size() > 32) {
             ok = false;
             break;
           }
+          f = offs.end() - 1;
         }
+        if (t >= hint.size()) hint.resize(t + 1, 0);
+        hint[t] = (int)(f - offs.begin());
       }
     if (ok) {
       std::sort(offs.begin(), offs.end());
@@ -868,12 +884,15 @@ int create_impl(spai_handle* out, int64_t n, int64_t nnz, const int32_t* rp, con
       h->Dp = h->D;
       for (int s2 = 0; s2 < h->D; s2++) h->dia_off[s2] = (int)offs[s2];
       d64.assign((size_t)n * h->Dp, 0.0);
-      for (int64_t i = 0; i < n; i++)
+      // columns ascend within a row, so the slots of a row ascend too
+      for (int64_t i = 0; i < n; i++) {
+        int s2 = 0;
         for (int64_t e = rp[i]; e < rp[i + 1]; e++) {
-          long long o = (long long)ci[e] - i;
-          int s2 = (int)(std::lower_bound(offs.begin(), offs.end(), o) - offs.begin());
+          const long long o = (long long)ci[e] - i;
+          while (offs[s2] < o) s2++;
           d64[(size_t)i * h->Dp + s2] = va[e];
         }
+      }
       if (h->prec == SPAI_MIXED) {
         d32.resize(d64.size());
         for (size_t k = 0; k < d64.size(); k++) d32[k] = (float)d64[k];

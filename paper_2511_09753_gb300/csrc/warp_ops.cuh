@@ -207,7 +207,13 @@ __device__ __forceinline__ double fix_to_double(Fix128 S, int eb) {
     }
     if (up) mant++;
   }
-  double r = ldexp(__ull2double_rn(mant), shift + eb - 1133);
+  // mant * 2^k; mant <= 2^53 converts exactly.  While the product stays
+  // normal and finite, scaling by 2^k only adds k to the exponent field.
+  const int k = shift + eb - 1133;
+  const double d = __ull2double_rn(mant);
+  const double r = (k >= -1022 && k <= 969)
+                       ? __longlong_as_double(__double_as_longlong(d) + (long long)k * (1ll << 52))
+                       : ldexp(d, k);
   return neg ? -r : r;
 }
 

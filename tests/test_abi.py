@@ -52,6 +52,33 @@ def test_validate_csr_accepts_generators():
         assert spai.validate_csr(n, rp, ci, v) == 0
 
 
+def test_validate_csr_symmetry_is_a_equals_a_transpose():
+    """The symmetry check agrees with A == A^T (scipy) on random perturbations
+    of values and of the pattern (an entry moved to another column)."""
+    sp = pytest.importorskip("scipy.sparse")
+    spai = _lib()
+    rng = np.random.default_rng(5)
+    n, rp, ci, v = I.varcoef_grid((9, 7), seed=3)
+    for t in range(200):
+        ci2, v2 = ci.copy(), v.copy()
+        e = int(rng.integers(len(v)))
+        i = int(np.searchsorted(rp, e, side="right") - 1)
+        if t % 3 == 0:
+            v2[e] = v2[e] * (1.0 + 1e-12)
+        elif t % 3 == 1:  # move an off-diagonal entry to a free column of its row
+            free = sorted(set(range(n)) - set(ci[rp[i]:rp[i + 1]].tolist()))
+            if ci[e] == i or not free:
+                continue
+            row = sorted(set(ci[rp[i]:rp[i + 1]].tolist()) - {int(ci[e])} | {free[t % len(free)]})
+            ci2[rp[i]:rp[i + 1]] = row
+            v2[rp[i]:rp[i + 1]] = [v[rp[i] + ci[rp[i]:rp[i + 1]].tolist().index(c)]
+                                   if c in ci[rp[i]:rp[i + 1]] else v[e] for c in row]
+        A = sp.csr_matrix((v2, ci2, rp), shape=(n, n))
+        sym = (A != A.T).nnz == 0
+        code = spai.validate_csr(n, rp, ci2, v2)
+        assert code == (0 if sym else -4), (t, code, sym)
+
+
 def test_validate_csr_rejects_bad_input():
     spai = _lib()
     n, rp, ci, v = I.laplacian_2d_5pt(4)
