@@ -189,7 +189,9 @@ def run_ours(args):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
+        torch.cuda.nvtx.range_push("step")  # lets an ncu launch list select the timed steps
         last = step(g)
+        torch.cuda.nvtx.range_pop()
         e1.record(stream)
         e1.synchronize()
         times.append(e0.elapsed_time(e1))
@@ -309,8 +311,9 @@ def run_ours(args):
 
 # DRAM bytes (read + write) per column-pass launch, from ncu captures of the
 # --profile mr|lomr|cg cases on this workload, weighted by the launch mix of
-# one step (51 MR, 51 LOMR, 50 + 50 CG passes).
-COLPASS_TRAFFIC_BYTES = 139.0e6
+# one step (51 MR, 51 LOMR, 50 + 50 CG passes); None until taken on the
+# current kernel.
+COLPASS_TRAFFIC_BYTES = None
 
 BATCH_ITERS = 30
 BATCH_RHS = 32
@@ -457,14 +460,15 @@ def run_batch(args):
 
 def profile_case(method, prec):
     """Small launch sequence for ncu captures: one handle on the workload,
-    3 iterations of `method` (4 column passes for MR/LOMR, 6 for CG)."""
+    10 iterations of `method` from M_0 (11 column passes for MR/LOMR, 20 for
+    CG); the later passes see columns filled to their caps as in the bench."""
     import torch
 
     from paper_2511_09753_gb300 import inputs as I
     from paper_2511_09753_gb300.spai import Spai
     n, rp, ci, v = I.varcoef_3d_7pt(64, sigma=1.5, ell=8.0, seed=0)
     g = Spai(n, rp, ci, v, prec=prec, cap_factor=CAP)
-    r = g.run(method, 3)
+    r = g.run(method, 10)
     torch.cuda.synchronize()
     print(json.dumps({"profile": method, "prec": prec, "resnorm": float(r["resnorm"][-1])}))
 

@@ -319,19 +319,25 @@ int spai_drop_global(spai_handle h, int which, int64_t m);
  * cap_j.  Forgets the method recurrence.  Single-matrix handles only. */
 int spai_drop_heuristic(spai_handle h, int64_t m);
 
-/* MR (Algorithm 1, method SPAI_MR) or MR_SPD (Algorithm 5, SPAI_MR_PI) with
- * the paper's global dropping inside every iteration, where its dropping
- * experiments place it (Sec. 7.2): R_i = I - A M_i explicitly; every
- * direction candidate (Pi) R_i kept, then the m_dir entries of largest |v|
- * over the whole matrix kept (Sec. 6.1, Eq. 6.2); alpha_i from that
- * direction, with spai_run's arithmetic; M_i + alpha_i P_i kept whole, then
- * Appendix A's heuristic with density cap m_M (see spai_drop_heuristic).
- * Each iteration takes three column passes and the two global selections.
- * The column capacities cap_j (from cap_factor) must hold the whole
- * candidate columns, else SPAI_ERR_CAPACITY.  hist as for spai_run:
- * resnorm[i] = ||R_i||_F of the dropped iterates, coef[2i] = alpha_i.
- * Returns SPAI_OK, SPAI_CONVERGED_EARLY or an error; forgets any method
- * recurrence.  Single-matrix handles only. */
+/* MR (Algorithm 1), LOMR (Algorithm 4) or CG (Algorithm 3), or their
+ * Pi forms (Algorithms 5, 8, 7; methods SPAI_*_PI), with the paper's
+ * global dropping inside every iteration, where its dropping experiments
+ * place it (Sec. 7.2).  R_i = I - A M_i is formed explicitly.  Every
+ * direction candidate is kept whole, then cut to the m_dir entries of
+ * largest |v| over the whole matrix (Sec. 6.1, Eq. 6.2).  The candidates
+ * are: MR: P_i from (Pi) R_i; LOMR: Z_i from (Pi) R_i and
+ * P_i from S_i = delta_i Z_i + gamma_i P_{i-1}; CG: P_i from
+ * (Pi) R_i + beta_{i-1} P_{i-1}.  The step coefficients come from those
+ * directions, with spai_run's arithmetic.  M_i + alpha_i P_i (MR, CG) or
+ * M_i + S_i (LOMR) is kept whole, then cut by Appendix A's heuristic with
+ * density cap m_M (see spai_drop_heuristic).  CG's beta_i uses the R of the
+ * dropped M_{i+1}.  The column capacities cap_j (from cap_factor) must hold
+ * the whole candidate columns, else SPAI_ERR_CAPACITY.  hist as for
+ * spai_run: resnorm[i] = ||R_i||_F of the dropped iterates;
+ * coef[2i], coef[2i+1] = (alpha_i, 0), (delta_i, gamma_i) or
+ * (alpha_i, beta_i).  Returns SPAI_OK, SPAI_CONVERGED_EARLY,
+ * SPAI_LOMR_FALLBACK or an error, and forgets any method recurrence.
+ * Single-matrix handles only. */
 int spai_run_global(spai_handle h, int method, int iters, int64_t m_dir, int64_t m_M,
                     spai_history *hist);
 

@@ -199,3 +199,180 @@ def run_global_mr(n, rowptr, colind, vals, iters, m_dir, m_M, mixed=False, use_p
         _, rr = residuals(M)
         res.append(math.sqrt(rr))
     return dict(M=M, resnorm=np.array(res), coef=np.array(coef), done=done)
+
+
+# ---------------------------------------------------------------------------
+# LOMR and CG with the same global dropping inside every iteration.  Columns
+# are held as {row: value} dicts; inner products are the column pass's
+# (exact terms x*y, or (x*y)*pi_k with Pi, summed by fixsum per column and
+# pairwise over columns).
+
+def _dicts(X):
+    cp, ri, va = X
+    return [dict(zip(ri[cp[j]:cp[j + 1]].tolist(), va[cp[j]:cp[j + 1]].tolist()))
+            for j in range(len(cp) - 1)]
+
+
+def _csc(n, cols):
+    out = []
+    for c in cols:
+        rows = sorted(r for r, v in c.items() if v != 0.0)
+        out.append((np.array(rows, np.int64), np.array([c[r] for r in rows])))
+    return _to_csc(n, out)
+
+
+def _inner(cols_x, cols_y, w=None):
+    """sum_j (X_j, Y_j) (weighted by w = diag(Pi) when given)."""
+    from oracle import fixsum, pairwise
+    parts = []
+    for x, y in zip(cols_x, cols_y):
+        rows = [r for r in x if r in y]
+        t = [(x[r] * y[r]) * w[r] if w is not None else x[r] * y[r] for r in rows]
+        parts.append(fixsum(np.array(t)))
+    return pairwise(parts)
+
+
+def _setup(n, rowptr, colind, vals, mixed):
+    from oracle import Oracle
+    o = Oracle(n, rowptr, colind, vals, mixed=mixed, cap_factor=float(n))
+    diag = np.zeros(n)
+    for i in range(n):
+        for q in range(rowptr[i], rowptr[i + 1]):
+            if colind[q] == i:
+                diag[i] = vals[q]
+    return o, 1.0 / diag
+
+
+def _residual(o, n, M):
+    """R = I - A M column by column (the method's arithmetic) as dicts."""
+    o.set_M(*M)
+    out = []
+    for j in range(n):
+        r, v = o.column_residual(j)
+        out.append(dict(zip(r.tolist(), v.tolist())))
+    return out
+
+
+def _product(o, n, X):
+    """A X_j for every column (the method's arithmetic) as dicts."""
+    out = []
+    for c in X:
+        rows = sorted(c)
+        r, v = o.product_column(np.array(rows, np.int64), np.array([c[k] for k in rows]))
+        out.append(dict(zip(r.tolist(), v.tolist())))
+    return out
+
+
+def _scaled(R, pi, use_pi, mixed):
+    """(Pi) R, rounded to the value type, exact zeros removed."""
+    if not use_pi:
+        return [dict(c) for c in R]
+    return [{r: _rv(pi[r] * v, mixed) for r, v in c.items() if _rv(pi[r] * v, mixed) != 0.0}
+            for c in R]
+
+
+def run_global_lomr(n, rowptr, colind, vals, iters, m_dir, m_M, mixed=False, use_pi=False):
+    """LOMR (Algorithm 4; LOMR_SPD, Algorithm 8, with Pi = diag(A)^{-1}) with
+    global dropping in every iteration: Z_i = the m_dir largest entries of
+    (Pi) R_i over the whole matrix; delta_i, gamma_i minimise over
+    span{A Z_i, A P_{i-1}} (Theorem 3, MR step when the 2x2 system is
+    near-singular, reading 6); S_i = delta_i Z_i + gamma_i P_{i-1};
+    P_i = the m_dir largest entries of S_i; M_{i+1} = Appendix A's heuristic
+    of M_i + S_i with density cap m_M.  Returns dict(M, resnorm, coef, done,
+    fallback)."""
+    import math
+    o, pi = _setup(n, rowptr, colind, vals, mixed)
+    w = pi if use_pi else None
+    M = o.get_M()
+    P = [dict() for _ in range(n)]  # P_{-1} = 0
+    res, coef = [], []
+    done, fallback = 0, False
+    eps = 2.220446049250313e-16
+    for i in range(iters):
+        R = _residual(o, n, M)
+        rr = _inner(R, R)
+        res.append(math.sqrt(rr))
+        if rr == 0.0:
+            break
+        Z = _dicts(hard_threshold(n, _csc(n, _scaled(R, pi, use_pi, mixed)), m_dir))
+        U, V = _product(o, n, Z), _product(o, n, P)
+        uu, vv, uv = _inner(U, U, w), _inner(V, V, w), _inner(U, V, w)
+        ur, vr = _inner(U, R, w), _inner(V, R, w)
+        if uu == 0.0:
+            break
+        t1, t2 = uu * vv, uv * uv
+        c = t1 - t2
+        if vv == 0.0 or c <= (64.0 * eps) * t1:
+            delta, gamma = ur / uu, 0.0
+            fallback |= vv != 0.0
+        else:
+            delta, gamma = (vv * ur - uv * vr) / c, (uu * vr - uv * ur) / c
+        if not (math.isfinite(delta) and math.isfinite(gamma)):
+            break
+        coef.append((delta, gamma))
+        S = []
+        for z, p in zip(Z, P):
+            S.append({r: _rv(_fma(delta, z.get(r, 0.0), gamma * p.get(r, 0.0)), mixed)
+                      for r in set(z) | set(p)})
+        S = [{r: v for r, v in s.items() if v != 0.0} for s in S]
+        T = []
+        for m, s in zip(_dicts(M), S):
+            T.append({r: _rv(m.get(r, 0.0) + s.get(r, 0.0), mixed) for r in set(m) | set(s)})
+        P = _dicts(hard_threshold(n, _csc(n, S), m_dir))
+        M = heuristic(n, rowptr, colind, vals, _csc(n, T), m_M, mixed=mixed)
+        done += 1
+    if done == iters:
+        R = _residual(o, n, M)
+        res.append(math.sqrt(_inner(R, R)))
+    return dict(M=M, resnorm=np.array(res), coef=np.array(coef).reshape(-1, 2), done=done,
+                fallback=fallback)
+
+
+def run_global_cg(n, rowptr, colind, vals, iters, m_dir, m_M, mixed=False, use_pi=False):
+    """CG on the Frobenius inner product (Algorithm 3; Algorithm 7 with
+    Pi = diag(A)^{-1}) with global dropping in every iteration:
+    P_0 = the m_dir largest entries of (Pi) R_0; alpha_i = (R_i, (Pi) R_i) /
+    (P_i, A P_i); M_{i+1} = Appendix A's heuristic of M_i + alpha_i P_i with
+    density cap m_M; R_{i+1} = I - A M_{i+1}; beta_i = (R_{i+1}, (Pi) R_{i+1})
+    / (R_i, (Pi) R_i); P_{i+1} = the m_dir largest entries of
+    (Pi) R_{i+1} + beta_i P_i.  Returns dict(M, resnorm, coef, done)."""
+    import math
+    o, pi = _setup(n, rowptr, colind, vals, mixed)
+    w = pi if use_pi else None
+    M = o.get_M()
+    R = _residual(o, n, M)
+    rr = _inner(R, R)
+    res, coef = [math.sqrt(rr)], []
+    rz = _inner(R, R, w) if use_pi else rr
+    P = _dicts(hard_threshold(n, _csc(n, _scaled(R, pi, use_pi, mixed)), m_dir))
+    done = 0
+    for i in range(iters):
+        if rz == 0.0:
+            break
+        Q = _product(o, n, P)
+        pq = _inner(P, Q)
+        if pq == 0.0:
+            break
+        alpha = rz / pq
+        if not math.isfinite(alpha):
+            break
+        T = []
+        for m, p in zip(_dicts(M), P):
+            T.append({r: _rv(_fma(alpha, p.get(r, 0.0), m.get(r, 0.0)), mixed) for r in set(m) | set(p)})
+        M = heuristic(n, rowptr, colind, vals, _csc(n, T), m_M, mixed=mixed)
+        R = _residual(o, n, M)
+        rr1 = _inner(R, R)
+        res.append(math.sqrt(rr1))
+        rz1 = _inner(R, R, w) if use_pi else rr1
+        beta = rz1 / rz
+        coef.append((alpha, beta))
+        done += 1
+        if rz1 == 0.0:
+            break
+        Zs = _scaled(R, pi, use_pi, mixed)
+        C = []
+        for z, p in zip(Zs, P):
+            C.append({r: _rv(_fma(beta, p.get(r, 0.0), z.get(r, 0.0)), mixed) for r in set(z) | set(p)})
+        P = _dicts(hard_threshold(n, _csc(n, C), m_dir))
+        rz = rz1
+    return dict(M=M, resnorm=np.array(res), coef=np.array(coef).reshape(-1, 2), done=done)

@@ -1257,7 +1257,7 @@ int spai_run(spai_handle h, int method, int iters, int drop_rule, spai_history* 
     } else {
       for (int i = 0; i < iters; i++) {
         CK(pass(kCGB, 0, 1, i, i == 0, keep_r && i > 0));
-        CK(pass(kCGA, 0, 1, i, 0, 0, keep_r && i + 1 < iters));
+        CK(pass(kCGA, 1, 1, i, 0, 0, keep_r && i + 1 < iters));
       }
     }
   }
@@ -2067,8 +2067,9 @@ static long long count_entries(spai_ctx* h, const int* d_len) {
   return s;
 }
 
+// which: 0 = M, 1 = P, 2 = Z (LOMR's residual direction, internal)
 static int drop_global_impl(spai_ctx* h, int which, int64_t m) {
-  int* len = which == 0 ? h->d_Mlen : h->d_Plen;
+  int* len = which == 0 ? h->d_Mlen : which == 1 ? h->d_Plen : h->d_Zlen;
   const long long N = count_entries(h, len);
   if (N < 0) return SPAI_ERR_CUDA;
   if (N > m) {
@@ -2077,8 +2078,8 @@ static int drop_global_impl(spai_ctx* h, int which, int64_t m) {
     a.n = h->n;
     a.off = h->d_off;
     a.len = len;
-    a.rows = which == 0 ? h->d_Mrow : h->d_Prow;
-    a.vals = which == 0 ? h->d_Mval : h->d_Pval;
+    a.rows = which == 0 ? h->d_Mrow : which == 1 ? h->d_Prow : h->d_Zrow;
+    a.vals = which == 0 ? h->d_Mval : which == 1 ? h->d_Pval : h->d_Zval;
     a.vs = h->prec == SPAI_MIXED ? 4 : 8;
     a.mode = 0;
     a.hist = nullptr;
@@ -2196,58 +2197,104 @@ int spai_drop_heuristic(spai_handle h, int64_t m) {
 int spai_run_global(spai_handle h, int method, int iters, int64_t m_dir, int64_t m_M,
                     spai_history* hist) {
   if (!h || iters < 0 || m_dir < 0 || m_M < 0) return SPAI_ERR_ARG;
-  if (method != SPAI_MR && method != SPAI_MR_PI) return SPAI_ERR_ARG;
+  if (method < SPAI_MR || method > SPAI_CG_PI) return SPAI_ERR_ARG;
   if (h->nseg) return SPAI_ERR_UNSUPPORTED;
-  const bool pim = method == SPAI_MR_PI;
+  const bool pim = method >= SPAI_MR_PI;
   if (pim && !h->pi_ok) return SPAI_ERR_UNSUPPORTED;
+  const int base = pim ? method - SPAI_MR_PI : method;
   int rc = ensure_hist(h, iters + 1);
   if (rc) return rc;
   h->last_iters = iters;
   cudaStream_t st = h->stream;
   CK(cudaMemsetAsync(h->d_Plen, 0, sizeof(int) * h->n, st));
   CK(cudaMemsetAsync(h->d_Zlen, 0, sizeof(int) * h->n, st));
+  CK(cudaMemsetAsync((char*)h->d_sc + offsetof(DevScalars, beta), 0, sizeof(double), st));
+  CK(cudaMemsetAsync((char*)h->d_sc + offsetof(DevScalars, rr), 0, sizeof(double), st));
   rc = reset_call_scalars(h);
   if (rc) return rc;
   CK(cudaMemsetAsync(h->d_hres, 0xff, sizeof(double) * (iters + 1), st));
   CK(cudaMemsetAsync(h->d_hcoef, 0xff, sizeof(double) * 2 * std::max(iters, 1), st));
   h->method = -1;
   invalidate_rows(h);
-  auto pass = [&](int upd, int dir, int iter, int from_slab) -> int {
-    PassParams p = base_params(h, kMR, false, pim);
+  // one column pass, no per-column dropping (drop = 0: columns are kept whole)
+  auto pass = [&](int kind, int upd, int dir, int iter, int from_slab, int store, int fresh) -> int {
+    PassParams p = base_params(h, kind, false, pim);
     p.do_update = upd;
     p.do_dir = dir;
     p.drop = 0;
     p.iter = iter;
+    p.fresh = fresh;
     p.dir_from_slab = from_slab;
-    CK(timed_launch(h, p, pim ? h->cfg_pi[kMR] : h->cfg[kMR], false));
+    p.dir_store = store;
+    CK(timed_launch(h, p, pim ? h->cfg_pi[kind] : h->cfg[kind], false));
     invalidate_rows(h);
     return SPAI_OK;
   };
   DevScalars sc;
+  memset(&sc, 0, sizeof(sc));
   auto read_sc = [&]() -> int {
     CK(cudaMemcpyAsync(&sc, h->d_sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     return SPAI_OK;
   };
+  auto halted = [&]() { return (sc.flags & (kFlagCapacity | kFlagNonfinite)) || sc.stop; };
   int i = 0;
-  for (; i < iters; i++) {
-    // R_i and every direction candidate (Pi) R_i, kept whole
-    if ((rc = pass(0, 1, i, 0)) || (rc = read_sc())) return rc;
-    if (sc.flags & (kFlagCapacity | kFlagNonfinite) || sc.stop) break;
-    // P_i: the m_dir largest entries over the whole matrix (Sec. 6.1)
-    if ((rc = drop_global_impl(h, 1, m_dir))) return rc;
-    // alpha_i from that P_i
-    if ((rc = pass(0, 1, i, 1)) || (rc = read_sc())) return rc;
-    if (sc.flags & (kFlagCapacity | kFlagNonfinite) || sc.stop) break;
-    // M_i + alpha_i P_i, whole, then the Appendix A heuristic with cap m_M
-    if ((rc = pass(1, 0, i + 1, 0)) || (rc = read_sc())) return rc;
-    if (sc.flags & kFlagCapacity) break;
-    if ((rc = drop_heuristic_impl(h, m_M))) return rc;
+  if (base == SPAI_MR) {
+    for (; i < iters; i++) {
+      // R_i and the direction candidate (Pi) R_i, kept whole
+      if ((rc = pass(kMR, 0, 0, i, 0, 1, 0)) || (rc = read_sc())) return rc;
+      if (halted()) break;
+      // P_i: the m_dir largest entries over the whole matrix (Sec. 6.1)
+      if ((rc = drop_global_impl(h, 1, m_dir))) return rc;
+      // alpha_i from that P_i
+      if ((rc = pass(kMR, 0, 1, i, 1, 0, 0)) || (rc = read_sc())) return rc;
+      if (halted()) break;
+      // M_i + alpha_i P_i, whole, then the Appendix A heuristic with cap m_M
+      if ((rc = pass(kMR, 1, 0, i + 1, 0, 0, 0)) || (rc = read_sc())) return rc;
+      if (sc.flags & kFlagCapacity) break;
+      if ((rc = drop_heuristic_impl(h, m_M))) return rc;
+    }
+  } else if (base == SPAI_LOMR) {
+    for (; i < iters; i++) {
+      // R_i and the candidate Z_i = (Pi) R_i, whole
+      if ((rc = pass(kLOMR, 0, 0, i, 0, 1, 0)) || (rc = read_sc())) return rc;
+      if (halted()) break;
+      if ((rc = drop_global_impl(h, 2, m_dir))) return rc;
+      // delta_i, gamma_i from that Z_i and P_{i-1} (Theorem 3)
+      if ((rc = pass(kLOMR, 0, 1, i, 1, 0, 0)) || (rc = read_sc())) return rc;
+      if (halted()) break;
+      // S_i = delta Z_i + gamma P_{i-1}; P_i = S_i and M_i + S_i, whole
+      if ((rc = pass(kLOMR, 1, 0, i + 1, 0, 0, 0)) || (rc = read_sc())) return rc;
+      if (sc.flags & kFlagCapacity) break;
+      if ((rc = drop_global_impl(h, 1, m_dir))) return rc;
+      if ((rc = drop_heuristic_impl(h, m_M))) return rc;
+    }
+  } else {
+    while (i < iters) {
+      // the candidate (Pi) R_i + beta_{i-1} P_{i-1} (P_{-1} = 0), whole
+      if ((rc = pass(kCGB, 0, 0, i, 0, 0, 0)) || (rc = read_sc())) return rc;
+      if (halted()) break;
+      if ((rc = drop_global_impl(h, 1, m_dir))) return rc;
+      // alpha_i from that P_i
+      if ((rc = pass(kCGB, 0, 1, i, 1, 0, i == 0)) || (rc = read_sc())) return rc;
+      if (halted()) break;
+      // M_i + alpha_i P_i, whole, then the heuristic; R_{i+1} and beta_i after it
+      if ((rc = pass(kCGA, 1, 0, i, 0, 0, 0)) || (rc = read_sc())) return rc;
+      if (sc.flags & kFlagCapacity) break;
+      if ((rc = drop_heuristic_impl(h, m_M))) return rc;
+      if ((rc = pass(kCGA, 0, 1, i, 0, 0, 0)) || (rc = read_sc())) return rc;
+      if (sc.flags & kFlagNonfinite) break;
+      i++;
+      if (sc.stop) break;
+    }
   }
-  if (i == iters && !(sc.flags & kFlagCapacity)) {
-    rc = reset_call_scalars(h);  // keep done; clear stop for the final norm
+  if (base != SPAI_CG && i == iters && !(sc.flags & kFlagCapacity)) {
+    const int f0 = sc.flags;
+    rc = reset_call_scalars(h);  // clear stop for the final norm
     if (rc) return rc;
-    if ((rc = pass(0, 0, iters, 0)) || (rc = read_sc())) return rc;
+    if ((rc = pass(base == SPAI_MR ? kMR : kLOMR, 0, 0, iters, 0, 0, 0)) || (rc = read_sc()))
+      return rc;
+    sc.flags |= f0;
   }
   if (hist && hist->resnorm)
     CK(cudaMemcpyAsync(hist->resnorm, h->d_hres, sizeof(double) * (iters + 1),

@@ -161,7 +161,7 @@ __device__ __forceinline__ int spgemm(const PassParams& p, const HashT& h, int* 
 // Column work of one pass.  part[0..nq) receives the column partials.
 // PI: the Pi-preconditioned forms (Algorithms 5, 7, 8 with Pi = diag(A)^{-1}):
 // directions from Z = Pi R, Pi-weighted coefficient inner products.
-template <typename VS, typename VC, bool PI>
+template <typename VS, typename VC, bool PI, int KIND>
 __device__ void column_work(ColCtx<VS, VC>& c, int j, double* part) {
   const PassParams& p = c.p;
   const WarpLayout& L = p.lay;
@@ -192,10 +192,10 @@ __device__ void column_work(ColCtx<VS, VC>& c, int j, double* part) {
   int* ovf = &c.overflow;
 
   // the columns this pass reads from the slabs, loaded together
-  const bool needP = (p.kind == kMR && p.do_update) || p.kind == kLOMR || p.kind == kCGA ||
-                     p.kind == kCGB;
-  const bool needZ = p.kind == kLOMR && p.do_update;
-  const bool needM = !(p.kind == kCGB && p.r_in);  // M only feeds R there
+  const bool needP = (KIND == kMR && p.do_update) || KIND == kLOMR ||
+                     (KIND == kCGA && p.do_update) || KIND == kCGB;
+  const bool needZ = KIND == kLOMR && p.do_update;
+  const bool needM = !(KIND == kCGB && p.r_in);  // M only feeds R there
   int Lm = needM ? p.Mlen[j] : 0;
   int Lp = needP ? p.Plen[j] : 0;
   const int Lz0 = needZ ? p.Zlen[j] : 0;
@@ -203,7 +203,7 @@ __device__ void column_work(ColCtx<VS, VC>& c, int j, double* part) {
   c.bytes += (unsigned long long)(Lm + Lp + Lz0) * (sizeof(int) + sizeof(VS)) +
              ((int)needM + (int)needP + (int)needZ) * sizeof(int);
 
-  if (p.kind == kSCORE) {
+  if constexpr (KIND == kSCORE) {
     // Appendix A, Eq. 430: dropping m_kj alone changes ||R||_F^2 by
     // m^2 ||A e_k||^2 + 2 m (A R)_kj; (A R)_kj from row k of A and the R table
     int cnt = spgemm(p, ha, Mr, Mv, Lm, j, Tr, Tv, lane, c.seg);
@@ -233,7 +233,7 @@ __device__ void column_work(ColCtx<VS, VC>& c, int j, double* part) {
     return;
   }
 
-  if (p.kind == kRES) {
+  if constexpr (KIND == kRES) {
     int cnt = spgemm(p, ha, Mr, Mv, Lm, j, Tr, Tv, lane, c.seg);
     int LR = table_to_list(ha, cnt, j, Rr, Rv, lane);
     hash_clear(ha, cnt, lane);
@@ -242,7 +242,7 @@ __device__ void column_work(ColCtx<VS, VC>& c, int j, double* part) {
     return;
   }
 
-  if (p.kind == kMR) {
+  if constexpr (KIND == kMR) {
     if (p.do_update) {
       CombAxpy<VC> f{c.sc->alpha};
       int Lt = warp_union(un, Mr, Mv, Lm, Pr, Pv, Lp, Tr, Tv, f, lane);
@@ -253,7 +253,7 @@ __device__ void column_work(ColCtx<VS, VC>& c, int j, double* part) {
     int LR = table_to_list(ha, cnt, j, Rr, Rv, lane);
     hash_clear(ha, cnt, lane);
     c.spg++;
-    if (!p.do_dir) {
+    if (!p.do_dir && !p.dir_store) {
       fixsum<1>(part, lane, TermSq<VC>{Rv}, LR);
       return;
     }
@@ -270,6 +270,10 @@ __device__ void column_work(ColCtx<VS, VC>& c, int j, double* part) {
       }
       store_col(c, p.Prow, p.Pval, p.Plen, j, off, Lp, Pr, Pv);
     }
+    if (!p.do_dir) {  // dir_store: the direction candidate is all this pass forms
+      fixsum<1>(part, lane, TermSq<VC>{Rv}, LR);
+      return;
+    }
     int cq = spgemm(p, ha, Pr, Pv, Lp, -1, Tr, Tv, lane, c.seg);  // table holds Q = A P
     c.spg++;
     if (PI)  // (R,R), (R,Pi Q), (Q,Pi Q)
@@ -282,7 +286,7 @@ __device__ void column_work(ColCtx<VS, VC>& c, int j, double* part) {
     return;
   }
 
-  if (p.kind == kLOMR) {
+  if constexpr (KIND == kLOMR) {
     int* Zr = c.template at<int>(L.Zr);
     VC* Zv = c.template at<VC>(L.Zv);
     int* Sr = c.template at<int>(L.Sr);
@@ -306,20 +310,28 @@ __device__ void column_work(ColCtx<VS, VC>& c, int j, double* part) {
     int LR = table_to_list(ha, cr, j, Rr, Rv, lane);
     hash_clear(ha, cr, lane);
     c.spg++;
-    if (!p.do_dir) {
+    if (!p.do_dir && !p.dir_store) {
       fixsum<1>(part, lane, TermSq<VC>{Rv}, LR);
       return;
     }
     int Lz;
-    if (PI) {  // Z = D(Pi R) (Algorithm 8)
-      int* Xr = c.template at<int>(L.zr);
-      VC* Xv = c.template at<VC>(L.zv);
-      int Lx = list_scale_pi(Rr, Rv, LR, p.pi, Xr, Xv, lane);
-      Lz = warp_select(Xr, Xv, Lx, cap, Zr, Zv, hist, tie, p.drop, ovf, lane);
+    if (p.dir_from_slab) {  // a Z chosen outside the pass (global dropping)
+      Lz = load_col(c, p.Zrow, p.Zval, off, p.Zlen[j], Zr, Zv);
     } else {
-      Lz = warp_select(Rr, Rv, LR, cap, Zr, Zv, hist, tie, p.drop, ovf, lane);
+      if (PI) {  // Z = D(Pi R) (Algorithm 8)
+        int* Xr = c.template at<int>(L.zr);
+        VC* Xv = c.template at<VC>(L.zv);
+        int Lx = list_scale_pi(Rr, Rv, LR, p.pi, Xr, Xv, lane);
+        Lz = warp_select(Xr, Xv, Lx, cap, Zr, Zv, hist, tie, p.drop, ovf, lane);
+      } else {
+        Lz = warp_select(Rr, Rv, LR, cap, Zr, Zv, hist, tie, p.drop, ovf, lane);
+      }
+      store_col(c, p.Zrow, p.Zval, p.Zlen, j, off, Lz, Zr, Zv);
     }
-    store_col(c, p.Zrow, p.Zval, p.Zlen, j, off, Lz, Zr, Zv);
+    if (!p.do_dir) {  // dir_store: the Z candidate is all this pass forms
+      fixsum<1>(part, lane, TermSq<VC>{Rv}, LR);
+      return;
+    }
     int cu = spgemm(p, ha, Zr, Zv, Lz, -1, Tr, Tv, lane, c.seg);   // table A: U = A Z
     double t3[3];
     if (PI)  // (R,R), (U,Pi U), (U,Pi R)
@@ -350,11 +362,17 @@ __device__ void column_work(ColCtx<VS, VC>& c, int j, double* part) {
     return;
   }
 
-  if (p.kind == kCGA) {
-    CombAxpy<VC> f{c.sc->alpha};
-    int Lt = warp_union(un, Mr, Mv, Lm, Pr, Pv, Lp, Tr, Tv, f, lane);
-    Lm = warp_select(Tr, Tv, Lt, cap, Mr, Mv, hist, tie, p.drop, ovf, lane);
-    store_col(c, p.Mrow, p.Mval, p.Mlen, j, off, Lm, Mr, Mv);
+  if constexpr (KIND == kCGA) {
+    if (p.do_update) {  // without it: R and beta of an M changed outside (global dropping)
+      CombAxpy<VC> f{c.sc->alpha};
+      int Lt = warp_union(un, Mr, Mv, Lm, Pr, Pv, Lp, Tr, Tv, f, lane);
+      Lm = warp_select(Tr, Tv, Lt, cap, Mr, Mv, hist, tie, p.drop, ovf, lane);
+      store_col(c, p.Mrow, p.Mval, p.Mlen, j, off, Lm, Mr, Mv);
+    }
+    if (!p.do_dir) {  // the update only: M is dropped outside before R is formed
+      part[0] = 0.0;
+      return;
+    }
     int cr = spgemm(p, ha, Mr, Mv, Lm, j, Tr, Tv, lane, c.seg);
     int LR = table_to_list(ha, cr, j, Rr, Rv, lane);
     hash_clear(ha, cr, lane);
@@ -367,8 +385,7 @@ __device__ void column_work(ColCtx<VS, VC>& c, int j, double* part) {
     return;
   }
 
-  // kCGB
-  {
+  if constexpr (KIND == kCGB) {
     int LR;
     if (p.r_in) {  // R as the previous pass A computed it
       LR = load_r(c, j, Rr, Rv);
@@ -378,18 +395,24 @@ __device__ void column_work(ColCtx<VS, VC>& c, int j, double* part) {
       hash_clear(ha, cr, lane);
       c.spg++;
     }
-    CombAxpy<VC> f{c.sc->beta};
-    int Lt;
-    if (PI) {  // P = D(Pi R + beta P) (Algorithm 7)
-      int* Zr = c.template at<int>(L.zr);
-      VC* Zv = c.template at<VC>(L.zv);
-      int Lz = list_scale_pi(Rr, Rv, LR, p.pi, Zr, Zv, lane);
-      Lt = warp_union(un, Zr, Zv, Lz, Pr, Pv, Lp, Tr, Tv, f, lane);
-    } else {
-      Lt = warp_union(un, Rr, Rv, LR, Pr, Pv, Lp, Tr, Tv, f, lane);
+    if (!p.dir_from_slab) {  // else P, loaded above, was chosen outside (global dropping)
+      CombAxpy<VC> f{c.sc->beta};
+      int Lt;
+      if (PI) {  // P = D(Pi R + beta P) (Algorithm 7)
+        int* Zr = c.template at<int>(L.zr);
+        VC* Zv = c.template at<VC>(L.zv);
+        int Lz = list_scale_pi(Rr, Rv, LR, p.pi, Zr, Zv, lane);
+        Lt = warp_union(un, Zr, Zv, Lz, Pr, Pv, Lp, Tr, Tv, f, lane);
+      } else {
+        Lt = warp_union(un, Rr, Rv, LR, Pr, Pv, Lp, Tr, Tv, f, lane);
+      }
+      Lp = warp_select(Tr, Tv, Lt, cap, Pr, Pv, hist, tie, p.drop, ovf, lane);
+      store_col(c, p.Prow, p.Pval, p.Plen, j, off, Lp, Pr, Pv);
     }
-    Lp = warp_select(Tr, Tv, Lt, cap, Pr, Pv, hist, tie, p.drop, ovf, lane);
-    store_col(c, p.Prow, p.Pval, p.Plen, j, off, Lp, Pr, Pv);
+    if (!p.do_dir) {  // the direction candidate only (global dropping follows)
+      fixsum<1>(part, lane, TermSq<VC>{Rv}, LR);
+      return;
+    }
     int cq = spgemm(p, ha, Pr, Pv, Lp, -1, Tr, Tv, lane, c.seg);  // table holds Q = A P
     c.spg++;
     if (PI)  // (R,R), (P,Q), (R,Pi R)
@@ -476,6 +499,7 @@ __device__ inline void coefficients(const PassParams& p, DevScalars* sc, double*
     return;
   }
   if (p.kind == kCGB) {
+    if (!p.do_dir) return;  // a direction candidate: no step
     // alpha = (R, R) / (P, AP), or (R, Pi R) / (P, AP) with Pi
     double rr = p.pi ? t[2] : t[0], pq = t[1];
     if (p.fresh && hist_res) hist_res[0] = __dsqrt_rn(t[0]);
@@ -495,6 +519,7 @@ __device__ inline void coefficients(const PassParams& p, DevScalars* sc, double*
     return;
   }
   // kCGA: beta = (R+, R+) / (R, R), or the Pi-weighted ratio with Pi
+  if (!p.do_dir) return;  // the update only: no R yet
   {
     double rr1 = p.pi ? t[1] : t[0];
     double beta = __ddiv_rn(rr1, sc->rr);
@@ -513,7 +538,9 @@ __device__ inline void coefficients(const PassParams& p, DevScalars* sc, double*
   }
 }
 
-template <typename VS, typename VC, bool PI>
+// One instantiation per pass kind keeps each kernel's code small: with all
+// kinds behind a runtime switch the instruction cache missed often.
+template <typename VS, typename VC, bool PI, int KIND>
 __global__ void __launch_bounds__(256, sizeof(VC) == 4 ? 4 : 3) colpass_kernel(const PassParams p) {
   extern __shared__ __align__(16) char smem[];
   const int seg = p.nseg ? p.seg_of_col[(long long)blockIdx.x * p.B] : -1;
@@ -521,7 +548,7 @@ __global__ void __launch_bounds__(256, sizeof(VC) == 4 ? 4 : 3) colpass_kernel(c
   if (sc->stop) return;  // set by an earlier pass for this matrix
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
-  const int nq = p.do_dir ? pass_nq(p.kind, PI) : 1;
+  const int nq = p.do_dir ? pass_nq(KIND, PI) : 1;
   double* part = (double*)(smem + p.part_off);  // [nq][B]
   double* red = (double*)(smem + p.red_off);    // reduction scratch (>= 1024 doubles)
   ColCtx<VS, VC> c(p, smem + warp * p.lay.bytes, lane, sc, seg);
@@ -530,11 +557,11 @@ __global__ void __launch_bounds__(256, sizeof(VC) == 4 ? 4 : 3) colpass_kernel(c
     h0.key = c.template at<int>(p.lay.hk);
     h0.H = p.lay.H;
     hash_clear_all(h0, lane);
-    if (p.kind == kLOMR) {
+    if (KIND == kLOMR) {
       h0.key = c.template at<int>(p.lay.gk);
       hash_clear_all(h0, lane);
     }
-    if (p.kind != kRES && p.kind != kSCORE) {
+    if (KIND != kRES && KIND != kSCORE) {
       h0.key = c.template at<int>(p.lay.uk);
       h0.H = p.lay.HU;
       hash_clear_all(h0, lane);
@@ -545,7 +572,7 @@ __global__ void __launch_bounds__(256, sizeof(VC) == 4 ? 4 : 3) colpass_kernel(c
   for (int cc = warp; cc < B; cc += p.NW) {
     long long j = j0 + cc;
     double pr[6] = {0, 0, 0, 0, 0, 0};
-    if (j < p.n) column_work<VS, VC, PI>(c, (int)j, pr);
+    if (j < p.n) column_work<VS, VC, PI, KIND>(c, (int)j, pr);
     if (lane == 0)
       for (int q = 0; q < nq; q++) part[q * B + cc] = pr[q];
   }

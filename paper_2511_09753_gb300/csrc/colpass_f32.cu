@@ -3,6 +3,7 @@
 
 namespace spai {
 cudaError_t launch_colpass_f32(const PassParams& p, int grid, int block, size_t smem, cudaStream_t st) {
-  return launch_colpass<float, float>(p, grid, block, smem, st);
+  return launch_colpass<float, float, false, kMR, kLOMR, kCGA, kCGB, kRES, kSCORE>(p, grid, block,
+                                                                              smem, st);
 }
 }  // namespace spai

@@ -5,6 +5,6 @@
 namespace spai {
 cudaError_t launch_colpass_pi_f32(const PassParams& p, int grid, int block, size_t smem,
                                    cudaStream_t st) {
-  return launch_colpass<float, float, true>(p, grid, block, smem, st);
+  return launch_colpass<float, float, true, kMR, kLOMR, kCGA, kCGB>(p, grid, block, smem, st);
 }
 }  // namespace spai

@@ -5,6 +5,6 @@
 namespace spai {
 cudaError_t launch_colpass_pi_f64(const PassParams& p, int grid, int block, size_t smem,
                                    cudaStream_t st) {
-  return launch_colpass<double, double, true>(p, grid, block, smem, st);
+  return launch_colpass<double, double, true, kMR, kLOMR, kCGA, kCGB>(p, grid, block, smem, st);
 }
 }  // namespace spai

@@ -33,7 +33,7 @@ enum : int {
 enum PassKind : int {
   kMR = 0,     // [update M with alpha] then R, P = D(R), Q = A P; partials rr, rq, qq
   kLOMR = 1,   // [S, P = D(S), M = D(M+S)] then R, Z = D(R), U = A Z, V = A P; 6 partials
-  kCGA = 2,    // M = D(M + alpha P); R; partial rr
+  kCGA = 2,    // [M = D(M + alpha P)]; R; partial rr
   kCGB = 3,    // R; P = D(R + beta P); Q = A P; partials rr, pq
   kRES = 4,    // R = I - A M in FP64; partial rr
   kSCORE = 5,  // R = I - A M, then the Appendix A drop score of every entry of M
@@ -64,7 +64,8 @@ struct PassParams {
   int capmax, pmax, lmax, tmax;
   int kind;
   int do_update, do_dir, drop;
-  int dir_from_slab;     // MR: take the direction P stored in its slab instead of selecting it from R
+  int dir_from_slab;     // take the direction (MR, CG: P; LOMR: Z) stored in its slab instead of forming it
+  int dir_store;         // MR, LOMR with do_dir = 0: still form the direction (P; Z) from R and store it
   int iter;          // history slot of this pass
   int fresh;         // CG: first B pass of a call (writes history[0])
   const long long* off;  // slab offsets (per column)

@@ -350,7 +350,8 @@ class Spai:
                     "spai_drop_global")
 
     def run_global(self, method, iters, m_dir, m_M):
-        """MR or MR_SPD with global dropping inside every iteration (see spai_run_global)."""
+        """MR, LOMR or CG (or their Pi forms) with global dropping inside every
+        iteration (see spai_run_global)."""
         m = METHODS[method] if isinstance(method, str) else int(method)
         res = np.full(iters + 1, np.nan)
         coef = np.full(2 * max(iters, 1), np.nan)

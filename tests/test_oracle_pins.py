@@ -699,3 +699,84 @@ def test_global_mr_flow_step_is_the_line_minimiser_of_the_thresholded_direction(
         M1 = dense_from_csc(n, *out["M"])
         np.testing.assert_allclose(out["resnorm"][-1], np.linalg.norm(np.eye(n) - A @ M1),
                                    rtol=1e-12)
+
+
+def _top(X, m):
+    """Brute-force global hard threshold: the m entries of largest |x|
+    (ties: smaller column, then smaller row)."""
+    n = X.shape[0]
+    ent = sorted((-abs(X[r, j]), j, r) for j in range(n) for r in range(n) if X[r, j] != 0)
+    P = np.zeros_like(X)
+    for _, j, r in ent[:m]:
+        P[r, j] = X[r, j]
+    return P
+
+
+def test_global_lomr_flow_steps_are_the_2d_minimisers():
+    """LOMR with global dropping: (delta_0, gamma_0) = (the line minimiser of
+    ||R_0 - d A Z_0||_W, 0) for Z_0 the brute-force top-m_dir of (Pi) R_0, and
+    (delta_1, gamma_1) minimise ||R_1 - A (d Z_1 + g P_0)||_W (Theorem 3) with
+    P_0 the top-m_dir of delta_0 Z_0 and R_1 the dense residual of the
+    returned M_1; W = I (LOMR) or Pi (LOMR_SPD)."""
+    from oracle import dropping as D
+    n, rp, ci, v = I.varcoef_grid((5, 6), seed=4)
+    A = I.csr_to_dense(n, rp, ci, v)
+    d = np.diag(A)
+    R0 = np.eye(n) - A @ np.diag(1.0 / d)
+    m_dir, m_M = 2 * len(v) // 3, 10 ** 9
+    for use_pi in (False, True):
+        Wd = 1.0 / d if use_pi else np.ones(n)
+        ip = lambda X, Y: np.sum(X * (Wd[:, None] * Y))
+        Z0 = _top(np.diag(1.0 / d) @ R0 if use_pi else R0, m_dir)
+        U = A @ Z0
+        d0 = ip(U, R0) / ip(U, U)
+        one = D.run_global_lomr(n, rp, ci, v, 1, m_dir, m_M, use_pi=use_pi)
+        assert one["done"] == 1
+        assert abs(one["coef"][0, 0] - d0) <= 1e-12 * abs(d0) and one["coef"][0, 1] == 0.0
+        M1 = dense_from_csc(n, *one["M"])
+        # M_1 = the heuristic (here: symmetrisation) of M_0 + S_0, S_0 = delta_0 Z_0
+        T = np.diag(1.0 / d) + d0 * Z0
+        np.testing.assert_allclose(M1, 0.5 * (T + T.T), rtol=0, atol=1e-14)
+        R1 = np.eye(n) - A @ M1
+        np.testing.assert_allclose(one["resnorm"][-1], np.linalg.norm(R1), rtol=1e-12)
+        P0 = _top(d0 * Z0, m_dir)
+        Z1 = _top(np.diag(1.0 / d) @ R1 if use_pi else R1, m_dir)
+        U, V = A @ Z1, A @ P0
+        G = np.array([[ip(U, U), ip(U, V)], [ip(U, V), ip(V, V)]])
+        dg = np.linalg.solve(G, [ip(U, R1), ip(V, R1)])
+        two = D.run_global_lomr(n, rp, ci, v, 2, m_dir, m_M, use_pi=use_pi)
+        assert two["done"] == 2
+        np.testing.assert_allclose(two["coef"][1], dg, rtol=1e-9)
+
+
+def test_global_cg_flow_coefficients_match_dense_cg():
+    """CG with global dropping: alpha_0 = (R_0, Pi R_0) / (P_0, A P_0) for P_0
+    the top-m_dir of (Pi) R_0; beta_0 = (R_1, Pi R_1) / (R_0, Pi R_0) with R_1
+    the dense residual of the returned M_1; alpha_1 from P_1 = the top-m_dir
+    of (Pi) R_1 + beta_0 P_0 (Algorithms 3 and 7; Pi = I for plain CG)."""
+    from oracle import dropping as D
+    n, rp, ci, v = I.varcoef_grid((5, 6), seed=4)
+    A = I.csr_to_dense(n, rp, ci, v)
+    d = np.diag(A)
+    R0 = np.eye(n) - A @ np.diag(1.0 / d)
+    m_dir, m_M = 2 * len(v) // 3, 10 ** 9
+    for use_pi in (False, True):
+        Pi = np.diag(1.0 / d) if use_pi else np.eye(n)
+        P0 = _top(Pi @ R0, m_dir)
+        rz0 = np.sum(R0 * (Pi @ R0))
+        a0 = rz0 / np.sum(P0 * (A @ P0))
+        one = D.run_global_cg(n, rp, ci, v, 1, m_dir, m_M, use_pi=use_pi)
+        assert one["done"] == 1
+        M1 = dense_from_csc(n, *one["M"])
+        T = np.diag(1.0 / d) + a0 * P0  # M_1 = the heuristic (symmetrisation) of M_0 + alpha_0 P_0
+        np.testing.assert_allclose(M1, 0.5 * (T + T.T), rtol=0, atol=1e-14)
+        R1 = np.eye(n) - A @ M1
+        rz1 = np.sum(R1 * (Pi @ R1))
+        np.testing.assert_allclose(one["coef"][0], [a0, rz1 / rz0], rtol=1e-12)
+        np.testing.assert_allclose(one["resnorm"], [np.linalg.norm(R0), np.linalg.norm(R1)],
+                                   rtol=1e-12)
+        P1 = _top(Pi @ R1 + (rz1 / rz0) * P0, m_dir)
+        a1 = rz1 / np.sum(P1 * (A @ P1))
+        two = D.run_global_cg(n, rp, ci, v, 2, m_dir, m_M, use_pi=use_pi)
+        assert two["done"] == 2
+        np.testing.assert_allclose(two["coef"][1, 0], a1, rtol=1e-10)
