@@ -313,7 +313,7 @@ def run_ours(args):
 # --profile mr|lomr|cg cases on this workload, weighted by the launch mix of
 # one step (51 MR, 51 LOMR, 50 + 50 CG passes); None until taken on the
 # current kernel.
-COLPASS_TRAFFIC_BYTES = None
+COLPASS_TRAFFIC_BYTES = 216.0e6
 
 BATCH_ITERS = 30
 BATCH_RHS = 32
