@@ -2288,11 +2288,13 @@ int spai_run_global(spai_handle h, int method, int iters, int64_t m_dir, int64_t
       if (sc.stop) break;
     }
   }
-  if (base != SPAI_CG && i == iters && !(sc.flags & kFlagCapacity)) {
+  // MR and LOMR end with the norm of the last M; CG's last pass A recorded
+  // it, except when no iteration was asked for
+  if ((base != SPAI_CG || iters == 0) && i == iters && !(sc.flags & kFlagCapacity)) {
     const int f0 = sc.flags;
     rc = reset_call_scalars(h);  // clear stop for the final norm
     if (rc) return rc;
-    if ((rc = pass(base == SPAI_MR ? kMR : kLOMR, 0, 0, iters, 0, 0, 0)) || (rc = read_sc()))
+    if ((rc = pass(base == SPAI_LOMR ? kLOMR : kMR, 0, 0, iters, 0, 0, 0)) || (rc = read_sc()))
       return rc;
     sc.flags |= f0;
   }

@@ -51,3 +51,16 @@ def test_run_global_then_plain_run_continues_from_the_dropped_m():
     rg, ro = g.run("cg", 3), o.run("cg", 3)
     np.testing.assert_array_equal(rg["resnorm"], ro["resnorm"])
     assert all(np.array_equal(a, b) for a, b in zip(g.get_M(), o.get_M()))
+
+
+@pytest.mark.parametrize("method", ["mr", "lomr", "cg_pi"])
+def test_run_global_zero_iterations_records_the_initial_residual(method):
+    import oracle as O
+    from paper_2511_09753_gb300 import spai
+    n, rp, ci, v = I.varcoef_grid((9, 11), seed=5)
+    g = spai.Spai(n, rp, ci, v, prec="fp64", cap_factor=12.0)
+    r = g.run_global(method, 0, 2 * len(v), int(1.5 * len(v)))
+    o = O.Oracle(n, rp, ci, v, cap_factor=12.0)
+    assert r["done"] == 0
+    assert r["resnorm"][0] == o.run("mr", 0)["resnorm"][0]  # ||I - A M_0||_F
+    assert all(np.array_equal(a, b) for a, b in zip(g.get_M(), o.get_M()))
