@@ -51,6 +51,30 @@ def test_method_parity(case, method, prec):
     assert g.residual_norm() == o.residual_norm()
 
 
+WIDE = {  # columns longer than 32 entries: the general diagonal-slot SpGEMM
+    "varcoef3d_12_cap6": (lambda: I.varcoef_3d_7pt(12, seed=7), 6.0),  # 7 slots, cap 42
+    "aniso9_30_cap4": (lambda: I.aniso_2d_9pt(30), 4.0),               # 9 slots, cap 36
+}
+
+
+@pytest.mark.parametrize("case", list(WIDE))
+@pytest.mark.parametrize("method", ["mr", "lomr", "cg"])
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_wide_columns_parity(case, method, prec):
+    spai = _spai()
+    make, capf = WIDE[case]
+    n, rp, ci, v = make()
+    g = spai.Spai(n, rp, ci, v, prec=prec, cap_factor=capf)
+    o = O.Oracle(n, rp, ci, v, mixed=(prec == "mixed"), cap_factor=capf)
+    rg, ro = g.run(method, 10), o.run(method, 10)
+    assert rg["done"] == ro["done"]
+    np.testing.assert_array_equal(rg["resnorm"], ro["resnorm"])
+    np.testing.assert_array_equal(rg["coef"][:ro["done"]], ro["coef"][:ro["done"]])
+    gm = g.get_M()
+    assert _same(gm, o.get_M())
+    assert np.diff(gm[0]).max() > 32  # the wide path was taken
+
+
 @pytest.mark.parametrize("method", ["mr", "lomr", "cg"])
 def test_mixed_within_tolerance_of_fp64_oracle(method):
     spai = _spai()
