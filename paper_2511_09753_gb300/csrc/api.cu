@@ -776,29 +776,14 @@ int create_impl(spai_handle* out, int64_t n, int64_t nnz, const int32_t* rp, con
   h->magicW = (uint32_t)((((uint64_t)1 << 32) + W - 1) / W);
   h->capmax = capmax;
   h->slab_total = off[n];
-  std::vector<int> ecol((size_t)n * W);
-  std::vector<double> e64((size_t)n * W);
-  std::vector<float> e32;
+  // A's ELL and diagonal-slot copies are built on the device from its CSR
+  // (launch_build_ell / launch_build_dia below); the host finds the diagonal
+  // and the slot offsets
   std::vector<double> diag(n);
-  for (int64_t i = 0; i < n; i++) {
-    int t = 0;
-    for (int64_t e = rp[i]; e < rp[i + 1]; e++, t++) {
-      ecol[(size_t)i * W + t] = ci[e];
-      e64[(size_t)i * W + t] = va[e];
+  for (int64_t i = 0; i < n; i++)
+    for (int64_t e = rp[i]; e < rp[i + 1]; e++)
       if (ci[e] == i) diag[i] = va[e];
-    }
-    for (; t < W; t++) {
-      ecol[(size_t)i * W + t] = -1;
-      e64[(size_t)i * W + t] = 0.0;
-    }
-  }
-  if (h->prec == SPAI_MIXED) {
-    e32.resize(e64.size());
-    for (size_t k = 0; k < e64.size(); k++) e32[k] = (float)e64[k];
-  }
   // diagonal-slot layout when A has at most 32 distinct offsets col - row
-  std::vector<double> d64;
-  std::vector<float> d32;
   std::vector<int> seg_D, seg_doff;
   if (bd) {
     // per-matrix diagonal slots; every matrix must have at most 32
@@ -837,21 +822,6 @@ int create_impl(spai_handle* out, int64_t n, int64_t nnz, const int32_t* rp, con
       h->D = Dmax;
       h->Dp = Dmax;
       for (int s2 = 0; s2 < 32; s2++) h->dia_off[s2] = 0;
-      d64.assign((size_t)n * h->Dp, 0.0);
-      for (int64_t i = 0; i < n; i++) {
-        const int m = seg_of_col[i];
-        const int* so = &seg_doff[(size_t)m * 32];
-        int s2 = 0;
-        for (int64_t e = rp[i]; e < rp[i + 1]; e++) {  // columns, hence slots, ascend
-          const int o = (int)((long long)ci[e] - i);
-          while (so[s2] < o) s2++;
-          d64[(size_t)i * h->Dp + s2] = va[e];
-        }
-      }
-      if (h->prec == SPAI_MIXED) {
-        d32.resize(d64.size());
-        for (size_t k = 0; k < d64.size(); k++) d32[k] = (float)d64[k];
-      }
     } else {
       seg_D.clear();
       seg_doff.clear();
@@ -883,20 +853,6 @@ int create_impl(spai_handle* out, int64_t n, int64_t nnz, const int32_t* rp, con
       h->D = (int)offs.size();
       h->Dp = h->D;
       for (int s2 = 0; s2 < h->D; s2++) h->dia_off[s2] = (int)offs[s2];
-      d64.assign((size_t)n * h->Dp, 0.0);
-      // columns ascend within a row, so the slots of a row ascend too
-      for (int64_t i = 0; i < n; i++) {
-        int s2 = 0;
-        for (int64_t e = rp[i]; e < rp[i + 1]; e++) {
-          const long long o = (long long)ci[e] - i;
-          while (offs[s2] < o) s2++;
-          d64[(size_t)i * h->Dp + s2] = va[e];
-        }
-      }
-      if (h->prec == SPAI_MIXED) {
-        d32.resize(d64.size());
-        for (size_t k = 0; k < d64.size(); k++) d32[k] = (float)d64[k];
-      }
     }
   }
   int dev = 0;
@@ -1011,20 +967,6 @@ int create_impl(spai_handle* out, int64_t n, int64_t nnz, const int32_t* rp, con
   std::vector<double> piv(n);
   for (int64_t i = 0; i < n; i++) piv[i] = 1.0 / diag[i];
   ok &= cudaMemcpyAsync(h->d_pi, piv.data(), sizeof(double) * n, cudaMemcpyHostToDevice, st) == 0;
-  ok &= cudaMemcpyAsync(h->d_ell_col, ecol.data(), sizeof(int) * ecol.size(), cudaMemcpyHostToDevice,
-                        st) == 0;
-  ok &= cudaMemcpyAsync(h->d_ell64, e64.data(), sizeof(double) * e64.size(), cudaMemcpyHostToDevice,
-                        st) == 0;
-  if (h->prec == SPAI_MIXED)
-    ok &= cudaMemcpyAsync(h->d_ell32, e32.data(), sizeof(float) * e32.size(),
-                          cudaMemcpyHostToDevice, st) == 0;
-  if (h->dia) {
-    ok &= cudaMemcpyAsync(h->d_dia64, d64.data(), sizeof(double) * d64.size(),
-                          cudaMemcpyHostToDevice, st) == 0;
-    if (h->prec == SPAI_MIXED)
-      ok &= cudaMemcpyAsync(h->d_dia32, d32.data(), sizeof(float) * d32.size(),
-                            cudaMemcpyHostToDevice, st) == 0;
-  }
   ok &= cudaMemcpyAsync(h->d_off, off.data(), sizeof(long long) * (n + 1), cudaMemcpyHostToDevice,
                         st) == 0;
   ok &= cudaMemcpyAsync(h->d_cap, cap.data(), sizeof(int) * n, cudaMemcpyHostToDevice, st) == 0;
@@ -1056,6 +998,14 @@ int create_impl(spai_handle* out, int64_t n, int64_t nnz, const int32_t* rp, con
   }
   ok &= cudaMemsetAsync(h->d_cnt1, 0, sizeof(unsigned) * h->red_ng, st) == 0;
   ok &= cudaMemsetAsync(h->d_cnt2, 0, sizeof(unsigned), st) == 0;
+  ok &= launch_build_ell((int)n, W, h->d_rowptr, h->d_colind, h->d_vals, h->d_ell_col, h->d_ell64,
+                         h->prec == SPAI_MIXED ? h->d_ell32 : nullptr, st) == 0;
+  if (h->dia)
+    ok &= launch_build_dia((int)n, h->Dp, h->d_rowptr, h->d_colind, h->d_vals,
+                           bd ? nullptr : h->dia_off, bd ? h->d_seg_of_col : nullptr,
+                           bd ? h->d_seg_doff : nullptr, bd ? h->d_seg_D : nullptr, h->d_dia64,
+                           h->prec == SPAI_MIXED ? h->d_dia32 : nullptr, st) == 0;
+  h->other_launches += h->dia ? 2 : 1;
   ok &= launch_init_slab(h->prec, (int)n, h->d_off, h->d_diag, h->d_Mrow, h->d_Mval, h->d_Mlen,
                          h->d_Plen, h->d_Zlen, st) == 0;
   ok &= cudaStreamSynchronize(st) == 0;

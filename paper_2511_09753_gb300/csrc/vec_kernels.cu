@@ -235,6 +235,67 @@ cudaError_t launch_init_slab(int prec, int n, const long long* off, const double
   return cudaGetLastError();
 }
 
+// A's ELL layout from its CSR: row i's entries in CSR order, then padding
+// column -1 with value 0; an FP32 copy of the values when v32 is given
+__global__ void k_build_ell(int n, int W, const int* rp, const int* ci, const double* v,
+                            int* ecol, double* e64, float* e32) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int e0 = rp[i], len = rp[i + 1] - e0;
+  for (int t = 0; t < W; t++) {
+    const long long d = i * W + t;
+    const int c = t < len ? ci[e0 + t] : -1;
+    const double x = t < len ? v[e0 + t] : 0.0;
+    ecol[d] = c;
+    e64[d] = x;
+    if (e32) e32[d] = __double2float_rn(x);
+  }
+}
+
+// A's diagonal slots: value of row i at slot s is a_{i, i + off_s}, 0 where
+// row i has no such entry.  The offsets of row i's matrix are doff (single
+// matrix) or seg_doff[seg_of_col[i]] (batch), ascending, and every entry's
+// offset is among them; columns ascend in a row, so slots do too.
+struct DiaOffs {
+  int off[32];
+};
+__global__ void k_build_dia(int n, int Dp, const int* rp, const int* ci, const double* v, DiaOffs doff,
+                            const int* seg_of_col, const int* seg_doff, const int* seg_D,
+                            double* d64, float* d32) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int m = seg_of_col ? seg_of_col[i] : -1;
+  const int D = m >= 0 ? seg_D[m] : Dp;
+  for (int s = 0; s < Dp; s++) {
+    d64[i * Dp + s] = 0.0;
+    if (d32) d32[i * Dp + s] = 0.0f;
+  }
+  int s = 0;
+  for (int e = rp[i]; e < rp[i + 1]; e++) {
+    const int o = ci[e] - (int)i;
+    while (s < D && (m >= 0 ? seg_doff[m * 32 + s] : doff.off[s]) < o) s++;
+    if (s >= D) return;  // not reached: every offset was found on the host
+    d64[i * Dp + s] = v[e];
+    if (d32) d32[i * Dp + s] = __double2float_rn(v[e]);
+  }
+}
+
+cudaError_t launch_build_ell(int n, int W, const int* rp, const int* ci, const double* v, int* ecol,
+                             double* e64, float* e32, cudaStream_t st) {
+  k_build_ell<<<(n + 255) / 256, 256, 0, st>>>(n, W, rp, ci, v, ecol, e64, e32);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_build_dia(int n, int Dp, const int* rp, const int* ci, const double* v,
+                             const int* doff, const int* seg_of_col, const int* seg_doff,
+                             const int* seg_D, double* d64, float* d32, cudaStream_t st) {
+  DiaOffs o;
+  for (int s = 0; s < 32; s++) o.off[s] = doff ? doff[s] : 0;
+  k_build_dia<<<(n + 255) / 256, 256, 0, st>>>(n, Dp, rp, ci, v, o, seg_of_col, seg_doff, seg_D,
+                                               d64, d32);
+  return cudaGetLastError();
+}
+
 // per-matrix scalars of a batched handle at the start of a call
 __global__ void k_seg_reset(DevScalars* sc, int nseg, int fresh) {
   int m = blockIdx.x * blockDim.x + threadIdx.x;
