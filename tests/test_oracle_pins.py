@@ -780,3 +780,78 @@ def test_global_cg_flow_coefficients_match_dense_cg():
         two = D.run_global_cg(n, rp, ci, v, 2, m_dir, m_M, use_pi=use_pi)
         assert two["done"] == 2
         np.testing.assert_allclose(two["coef"][1, 0], a1, rtol=1e-10)
+
+
+# ---------------------------------------- exact arithmetic of the products
+
+def _round_f32(q):
+    """The float32 nearest to the rational q (ties to even), as a float."""
+    from fractions import Fraction
+    if q == 0:
+        return 0.0
+    neg, q = q < 0, abs(q)
+    e = q.numerator.bit_length() - q.denominator.bit_length()
+    if Fraction(2) ** e > q:
+        e -= 1
+    qe = max(e - 23, -149)  # 24-bit significand; subnormal quantum 2^-149
+    scaled = q / Fraction(2) ** qe
+    k = scaled.numerator // scaled.denominator
+    rem = scaled - k
+    if rem > Fraction(1, 2) or (rem == Fraction(1, 2) and k % 2 == 1):
+        k += 1
+    x = float(Fraction(k) * Fraction(2) ** qe)
+    return -x if neg else x
+
+
+def test_product_column_is_the_exact_rounded_fma_chain():
+    """A X_j, both precisions, against an independent construction: each
+    fma of the ascending-k chain acc = fma(a_rk, x_k, acc) evaluated exactly
+    on rationals and rounded once to FP64 or FP32 (reading 10; the mixed
+    path rounds A's values to FP32 first, reading 11)."""
+    from fractions import Fraction
+    n, rp, ci, v = I.varcoef_grid((7, 8), seed=21)
+    rng = np.random.default_rng(3)
+    for mixed in (False, True):
+        o = O.Oracle(n, rp, ci, v, mixed=mixed, cap_factor=4.0)
+        av = [float(np.float32(x)) for x in v] if mixed else list(v)
+        rnd = _round_f32 if mixed else (lambda q: float(q))
+        for trial in range(6):
+            rows = np.sort(rng.choice(n, size=9, replace=False))
+            vals = rng.standard_normal(9) * 10.0 ** rng.integers(-3, 4, 9)
+            if mixed:
+                vals = vals.astype(np.float32).astype(np.float64)
+            want = {}
+            for k, x in zip(rows.tolist(), vals.tolist()):  # ascending k
+                for q in range(rp[k], rp[k + 1]):
+                    r = int(ci[q])
+                    want[r] = rnd(Fraction(av[q]) * Fraction(x) + Fraction(want.get(r, 0.0)))
+            gr, gv = o.product_column(rows, vals)
+            exp = sorted((r, x) for r, x in want.items() if x != 0.0)
+            assert gr.tolist() == [r for r, _ in exp]
+            assert gv.tolist() == [x for _, x in exp]
+
+
+def test_column_residual_is_exact_chain_then_one_rounding():
+    """R_j = e_j - A M_j: the exact-rational fma chain of A M_j, then 1 - s on
+    the diagonal rounded once to the value type and -s elsewhere, exact
+    zeros removed (reading 10), for the stored M after a few MR steps."""
+    from fractions import Fraction
+    n, rp, ci, v = I.varcoef_grid((6, 7), seed=22)
+    for mixed in (False, True):
+        o = O.Oracle(n, rp, ci, v, mixed=mixed, cap_factor=3.0)
+        o.run("mr", 3)
+        cp, ri, mv = o.get_M()
+        av = [float(np.float32(x)) for x in v] if mixed else list(v)
+        rnd = _round_f32 if mixed else (lambda q: float(q))
+        for j in range(0, n, 5):
+            acc = {}
+            for k, x in zip(ri[cp[j]:cp[j + 1]].tolist(), mv[cp[j]:cp[j + 1]].tolist()):
+                for q in range(rp[k], rp[k + 1]):
+                    r = int(ci[q])
+                    acc[r] = rnd(Fraction(av[q]) * Fraction(x) + Fraction(acc.get(r, 0.0)))
+            want = {r: -x for r, x in acc.items()}
+            want[j] = rnd(Fraction(1) - Fraction(acc.get(j, 0.0)))
+            exp = sorted((r, x) for r, x in want.items() if x != 0.0)
+            gr, gv = o.column_residual(j)
+            assert gr.tolist() == [r for r, _ in exp]
+            assert gv.tolist() == [x for _, x in exp]
