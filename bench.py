@@ -600,6 +600,23 @@ def profile_bpcg(prec):
     print(json.dumps({"profile": "bpcg", "prec": prec, "iters_max": int(p["iters"].max())}))
 
 
+def profile_pcg(prec):
+    """Launch sequence for ncu captures of the one-vector PCG kernels: the
+    bench workload, 50 MR iterations (mixed values), then 64 PCG iterations
+    with the symmetric part of M (products in `prec`), as in the bench step."""
+    import torch
+
+    from paper_2511_09753_gb300 import inputs as I
+    from paper_2511_09753_gb300.spai import PREC_SPAI_SYM, Spai
+    n, rp, ci, v = I.varcoef_3d_7pt(64, sigma=1.5, ell=8.0, seed=0)
+    g = Spai(n, rp, ci, v, prec="mixed", cap_factor=CAP)
+    g.set_pcg_prec(prec)
+    g.run("mr", ITERS)
+    p = g.pcg(I.rhs_uniform(n, 0), rtol=1e-8, maxit=64, precond=PREC_SPAI_SYM)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile": "pcg", "prec": prec, "iters": int(p["iters"])}))
+
+
 def cpu_baseline(sample_iters=1):
     """The CPU oracle (single thread) on a bounded sample of the workload:
     `sample_iters` MR iterations on the full operator (mixed arithmetic)."""
@@ -657,15 +674,18 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline sample")
-    ap.add_argument("--profile", choices=list(METHODS) + ["bpcg"], default=None,
-                    help="profiling case for ncu: 3 iterations of one method on the workload, "
-                         "or (bpcg) one block PCG solve of the 64-matrix batch")
+    ap.add_argument("--profile", choices=list(METHODS) + ["pcg", "bpcg"], default=None,
+                    help="profiling case for ncu: 10 iterations of one method on the workload, "
+                         "(pcg) 64 iterations of its vector PCG, or (bpcg) one block PCG "
+                         "solve of the 64-matrix batch")
     ap.add_argument("--prec", choices=["mixed", "fp64"], default="mixed")
     ap.add_argument("--workload", choices=[WORKLOAD, "batch64", "aniso1024", "fpmr"],
                     default=WORKLOAD)
     args = ap.parse_args()
     if args.profile == "bpcg":
         profile_bpcg(args.prec)
+    elif args.profile == "pcg":
+        profile_pcg(args.prec)
     elif args.profile:
         profile_case(args.profile, args.prec)
     elif args.workload == "batch64" and args.impl == "ours":
