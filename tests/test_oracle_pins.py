@@ -855,3 +855,57 @@ def test_column_residual_is_exact_chain_then_one_rounding():
             gr, gv = o.column_residual(j)
             assert gr.tolist() == [r for r, _ in exp]
             assert gv.tolist() == [x for _, x in exp]
+
+
+def _cols(X):
+    cp, ri, va = X
+    return [dict(zip(ri[cp[j]:cp[j + 1]].tolist(), va[cp[j]:cp[j + 1]].tolist()))
+            for j in range(len(cp) - 1)]
+
+
+def test_update_combinations_are_single_roundings():
+    """The iterate updates of reading 10, checked entry by entry against exact
+    rational arithmetic: MR and CG M+ = fl(m + alpha p); CG P+ = fl(r + beta p);
+    LOMR S = fl(delta z + fl(gamma p)), P = S, M+ = fl(m + s), each rounded
+    once to FP64 (then once more to FP32 on the mixed path), exact zeros
+    removed (no dropping here, so nothing else changes the entries)."""
+    from fractions import Fraction
+    n, rp, ci, v = I.varcoef_grid((6, 5), seed=23)
+
+    def f64(q):
+        return float(q)
+
+    for mixed in (False, True):
+        rv = (lambda x: float(np.float32(x))) if mixed else (lambda x: x)
+
+        def comb(c, y, x):  # fl(x + c y), one FP64 rounding, then the value type
+            return rv(f64(Fraction(c) * Fraction(y) + Fraction(x)))
+
+        for method in ("mr", "cg", "lomr"):
+            o = O.Oracle(n, rp, ci, v, mixed=mixed, cap_factor=float(n))
+            o.run(method, 1, drop=O.DROP_NONE)
+            M1, P1 = _cols(o.get(0)), _cols(o.get(1))
+            r = o.run(method, 1, drop=O.DROP_NONE)  # continues the recurrence
+            M2, P2, Z2 = _cols(o.get(0)), _cols(o.get(1)), _cols(o.get(2))
+            c0, c1 = r["coef"][0]
+            for j in range(n):
+                if method == "mr":  # M2 = M1 + alpha_1 P_1 (P_1 = R_1 now in P2)
+                    want = {k: comb(c0, P2[j].get(k, 0.0), M1[j].get(k, 0.0))
+                            for k in set(M1[j]) | set(P2[j])}
+                    got = M2[j]
+                elif method == "cg":  # M2 = M1 + alpha_1 P_1 with the P of the first call
+                    want = {k: comb(c0, P1[j].get(k, 0.0), M1[j].get(k, 0.0))
+                            for k in set(M1[j]) | set(P1[j])}
+                    got = M2[j]
+                else:  # LOMR: S_1 = delta Z_1 + gamma P_0 (P1), P2 = S_1, M2 = M1 + S_1
+                    S = {}
+                    for k in set(Z2[j]) | set(P1[j]):
+                        g = c1 * P1[j].get(k, 0.0)  # FP64 product, rounded
+                        S[k] = rv(f64(Fraction(c0) * Fraction(Z2[j].get(k, 0.0)) + Fraction(g)))
+                    S = {k: x for k, x in S.items() if x != 0.0}
+                    assert P2[j] == S
+                    want = {k: rv(f64(Fraction(M1[j].get(k, 0.0)) + Fraction(S.get(k, 0.0))))
+                            for k in set(M1[j]) | set(S)}
+                    got = M2[j]
+                want = {k: x for k, x in want.items() if x != 0.0}
+                assert got == want, (method, mixed, j)
