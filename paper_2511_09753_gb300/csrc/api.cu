@@ -1166,7 +1166,9 @@ int spai_run(spai_handle h, int method, int iters, int drop_rule, spai_history* 
   const int drop = drop_rule == SPAI_DROP_TOPK_COL ? 1 : 0;
   // CG: pass A keeps R_{i+1} for pass B of the next iteration, which then
   // reads it instead of repeating the product (the same values)
-  const bool keep_r = base == SPAI_CG && iters > 1;
+  // (the slab is an optimisation: without device memory for it, pass B
+  // recomputes R as before)
+  bool keep_r = base == SPAI_CG && iters > 1;
   if (keep_r && !h->d_Rrow) {
     const size_t cnt = (size_t)h->n * ((size_t)h->capmax * h->W + 1);
     const size_t vb = h->prec == SPAI_FP64 ? 8 : 4;
@@ -1177,7 +1179,8 @@ int spai_run(spai_handle h, int method, int iters, int drop_rule, spai_history* 
       dfree(h->d_Rrow);
       dfree(h->d_Rval);
       dfree(h->d_Rlen);
-      return rc;
+      keep_r = false;
+      rc = SPAI_OK;
     }
   }
   auto pass = [&](int kind, int upd, int dir, int iter, int fresh_b, int r_in = 0,
