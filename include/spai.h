@@ -192,6 +192,9 @@ int spai_run(spai_handle h, int method, int iters, int drop_rule, spai_history *
  * recurrence.  *best_ms (may be NULL): the chosen shape's time per
  * iteration. */
 int spai_autotune(spai_handle h, int method, int iters, double *best_ms);
+
+/* spai_run with method SPAI_MR, SPAI_LOMR or SPAI_CG (same arguments, same
+ * results and return codes). */
 int spai_mr(spai_handle h, int iters, int drop_rule, spai_history *hist);
 int spai_lomr(spai_handle h, int iters, int drop_rule, spai_history *hist);
 int spai_cg(spai_handle h, int iters, int drop_rule, spai_history *hist);
