@@ -617,6 +617,25 @@ def profile_pcg(prec):
     print(json.dumps({"profile": "pcg", "prec": prec, "iters": int(p["iters"])}))
 
 
+def profile_fpmr(prec):
+    """Launch sequence for ncu captures of the differentiation kernels: the
+    64^3 variable-coefficient operator, K = 10 fixed-pattern MR steps, one
+    forward and one backward pass (values in `prec`)."""
+    import torch
+
+    from paper_2511_09753_gb300 import inputs as I
+    from paper_2511_09753_gb300.spai import FixedPatternMR
+    n, rp, ci, v = I.varcoef_3d_7pt(64, sigma=1.5, ell=8.0, seed=0)
+    f = FixedPatternMR(n, rp, ci, 10, prec=prec)
+    vd = torch.tensor(v, dtype=torch.float64, device="cuda")
+    gd = torch.empty_like(vd)
+    loss = f.forward(vd)
+    f.backward(1.0, gd)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile": "fpmr", "prec": prec, "loss": float(loss), **f.info()}))
+    f.close()
+
+
 def cpu_baseline(sample_iters=1):
     """The CPU oracle (single thread) on a bounded sample of the workload:
     `sample_iters` MR iterations on the full operator (mixed arithmetic)."""
@@ -674,10 +693,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline sample")
-    ap.add_argument("--profile", choices=list(METHODS) + ["pcg", "bpcg"], default=None,
+    ap.add_argument("--profile", choices=list(METHODS) + ["pcg", "bpcg", "fpmr"], default=None,
                     help="profiling case for ncu: 10 iterations of one method on the workload, "
-                         "(pcg) 64 iterations of its vector PCG, or (bpcg) one block PCG "
-                         "solve of the 64-matrix batch")
+                         "(pcg) 64 iterations of its vector PCG, (bpcg) one block PCG "
+                         "solve of the 64-matrix batch, or (fpmr) one gradient at 64^3")
     ap.add_argument("--prec", choices=["mixed", "fp64"], default="mixed")
     ap.add_argument("--workload", choices=[WORKLOAD, "batch64", "aniso1024", "fpmr"],
                     default=WORKLOAD)
@@ -686,6 +705,8 @@ def main():
         profile_bpcg(args.prec)
     elif args.profile == "pcg":
         profile_pcg(args.prec)
+    elif args.profile == "fpmr":
+        profile_fpmr(args.prec)
     elif args.profile:
         profile_case(args.profile, args.prec)
     elif args.workload == "batch64" and args.impl == "ours":
