@@ -636,6 +636,25 @@ def profile_fpmr(prec):
     f.close()
 
 
+def profile_fixed_pattern():
+    """Launch sequence for ncu captures of the definiteness diagnostics: the
+    rotated anisotropic 9-point operator on a 256^2 grid, the best SPAI on
+    supp(A^2) (FP64), then 100 Lanczos steps on its symmetric part."""
+    import numpy as np
+    import torch
+
+    from paper_2511_09753_gb300 import inputs as I
+    from paper_2511_09753_gb300.spai import Spai
+    n, rp, ci, v = I.aniso_2d_9pt(256)
+    h = Spai(n, rp, ci, v, prec="fp64", cap_factor=10.0)
+    h.fixed_pattern(2)
+    sp = h.sym_spectrum(steps=100, v0=np.random.default_rng(0).standard_normal(n))
+    torch.cuda.synchronize()
+    print(json.dumps({"profile": "fixed_pattern", "nnz": h.nnz_M(), "lmin": sp["lmin"],
+                      "lmax": sp["lmax"]}))
+    h.close()
+
+
 def cpu_baseline(sample_iters=1):
     """The CPU oracle (single thread) on a bounded sample of the workload:
     `sample_iters` MR iterations on the full operator (mixed arithmetic)."""
@@ -693,10 +712,12 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline sample")
-    ap.add_argument("--profile", choices=list(METHODS) + ["pcg", "bpcg", "fpmr"], default=None,
+    ap.add_argument("--profile", choices=list(METHODS) + ["pcg", "bpcg", "fpmr", "fixed_pattern"],
+                    default=None,
                     help="profiling case for ncu: 10 iterations of one method on the workload, "
                          "(pcg) 64 iterations of its vector PCG, (bpcg) one block PCG "
-                         "solve of the 64-matrix batch, or (fpmr) one gradient at 64^3")
+                         "solve of the 64-matrix batch, (fpmr) one gradient at 64^3, or "
+                         "(fixed_pattern) the SPAI on supp(A^2) and Lanczos at 256^2")
     ap.add_argument("--prec", choices=["mixed", "fp64"], default="mixed")
     ap.add_argument("--workload", choices=[WORKLOAD, "batch64", "aniso1024", "fpmr"],
                     default=WORKLOAD)
@@ -707,6 +728,8 @@ def main():
         profile_pcg(args.prec)
     elif args.profile == "fpmr":
         profile_fpmr(args.prec)
+    elif args.profile == "fixed_pattern":
+        profile_fixed_pattern()
     elif args.profile:
         profile_case(args.profile, args.prec)
     elif args.workload == "batch64" and args.impl == "ours":
