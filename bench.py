@@ -473,6 +473,61 @@ def profile_case(method, prec):
     print(json.dumps({"profile": method, "prec": prec, "resnorm": float(r["resnorm"][-1])}))
 
 
+PHASES = ("load", "union", "select", "store", "spgemm", "to_list+clear", "fixsum")
+KIND_NAMES = {0: "mr", 1: "lomr", 2: "cg_a", 3: "cg_b"}
+
+
+def run_phase_clocks(args):
+    """Per-phase cycle budget of the FP32 column pass on the bench workload:
+    builds libspai_phase.so (the same sources with SPAI_PHASE_CLOCKS), runs
+    args.warmup untimed steps and one counted step of the bench (50 MR, 50
+    LOMR, 50 CG iterations; no PCG), and prints, per pass kind, the clock64()
+    cycles per column of each phase, summed over warps and divided by the
+    columns processed.  Timings of this build are not bench values."""
+    import ctypes as C
+
+    import torch
+
+    from paper_2511_09753_gb300 import build as B
+    from paper_2511_09753_gb300 import inputs as I
+    from paper_2511_09753_gb300 import spai as S
+    S.use_library(B.build(variant="phase"))
+    lib = S.load()
+    lib.spai_phase_clocks.restype = C.c_int
+    lib.spai_phase_clocks.argtypes = [C.c_void_p, C.c_int]
+    n, rp, ci, v = I.varcoef_3d_7pt(64, sigma=1.5, ell=8.0, seed=0)
+    g = S.Spai(n, rp, ci, v, prec="mixed", cap_factor=CAP)
+    for m in METHODS:
+        g.autotune(m, 10)
+    buf = (C.c_ulonglong * 128)()
+
+    def step():
+        for m in METHODS:
+            g.reset()
+            g.run(m, ITERS)
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        step()
+    assert lib.spai_phase_clocks(buf, 1) == 0
+    step()
+    assert lib.spai_phase_clocks(buf, 1) == 0
+    out = {}
+    for k, name in KIND_NAMES.items():
+        row = [buf[k * 16 + q] for q in range(16)]
+        cols = row[8]
+        if cols == 0:
+            continue
+        ph = {PHASES[q]: row[q] / cols for q in range(len(PHASES))}
+        ph["sum_of_phases"] = sum(row[q] for q in range(7)) / cols
+        ph["warp_cycles_per_column"] = row[9] / cols
+        ph["cta_tail_cycles_per_column"] = row[7] / cols
+        ph["columns"] = cols
+        out[name] = ph
+    print(json.dumps({"phase_clocks": out, "workload": WORKLOAD, "prec": "mixed",
+                      "unit": "clock64 cycles per column (warp view)"}))
+
+
 def run_aniso(args):
     """Rotated anisotropic 9-point operator, 1024^2 (eps 1e-3, theta pi/6):
     LOMR and CG, 100 iterations each at caps 2, 4 and 8 nnz(A[:,j]) (mixed),
@@ -718,11 +773,15 @@ def main():
                          "(pcg) 64 iterations of its vector PCG, (bpcg) one block PCG "
                          "solve of the 64-matrix batch, (fpmr) one gradient at 64^3, or "
                          "(fixed_pattern) the SPAI on supp(A^2) and Lanczos at 256^2")
+    ap.add_argument("--phase-clocks", action="store_true",
+                    help="per-phase cycles per column of the FP32 column pass (profiling build)")
     ap.add_argument("--prec", choices=["mixed", "fp64"], default="mixed")
     ap.add_argument("--workload", choices=[WORKLOAD, "batch64", "aniso1024", "fpmr"],
                     default=WORKLOAD)
     args = ap.parse_args()
-    if args.profile == "bpcg":
+    if args.phase_clocks:
+        run_phase_clocks(args)
+    elif args.profile == "bpcg":
         profile_bpcg(args.prec)
     elif args.profile == "pcg":
         profile_pcg(args.prec)

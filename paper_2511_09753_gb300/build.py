@@ -45,8 +45,16 @@ def _stale(obj, deps):
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(verbose: bool = False, force: bool = False) -> str:
-    os.makedirs(BUILD, exist_ok=True)
+def build(verbose: bool = False, force: bool = False, variant: str = "") -> str:
+    """Build libspai.so; variant="phase" builds libspai_phase.so instead, the
+    same sources compiled with SPAI_PHASE_CLOCKS (per-phase clock64() counts
+    in the column pass, read with spai_phase_clocks; a profiling build)."""
+    if variant not in ("", "phase"):
+        raise ValueError(variant)
+    build_dir = BUILD + ("_" + variant if variant else "")
+    lib_path = os.path.join(HERE, "libspai_phase.so") if variant else LIB
+    extra = ["-DSPAI_PHASE_CLOCKS"] if variant == "phase" else []
+    os.makedirs(build_dir, exist_ok=True)
     headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))]
     headers.append(os.path.join(ROOT, "include", "spai.h"))
     cc = nvcc()
@@ -54,10 +62,10 @@ def build(verbose: bool = False, force: bool = False) -> str:
     objs = []
     for src in SOURCES:
         s = os.path.join(CSRC, src)
-        o = os.path.join(BUILD, src.replace(".cu", ".o"))
+        o = os.path.join(build_dir, src.replace(".cu", ".o"))
         objs.append(o)
         if force or _stale(o, [s] + headers):
-            jobs.append([cc] + _flags() + ["-c", s, "-o", o])
+            jobs.append([cc] + _flags() + extra + ["-c", s, "-o", o])
     if jobs:
         with cf.ThreadPoolExecutor(max_workers=len(jobs)) as ex:
             futs = [ex.submit(subprocess.run, j, capture_output=True, text=True) for j in jobs]
@@ -67,15 +75,16 @@ def build(verbose: bool = False, force: bool = False) -> str:
                     sys.stderr.write(r.stdout + r.stderr)
                 if r.returncode != 0:
                     raise RuntimeError("nvcc failed: " + " ".join(j) + "\n" + r.stdout + r.stderr)
-    if force or jobs or _stale(LIB, objs):
-        tmp = LIB + f".tmp{os.getpid()}"
+    if force or jobs or _stale(lib_path, objs):
+        tmp = lib_path + f".tmp{os.getpid()}"
         r = subprocess.run([cc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart_static", "-lrt",
                            "-lpthread", "-ldl"], capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("link failed\n" + r.stdout + r.stderr)
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib_path)
+    return lib_path
 
 
 if __name__ == "__main__":
-    print(build(verbose=True, force="--force" in sys.argv))
+    print(build(verbose=True, force="--force" in sys.argv,
+                variant="phase" if "--phase" in sys.argv else ""))

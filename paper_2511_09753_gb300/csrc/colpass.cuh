@@ -32,6 +32,19 @@ __device__ inline double block_tree_global(const double* v, int len, double* red
   return s;
 }
 
+// Per-phase cycle counts of the column pass, kept only in the library built
+// with SPAI_PHASE_CLOCKS (a profiling build; the product library has none of
+// this).  g_phase_clk[kind * 16 + phase] sums, over all warps, the clock64()
+// cycles a warp spent in that phase; kPhCols counts the columns and kPhTail
+// the cycles thread 0 of each CTA spent in the reduction tail.
+enum : int {
+  kPhLoad = 0, kPhUnion, kPhSelect, kPhStore, kPhSpgemm, kPhList, kPhFixsum, kPhTail, kPhCols,
+  kPhWarp, kPhCount
+};
+#ifdef SPAI_PHASE_CLOCKS
+__device__ unsigned long long g_phase_clk[8 * 16];
+#endif
+
 template <typename VS, typename VC>
 struct ColCtx {
   const PassParams& p;
@@ -42,8 +55,25 @@ struct ColCtx {
   unsigned long long spg;
   const DevScalars* sc;  // the coefficients of this column's matrix
   int seg;               // its segment in batched mode, else -1
+#ifdef SPAI_PHASE_CLOCKS
+  long long ph_t0;
+  long long ph[kPhCount];
+  __device__ ColCtx(const PassParams& pp, char* w, int l, const DevScalars* s, int sg)
+      : p(pp), ws(w), lane(l), overflow(0), bytes(0), spg(0), sc(s), seg(sg), ph_t0(0) {
+    for (int k = 0; k < kPhCount; k++) ph[k] = 0;
+  }
+  __device__ __forceinline__ void ph_start() { ph_t0 = clock64(); }
+  __device__ __forceinline__ void mark(int k) {
+    const long long t = clock64();
+    ph[k] += t - ph_t0;
+    ph_t0 = t;
+  }
+#else
   __device__ ColCtx(const PassParams& pp, char* w, int l, const DevScalars* s, int sg)
       : p(pp), ws(w), lane(l), overflow(0), bytes(0), spg(0), sc(s), seg(sg) {}
+  __device__ __forceinline__ void ph_start() {}
+  __device__ __forceinline__ void mark(int) {}
+#endif
   template <typename T> __device__ T* at(int off) const { return (T*)(ws + off); }
 };
 
@@ -200,6 +230,7 @@ __device__ void column_work(ColCtx<VS, VC>& c, int j, double* part) {
   int Lp = needP ? p.Plen[j] : 0;
   const int Lz0 = needZ ? p.Zlen[j] : 0;
   load_cols(c, off, Lm, Mr, Mv, Lp, Pr, Pv, Lz0, c.template at<int>(L.Zr), c.template at<VC>(L.Zv));
+  c.mark(kPhLoad);
   c.bytes += (unsigned long long)(Lm + Lp + Lz0) * (sizeof(int) + sizeof(VS)) +
              ((int)needM + (int)needP + (int)needZ) * sizeof(int);
 
@@ -246,12 +277,17 @@ __device__ void column_work(ColCtx<VS, VC>& c, int j, double* part) {
     if (p.do_update) {
       CombAxpy<VC> f{c.sc->alpha};
       int Lt = warp_union(un, Mr, Mv, Lm, Pr, Pv, Lp, Tr, Tv, f, lane);
+      c.mark(kPhUnion);
       Lm = warp_select(Tr, Tv, Lt, cap, Mr, Mv, hist, tie, p.drop, ovf, lane);
+      c.mark(kPhSelect);
       store_col(c, p.Mrow, p.Mval, p.Mlen, j, off, Lm, Mr, Mv);
+      c.mark(kPhStore);
     }
     int cnt = spgemm(p, ha, Mr, Mv, Lm, j, Tr, Tv, lane, c.seg);
+    c.mark(kPhSpgemm);
     int LR = table_to_list(ha, cnt, j, Rr, Rv, lane);
     hash_clear(ha, cnt, lane);
+    c.mark(kPhList);
     c.spg++;
     if (!p.do_dir && !p.dir_store) {
       fixsum<1>(part, lane, TermSq<VC>{Rv}, LR);
@@ -268,13 +304,16 @@ __device__ void column_work(ColCtx<VS, VC>& c, int j, double* part) {
       } else {
         Lp = warp_select(Rr, Rv, LR, cap, Pr, Pv, hist, tie, p.drop, ovf, lane);
       }
+      c.mark(kPhSelect);
       store_col(c, p.Prow, p.Pval, p.Plen, j, off, Lp, Pr, Pv);
+      c.mark(kPhStore);
     }
     if (!p.do_dir) {  // dir_store: the direction candidate is all this pass forms
       fixsum<1>(part, lane, TermSq<VC>{Rv}, LR);
       return;
     }
     int cq = spgemm(p, ha, Pr, Pv, Lp, -1, Tr, Tv, lane, c.seg);  // table holds Q = A P
+    c.mark(kPhSpgemm);
     c.spg++;
     if (PI)  // (R,R), (R,Pi Q), (Q,Pi Q)
       fixsum<3>(part, lane, TermSq<VC>{Rv}, LR, TermWProdFind<VC>{Rr, Rv, ha, p.pi}, LR,
@@ -282,7 +321,9 @@ __device__ void column_work(ColCtx<VS, VC>& c, int j, double* part) {
     else     // (R,R), (R,Q), (Q,Q)
       fixsum<3>(part, lane, TermSq<VC>{Rv}, LR, TermProdFind<VC>{Rr, Rv, ha}, LR,
                 TermSqTable<VC>{(const VC*)ha.val, ha.occ}, cq);
+    c.mark(kPhFixsum);
     hash_clear(ha, cq, lane);
+    c.mark(kPhList);
     return;
   }
 
@@ -299,16 +340,24 @@ __device__ void column_work(ColCtx<VS, VC>& c, int j, double* part) {
     if (p.do_update) {
       CombLin<VC> fl{c.sc->delta, c.sc->gamma};
       int Ls = warp_union(un, Zr, Zv, Lz0, Pr, Pv, Lp, Sr, Sv, fl, lane);
+      c.mark(kPhUnion);
       Lp = warp_select(Sr, Sv, Ls, cap, Pr, Pv, hist, tie, p.drop, ovf, lane);
+      c.mark(kPhSelect);
       store_col(c, p.Prow, p.Pval, p.Plen, j, off, Lp, Pr, Pv);
+      c.mark(kPhStore);
       CombAdd<VC> fa;
       int Lt = warp_union(un, Mr, Mv, Lm, Sr, Sv, Ls, Tr, Tv, fa, lane);
+      c.mark(kPhUnion);
       Lm = warp_select(Tr, Tv, Lt, cap, Mr, Mv, hist, tie, p.drop, ovf, lane);
+      c.mark(kPhSelect);
       store_col(c, p.Mrow, p.Mval, p.Mlen, j, off, Lm, Mr, Mv);
+      c.mark(kPhStore);
     }
     int cr = spgemm(p, ha, Mr, Mv, Lm, j, Tr, Tv, lane, c.seg);
+    c.mark(kPhSpgemm);
     int LR = table_to_list(ha, cr, j, Rr, Rv, lane);
     hash_clear(ha, cr, lane);
+    c.mark(kPhList);
     c.spg++;
     if (!p.do_dir && !p.dir_store) {
       fixsum<1>(part, lane, TermSq<VC>{Rv}, LR);
@@ -326,13 +375,16 @@ __device__ void column_work(ColCtx<VS, VC>& c, int j, double* part) {
       } else {
         Lz = warp_select(Rr, Rv, LR, cap, Zr, Zv, hist, tie, p.drop, ovf, lane);
       }
+      c.mark(kPhSelect);
       store_col(c, p.Zrow, p.Zval, p.Zlen, j, off, Lz, Zr, Zv);
+      c.mark(kPhStore);
     }
     if (!p.do_dir) {  // dir_store: the Z candidate is all this pass forms
       fixsum<1>(part, lane, TermSq<VC>{Rv}, LR);
       return;
     }
     int cu = spgemm(p, ha, Zr, Zv, Lz, -1, Tr, Tv, lane, c.seg);   // table A: U = A Z
+    c.mark(kPhSpgemm);
     double t3[3];
     if (PI)  // (R,R), (U,Pi U), (U,Pi R)
       fixsum<3>(t3, lane, TermSq<VC>{Rv}, LR,
@@ -344,8 +396,11 @@ __device__ void column_work(ColCtx<VS, VC>& c, int j, double* part) {
     part[0] = t3[0];
     part[1] = t3[1];
     part[4] = t3[2];
+    c.mark(kPhFixsum);
     hash_clear_all(hb, lane);  // its bytes also held the union table and the select scratch
+    c.mark(kPhList);
     int cv = spgemm(p, hb, Pr, Pv, Lp, -1, Tr, Tv, lane, c.seg);   // table B: V = A P
+    c.mark(kPhSpgemm);
     c.spg += 2;
     if (PI)  // (V,Pi V), (U,Pi V), (V,Pi R)
       fixsum<3>(t3, lane, TermWSqTable<VC>{hb.key, (const VC*)hb.val, hb.occ, p.pi}, cv,
@@ -358,7 +413,9 @@ __device__ void column_work(ColCtx<VS, VC>& c, int j, double* part) {
     part[2] = t3[0];
     part[3] = t3[1];
     part[5] = t3[2];
+    c.mark(kPhFixsum);
     hash_clear(ha, cu, lane);
+    c.mark(kPhList);
     return;
   }
 
@@ -366,22 +423,29 @@ __device__ void column_work(ColCtx<VS, VC>& c, int j, double* part) {
     if (p.do_update) {  // without it: R and beta of an M changed outside (global dropping)
       CombAxpy<VC> f{c.sc->alpha};
       int Lt = warp_union(un, Mr, Mv, Lm, Pr, Pv, Lp, Tr, Tv, f, lane);
+      c.mark(kPhUnion);
       Lm = warp_select(Tr, Tv, Lt, cap, Mr, Mv, hist, tie, p.drop, ovf, lane);
+      c.mark(kPhSelect);
       store_col(c, p.Mrow, p.Mval, p.Mlen, j, off, Lm, Mr, Mv);
+      c.mark(kPhStore);
     }
     if (!p.do_dir) {  // the update only: M is dropped outside before R is formed
       part[0] = 0.0;
       return;
     }
     int cr = spgemm(p, ha, Mr, Mv, Lm, j, Tr, Tv, lane, c.seg);
+    c.mark(kPhSpgemm);
     int LR = table_to_list(ha, cr, j, Rr, Rv, lane);
     hash_clear(ha, cr, lane);
+    c.mark(kPhList);
     c.spg++;
     if (p.r_out) store_r(c, j, LR, Rr, Rv);
+    c.mark(kPhStore);
     if (PI)  // (R,R), (R,Pi R)
       fixsum<2>(part, lane, TermSq<VC>{Rv}, LR, TermWSq<VC>{Rr, Rv, p.pi}, LR);
     else
       fixsum<1>(part, lane, TermSq<VC>{Rv}, LR);
+    c.mark(kPhFixsum);
     return;
   }
 
@@ -389,6 +453,7 @@ __device__ void column_work(ColCtx<VS, VC>& c, int j, double* part) {
     int LR;
     if (p.r_in) {  // R as the previous pass A computed it
       LR = load_r(c, j, Rr, Rv);
+      c.mark(kPhLoad);
     } else {
       int cr = spgemm(p, ha, Mr, Mv, Lm, j, Tr, Tv, lane, c.seg);
       LR = table_to_list(ha, cr, j, Rr, Rv, lane);
@@ -406,21 +471,27 @@ __device__ void column_work(ColCtx<VS, VC>& c, int j, double* part) {
       } else {
         Lt = warp_union(un, Rr, Rv, LR, Pr, Pv, Lp, Tr, Tv, f, lane);
       }
+      c.mark(kPhUnion);
       Lp = warp_select(Tr, Tv, Lt, cap, Pr, Pv, hist, tie, p.drop, ovf, lane);
+      c.mark(kPhSelect);
       store_col(c, p.Prow, p.Pval, p.Plen, j, off, Lp, Pr, Pv);
+      c.mark(kPhStore);
     }
     if (!p.do_dir) {  // the direction candidate only (global dropping follows)
       fixsum<1>(part, lane, TermSq<VC>{Rv}, LR);
       return;
     }
     int cq = spgemm(p, ha, Pr, Pv, Lp, -1, Tr, Tv, lane, c.seg);  // table holds Q = A P
+    c.mark(kPhSpgemm);
     c.spg++;
     if (PI)  // (R,R), (P,Q), (R,Pi R)
       fixsum<3>(part, lane, TermSq<VC>{Rv}, LR, TermProdFind<VC>{Pr, Pv, ha}, Lp,
                 TermWSq<VC>{Rr, Rv, p.pi}, LR);
     else     // (R,R), (P,Q)
       fixsum<2>(part, lane, TermSq<VC>{Rv}, LR, TermProdFind<VC>{Pr, Pv, ha}, Lp);
+    c.mark(kPhFixsum);
     hash_clear(ha, cq, lane);
+    c.mark(kPhList);
   }
 }
 
@@ -569,13 +640,36 @@ __global__ void __launch_bounds__(256, sizeof(VC) == 4 ? 4 : 3) colpass_kernel(c
   }
   const int B = p.B;
   const long long j0 = (long long)blockIdx.x * B;
+#ifdef SPAI_PHASE_CLOCKS
+  const long long w_t0 = clock64();
+#endif
   for (int cc = warp; cc < B; cc += p.NW) {
     long long j = j0 + cc;
     double pr[6] = {0, 0, 0, 0, 0, 0};
-    if (j < p.n) column_work<VS, VC, PI, KIND>(c, (int)j, pr);
+    c.ph_start();
+    if (j < p.n) {
+      column_work<VS, VC, PI, KIND>(c, (int)j, pr);
+#ifdef SPAI_PHASE_CLOCKS
+      c.ph[kPhCols]++;
+#endif
+    }
     if (lane == 0)
       for (int q = 0; q < nq; q++) part[q * B + cc] = pr[q];
   }
+#ifdef SPAI_PHASE_CLOCKS
+  c.ph[kPhWarp] = clock64() - w_t0;
+  if (lane == 0)
+    for (int k = 0; k < kPhCount; k++)
+      if (k != kPhTail) atomicAdd(&g_phase_clk[KIND * 16 + k], (unsigned long long)c.ph[k]);
+  const long long t_tail = clock64();  // thread 0 adds the cycles from here to its return
+#define SPAI_TAIL_DONE()                                                                 \
+  do {                                                                                   \
+    if (threadIdx.x == 0)                                                                \
+      atomicAdd(&g_phase_clk[KIND * 16 + kPhTail], (unsigned long long)(clock64() - t_tail)); \
+  } while (0)
+#else
+#define SPAI_TAIL_DONE() ((void)0)
+#endif
   // per-CTA counters
   __shared__ unsigned long long s_bytes, s_spg;
   __shared__ int s_ovf, s_last1, s_last2;
@@ -622,7 +716,10 @@ __global__ void __launch_bounds__(256, sizeof(VC) == 4 ? 4 : 3) colpass_kernel(c
       s_last1 = (old == (unsigned)(p.seg_npad[seg] / p.B - 1));
     }
     __syncthreads();
-    if (!s_last1) return;
+    if (!s_last1) {
+      SPAI_TAIL_DONE();
+      return;
+    }
     __threadfence();
     for (int q = 0; q < nq; q++) {
       double s = block_tree_global(p.bsum + (long long)q * p.nb + p.seg_col0[seg] / p.B,
@@ -637,6 +734,7 @@ __global__ void __launch_bounds__(256, sizeof(VC) == 4 ? 4 : 3) colpass_kernel(c
                    tot);
       __threadfence();
     }
+    SPAI_TAIL_DONE();
     return;
   }
   // last-arriver tree: groups of kGroup blocks, then all groups
@@ -651,7 +749,10 @@ __global__ void __launch_bounds__(256, sizeof(VC) == 4 ? 4 : 3) colpass_kernel(c
     s_last1 = (old == (unsigned)(gsize - 1));
   }
   __syncthreads();
-  if (!s_last1) return;
+  if (!s_last1) {
+    SPAI_TAIL_DONE();
+    return;
+  }
   __threadfence();
   {
     int gsize = min(kGroup, p.nb - g * kGroup);
@@ -674,7 +775,10 @@ __global__ void __launch_bounds__(256, sizeof(VC) == 4 ? 4 : 3) colpass_kernel(c
     s_last2 = (old == (unsigned)(p.ngroups - 1));
   }
   __syncthreads();
-  if (!s_last2) return;
+  if (!s_last2) {
+    SPAI_TAIL_DONE();
+    return;
+  }
   __threadfence();
   for (int q = 0; q < nq; q++) {
     double s = block_tree_global(p.gsum + (long long)q * p.ngroups, p.ngroups, red, lane, warp);
@@ -686,6 +790,8 @@ __global__ void __launch_bounds__(256, sizeof(VC) == 4 ? 4 : 3) colpass_kernel(c
     coefficients(p, p.sc, p.hist_res, p.hist_coef, tot);
     __threadfence();
   }
+  SPAI_TAIL_DONE();
 }
+#undef SPAI_TAIL_DONE
 
 }  // namespace spai

@@ -59,6 +59,16 @@ class _Stats(C.Structure):
 
 
 _lib = None
+_lib_path = LIB_PATH
+
+
+def use_library(path: str) -> None:
+    """Bind to another build of the same library (the profiling build
+    libspai_phase.so) instead of libspai.so; call before the first load()."""
+    global _lib_path
+    if _lib is not None and path != _lib_path:
+        raise RuntimeError("the library is already loaded")
+    _lib_path = path
 
 
 def load():
@@ -66,9 +76,9 @@ def load():
     global _lib
     if _lib is not None:
         return _lib
-    if not os.path.exists(LIB_PATH):
-        raise RuntimeError(f"libspai.so not built ({LIB_PATH}); run paper_2511_09753_gb300.build")
-    lib = C.CDLL(LIB_PATH)
+    if not os.path.exists(_lib_path):
+        raise RuntimeError(f"libspai.so not built ({_lib_path}); run paper_2511_09753_gb300.build")
+    lib = C.CDLL(_lib_path)
     vp, i64, i32, dbl = C.c_void_p, C.c_int64, C.c_int, C.c_double
     sig = {
         "spai_validate_csr": (i32, [i64, i64, vp, vp, vp, i32]),
