@@ -2,8 +2,11 @@
 
 Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline
 leg may import this package.  It compiles ``spai_oracle.c`` with gcc
-(``-O2 -ffp-contract=off``) into ``oracle/_build/liboracle.so`` and wraps it
-with ctypes.  It imports nothing from the product package.
+(``-O2 -ffp-contract=off``) into ``oracle/_build/liboracle.so`` and, with
+``-fopenmp`` added, into ``oracle/_build/liboracle_omp.so`` (the loops over
+columns and PCG rows shared among threads; the same bits as the serial
+build), and wraps them with ctypes.  It imports nothing from the product
+package.
 
 Method definitions followed (Venkovic & Anzt): MR = Algorithm 1, CG =
 Algorithm 3 (Def. 1, Prop. 2), LOMR = Algorithm 4 (Def. 2, Theorem 3), hard
@@ -24,8 +27,9 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "spai_oracle.c")
 _BUILD = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_BUILD, "liboracle.so")
+_LIB_OMP = os.path.join(_BUILD, "liboracle_omp.so")
 _lock = threading.Lock()
-_lib = None
+_libs = {}
 
 MR, LOMR, CG = 0, 1, 2
 MR_PI, LOMR_PI, CG_PI = 3, 4, 5  # Section 5's forms with Pi = diag(A)^{-1} (Algorithms 5, 8, 7)
@@ -34,26 +38,29 @@ FLAG_CONVERGED, FLAG_FALLBACK, FLAG_NONFINITE = 1, 2, 4
 DROP_NONE, DROP_TOPK, DROP_DIRECTIONS = 0, 1, 2
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle shared library (idempotent)."""
+def build(force: bool = False, omp: bool = False) -> str:
+    """Compile the oracle shared library (idempotent); omp=True builds the
+    OpenMP one."""
     os.makedirs(_BUILD, exist_ok=True)
-    if (not force and os.path.exists(_LIB)
-            and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
-        return _LIB
-    tmp = _LIB + f".tmp{os.getpid()}"
+    out = _LIB_OMP if omp else _LIB
+    if (not force and os.path.exists(out)
+            and os.path.getmtime(out) >= os.path.getmtime(_SRC)):
+        return out
+    tmp = out + f".tmp{os.getpid()}"
     cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
            "-o", tmp, _SRC, "-lm"]
+    if omp:
+        cmd.insert(1, "-fopenmp")
     subprocess.run(cmd, check=True)
-    os.replace(tmp, _LIB)
-    return _LIB
+    os.replace(tmp, out)
+    return out
 
 
-def _load():
-    global _lib
+def _load(omp: bool = False):
     with _lock:
-        if _lib is not None:
-            return _lib
-        lib = C.CDLL(build())
+        if omp in _libs:
+            return _libs[omp]
+        lib = C.CDLL(build(omp=omp))
         p_i32 = np.ctypeslib.ndpointer(np.int32, flags="C_CONTIGUOUS")
         p_f64 = np.ctypeslib.ndpointer(np.float64, flags="C_CONTIGUOUS")
         lib.orc_new.restype = C.c_void_p
@@ -88,7 +95,7 @@ def _load():
                                 C.POINTER(C.c_int), C.POINTER(C.c_double), C.c_int]
         lib.orc_lanczos.restype = C.c_int
         lib.orc_lanczos.argtypes = [C.c_int, p_i32, p_i32, p_f64, p_f64, C.c_int, p_f64, p_f64]
-        _lib = lib
+        _libs[omp] = lib
         return lib
 
 
@@ -110,11 +117,12 @@ class Oracle:
 
     ``mixed=True`` emulates the FP32-value / FP64-reduction arithmetic
     exactly; ``cap_factor`` sets cap_j = floor(f * nnz(A[:, j])) in [1, n].
-    M starts at diag(A)^{-1}.
+    M starts at diag(A)^{-1}.  ``omp=True`` uses the OpenMP build (all
+    threads OpenMP is given; the same results bit for bit).
     """
 
-    def __init__(self, n, rowptr, colind, vals, mixed=False, cap_factor=2.0):
-        self.lib = _load()
+    def __init__(self, n, rowptr, colind, vals, mixed=False, cap_factor=2.0, omp=False):
+        self.lib = _load(omp)
         self.n = int(n)
         self.rowptr = np.ascontiguousarray(rowptr, dtype=np.int32)
         self.colind = np.ascontiguousarray(colind, dtype=np.int32)
@@ -188,15 +196,17 @@ def drop_column(rows, vals, cap):
     return rows[:L], vals[:L]
 
 
-def pcg(n, rowptr, colind, vals, b, rtol=1e-8, maxit=10000, precond=0, M=None, mixed=False):
+def pcg(n, rowptr, colind, vals, b, rtol=1e-8, maxit=10000, precond=0, M=None, mixed=False,
+        omp=False):
     """Vector PCG with x0 = 0; precond 0 none, 1 Jacobi, 2 SPAI M, 3 symmetric
     part (M + M^T)/2 of the SPAI (M given as a CSC triple).  mixed: products
     with A and with M (or its symmetric part) in FP32 values (FP32 operand
     copy, FP32 fma chain); vectors, inner products and scalars in FP64.
 
     Returns dict(iters, status (0 conv / 1 maxit / 2 breakdown), relres, x).
+    omp=True: the OpenMP build (the same results bit for bit).
     """
-    lib = _load()
+    lib = _load(omp)
     rowptr = np.ascontiguousarray(rowptr, dtype=np.int32)
     colind = np.ascontiguousarray(colind, dtype=np.int32)
     vals = np.ascontiguousarray(vals, dtype=np.float64)

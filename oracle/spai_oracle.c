@@ -7,7 +7,12 @@
  * calls this file; only the tests, the smoke check and the benchmark's
  * CPU-baseline leg do.  It shares no code with the CUDA library.
  *
- * Plain, slow, single threaded.  Every matrix iterate is a list of columns;
+ * Plain and slow.  Built twice from this one file: single threaded, and with
+ * -fopenmp, where the loops over columns (and the PCG's loops over rows) are
+ * shared among threads.  Every column is computed by one thread exactly as
+ * in the serial build and every sum over columns or rows is taken after its
+ * loop with the same pairwise tree, so both builds give the same bits.
+ * Every matrix iterate is a list of columns;
  * each column is a row-sorted list of (row, value) with value != 0.  Build
  * with -ffp-contract=off so that a*b+c is never fused implicitly; the only
  * fused operations are the explicit fma()/fmaf() calls below.
@@ -51,6 +56,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define ORC_MR 0
 #define ORC_LOMR 1
@@ -71,6 +79,18 @@ typedef struct {
   double *val;
 } ocol;
 
+/* Per-thread scratch: the SpGEMM accumulator (a dense value and flag per
+ * row, and the list of rows touched), the buffer of inner-product terms and
+ * two column buffers.  One per thread (one in the serial build). */
+typedef struct {
+  double *acc;
+  char *seen;
+  int *touched;
+  double *tmp;
+  int tmpcap;
+  ocol c1, c2;
+} owork;
+
 typedef struct {
   int n;
   int *rowptr, *colind;
@@ -87,11 +107,28 @@ typedef struct {
   double rr;   /* CG: numerator of alpha for the current residual, (R,R) or (R,Pi R) */
   double rr_hist; /* CG: ||R_i||^2 of the current residual */
   int64_t spgemm_count;
-  /* workspace */
-  double *acc;
-  char *seen;
-  int *touched;
+  /* scratch, one per thread */
+  owork *work;
+  int nwork;
 } orc_state;
+
+#ifdef _OPENMP
+#define ORC_TID() omp_get_thread_num()
+#else
+#define ORC_TID() 0
+#endif
+
+static owork *wk(orc_state *s) { return &s->work[ORC_TID()]; }
+
+static double *wtmp(owork *w, int need) {
+  if (need > w->tmpcap) {
+    int c = w->tmpcap ? w->tmpcap : 64;
+    while (c < need) c *= 2;
+    w->tmp = (double *)realloc(w->tmp, sizeof(double) * (size_t)c);
+    w->tmpcap = c;
+  }
+  return w->tmp;
+}
 
 /* ---------------------------------------------------------------- columns */
 
@@ -228,7 +265,8 @@ double orc_fixsum(const double *t, int64_t L) {
 }
 
 /* column inner product over the common rows, Sec. 2 Eq. (2.1) */
-static double col_dot(const ocol *x, const ocol *y, double *tmp) {
+static double col_dot(const ocol *x, const ocol *y, owork *w) {
+  double *tmp = wtmp(w, x->len < y->len ? x->len : y->len);
   int a = 0, b = 0, L = 0;
   while (a < x->len && b < y->len) {
     if (x->row[a] < y->row[b]) a++;
@@ -242,7 +280,8 @@ static double col_dot(const ocol *x, const ocol *y, double *tmp) {
   return orc_fixsum(tmp, L);
 }
 
-static double col_nrm2(const ocol *x, double *tmp) {
+static double col_nrm2(const ocol *x, owork *w) {
+  double *tmp = wtmp(w, x->len);
   for (int a = 0; a < x->len; a++) tmp[a] = x->val[a] * x->val[a];
   return orc_fixsum(tmp, x->len);
 }
@@ -250,7 +289,8 @@ static double col_nrm2(const ocol *x, double *tmp) {
 /* Pi-weighted column inner product (X, Pi Y) of Section 5: each term is the
  * product of the two values (exact for FP32 values) times pi_k, rounded in
  * FP64, and the terms are summed exactly like col_dot's. */
-static double col_wdot(const ocol *x, const ocol *y, const double *pi, double *tmp) {
+static double col_wdot(const ocol *x, const ocol *y, const double *pi, owork *w) {
+  double *tmp = wtmp(w, x->len < y->len ? x->len : y->len);
   int a = 0, b = 0, L = 0;
   while (a < x->len && b < y->len) {
     if (x->row[a] < y->row[b]) a++;
@@ -264,7 +304,8 @@ static double col_wdot(const ocol *x, const ocol *y, const double *pi, double *t
   return orc_fixsum(tmp, L);
 }
 
-static double col_wnrm2(const ocol *x, const double *pi, double *tmp) {
+static double col_wnrm2(const ocol *x, const double *pi, owork *w) {
+  double *tmp = wtmp(w, x->len);
   for (int a = 0; a < x->len; a++) tmp[a] = (x->val[a] * x->val[a]) * pi[x->row[a]];
   return orc_fixsum(tmp, x->len);
 }
@@ -272,7 +313,10 @@ static double col_wnrm2(const ocol *x, const double *pi, double *tmp) {
 /* ------------------------------------------------------------- operations */
 
 /* out = A X_j (Sec. 6.2: one SpGEMM column) */
-static void spgemm_col(orc_state *s, const ocol *x, ocol *out) {
+static void spgemm_col(orc_state *s, owork *w, const ocol *x, ocol *out) {
+  double *acc = w->acc;
+  char *seen = w->seen;
+  int *touched = w->touched;
   int nt = 0;
   for (int e = 0; e < x->len; e++) {
     int k = x->row[e];
@@ -280,23 +324,23 @@ static void spgemm_col(orc_state *s, const ocol *x, ocol *out) {
     for (int q = s->rowptr[k]; q < s->rowptr[k + 1]; q++) {
       int r = s->colind[q];
       double a = s->av[q]; /* a_kr == a_rk: A is exactly symmetric */
-      if (!s->seen[r]) {
-        s->seen[r] = 1;
-        s->acc[r] = 0.0;
-        s->touched[nt++] = r;
+      if (!seen[r]) {
+        seen[r] = 1;
+        acc[r] = 0.0;
+        touched[nt++] = r;
       }
       if (s->mixed)
-        s->acc[r] = (double)fmaf((float)a, (float)xv, (float)s->acc[r]);
+        acc[r] = (double)fmaf((float)a, (float)xv, (float)acc[r]);
       else
-        s->acc[r] = fma(a, xv, s->acc[r]);
+        acc[r] = fma(a, xv, acc[r]);
     }
   }
-  qsort(s->touched, (size_t)nt, sizeof(int), cmp_int);
+  qsort(touched, (size_t)nt, sizeof(int), cmp_int);
   out->len = 0;
   for (int t = 0; t < nt; t++) {
-    int r = s->touched[t];
-    double v = s->acc[r];
-    s->seen[r] = 0;
+    int r = touched[t];
+    double v = acc[r];
+    seen[r] = 0;
     if (v != 0.0) col_push(out, r, v);
   }
 }
@@ -441,9 +485,17 @@ orc_state *orc_new(int n, const int *rowptr, const int *colind, const double *va
   s->M = mat_new(n);
   s->P = mat_new(n);
   s->Z = mat_new(n);
-  s->acc = (double *)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
-  s->seen = (char *)calloc((size_t)(n > 0 ? n : 1), 1);
-  s->touched = (int *)malloc(sizeof(int) * (size_t)(n > 0 ? n : 1));
+#ifdef _OPENMP
+  s->nwork = omp_get_max_threads();
+#else
+  s->nwork = 1;
+#endif
+  s->work = (owork *)calloc((size_t)s->nwork, sizeof(owork));
+  for (int t = 0; t < s->nwork; t++) {
+    s->work[t].acc = (double *)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
+    s->work[t].seen = (char *)calloc((size_t)(n > 0 ? n : 1), 1);
+    s->work[t].touched = (int *)malloc(sizeof(int) * (size_t)(n > 0 ? n : 1));
+  }
   s->method = -1;
   s->pi = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
   for (int j = 0; j < n; j++) {
@@ -474,9 +526,15 @@ void orc_free(orc_state *s) {
   free(s->av);
   free(s->pi);
   free(s->capj);
-  free(s->acc);
-  free(s->seen);
-  free(s->touched);
+  for (int t = 0; t < s->nwork; t++) {
+    free(s->work[t].acc);
+    free(s->work[t].seen);
+    free(s->work[t].touched);
+    free(s->work[t].tmp);
+    col_free(&s->work[t].c1);
+    col_free(&s->work[t].c2);
+  }
+  free(s->work);
   free(s);
 }
 
@@ -521,20 +579,21 @@ int64_t orc_spgemm_count(const orc_state *s) { return s->spgemm_count; }
 /* -------------------------------------------------------------- the passes */
 
 /* R = I - A M for all columns; returns ||R||_F^2 (global pairwise) */
-static double residual_all(orc_state *s, ocol *R, double *partial, double *tmp) {
-  ocol am = {0};
+static double residual_all(orc_state *s, ocol *R, double *partial) {
+#pragma omp parallel for schedule(dynamic, 64) num_threads(s->nwork)
   for (int j = 0; j < s->n; j++) {
-    spgemm_col(s, &s->M[j], &am);
-    residual_col(s, j, &am, &R[j]);
-    partial[j] = col_nrm2(&R[j], tmp);
+    owork *w = wk(s);
+    spgemm_col(s, w, &s->M[j], &w->c1);
+    residual_col(s, j, &w->c1, &R[j]);
+    partial[j] = col_nrm2(&R[j], w);
   }
-  col_free(&am);
   s->spgemm_count++;
   return pairwise64(partial, s->n);
 }
 
 static void product_all(orc_state *s, ocol *X, ocol *out) {
-  for (int j = 0; j < s->n; j++) spgemm_col(s, &X[j], &out[j]);
+#pragma omp parallel for schedule(dynamic, 64) num_threads(s->nwork)
+  for (int j = 0; j < s->n; j++) spgemm_col(s, wk(s), &X[j], &out[j]);
   s->spgemm_count++;
 }
 
@@ -571,31 +630,32 @@ int orc_run(orc_state *s, int method, int iters, int drop, double *resnorm, doub
     s->method = method;
   }
   ocol *R = mat_new(n), *Q = mat_new(n), *U = mat_new(n), *V = mat_new(n), *S = mat_new(n);
-  ocol tmpc = {0};
   double *partial = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
   double *p2 = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
   double *p3 = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
   double *p4 = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
   double *p5 = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
-  double *tmp = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1) * 2);
   int dropM = (drop == 1), dropD = (drop >= 1);
 
   if (base == ORC_MR) {
     /* Algorithm 1 with explicit residual, P_i = D(R_i); with Pi
        (Algorithm 5): P_i = D(Pi R_i), alpha = (Pi R, A P) / (A P, Pi A P) */
     for (int i = 0; i < iters; i++) {
-      double rr = residual_all(s, R, partial, tmp);
+      double rr = residual_all(s, R, partial);
       resnorm[i] = sqrt(rr);
       if (rr == 0.0) { *flags |= ORC_FLAG_CONVERGED; break; }
+#pragma omp parallel for schedule(dynamic, 64) num_threads(s->nwork)
       for (int j = 0; j < n; j++) {
         if (use_pi) pi_col(s, &R[j], &s->P[j]);
         else col_copy(&s->P[j], &R[j]);
         if (dropD) drop_col(&s->P[j], s->capj[j]);
       }
       product_all(s, s->P, Q);
+#pragma omp parallel for schedule(dynamic, 64) num_threads(s->nwork)
       for (int j = 0; j < n; j++) {
-        p2[j] = use_pi ? col_wdot(&R[j], &Q[j], s->pi, tmp) : col_dot(&R[j], &Q[j], tmp);
-        p3[j] = use_pi ? col_wnrm2(&Q[j], s->pi, tmp) : col_nrm2(&Q[j], tmp);
+        owork *w = wk(s);
+        p2[j] = use_pi ? col_wdot(&R[j], &Q[j], s->pi, w) : col_dot(&R[j], &Q[j], w);
+        p3[j] = use_pi ? col_wnrm2(&Q[j], s->pi, w) : col_nrm2(&Q[j], w);
       }
       double rq = pairwise64(p2, n), qq = pairwise64(p3, n);
       if (qq == 0.0) { *flags |= ORC_FLAG_CONVERGED; break; }
@@ -603,23 +663,26 @@ int orc_run(orc_state *s, int method, int iters, int drop, double *resnorm, doub
       if (!isfin(alpha)) { *flags |= ORC_FLAG_NONFINITE; break; }
       coef[2 * i] = alpha;
       coef[2 * i + 1] = 0.0;
+#pragma omp parallel for schedule(dynamic, 64) num_threads(s->nwork)
       for (int j = 0; j < n; j++) {
-        combine_col(s, COMB_AXPY, alpha, 0.0, &s->M[j], &s->P[j], &tmpc);
-        if (dropM) drop_col(&tmpc, s->capj[j]);
-        col_copy(&s->M[j], &tmpc);
+        owork *w = wk(s);
+        combine_col(s, COMB_AXPY, alpha, 0.0, &s->M[j], &s->P[j], &w->c2);
+        if (dropM) drop_col(&w->c2, s->capj[j]);
+        col_copy(&s->M[j], &w->c2);
       }
       done++;
       s->it++;
     }
-    if (done == iters) resnorm[iters] = sqrt(residual_all(s, R, partial, tmp));
+    if (done == iters) resnorm[iters] = sqrt(residual_all(s, R, partial));
   } else if (base == ORC_LOMR) {
     /* Algorithm 4 with explicit residual: Z_i = D(R_i), P_i = D(S_i),
        M_{i+1} = D(M_i + S_i), S_i = delta Z_i + gamma P_{i-1}. s->P holds
        P_{i-1} between iterations. */
     for (int i = 0; i < iters; i++) {
-      double rr = residual_all(s, R, partial, tmp);
+      double rr = residual_all(s, R, partial);
       resnorm[i] = sqrt(rr);
       if (rr == 0.0) { *flags |= ORC_FLAG_CONVERGED; break; }
+#pragma omp parallel for schedule(dynamic, 64) num_threads(s->nwork)
       for (int j = 0; j < n; j++) {
         if (use_pi) pi_col(s, &R[j], &s->Z[j]);
         else col_copy(&s->Z[j], &R[j]);
@@ -627,19 +690,21 @@ int orc_run(orc_state *s, int method, int iters, int drop, double *resnorm, doub
       }
       product_all(s, s->Z, U);
       product_all(s, s->P, V);
+#pragma omp parallel for schedule(dynamic, 64) num_threads(s->nwork)
       for (int j = 0; j < n; j++) {
+        owork *w = wk(s);
         if (use_pi) { /* Algorithm 8: (AZ, Pi AZ), ..., (Pi R, AZ), (Pi R, AP) */
-          partial[j] = col_wnrm2(&U[j], s->pi, tmp);
-          p2[j] = col_wnrm2(&V[j], s->pi, tmp);
-          p3[j] = col_wdot(&U[j], &V[j], s->pi, tmp);
-          p4[j] = col_wdot(&U[j], &R[j], s->pi, tmp);
-          p5[j] = col_wdot(&V[j], &R[j], s->pi, tmp);
+          partial[j] = col_wnrm2(&U[j], s->pi, w);
+          p2[j] = col_wnrm2(&V[j], s->pi, w);
+          p3[j] = col_wdot(&U[j], &V[j], s->pi, w);
+          p4[j] = col_wdot(&U[j], &R[j], s->pi, w);
+          p5[j] = col_wdot(&V[j], &R[j], s->pi, w);
         } else {
-          partial[j] = col_nrm2(&U[j], tmp);
-          p2[j] = col_nrm2(&V[j], tmp);
-          p3[j] = col_dot(&U[j], &V[j], tmp);
-          p4[j] = col_dot(&U[j], &R[j], tmp);
-          p5[j] = col_dot(&V[j], &R[j], tmp);
+          partial[j] = col_nrm2(&U[j], w);
+          p2[j] = col_nrm2(&V[j], w);
+          p3[j] = col_dot(&U[j], &V[j], w);
+          p4[j] = col_dot(&U[j], &R[j], w);
+          p5[j] = col_dot(&V[j], &R[j], w);
         }
       }
       double uu = pairwise64(partial, n), vv = pairwise64(p2, n), uv = pairwise64(p3, n);
@@ -662,18 +727,20 @@ int orc_run(orc_state *s, int method, int iters, int drop, double *resnorm, doub
       if (!isfin(delta) || !isfin(gamma)) { *flags |= ORC_FLAG_NONFINITE; break; }
       coef[2 * i] = delta;
       coef[2 * i + 1] = gamma;
+#pragma omp parallel for schedule(dynamic, 64) num_threads(s->nwork)
       for (int j = 0; j < n; j++) {
+        owork *w = wk(s);
         combine_col(s, COMB_LIN, delta, gamma, &s->Z[j], &s->P[j], &S[j]);
         col_copy(&s->P[j], &S[j]);
         if (dropD) drop_col(&s->P[j], s->capj[j]);
-        combine_col(s, COMB_ADD, 0.0, 0.0, &s->M[j], &S[j], &tmpc);
-        if (dropM) drop_col(&tmpc, s->capj[j]);
-        col_copy(&s->M[j], &tmpc);
+        combine_col(s, COMB_ADD, 0.0, 0.0, &s->M[j], &S[j], &w->c2);
+        if (dropM) drop_col(&w->c2, s->capj[j]);
+        col_copy(&s->M[j], &w->c2);
       }
       done++;
       s->it++;
     }
-    if (done == iters) resnorm[iters] = sqrt(residual_all(s, R, partial, tmp));
+    if (done == iters) resnorm[iters] = sqrt(residual_all(s, R, partial));
   } else if (base == ORC_CG) {
     /* Algorithm 3 with explicit residual: P_0 = D(R_0),
        P_{i+1} = D(R_{i+1} + beta P_i).  With Pi (Algorithm 7): Z = Pi R,
@@ -682,14 +749,16 @@ int orc_run(orc_state *s, int method, int iters, int drop, double *resnorm, doub
        numerator (R_i, R_i) or (R_i, Pi R_i). */
     double rz;
     if (!cont || s->it == 0) {
-      double rr0 = residual_all(s, R, partial, tmp);
+      double rr0 = residual_all(s, R, partial);
       resnorm[0] = sqrt(rr0);
       if (use_pi) {
-        for (int j = 0; j < n; j++) partial[j] = col_wnrm2(&R[j], s->pi, tmp);
+  #pragma omp parallel for schedule(dynamic, 64) num_threads(s->nwork)
+        for (int j = 0; j < n; j++) partial[j] = col_wnrm2(&R[j], s->pi, wk(s));
         rz = pairwise64(partial, n);
       } else {
         rz = rr0;
       }
+#pragma omp parallel for schedule(dynamic, 64) num_threads(s->nwork)
       for (int j = 0; j < n; j++) {
         if (use_pi) pi_col(s, &R[j], &s->P[j]);
         else col_copy(&s->P[j], &R[j]);
@@ -702,21 +771,25 @@ int orc_run(orc_state *s, int method, int iters, int drop, double *resnorm, doub
     for (int i = 0; i < iters; i++) {
       if (rz == 0.0) { *flags |= ORC_FLAG_CONVERGED; break; }
       product_all(s, s->P, Q);
-      for (int j = 0; j < n; j++) p2[j] = col_dot(&s->P[j], &Q[j], tmp);
+#pragma omp parallel for schedule(dynamic, 64) num_threads(s->nwork)
+      for (int j = 0; j < n; j++) p2[j] = col_dot(&s->P[j], &Q[j], wk(s));
       double pq = pairwise64(p2, n);
       if (pq == 0.0) { *flags |= ORC_FLAG_CONVERGED; break; }
       double alpha = rz / pq;
       if (!isfin(alpha)) { *flags |= ORC_FLAG_NONFINITE; break; }
+#pragma omp parallel for schedule(dynamic, 64) num_threads(s->nwork)
       for (int j = 0; j < n; j++) {
-        combine_col(s, COMB_AXPY, alpha, 0.0, &s->M[j], &s->P[j], &tmpc);
-        if (dropM) drop_col(&tmpc, s->capj[j]);
-        col_copy(&s->M[j], &tmpc);
+        owork *w = wk(s);
+        combine_col(s, COMB_AXPY, alpha, 0.0, &s->M[j], &s->P[j], &w->c2);
+        if (dropM) drop_col(&w->c2, s->capj[j]);
+        col_copy(&s->M[j], &w->c2);
       }
-      double rr1 = residual_all(s, R, partial, tmp);
+      double rr1 = residual_all(s, R, partial);
       resnorm[i + 1] = sqrt(rr1);
       double rz1 = rr1;
       if (use_pi) {
-        for (int j = 0; j < n; j++) partial[j] = col_wnrm2(&R[j], s->pi, tmp);
+  #pragma omp parallel for schedule(dynamic, 64) num_threads(s->nwork)
+        for (int j = 0; j < n; j++) partial[j] = col_wnrm2(&R[j], s->pi, wk(s));
         rz1 = pairwise64(partial, n);
       }
       double beta = rz1 / rz;
@@ -727,15 +800,17 @@ int orc_run(orc_state *s, int method, int iters, int drop, double *resnorm, doub
       s->rr = rz1;
       s->rr_hist = rr1;
       if (rz1 == 0.0) { *flags |= ORC_FLAG_CONVERGED; rz = rz1; break; }
+#pragma omp parallel for schedule(dynamic, 64) num_threads(s->nwork)
       for (int j = 0; j < n; j++) {
+        owork *w = wk(s);
         if (use_pi) {
           pi_col(s, &R[j], &S[j]);
-          combine_col(s, COMB_AXPY, beta, 0.0, &S[j], &s->P[j], &tmpc);
+          combine_col(s, COMB_AXPY, beta, 0.0, &S[j], &s->P[j], &w->c2);
         } else {
-          combine_col(s, COMB_AXPY, beta, 0.0, &R[j], &s->P[j], &tmpc);
+          combine_col(s, COMB_AXPY, beta, 0.0, &R[j], &s->P[j], &w->c2);
         }
-        if (dropD) drop_col(&tmpc, s->capj[j]);
-        col_copy(&s->P[j], &tmpc);
+        if (dropD) drop_col(&w->c2, s->capj[j]);
+        col_copy(&s->P[j], &w->c2);
       }
       rz = rz1;
     }
@@ -746,13 +821,11 @@ int orc_run(orc_state *s, int method, int iters, int drop, double *resnorm, doub
   mat_free(U, n);
   mat_free(V, n);
   mat_free(S, n);
-  col_free(&tmpc);
   free(partial);
   free(p2);
   free(p3);
   free(p4);
   free(p5);
-  free(tmp);
   return done;
 }
 
@@ -763,28 +836,25 @@ double orc_residual_norm(orc_state *s) {
   int mixed = s->mixed;
   s->av = s->a64;
   s->mixed = 0;
-  ocol am = {0}, r = {0};
   double *partial = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
-  double *tmp = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1) * 2);
+#pragma omp parallel for schedule(dynamic, 64) num_threads(s->nwork)
   for (int j = 0; j < n; j++) {
-    spgemm_col(s, &s->M[j], &am);
-    residual_col(s, j, &am, &r);
-    partial[j] = col_nrm2(&r, tmp);
+    owork *w = wk(s);
+    spgemm_col(s, w, &s->M[j], &w->c1);
+    residual_col(s, j, &w->c1, &w->c2);
+    partial[j] = col_nrm2(&w->c2, w);
   }
   double rr = pairwise64(partial, n);
   s->av = saved;
   s->mixed = mixed;
-  col_free(&am);
-  col_free(&r);
   free(partial);
-  free(tmp);
   return sqrt(rr);
 }
 
 /* R_j and (A P)_j of one column, for sampled checks of large runs */
 int orc_column_residual(orc_state *s, int j, int *rows, double *vals) {
   ocol am = {0}, r = {0};
-  spgemm_col(s, &s->M[j], &am);
+  spgemm_col(s, &s->work[0], &s->M[j], &am);
   residual_col(s, j, &am, &r);
   int L = r.len;
   if (rows) {
@@ -803,7 +873,7 @@ int orc_product_column(orc_state *s, int len, const int *rows, const double *val
                        double *out_vals) {
   ocol x = {0}, y = {0};
   for (int e = 0; e < len; e++) col_push(&x, rows[e], vals[e]);
-  spgemm_col(s, &x, &y);
+  spgemm_col(s, &s->work[0], &x, &y);
   int L = y.len;
   if (out_rows) {
     memcpy(out_rows, y.row, sizeof(int) * (size_t)L);
@@ -820,6 +890,7 @@ int orc_product_column(orc_state *s, int len, const int *rows, const double *val
 static void spmv_rows(int n, const int *rp, const int *ci, const double *v, const double *x, double *y,
                       double *tmp) {
   (void)tmp;
+#pragma omp parallel for schedule(static, 4096)
   for (int i = 0; i < n; i++) {
     double acc = 0.0;
     for (int q = rp[i]; q < rp[i + 1]; q++) acc = fma(v[q], x[ci[q]], acc);
@@ -832,7 +903,9 @@ static void spmv_rows(int n, const int *rp, const int *ci, const double *v, cons
  * the row result is widened to FP64. */
 static void spmv_rows_f32(int n, const int *rp, const int *ci, const float *v, const double *x,
                           double *y, float *x32) {
+#pragma omp parallel for schedule(static, 4096)
   for (int i = 0; i < n; i++) x32[i] = (float)x[i];
+#pragma omp parallel for schedule(static, 4096)
   for (int i = 0; i < n; i++) {
     float acc = 0.0f;
     for (int q = rp[i]; q < rp[i + 1]; q++) acc = fmaf(v[q], x32[ci[q]], acc);
@@ -841,6 +914,7 @@ static void spmv_rows_f32(int n, const int *rp, const int *ci, const float *v, c
 }
 
 static double vdot(int n, const double *x, const double *y, double *tmp) {
+#pragma omp parallel for schedule(static, 4096)
   for (int i = 0; i < n; i++) tmp[i] = x[i] * y[i];
   return pairwise64(tmp, n);
 }
@@ -960,6 +1034,7 @@ int orc_pcg(int n, const int *rp, const int *ci, const double *av, int precond, 
     double pq = vdot(n, p, q, tmp);
     if (pq == 0.0 || !isfin(pq)) { *status = 2; break; }
     double alpha = rho / pq;
+#pragma omp parallel for schedule(static, 4096)
     for (int i = 0; i < n; i++) {
       x[i] = fma(alpha, p[i], x[i]);
       r[i] = fma(-alpha, q[i], r[i]);
@@ -972,6 +1047,7 @@ int orc_pcg(int n, const int *rp, const int *ci, const double *av, int precond, 
     double rho1 = vdot(n, r, z, tmp);
     if (rho1 == 0.0 || !isfin(rho1)) { *status = 2; break; }
     double beta = rho1 / rho;
+#pragma omp parallel for schedule(static, 4096)
     for (int i = 0; i < n; i++) p[i] = fma(beta, p[i], z[i]);
     rho = rho1;
   }
