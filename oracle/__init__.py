@@ -67,8 +67,9 @@ def _load(omp: bool = False):
         lib.orc_new.argtypes = [C.c_int, p_i32, p_i32, p_f64, C.c_int, C.c_double]
         lib.orc_free.argtypes = [C.c_void_p]
         lib.orc_run.restype = C.c_int
-        lib.orc_run.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int, p_f64, p_f64,
+        lib.orc_run.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int, p_f64, p_f64, C.c_void_p,
                                 C.POINTER(C.c_int)]
+        lib.orc_set_keep_diag.argtypes = [C.c_void_p, C.c_int]
         lib.orc_nnz.restype = C.c_int64
         lib.orc_nnz.argtypes = [C.c_void_p, C.c_int]
         lib.orc_get.argtypes = [C.c_void_p, C.c_int, p_i32, p_i32, p_f64]
@@ -84,7 +85,7 @@ def _load(omp: bool = False):
         lib.orc_product_column.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
                                            C.c_void_p]
         lib.orc_drop_column.restype = C.c_int
-        lib.orc_drop_column.argtypes = [C.c_int, p_i32, p_f64, C.c_int]
+        lib.orc_drop_column.argtypes = [C.c_int, p_i32, p_f64, C.c_int, C.c_int]
         lib.orc_fixsum.restype = C.c_double
         lib.orc_fixsum.argtypes = [p_f64, C.c_int64]
         lib.orc_pairwise.restype = C.c_double
@@ -138,12 +139,22 @@ class Oracle:
             self.h = None
 
     def run(self, method, iters, drop=DROP_TOPK):
+        """Returns dict(done, resnorm[0..iters], coef[iters][2], nnz[0..iters],
+        flags); nnz[i] = nnz(M_i), the iterate whose residual resnorm[i] is
+        (-1 past an early stop)."""
         m = METHODS[method] if isinstance(method, str) else int(method)
         res = np.full(iters + 1, np.nan)
         coef = np.full(2 * max(iters, 1), np.nan)
+        nnz = np.full(iters + 1, -1, dtype=np.int64)
         flags = C.c_int(0)
-        done = self.lib.orc_run(self.h, m, int(iters), int(drop), res, coef, C.byref(flags))
-        return dict(done=done, resnorm=res, coef=coef.reshape(-1, 2), flags=flags.value)
+        done = self.lib.orc_run(self.h, m, int(iters), int(drop), res, coef, nnz.ctypes.data,
+                                C.byref(flags))
+        return dict(done=done, resnorm=res, coef=coef.reshape(-1, 2), nnz=nnz, flags=flags.value)
+
+    def set_keep_diag(self, on=True):
+        """Every later per-column drop keeps the column's diagonal entry
+        (Appendix A: the diagonal is never dropped); it counts toward cap_j."""
+        self.lib.orc_set_keep_diag(self.h, 1 if on else 0)
 
     def get(self, which=0):
         """CSC (colptr, rowind, vals) of M (0), P (1) or Z (2)."""
@@ -188,11 +199,12 @@ class Oracle:
         return rows[:L], vals[:L]
 
 
-def drop_column(rows, vals, cap):
-    """Hard-threshold one row-sorted column to ``cap`` entries (Sec. 6.1, per column)."""
+def drop_column(rows, vals, cap, keep_row=-1):
+    """Hard-threshold one row-sorted column to ``cap`` entries (Sec. 6.1, per
+    column); row ``keep_row`` (>= 0) is kept whenever present."""
     rows = np.array(rows, dtype=np.int32)
     vals = np.array(vals, dtype=np.float64)
-    L = _load().orc_drop_column(len(rows), rows, vals, int(cap))
+    L = _load().orc_drop_column(len(rows), rows, vals, int(cap), int(keep_row))
     return rows[:L], vals[:L]
 
 

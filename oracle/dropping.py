@@ -275,8 +275,9 @@ def run_global_lomr(n, rowptr, colind, vals, iters, m_dir, m_M, mixed=False, use
     """LOMR (Algorithm 4; LOMR_SPD, Algorithm 8, with Pi = diag(A)^{-1}) with
     global dropping in every iteration: Z_i = the m_dir largest entries of
     (Pi) R_i over the whole matrix; delta_i, gamma_i minimise over
-    span{A Z_i, A P_{i-1}} (Theorem 3, MR step when the 2x2 system is
-    near-singular, reading 6); S_i = delta_i Z_i + gamma_i P_{i-1};
+    span{A Z_i, A P_{i-1}} (Theorem 3; the paper does not treat a singular
+    2x2 system, so an MR step is taken when c <= 64 eps uu vv or vv = 0);
+    S_i = delta_i Z_i + gamma_i P_{i-1};
     P_i = the m_dir largest entries of S_i; M_{i+1} = Appendix A's heuristic
     of M_i + S_i with density cap m_M.  Returns dict(M, resnorm, coef, done,
     fallback)."""

@@ -99,6 +99,7 @@ typedef struct {
   double *pi;  /* pi_k = 1 / a_kk in FP64: the diagonal of Pi = diag(A)^{-1} */
   int mixed;
   int *capj;   /* per-column cap */
+  int keep_diag; /* 1: every per-column drop keeps the column's diagonal entry */
   /* iterates */
   ocol *M, *P, *Z;
   /* method continuation state */
@@ -410,22 +411,27 @@ static void combine_col(orc_state *s, int kind, double c1, double c2, const ocol
 typedef struct {
   double a;
   int r;
+  int keep; /* 1: the row that is always kept (the column's diagonal) */
 } dkey;
 
 static int cmp_dkey(const void *p, const void *q) {
   const dkey *u = (const dkey *)p, *w = (const dkey *)q;
+  if (u->keep != w->keep) return w->keep - u->keep;
   if (u->a > w->a) return -1;
   if (u->a < w->a) return 1;
   return (u->r > w->r) - (u->r < w->r);
 }
 
-/* hard thresholding of one column to its cap (Sec. 6.1, Eq. (6.2), per column) */
-static void drop_col(ocol *c, int cap) {
+/* hard thresholding of one column to its cap (Sec. 6.1, Eq. (6.2), per
+ * column); keep_row >= 0 (the column's diagonal, Appendix A's rule that the
+ * diagonal is never dropped) is kept whenever present and counts toward cap */
+static void drop_col(ocol *c, int cap, int keep_row) {
   if (c->len <= cap) return;
   dkey *k = (dkey *)malloc(sizeof(dkey) * (size_t)c->len);
   for (int e = 0; e < c->len; e++) {
     k[e].a = fabs(c->val[e]);
     k[e].r = c->row[e];
+    k[e].keep = c->row[e] == keep_row;
   }
   qsort(k, (size_t)c->len, sizeof(dkey), cmp_dkey);
   int *keep = (int *)malloc(sizeof(int) * (size_t)cap);
@@ -446,10 +452,10 @@ static void drop_col(ocol *c, int cap) {
 }
 
 /* test hook: drop one row-sorted column in place, returns the new length */
-int orc_drop_column(int len, int *rows, double *vals, int cap) {
+int orc_drop_column(int len, int *rows, double *vals, int cap, int keep_row) {
   ocol c = {0};
   for (int e = 0; e < len; e++) col_push(&c, rows[e], vals[e]);
-  drop_col(&c, cap);
+  drop_col(&c, cap, keep_row);
   for (int e = 0; e < c.len; e++) {
     rows[e] = c.row[e];
     vals[e] = c.val[e];
@@ -552,6 +558,9 @@ int orc_set_M(orc_state *s, const int *colptr, const int *rowind, const double *
   return 0;
 }
 
+/* every later per-column drop keeps the column's diagonal entry (on != 0) */
+void orc_set_keep_diag(orc_state *s, int on) { s->keep_diag = on != 0; }
+
 int64_t orc_nnz(const orc_state *s, int which) {
   const ocol *m = which == 0 ? s->M : which == 1 ? s->P : s->Z;
   int64_t t = 0;
@@ -607,6 +616,8 @@ static int isfin(double x) { return !isnan(x) && !isinf(x); }
  *   resnorm[0..iters]: ||R_i||_F (entries past an early stop are left alone)
  *   coef[2*i], coef[2*i+1]: (alpha_i, 0) for MR, (delta_i, gamma_i) for
  *   LOMR, (alpha_i, beta_{i+1}) for CG.
+ *   nnzhist[0..iters] (may be NULL): nnz(M_i) of the iterate whose residual
+ *   resnorm[i] records.
  * ORC_MR_PI / ORC_LOMR_PI / ORC_CG_PI run the Pi-preconditioned forms
  * (Algorithms 5, 8, 7 with Pi = diag(A)^{-1}): the direction is built from
  * Z = Pi R instead of R, and every coefficient inner product is the
@@ -614,8 +625,11 @@ static int isfin(double x) { return !isnan(x) && !isinf(x); }
  * records ||R_i||_F.
  * Returns the number of iterations done; *flags gets ORC_FLAG_* bits.
  */
-int orc_run(orc_state *s, int method, int iters, int drop, double *resnorm, double *coef, int *flags) {
+int orc_run(orc_state *s, int method, int iters, int drop, double *resnorm, double *coef,
+            int64_t *nnzhist, int *flags) {
   int n = s->n;
+#define KEEP(j) (s->keep_diag ? (j) : -1)
+#define NNZ(i) do { if (nnzhist) nnzhist[i] = orc_nnz(s, 0); } while (0)
   const int use_pi = method >= ORC_MR_PI;
   const int base = use_pi ? method - ORC_MR_PI : method;
   int done = 0;
@@ -641,6 +655,7 @@ int orc_run(orc_state *s, int method, int iters, int drop, double *resnorm, doub
     /* Algorithm 1 with explicit residual, P_i = D(R_i); with Pi
        (Algorithm 5): P_i = D(Pi R_i), alpha = (Pi R, A P) / (A P, Pi A P) */
     for (int i = 0; i < iters; i++) {
+      NNZ(i);
       double rr = residual_all(s, R, partial);
       resnorm[i] = sqrt(rr);
       if (rr == 0.0) { *flags |= ORC_FLAG_CONVERGED; break; }
@@ -648,7 +663,7 @@ int orc_run(orc_state *s, int method, int iters, int drop, double *resnorm, doub
       for (int j = 0; j < n; j++) {
         if (use_pi) pi_col(s, &R[j], &s->P[j]);
         else col_copy(&s->P[j], &R[j]);
-        if (dropD) drop_col(&s->P[j], s->capj[j]);
+        if (dropD) drop_col(&s->P[j], s->capj[j], KEEP(j));
       }
       product_all(s, s->P, Q);
 #pragma omp parallel for schedule(dynamic, 64) num_threads(s->nwork)
@@ -667,18 +682,22 @@ int orc_run(orc_state *s, int method, int iters, int drop, double *resnorm, doub
       for (int j = 0; j < n; j++) {
         owork *w = wk(s);
         combine_col(s, COMB_AXPY, alpha, 0.0, &s->M[j], &s->P[j], &w->c2);
-        if (dropM) drop_col(&w->c2, s->capj[j]);
+        if (dropM) drop_col(&w->c2, s->capj[j], KEEP(j));
         col_copy(&s->M[j], &w->c2);
       }
       done++;
       s->it++;
     }
-    if (done == iters) resnorm[iters] = sqrt(residual_all(s, R, partial));
+    if (done == iters) {
+      NNZ(iters);
+      resnorm[iters] = sqrt(residual_all(s, R, partial));
+    }
   } else if (base == ORC_LOMR) {
     /* Algorithm 4 with explicit residual: Z_i = D(R_i), P_i = D(S_i),
        M_{i+1} = D(M_i + S_i), S_i = delta Z_i + gamma P_{i-1}. s->P holds
        P_{i-1} between iterations. */
     for (int i = 0; i < iters; i++) {
+      NNZ(i);
       double rr = residual_all(s, R, partial);
       resnorm[i] = sqrt(rr);
       if (rr == 0.0) { *flags |= ORC_FLAG_CONVERGED; break; }
@@ -686,7 +705,7 @@ int orc_run(orc_state *s, int method, int iters, int drop, double *resnorm, doub
       for (int j = 0; j < n; j++) {
         if (use_pi) pi_col(s, &R[j], &s->Z[j]);
         else col_copy(&s->Z[j], &R[j]);
-        if (dropD) drop_col(&s->Z[j], s->capj[j]);
+        if (dropD) drop_col(&s->Z[j], s->capj[j], KEEP(j));
       }
       product_all(s, s->Z, U);
       product_all(s, s->P, V);
@@ -732,15 +751,18 @@ int orc_run(orc_state *s, int method, int iters, int drop, double *resnorm, doub
         owork *w = wk(s);
         combine_col(s, COMB_LIN, delta, gamma, &s->Z[j], &s->P[j], &S[j]);
         col_copy(&s->P[j], &S[j]);
-        if (dropD) drop_col(&s->P[j], s->capj[j]);
+        if (dropD) drop_col(&s->P[j], s->capj[j], KEEP(j));
         combine_col(s, COMB_ADD, 0.0, 0.0, &s->M[j], &S[j], &w->c2);
-        if (dropM) drop_col(&w->c2, s->capj[j]);
+        if (dropM) drop_col(&w->c2, s->capj[j], KEEP(j));
         col_copy(&s->M[j], &w->c2);
       }
       done++;
       s->it++;
     }
-    if (done == iters) resnorm[iters] = sqrt(residual_all(s, R, partial));
+    if (done == iters) {
+      NNZ(iters);
+      resnorm[iters] = sqrt(residual_all(s, R, partial));
+    }
   } else if (base == ORC_CG) {
     /* Algorithm 3 with explicit residual: P_0 = D(R_0),
        P_{i+1} = D(R_{i+1} + beta P_i).  With Pi (Algorithm 7): Z = Pi R,
@@ -748,6 +770,7 @@ int orc_run(orc_state *s, int method, int iters, int drop, double *resnorm, doub
        beta = (R_{i+1}, Z_{i+1}) / (R_i, Z_i).  s->P holds P_i, s->rr the
        numerator (R_i, R_i) or (R_i, Pi R_i). */
     double rz;
+    NNZ(0);
     if (!cont || s->it == 0) {
       double rr0 = residual_all(s, R, partial);
       resnorm[0] = sqrt(rr0);
@@ -762,7 +785,7 @@ int orc_run(orc_state *s, int method, int iters, int drop, double *resnorm, doub
       for (int j = 0; j < n; j++) {
         if (use_pi) pi_col(s, &R[j], &s->P[j]);
         else col_copy(&s->P[j], &R[j]);
-        if (dropD) drop_col(&s->P[j], s->capj[j]);
+        if (dropD) drop_col(&s->P[j], s->capj[j], KEEP(j));
       }
     } else {
       rz = s->rr;
@@ -781,9 +804,10 @@ int orc_run(orc_state *s, int method, int iters, int drop, double *resnorm, doub
       for (int j = 0; j < n; j++) {
         owork *w = wk(s);
         combine_col(s, COMB_AXPY, alpha, 0.0, &s->M[j], &s->P[j], &w->c2);
-        if (dropM) drop_col(&w->c2, s->capj[j]);
+        if (dropM) drop_col(&w->c2, s->capj[j], KEEP(j));
         col_copy(&s->M[j], &w->c2);
       }
+      NNZ(i + 1);
       double rr1 = residual_all(s, R, partial);
       resnorm[i + 1] = sqrt(rr1);
       double rz1 = rr1;
@@ -809,7 +833,7 @@ int orc_run(orc_state *s, int method, int iters, int drop, double *resnorm, doub
         } else {
           combine_col(s, COMB_AXPY, beta, 0.0, &R[j], &s->P[j], &w->c2);
         }
-        if (dropD) drop_col(&w->c2, s->capj[j]);
+        if (dropD) drop_col(&w->c2, s->capj[j], KEEP(j));
         col_copy(&s->P[j], &w->c2);
       }
       rz = rz1;
@@ -826,6 +850,8 @@ int orc_run(orc_state *s, int method, int iters, int drop, double *resnorm, doub
   free(p3);
   free(p4);
   free(p5);
+#undef KEEP
+#undef NNZ
   return done;
 }
 

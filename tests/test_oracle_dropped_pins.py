@@ -234,3 +234,93 @@ def test_mr_dropped_direction_steps_match_brute_force():
             Mp = _nz({k: _fl(Fraction(a) * Fraction(P[j].get(k, 0.0)) + Fraction(M[j].get(k, 0.0)))
                       for k in set(M[j]) | set(P[j])})
             assert Mo[j] == _brute_drop(Mp, caps[j]), (i, j)
+
+
+def _brute_drop_keep(col, cap, keep_row):
+    """The drop with the column's diagonal always kept (it counts toward the
+    cap): the diagonal, then the cap - 1 largest |v| of the other rows."""
+    if len(col) <= cap:
+        return dict(col)
+    if keep_row not in col:
+        return _brute_drop(col, cap)
+    rest = {r: x for r, x in col.items() if r != keep_row}
+    out = _brute_drop(rest, cap - 1) if cap > 1 else {}
+    out[keep_row] = col[keep_row]
+    return out
+
+
+def test_drop_column_keep_diag_brute_force():
+    rng = np.random.default_rng(7)
+    for trial in range(300):
+        L = int(rng.integers(1, 50))
+        rows = np.sort(rng.choice(200, L, replace=False))
+        vals = rng.choice([-0.5, -0.25, 0.25, 0.5, 1.0, 3.0, 1e-3], L) * rng.choice([1.0, 0.999], L)
+        cap = int(rng.integers(1, 30))
+        keep = int(rows[rng.integers(0, L)]) if trial % 4 else 999  # 999: absent
+        r1, v1 = O.drop_column(rows, vals, cap, keep_row=keep)
+        want = _brute_drop_keep(dict(zip(rows.tolist(), vals.tolist())), cap, keep)
+        assert dict(zip(r1.tolist(), v1.tolist())) == want
+    # the smallest entry survives when it is the diagonal
+    r, v = O.drop_column([1, 3, 5], [5.0, -1e-9, 4.0], 2, keep_row=3)
+    assert list(r) == [1, 3] and list(v) == [5.0, -1e-9]
+
+
+@pytest.mark.parametrize("method", ["mr", "lomr", "cg"])
+def test_keep_diag_steps_match_brute_force(method):
+    """With keep_diag every per-column drop (of M and of the directions)
+    keeps row j of column j: one LOMR/MR/CG step rebuilt densely with that
+    drop equals the oracle's, and M's diagonal never vanishes."""
+    n, rp, ci, v = I.varcoef_grid((4, 4), seed=9)
+    A = I.csr_to_dense(n, rp, ci, v)
+    f = 0.6
+    caps = _caps(n, rp, f)
+    o = O.Oracle(n, rp, ci, v, cap_factor=f)
+    o.set_keep_diag(True)
+    if method == "cg":
+        o.run("cg", 0)
+    for i in range(4):
+        M = _cols(o.get(0))
+        R = _residual_cols(o, n)
+        Pprev = _cols(o.get(1))
+        r = o.run(method, 1)
+        a, g = r["coef"][0]
+        Mo, Po = _cols(o.get(0)), _cols(o.get(1))
+        for j in range(n):
+            if method == "mr":
+                P = _brute_drop_keep(R[j], caps[j], j)
+                assert Po[j] == P
+                Mp = _nz({k: _fl(Fraction(a) * Fraction(P.get(k, 0.0)) + Fraction(M[j].get(k, 0.0)))
+                          for k in set(M[j]) | set(P)})
+            elif method == "cg":
+                Mp = _nz({k: _fl(Fraction(a) * Fraction(Pprev[j].get(k, 0.0))
+                                 + Fraction(M[j].get(k, 0.0)))
+                          for k in set(M[j]) | set(Pprev[j])})
+            else:
+                Z = _brute_drop_keep(R[j], caps[j], j)
+                assert _cols(o.get(2))[j] == Z
+                S = _nz({k: _fl(Fraction(a) * Fraction(Z.get(k, 0.0))
+                                + Fraction(g * Pprev[j].get(k, 0.0)))
+                         for k in set(Z) | set(Pprev[j])})
+                assert Po[j] == _brute_drop_keep(S, caps[j], j)
+                Mp = _nz({k: _fl(Fraction(M[j].get(k, 0.0)) + Fraction(S.get(k, 0.0)))
+                          for k in set(M[j]) | set(S)})
+            assert Mo[j] == _brute_drop_keep(Mp, caps[j], j), (i, j)
+            assert j in Mo[j]
+        assert r["nnz"][0] == sum(len(c) for c in M)
+        assert r["nnz"][1] == sum(len(c) for c in Mo)
+
+
+@pytest.mark.parametrize("method", ["mr", "lomr", "cg"])
+def test_nnz_history_counts_the_iterates(method):
+    """nnz[i] is nnz(M_i) of the iterate whose residual resnorm[i] records:
+    checked against the iterate exported after each single step."""
+    n, rp, ci, v = I.laplacian_2d_5pt(6)
+    o = O.Oracle(n, rp, ci, v, cap_factor=2.0)
+    o2 = O.Oracle(n, rp, ci, v, cap_factor=2.0)
+    r = o.run(method, 5)
+    seen = [int(o2.get(0)[0][-1])]
+    for i in range(5):
+        o2.run(method, 1)
+        seen.append(int(o2.get(0)[0][-1]))
+    assert list(r["nnz"]) == seen
+    assert seen[0] == n and seen[-1] > seen[1] > n

@@ -621,6 +621,39 @@ def test_fpmr_gradient_matches_central_differences(K):
         assert abs(fd - g[e]) <= 1e-6 * max(abs(g).max(), 1e-300), (e, fd, g[e])
 
 
+@pytest.mark.parametrize("K", [1, 3, 10])
+def test_fplomr_gradient_matches_central_differences(K):
+    """Fixed-pattern LOMR (Algorithm 4 / Theorem 3 on supp(A)): the hand-written
+    adjoint against central differences (h = 1e-6 relative) on 50 entries."""
+    from oracle import fpmr
+    n, rp, ci, v = I.varcoef_3d_7pt(6, seed=4)
+    loss, g = fpmr.gradient_lomr(n, rp, ci, v, K)
+    rng = np.random.default_rng(100 + K)
+    for e in rng.choice(len(v), 50, replace=False):
+        h = 1e-6 * abs(v[e])
+        vp, vm = v.copy(), v.copy()
+        vp[e] += h
+        vm[e] -= h
+        fd = (fpmr.forward_lomr(n, rp, ci, vp, K) - fpmr.forward_lomr(n, rp, ci, vm, K)) / (2 * h)
+        assert abs(fd - g[e]) <= 1e-6 * max(abs(g).max(), 1e-300), (e, fd, g[e])
+
+
+def test_fplomr_first_step_is_the_mr_step():
+    """With P_{-1} = 0 the first LOMR step is the MR step (Algorithm 4), so one
+    step of each gives the same loss and gradient; later LOMR steps reach a
+    loss no larger than MR's from the same iterate (Eq. 4.3): checked from
+    M_1 on by a step of each."""
+    from oracle import fpmr
+    n, rp, ci, v = I.varcoef_grid((5, 6), seed=8)
+    l1, g1 = fpmr.gradient_lomr(n, rp, ci, v, 1)
+    l2, g2 = fpmr.gradient(n, rp, ci, v, 1)
+    assert abs(l1 - l2) <= 1e-13 * l2
+    np.testing.assert_allclose(g1, g2, rtol=1e-10, atol=1e-12 * abs(g2).max())
+    _, st = fpmr.forward_lomr(n, rp, ci, v, 2, keep=True)
+    assert not st["coefs"][1][2]  # a genuine 2-D step
+    assert fpmr.forward_lomr(n, rp, ci, v, 2) <= fpmr.forward(n, rp, ci, v, 2) * (1 + 1e-12)
+
+
 # ------------------------------------------ global dropping (Sec. 6.1, App. A)
 
 def test_hard_threshold_global_cap_brute_force():
@@ -806,8 +839,8 @@ def _round_f32(q):
 def test_product_column_is_the_exact_rounded_fma_chain():
     """A X_j, both precisions, against an independent construction: each
     fma of the ascending-k chain acc = fma(a_rk, x_k, acc) evaluated exactly
-    on rationals and rounded once to FP64 or FP32 (reading 10; the mixed
-    path rounds A's values to FP32 first, reading 11)."""
+    on rationals and rounded once to FP64 or FP32 (the fixed order of the
+    product chain; the mixed path rounds A's values to FP32 first)."""
     from fractions import Fraction
     n, rp, ci, v = I.varcoef_grid((7, 8), seed=21)
     rng = np.random.default_rng(3)
@@ -834,7 +867,8 @@ def test_product_column_is_the_exact_rounded_fma_chain():
 def test_column_residual_is_exact_chain_then_one_rounding():
     """R_j = e_j - A M_j: the exact-rational fma chain of A M_j, then 1 - s on
     the diagonal rounded once to the value type and -s elsewhere, exact
-    zeros removed (reading 10), for the stored M after a few MR steps."""
+    zeros removed (supp holds nonzeros only, Sec. 6.1), for the stored M after
+    a few MR steps."""
     from fractions import Fraction
     n, rp, ci, v = I.varcoef_grid((6, 7), seed=22)
     for mixed in (False, True):
@@ -864,7 +898,7 @@ def _cols(X):
 
 
 def test_update_combinations_are_single_roundings():
-    """The iterate updates of reading 10, checked entry by entry against exact
+    """The iterate updates in their fixed rounding order, checked entry by entry against exact
     rational arithmetic: MR and CG M+ = fl(m + alpha p); CG P+ = fl(r + beta p);
     LOMR S = fl(delta z + fl(gamma p)), P = S, M+ = fl(m + s), each rounded
     once to FP64 (then once more to FP32 on the mixed path), exact zeros

@@ -27,7 +27,7 @@ def _rank(rank, world, port, out):
 
 def test_max_over_ranks_and_job_throughput_with_two_gloo_ranks():
     port = 29500 + (os.getpid() % 1000)
-    with mp.Manager() as mgr:
+    with mp.get_context("spawn").Manager() as mgr:  # no fork of a threaded process
         out = mgr.dict()
         mp.spawn(_rank, args=(2, port, out), nprocs=2, join=True)
         res = dict(out)
