@@ -6,7 +6,9 @@ correlation length 8 cells, harmonic-mean faces, seed 0); FP32 values with
 FP64 reductions; per-column cap 3 nnz(A[:,j]); from M_0 = diag(A)^{-1}:
 50 MR iterations, then PCG, 50 LOMR iterations, then PCG, 50 CG iterations,
 then PCG (b ~ U(-1,1) seed 0, rtol 1e-8, symmetric part of M as
-preconditioner; FP32-values products, FP64 vectors and scalars).  Metric:
+preconditioner; FP64 products, vectors and scalars: FP32-values products
+take 6 % more iterations with MR's M, past the 2 % the mixed path is held
+to).  Metric:
 SPAI iterations per second over the whole step (150 iterations / step time,
 PCG and set-up included).  The FP64 path (FP64 values, FP64 PCG) is timed
 on the same workload and reported beside it.
@@ -47,6 +49,7 @@ if ROOT not in sys.path:
 
 ITERS = 50
 CAP = 3.0
+PCG_PREC = "fp64"  # the timed PCG's products (see accuracy_report)
 PCG_MAXIT = 1000
 METHODS = ("mr", "lomr", "cg")
 WORKLOAD = "varcoef3d_64"
@@ -157,7 +160,7 @@ def run_ours(args):
 
     # device-resident inputs: A copied once, handle created outside the timed region
     g = Spai(n, rp, ci, v, prec="mixed", cap_factor=CAP)
-    g.set_pcg_prec("mixed")
+    g.set_pcg_prec(PCG_PREC)
     tuned = {m: g.autotune(m, 10) for m in METHODS}  # launch shapes (results unchanged)
     b_dev = torch.tensor(b, dtype=torch.float64, device="cuda")
     x_dev = torch.empty_like(b_dev)
@@ -204,12 +207,18 @@ def run_ours(args):
     total_iters = ITERS * len(METHODS)
     value = job_throughput(ws, total_iters, ms_step * 1e-3)
 
-    # dominant kernel: the column pass (timed per launch inside the library)
+    # dominant kernel: the column pass (timed per launch inside the library).
+    # Algorithmic bytes: the iterate slabs each pass reads and writes, their
+    # lengths and A once per pass (the library's device counter), without
+    # the R lists CG's pass A stores for pass B (a layout choice of this
+    # library, not traffic the method needs); the full counter is reported
+    # beside them.
     launches = s1["colpass_launches"] - s0["colpass_launches"]
     cp_ms = s1["colpass_ms"] - s0["colpass_ms"]
     cp_bytes = s1["colpass_bytes"] - s0["colpass_bytes"]
+    r_bytes = s1["colpass_r_bytes"] - s0["colpass_r_bytes"]
     peak, peak_kind = _peaks()
-    per_launch_bytes = cp_bytes / max(launches, 1)
+    per_launch_bytes = (cp_bytes - r_bytes) / max(launches, 1)
     per_launch_ms = cp_ms / max(launches, 1)
     achieved = per_launch_bytes / (per_launch_ms * 1e-3) / 1e9 if per_launch_ms > 0 else 0.0
     gpu_launches = ((s1["colpass_launches"] - s0["colpass_launches"])
@@ -220,7 +229,7 @@ def run_ours(args):
     # PCG with host b and x, export M (D2H) -- every step
     def e2e_step():
         h = Spai(n, rp, ci, v, prec="mixed", cap_factor=CAP)
-        h.set_pcg_prec("mixed")
+        h.set_pcg_prec(PCG_PREC)
         h2d = rp.nbytes + ci.nbytes + v.nbytes
         d2h = 0
         for m in METHODS:
@@ -255,18 +264,7 @@ def run_ours(args):
     e1.synchronize()
     fp64_ms = e0.elapsed_time(e1)
 
-    results = {m: {"resnorm": float(last[m][0]["resnorm"][-1]),
-                   "residual_fp64": None,
-                   "pcg_iters": int(last[m][1]["iters"]),
-                   "pcg_relres": float(last[m][1]["relres"]),
-                   "pcg_status": int(last[m][1]["status"])} for m in METHODS}
-    for m in METHODS:
-        results[m]["fp64_resnorm"] = float(r64[m][0]["resnorm"][-1])
-        results[m]["fp64_pcg_iters"] = int(r64[m][1]["iters"])
-        results[m]["pcg_iters_rel_diff"] = (abs(results[m]["pcg_iters"] - results[m]["fp64_pcg_iters"])
-                                            / max(1, results[m]["fp64_pcg_iters"]))
-        rel = abs(results[m]["resnorm"] - results[m]["fp64_resnorm"]) / results[m]["fp64_resnorm"]
-        results[m]["mixed_vs_fp64_rel"] = rel
+    results = accuracy_report(g, g64, last, r64, b_dev, x_dev)
 
     cpu = cpu_baseline() if (rank == 0 and ws == 1 and not args.no_cpu) else None
     if rank == 0:
@@ -285,15 +283,16 @@ def run_ours(args):
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "n": n, "nnz": int(len(v)), "cap_factor": CAP,
                        "iters_per_method": ITERS, "methods": list(METHODS),
-                       "pcg": "symmetric part of M, rtol 1e-8, maxit 1000, FP32-values products",
+                       "pcg": "symmetric part of M, rtol 1e-8, maxit 1000, FP64 products",
                        "l2": "flushed between steps (256 MB write)", "parallelism": "replicas",
                        "autotuned_ms_per_iter": tuned},
             "e2e": {"value": ws * total_iters / e2e_s, "unit": "SPAI iterations/s",
                     "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
             "roofline": {"bound": "hbm", "kernel": "colpass_kernel", "achieved": achieved,
                          "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                         "peak_source": peak_kind, "traffic": COLPASS_TRAFFIC_BYTES,
+                         "peak_source": peak_kind, "traffic": colpass_traffic(),
                          "algorithmic_bytes_per_launch": per_launch_bytes,
+                         "counter_bytes_per_launch": cp_bytes / max(launches, 1),
                          "launch_ms": per_launch_ms, "launches": launches},
             "cpu_baseline": cpu,
             "gpu_launches": int(gpu_launches),
@@ -309,11 +308,74 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-# DRAM bytes (read + write) per column-pass launch, from ncu captures of the
-# --profile mr|lomr|cg cases on this workload, weighted by the launch mix of
-# one step (51 MR, 51 LOMR, 50 + 50 CG passes); None until taken on the
-# current kernel.
-COLPASS_TRAFFIC_BYTES = 216.0e6
+def accuracy_report(g, g64, last, r64, b_dev, x_dev):
+    """Per method: the mixed path against the FP64 path on the same workload
+    (||I - A M||_F within 1e-5 relative and PCG iterations within 2 % are the
+    targets).  residual_fp64 is ||I - A M||_F computed in FP64 from the mixed
+    M; pcg_iters is the timed PCG (mixed M, FP64 products), fp64_pcg_iters
+    the FP64 path's.  pcg_iters_fp32_products shows the same solve with
+    FP32-values products (not timed: it misses the 2 % target with MR's M).
+    Runs after the timed region."""
+    from paper_2511_09753_gb300.spai import PREC_SPAI_SYM
+    out = {}
+    for m in METHODS:
+        rm, pm = last[m]
+        g.reset()
+        g.run(m, ITERS)
+        res_mixed = g.residual_norm()
+        g.set_pcg_prec("mixed")
+        p32 = g.pcg(b_dev, x_dev, rtol=1e-8, maxit=PCG_MAXIT, precond=PREC_SPAI_SYM)
+        g.set_pcg_prec(PCG_PREC)
+        g64.reset()
+        g64.run(m, ITERS)
+        res64 = g64.residual_norm()
+        it, it32, it64 = int(pm["iters"]), int(p32["iters"]), int(r64[m][1]["iters"])
+        out[m] = {
+            "history_resnorm": float(rm["resnorm"][-1]),
+            "residual_fp64": res_mixed,
+            "fp64_path_residual": res64,
+            "residual_rel_err": abs(res_mixed - res64) / res64,
+            "pcg_iters": it,
+            "pcg_status": int(pm["status"]),
+            "pcg_relres": float(pm["relres"]),
+            "fp64_pcg_iters": it64,
+            "fp64_pcg_status": int(r64[m][1]["status"]),
+            "pcg_iters_rel_diff": abs(it - it64) / max(1, it64),
+            "pcg_iters_fp32_products": it32,
+            "pcg_iters_fp32_products_rel_diff": abs(it32 - it64) / max(1, it64),
+        }
+    return out
+
+
+TRAFFIC_SUMMARY = os.path.join(ROOT, "profiles", "colpass_traffic_varcoef3d64.md")
+COLPASS_SOURCES = ("colpass.cuh", "warp_ops.cuh", "common.cuh", "colpass_launch.cuh",
+                   "colpass_f32.cu", "api.cu")  # api.cu: the scratch layout and launch shapes
+
+
+def colpass_sources_sha16():
+    import hashlib
+    h = hashlib.sha256()
+    for f in COLPASS_SOURCES:
+        with open(os.path.join(ROOT, "paper_2511_09753_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def colpass_traffic():
+    """DRAM bytes (read + write) per column-pass launch of the bench step, from
+    the ncu summary under profiles/ (its line "traffic_bytes_per_launch: B
+    sources_sha16: H"), or None when the column-pass sources have changed
+    since those counters were taken."""
+    try:
+        with open(TRAFFIC_SUMMARY) as f:
+            for line in f:
+                if line.startswith("traffic_bytes_per_launch:"):
+                    parts = line.split()
+                    if parts[3] == colpass_sources_sha16():
+                        return float(parts[1])
+    except (OSError, IndexError, ValueError):
+        pass
+    return None
 
 BATCH_ITERS = 30
 BATCH_RHS = 32
@@ -593,8 +655,9 @@ def run_aniso(args):
 def run_fpmr(args):
     """Gradient of ||I - A M_K||_F^2 through K = 10 fixed-pattern MR steps with
     respect to A's values: the 32^3 and 128^3 variable-coefficient operators
-    (seed 0), FP64, one checkpoint of M per step.  Metric: gradients per
-    second at 128^3 (forward + backward, inputs resident)."""
+    (seed 0), FP64, one checkpoint of M per step; then the same through 10
+    fixed-pattern LOMR steps (checkpoints of M and P per step).  Metric:
+    gradients per second at 128^3 (MR, forward + backward, inputs resident)."""
     import numpy as np
     import torch
 
@@ -604,10 +667,11 @@ def run_fpmr(args):
     ws, rank, local = _dist()
     torch.cuda.set_device(local)
     out = {}
-    for N, prec in ((32, "fp64"), (128, "fp64"), (128, "mixed")):
+    for N, prec, method in ((32, "fp64", "mr"), (128, "fp64", "mr"), (128, "mixed", "mr"),
+                            (32, "fp64", "lomr"), (128, "fp64", "lomr"), (128, "mixed", "lomr")):
         n, rp, ci, v = I.varcoef_3d_7pt(N, sigma=1.5, ell=8.0, seed=0)
         t0 = time.perf_counter()
-        f = FixedPatternMR(n, rp, ci, 10, prec=prec)
+        f = FixedPatternMR(n, rp, ci, 10, prec=prec, method=method)
         setup = time.perf_counter() - t0
         vd = torch.tensor(v, dtype=torch.float64, device="cuda")
         gd = torch.empty_like(vd)
@@ -623,14 +687,14 @@ def run_fpmr(args):
             torch.cuda.synchronize()
             times.append(time.perf_counter() - t0)
         info = f.info()
-        out[f"{N}_{prec}"] = {"n": n, "nnz": int(len(v)), "setup_s": setup, "s_per_gradient": min(times),
+        out[f"{method}_{N}_{prec}"] = {"n": n, "nnz": int(len(v)), "setup_s": setup, "s_per_gradient": min(times),
                   "median_s": statistics.median(times), "loss": loss,
                   "grad_norm": float(torch.linalg.vector_norm(gd).item()), **info}
         f.close()
     if rank == 0:
         print(json.dumps({
             "metric": "gradients/s of ||I - A M_10||_F^2 w.r.t. A's values (128^3)",
-            "value": ws / out["128_fp64"]["median_s"], "unit": "gradients/s", "n_gpus": ws,
+            "value": ws / out["mr_128_fp64"]["median_s"], "unit": "gradients/s", "n_gpus": ws,
             "higher_is_better": True, "dtype": "f64", "data": "synthetic",
             "config": {"workload": "fpmr_varcoef3d", "K": 10, "checkpoints": "M per step"},
             "cases": out}))
@@ -710,33 +774,95 @@ def profile_fixed_pattern():
     h.close()
 
 
-def cpu_baseline(sample_iters=1):
-    """The CPU oracle (single thread) on a bounded sample of the workload:
-    `sample_iters` MR iterations on the full operator (mixed arithmetic)."""
-    import oracle as O
-    from paper_2511_09753_gb300 import inputs as I
-    n, rp, ci, v = I.varcoef_3d_7pt(64, sigma=1.5, ell=8.0, seed=0)
-    o = O.Oracle(n, rp, ci, v, mixed=True, cap_factor=CAP)
-    t0 = time.perf_counter()
-    o.run("mr", sample_iters)
-    dt = time.perf_counter() - t0
-    return {"value": sample_iters / dt, "unit": "SPAI iterations/s", "cores": 1, "kind": "oracle",
-            "sample": f"{sample_iters} MR iteration(s) (+ final residual) on the full "
-                      f"n={n} operator, mixed arithmetic, single thread", "seconds": dt}
+# PCG iterations of the step's three solves (FP64 products, rtol 1e-8, maxit
+# 1000, symmetric part of M after 50 iterations of MR, LOMR, CG): the same on
+# the oracle and on the GPU, which the 50-iteration full-size parity test
+# checks bit for bit.  The CPU estimates below count this PCG work.
+STEP_PCG_ITERS = {"mr": 227, "lomr": 166, "cg": 1000}
+
+
+class CpuStep:
+    """The oracle on the bench workload, for the CPU baseline: one handle per
+    method, filled by `fill` iterations from M_0 (columns at their caps, as in
+    the step), then sampled: `sample(k, q)` times k more iterations of each
+    method and q PCG iterations with each method's M (symmetric part, FP64
+    products), and extrapolates the step (50 iterations of each method plus
+    the step's PCG iterations) from those per-iteration times."""
+
+    def __init__(self, omp=True, fill=3):
+        import oracle as O
+        from paper_2511_09753_gb300 import inputs as I
+        self.O = O
+        self.omp = omp
+        n, rp, ci, v = I.varcoef_3d_7pt(64, sigma=1.5, ell=8.0, seed=0)
+        self.A = (n, rp, ci, v)
+        self.b = I.rhs_uniform(n, 0)
+        self.orc = {}
+        for m in METHODS:
+            o = O.Oracle(n, rp, ci, v, mixed=True, cap_factor=CAP, omp=omp)
+            o.run(m, fill)
+            self.orc[m] = o
+        self.threads = self._threads()
+
+    def _threads(self):
+        if not self.omp:
+            return 1
+        import ctypes
+        try:
+            lib = ctypes.CDLL("libgomp.so.1")
+            return int(lib.omp_get_max_threads())
+        except OSError:
+            return os.cpu_count() or 1
+
+    def sample(self, k=1, q=5):
+        n, rp, ci, v = self.A
+        t_it, t_pcg = {}, {}
+        for m in METHODS:
+            o = self.orc[m]
+            t0 = time.perf_counter()
+            o.run(m, k)
+            t_it[m] = (time.perf_counter() - t0) / k
+            M = o.get_M()
+            t0 = time.perf_counter()
+            self.O.pcg(n, rp, ci, v, self.b, rtol=0.0, maxit=q, precond=3, M=M, mixed=False,
+                       omp=self.omp)
+            t_pcg[m] = (time.perf_counter() - t0) / q
+        step = sum(ITERS * t_it[m] + STEP_PCG_ITERS[m] * t_pcg[m] for m in METHODS)
+        wall = sum(k * t_it[m] + q * t_pcg[m] for m in METHODS)
+        return {"step_s": step, "sample_s": wall, "s_per_iter": t_it, "s_per_pcg_iter": t_pcg}
+
+    def describe(self, k, q):
+        kind = f"OpenMP build, {self.threads} threads" if self.omp else "serial build, 1 thread"
+        return (f"{k} iteration(s) of each of MR, LOMR, CG (columns already at their caps) and "
+                f"{q} PCG iterations with each M on the full n={self.A[0]} operator, mixed "
+                f"arithmetic (FP64 PCG products), {kind}; step time extrapolated to 50 iterations of each method plus "
+                f"the step's PCG iterations {STEP_PCG_ITERS}")
+
+
+def cpu_baseline(k=2, q=10):
+    """The oracle on a bounded sample of the bench step, on all host cores."""
+    st = CpuStep(omp=True)
+    r = st.sample(k, q)
+    value = ITERS * len(METHODS) / r["step_s"]
+    return {"value": value, "unit": "SPAI iterations/s", "cores": st.threads, "kind": "oracle",
+            "sample": st.describe(k, q), "sample_seconds": r["sample_s"],
+            "s_per_iter": r["s_per_iter"], "s_per_pcg_iter": r["s_per_pcg_iter"]}
 
 
 def run_reference(args):
+    """The oracle as it stands on the host cores: each step is a bounded sample
+    (one iteration of each method, five PCG iterations with each M) from
+    which the bench step's time is extrapolated."""
     ws, rank, _ = _dist()
     if rank != 0:
         return
     k = max(1, args.steps)
-    vals = []
-    for _ in range(max(0, min(args.warmup, 1))):
-        cpu_baseline(1)
-    for _ in range(k):
-        vals.append(cpu_baseline(1))
-    secs = sum(c["seconds"] for c in vals) / k
-    value = 1.0 / secs
+    st = CpuStep(omp=True)
+    for _ in range(args.warmup):
+        st.sample(1, 5)
+    steps = [st.sample(1, 5) for _ in range(k)]
+    secs = sum(r["step_s"] for r in steps) / k
+    value = ITERS * len(METHODS) / secs
     line = {
         "impl": "reference",
         "metric": "SPAI iterations/s (MR+LOMR+CG, 50 each, with PCG assessment)",
@@ -751,9 +877,10 @@ def run_reference(args):
         "vs_baseline": None,
         "dtype": "f32 values / f64 reductions",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "cap_factor": CAP, "parallelism": "cpu, single thread"},
-        "cpu_baseline": {"value": value, "unit": "SPAI iterations/s", "cores": 1, "kind": "oracle",
-                         "sample": vals[0]["sample"]},
+        "config": {"workload": WORKLOAD, "cap_factor": CAP,
+                   "parallelism": f"cpu, {st.threads} OpenMP threads"},
+        "cpu_baseline": {"value": value, "unit": "SPAI iterations/s", "cores": st.threads,
+                         "kind": "oracle", "sample": st.describe(1, 5)},
         "e2e": {"value": value, "unit": "SPAI iterations/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }

@@ -55,7 +55,7 @@ extern "C" {
 /* --------------------------------------------------------------- options */
 enum { SPAI_FP64 = 0, SPAI_MIXED = 1 };           /* MIXED: FP32 values, FP64 reductions */
 enum { SPAI_MR = 0, SPAI_LOMR = 1, SPAI_CG = 2, SPAI_MR_PI = 3, SPAI_LOMR_PI = 4, SPAI_CG_PI = 5 };
-enum { SPAI_DROP_NONE = 0, SPAI_DROP_TOPK_COL = 1 };
+enum { SPAI_DROP_NONE = 0, SPAI_DROP_TOPK_COL = 1, SPAI_DROP_TOPK_COL_DIAG = 2 };
 enum { SPAI_PREC_NONE = 0, SPAI_PREC_JACOBI = 1, SPAI_PREC_SPAI = 2, SPAI_PREC_SPAI_SYM = 3 };
 
 typedef struct spai_ctx *spai_handle;
@@ -72,6 +72,10 @@ typedef struct {
                         (alpha_i, beta_{i+1}) CG */
   int iters_done;    /* out: iterations completed */
   int flags;         /* out: bit0 converged early, bit1 LOMR fallback */
+  int64_t *nnz;      /* host, [iters+1] or NULL: nnz(M_i), i = 0..iters, the iterate
+                        whose residual resnorm[i] records (spai_run and its
+                        shorthands on a single-matrix handle; entries past an
+                        early stop are left alone) */
 } spai_history;
 
 typedef struct {
@@ -81,6 +85,9 @@ typedef struct {
   int64_t pcg_launches;       /* PCG kernels launched since create */
   int64_t other_launches;     /* set-up / transpose / norm kernels */
   int64_t spgemm_columns;     /* column SpGEMMs performed (Table 2 check) */
+  int64_t colpass_r_bytes;    /* of colpass_bytes: the R lists CG's pass A stores for the next
+                                 pass B (a layout choice of this library, not the method's
+                                 own traffic) */
 } spai_stats;
 
 /* ------------------------------------------------------------- host only */
@@ -174,11 +181,19 @@ int spai_set_stream(spai_handle h, void *stream);
  *           (R, Pi R)/(P, A P), beta = (R+, Pi R+)/(R, Pi R), P = D(Pi R + beta P).
  *           The history still records ||R_i||_F.
  * D is the per-column hard threshold of Sec. 6.1 (keep the cap_j largest |v|,
- * ties to the smaller row; exact zeros never stored) for SPAI_DROP_TOPK_COL,
- * or the identity for SPAI_DROP_NONE (a column that outgrows its capacity
+ * ties to the smaller row; exact zeros never stored) for SPAI_DROP_TOPK_COL;
+ * SPAI_DROP_TOPK_COL_DIAG is the same drop except that row j of column j,
+ * when present, is always kept and counts toward cap_j (Appendix A: the
+ * diagonal is never dropped), for M and for the directions alike;
+ * D is the identity for SPAI_DROP_NONE (a column that outgrows its capacity
  * then fails the call with SPAI_ERR_CAPACITY).  R is always the explicit
  * residual I - A M (Sec. 6.2).  hist may be NULL.  Returns SPAI_OK,
- * SPAI_CONVERGED_EARLY, SPAI_LOMR_FALLBACK or an error. */
+ * SPAI_CONVERGED_EARLY, SPAI_LOMR_FALLBACK or an error.
+ * CG keeps the R of each pass A in a device slab for the next pass B, which
+ * then reads it instead of forming A M again (Table 2's two products per
+ * iteration); when that slab cannot be allocated, or the environment
+ * variable SPAI_CG_NO_R_SLAB is 1, pass B forms R itself, with the same
+ * results. */
 int spai_run(spai_handle h, int method, int iters, int drop_rule, spai_history *hist);
 
 /* Launch-shape autotuner (no counterpart in the paper).  For the column
@@ -371,6 +386,21 @@ int spai_fpmr_create(spai_fpmr_handle *out, int64_t n, int64_t nnz, const int32_
                      const int32_t *colind, int K, int prec, void *stream);
 int spai_fpmr_forward(spai_fpmr_handle h, const double *vals, int on_device, double *loss);
 int spai_fpmr_backward(spai_fpmr_handle h, double dloss, double *dvals, int on_device);
+/* Choose the steps the handle differentiates: SPAI_MR (the default, above)
+ * or SPAI_LOMR, K steps of LOMR on the same fixed pattern (Algorithm 4 with
+ * the 2-D minimiser of Theorem 3):
+ *   P_{-1} = 0, Z_i = mask_S(R_i), U = A Z_i, V = A P_{i-1},
+ *   (delta_i, gamma_i) solving the 2x2 normal equations in (U,U), (V,V),
+ *   (U,V), (U,R_i), (V,R_i) -- or the MR step delta_i = (U,R_i)/(U,U),
+ *   gamma_i = 0 when (V,V) = 0 (i = 0) or the system is near singular, as in
+ *   spai_run --, S_i = delta_i Z_i + gamma_i P_{i-1}, M_{i+1} = M_i + S_i,
+ *   P_i = S_i.
+ * The gradient flows through delta_i, gamma_i (the derivatives of the 2x2
+ * solution), U, V, Z_i, R_i and P_{i-1}.  LOMR keeps one more checkpoint per
+ * step (P_{i-1}) and 5 more arrays on S or T (allocated here: SPAI_ERR_OOM if
+ * they do not fit).  Clears the last forward call (SPAI_ERR_STATE for a
+ * backward call before the next forward).  SPAI_ERR_ARG for another method. */
+int spai_fpmr_set_method(spai_fpmr_handle h, int method);
 /* nnz(T), product-list entries and kernel launches so far (any may be NULL). */
 int spai_fpmr_info(spai_fpmr_handle h, int64_t *nnz_t, int64_t *list_entries, int64_t *launches);
 int spai_fpmr_destroy(spai_fpmr_handle h);
@@ -392,7 +422,9 @@ int spai_load_state(spai_handle h, const void *buf, size_t bytes);
  * Workspace: a fixed ~1 MB array inside the library (every GPU that loads the
  * library holds it until exit); n above 16,777,216 returns
  * SPAI_ERR_UNSUPPORTED.  The first call on each device looks up that array's
- * device address, so make it before starting any stream capture.  All calls
+ * device address, so make it before starting any stream capture; the address
+ * is kept for the life of the process, so cudaDeviceReset after that first
+ * call is not supported (the reloaded library image gets a new one).  All calls
  * share the array: calls that overlap on the GPU race; order them on one
  * stream.  No cudaMalloc, cudaFree or allocating library routine is called. */
 int spai_true_residual_noalloc(int64_t n, const int32_t *rowptr, const int32_t *colind,

@@ -80,6 +80,7 @@ struct spai_ctx {
   // scalars and reduction workspace
   DevScalars* d_sc = nullptr;
   double *d_hres = nullptr, *d_hcoef = nullptr;
+  unsigned long long* d_hnnz = nullptr;  // nnz(M_i) history
   int hist_cap = 0;
   double *d_bsum = nullptr, *d_gsum = nullptr;
   unsigned *d_cnt1 = nullptr, *d_cnt2 = nullptr;
@@ -118,11 +119,20 @@ struct spai_ctx {
   long long* d_srp = nullptr;
   int* d_sci = nullptr;
   double* d_sv = nullptr;
+  // S's rows in sliced ELL for the FP64 PCG products (built with S)
+  long long* d_ssp = nullptr;
+  int* d_sscol = nullptr;
+  double* d_ssval = nullptr;
+  long long ss_cap = 0;
+  int* d_slong = nullptr;  // rows of S too long for the sliced ELL, and their count
+  int* d_nlong = nullptr;
+  int nlong = 0;
   int* d_cnt = nullptr;
   long long* d_scan = nullptr;
   int *d_tmpi = nullptr;
   double* d_tmpv = nullptr;
   long long mt_cap = 0, sym_cap = 0;
+  bool ssell_valid = false;
   // sliced-ELL copies for PCG: A (built on first use), and M or S
   long long* d_asp = nullptr;
   int *d_acol = nullptr, *d_w32 = nullptr;
@@ -156,6 +166,8 @@ struct spai_ctx {
   long long* d_bseg_boff = nullptr;
   cudaGraphExec_t bp_graph = nullptr;
   unsigned char bp_graph_key[sizeof(spai::BpcgArgs)];
+  cudaGraphExec_t pcg_graph = nullptr;  // a chunk of vector-PCG iterations
+  unsigned char pcg_graph_key[sizeof(spai::PcgArgs)];
   // stats
   long long colpass_launches = 0, pcg_launches = 0, other_launches = 0;
   unsigned long long a_bytes_total = 0;
@@ -223,50 +235,73 @@ WarpLayout make_layout(int kind, int vc, int CAP, int W, bool dia, bool pi = fal
   };
   const bool hasP = kind != kRES;
   const bool lomr = kind == kLOMR;
-  (void)dia;
   L.H = H;
   L.HU = HU;
+  // The R list comes first.  The update phase of MR, LOMR and CG pass A (the
+  // union, LOMR's S list, and -- with A in diagonal slots -- the union's
+  // output T) is over before R is formed, so those buffers share R's bytes;
+  // T stays apart on the ELL path, which also uses it as the input-sort
+  // scratch of products taken while R is live.
+  L.Rr = take(4 * LMAX);
+  L.Rv = take(vc * LMAX);
+  const int rbase = L.Rr, rbytes = o - L.Rr;
+  const bool upd = kind == kMR || kind == kLOMR || kind == kCGA;
+  int ru = 0;  // bytes of R's region handed out so far
+  auto in_r = [&](int bytes) {
+    if (!upd || ru + align16(bytes) > rbytes) return -1;
+    int at = rbase + ru;
+    ru += align16(bytes);
+    return at;
+  };
   L.hk = take(4 * H);
   L.hv = take(vc * H);
   L.ho = take(2 * H);
   L.gk = take(lomr ? 4 * H : 0);
   L.gv = take(lomr ? vc * H : 0);
   L.go = take(lomr ? 2 * H : 0);
-  // LOMR: the union table and the select scratch (tie rows, histogram) live
-  // in table B's bytes, which they use only while table B is empty (the
-  // pass clears it before its first product)
+  // the union table: in R's region when it fits, else with the tie scratch
+  const int u_bytes = align16(4 * HU) + 2 * align16(vc * HU) + align16(2 * HU);
+  const int uat = in_r(u_bytes);
+  bool u_placed = false;
+  if (uat >= 0) {
+    L.uk = uat;
+    L.ua = L.uk + align16(4 * HU);
+    L.ub = L.ua + align16(vc * HU);
+    L.uo = L.ub + align16(vc * HU);
+    u_placed = true;
+  }
+  // LOMR: the select scratch (tie rows, histogram), and the union table when
+  // R's region had no room, live in table B's bytes, which they use only
+  // while table B is empty (the pass clears it before its first product);
+  // the tie rows share the union table's bytes (a drop runs after its union)
   bool in_b = false;
   if (lomr) {
-    int u = 0;
-    auto sub = [&](int bytes) {
-      int at = L.gk + u;
-      u = align16(u + bytes);
-      return at;
-    };
-    L.uk = sub(4 * HU);
-    L.ua = sub(vc * HU);
-    L.ub = sub(vc * HU);
-    L.uo = sub(2 * HU);
+    const int u = u_placed ? 0 : u_bytes;
     const int hist_at = align16(std::max(u, 4 * LIST));
-    if (hist_at + 4 * 128 <= o - L.gk) {
+    if (hist_at + 4 * 128 <= o - L.gk) {  // all of it fits in table B
+      if (!u_placed) {
+        L.uk = L.gk;
+        L.ua = L.uk + align16(4 * HU);
+        L.ub = L.ua + align16(vc * HU);
+        L.uo = L.ub + align16(vc * HU);
+        u_placed = true;
+      }
       L.tie = L.gk;
       L.hist = L.gk + hist_at;
       in_b = true;
     }
   }
-  // union table and tie scratch share one region
+  // the union table (if not placed yet) and the tie scratch share one region
   if (!in_b) {
     int base = o;
     int u = 0;
-    auto sub = [&](int bytes) {
-      int at = base + u;
-      u = align16(u + bytes);
-      return at;
-    };
-    L.uk = sub(4 * HU);
-    L.ua = sub(vc * HU);
-    L.ub = sub(vc * HU);
-    L.uo = sub(2 * HU);
+    if (!u_placed) {
+      L.uk = base;
+      L.ua = L.uk + align16(4 * HU);
+      L.ub = L.ua + align16(vc * HU);
+      L.uo = L.ub + align16(vc * HU);
+      u = u_bytes;
+    }
     int region = std::max(u, 4 * LIST);
     L.tie = base;
     o = align16(base + region);
@@ -277,12 +312,16 @@ WarpLayout make_layout(int kind, int vc, int CAP, int W, bool dia, bool pi = fal
   L.Pv = take(hasP ? vc * CAP : 0);
   L.Zr = take(lomr ? 4 * CAP : 0);
   L.Zv = take(lomr ? vc * CAP : 0);
-  L.Sr = take(lomr ? 4 * 2 * CAP : 0);
-  L.Sv = take(lomr ? vc * 2 * CAP : 0);
-  L.Tr = take(4 * TMAX);
-  L.Tv = take(vc * TMAX);
-  L.Rr = take(4 * LMAX);
-  L.Rv = take(vc * LMAX);
+  if (lomr) {
+    const int sr = in_r(4 * 2 * CAP), sv = sr >= 0 ? in_r(vc * 2 * CAP) : -1;
+    L.Sr = sr >= 0 && sv >= 0 ? sr : take(4 * 2 * CAP);
+    L.Sv = sr >= 0 && sv >= 0 ? sv : take(vc * 2 * CAP);
+  }
+  {
+    const int tr = dia ? in_r(4 * TMAX) : -1, tv = tr >= 0 ? in_r(vc * TMAX) : -1;
+    L.Tr = tr >= 0 && tv >= 0 ? tr : take(4 * TMAX);
+    L.Tv = tr >= 0 && tv >= 0 ? tv : take(vc * TMAX);
+  }
   if (!in_b) L.hist = take(4 * 128);  // 256 packed 16-bit bins
   L.zr = take(pi ? 4 * LMAX : 0);
   L.zv = take(pi ? vc * LMAX : 0);
@@ -352,10 +391,13 @@ int ensure_hist(spai_ctx* h, int iters) {
   if (iters + 1 <= h->hist_cap) return SPAI_OK;
   dfree(h->d_hres);
   dfree(h->d_hcoef);
+  dfree(h->d_hnnz);
   int cap = std::max(iters + 1, 64);
   int rc = dalloc(&h->d_hres, cap);
   if (rc) return rc;
   rc = dalloc(&h->d_hcoef, 2 * cap);
+  if (rc) return rc;
+  rc = dalloc(&h->d_hnnz, cap);
   if (rc) return rc;
   h->hist_cap = cap;
   return SPAI_OK;
@@ -499,6 +541,7 @@ void free_all(spai_ctx* h) {
   dfree(h->d_seg_cnt);
   dfree(h->d_hres);
   dfree(h->d_hcoef);
+  dfree(h->d_hnnz);
   dfree(h->d_bsum);
   dfree(h->d_gsum);
   dfree(h->d_cnt1);
@@ -512,6 +555,11 @@ void free_all(spai_ctx* h) {
   dfree(h->d_srp);
   dfree(h->d_sci);
   dfree(h->d_sv);
+  dfree(h->d_ssp);
+  dfree(h->d_sscol);
+  dfree(h->d_ssval);
+  dfree(h->d_slong);
+  dfree(h->d_nlong);
   dfree(h->d_cnt);
   dfree(h->d_scan);
   dfree(h->d_tmpi);
@@ -562,6 +610,8 @@ void free_all(spai_ctx* h) {
   dfree(h->d_bseg_boff);
   if (h->bp_graph) cudaGraphExecDestroy(h->bp_graph);
   h->bp_graph = nullptr;
+  if (h->pcg_graph) cudaGraphExecDestroy(h->pcg_graph);
+  h->pcg_graph = nullptr;
   for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
   h->ev.clear();
 }
@@ -646,13 +696,44 @@ int ensure_rows(spai_ctx* h, bool sym) {
     h->sym_nnz = tot;
     h->other_launches += 5;
     h->sym_valid = true;
+    h->ssell_valid = false;
   }
+  return SPAI_OK;
+}
+
+// S's rows in sliced ELL (coalesced loads for the FP64 preconditioner
+// product); needs ensure_rows(h, true) first
+int ensure_sym_sell(spai_ctx* h) {
+  if (h->ssell_valid) return SPAI_OK;
+  const int n = h->n, ns = (n + 31) / 32;
+  if (!h->d_ssp) {
+    int rc = dalloc(&h->d_ssp, (size_t)ns + 1);
+    if (rc) return rc;
+  }
+  if (!h->d_w32) {
+    int rc = dalloc(&h->d_w32, (size_t)ns + 1);
+    if (rc) return rc;
+  }
+  long long tot = 0;
+  CK(launch_sell_build_i64(n, h->d_srp, h->d_sci, h->d_sv, h->d_w32, h->d_ssp, h->d_scan,
+                           &h->d_sscol, &h->d_ssval, &h->ss_cap, &tot, h->stream));
+  if (!h->d_slong) {
+    int rc = dalloc(&h->d_slong, (size_t)n);
+    if (!rc) rc = dalloc(&h->d_nlong, 1);
+    if (rc) return rc;
+  }
+  CK(launch_long_rows(n, h->d_srp, h->d_slong, h->d_nlong, h->stream));
+  CK(cudaMemcpyAsync(&h->nlong, h->d_nlong, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  h->other_launches += 6;
+  h->ssell_valid = true;
   return SPAI_OK;
 }
 
 void invalidate_rows(spai_ctx* h) {
   h->mt_valid = false;
   h->sym_valid = false;
+  h->ssell_valid = false;
   h->m32_valid = false;
   h->s32_valid = false;
 }
@@ -1144,7 +1225,9 @@ int spai_run(spai_handle h, int method, int iters, int drop_rule, spai_history* 
   const bool pim = method >= SPAI_MR_PI;  // Section 5's forms with Pi = diag(A)^{-1}
   if (pim && !h->pi_ok) return SPAI_ERR_UNSUPPORTED;
   const int base = pim ? method - SPAI_MR_PI : method;
-  if (drop_rule != SPAI_DROP_NONE && drop_rule != SPAI_DROP_TOPK_COL) return SPAI_ERR_ARG;
+  if (drop_rule != SPAI_DROP_NONE && drop_rule != SPAI_DROP_TOPK_COL &&
+      drop_rule != SPAI_DROP_TOPK_COL_DIAG)
+    return SPAI_ERR_ARG;
   const int nh = std::max(h->nseg, 1);
   int rc = ensure_hist(h, (iters + 1) * nh);
   if (rc) return rc;
@@ -1162,13 +1245,16 @@ int spai_run(spai_handle h, int method, int iters, int drop_rule, spai_history* 
   if (h->nseg) CK(launch_seg_reset(h->d_segsc, h->nseg, fresh ? 1 : 0, st));
   CK(cudaMemsetAsync(h->d_hres, 0xff, sizeof(double) * (iters + 1) * nh, st));
   CK(cudaMemsetAsync(h->d_hcoef, 0xff, sizeof(double) * 2 * std::max(iters, 1) * nh, st));
+  CK(cudaMemsetAsync(h->d_hnnz, 0, sizeof(unsigned long long) * (iters + 1) * nh, st));
   invalidate_rows(h);
-  const int drop = drop_rule == SPAI_DROP_TOPK_COL ? 1 : 0;
+  const int drop = drop_rule != SPAI_DROP_NONE ? 1 : 0;
+  const int keep_diag = drop_rule == SPAI_DROP_TOPK_COL_DIAG ? 1 : 0;
   // CG: pass A keeps R_{i+1} for pass B of the next iteration, which then
   // reads it instead of repeating the product (the same values)
   // (the slab is an optimisation: without device memory for it, pass B
   // recomputes R as before)
-  bool keep_r = base == SPAI_CG && iters > 1;
+  // SPAI_CG_NO_R_SLAB=1 takes the recomputing path on purpose (tests)
+  bool keep_r = base == SPAI_CG && iters > 1 && !env_int("SPAI_CG_NO_R_SLAB", 0);
   if (keep_r && !h->d_Rrow) {
     const size_t cnt = (size_t)h->n * ((size_t)h->capmax * h->W + 1);
     const size_t vb = h->prec == SPAI_FP64 ? 8 : 4;
@@ -1189,6 +1275,8 @@ int spai_run(spai_handle h, int method, int iters, int drop_rule, spai_history* 
     p.do_update = upd;
     p.do_dir = dir;
     p.drop = drop;
+    p.keep_diag = keep_diag;
+    p.hist_nnz = h->d_hnnz;
     p.iter = iter;
     p.fresh = fresh_b;
     p.r_in = r_in;
@@ -1222,6 +1310,12 @@ int spai_run(spai_handle h, int method, int iters, int drop_rule, spai_history* 
   if (hist && hist->coef && iters > 0)
     CK(cudaMemcpyAsync(hist->coef, h->d_hcoef, sizeof(double) * 2 * iters, cudaMemcpyDeviceToHost,
                        st));
+  std::vector<unsigned long long> hnnz;
+  if (hist && hist->nnz && !h->nseg) {
+    hnnz.resize(iters + 1);
+    CK(cudaMemcpyAsync(hnnz.data(), h->d_hnnz, sizeof(unsigned long long) * (iters + 1),
+                       cudaMemcpyDeviceToHost, st));
+  }
   std::vector<DevScalars> ssc;
   if (h->nseg) {
     ssc.resize(h->nseg);
@@ -1243,6 +1337,12 @@ int spai_run(spai_handle h, int method, int iters, int drop_rule, spai_history* 
   if (hist) {
     hist->iters_done = sc.done;
     hist->flags = sc.flags & 3;
+    // entries up to the last history entry written: iters_done (+1 for the
+    // final residual when every iteration ran)
+    if (hist->nnz && !h->nseg) {
+      const int last = sc.done == iters ? iters : sc.done;
+      for (int i = 0; i <= last && i <= iters; i++) hist->nnz[i] = (int64_t)hnnz[i];
+    }
   }
   h->method = method;
   h->it += sc.done;
@@ -1690,6 +1790,15 @@ int pcg_solve(spai_handle h, const double* b, double* x, int nrhs, double rtol, 
     a.mrp = h->d_srp;
     a.mci = h->d_sci;
     a.mv = h->d_sv;
+    if (h->pcg_prec != SPAI_MIXED) {
+      rc = ensure_sym_sell(h);
+      if (rc) return rc;
+      a.sell.sptr = h->d_ssp;
+      a.sell.col = h->d_sscol;
+      a.sell.val = h->d_ssval;
+      a.longrows = h->d_slong;
+      a.nlong = h->nlong;
+    }
   }
   a.b = h->d_b;
   a.x = h->d_x;
@@ -1715,9 +1824,32 @@ int pcg_solve(spai_handle h, const double* b, double* x, int nrhs, double rtol, 
   a.ws.ngroups = (a.ws.nb + kGroup - 1) / kGroup;
   CK(launch_pcg_init(a, st));
   h->pcg_launches += 3;
+  // the iterations run as replays of a captured graph of `chunk` iterations
+  // (their kernels read every scalar from device memory, so the launches do
+  // not change while the arguments do not); the host polls the done flag
+  // between replays
   const int chunk = 16;
+  if (!h->pcg_graph || memcmp(h->pcg_graph_key, &a, sizeof(a)) != 0) {
+    if (h->pcg_graph) cudaGraphExecDestroy(h->pcg_graph);
+    h->pcg_graph = nullptr;
+    cudaGraph_t g = nullptr;
+    if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+      cudaError_t e = cudaSuccess;
+      for (int c = 0; c < chunk && e == cudaSuccess; c++) e = launch_pcg_iter(a, st);
+      cudaError_t e2 = cudaStreamEndCapture(st, &g);
+      if (e == cudaSuccess && e2 == cudaSuccess && g)
+        if (cudaGraphInstantiate(&h->pcg_graph, g, 0) != cudaSuccess) h->pcg_graph = nullptr;
+      if (g) cudaGraphDestroy(g);
+    }
+    (void)cudaGetLastError();
+    if (h->pcg_graph) memcpy(h->pcg_graph_key, &a, sizeof(a));
+  }
   for (;;) {
-    for (int c = 0; c < chunk; c++) CK(launch_pcg_iter(a, st));
+    if (h->pcg_graph) {
+      CK(cudaGraphLaunch(h->pcg_graph, st));
+    } else {
+      for (int c = 0; c < chunk; c++) CK(launch_pcg_iter(a, st));
+    }
     h->pcg_launches += 4 * chunk;
     CK(cudaMemcpyAsync(&ps, h->d_ps, sizeof(ps), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
@@ -2617,6 +2749,7 @@ int spai_load_state(spai_handle h, const void* buf, size_t bytes) {
   memcpy(&sv, o, sizeof(sv));
   sv.bytes = cur.bytes;
   sv.spgemm_cols = cur.spgemm_cols;
+  sv.r_bytes = cur.r_bytes;
   CK(cudaMemcpyAsync(h->d_sc, &sv, sizeof(DevScalars), cudaMemcpyHostToDevice, st));
   CK(cudaStreamSynchronize(st));
   o += sizeof(DevScalars);
@@ -2655,6 +2788,7 @@ int spai_get_stats(spai_handle h, spai_stats* out) {
   out->pcg_launches = h->pcg_launches;
   out->other_launches = h->other_launches;
   out->spgemm_columns = (int64_t)sc.spgemm_cols;
+  out->colpass_r_bytes = (int64_t)sc.r_bytes;
   return SPAI_OK;
 }
 

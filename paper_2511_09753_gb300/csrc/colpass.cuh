@@ -52,14 +52,17 @@ struct ColCtx {
   int lane;
   int overflow;
   unsigned long long bytes;
+  unsigned long long rbytes;  // of bytes: CG's R slab
   unsigned long long spg;
+  unsigned long long nnzM;    // nnz of the M columns this warp produced (history)
   const DevScalars* sc;  // the coefficients of this column's matrix
   int seg;               // its segment in batched mode, else -1
 #ifdef SPAI_PHASE_CLOCKS
   long long ph_t0;
   long long ph[kPhCount];
   __device__ ColCtx(const PassParams& pp, char* w, int l, const DevScalars* s, int sg)
-      : p(pp), ws(w), lane(l), overflow(0), bytes(0), spg(0), sc(s), seg(sg), ph_t0(0) {
+      : p(pp), ws(w), lane(l), overflow(0), bytes(0), rbytes(0), spg(0), nnzM(0), sc(s), seg(sg),
+        ph_t0(0) {
     for (int k = 0; k < kPhCount; k++) ph[k] = 0;
   }
   __device__ __forceinline__ void ph_start() { ph_t0 = clock64(); }
@@ -70,7 +73,7 @@ struct ColCtx {
   }
 #else
   __device__ ColCtx(const PassParams& pp, char* w, int l, const DevScalars* s, int sg)
-      : p(pp), ws(w), lane(l), overflow(0), bytes(0), spg(0), sc(s), seg(sg) {}
+      : p(pp), ws(w), lane(l), overflow(0), bytes(0), rbytes(0), spg(0), nnzM(0), sc(s), seg(sg) {}
   __device__ __forceinline__ void ph_start() {}
   __device__ __forceinline__ void mark(int) {}
 #endif
@@ -144,7 +147,9 @@ __device__ void store_r(ColCtx<VS, VC>& c, int j, int LR, const int* Rr, const V
     gv[o + e] = Rv[e];
   }
   if (c.lane == 0) p.Rlen[j] = LR;
-  c.bytes += (unsigned long long)LR * (sizeof(int) + sizeof(VC)) + sizeof(int);
+  const unsigned long long b = (unsigned long long)LR * (sizeof(int) + sizeof(VC)) + sizeof(int);
+  c.bytes += b;
+  c.rbytes += b;
 }
 
 template <typename VS, typename VC>
@@ -160,7 +165,9 @@ __device__ int load_r(ColCtx<VS, VC>& c, int j, int* Rr, VC* Rv) {
     Rv[e] = v;
   }
   __syncwarp();
-  c.bytes += (unsigned long long)LR * (sizeof(int) + sizeof(VC)) + sizeof(int);
+  const unsigned long long b = (unsigned long long)LR * (sizeof(int) + sizeof(VC)) + sizeof(int);
+  c.bytes += b;
+  c.rbytes += b;
   return LR;
 }
 
@@ -198,6 +205,7 @@ __device__ void column_work(ColCtx<VS, VC>& c, int j, double* part) {
   const int lane = c.lane;
   const long long off = p.off[j];
   const int cap = p.cap[j];
+  const int keep = p.keep_diag ? j : -1;  // the row every drop of this column keeps
   int* Mr = c.template at<int>(L.Mr);
   VC* Mv = c.template at<VC>(L.Mv);
   int* Pr = c.template at<int>(L.Pr);
@@ -278,11 +286,12 @@ __device__ void column_work(ColCtx<VS, VC>& c, int j, double* part) {
       CombAxpy<VC> f{c.sc->alpha};
       int Lt = warp_union(un, Mr, Mv, Lm, Pr, Pv, Lp, Tr, Tv, f, lane);
       c.mark(kPhUnion);
-      Lm = warp_select(Tr, Tv, Lt, cap, Mr, Mv, hist, tie, p.drop, ovf, lane);
+      Lm = warp_select(Tr, Tv, Lt, cap, Mr, Mv, hist, tie, p.drop, ovf, lane, keep);
       c.mark(kPhSelect);
       store_col(c, p.Mrow, p.Mval, p.Mlen, j, off, Lm, Mr, Mv);
       c.mark(kPhStore);
     }
+    c.nnzM += Lm;  // M_iter
     int cnt = spgemm(p, ha, Mr, Mv, Lm, j, Tr, Tv, lane, c.seg);
     c.mark(kPhSpgemm);
     int LR = table_to_list(ha, cnt, j, Rr, Rv, lane);
@@ -300,9 +309,9 @@ __device__ void column_work(ColCtx<VS, VC>& c, int j, double* part) {
         int* Zr = c.template at<int>(L.zr);
         VC* Zv = c.template at<VC>(L.zv);
         int Lz = list_scale_pi(Rr, Rv, LR, p.pi, Zr, Zv, lane);
-        Lp = warp_select(Zr, Zv, Lz, cap, Pr, Pv, hist, tie, p.drop, ovf, lane);
+        Lp = warp_select(Zr, Zv, Lz, cap, Pr, Pv, hist, tie, p.drop, ovf, lane, keep);
       } else {
-        Lp = warp_select(Rr, Rv, LR, cap, Pr, Pv, hist, tie, p.drop, ovf, lane);
+        Lp = warp_select(Rr, Rv, LR, cap, Pr, Pv, hist, tie, p.drop, ovf, lane, keep);
       }
       c.mark(kPhSelect);
       store_col(c, p.Prow, p.Pval, p.Plen, j, off, Lp, Pr, Pv);
@@ -341,18 +350,19 @@ __device__ void column_work(ColCtx<VS, VC>& c, int j, double* part) {
       CombLin<VC> fl{c.sc->delta, c.sc->gamma};
       int Ls = warp_union(un, Zr, Zv, Lz0, Pr, Pv, Lp, Sr, Sv, fl, lane);
       c.mark(kPhUnion);
-      Lp = warp_select(Sr, Sv, Ls, cap, Pr, Pv, hist, tie, p.drop, ovf, lane);
+      Lp = warp_select(Sr, Sv, Ls, cap, Pr, Pv, hist, tie, p.drop, ovf, lane, keep);
       c.mark(kPhSelect);
       store_col(c, p.Prow, p.Pval, p.Plen, j, off, Lp, Pr, Pv);
       c.mark(kPhStore);
       CombAdd<VC> fa;
       int Lt = warp_union(un, Mr, Mv, Lm, Sr, Sv, Ls, Tr, Tv, fa, lane);
       c.mark(kPhUnion);
-      Lm = warp_select(Tr, Tv, Lt, cap, Mr, Mv, hist, tie, p.drop, ovf, lane);
+      Lm = warp_select(Tr, Tv, Lt, cap, Mr, Mv, hist, tie, p.drop, ovf, lane, keep);
       c.mark(kPhSelect);
       store_col(c, p.Mrow, p.Mval, p.Mlen, j, off, Lm, Mr, Mv);
       c.mark(kPhStore);
     }
+    c.nnzM += Lm;  // M_iter
     int cr = spgemm(p, ha, Mr, Mv, Lm, j, Tr, Tv, lane, c.seg);
     c.mark(kPhSpgemm);
     int LR = table_to_list(ha, cr, j, Rr, Rv, lane);
@@ -371,9 +381,9 @@ __device__ void column_work(ColCtx<VS, VC>& c, int j, double* part) {
         int* Xr = c.template at<int>(L.zr);
         VC* Xv = c.template at<VC>(L.zv);
         int Lx = list_scale_pi(Rr, Rv, LR, p.pi, Xr, Xv, lane);
-        Lz = warp_select(Xr, Xv, Lx, cap, Zr, Zv, hist, tie, p.drop, ovf, lane);
+        Lz = warp_select(Xr, Xv, Lx, cap, Zr, Zv, hist, tie, p.drop, ovf, lane, keep);
       } else {
-        Lz = warp_select(Rr, Rv, LR, cap, Zr, Zv, hist, tie, p.drop, ovf, lane);
+        Lz = warp_select(Rr, Rv, LR, cap, Zr, Zv, hist, tie, p.drop, ovf, lane, keep);
       }
       c.mark(kPhSelect);
       store_col(c, p.Zrow, p.Zval, p.Zlen, j, off, Lz, Zr, Zv);
@@ -424,10 +434,11 @@ __device__ void column_work(ColCtx<VS, VC>& c, int j, double* part) {
       CombAxpy<VC> f{c.sc->alpha};
       int Lt = warp_union(un, Mr, Mv, Lm, Pr, Pv, Lp, Tr, Tv, f, lane);
       c.mark(kPhUnion);
-      Lm = warp_select(Tr, Tv, Lt, cap, Mr, Mv, hist, tie, p.drop, ovf, lane);
+      Lm = warp_select(Tr, Tv, Lt, cap, Mr, Mv, hist, tie, p.drop, ovf, lane, keep);
       c.mark(kPhSelect);
       store_col(c, p.Mrow, p.Mval, p.Mlen, j, off, Lm, Mr, Mv);
       c.mark(kPhStore);
+      c.nnzM += Lm;  // M_{iter+1}
     }
     if (!p.do_dir) {  // the update only: M is dropped outside before R is formed
       part[0] = 0.0;
@@ -450,6 +461,7 @@ __device__ void column_work(ColCtx<VS, VC>& c, int j, double* part) {
   }
 
   if constexpr (KIND == kCGB) {
+    if (p.fresh) c.nnzM += Lm;  // M_0 of the call (loaded: no R slab on the first pass)
     int LR;
     if (p.r_in) {  // R as the previous pass A computed it
       LR = load_r(c, j, Rr, Rv);
@@ -472,7 +484,7 @@ __device__ void column_work(ColCtx<VS, VC>& c, int j, double* part) {
         Lt = warp_union(un, Rr, Rv, LR, Pr, Pv, Lp, Tr, Tv, f, lane);
       }
       c.mark(kPhUnion);
-      Lp = warp_select(Tr, Tv, Lt, cap, Pr, Pv, hist, tie, p.drop, ovf, lane);
+      Lp = warp_select(Tr, Tv, Lt, cap, Pr, Pv, hist, tie, p.drop, ovf, lane, keep);
       c.mark(kPhSelect);
       store_col(c, p.Prow, p.Pval, p.Plen, j, off, Lp, Pr, Pv);
       c.mark(kPhStore);
@@ -484,11 +496,19 @@ __device__ void column_work(ColCtx<VS, VC>& c, int j, double* part) {
     int cq = spgemm(p, ha, Pr, Pv, Lp, -1, Tr, Tv, lane, c.seg);  // table holds Q = A P
     c.mark(kPhSpgemm);
     c.spg++;
-    if (PI)  // (R,R), (P,Q), (R,Pi R)
-      fixsum<3>(part, lane, TermSq<VC>{Rv}, LR, TermProdFind<VC>{Pr, Pv, ha}, Lp,
-                TermWSq<VC>{Rr, Rv, p.pi}, LR);
-    else     // (R,R), (P,Q)
-      fixsum<2>(part, lane, TermSq<VC>{Rv}, LR, TermProdFind<VC>{Pr, Pv, ha}, Lp);
+    // (R,R) and (R,Pi R) are needed only by the first pass B of a call: the
+    // pass A before each later one has stored them (alpha's numerator)
+    if (p.fresh) {
+      if (PI)  // (R,R), (P,Q), (R,Pi R)
+        fixsum<3>(part, lane, TermSq<VC>{Rv}, LR, TermProdFind<VC>{Pr, Pv, ha}, Lp,
+                  TermWSq<VC>{Rr, Rv, p.pi}, LR);
+      else     // (R,R), (P,Q)
+        fixsum<2>(part, lane, TermSq<VC>{Rv}, LR, TermProdFind<VC>{Pr, Pv, ha}, Lp);
+    } else {  // (P,Q)
+      part[0] = 0.0;
+      part[2] = 0.0;
+      fixsum<1>(part + 1, lane, TermProdFind<VC>{Pr, Pv, ha}, Lp);
+    }
     c.mark(kPhFixsum);
     hash_clear(ha, cq, lane);
     c.mark(kPhList);
@@ -571,8 +591,10 @@ __device__ inline void coefficients(const PassParams& p, DevScalars* sc, double*
   }
   if (p.kind == kCGB) {
     if (!p.do_dir) return;  // a direction candidate: no step
-    // alpha = (R, R) / (P, AP), or (R, Pi R) / (P, AP) with Pi
-    double rr = p.pi ? t[2] : t[0], pq = t[1];
+    // alpha = (R, R) / (P, AP), or (R, Pi R) / (P, AP) with Pi; after the
+    // first pass B of a call the numerator is the one the pass A before it
+    // stored (the same sum over the same R), and this pass skips it
+    double rr = p.fresh ? (p.pi ? t[2] : t[0]) : sc->rr, pq = t[1];
     if (p.fresh && hist_res) hist_res[0] = __dsqrt_rn(t[0]);
     if (rr == 0.0 || pq == 0.0) {
       sc->stop = 1;
@@ -671,17 +693,21 @@ __global__ void __launch_bounds__(256, sizeof(VC) == 4 ? 4 : 3) colpass_kernel(c
 #define SPAI_TAIL_DONE() ((void)0)
 #endif
   // per-CTA counters
-  __shared__ unsigned long long s_bytes, s_spg;
+  __shared__ unsigned long long s_bytes, s_spg, s_rbytes, s_nnz;
   __shared__ int s_ovf, s_last1, s_last2;
   if (threadIdx.x == 0) {
     s_bytes = 0;
     s_spg = 0;
+    s_rbytes = 0;
+    s_nnz = 0;
     s_ovf = 0;
   }
   __syncthreads();
   if (lane == 0) {
     atomicAdd(&s_bytes, c.bytes);
     atomicAdd(&s_spg, c.spg);
+    if (KIND == kCGA || KIND == kCGB) atomicAdd(&s_rbytes, c.rbytes);
+    if (KIND <= kCGB) atomicAdd(&s_nnz, c.nnzM);
     if (c.overflow) atomicOr(&s_ovf, 1);
   }
   // CTA tree over the B column partials of each quantity
@@ -703,6 +729,13 @@ __global__ void __launch_bounds__(256, sizeof(VC) == 4 ? 4 : 3) colpass_kernel(c
     if (threadIdx.x == 0) p.bsum[(long long)q * p.nb + blockIdx.x] = s;
   }
   __syncthreads();
+  // nnz(M_i) history: MR, LOMR passes hold M_iter, CG pass A M_{iter+1},
+  // the first CG pass B of a call M_0
+  if (KIND <= kCGB && threadIdx.x == 0 && p.hist_nnz && (KIND != kCGB || p.fresh) &&
+      (KIND != kCGA || p.do_update)) {
+    const int idx = KIND == kCGA ? p.iter + 1 : KIND == kCGB ? 0 : p.iter;
+    atomicAdd(p.hist_nnz + (seg >= 0 ? (long long)seg * p.hist_stride : 0LL) + idx, s_nnz);
+  }
   __shared__ double tot[6];
   if (seg >= 0) {
     // batched: the last CTA of this matrix reduces its CTAs' sums (aligned,
@@ -711,6 +744,7 @@ __global__ void __launch_bounds__(256, sizeof(VC) == 4 ? 4 : 3) colpass_kernel(c
       if (s_ovf) atomicOr(&sc->flags, kFlagCapacity);
       atomicAdd(&p.sc->bytes, s_bytes);
       atomicAdd(&p.sc->spgemm_cols, s_spg);
+      if (KIND == kCGA || KIND == kCGB) atomicAdd(&p.sc->r_bytes, s_rbytes);
       __threadfence();
       unsigned old = atomicAdd(&p.seg_cnt[seg], 1u);
       s_last1 = (old == (unsigned)(p.seg_npad[seg] / p.B - 1));
@@ -743,6 +777,7 @@ __global__ void __launch_bounds__(256, sizeof(VC) == 4 ? 4 : 3) colpass_kernel(c
     if (s_ovf) atomicOr(&p.sc->flags, kFlagCapacity);
     atomicAdd(&p.sc->bytes, s_bytes);
     atomicAdd(&p.sc->spgemm_cols, s_spg);
+    if (KIND == kCGA || KIND == kCGB) atomicAdd(&p.sc->r_bytes, s_rbytes);
     __threadfence();
     int gsize = min(kGroup, p.nb - g * kGroup);
     unsigned old = atomicAdd(&p.cnt1[g], 1u);

@@ -20,6 +20,7 @@ struct DevScalars {
   int pad;
   unsigned long long bytes;          // algorithmic bytes moved by column passes
   unsigned long long spgemm_cols;    // column SpGEMMs performed
+  unsigned long long r_bytes;        // of bytes: CG's R slab (pass A writes it, pass B reads it)
 };
 
 enum : int {
@@ -64,6 +65,7 @@ struct PassParams {
   int capmax, pmax, lmax, tmax;
   int kind;
   int do_update, do_dir, drop;
+  int keep_diag;     // per-column drops keep the column's diagonal entry
   int dir_from_slab;     // take the direction (MR, CG: P; LOMR: Z) stored in its slab instead of forming it
   int dir_store;         // MR, LOMR with do_dir = 0: still form the direction (P; Z) from R and store it
   int iter;          // history slot of this pass
@@ -88,6 +90,7 @@ struct PassParams {
   const double* anrm;    // kSCORE: ||A e_k||^2 per row k
   DevScalars* sc;
   double* hist_res;      // [iters+1]
+  unsigned long long* hist_nnz;  // [iters+1] nnz(M_i) (counts added per CTA), or null
   double* hist_coef;     // [2*iters]
   double* bsum;          // [NQ][nb]
   double* gsum;          // [NQ][ngroups]

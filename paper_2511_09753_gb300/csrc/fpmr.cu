@@ -1,7 +1,14 @@
-// Differentiation of fixed-pattern MR (no counterpart in the paper; its
-// objective and gradient form are Sec. 2 and Sec. 3 Eq. (gradient)):
-//   M_0 = diag(A)^{-1};  R_i = I - A M_i;  P_i = mask_S(R_i);  Q_i = A P_i;
-//   alpha_i = (R_i, Q_i)_F / (Q_i, Q_i)_F;  M_{i+1} = M_i + alpha_i P_i;
+// Differentiation of fixed-pattern MR and LOMR (no counterpart in the paper;
+// the objective and its gradient form are Sec. 2 and Sec. 3 Eq. (gradient)):
+//   MR (Algorithm 1 on S):  M_0 = diag(A)^{-1};  R_i = I - A M_i;
+//     P_i = mask_S(R_i);  Q_i = A P_i;  alpha_i = (R_i, Q_i)_F / (Q_i, Q_i)_F;
+//     M_{i+1} = M_i + alpha_i P_i;
+//   LOMR (Algorithm 4 / Theorem 3 on S):  P_{-1} = 0;  Z_i = mask_S(R_i);
+//     U = A Z_i;  V = A P_{i-1};  (delta_i, gamma_i) from the 2x2 normal
+//     equations in (U,U), (V,V), (U,V), (U,R_i), (V,R_i), or the MR step
+//     delta_i = (U,R_i)/(U,U), gamma_i = 0 when (V,V) = 0 or the system is
+//     near singular;  S_i = delta_i Z_i + gamma_i P_{i-1};  M_{i+1} = M_i + S_i;
+//     P_i = S_i;
 //   L = ||I - A M_K||_F^2,  S = supp(A),
 // and dL/dA over A's stored entries (independent values) by reverse mode.
 //
@@ -15,12 +22,14 @@
 // the host in the order of the fma chain (ascending inner index) by merging
 // sorted rows, so the GPU side is a gather-fma per output entry.  The
 // backward pass recomputes R_i, P_i, Q_i from the stored M_i (one checkpoint
-// per step).  Values are FP64, or FP32 on the mixed path (FP32 products and
+// per step, and of P_{i-1} for LOMR).  Values are FP64, or FP32 on the mixed
+// path (FP32 products and
 // stored values; inner products, step scalars and the axpy arithmetic in
 // FP64, each stored value rounded once).
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -29,6 +38,7 @@
 #include <vector>
 
 #include "spai.h"
+#include "vec_kernels.cuh"
 
 namespace {
 
@@ -43,6 +53,7 @@ struct ProdList {
 
 struct spai_fpmr_ctx {
   int n = 0, K = 0;
+  int method = SPAI_MR;    // SPAI_MR or SPAI_LOMR
   long long nS = 0, nT = 0;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
@@ -54,6 +65,12 @@ struct spai_fpmr_ctx {
   void *d_A = nullptr, *d_Mck = nullptr, *d_P = nullptr, *d_dM = nullptr, *d_dP = nullptr,
        *d_dA = nullptr;
   void *d_R = nullptr, *d_Q = nullptr, *d_dR = nullptr, *d_dQ = nullptr;
+  // LOMR: checkpoints P_{i-1} ([K+1][nS], P_{-1} = 0 first), V = A P_{i-1}
+  // and its adjoint on T, dS, dP_{i-1} and the incoming dP_i on S
+  void *d_Pck = nullptr, *d_V = nullptr, *d_dV = nullptr, *d_dS = nullptr, *d_dPp = nullptr,
+       *d_dPn = nullptr;
+  std::vector<double> delta, gamma, prod;  // prod: uu, vv, uv, ur, vr per step
+  std::vector<char> mrstep;
   double *d_part = nullptr, *d_res = nullptr, *d_stage = nullptr;
   std::vector<double> alpha, num, den;
   std::vector<double> diag;  // a_jj of the last forward values
@@ -153,6 +170,15 @@ template <typename T>
 __global__ void k_lin2(long long m, double a, const T* x, double b, const T* y, T* z) {
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (e < m) z[e] = (T)__fma_rn(a, (double)x[e], __dmul_rn(b, (double)y[e]));
+}
+
+// z = a x + b y + c w as fma(a, x, fma(b, y, c w)) in FP64, rounded to the value type
+template <typename T>
+__global__ void k_lin3(long long m, double a, const T* x, double b, const T* y, double c,
+                       const T* w, T* z) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < m)
+    z[e] = (T)__fma_rn(a, (double)x[e], __fma_rn(b, (double)y[e], __dmul_rn(c, (double)w[e])));
 }
 
 template <typename T>
@@ -334,6 +360,12 @@ void free_fpmr(spai_fpmr_ctx* h) {
   ffree(h->d_Q);
   ffree(h->d_dR);
   ffree(h->d_dQ);
+  ffree(h->d_Pck);
+  ffree(h->d_V);
+  ffree(h->d_dV);
+  ffree(h->d_dS);
+  ffree(h->d_dPp);
+  ffree(h->d_dPn);
   ffree(h->d_part);
   ffree(h->d_res);
   ffree(h->d_stage);
@@ -364,17 +396,343 @@ inline long long find_pos(const std::vector<long long>& ptr, const std::vector<i
   return (f != e && *f == c) ? (long long)(f - col.data()) : -1;
 }
 
-}  // namespace
+// ------------------------------------------------ set-up on the device
+// The patterns and product lists of spai_fpmr_create, built on the GPU when
+// A's rows hold at most kSetupW entries: thread per row, two passes (count,
+// then fill at the exclusive scan of the counts), so every list comes out
+// in the order the host construction gives: output entries in CSR order,
+// each with its pairs in ascending inner index.
+constexpr int kSetupW = 64;
 
-extern "C" {
+__device__ __forceinline__ int dfind(const int* col, long long b, long long e, int c) {
+  while (b < e) {  // position of c in col[b, e) (sorted), or -1
+    const long long m = (b + e) >> 1;
+    const int x = col[m];
+    if (x == c) return (int)m;
+    if (x < c) b = m + 1;
+    else e = m;
+  }
+  return -1;
+}
+__device__ __forceinline__ long long dfind64(const int* col, long long b, long long e, int c) {
+  while (b < e) {
+    const long long m = (b + e) >> 1;
+    const int x = col[m];
+    if (x == c) return m;
+    if (x < c) b = m + 1;
+    else e = m;
+  }
+  return -1;
+}
 
-int spai_fpmr_create(spai_fpmr_handle* out, int64_t n, int64_t nnz, const int32_t* rowptr,
-                     const int32_t* colind, int K, int prec, void* stream) {
-  if (!out) return SPAI_ERR_ARG;
-  *out = nullptr;
-  if (n < 1 || nnz < 1 || !rowptr || !colind || K < 0 || K > 1000) return SPAI_ERR_ARG;
-  if (prec != SPAI_FP64 && prec != SPAI_MIXED) return SPAI_ERR_ARG;
-  if (n >= (1LL << 31) || nnz >= (1LL << 31)) return SPAI_ERR_UNSUPPORTED;
+// rows strictly ascending and in range: err[0] = 1 on any violation
+__global__ void k_su_check(int n, const int* sp, const int* sc, int* err) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  const int b = sp[r], e = sp[r + 1];
+  if (e < b) {
+    atomicOr(err, 1);
+    return;
+  }
+  for (int q = b; q < e; q++)
+    if (sc[q] < 0 || sc[q] >= n || (q > b && sc[q] <= sc[q - 1])) atomicOr(err, 1);
+}
+
+// first row without a diagonal (err[1]) and first row with an entry whose
+// mirror is missing (err[2]), as atomicMin over the row index
+__global__ void k_su_diag_sym(int n, const int* sp, const int* sc, int* diagS, int* err) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  const int d = dfind(sc, sp[r], sp[r + 1], r);
+  diagS[r] = d;
+  if (d < 0) atomicMin(err + 1, r);
+  for (int q = sp[r]; q < sp[r + 1]; q++) {
+    const int c = sc[q];
+    if (dfind(sc, sp[c], sp[c + 1], r) < 0) {
+      atomicMin(err + 2, r);
+      break;
+    }
+  }
+}
+
+// T(r) = {r} u union over k in S(r) of S(k), sorted: a merge of the rows k
+// (at most kSetupW of them) by their heads.  fill = 0: count into tlen[r].
+__global__ void k_su_trow(int n, const int* sp, const int* sc, int* tlen, const long long* tp,
+                          int* tc, int fill) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  int head[kSetupW];
+  const int b = sp[r], L = sp[r + 1] - b;
+  for (int t = 0; t < L; t++) head[t] = sp[sc[b + t]];
+  long long out = fill ? tp[r] : 0;
+  int cnt = 0, last = -1;
+  bool diag_done = false;
+  for (;;) {
+    int best = 0x7fffffff;
+    for (int t = 0; t < L; t++) {
+      const int k = sc[b + t];
+      if (head[t] < sp[k + 1]) best = min(best, sc[head[t]]);
+    }
+    if (!diag_done && r < best) best = r;  // the identity's entry
+    if (best == 0x7fffffff) break;
+    if (best == r) diag_done = true;
+    for (int t = 0; t < L; t++) {
+      const int k = sc[b + t];
+      if (head[t] < sp[k + 1] && sc[head[t]] == best) head[t]++;
+    }
+    if (best != last) {
+      if (fill) tc[out + cnt] = best;
+      cnt++;
+      last = best;
+    }
+  }
+  if (!fill) tlen[r] = cnt;
+}
+
+// s2t (S entry -> its T position) and diagT
+__global__ void k_su_s2t(int n, const int* sp, const int* sc, const long long* tp, const int* tc,
+                         int* s2t, int* diagT) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  for (int q = sp[r]; q < sp[r + 1]; q++) s2t[q] = (int)dfind64(tc, tp[r], tp[r + 1], sc[q]);
+  diagT[r] = (int)dfind64(tc, tp[r], tp[r + 1], r);
+}
+
+// Y = A X: for (r,j) in T, k over S(r) merged with S(j); pairs (a_rk, x_kj)
+__global__ void k_su_y(int n, const int* sp, const int* sc, const long long* tp, const int* tc,
+                       int* cnt, const long long* ptr, int* ia, int* ib, int fill) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  for (long long f = tp[r]; f < tp[r + 1]; f++) {
+    const int j = tc[f];
+    int p = sp[r], q = sp[j], c = 0;
+    long long o = fill ? ptr[f] : 0;
+    while (p < sp[r + 1] && q < sp[j + 1]) {
+      if (sc[p] < sc[q]) p++;
+      else if (sc[q] < sc[p]) q++;
+      else {
+        if (fill) {
+          const int k = sc[p];
+          ia[o + c] = p;
+          ib[o + c] = dfind(sc, sp[k], sp[k + 1], j);
+        }
+        c++;
+        p++;
+        q++;
+      }
+    }
+    if (!fill) cnt[f] = c;
+  }
+}
+
+// dX[k,j] = sum_r a_rk dy_rj: r over S(k) merged with T(j); pairs (a_rk, dy_rj)
+__global__ void k_su_x(int n, const int* sp, const int* sc, const long long* tp, const int* tc,
+                       int* cnt, const long long* ptr, int* ia, int* ib, int fill) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  for (int e = sp[k]; e < sp[k + 1]; e++) {
+    const int j = sc[e];
+    int p = sp[k];
+    long long q = tp[j];
+    int c = 0;
+    long long o = fill ? ptr[e] : 0;
+    while (p < sp[k + 1] && q < tp[j + 1]) {
+      if (sc[p] < tc[q]) p++;
+      else if (tc[q] < sc[p]) q++;
+      else {
+        if (fill) {
+          const int r = sc[p];
+          ia[o + c] = dfind(sc, sp[r], sp[r + 1], k);
+          ib[o + c] = (int)dfind64(tc, tp[r], tp[r + 1], j);
+        }
+        c++;
+        p++;
+        q++;
+      }
+    }
+    if (!fill) cnt[e] = c;
+  }
+}
+
+// dA[r,k] = sum_j dy_rj x_kj: j over T(r) merged with S(k); pairs (dy_rj, x_kj)
+__global__ void k_su_d(int n, const int* sp, const int* sc, const long long* tp, const int* tc,
+                       int* cnt, const long long* ptr, int* ia, int* ib, int fill) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  for (int e = sp[r]; e < sp[r + 1]; e++) {
+    const int k = sc[e];
+    long long p = tp[r];
+    int q = sp[k], c = 0;
+    long long o = fill ? ptr[e] : 0;
+    while (p < tp[r + 1] && q < sp[k + 1]) {
+      if (tc[p] < sc[q]) p++;
+      else if (sc[q] < tc[p]) q++;
+      else {
+        if (fill) {
+          ia[o + c] = (int)p;
+          ib[o + c] = q;
+        }
+        c++;
+        p++;
+        q++;
+      }
+    }
+    if (!fill) cnt[e] = c;
+  }
+}
+
+// LOMR's step coefficients from uu, vv, uv, ur, vr (the same formulas and
+// fallback as the column pass); returns true for an MR step (gamma = 0)
+bool lomr_coef(const double* t, double* delta, double* gamma) {
+  const double uu = t[0], vv = t[1], uv = t[2], ur = t[3], vr = t[4];
+  const double t1 = uu * vv, t2 = uv * uv, cc = t1 - t2;
+  if (vv == 0.0 || cc <= (64.0 * 2.220446049250313e-16) * t1) {
+    *delta = ur / uu;
+    *gamma = 0.0;
+    return true;
+  }
+  const double d1 = vv * ur, d2 = uv * vr, g1 = uu * vr, g2 = uv * ur;
+  *delta = (d1 - d2) / cc;
+  *gamma = (g1 - g2) / cc;
+  return false;
+}
+
+// LOMR buffers, allocated when the method is chosen
+int alloc_lomr(spai_fpmr_ctx* h) {
+  if (h->d_Pck) return SPAI_OK;
+  const int vs = h->vs;
+  int rc = valloc(&h->d_Pck, (size_t)(h->K + 1) * h->nS, vs);
+  rc = rc ? rc : valloc(&h->d_V, h->nT, vs);
+  rc = rc ? rc : valloc(&h->d_dV, h->nT, vs);
+  rc = rc ? rc : valloc(&h->d_dS, h->nS, vs);
+  rc = rc ? rc : valloc(&h->d_dPp, h->nS, vs);
+  rc = rc ? rc : valloc(&h->d_dPn, h->nS, vs);
+  if (rc) {
+    ffree(h->d_Pck);
+    ffree(h->d_V);
+    ffree(h->d_dV);
+    ffree(h->d_dS);
+    ffree(h->d_dPp);
+    ffree(h->d_dPn);
+  }
+  return rc;
+}
+
+// K LOMR steps from the M_0 already in the first checkpoint; loss in *loss
+int forward_lomr(spai_fpmr_ctx* h, double* loss) {
+  const long long nS = h->nS, nT = h->nT;
+  const int vs = h->vs, K = h->K;
+  FP_DISPATCH(h, k_m0, nblk(nS), nS, (T_*)h->d_Pck);  // P_{-1} = 0
+  FCK(cudaGetLastError());
+  h->delta.assign(K, 0.0);
+  h->gamma.assign(K, 0.0);
+  h->prod.assign(5 * (size_t)K, 0.0);
+  h->mrstep.assign(K, 0);
+  for (int i = 0; i < K; i++) {
+    void* M = at(h->d_Mck, vs, (long long)i * nS);
+    void* Mn = at(h->d_Mck, vs, (long long)(i + 1) * nS);
+    void* Pp = at(h->d_Pck, vs, (long long)i * nS);
+    void* Pn = at(h->d_Pck, vs, (long long)(i + 1) * nS);
+    // R, Z = mask_S(R) (in d_P), U = A Z (in d_Q), V = A P_{i-1}
+    int rc = step_products(h, M, true);
+    if (!rc) rc = seg_prod(h, h->Y, h->d_A, Pp, h->d_V, 1.0, 0);
+    if (!rc) rc = dot(h, nT, h->d_Q, h->d_Q, 0);
+    if (!rc) rc = dot(h, nT, h->d_V, h->d_V, 1);
+    if (!rc) rc = dot(h, nT, h->d_Q, h->d_V, 2);
+    if (!rc) rc = dot(h, nT, h->d_Q, h->d_R, 3);
+    if (!rc) rc = dot(h, nT, h->d_V, h->d_R, 4);
+    double t[5];
+    if (!rc) rc = read_res(h, t, 5);
+    if (rc) return rc;
+    if (!(t[0] > 0.0)) return SPAI_ERR_NONFINITE;
+    double d, g;
+    h->mrstep[i] = lomr_coef(t, &d, &g) ? 1 : 0;
+    if (!std::isfinite(d) || !std::isfinite(g)) return SPAI_ERR_NONFINITE;
+    h->delta[i] = d;
+    h->gamma[i] = g;
+    for (int q = 0; q < 5; q++) h->prod[5 * (size_t)i + q] = t[q];
+    // S = delta Z + gamma P_{i-1} (= P_i);  M_{i+1} = M_i + S
+    FP_DISPATCH(h, k_lin2, nblk(nS), nS, d, (const T_*)h->d_P, g, (const T_*)Pp, (T_*)Pn);
+    FP_DISPATCH(h, k_copy, nblk(nS), nS, (const T_*)M, (T_*)Mn);
+    FP_DISPATCH(h, k_axby, nblk(nS), nS, 1.0, (const T_*)Pn, 1.0, (T_*)Mn);
+    FCK(cudaGetLastError());
+  }
+  int rc = step_products(h, at(h->d_Mck, vs, (long long)K * nS), false);
+  if (!rc) rc = dot(h, nT, h->d_R, h->d_R, 0);
+  if (!rc) rc = read_res(h, loss, 1);
+  return rc;
+}
+
+// reverse mode through the K LOMR steps; dA (d_dA) and dM (d_dM) already
+// hold the contributions of the final residual
+int backward_lomr(spai_fpmr_ctx* h) {
+  const long long nS = h->nS, nT = h->nT;
+  const int vs = h->vs;
+  FP_DISPATCH(h, k_m0, nblk(nS), nS, (T_*)h->d_dPn);  // nothing flows into P_{K-1}
+  FCK(cudaGetLastError());
+  for (int i = h->K - 1; i >= 0; i--) {
+    const void* M = at(h->d_Mck, vs, (long long)i * nS);
+    const void* Pp = at(h->d_Pck, vs, (long long)i * nS);
+    const double d = h->delta[i], g = h->gamma[i];
+    const double* t = &h->prod[5 * (size_t)i];
+    const double uu = t[0], vv = t[1], uv = t[2], ur = t[3], vr = t[4];
+    int rc = step_products(h, M, true);  // R, Z (d_P), U (d_Q)
+    if (!rc) rc = seg_prod(h, h->Y, h->d_A, Pp, h->d_V, 1.0, 0);
+    if (rc) return rc;
+    // dS = dM_{i+1} + dP_i;  d(delta) = (dS, Z), d(gamma) = (dS, P_{i-1})
+    FP_DISPATCH(h, k_lin2, nblk(nS), nS, 1.0, (const T_*)h->d_dM, 1.0, (const T_*)h->d_dPn,
+                (T_*)h->d_dS);
+    FCK(cudaGetLastError());
+    rc = dot(h, nS, h->d_dS, h->d_P, 0);
+    if (!rc) rc = dot(h, nS, h->d_dS, Pp, 1);
+    double dg2[2];
+    if (!rc) rc = read_res(h, dg2, 2);
+    if (rc) return rc;
+    const double dd = dg2[0], dgam = dg2[1];
+    double duu, dvv, duv, dur, dvr;
+    if (h->mrstep[i]) {
+      duu = -dd * d / uu;
+      dur = dd / uu;
+      dvv = duv = dvr = 0.0;
+    } else {
+      const double c = uu * vv - uv * uv;
+      duu = (dd * (-d * vv) + dgam * (vr - g * vv)) / c;
+      dvv = (dd * (ur - d * uu) + dgam * (-g * uu)) / c;
+      duv = (dd * (-vr + 2.0 * d * uv) + dgam * (-ur + 2.0 * g * uv)) / c;
+      dur = (dd * vv - dgam * uv) / c;
+      dvr = (-dd * uv + dgam * uu) / c;
+    }
+    // dZ = delta dS (in d_dP), dP_{i-1} = gamma dS;  dU, dV, dR on T
+    FP_DISPATCH(h, k_axby, nblk(nS), nS, d, (const T_*)h->d_dS, 0.0, (T_*)h->d_dP);
+    FP_DISPATCH(h, k_axby, nblk(nS), nS, g, (const T_*)h->d_dS, 0.0, (T_*)h->d_dPp);
+    FP_DISPATCH(h, k_lin3, nblk(nT), nT, 2.0 * duu, (const T_*)h->d_Q, duv, (const T_*)h->d_V, dur,
+                (const T_*)h->d_R, (T_*)h->d_dQ);
+    FP_DISPATCH(h, k_lin3, nblk(nT), nT, 2.0 * dvv, (const T_*)h->d_V, duv, (const T_*)h->d_Q, dvr,
+                (const T_*)h->d_R, (T_*)h->d_dV);
+    FP_DISPATCH(h, k_lin2, nblk(nT), nT, dur, (const T_*)h->d_Q, dvr, (const T_*)h->d_V,
+                (T_*)h->d_dR);
+    FCK(cudaGetLastError());
+    // U = A Z: dA += mask_S(dU Z^T), dZ += mask_S(A^T dU);  V = A P_{i-1} likewise
+    rc = seg_prod(h, h->D, h->d_dQ, h->d_P, h->d_dA, 1.0, 1);
+    if (!rc) rc = seg_prod(h, h->X, h->d_A, h->d_dQ, h->d_dP, 1.0, 1);
+    if (!rc) rc = seg_prod(h, h->D, h->d_dV, Pp, h->d_dA, 1.0, 1);
+    if (!rc) rc = seg_prod(h, h->X, h->d_A, h->d_dV, h->d_dPp, 1.0, 1);
+    if (rc) return rc;
+    // Z = mask_S(R): dR += dZ;  R = I - A M: dA -= mask_S(dR M^T), dM -= mask_S(A^T dR)
+    FP_DISPATCH(h, k_scatter_add, nblk(nS), nS, h->d_s2t, (const T_*)h->d_dP, (T_*)h->d_dR);
+    FCK(cudaGetLastError());
+    rc = seg_prod(h, h->D, h->d_dR, M, h->d_dA, -1.0, 1);
+    if (!rc) rc = seg_prod(h, h->X, h->d_A, h->d_dR, h->d_dM, -1.0, 1);
+    if (rc) return rc;
+    std::swap(h->d_dPn, h->d_dPp);  // dP_{i-1} flows into the step before
+  }
+  return SPAI_OK;
+}
+
+// The patterns and product lists built on the host (rows of any length).
+int setup_host(spai_fpmr_ctx* h, const int32_t* rowptr, const int32_t* colind) {
+  const int64_t n = h->n, nnz = h->nS;
+  cudaStream_t st = h->stream;
   // S: A's pattern, rows strictly ascending, symmetric, full diagonal
   std::vector<long long> sp(n + 1);
   std::vector<int> sc(colind, colind + nnz);
@@ -420,6 +778,7 @@ int spai_fpmr_create(spai_fpmr_handle* out, int64_t n, int64_t nnz, const int32_
   }
   const long long nS = nnz, nT = (long long)tc.size();
   if (nT >= (1LL << 31)) return SPAI_ERR_UNSUPPORTED;
+  h->nT = nT;
   std::vector<int> s2t(nS);
   for (int64_t r = 0; r < n; r++) {
     diagT[r] = (int)find_pos(tp, tc, (int)r, (int)r);
@@ -481,30 +840,131 @@ int spai_fpmr_create(spai_fpmr_handle* out, int64_t n, int64_t nnz, const int32_
       }
       dp[e + 1] = (long long)da.size();
     }
-  spai_fpmr_ctx* h = new (std::nothrow) spai_fpmr_ctx();
-  if (!h) return SPAI_ERR_OOM;
-  h->n = (int)n;
-  h->K = K;
-  h->vs = prec == SPAI_MIXED ? 4 : 8;
-  h->nS = nS;
-  h->nT = nT;
-  if (stream) {
-    h->stream = (cudaStream_t)stream;
-  } else {
-    if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess) {
-      (void)cudaGetLastError();
-      delete h;
-      return SPAI_ERR_CUDA;
-    }
-    h->own_stream = true;
-  }
-  cudaStream_t st = h->stream;
-  const long long nbmax = (nT + (long long)kDotBlock * kDotChunk - 1) / ((long long)kDotBlock * kDotChunk);
   int rc = SPAI_OK;
   rc = rc ? rc : falloc(&h->d_diagS, n);
   rc = rc ? rc : falloc(&h->d_diagT, n);
   rc = rc ? rc : falloc(&h->d_s2t, nS);
-  const int vs = h->vs;
+  rc = rc ? rc : upload_list(h->Y, yp, ya, yb, st);
+  rc = rc ? rc : upload_list(h->X, xp, xa, xb, st);
+  rc = rc ? rc : upload_list(h->D, dp, da, db, st);
+  if (!rc) {
+    bool ok = cudaMemcpyAsync(h->d_diagS, diagS.data(), sizeof(int) * n, cudaMemcpyHostToDevice, st) == 0;
+    ok &= cudaMemcpyAsync(h->d_diagT, diagT.data(), sizeof(int) * n, cudaMemcpyHostToDevice, st) == 0;
+    ok &= cudaMemcpyAsync(h->d_s2t, s2t.data(), sizeof(int) * nS, cudaMemcpyHostToDevice, st) == 0;
+    ok &= cudaStreamSynchronize(st) == 0;
+    if (!ok) rc = SPAI_ERR_CUDA;
+  }
+  return rc;
+}
+
+// The patterns and product lists built on the GPU (rows of at most kSetupW
+// entries), in the same order as setup_host.
+int setup_device(spai_fpmr_ctx* h, const int32_t* rowptr, const int32_t* colind) {
+  const int n = h->n;
+  const long long nS = h->nS;
+  cudaStream_t st = h->stream;
+  int *d_sp = nullptr, *d_sc = nullptr, *d_err = nullptr, *d_tlen = nullptr, *d_tc = nullptr,
+      *d_cnt = nullptr;
+  long long *d_tp = nullptr, *d_tmp = nullptr;
+  auto done = [&](int rc) {
+    ffree(d_sp);
+    ffree(d_sc);
+    ffree(d_err);
+    ffree(d_tlen);
+    ffree(d_tc);
+    ffree(d_cnt);
+    ffree(d_tp);
+    ffree(d_tmp);
+    return rc;
+  };
+  const unsigned gr = nblk(n);
+  int rc = falloc(&d_sp, (size_t)n + 1);
+  rc = rc ? rc : falloc(&d_sc, (size_t)nS);
+  rc = rc ? rc : falloc(&d_err, 3);
+  rc = rc ? rc : falloc(&h->d_diagS, (size_t)n);
+  rc = rc ? rc : falloc(&h->d_diagT, (size_t)n);
+  rc = rc ? rc : falloc(&h->d_s2t, (size_t)nS);
+  rc = rc ? rc : falloc(&d_tlen, (size_t)n);
+  rc = rc ? rc : falloc(&d_tp, (size_t)n + 1);
+  if (rc) return done(rc);
+  const int err0[3] = {0, 0x7fffffff, 0x7fffffff};
+  int err[3];
+  if (cudaMemcpyAsync(d_sp, rowptr, sizeof(int) * ((size_t)n + 1), cudaMemcpyHostToDevice, st) ||
+      cudaMemcpyAsync(d_sc, colind, sizeof(int) * (size_t)nS, cudaMemcpyHostToDevice, st) ||
+      cudaMemcpyAsync(d_err, err0, sizeof(err0), cudaMemcpyHostToDevice, st))
+    return done(SPAI_ERR_CUDA);
+  // S: rows strictly ascending and in range; full diagonal; symmetric
+  k_su_check<<<gr, 256, 0, st>>>(n, d_sp, d_sc, d_err);
+  k_su_diag_sym<<<gr, 256, 0, st>>>(n, d_sp, d_sc, h->d_diagS, d_err);
+  if (cudaMemcpyAsync(err, d_err, sizeof(err), cudaMemcpyDeviceToHost, st) ||
+      cudaStreamSynchronize(st))
+    return done(SPAI_ERR_CUDA);
+  if (err[0]) return done(SPAI_ERR_CSR);
+  if (err[1] != 0x7fffffff && err[1] <= err[2]) return done(SPAI_ERR_NOT_SPD_DIAG);
+  if (err[2] != 0x7fffffff) return done(SPAI_ERR_NOT_SYMMETRIC);
+  // an exclusive scan of counts c[0..m) into p[0..m], total read back
+  long long tmp_cap = 0;
+  auto scan = [&](const int* c, long long* p, long long m, long long* total) -> int {
+    const long long need = 2 * ((m + 1023) / 1024) + 2;
+    if (need > tmp_cap) {
+      ffree(d_tmp);
+      int r2 = falloc(&d_tmp, (size_t)need);
+      if (r2) return r2;
+      tmp_cap = need;
+    }
+    if (spai::launch_exclusive_scan(c, p, (int)m, d_tmp, st) != cudaSuccess) return SPAI_ERR_CUDA;
+    if (cudaMemcpyAsync(total, p + m, sizeof(long long), cudaMemcpyDeviceToHost, st) ||
+        cudaStreamSynchronize(st))
+      return SPAI_ERR_CUDA;
+    return SPAI_OK;
+  };
+  // T = supp(A S) + I
+  k_su_trow<<<gr, 256, 0, st>>>(n, d_sp, d_sc, d_tlen, nullptr, nullptr, 0);
+  long long nT = 0;
+  rc = scan(d_tlen, d_tp, n, &nT);
+  if (rc) return done(rc);
+  if (nT >= (1LL << 31)) return done(SPAI_ERR_UNSUPPORTED);
+  h->nT = nT;
+  rc = falloc(&d_tc, (size_t)nT);
+  if (rc) return done(rc);
+  k_su_trow<<<gr, 256, 0, st>>>(n, d_sp, d_sc, nullptr, d_tp, d_tc, 1);
+  k_su_s2t<<<gr, 256, 0, st>>>(n, d_sp, d_sc, d_tp, d_tc, h->d_s2t, h->d_diagT);
+  // the three product lists: count, scan, fill
+  rc = falloc(&d_cnt, (size_t)std::max(nT, nS));
+  if (rc) return done(rc);
+  for (int which = 0; which < 3; which++) {
+    ProdList& L = which == 0 ? h->Y : which == 1 ? h->X : h->D;
+    const long long nout = which == 0 ? nT : nS;
+    auto run = [&](long long* ptr, int* ia, int* ib, int fill) {
+      if (which == 0) k_su_y<<<gr, 256, 0, st>>>(n, d_sp, d_sc, d_tp, d_tc, d_cnt, ptr, ia, ib, fill);
+      else if (which == 1) k_su_x<<<gr, 256, 0, st>>>(n, d_sp, d_sc, d_tp, d_tc, d_cnt, ptr, ia, ib, fill);
+      else k_su_d<<<gr, 256, 0, st>>>(n, d_sp, d_sc, d_tp, d_tc, d_cnt, ptr, ia, ib, fill);
+    };
+    run(nullptr, nullptr, nullptr, 0);
+    rc = falloc(&L.ptr, (size_t)nout + 1);
+    if (rc) return done(rc);
+    long long len = 0;
+    rc = scan(d_cnt, L.ptr, nout, &len);
+    if (rc) return done(rc);
+    L.nout = nout;
+    L.len = len;
+    rc = falloc(&L.ia, (size_t)len);
+    rc = rc ? rc : falloc(&L.ib, (size_t)len);
+    if (rc) return done(rc);
+    run(L.ptr, L.ia, L.ib, 1);
+  }
+  if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess)
+    return done(SPAI_ERR_CUDA);
+  return done(SPAI_OK);
+}
+
+// the value arrays of the forward and backward passes
+int alloc_values(spai_fpmr_ctx* h) {
+  const long long nS = h->nS, nT = h->nT;
+  const int vs = h->vs, K = h->K;
+  const long long nbmax =
+      (nT + (long long)kDotBlock * kDotChunk - 1) / ((long long)kDotBlock * kDotChunk);
+  int rc = SPAI_OK;
   rc = rc ? rc : valloc(&h->d_A, nS, vs);
   rc = rc ? rc : valloc(&h->d_Mck, (size_t)(K + 1) * nS, vs);
   rc = rc ? rc : valloc(&h->d_P, nS, vs);
@@ -518,16 +978,58 @@ int spai_fpmr_create(spai_fpmr_handle* out, int64_t n, int64_t nnz, const int32_
   rc = rc ? rc : falloc(&h->d_stage, nS);
   rc = rc ? rc : falloc(&h->d_part, std::max(nbmax, 1LL));
   rc = rc ? rc : falloc(&h->d_res, 8);
-  rc = rc ? rc : upload_list(h->Y, yp, ya, yb, st);
-  rc = rc ? rc : upload_list(h->X, xp, xa, xb, st);
-  rc = rc ? rc : upload_list(h->D, dp, da, db, st);
-  if (!rc) {
-    bool ok = cudaMemcpyAsync(h->d_diagS, diagS.data(), sizeof(int) * n, cudaMemcpyHostToDevice, st) == 0;
-    ok &= cudaMemcpyAsync(h->d_diagT, diagT.data(), sizeof(int) * n, cudaMemcpyHostToDevice, st) == 0;
-    ok &= cudaMemcpyAsync(h->d_s2t, s2t.data(), sizeof(int) * nS, cudaMemcpyHostToDevice, st) == 0;
-    ok &= cudaStreamSynchronize(st) == 0;
-    if (!ok) rc = SPAI_ERR_CUDA;
+  return rc;
+}
+
+}  // namespace
+
+extern "C" {
+
+int spai_fpmr_set_method(spai_fpmr_handle h, int method) {
+  if (!h || (method != SPAI_MR && method != SPAI_LOMR)) return SPAI_ERR_ARG;
+  if (method == SPAI_LOMR) {
+    int rc = alloc_lomr(h);
+    if (rc) return rc;
   }
+  h->method = method;
+  h->have_forward = false;
+  return SPAI_OK;
+}
+
+int spai_fpmr_create(spai_fpmr_handle* out, int64_t n, int64_t nnz, const int32_t* rowptr,
+                     const int32_t* colind, int K, int prec, void* stream) {
+  if (!out) return SPAI_ERR_ARG;
+  *out = nullptr;
+  if (n < 1 || nnz < 1 || !rowptr || !colind || K < 0 || K > 1000) return SPAI_ERR_ARG;
+  if (prec != SPAI_FP64 && prec != SPAI_MIXED) return SPAI_ERR_ARG;
+  if (n >= (1LL << 31) || nnz >= (1LL << 31)) return SPAI_ERR_UNSUPPORTED;
+  if (rowptr[0] != 0 || rowptr[n] != nnz) return SPAI_ERR_CSR;
+  int W = 0;
+  for (int64_t i = 0; i < n; i++) {
+    if (rowptr[i + 1] < rowptr[i]) return SPAI_ERR_CSR;
+    W = std::max(W, rowptr[i + 1] - rowptr[i]);
+  }
+  spai_fpmr_ctx* h = new (std::nothrow) spai_fpmr_ctx();
+  if (!h) return SPAI_ERR_OOM;
+  h->n = (int)n;
+  h->K = K;
+  h->vs = prec == SPAI_MIXED ? 4 : 8;
+  h->nS = nnz;
+  if (stream) {
+    h->stream = (cudaStream_t)stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      (void)cudaGetLastError();
+      delete h;
+      return SPAI_ERR_CUDA;
+    }
+    h->own_stream = true;
+  }
+  // SPAI_FPMR_HOST_SETUP=1 takes the host construction for any pattern (tests)
+  const char* hs = getenv("SPAI_FPMR_HOST_SETUP");
+  const bool host = W > kSetupW || (hs && atoi(hs) == 1);
+  int rc = host ? setup_host(h, rowptr, colind) : setup_device(h, rowptr, colind);
+  if (!rc) rc = alloc_values(h);
   if (rc) {
     (void)cudaGetLastError();
     free_fpmr(h);
@@ -559,6 +1061,14 @@ int spai_fpmr_forward(spai_fpmr_handle h, const double* vals, int on_device, dou
   FP_DISPATCH(h, k_m0, nblk(nS), nS, (T_*)h->d_Mck);
   FP_DISPATCH(h, k_m0_diag, nblk(h->n), h->n, h->d_diagS, (const T_*)h->d_A, (T_*)h->d_Mck);
   FCK(cudaGetLastError());
+  if (h->method == SPAI_LOMR) {
+    double l = 0.0;
+    int rc = forward_lomr(h, &l);
+    if (rc) return rc;
+    *loss = l;
+    h->have_forward = true;
+    return std::isfinite(l) ? SPAI_OK : SPAI_ERR_NONFINITE;
+  }
   h->alpha.assign(h->K, 0.0);
   h->num.assign(h->K, 0.0);
   h->den.assign(h->K, 0.0);
@@ -605,7 +1115,9 @@ int spai_fpmr_backward(spai_fpmr_handle h, double dloss, double* dvals, int on_d
   rc = seg_prod(h, h->D, h->d_dR, MK, h->d_dA, -1.0, 0);
   if (!rc) rc = seg_prod(h, h->X, h->d_A, h->d_dR, h->d_dM, -1.0, 0);
   if (rc) return rc;
-  for (int i = K - 1; i >= 0; i--) {
+  if (h->method == SPAI_LOMR) rc = backward_lomr(h);
+  if (rc) return rc;
+  for (int i = h->method == SPAI_LOMR ? -1 : K - 1; i >= 0; i--) {
     const void* M = at(h->d_Mck, vs, (long long)i * nS);
     const double a = h->alpha[i], den = h->den[i];
     rc = step_products(h, M, true);  // R_i, P_i, Q_i

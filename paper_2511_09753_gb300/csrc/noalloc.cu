@@ -103,8 +103,9 @@ k_true_residual_noalloc(int n, const int32_t* rp, const int32_t* ci, const doubl
       if (lane == 0) ws->gsum[q][g] = s;
     }
   }
+  // the host clears cnt1 and cnt2 before every launch (they keep whatever an
+  // earlier or aborted call left), so the kernel leaves them as they are
   if (threadIdx.x == 0) {
-    ws->cnt1[g] = 0;
     __threadfence();
     unsigned old = atomicAdd(&ws->cnt2, 1u);
     s_last = old == (unsigned)(ngroups - 1);
@@ -127,7 +128,6 @@ k_true_residual_noalloc(int n, const int32_t* rp, const int32_t* ci, const doubl
       __syncwarp();
     }
   }
-  if (threadIdx.x == 0) ws->cnt2 = 0;
 }
 
 std::mutex g_na_mutex;

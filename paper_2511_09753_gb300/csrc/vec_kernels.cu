@@ -13,6 +13,10 @@
 
 namespace spai {
 
+// rows of S longer than this are multiplied by a whole warp (sliced-ELL
+// threads take the others)
+constexpr int kLongRow = 64;
+
 // ------------------------------------------------------------- reduction
 
 // Each thread contributes one term (its element); the CTA (256 threads)
@@ -117,6 +121,22 @@ __device__ __forceinline__ double sell_chain_f32(const SellM& m, const float* v3
   return (double)acc;
 }
 
+// Row i of a CSR matrix (row pointers rp) from its sliced-ELL copy: the loads
+// are coalesced as in sell_chain, and the chain stops at the row's own length,
+// so it is the CSR chain of row_chain entry for entry.
+__device__ __forceinline__ double sell_row_chain(const SellM& m, const long long* rp,
+                                                 const double* x, int i) {
+  const int s = i >> 5, lane = i & 31;
+  const long long b = m.sptr[s];
+  const int len = (int)(rp[i + 1] - rp[i]);
+  double acc = 0.0;
+  for (int t = 0; t < len; t++) {
+    long long e = b + 32LL * t + lane;
+    acc = __fma_rn(m.val[e], x[m.col[e]], acc);
+  }
+  return acc;
+}
+
 template <typename RP>
 __device__ __forceinline__ double row_chain_f32(const RP* rp, const int* ci, const float* v,
                                                 const float* x, int i) {
@@ -137,19 +157,24 @@ cudaError_t launch_to_f32(const double* in, float* out, long long count, cudaStr
   return cudaGetLastError();
 }
 
+// Rows longer than maxw are left out of the sliced ELL (stored as empty rows):
+// their products are formed from the CSR arrays by a whole warp.
 template <typename RP>
-__global__ void k_sell_width(int n, const RP* rp, int* w32) {
+__global__ void k_sell_width(int n, const RP* rp, int* w32, int maxw) {
   int s = blockIdx.x * blockDim.x + threadIdx.x;
   int ns = (n + 31) / 32;
   if (s >= ns) return;
   int w = 0;
-  for (int i = 32 * s; i < min(n, 32 * s + 32); i++) w = max(w, (int)(rp[i + 1] - rp[i]));
+  for (int i = 32 * s; i < min(n, 32 * s + 32); i++) {
+    const int len = (int)(rp[i + 1] - rp[i]);
+    if (len <= maxw) w = max(w, len);
+  }
   w32[s] = 32 * w;
 }
 
 template <typename RP>
 __global__ void k_sell_fill(int n, const RP* rp, const int* ci, const double* v,
-                            const long long* sptr, int* scol, double* sval) {
+                            const long long* sptr, int* scol, double* sval, int maxw) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   int ns = (n + 31) / 32;
   if (i >= 32 * ns) return;
@@ -157,6 +182,7 @@ __global__ void k_sell_fill(int n, const RP* rp, const int* ci, const double* v,
   const long long b = sptr[s];
   const int w = (int)((sptr[s + 1] - b) >> 5);
   long long e0 = i < n ? (long long)rp[i] : 0, e1 = i < n ? (long long)rp[i + 1] : 0;
+  if (e1 - e0 > maxw) e1 = e0;
   for (int t = 0; t < w; t++) {
     long long e = e0 + t;
     long long d = b + 32LL * t + lane;
@@ -173,9 +199,9 @@ __global__ void k_sell_fill(int n, const RP* rp, const int* ci, const double* v,
 template <typename RP>
 static cudaError_t sell_build_t(int n, const RP* rp, const int* ci, const double* v, int* w32,
                                 long long* sptr, long long* scan_tmp, int** scol, double** sval,
-                                long long* cap, long long* total, cudaStream_t st) {
+                                long long* cap, long long* total, cudaStream_t st, int maxw) {
   int ns = (n + 31) / 32;
-  k_sell_width<RP><<<(ns + 255) / 256, 256, 0, st>>>(n, rp, w32);
+  k_sell_width<RP><<<(ns + 255) / 256, 256, 0, st>>>(n, rp, w32, maxw);
   cudaError_t e = launch_exclusive_scan(w32, sptr, ns, scan_tmp, st);
   if (e != cudaSuccess) return e;
   long long tot = 0;
@@ -192,7 +218,7 @@ static cudaError_t sell_build_t(int n, const RP* rp, const int* ci, const double
     if (e != cudaSuccess) return e;
     *cap = tot;
   }
-  k_sell_fill<RP><<<(32 * ns + 255) / 256, 256, 0, st>>>(n, rp, ci, v, sptr, *scol, *sval);
+  k_sell_fill<RP><<<(32 * ns + 255) / 256, 256, 0, st>>>(n, rp, ci, v, sptr, *scol, *sval, maxw);
   *total = tot;
   return cudaGetLastError();
 }
@@ -200,13 +226,15 @@ static cudaError_t sell_build_t(int n, const RP* rp, const int* ci, const double
 cudaError_t launch_sell_build_i32(int n, const int* rp, const int* ci, const double* v, int* w32,
                                   long long* sptr, long long* scan_tmp, int** scol, double** sval,
                                   long long* cap, long long* total, cudaStream_t st) {
-  return sell_build_t<int>(n, rp, ci, v, w32, sptr, scan_tmp, scol, sval, cap, total, st);
+  return sell_build_t<int>(n, rp, ci, v, w32, sptr, scan_tmp, scol, sval, cap, total, st,
+                           0x7fffffff);
 }
 
 cudaError_t launch_sell_build_i64(int n, const long long* rp, const int* ci, const double* v,
                                   int* w32, long long* sptr, long long* scan_tmp, int** scol,
                                   double** sval, long long* cap, long long* total, cudaStream_t st) {
-  return sell_build_t<long long>(n, rp, ci, v, w32, sptr, scan_tmp, scol, sval, cap, total, st);
+  return sell_build_t<long long>(n, rp, ci, v, w32, sptr, scan_tmp, scol, sval, cap, total, st,
+                                 kLongRow);
 }
 
 // ------------------------------------------------------------ set-up
@@ -558,6 +586,50 @@ __device__ __forceinline__ double precond_apply(const PcgArgs& a, int i) {
   return row_chain(a.mrp, a.mci, a.mv, a.r, i);
 }
 
+// z_i = (S r)_i of a row of at most kLongRow entries from the sliced ELL (a
+// longer row's z_i was written by k_pcg_prec_long before)
+__device__ __forceinline__ double precond_sell(const PcgArgs& a, int i) {
+  const int len = (int)(a.mrp[i + 1] - a.mrp[i]);
+  if (len > kLongRow) return a.z[i];
+  return sell_row_chain(a.sell, a.mrp, a.r, i);
+}
+
+// z_i of the rows longer than kLongRow, a warp each: the lanes load 32
+// consecutive CSR entries and their operands at once; the chain itself --
+// the same fma chain over ascending column -- runs on the shuffled values
+__global__ void k_pcg_prec_long(PcgArgs a) {
+  if (a.s->done) return;
+  const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (w >= a.nlong) return;
+  const int row = a.longrows[w];
+  const long long rb = a.mrp[row], re = a.mrp[row + 1];
+  double acc = 0.0;
+  for (long long base = rb; base < re; base += 32) {
+    const long long e = base + lane;
+    double vv = 0.0, xx = 0.0;
+    if (e < re) {
+      vv = a.mv[e];
+      xx = a.r[a.mci[e]];
+    }
+    const int cnt = (int)min(32LL, re - base);
+    for (int t = 0; t < cnt; t++)
+      acc = __fma_rn(__shfl_sync(kFull, vv, t), __shfl_sync(kFull, xx, t), acc);
+  }
+  if (lane == 0) a.z[row] = acc;
+}
+
+__global__ void k_long_rows(int n, const long long* rp, int* out, int* nout) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n && rp[i + 1] - rp[i] > kLongRow) out[atomicAdd(nout, 1)] = i;
+}
+
+cudaError_t launch_long_rows(int n, const long long* rp, int* out, int* nout, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(nout, 0, sizeof(int), st);
+  if (e != cudaSuccess) return e;
+  k_long_rows<<<(n + 255) / 256, 256, 0, st>>>(n, rp, out, nout);
+  return cudaGetLastError();
+}
+
 // init: x = 0, r = b, terms b_i^2 -> bn
 __global__ void k_pcg_init(PcgArgs a) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -583,7 +655,13 @@ __global__ void k_pcg_prec(PcgArgs a, int first) {
   if (a.s->done) return;
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   double term = 0.0;
-  if (i < a.n) {
+  if (a.sell.sptr) {  // S in sliced ELL (FP64 products)
+    if (i < a.n) {
+      const double z = precond_sell(a, i);
+      a.z[i] = z;
+      term = __dmul_rn(a.r[i], z);
+    }
+  } else if (i < a.n) {
     double z = precond_apply(a, i);
     a.z[i] = z;
     term = __dmul_rn(a.r[i], z);
@@ -762,6 +840,7 @@ cudaError_t launch_lz_step(const LzArgs& a, int j, cudaStream_t st) {
 cudaError_t launch_pcg_init(const PcgArgs& a, cudaStream_t st) {
   int g = (a.n + 255) / 256;
   k_pcg_init<<<g, 256, 0, st>>>(a);
+  if (a.nlong) k_pcg_prec_long<<<(a.nlong + 7) / 8, 256, 0, st>>>(a);
   k_pcg_prec<<<g, 256, 0, st>>>(a, 1);
   k_pcg_dir<<<g, 256, 0, st>>>(a, 1);
   return cudaGetLastError();
@@ -771,6 +850,7 @@ cudaError_t launch_pcg_iter(const PcgArgs& a, cudaStream_t st) {
   int g = (a.n + 255) / 256;
   k_pcg_spmv<<<g, 256, 0, st>>>(a);
   k_pcg_update<<<g, 256, 0, st>>>(a);
+  if (a.nlong) k_pcg_prec_long<<<(a.nlong + 7) / 8, 256, 0, st>>>(a);
   k_pcg_prec<<<g, 256, 0, st>>>(a, 0);
   k_pcg_dir<<<g, 256, 0, st>>>(a, 0);
   return cudaGetLastError();

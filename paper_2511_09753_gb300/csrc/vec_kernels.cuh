@@ -33,6 +33,13 @@ struct PcgArgs {
   const long long* mrp;
   const int* mci;
   const double* mv;
+  // the same rows of S = (M + M^T)/2 in sliced ELL (FP64 products with
+  // precond 3 only; sell.sptr null: the CSR rows above are used); rows
+  // longer than the sliced ELL's limit are listed in longrows[0..nlong) and
+  // get a warp each
+  SellM sell;
+  const int* longrows;
+  int nlong;
   const double* b;
   double *x, *r, *z, *p, *q;
   PcgScalars* s;
@@ -74,6 +81,9 @@ cudaError_t launch_sell_build_i64(int n, const long long* rp, const int* ci, con
                                   int* w32, long long* sptr, long long* scan_tmp, int** scol,
                                   double** sval, long long* cap, long long* total, cudaStream_t st);
 cudaError_t launch_to_f32(const double* in, float* out, long long count, cudaStream_t st);
+// rows of a CSR pattern longer than the sliced ELL's limit, compacted into out
+// (count in *nout, device)
+cudaError_t launch_long_rows(int n, const long long* rp, int* out, int* nout, cudaStream_t st);
 
 // Lanczos on the rows of a symmetric matrix S (definiteness diagnostics)
 struct LzArgs {

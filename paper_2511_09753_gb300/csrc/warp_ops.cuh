@@ -161,15 +161,27 @@ __device__ __forceinline__ void term_add(Fix128& S, const Term& t, int eb) {
   }
 }
 
+// Warp sum of the 32 lanes' accumulators: each 128-bit two's-complement value
+// is cut into six 24-bit limbs (the top one sign-extended to 24 bits, so the
+// limbs represent it modulo 2^144); a limb's warp sum stays below 2^29 and
+// comes from one redux.sync; the limb sums, shifted into place, add up to the
+// total modulo 2^128, which is exact because the total fits in 128 bits.
 __device__ __forceinline__ void fix_allreduce(Fix128& S) {
-#pragma unroll
-  for (int o = 16; o >= 1; o >>= 1) {
-    unsigned long long lo2 = __shfl_xor_sync(kFull, S.lo, o);
-    long long hi2 = __shfl_xor_sync(kFull, S.hi, o);
-    unsigned long long sum = S.lo + lo2;
-    S.hi = S.hi + hi2 + (sum < lo2 ? 1 : 0);
-    S.lo = sum;
-  }
+  const unsigned long long lo = S.lo, hi = (unsigned long long)S.hi;
+  const unsigned l0 = (unsigned)lo & 0xffffffu;
+  const unsigned l1 = (unsigned)(lo >> 24) & 0xffffffu;
+  const unsigned l2 = (unsigned)((lo >> 48) | (hi << 16)) & 0xffffffu;
+  const unsigned l3 = (unsigned)(hi >> 8) & 0xffffffu;
+  const unsigned l4 = (unsigned)(hi >> 32) & 0xffffffu;
+  const unsigned l5 = (unsigned)(hi >> 56) | (S.hi < 0 ? 0xffff00u : 0u);
+  const unsigned s0 = __reduce_add_sync(kFull, l0), s1 = __reduce_add_sync(kFull, l1);
+  const unsigned s2 = __reduce_add_sync(kFull, l2), s3 = __reduce_add_sync(kFull, l3);
+  const unsigned s4 = __reduce_add_sync(kFull, l4), s5 = __reduce_add_sync(kFull, l5);
+  unsigned __int128 t = (unsigned __int128)s0 + ((unsigned __int128)s1 << 24) +
+                        ((unsigned __int128)s2 << 48) + ((unsigned __int128)s3 << 72) +
+                        ((unsigned __int128)s4 << 96) + ((unsigned __int128)s5 << 120);
+  S.lo = (unsigned long long)t;
+  S.hi = (long long)(unsigned long long)(t >> 64);
 }
 
 // round S * 2^(eb-1133) to the nearest double (ties to even)
@@ -440,24 +452,31 @@ __device__ __forceinline__ void hist_load(const uint32_t* hist, int lane, unsign
   c[4] = a.z & 0xffffu; c[5] = a.z >> 16; c[6] = a.w & 0xffffu; c[7] = a.w >> 16;
 }
 
-// one count per active lane in bin d, one atomic per distinct digit
+// one count per active lane in bin d: a shared-memory atomic per lane (lanes
+// with the same digit are serialised by the hardware; measured faster than
+// grouping them with __match_any_sync first)
 __device__ __forceinline__ void hist_add(uint32_t* hist, bool act, unsigned d) {
-  unsigned am = __ballot_sync(kFull, act);
-  if (act) {
-    unsigned peers = __match_any_sync(am, d);
-    if ((peers & lanemask_lt()) == 0)
-      atomicAdd(&hist[d >> 1], (unsigned)__popc(peers) << ((d & 1u) * 16u));
-  }
+  if (act) atomicAdd(&hist[d >> 1], 1u << ((d & 1u) * 16u));
+}
+
+// The selection key of an entry: |v| as bits, or the largest key for the row
+// that is always kept (keep_row; -1 for none), so that it ranks first.
+template <typename V>
+__device__ __forceinline__ typename KeyOf<V>::T sel_key(V v, int r, int keep_row) {
+  typedef typename KeyOf<V>::T K;
+  return r == keep_row ? (K)(~(K)0 >> 1) : absbits(v);
 }
 
 // Hard thresholding (Sec. 6.1, per column): copy the `cap` entries of list
 // src with the largest |v| to dst (ties: smaller row), keeping src order.
-// With L <= cap the list is copied.  When `drop` is 0 the list is not
+// Row keep_row (>= 0), when present, is kept and counts toward cap.  With
+// L <= cap the list is copied.  When `drop` is 0 the list is not
 // thresholded; a list longer than cap then raises *overflow and is truncated
 // so that no buffer is overrun.  tie: scratch of L ints.
 template <typename V>
 __device__ int warp_select(const int* sr, const V* sv, int L, int cap, int* dr, V* dv,
-                           uint32_t* hist, int* tie, int drop, int* overflow, int lane) {
+                           uint32_t* hist, int* tie, int drop, int* overflow, int lane,
+                           int keep_row) {
   typedef typename KeyOf<V>::T K;
   if (L <= cap || !drop) {
     if (L > cap) {
@@ -474,8 +493,11 @@ __device__ int warp_select(const int* sr, const V* sv, int L, int cap, int* dr, 
   K prefix = 0, pmask = 0;
   int need = cap;
   bool exact = false;
-  for (int d = (int)sizeof(K) - 1; d >= 0; d--) {
-    const int shift = 8 * d;
+  // digits of 8 bits from the top of the key's 31 (63) significant bits, so
+  // the first digit is the exponent field of an FP32 |v|; the last is shorter
+  for (int hi = 8 * (int)sizeof(K) - 1; hi > 0; hi -= 8) {
+    const int shift = hi > 8 ? hi - 8 : 0;
+    const unsigned dmask = (1u << (hi - shift)) - 1u;
     hist_clear(hist, lane);
     __syncwarp();
     for (int base = 0; base < L; base += 32) {
@@ -483,9 +505,9 @@ __device__ int warp_select(const int* sr, const V* sv, int L, int cap, int* dr, 
       bool act = false;
       unsigned dig = 0;
       if (i < L) {
-        K k = absbits(sv[i]);
+        K k = sel_key(sv[i], sr[i], keep_row);
         act = (k & pmask) == prefix;
-        dig = (unsigned)(k >> shift) & 255u;
+        dig = (unsigned)(k >> shift) & dmask;
       }
       hist_add(hist, act, dig);
     }
@@ -519,7 +541,7 @@ __device__ int warp_select(const int* sr, const V* sv, int L, int cap, int* dr, 
     f_cnt = __shfl_sync(kFull, f_cnt, src);
     need -= f_above;
     prefix |= (K)found << shift;
-    pmask |= (K)255 << shift;
+    pmask |= (K)dmask << shift;
     __syncwarp();
     if (f_cnt == need) {
       exact = true;
@@ -533,7 +555,7 @@ __device__ int warp_select(const int* sr, const V* sv, int L, int cap, int* dr, 
   if (!exact) {
     for (int base = 0; base < L; base += 32) {
       int i = base + lane;
-      bool t = i < L && absbits(sv[i]) == prefix;
+      bool t = i < L && sel_key(sv[i], sr[i], keep_row) == prefix;
       unsigned b = __ballot_sync(kFull, t);
       if (t) tie[ntie + __popc(b & lanemask_lt())] = sr[i];
       ntie += __popc(b);
@@ -549,7 +571,7 @@ __device__ int warp_select(const int* sr, const V* sv, int L, int cap, int* dr, 
     if (i < L) {
       rr = sr[i];
       vv = sv[i];
-      K k = absbits(vv) & pmask;
+      K k = sel_key(vv, rr, keep_row) & pmask;
       keep = k > prefix;
       if (k == prefix) {
         if (exact) {

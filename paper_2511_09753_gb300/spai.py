@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(_HERE, "libspai.so")
 
 SPAI_FP64, SPAI_MIXED = 0, 1
 SPAI_MR, SPAI_LOMR, SPAI_CG = 0, 1, 2
-SPAI_DROP_NONE, SPAI_DROP_TOPK_COL = 0, 1
+SPAI_DROP_NONE, SPAI_DROP_TOPK_COL, SPAI_DROP_TOPK_COL_DIAG = 0, 1, 2
 PREC_NONE, PREC_JACOBI, PREC_SPAI, PREC_SPAI_SYM = 0, 1, 2, 3
 METHODS = {"mr": SPAI_MR, "lomr": SPAI_LOMR, "cg": SPAI_CG,
            "mr_pi": 3, "lomr_pi": 4, "cg_pi": 5}  # Section 5's forms with Pi = diag(A)^{-1}
@@ -34,7 +34,7 @@ EXPORTED = ["spai_validate_csr", "spai_status_string", "spai_create", "spai_dest
             "spai_batch_get_M", "pcg_solve_block", "spai_set_pcg_prec", "spai_sym_lanczos",
             "spai_fixed_pattern", "spai_fpmr_create", "spai_fpmr_forward", "spai_fpmr_backward",
             "spai_fpmr_info", "spai_fpmr_destroy", "spai_autotune", "spai_drop_global",
-            "spai_drop_heuristic", "spai_run_global"]
+            "spai_drop_heuristic", "spai_run_global", "spai_fpmr_set_method"]
 
 
 class SpaiError(RuntimeError):
@@ -49,13 +49,14 @@ class _Opts(C.Structure):
 
 class _Hist(C.Structure):
     _fields_ = [("resnorm", C.c_void_p), ("coef", C.c_void_p), ("iters_done", C.c_int),
-                ("flags", C.c_int)]
+                ("flags", C.c_int), ("nnz", C.c_void_p)]
 
 
 class _Stats(C.Structure):
     _fields_ = [("colpass_launches", C.c_int64), ("colpass_bytes", C.c_int64),
                 ("colpass_ms", C.c_double), ("pcg_launches", C.c_int64),
-                ("other_launches", C.c_int64), ("spgemm_columns", C.c_int64)]
+                ("other_launches", C.c_int64), ("spgemm_columns", C.c_int64),
+                ("colpass_r_bytes", C.c_int64)]
 
 
 _lib = None
@@ -105,6 +106,7 @@ def load():
         "spai_fpmr_backward": (i32, [vp, dbl, vp, i32]),
         "spai_fpmr_info": (i32, [vp, C.POINTER(i64), C.POINTER(i64), C.POINTER(i64)]),
         "spai_fpmr_destroy": (i32, [vp]),
+        "spai_fpmr_set_method": (i32, [vp, i32]),
         "spai_autotune": (i32, [vp, i32, i32, C.POINTER(dbl)]),
         "spai_drop_global": (i32, [vp, i32, i64]),
         "spai_drop_heuristic": (i32, [vp, i64]),
@@ -146,10 +148,44 @@ def _ptr(a):
     return a.ctypes.data, 0, a
 
 
+def _check_noalloc_args(n, rowptr, colind, vals, b, x, out):
+    """The C entry point trusts its device pointers; a host tensor, a wrong
+    dtype or a short array would make the kernel read or write out of bounds.
+    Checked here, before anything is launched."""
+    import torch
+    n = int(n)
+    named = (("rowptr", rowptr, torch.int32), ("colind", colind, torch.int32),
+             ("vals", vals, torch.float64), ("b", b, torch.float64), ("x", x, torch.float64),
+             ("out", out, torch.float64))
+    cur = torch.cuda.current_device() if torch.cuda.is_available() else None
+    for name, t, dt in named:
+        if not getattr(t, "is_cuda", False):
+            raise ValueError(f"{name} must be a CUDA tensor")
+        if t.device.index != cur:
+            raise ValueError(f"{name} is on cuda:{t.device.index}, not the current device")
+        if t.dtype != dt:
+            raise ValueError(f"{name} must be {dt}, got {t.dtype}")
+        if not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+    if 1 <= n <= (1 << 24):  # the library itself rejects other n with a status code
+        if rowptr.numel() != n + 1:
+            raise ValueError(f"rowptr needs n + 1 = {n + 1} entries, has {rowptr.numel()}")
+        if b.numel() != n or x.numel() != n:
+            raise ValueError(f"b and x need n = {n} entries")
+        if colind.numel() != vals.numel():
+            raise ValueError("colind and vals differ in length")
+    if out.numel() < 2:
+        raise ValueError("out needs 2 entries")
+
+
 def true_residual_noalloc(n, rowptr, colind, vals, b, x, out, stream=None) -> int:
     """Allocation-free ||b - A x||_2 and ||b||_2 into the 2-element FP64 CUDA
-    tensor `out` (all arguments CUDA tensors).  For callers that cannot
-    allocate device memory; see include/spai.h.  Returns the status code."""
+    tensor `out` (all arguments contiguous CUDA tensors on the current
+    device: rowptr and colind int32, vals, b, x and out float64).  For
+    callers that cannot allocate device memory; see include/spai.h.  Raises
+    ValueError on a bad argument before anything runs; returns the status
+    code of the C call."""
+    _check_noalloc_args(n, rowptr, colind, vals, b, x, out)
     return load().spai_true_residual_noalloc(int(n), rowptr.data_ptr(), colind.data_ptr(),
                                              vals.data_ptr(), b.data_ptr(), x.data_ptr(),
                                              out.data_ptr(), _stream_ptr(stream))
@@ -217,25 +253,32 @@ class Spai:
             raise SpaiError(rc, where)
         return rc
 
-    def run(self, method, iters, drop=True):
+    def run(self, method, iters, drop=True, keep_diag=False):
+        """iters iterations of method; drop: the per-column hard threshold
+        (keep_diag: it always keeps the column's diagonal entry).  Returns
+        dict(status, done, flags, resnorm[0..iters], coef, nnz[0..iters]) with
+        nnz[i] = nnz(M_i) (-1 where not recorded: past an early stop, or on a
+        batched handle)."""
         m = METHODS[method] if isinstance(method, str) else int(method)
         res = np.full(iters + 1, np.nan)
         coef = np.full(2 * max(iters, 1), np.nan)
-        hist = _Hist(res.ctypes.data, coef.ctypes.data, 0, 0)
-        rc = self.lib.spai_run(self.h, m, int(iters), SPAI_DROP_TOPK_COL if drop else SPAI_DROP_NONE,
-                               C.byref(hist))
+        nnz = np.full(iters + 1, -1, dtype=np.int64)
+        hist = _Hist(res.ctypes.data, coef.ctypes.data, 0, 0, nnz.ctypes.data)
+        rule = (SPAI_DROP_NONE if not drop else
+                SPAI_DROP_TOPK_COL_DIAG if keep_diag else SPAI_DROP_TOPK_COL)
+        rc = self.lib.spai_run(self.h, m, int(iters), rule, C.byref(hist))
         self._check(rc, "spai_run")
         return dict(status=rc, done=hist.iters_done, flags=hist.flags, resnorm=res,
-                    coef=coef.reshape(-1, 2))
+                    coef=coef.reshape(-1, 2), nnz=nnz)
 
-    def mr(self, iters, drop=True):
-        return self.run("mr", iters, drop)
+    def mr(self, iters, drop=True, keep_diag=False):
+        return self.run("mr", iters, drop, keep_diag)
 
-    def lomr(self, iters, drop=True):
-        return self.run("lomr", iters, drop)
+    def lomr(self, iters, drop=True, keep_diag=False):
+        return self.run("lomr", iters, drop, keep_diag)
 
-    def cg(self, iters, drop=True):
-        return self.run("cg", iters, drop)
+    def cg(self, iters, drop=True, keep_diag=False):
+        return self.run("cg", iters, drop, keep_diag)
 
     def reset(self):
         self._check(self.lib.spai_reset(self.h), "spai_reset")
@@ -365,7 +408,7 @@ class Spai:
         m = METHODS[method] if isinstance(method, str) else int(method)
         res = np.full(iters + 1, np.nan)
         coef = np.full(2 * max(iters, 1), np.nan)
-        hist = _Hist(res.ctypes.data, coef.ctypes.data, 0, 0)
+        hist = _Hist(res.ctypes.data, coef.ctypes.data, 0, 0, None)
         rc = self.lib.spai_run_global(self.h, m, int(iters), int(m_dir), int(m_M), C.byref(hist))
         self._check(rc, "spai_run_global")
         return dict(status=rc, done=hist.iters_done, flags=hist.flags, resnorm=res,
@@ -447,8 +490,8 @@ class SpaiBatch(Spai):
         # padded block-diagonal size: each matrix rounded up to 256
         return int(sum((int(x) + 255) // 256 * 256 for x in self.ns))
 
-    def run(self, method, iters, drop=True):
-        r = super().run(method, iters, drop)
+    def run(self, method, iters, drop=True, keep_diag=False):
+        r = super().run(method, iters, drop, keep_diag)
         res = np.full(self.nmat * (iters + 1), np.nan)
         done = np.zeros(self.nmat, dtype=np.int32)
         flags = np.zeros(self.nmat, dtype=np.int32)
@@ -490,10 +533,11 @@ class SpaiBatch(Spai):
 
 
 class FixedPatternMR:
-    """K fixed-pattern MR steps on supp(A) and the gradient of ||I - A M_K||_F^2
-    with respect to A's stored values (see spai_fpmr_* in include/spai.h)."""
+    """K fixed-pattern MR (or, method="lomr", LOMR) steps on supp(A) and the
+    gradient of ||I - A M_K||_F^2 with respect to A's stored values (see
+    spai_fpmr_* in include/spai.h)."""
 
-    def __init__(self, n, rowptr, colind, K, prec="fp64", stream=None):
+    def __init__(self, n, rowptr, colind, K, prec="fp64", stream=None, method="mr"):
         self.lib = load()
         rp, ci = _np(rowptr, np.int32), _np(colind, np.int32)
         h = C.c_void_p()
@@ -503,6 +547,11 @@ class FixedPatternMR:
         if rc != 0:
             raise SpaiError(rc, "spai_fpmr_create")
         self.h, self.n, self.nnz, self.K = h, int(n), len(ci), int(K)
+        if method != "mr":
+            rc = self.lib.spai_fpmr_set_method(self.h, METHODS[method])
+            if rc != 0:
+                self.close()
+                raise SpaiError(rc, "spai_fpmr_set_method")
 
     def _ptr(self, a):
         if hasattr(a, "data_ptr"):

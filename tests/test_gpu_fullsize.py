@@ -1,9 +1,19 @@
 """Parity at the full size of the benchmark workload: the 64^3 variable-
-coefficient operator (n = 262,144, 1,810,432 entries), mixed arithmetic,
-cap 3 nnz(A[:,j]), with the launch shapes the autotuner picks (as
-bench.py does).  Three iterations of each method against the oracle, bit for
-bit: histories, coefficients and all 5.4 M entries of M; then 30 iterations
-of the mixed PCG with the symmetric part of M, x bit for bit."""
+coefficient operator (n = 262,144, 1,810,432 entries), cap 3 nnz(A[:,j]),
+with the launch shapes the autotuner picks (as bench.py does).
+
+- mixed arithmetic, 50 iterations of each method (the bench's count) against
+  the oracle, bit for bit: histories, coefficients, nnz(M_i) and every
+  entry of M; then up to 300 iterations of PCG with the symmetric part of M
+  and FP64 products (the benchmark's arithmetic), iteration count and x bit
+  for bit;
+- FP64 arithmetic, 3 iterations of each method, bit for bit;
+- the rotated anisotropic 9-point operator (eps 1e-3, theta pi/6) at 128^2
+  with cap 8 nnz(A[:,j]) = 72 entries per column (the widest columns the
+  benchmark's cap-8 runs produce), mixed, 10 LOMR and 10 CG iterations, bit
+  for bit.
+
+The oracle runs its OpenMP build here (the same bits as the serial one)."""
 import numpy as np
 import pytest
 
@@ -20,24 +30,61 @@ def workload():
     return I.varcoef_3d_7pt(64, sigma=1.5, ell=8.0, seed=0)
 
 
+def _same_run(r, ro, iters):
+    assert r["done"] == ro["done"] == iters
+    np.testing.assert_array_equal(r["resnorm"], ro["resnorm"])
+    np.testing.assert_array_equal(r["coef"][:iters], ro["coef"][:iters])
+
+
 @pytest.mark.parametrize("method", ["mr", "lomr", "cg"])
-def test_bench_workload_matches_oracle(workload, method):
+def test_bench_workload_50_iterations_match_oracle(workload, method):
     from paper_2511_09753_gb300 import spai
     n, rp, ci, v = workload
     g = spai.Spai(n, rp, ci, v, prec="mixed", cap_factor=3.0)
-    g.set_pcg_prec("mixed")
+    g.set_pcg_prec("fp64")
     g.autotune(method, 2)
-    r = g.run(method, 3)
-    o = O.Oracle(n, rp, ci, v, mixed=True, cap_factor=3.0)
-    ro = o.run(method, 3)
-    assert r["done"] == ro["done"] == 3
-    np.testing.assert_array_equal(r["resnorm"], ro["resnorm"])
-    np.testing.assert_array_equal(r["coef"][:3], ro["coef"][:3])
+    r = g.run(method, 50)
+    o = O.Oracle(n, rp, ci, v, mixed=True, cap_factor=3.0, omp=True)
+    ro = o.run(method, 50)
+    _same_run(r, ro, 50)
+    np.testing.assert_array_equal(r["nnz"], ro["nnz"])
     gm, om = g.get_M(), o.get_M()
     assert all(np.array_equal(a, b) for a, b in zip(gm, om))
+    assert g.residual_norm() == o.residual_norm()
     b = I.rhs_uniform(n, 0)
-    p = g.pcg(b.copy(), rtol=1e-8, maxit=30, precond=spai.PREC_SPAI_SYM)
-    po = O.pcg(n, rp, ci, v, b, rtol=1e-8, maxit=30, precond=3, M=om, mixed=True)
-    assert p["iters"] == po["iters"] == 30
+    p = g.pcg(b.copy(), rtol=1e-8, maxit=300, precond=spai.PREC_SPAI_SYM)
+    po = O.pcg(n, rp, ci, v, b, rtol=1e-8, maxit=300, precond=3, M=om, mixed=False, omp=True)
+    assert p["iters"] == po["iters"]
     assert p["status"] == STATUS[po["status"]]
     assert np.array_equal(p["x"], po["x"])
+    g.close()
+
+
+@pytest.mark.parametrize("method", ["mr", "lomr", "cg"])
+def test_bench_workload_fp64_matches_oracle(workload, method):
+    from paper_2511_09753_gb300 import spai
+    n, rp, ci, v = workload
+    g = spai.Spai(n, rp, ci, v, prec="fp64", cap_factor=3.0)
+    g.autotune(method, 2)
+    r = g.run(method, 3)
+    o = O.Oracle(n, rp, ci, v, mixed=False, cap_factor=3.0, omp=True)
+    ro = o.run(method, 3)
+    _same_run(r, ro, 3)
+    assert all(np.array_equal(a, b) for a, b in zip(g.get_M(), o.get_M()))
+    g.close()
+
+
+@pytest.mark.parametrize("method", ["lomr", "cg"])
+def test_aniso_cap8_wide_columns_match_oracle(method):
+    from paper_2511_09753_gb300 import spai
+    n, rp, ci, v = I.aniso_2d_9pt(128)
+    g = spai.Spai(n, rp, ci, v, prec="mixed", cap_factor=8.0)
+    g.autotune(method, 2)
+    r = g.run(method, 10)
+    o = O.Oracle(n, rp, ci, v, mixed=True, cap_factor=8.0, omp=True)
+    ro = o.run(method, 10)
+    _same_run(r, ro, 10)
+    cp, ri, va = o.get_M()
+    assert np.diff(cp).max() == 72  # columns at the cap of 8 x 9 entries
+    assert all(np.array_equal(a, b) for a, b in zip(g.get_M(), (cp, ri, va)))
+    g.close()

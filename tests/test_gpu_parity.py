@@ -47,6 +47,7 @@ def test_method_parity(case, method, prec):
     assert rg["done"] == ro["done"]
     np.testing.assert_array_equal(rg["resnorm"], ro["resnorm"])
     np.testing.assert_array_equal(rg["coef"][:ro["done"]], ro["coef"][:ro["done"]])
+    np.testing.assert_array_equal(rg["nnz"], ro["nnz"])  # nnz(M_i) history
     assert _same(g.get_M(), o.get_M())
     assert g.residual_norm() == o.residual_norm()
 
@@ -214,3 +215,53 @@ def test_autotune_keeps_results_bitwise(method):
     rb = b.run(method, 6)
     np.testing.assert_array_equal(ra["resnorm"], rb["resnorm"])
     assert _same(a.get_M(), b.get_M())
+
+
+@pytest.mark.parametrize("case", ["varcoef3d_16", "aniso9_45"])
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_cg_without_the_r_slab_matches_oracle(case, prec, monkeypatch):
+    """CG's pass B recomputing R (the path taken when the R slab cannot be
+    allocated, forced here with SPAI_CG_NO_R_SLAB=1) gives the oracle's
+    results bit for bit, over several calls that continue the recurrence."""
+    spai = _spai()
+    monkeypatch.setenv("SPAI_CG_NO_R_SLAB", "1")
+    n, rp, ci, v = CASES[case]()
+    capf = 3.0 if case.startswith("varcoef3d") else 2.0
+    g = spai.Spai(n, rp, ci, v, prec=prec, cap_factor=capf)
+    o = O.Oracle(n, rp, ci, v, mixed=(prec == "mixed"), cap_factor=capf)
+    for iters in (5, 4):
+        rg = g.run("cg", iters)
+        ro = o.run("cg", iters)
+        assert rg["done"] == ro["done"] == iters
+        np.testing.assert_array_equal(rg["resnorm"], ro["resnorm"])
+        np.testing.assert_array_equal(rg["coef"][:iters], ro["coef"][:iters])
+        assert _same(g.get_M(), o.get_M())
+    g.close()
+
+
+@pytest.mark.parametrize("case", ["lap2d_32", "varcoef3d_16", "aniso9_45"])
+@pytest.mark.parametrize("method", ["mr", "lomr", "cg"])
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_keep_diag_parity(case, method, prec):
+    """The drop that always keeps the column's diagonal (Appendix A's rule,
+    SPAI_DROP_TOPK_COL_DIAG) against the oracle's, bit for bit, with a cap
+    small enough that it decides (0.6 nnz(A[:,j])); every column of M keeps
+    its diagonal.  Also the nnz(M_i) history over two continued calls."""
+    spai = _spai()
+    n, rp, ci, v = CASES[case]()
+    capf = 0.6
+    g = spai.Spai(n, rp, ci, v, prec=prec, cap_factor=capf)
+    o = O.Oracle(n, rp, ci, v, mixed=(prec == "mixed"), cap_factor=capf)
+    o.set_keep_diag(True)
+    for iters in (6, 4):
+        rg = g.run(method, iters, keep_diag=True)
+        ro = o.run(method, iters)
+        assert rg["done"] == ro["done"]
+        np.testing.assert_array_equal(rg["resnorm"], ro["resnorm"])
+        np.testing.assert_array_equal(rg["coef"][:ro["done"]], ro["coef"][:ro["done"]])
+        np.testing.assert_array_equal(rg["nnz"], ro["nnz"])
+        gm = g.get_M()
+        assert _same(gm, o.get_M())
+    cp, ri, _ = gm
+    assert all(j in ri[cp[j]:cp[j + 1]] for j in range(n))
+    g.close()

@@ -26,8 +26,14 @@ def _device_problem(n, rp, ci, v, b, x):
             torch.tensor(x, dtype=torch.float64, device=dev))
 
 
+# n = 1,024 and 8,000 fit in one group of 64 CTAs; n = 40,000 takes three
+# groups (the cross-group hand-off) and n = 592,704 thirty-seven (the top
+# level of the tree over more than 32 group sums)
 @pytest.mark.parametrize("make", [lambda: I.laplacian_2d_5pt(32),
-                                  lambda: I.varcoef_3d_7pt(20, seed=2)])
+                                  lambda: I.varcoef_3d_7pt(20, seed=2),
+                                  lambda: I.laplacian_2d_5pt(200),
+                                  lambda: I.varcoef_3d_7pt(84, seed=4)],
+                         ids=["lap32", "varcoef20", "lap200", "varcoef84"])
 def test_noalloc_residual_matches_pcg_relres_twice(make):
     import torch
     from paper_2511_09753_gb300 import spai
