@@ -225,21 +225,33 @@ def run_ours(args):
                     + (s1["pcg_launches"] - s0["pcg_launches"])
                     + (s1["other_launches"] - s0["other_launches"]))
 
-    # end to end through the C ABI with host buffers: create (H2D of A), run,
-    # PCG with host b and x, export M (D2H) -- every step
+    # end to end through the C ABI with host buffers in pinned memory: create
+    # (H2D of A), run, PCG with host b and x, export M (D2H) -- every step
+    def pinned(a):
+        t = torch.empty(a.shape, dtype=getattr(torch, a.dtype.name), pin_memory=True).numpy()
+        t[...] = a
+        return t
+
+    rp_h, ci_h, v_h, b_h = pinned(rp), pinned(ci), pinned(v), pinned(b)
+    x_h = pinned(np.zeros(n))
+    slots = int(np.sum(np.clip(np.floor(CAP * np.diff(rp)), 1, n)))  # M's capacity
+    m_out = (pinned(np.zeros(n + 1, np.int32)), pinned(np.zeros(slots, np.int32)),
+             pinned(np.zeros(slots)))
+
     def e2e_step():
-        h = Spai(n, rp, ci, v, prec="mixed", cap_factor=CAP)
+        h = Spai(n, rp_h, ci_h, v_h, prec="mixed", cap_factor=CAP)
         h.set_pcg_prec(PCG_PREC)
-        h2d = rp.nbytes + ci.nbytes + v.nbytes
+        h2d = rp_h.nbytes + ci_h.nbytes + v_h.nbytes
         d2h = 0
         for m in METHODS:
             h.reset()
             h.run(m, ITERS)
-            p = h.pcg(b, rtol=1e-8, maxit=PCG_MAXIT, precond=PREC_SPAI_SYM)
-            h2d += b.nbytes
-            d2h += p["x"].nbytes
-            cp, ri, va = h.get_M()
-            d2h += cp.nbytes + ri.nbytes + va.nbytes
+            p = h.pcg(b_h, x_h, rtol=1e-8, maxit=PCG_MAXIT, precond=PREC_SPAI_SYM)
+            h2d += b_h.nbytes
+            d2h += x_h.nbytes
+            cp, ri, va = h.get_M(out=m_out)
+            nz = int(cp[n])
+            d2h += cp.nbytes + 4 * nz + 8 * nz
         h.close()
         return h2d, d2h
 

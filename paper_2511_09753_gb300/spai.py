@@ -293,13 +293,20 @@ class Spai:
         self._check(self.lib.spai_get_nnz(self.h, C.byref(out)), "spai_get_nnz")
         return out.value
 
-    def get_M(self):
-        """CSC triple (colptr int32[n+1], rowind int32[nnz], vals float64[nnz]) on the host."""
+    def get_M(self, out=None):
+        """CSC triple (colptr int32[n+1], rowind int32[nnz], vals float64[nnz]) on the host;
+        out: host arrays to fill (for example views of pinned memory), long enough."""
         nnz = C.c_int64()
         self._check(self.lib.spai_get_M(self.h, C.byref(nnz), None, None, None, 0), "spai_get_M")
-        cp = np.zeros(self.n + 1, dtype=np.int32)
-        ri = np.zeros(max(nnz.value, 1), dtype=np.int32)
-        va = np.zeros(max(nnz.value, 1), dtype=np.float64)
+        if out is not None:
+            cp, ri, va = out
+            if (len(cp) < self.n + 1 or len(ri) < nnz.value or len(va) < nnz.value
+                    or cp.dtype != np.int32 or ri.dtype != np.int32 or va.dtype != np.float64):
+                raise ValueError("get_M: out arrays too short or of the wrong dtype")
+        else:
+            cp = np.zeros(self.n + 1, dtype=np.int32)
+            ri = np.zeros(max(nnz.value, 1), dtype=np.int32)
+            va = np.zeros(max(nnz.value, 1), dtype=np.float64)
         self._check(self.lib.spai_get_M(self.h, C.byref(nnz), cp.ctypes.data, ri.ctypes.data,
                                         va.ctypes.data, 0), "spai_get_M")
         return cp, ri[:nnz.value], va[:nnz.value]
