@@ -714,7 +714,7 @@ int create_impl(spai_handle* out, int64_t n, int64_t nnz, const int32_t* rp, con
     if (ok) {
       h->dia = true;
       h->D = Dmax;
-      h->Dp = Dmax;
+      h->Dp = (Dmax + 3) & ~3;
       for (int s2 = 0; s2 < 32; s2++) h->dia_off[s2] = 0;
     } else {
       seg_D.clear();
@@ -745,7 +745,7 @@ int create_impl(spai_handle* out, int64_t n, int64_t nnz, const int32_t* rp, con
       std::sort(offs.begin(), offs.end());
       h->dia = true;
       h->D = (int)offs.size();
-      h->Dp = h->D;
+      h->Dp = (h->D + 3) & ~3;
       for (int s2 = 0; s2 < h->D; s2++) h->dia_off[s2] = (int)offs[s2];
     }
   }
@@ -895,7 +895,7 @@ int create_impl(spai_handle* out, int64_t n, int64_t nnz, const int32_t* rp, con
   ok &= launch_build_ell((int)n, W, h->d_rowptr, h->d_colind, h->d_vals, h->d_ell_col, h->d_ell64,
                          h->prec == SPAI_MIXED ? h->d_ell32 : nullptr, st) == 0;
   if (h->dia)
-    ok &= launch_build_dia((int)n, h->Dp, h->d_rowptr, h->d_colind, h->d_vals,
+    ok &= launch_build_dia((int)n, h->D, h->Dp, h->d_rowptr, h->d_colind, h->d_vals,
                            bd ? nullptr : h->dia_off, bd ? h->d_seg_of_col : nullptr,
                            bd ? h->d_seg_doff : nullptr, bd ? h->d_seg_D : nullptr, h->d_dia64,
                            h->prec == SPAI_MIXED ? h->d_dia32 : nullptr, st) == 0;

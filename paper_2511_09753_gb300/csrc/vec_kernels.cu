@@ -287,13 +287,13 @@ __global__ void k_build_ell(int n, int W, const int* rp, const int* ci, const do
 struct DiaOffs {
   int off[32];
 };
-__global__ void k_build_dia(int n, int Dp, const int* rp, const int* ci, const double* v, DiaOffs doff,
+__global__ void k_build_dia(int n, int D0, int Dp, const int* rp, const int* ci, const double* v, DiaOffs doff,
                             const int* seg_of_col, const int* seg_doff, const int* seg_D,
                             double* d64, float* d32) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const int m = seg_of_col ? seg_of_col[i] : -1;
-  const int D = m >= 0 ? seg_D[m] : Dp;
+  const int D = m >= 0 ? seg_D[m] : D0;
   for (int s = 0; s < Dp; s++) {
     d64[i * Dp + s] = 0.0;
     if (d32) d32[i * Dp + s] = 0.0f;
@@ -314,12 +314,12 @@ cudaError_t launch_build_ell(int n, int W, const int* rp, const int* ci, const d
   return cudaGetLastError();
 }
 
-cudaError_t launch_build_dia(int n, int Dp, const int* rp, const int* ci, const double* v,
+cudaError_t launch_build_dia(int n, int D, int Dp, const int* rp, const int* ci, const double* v,
                              const int* doff, const int* seg_of_col, const int* seg_doff,
                              const int* seg_D, double* d64, float* d32, cudaStream_t st) {
   DiaOffs o;
   for (int s = 0; s < 32; s++) o.off[s] = doff ? doff[s] : 0;
-  k_build_dia<<<(n + 255) / 256, 256, 0, st>>>(n, Dp, rp, ci, v, o, seg_of_col, seg_doff, seg_D,
+  k_build_dia<<<(n + 255) / 256, 256, 0, st>>>(n, D, Dp, rp, ci, v, o, seg_of_col, seg_doff, seg_D,
                                                d64, d32);
   return cudaGetLastError();
 }

@@ -55,7 +55,7 @@ struct PcgArgs {
 cudaError_t launch_seg_reset(DevScalars* sc, int nseg, int fresh, cudaStream_t st);
 cudaError_t launch_build_ell(int n, int W, const int* rp, const int* ci, const double* v, int* ecol,
                              double* e64, float* e32, cudaStream_t st);
-cudaError_t launch_build_dia(int n, int Dp, const int* rp, const int* ci, const double* v,
+cudaError_t launch_build_dia(int n, int D, int Dp, const int* rp, const int* ci, const double* v,
                              const int* doff, const int* seg_of_col, const int* seg_doff,
                              const int* seg_D, double* d64, float* d32, cudaStream_t st);
 cudaError_t launch_init_slab(int prec, int n, const long long* off, const double* diag, int* Mrow,

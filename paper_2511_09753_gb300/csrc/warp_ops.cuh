@@ -166,7 +166,7 @@ __device__ __forceinline__ void term_add(Fix128& S, const Term& t, int eb) {
 // limbs represent it modulo 2^144); a limb's warp sum stays below 2^29 and
 // comes from one redux.sync; the limb sums, shifted into place, add up to the
 // total modulo 2^128, which is exact because the total fits in 128 bits.
-__device__ __forceinline__ void fix_allreduce(Fix128& S) {
+__device__ __forceinline__ void fix_limb_sums(const Fix128& S, unsigned s[6]) {
   const unsigned long long lo = S.lo, hi = (unsigned long long)S.hi;
   const unsigned l0 = (unsigned)lo & 0xffffffu;
   const unsigned l1 = (unsigned)(lo >> 24) & 0xffffffu;
@@ -174,14 +174,28 @@ __device__ __forceinline__ void fix_allreduce(Fix128& S) {
   const unsigned l3 = (unsigned)(hi >> 8) & 0xffffffu;
   const unsigned l4 = (unsigned)(hi >> 32) & 0xffffffu;
   const unsigned l5 = (unsigned)(hi >> 56) | (S.hi < 0 ? 0xffff00u : 0u);
-  const unsigned s0 = __reduce_add_sync(kFull, l0), s1 = __reduce_add_sync(kFull, l1);
-  const unsigned s2 = __reduce_add_sync(kFull, l2), s3 = __reduce_add_sync(kFull, l3);
-  const unsigned s4 = __reduce_add_sync(kFull, l4), s5 = __reduce_add_sync(kFull, l5);
-  unsigned __int128 t = (unsigned __int128)s0 + ((unsigned __int128)s1 << 24) +
-                        ((unsigned __int128)s2 << 48) + ((unsigned __int128)s3 << 72) +
-                        ((unsigned __int128)s4 << 96) + ((unsigned __int128)s5 << 120);
+  s[0] = __reduce_add_sync(kFull, l0);
+  s[1] = __reduce_add_sync(kFull, l1);
+  s[2] = __reduce_add_sync(kFull, l2);
+  s[3] = __reduce_add_sync(kFull, l3);
+  s[4] = __reduce_add_sync(kFull, l4);
+  s[5] = __reduce_add_sync(kFull, l5);
+}
+
+__device__ __forceinline__ Fix128 fix_from_limbs(const unsigned s[6]) {
+  unsigned __int128 t = (unsigned __int128)s[0] + ((unsigned __int128)s[1] << 24) +
+                        ((unsigned __int128)s[2] << 48) + ((unsigned __int128)s[3] << 72) +
+                        ((unsigned __int128)s[4] << 96) + ((unsigned __int128)s[5] << 120);
+  Fix128 S;
   S.lo = (unsigned long long)t;
   S.hi = (long long)(unsigned long long)(t >> 64);
+  return S;
+}
+
+__device__ __forceinline__ void fix_allreduce(Fix128& S) {
+  unsigned s[6];
+  fix_limb_sums(S, s);
+  S = fix_from_limbs(s);
 }
 
 // round S * 2^(eb-1133) to the nearest double (ties to even)
@@ -276,12 +290,25 @@ __device__ void fixsum(double* out, int lane, const F0& f0, int L0, const F1& f1
     if (lane + 32 < L2) term_add(S2, b2, e2);
     for (int i = lane + 64; i < L2; i += 32) term_add(S2, f2(i), e2);
   }
-  fix_allreduce(S0);
-  if (K > 1) fix_allreduce(S1);
-  if (K > 2) fix_allreduce(S2);
-  out[0] = fix_to_double(S0, e0);
-  if (K > 1) out[1] = fix_to_double(S1, e1);
-  if (K > 2) out[2] = fix_to_double(S2, e2);
+  if (K == 1) {
+    fix_allreduce(S0);
+    out[0] = fix_to_double(S0, e0);
+    return;
+  }
+  // lane q < K rounds sum q (the other lanes sum 0); the doubles are then
+  // broadcast, so each rounding runs once per warp instead of K times
+  unsigned a[6], b[6], c[6] = {0u, 0u, 0u, 0u, 0u, 0u};
+  fix_limb_sums(S0, a);
+  fix_limb_sums(S1, b);
+  if (K > 2) fix_limb_sums(S2, c);
+  unsigned s[6];
+#pragma unroll
+  for (int i = 0; i < 6; i++) s[i] = lane == 1 ? b[i] : (K > 2 && lane == 2) ? c[i] : a[i];
+  const int e = lane == 1 ? e1 : (K > 2 && lane == 2) ? e2 : e0;
+  const double d = fix_to_double(fix_from_limbs(s), e);
+  out[0] = __shfl_sync(kFull, d, 0);
+  out[1] = __shfl_sync(kFull, d, 1);
+  if (K > 2) out[2] = __shfl_sync(kFull, d, 2);
 }
 
 // ------------------------------------------------------------- hash table
@@ -297,8 +324,10 @@ struct HashT {
   int H;
 };
 
+// the top log2(H) bits of the product (H a power of two, at least 32 in
+// every layout)
 __device__ __forceinline__ int hslot(int r, int H) {
-  return (int)(((unsigned)r * 0x9E3779B1u) >> (33 - __ffs(H))) & (H - 1);
+  return (int)(((unsigned)r * 0x9E3779B1u) >> (__clz(H) + 1));
 }
 
 // insert r; a new slot gets value 0 and *isnew = true
@@ -446,12 +475,6 @@ __device__ __forceinline__ void hist_clear(uint32_t* hist, int lane) {
   ((uint4*)hist)[lane] = make_uint4(0u, 0u, 0u, 0u);
 }
 
-__device__ __forceinline__ void hist_load(const uint32_t* hist, int lane, unsigned c[8]) {
-  uint4 a = ((const uint4*)hist)[lane];
-  c[0] = a.x & 0xffffu; c[1] = a.x >> 16; c[2] = a.y & 0xffffu; c[3] = a.y >> 16;
-  c[4] = a.z & 0xffffu; c[5] = a.z >> 16; c[6] = a.w & 0xffffu; c[7] = a.w >> 16;
-}
-
 // one count per active lane in bin d: a shared-memory atomic per lane (lanes
 // with the same digit are serialised by the hardware; measured faster than
 // grouping them with __match_any_sync first)
@@ -505,40 +528,46 @@ __device__ int warp_select(const int* sr, const V* sv, int L, int cap, int* dr, 
       bool act = false;
       unsigned dig = 0;
       if (i < L) {
-        K k = sel_key(sv[i], sr[i], keep_row);
+        K k = absbits(sv[i]);
+        if (keep_row >= 0 && sr[i] == keep_row) k = ~(K)0 >> 1;
         act = (k & pmask) == prefix;
         dig = (unsigned)(k >> shift) & dmask;
       }
       hist_add(hist, act, dig);
     }
     __syncwarp();
-    unsigned c[8];
-    hist_load(hist, lane, c);
-    int tot = 0;
-#pragma unroll
-    for (int t = 0; t < 8; t++) tot += (int)c[t];
+    // the lane's 8 bins in two packed sums (their halves cannot carry: the
+    // counts of all bins add up to at most L < 2^16)
+    const uint4 w = ((const uint4*)hist)[lane];
+    const unsigned ws = w.x + w.y + w.z + w.w;
+    const int tot = (int)((ws & 0xffffu) + (ws >> 16));
     int suf = tot;  // inclusive suffix over lanes >= lane
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       int x = __shfl_down_sync(kFull, suf, o);
       if (lane + o < 32) suf += x;
     }
-    int above = suf - tot;
-    int found = -1, f_above = 0, f_cnt = 0;
-#pragma unroll
-    for (int t = 7; t >= 0; t--) {
-      if (found < 0 && above < need && above + (int)c[t] >= need) {
-        found = 8 * lane + t;
-        f_above = above;
-        f_cnt = (int)c[t];
-      }
-      above += (int)c[t];
+    const int above = suf - tot;
+    // the one lane whose bins hold the need-th largest key (1 <= need <= the
+    // entries left), then its bins from the top, one per lane 0..7
+    const int lh = max(__ffs(__ballot_sync(kFull, above < need && suf >= need)) - 1, 0);
+    const int ab = __shfl_sync(kFull, above, lh);
+    int ct = 0;
+    if (lane < 8) {
+      const int bin = 8 * lh + 7 - lane;
+      ct = (int)((hist[bin >> 1] >> ((bin & 1) * 16)) & 0xffffu);
     }
-    unsigned fb = __ballot_sync(kFull, found >= 0);
-    int src = __ffs(fb) - 1;
-    found = __shfl_sync(kFull, found, src);
-    f_above = __shfl_sync(kFull, f_above, src);
-    f_cnt = __shfl_sync(kFull, f_cnt, src);
+    int inc = ct;  // inclusive prefix over lanes 0..7
+#pragma unroll
+    for (int o = 1; o < 8; o <<= 1) {
+      int x = __shfl_up_sync(kFull, inc, o);
+      if (lane >= o) inc += x;
+    }
+    const int t =
+        max(__ffs(__ballot_sync(kFull, lane < 8 && ab + inc >= need && ab + inc - ct < need)) - 1, 0);
+    const int found = 8 * lh + 7 - t;
+    const int f_cnt = __shfl_sync(kFull, ct, t);
+    const int f_above = ab + __shfl_sync(kFull, inc - ct, t);
     need -= f_above;
     prefix |= (K)found << shift;
     pmask |= (K)dmask << shift;
@@ -663,9 +692,26 @@ __device__ int spgemm_dia32(const PassParams& p, const HashT& h, const int* xr, 
   VC a[8];
   int sl[8];
 #pragma unroll
-  for (int s = 0; s < 8; s++) {
-    a[s] = VC(0);
-    if (act && s < D) a[s] = __ldg(dv + (long long)k * p.Dp + s);
+  for (int s = 0; s < 8; s++) a[s] = VC(0);
+  if (act) {  // rows padded to a multiple of 4 slots (zeros): whole vectors
+    const VC* row = dv + (long long)k * p.Dp;
+    if constexpr (sizeof(VC) == 4) {
+      const float4 v0 = __ldg((const float4*)row);
+      a[0] = v0.x; a[1] = v0.y; a[2] = v0.z; a[3] = v0.w;
+      if (D > 4) {
+        const float4 v1 = __ldg((const float4*)row + 1);
+        a[4] = v1.x; a[5] = v1.y; a[6] = v1.z; a[7] = v1.w;
+      }
+    } else {
+#pragma unroll
+      for (int q = 0; q < 4; q++) {
+        if (2 * q < D) {
+          const double2 v = __ldg((const double2*)row + q);
+          a[2 * q] = v.x;
+          a[2 * q + 1] = v.y;
+        }
+      }
+    }
   }
   // first attempts: sl = the key found at the home slot (-1: claimed), or
   // -2 when there is no product
