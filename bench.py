@@ -361,7 +361,7 @@ def accuracy_report(g, g64, last, r64, b_dev, x_dev):
 
 TRAFFIC_SUMMARY = os.path.join(ROOT, "profiles", "colpass_traffic_varcoef3d64.md")
 COLPASS_SOURCES = ("colpass.cuh", "warp_ops.cuh", "common.cuh", "colpass_launch.cuh",
-                   "colpass_f32.cu", "colpass_shape.cuh")
+                   "colpass_f32.cu", "colpass_hot.cu", "colpass_shape.cuh")
 
 
 def colpass_sources_sha16():

@@ -88,6 +88,10 @@ typedef struct {
   int64_t colpass_r_bytes;    /* of colpass_bytes: the R lists CG's pass A stores for the next
                                  pass B (a layout choice of this library, not the method's
                                  own traffic) */
+  int64_t colpass_steady_launches; /* of colpass_launches: mid-run passes that ran the kernels
+                                      compiled for steady-state flags (same results as the
+                                      general kernels; chosen when every column product has
+                                      the short DIA form) */
 } spai_stats;
 
 /* ------------------------------------------------------------- host only */

@@ -19,9 +19,9 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libspai.so")
-SOURCES = ["colpass_f32.cu", "colpass_f64.cu", "colpass_pi_f32.cu", "colpass_pi_f64.cu",
-           "vec_kernels.cu", "bpcg.cu", "fixed_pattern.cu", "fpmr.cu", "dropping.cu", "api.cu",
-           "noalloc.cu"]
+SOURCES = ["colpass_f32.cu", "colpass_f64.cu", "colpass_hot.cu", "colpass_pi_f32.cu",
+           "colpass_pi_f64.cu", "vec_kernels.cu", "bpcg.cu", "fixed_pattern.cu", "fpmr.cu",
+           "dropping.cu", "api.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -163,9 +163,13 @@ struct spai_ctx {
   unsigned char pcg_graph_key[sizeof(spai::PcgArgs)];
   // stats
   long long colpass_launches = 0, pcg_launches = 0, other_launches = 0;
+  long long steady_launches = 0;
   unsigned long long a_bytes_total = 0;
   double colpass_ms = 0.0;
   bool timing = false;
+  // SPAI_GENERAL_KERNELS=1 at a run's start: steady-state passes take the
+  // general kernels too (tests compare the two)
+  bool general_only = false;
   std::vector<cudaEvent_t> ev;
   int ev_used = 0;
 };
@@ -237,6 +241,11 @@ cudaError_t timed_launch(spai_ctx* h, const PassParams& p, const PassCfg& c, boo
                                 : launch_colpass_pi_f64(p, c.grid, 32 * c.NW, c.smem, h->stream);
   else if (res && h->prec == SPAI_MIXED)
     err = launch_colpass_res_f32(p, c.grid, 32 * c.NW, c.smem, h->stream);
+  else if (!res && !h->general_only && steady_pass(p)) {
+    err = h->prec == SPAI_MIXED ? launch_colpass_hot_f32(p, c.grid, 32 * c.NW, c.smem, h->stream)
+                                : launch_colpass_hot_f64(p, c.grid, 32 * c.NW, c.smem, h->stream);
+    h->steady_launches++;
+  }
   else if (res || h->prec == SPAI_FP64)
     err = launch_colpass_f64(p, c.grid, 32 * c.NW, c.smem, h->stream);
   else
@@ -1068,6 +1077,7 @@ int spai_run(spai_handle h, int method, int iters, int drop_rule, spai_history* 
   // recomputes R as before)
   // SPAI_CG_NO_R_SLAB=1 takes the recomputing path on purpose (tests)
   bool keep_r = base == SPAI_CG && iters > 1 && !env_int("SPAI_CG_NO_R_SLAB", 0);
+  h->general_only = env_int("SPAI_GENERAL_KERNELS", 0) != 0;
   if (keep_r && !h->d_Rrow) {
     const size_t cnt = (size_t)h->n * ((size_t)h->capmax * h->W + 1);
     const size_t vb = h->prec == SPAI_FP64 ? 8 : 4;
@@ -2602,6 +2612,7 @@ int spai_get_stats(spai_handle h, spai_stats* out) {
   out->other_launches = h->other_launches;
   out->spgemm_columns = (int64_t)sc.spgemm_cols;
   out->colpass_r_bytes = (int64_t)sc.r_bytes;
+  out->colpass_steady_launches = h->steady_launches;
   return SPAI_OK;
 }
 

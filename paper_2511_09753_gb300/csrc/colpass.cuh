@@ -183,9 +183,12 @@ __device__ void store_col(ColCtx<VS, VC>& c, int* grow, void* gval, int* glen, i
   c.bytes += (unsigned long long)len * (sizeof(int) + sizeof(VS)) + sizeof(int);
 }
 
-template <typename VC>
+// HOT: the kernel of steady-state passes (steady_pass), whose inputs all have
+// the short DIA form, so only that product is compiled in.
+template <bool HOT, typename VC>
 __device__ __forceinline__ int spgemm(const PassParams& p, const HashT& h, int* xr, VC* xv, int L,
                                       int diag, int* sr, VC* sv, int lane, int seg) {
+  if constexpr (HOT) return spgemm_dia32(p, h, xr, xv, L, diag, seg, lane);
   if (p.dia) {
     if (L <= 32 && (seg >= 0 ? p.seg_D[seg] : p.D) <= 8)
       return spgemm_dia32(p, h, xr, xv, L, diag, seg, lane);
@@ -198,7 +201,10 @@ __device__ __forceinline__ int spgemm(const PassParams& p, const HashT& h, int* 
 // Column work of one pass.  part[0..nq) receives the column partials.
 // PI: the Pi-preconditioned forms (Algorithms 5, 7, 8 with Pi = diag(A)^{-1}):
 // directions from Z = Pi R, Pi-weighted coefficient inner products.
-template <typename VS, typename VC, bool PI, int KIND>
+// HOT: a steady-state pass (steady_pass), whose flags are fixed at compile
+// time, so the kernel holds only the code such a pass runs (a smaller kernel
+// misses less in the instruction cache).
+template <typename VS, typename VC, bool PI, int KIND, bool HOT>
 __device__ void column_work(ColCtx<VS, VC>& c, int j, double* part) {
   const PassParams& p = c.p;
   const WarpLayout& L = p.lay;
@@ -206,6 +212,9 @@ __device__ void column_work(ColCtx<VS, VC>& c, int j, double* part) {
   const long long off = p.off[j];
   const int cap = p.cap[j];
   const int keep = p.keep_diag ? j : -1;  // the row every drop of this column keeps
+  const bool upd = HOT || p.do_update, dir = HOT || p.do_dir;
+  const bool slab = !HOT && p.dir_from_slab, store = !HOT && p.dir_store;
+  const bool fresh = !HOT && p.fresh, rin = HOT || p.r_in, rout = HOT || p.r_out;
   int* Mr = c.template at<int>(L.Mr);
   VC* Mv = c.template at<VC>(L.Mv);
   int* Pr = c.template at<int>(L.Pr);
@@ -230,10 +239,10 @@ __device__ void column_work(ColCtx<VS, VC>& c, int j, double* part) {
   int* ovf = &c.overflow;
 
   // the columns this pass reads from the slabs, loaded together
-  const bool needP = (KIND == kMR && p.do_update) || KIND == kLOMR ||
-                     (KIND == kCGA && p.do_update) || KIND == kCGB;
-  const bool needZ = KIND == kLOMR && p.do_update;
-  const bool needM = !(KIND == kCGB && p.r_in);  // M only feeds R there
+  const bool needP = (KIND == kMR && upd) || KIND == kLOMR ||
+                     (KIND == kCGA && upd) || KIND == kCGB;
+  const bool needZ = KIND == kLOMR && upd;
+  const bool needM = !(KIND == kCGB && rin);  // M only feeds R there
   int Lm = needM ? p.Mlen[j] : 0;
   int Lp = needP ? p.Plen[j] : 0;
   const int Lz0 = needZ ? p.Zlen[j] : 0;
@@ -245,7 +254,7 @@ __device__ void column_work(ColCtx<VS, VC>& c, int j, double* part) {
   if constexpr (KIND == kSCORE) {
     // Appendix A, Eq. 430: dropping m_kj alone changes ||R||_F^2 by
     // m^2 ||A e_k||^2 + 2 m (A R)_kj; (A R)_kj from row k of A and the R table
-    int cnt = spgemm(p, ha, Mr, Mv, Lm, j, Tr, Tv, lane, c.seg);
+    int cnt = spgemm<HOT>(p, ha, Mr, Mv, Lm, j, Tr, Tv, lane, c.seg);
     table_to_list(ha, cnt, j, Rr, Rv, lane);  // the table now holds R
     c.spg++;
     const VC* av = (const VC*)p.ell_val;
@@ -273,7 +282,7 @@ __device__ void column_work(ColCtx<VS, VC>& c, int j, double* part) {
   }
 
   if constexpr (KIND == kRES) {
-    int cnt = spgemm(p, ha, Mr, Mv, Lm, j, Tr, Tv, lane, c.seg);
+    int cnt = spgemm<HOT>(p, ha, Mr, Mv, Lm, j, Tr, Tv, lane, c.seg);
     int LR = table_to_list(ha, cnt, j, Rr, Rv, lane);
     hash_clear(ha, cnt, lane);
     c.spg++;
@@ -282,7 +291,7 @@ __device__ void column_work(ColCtx<VS, VC>& c, int j, double* part) {
   }
 
   if constexpr (KIND == kMR) {
-    if (p.do_update) {
+    if (upd) {
       CombAxpy<VC> f{c.sc->alpha};
       int Lt = warp_union(un, Mr, Mv, Lm, Pr, Pv, Lp, Tr, Tv, f, lane);
       c.mark(kPhUnion);
@@ -292,17 +301,17 @@ __device__ void column_work(ColCtx<VS, VC>& c, int j, double* part) {
       c.mark(kPhStore);
     }
     c.nnzM += Lm;  // M_iter
-    int cnt = spgemm(p, ha, Mr, Mv, Lm, j, Tr, Tv, lane, c.seg);
+    int cnt = spgemm<HOT>(p, ha, Mr, Mv, Lm, j, Tr, Tv, lane, c.seg);
     c.mark(kPhSpgemm);
     int LR = table_to_list(ha, cnt, j, Rr, Rv, lane);
     hash_clear(ha, cnt, lane);
     c.mark(kPhList);
     c.spg++;
-    if (!p.do_dir && !p.dir_store) {
+    if (!dir && !store) {
       fixsum<1>(part, lane, TermSq<VC>{Rv}, LR);
       return;
     }
-    if (p.dir_from_slab) {  // a direction chosen outside the pass (global dropping)
+    if (slab) {  // a direction chosen outside the pass (global dropping)
       Lp = load_col(c, p.Prow, p.Pval, off, p.Plen[j], Pr, Pv);
     } else {
       if (PI) {  // P = D(Pi R) (Algorithm 5)
@@ -317,11 +326,11 @@ __device__ void column_work(ColCtx<VS, VC>& c, int j, double* part) {
       store_col(c, p.Prow, p.Pval, p.Plen, j, off, Lp, Pr, Pv);
       c.mark(kPhStore);
     }
-    if (!p.do_dir) {  // dir_store: the direction candidate is all this pass forms
+    if (!dir) {  // dir_store: the direction candidate is all this pass forms
       fixsum<1>(part, lane, TermSq<VC>{Rv}, LR);
       return;
     }
-    int cq = spgemm(p, ha, Pr, Pv, Lp, -1, Tr, Tv, lane, c.seg);  // table holds Q = A P
+    int cq = spgemm<HOT>(p, ha, Pr, Pv, Lp, -1, Tr, Tv, lane, c.seg);  // table holds Q = A P
     c.mark(kPhSpgemm);
     c.spg++;
     if (PI)  // (R,R), (R,Pi Q), (Q,Pi Q)
@@ -346,7 +355,7 @@ __device__ void column_work(ColCtx<VS, VC>& c, int j, double* part) {
     hb.val = c.template at<VC>(L.gv);
     hb.occ = c.template at<uint16_t>(L.go);
     hb.H = L.H;
-    if (p.do_update) {
+    if (upd) {
       CombLin<VC> fl{c.sc->delta, c.sc->gamma};
       int Ls = warp_union(un, Zr, Zv, Lz0, Pr, Pv, Lp, Sr, Sv, fl, lane);
       c.mark(kPhUnion);
@@ -363,18 +372,18 @@ __device__ void column_work(ColCtx<VS, VC>& c, int j, double* part) {
       c.mark(kPhStore);
     }
     c.nnzM += Lm;  // M_iter
-    int cr = spgemm(p, ha, Mr, Mv, Lm, j, Tr, Tv, lane, c.seg);
+    int cr = spgemm<HOT>(p, ha, Mr, Mv, Lm, j, Tr, Tv, lane, c.seg);
     c.mark(kPhSpgemm);
     int LR = table_to_list(ha, cr, j, Rr, Rv, lane);
     hash_clear(ha, cr, lane);
     c.mark(kPhList);
     c.spg++;
-    if (!p.do_dir && !p.dir_store) {
+    if (!dir && !store) {
       fixsum<1>(part, lane, TermSq<VC>{Rv}, LR);
       return;
     }
     int Lz;
-    if (p.dir_from_slab) {  // a Z chosen outside the pass (global dropping)
+    if (slab) {  // a Z chosen outside the pass (global dropping)
       Lz = load_col(c, p.Zrow, p.Zval, off, p.Zlen[j], Zr, Zv);
     } else {
       if (PI) {  // Z = D(Pi R) (Algorithm 8)
@@ -389,11 +398,11 @@ __device__ void column_work(ColCtx<VS, VC>& c, int j, double* part) {
       store_col(c, p.Zrow, p.Zval, p.Zlen, j, off, Lz, Zr, Zv);
       c.mark(kPhStore);
     }
-    if (!p.do_dir) {  // dir_store: the Z candidate is all this pass forms
+    if (!dir) {  // dir_store: the Z candidate is all this pass forms
       fixsum<1>(part, lane, TermSq<VC>{Rv}, LR);
       return;
     }
-    int cu = spgemm(p, ha, Zr, Zv, Lz, -1, Tr, Tv, lane, c.seg);   // table A: U = A Z
+    int cu = spgemm<HOT>(p, ha, Zr, Zv, Lz, -1, Tr, Tv, lane, c.seg);   // table A: U = A Z
     c.mark(kPhSpgemm);
     double t3[3];
     if (PI)  // (R,R), (U,Pi U), (U,Pi R)
@@ -409,7 +418,7 @@ __device__ void column_work(ColCtx<VS, VC>& c, int j, double* part) {
     c.mark(kPhFixsum);
     hash_clear_all(hb, lane);  // its bytes also held the union table and the select scratch
     c.mark(kPhList);
-    int cv = spgemm(p, hb, Pr, Pv, Lp, -1, Tr, Tv, lane, c.seg);   // table B: V = A P
+    int cv = spgemm<HOT>(p, hb, Pr, Pv, Lp, -1, Tr, Tv, lane, c.seg);   // table B: V = A P
     c.mark(kPhSpgemm);
     c.spg += 2;
     if (PI)  // (V,Pi V), (U,Pi V), (V,Pi R)
@@ -430,7 +439,7 @@ __device__ void column_work(ColCtx<VS, VC>& c, int j, double* part) {
   }
 
   if constexpr (KIND == kCGA) {
-    if (p.do_update) {  // without it: R and beta of an M changed outside (global dropping)
+    if (upd) {  // without it: R and beta of an M changed outside (global dropping)
       CombAxpy<VC> f{c.sc->alpha};
       int Lt = warp_union(un, Mr, Mv, Lm, Pr, Pv, Lp, Tr, Tv, f, lane);
       c.mark(kPhUnion);
@@ -440,17 +449,17 @@ __device__ void column_work(ColCtx<VS, VC>& c, int j, double* part) {
       c.mark(kPhStore);
       c.nnzM += Lm;  // M_{iter+1}
     }
-    if (!p.do_dir) {  // the update only: M is dropped outside before R is formed
+    if (!dir) {  // the update only: M is dropped outside before R is formed
       part[0] = 0.0;
       return;
     }
-    int cr = spgemm(p, ha, Mr, Mv, Lm, j, Tr, Tv, lane, c.seg);
+    int cr = spgemm<HOT>(p, ha, Mr, Mv, Lm, j, Tr, Tv, lane, c.seg);
     c.mark(kPhSpgemm);
     int LR = table_to_list(ha, cr, j, Rr, Rv, lane);
     hash_clear(ha, cr, lane);
     c.mark(kPhList);
     c.spg++;
-    if (p.r_out) store_r(c, j, LR, Rr, Rv);
+    if (rout) store_r(c, j, LR, Rr, Rv);
     c.mark(kPhStore);
     if (PI)  // (R,R), (R,Pi R)
       fixsum<2>(part, lane, TermSq<VC>{Rv}, LR, TermWSq<VC>{Rr, Rv, p.pi}, LR);
@@ -461,18 +470,18 @@ __device__ void column_work(ColCtx<VS, VC>& c, int j, double* part) {
   }
 
   if constexpr (KIND == kCGB) {
-    if (p.fresh) c.nnzM += Lm;  // M_0 of the call (loaded: no R slab on the first pass)
+    if (fresh) c.nnzM += Lm;  // M_0 of the call (loaded: no R slab on the first pass)
     int LR;
-    if (p.r_in) {  // R as the previous pass A computed it
+    if (rin) {  // R as the previous pass A computed it
       LR = load_r(c, j, Rr, Rv);
       c.mark(kPhLoad);
     } else {
-      int cr = spgemm(p, ha, Mr, Mv, Lm, j, Tr, Tv, lane, c.seg);
+      int cr = spgemm<HOT>(p, ha, Mr, Mv, Lm, j, Tr, Tv, lane, c.seg);
       LR = table_to_list(ha, cr, j, Rr, Rv, lane);
       hash_clear(ha, cr, lane);
       c.spg++;
     }
-    if (!p.dir_from_slab) {  // else P, loaded above, was chosen outside (global dropping)
+    if (!slab) {  // else P, loaded above, was chosen outside (global dropping)
       CombAxpy<VC> f{c.sc->beta};
       int Lt;
       if (PI) {  // P = D(Pi R + beta P) (Algorithm 7)
@@ -489,16 +498,16 @@ __device__ void column_work(ColCtx<VS, VC>& c, int j, double* part) {
       store_col(c, p.Prow, p.Pval, p.Plen, j, off, Lp, Pr, Pv);
       c.mark(kPhStore);
     }
-    if (!p.do_dir) {  // the direction candidate only (global dropping follows)
+    if (!dir) {  // the direction candidate only (global dropping follows)
       fixsum<1>(part, lane, TermSq<VC>{Rv}, LR);
       return;
     }
-    int cq = spgemm(p, ha, Pr, Pv, Lp, -1, Tr, Tv, lane, c.seg);  // table holds Q = A P
+    int cq = spgemm<HOT>(p, ha, Pr, Pv, Lp, -1, Tr, Tv, lane, c.seg);  // table holds Q = A P
     c.mark(kPhSpgemm);
     c.spg++;
     // (R,R) and (R,Pi R) are needed only by the first pass B of a call: the
     // pass A before each later one has stored them (alpha's numerator)
-    if (p.fresh) {
+    if (fresh) {
       if (PI)  // (R,R), (P,Q), (R,Pi R)
         fixsum<3>(part, lane, TermSq<VC>{Rv}, LR, TermProdFind<VC>{Pr, Pv, ha}, Lp,
                   TermWSq<VC>{Rr, Rv, p.pi}, LR);
@@ -633,7 +642,7 @@ __device__ inline void coefficients(const PassParams& p, DevScalars* sc, double*
 
 // One instantiation per pass kind keeps each kernel's code small: with all
 // kinds behind a runtime switch the instruction cache missed often.
-template <typename VS, typename VC, bool PI, int KIND>
+template <typename VS, typename VC, bool PI, int KIND, bool HOT = false>
 __global__ void __launch_bounds__(256, sizeof(VC) == 4 ? 4 : 3) colpass_kernel(const PassParams p) {
   extern __shared__ __align__(16) char smem[];
   const int seg = p.nseg ? p.seg_of_col[(long long)blockIdx.x * p.B] : -1;
@@ -670,7 +679,7 @@ __global__ void __launch_bounds__(256, sizeof(VC) == 4 ? 4 : 3) colpass_kernel(c
     double pr[6] = {0, 0, 0, 0, 0, 0};
     c.ph_start();
     if (j < p.n) {
-      column_work<VS, VC, PI, KIND>(c, (int)j, pr);
+      column_work<VS, VC, PI, KIND, HOT>(c, (int)j, pr);
 #ifdef SPAI_PHASE_CLOCKS
       c.ph[kPhCols]++;
 #endif

@@ -113,6 +113,20 @@ struct PassParams {
   int red_off;           // byte offset of CTA reduction scratch
 };
 
+// A steady-state pass: an update-and-direction pass of MR, LOMR or CG in the
+// middle of a run (CG's passes exchanging R through its slab), in the plain
+// forms, on an operator whose column products all take the short DIA form
+// (columns of at most 32 entries, at most 8 diagonal slots).  Such passes
+// run a kernel compiled for exactly these flags.
+__host__ __device__ inline bool steady_pass(const PassParams& p) {
+  if (p.kind != kMR && p.kind != kLOMR && p.kind != kCGA && p.kind != kCGB) return false;
+  if (p.pi || !p.dia || p.capmax > 32 || p.D > 8) return false;
+  if (!p.do_dir || p.dir_from_slab || p.dir_store) return false;
+  if (p.kind == kCGB) return !p.fresh && p.r_in;
+  if (p.kind == kCGA) return p.do_update && p.r_out;
+  return p.do_update != 0;
+}
+
 constexpr int kGroup = 64;  // blocks per group in the last-arriver reduction tree
 
 // partials per column: MR (R,R) (R,Q) (Q,Q); LOMR (R,R) (U,U) (V,V) (U,V)

@@ -111,5 +111,10 @@ cudaError_t launch_colpass_pi_f32(const PassParams& p, int grid, int block, size
                                   cudaStream_t st);
 cudaError_t launch_colpass_pi_f64(const PassParams& p, int grid, int block, size_t smem,
                                   cudaStream_t st);
+// steady-state passes only (steady_pass(p))
+cudaError_t launch_colpass_hot_f32(const PassParams& p, int grid, int block, size_t smem,
+                                   cudaStream_t st);
+cudaError_t launch_colpass_hot_f64(const PassParams& p, int grid, int block, size_t smem,
+                                   cudaStream_t st);
 
 }  // namespace spai

@@ -56,7 +56,7 @@ class _Stats(C.Structure):
     _fields_ = [("colpass_launches", C.c_int64), ("colpass_bytes", C.c_int64),
                 ("colpass_ms", C.c_double), ("pcg_launches", C.c_int64),
                 ("other_launches", C.c_int64), ("spgemm_columns", C.c_int64),
-                ("colpass_r_bytes", C.c_int64)]
+                ("colpass_r_bytes", C.c_int64), ("colpass_steady_launches", C.c_int64)]
 
 
 _lib = None

@@ -239,6 +239,34 @@ def test_cg_without_the_r_slab_matches_oracle(case, prec, monkeypatch):
     g.close()
 
 
+@pytest.mark.parametrize("method", ["mr", "lomr", "cg"])
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_steady_and_general_kernels_match_oracle(method, prec, monkeypatch):
+    """Mid-run passes on an operator whose column products all take the short
+    DIA form (7-point stencil, cap 21) run the kernels compiled for
+    steady-state flags; with SPAI_GENERAL_KERNELS=1 the same passes run the
+    general kernels.  Both give the oracle's results bit for bit, and the
+    launch counts show which kernels ran (6 iterations: MR and LOMR have 5
+    mid-run passes, CG 5 passes B reading R and 5 passes A storing it)."""
+    spai = _spai()
+    n, rp, ci, v = CASES["varcoef3d_16"]()
+    o = O.Oracle(n, rp, ci, v, mixed=(prec == "mixed"), cap_factor=3.0)
+    ro = o.run(method, 6)
+    Mo = o.get_M()
+    for general in (False, True):
+        if general:
+            monkeypatch.setenv("SPAI_GENERAL_KERNELS", "1")
+        g = spai.Spai(n, rp, ci, v, prec=prec, cap_factor=3.0)
+        rg = g.run(method, 6)
+        assert rg["done"] == ro["done"] == 6
+        np.testing.assert_array_equal(rg["resnorm"], ro["resnorm"])
+        np.testing.assert_array_equal(rg["coef"][:6], ro["coef"][:6])
+        assert _same(g.get_M(), Mo)
+        steady = g.stats()["colpass_steady_launches"]
+        assert steady == (0 if general else (10 if method == "cg" else 5))
+        g.close()
+
+
 @pytest.mark.parametrize("case", ["lap2d_32", "varcoef3d_16", "aniso9_45"])
 @pytest.mark.parametrize("method", ["mr", "lomr", "cg"])
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
