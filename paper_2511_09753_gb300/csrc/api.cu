@@ -160,6 +160,10 @@ struct spai_ctx {
   cudaGraphExec_t bp_graph = nullptr;
   unsigned char bp_graph_key[sizeof(spai::BpcgArgs)];
   cudaGraphExec_t pcg_graph = nullptr;  // a chunk of vector-PCG iterations
+  // S's long rows run beside the others on a second stream (made on first use)
+  cudaStream_t pcg_st2 = nullptr;
+  cudaEvent_t pcg_fork = nullptr, pcg_join = nullptr;
+  bool pcg_graph_forked = false;  // pcg_graph was captured with the second stream
   unsigned char pcg_graph_key[sizeof(spai::PcgArgs)];
   // stats
   long long colpass_launches = 0, pcg_launches = 0, other_launches = 0;
@@ -434,6 +438,11 @@ void free_all(spai_ctx* h) {
   h->bp_graph = nullptr;
   if (h->pcg_graph) cudaGraphExecDestroy(h->pcg_graph);
   h->pcg_graph = nullptr;
+  if (h->pcg_fork) cudaEventDestroy(h->pcg_fork);
+  if (h->pcg_join) cudaEventDestroy(h->pcg_join);
+  if (h->pcg_st2) cudaStreamDestroy(h->pcg_st2);
+  h->pcg_fork = h->pcg_join = nullptr;
+  h->pcg_st2 = nullptr;
   for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
   h->ev.clear();
 }
@@ -1645,20 +1654,40 @@ int pcg_solve(spai_handle h, const double* b, double* x, int nrhs, double rtol, 
   a.ws.cnt2 = h->d_vcnt2;
   a.ws.nb = (n + 255) / 256;
   a.ws.ngroups = (a.ws.nb + kGroup - 1) / kGroup;
-  CK(launch_pcg_init(a, st));
-  h->pcg_launches += a.nlong ? 4 : 3;
+  PcgFork fk{nullptr, nullptr, nullptr};
+  if (a.nlong) {
+    if (!h->pcg_st2) {
+      bool ok = cudaStreamCreateWithFlags(&h->pcg_st2, cudaStreamNonBlocking) == cudaSuccess;
+      ok = ok && cudaEventCreateWithFlags(&h->pcg_fork, cudaEventDisableTiming) == cudaSuccess;
+      ok = ok && cudaEventCreateWithFlags(&h->pcg_join, cudaEventDisableTiming) == cudaSuccess;
+      if (!ok) {  // one stream then
+        (void)cudaGetLastError();
+        if (h->pcg_fork) cudaEventDestroy(h->pcg_fork);
+        if (h->pcg_st2) cudaStreamDestroy(h->pcg_st2);
+        h->pcg_fork = h->pcg_join = nullptr;
+        h->pcg_st2 = nullptr;
+      }
+    }
+    if (h->pcg_st2) fk = PcgFork{h->pcg_st2, h->pcg_fork, h->pcg_join};
+  }
+  // kernels of one preconditioner application: 1, or 2 (long rows, then the
+  // others), or 3 (long rows beside the others, then the inner product)
+  const int prec_launches = !a.nlong ? 1 : fk.st2 ? 3 : 2;
+  CK(launch_pcg_init(a, fk, st));
+  h->pcg_launches += 2 + prec_launches;
   // the iterations run as replays of a captured graph of `chunk` iterations
   // (their kernels read every scalar from device memory, so the launches do
   // not change while the arguments do not); the host polls the done flag
   // between replays
   const int chunk = 16;
-  if (!h->pcg_graph || memcmp(h->pcg_graph_key, &a, sizeof(a)) != 0) {
+  if (!h->pcg_graph || memcmp(h->pcg_graph_key, &a, sizeof(a)) != 0 ||
+      h->pcg_graph_forked != (fk.st2 != nullptr)) {
     if (h->pcg_graph) cudaGraphExecDestroy(h->pcg_graph);
     h->pcg_graph = nullptr;
     cudaGraph_t g = nullptr;
     if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
       cudaError_t e = cudaSuccess;
-      for (int c = 0; c < chunk && e == cudaSuccess; c++) e = launch_pcg_iter(a, st);
+      for (int c = 0; c < chunk && e == cudaSuccess; c++) e = launch_pcg_iter(a, fk, st);
       cudaError_t e2 = cudaStreamEndCapture(st, &g);
       if (e == cudaSuccess && e2 == cudaSuccess && g)
         if (cudaGraphInstantiate(&h->pcg_graph, g, 0) != cudaSuccess) h->pcg_graph = nullptr;
@@ -1666,14 +1695,15 @@ int pcg_solve(spai_handle h, const double* b, double* x, int nrhs, double rtol, 
     }
     (void)cudaGetLastError();
     if (h->pcg_graph) memcpy(h->pcg_graph_key, &a, sizeof(a));
+    h->pcg_graph_forked = fk.st2 != nullptr;
   }
   for (;;) {
     if (h->pcg_graph) {
       CK(cudaGraphLaunch(h->pcg_graph, st));
     } else {
-      for (int c = 0; c < chunk; c++) CK(launch_pcg_iter(a, st));
+      for (int c = 0; c < chunk; c++) CK(launch_pcg_iter(a, fk, st));
     }
-    h->pcg_launches += (a.nlong ? 5 : 4) * chunk;
+    h->pcg_launches += (3 + prec_launches) * chunk;
     CK(cudaMemcpyAsync(&ps, h->d_ps, sizeof(ps), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     if (ps.done) break;

@@ -22,16 +22,31 @@ constexpr int kLongRow = 64;
 // Each thread contributes one term (its element); the CTA (256 threads)
 // reduces by a contiguous tree, then the last-arriving CTA of each group of
 // kGroup CTAs, then the last group, calls finish(total) in its thread 0.
+//
+// The CTA's tree runs in one warp: the terms are staged in shared memory and
+// lane l adds its 8 consecutive terms pairwise before the warp's
+// tree (GB300's FP64 pipe takes about 20 SM cycles per warp instruction,
+// active lanes or not, so 13 such instructions replace 45).  The trailing
+// + 0 stands for the zero-padded top of a tree over 32 warps of 32 (it
+// turns -0 into +0 and changes nothing else).
 template <typename F>
 __device__ void reduce_finish(double term, const RedWS& w, F finish) {
   __shared__ double red[1024];
   __shared__ int s_last;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int nw = blockDim.x >> 5;
-  double s = warp_tree32(term);
-  if (lane == 0) red[warp] = s;
+  red[threadIdx.x] = term;  // blockDim.x == 256 for every caller
   __syncthreads();
-  if (warp == 0) s = warp_tree32(lane < nw ? red[lane] : 0.0);
+  double s = 0.0;
+  if (warp == 0) {
+    double t[8];
+#pragma unroll
+    for (int q = 0; q < 8; q++) t[q] = red[lane * 8 + q];
+#pragma unroll
+    for (int len = 8; len > 1; len >>= 1)
+#pragma unroll
+      for (int q = 0; 2 * q + 1 < len; q++) t[q] = __dadd_rn(t[2 * q], t[2 * q + 1]);
+    s = __dadd_rn(warp_tree32(t[0]), 0.0);
+  }
   const int g = blockIdx.x / kGroup;
   if (threadIdx.x == 0) {
     w.bsum[blockIdx.x] = s;
@@ -650,13 +665,35 @@ __global__ void k_pcg_init(PcgArgs a) {
   });
 }
 
-// z = Prec(r), terms r_i z_i -> rho (first = 1: initial rho, p = z follows)
-__global__ void k_pcg_prec(PcgArgs a, int first) {
+// rho = r.z of the iteration (breakdown if 0 or not finite) and beta
+__device__ __forceinline__ void rho_finish(PcgScalars* s, int first, double rho1) {
+  if (rho1 == 0.0 || !finite_d(rho1)) {
+    s->done = 1;
+    s->status = 2;
+    return;
+  }
+  if (first) {
+    s->rho = rho1;
+    s->beta = 0.0;
+  } else {
+    s->beta = __ddiv_rn(rho1, s->rho);
+    s->rho = rho1;
+  }
+}
+
+// z = Prec(r), terms r_i z_i -> rho (first = 1: initial rho, p = z follows).
+// zonly: z of the rows up to kLongRow entries only, no inner product (the
+// long rows run beside it in k_pcg_prec_long, k_pcg_rz follows both)
+__global__ void k_pcg_prec(PcgArgs a, int first, int zonly) {
   if (a.s->done) return;
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   double term = 0.0;
   if (a.sell.sptr) {  // S in sliced ELL (FP64 products)
     if (i < a.n) {
+      if (zonly) {
+        if (a.mrp[i + 1] - a.mrp[i] <= kLongRow) a.z[i] = sell_row_chain(a.sell, a.mrp, a.r, i);
+        return;
+      }
       const double z = precond_sell(a, i);
       a.z[i] = z;
       term = __dmul_rn(a.r[i], z);
@@ -666,21 +703,18 @@ __global__ void k_pcg_prec(PcgArgs a, int first) {
     a.z[i] = z;
     term = __dmul_rn(a.r[i], z);
   }
+  if (zonly) return;
   PcgScalars* s = a.s;
-  reduce_finish(term, a.ws, [s, first](double rho1) {
-    if (rho1 == 0.0 || !finite_d(rho1)) {
-      s->done = 1;
-      s->status = 2;
-      return;
-    }
-    if (first) {
-      s->rho = rho1;
-      s->beta = 0.0;
-    } else {
-      s->beta = __ddiv_rn(rho1, s->rho);
-      s->rho = rho1;
-    }
-  });
+  reduce_finish(term, a.ws, [s, first](double rho1) { rho_finish(s, first, rho1); });
+}
+
+// terms r_i z_i -> rho, after k_pcg_prec (zonly) and k_pcg_prec_long
+__global__ void k_pcg_rz(PcgArgs a, int first) {
+  if (a.s->done) return;
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const double term = i < a.n ? __dmul_rn(a.r[i], a.z[i]) : 0.0;
+  PcgScalars* s = a.s;
+  reduce_finish(term, a.ws, [s, first](double rho1) { rho_finish(s, first, rho1); });
 }
 
 // p = z (first) or p = fma(beta, p, z)
@@ -837,21 +871,48 @@ cudaError_t launch_lz_step(const LzArgs& a, int j, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_pcg_init(const PcgArgs& a, cudaStream_t st) {
+// z = Prec(r) and rho: with rows longer than kLongRow (and a second stream),
+// the long rows run on st2 beside the others on st, and k_pcg_rz joins them
+static cudaError_t launch_pcg_prec(const PcgArgs& a, int first, const PcgFork& f,
+                                   cudaStream_t st) {
+  int g = (a.n + 255) / 256;
+  if (!a.nlong) {
+    k_pcg_prec<<<g, 256, 0, st>>>(a, first, 0);
+    return cudaGetLastError();
+  }
+  if (!f.st2) {
+    k_pcg_prec_long<<<(a.nlong + 7) / 8, 256, 0, st>>>(a);
+    k_pcg_prec<<<g, 256, 0, st>>>(a, first, 0);
+    return cudaGetLastError();
+  }
+  cudaError_t e = cudaEventRecord(f.fork, st);
+  if (!e) e = cudaStreamWaitEvent(f.st2, f.fork, 0);
+  if (e) return e;
+  k_pcg_prec_long<<<(a.nlong + 7) / 8, 256, 0, f.st2>>>(a);
+  e = cudaEventRecord(f.join, f.st2);
+  if (e) return e;
+  k_pcg_prec<<<g, 256, 0, st>>>(a, first, 1);
+  e = cudaStreamWaitEvent(st, f.join, 0);
+  if (e) return e;
+  k_pcg_rz<<<g, 256, 0, st>>>(a, first);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pcg_init(const PcgArgs& a, const PcgFork& f, cudaStream_t st) {
   int g = (a.n + 255) / 256;
   k_pcg_init<<<g, 256, 0, st>>>(a);
-  if (a.nlong) k_pcg_prec_long<<<(a.nlong + 7) / 8, 256, 0, st>>>(a);
-  k_pcg_prec<<<g, 256, 0, st>>>(a, 1);
+  cudaError_t e = launch_pcg_prec(a, 1, f, st);
+  if (e) return e;
   k_pcg_dir<<<g, 256, 0, st>>>(a, 1);
   return cudaGetLastError();
 }
 
-cudaError_t launch_pcg_iter(const PcgArgs& a, cudaStream_t st) {
+cudaError_t launch_pcg_iter(const PcgArgs& a, const PcgFork& f, cudaStream_t st) {
   int g = (a.n + 255) / 256;
   k_pcg_spmv<<<g, 256, 0, st>>>(a);
   k_pcg_update<<<g, 256, 0, st>>>(a);
-  if (a.nlong) k_pcg_prec_long<<<(a.nlong + 7) / 8, 256, 0, st>>>(a);
-  k_pcg_prec<<<g, 256, 0, st>>>(a, 0);
+  cudaError_t e = launch_pcg_prec(a, 0, f, st);
+  if (e) return e;
   k_pcg_dir<<<g, 256, 0, st>>>(a, 0);
   return cudaGetLastError();
 }

@@ -99,8 +99,14 @@ struct LzArgs {
 };
 cudaError_t launch_lz_start(const LzArgs& a, cudaStream_t st);
 cudaError_t launch_lz_step(const LzArgs& a, int j, cudaStream_t st);
-cudaError_t launch_pcg_init(const PcgArgs& a, cudaStream_t st);
-cudaError_t launch_pcg_iter(const PcgArgs& a, cudaStream_t st);
+// a second stream and two events for running S's long rows beside the
+// others (st2 null: one stream)
+struct PcgFork {
+  cudaStream_t st2;
+  cudaEvent_t fork, join;
+};
+cudaError_t launch_pcg_init(const PcgArgs& a, const PcgFork& f, cudaStream_t st);
+cudaError_t launch_pcg_iter(const PcgArgs& a, const PcgFork& f, cudaStream_t st);
 cudaError_t launch_true_res(const PcgArgs& a, cudaStream_t st);
 
 cudaError_t launch_colpass_f32(const PassParams& p, int grid, int block, size_t smem, cudaStream_t st);
