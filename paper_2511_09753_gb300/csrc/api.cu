@@ -1670,9 +1670,10 @@ int pcg_solve(spai_handle h, const double* b, double* x, int nrhs, double rtol, 
     }
     if (h->pcg_st2) fk = PcgFork{h->pcg_st2, h->pcg_fork, h->pcg_join};
   }
-  // kernels of one preconditioner application: 1, or 2 (long rows, then the
-  // others), or 3 (long rows beside the others, then the inner product)
-  const int prec_launches = !a.nlong ? 1 : fk.st2 ? 3 : 2;
+  // kernels of one preconditioner application with its inner product: 2, or
+  // 3 (long rows, the others, the total), or 4 (long rows beside the others,
+  // then the inner product and its total)
+  const int prec_launches = !a.nlong ? 2 : fk.st2 ? 4 : 3;
   CK(launch_pcg_init(a, fk, st));
   h->pcg_launches += 2 + prec_launches;
   // the iterations run as replays of a captured graph of `chunk` iterations
@@ -1703,7 +1704,7 @@ int pcg_solve(spai_handle h, const double* b, double* x, int nrhs, double rtol, 
     } else {
       for (int c = 0; c < chunk; c++) CK(launch_pcg_iter(a, fk, st));
     }
-    h->pcg_launches += (3 + prec_launches) * chunk;
+    h->pcg_launches += (5 + prec_launches) * chunk;
     CK(cudaMemcpyAsync(&ps, h->d_ps, sizeof(ps), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     if (ps.done) break;

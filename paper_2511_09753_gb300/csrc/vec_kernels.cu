@@ -593,6 +593,86 @@ __global__ void k_true_res(PcgArgs a) {
 }
 
 // ------------------------------------------------------------------- PCG
+//
+// An inner product of the iteration leaves one partial per CTA (the kernel
+// that forms its terms stores them); k_pcg_fin, one CTA launched right after,
+// adds the partials and takes the scalar step.  Between kernels of a graph
+// this is shorter than the last-arriver chain of reduce_finish (fences and
+// counter atomics in series), with the same tree.
+
+// The CTA's contiguous tree of its 256 terms (in one warp, as reduce_finish
+// forms it), stored to out[blockIdx.x] by thread 0.
+__device__ __forceinline__ void cta_partial(double term, double* out) {
+  __shared__ double red[256];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  red[threadIdx.x] = term;
+  __syncthreads();
+  if (warp == 0) {
+    double t[8];
+#pragma unroll
+    for (int q = 0; q < 8; q++) t[q] = red[lane * 8 + q];
+#pragma unroll
+    for (int len = 8; len > 1; len >>= 1)
+#pragma unroll
+      for (int q = 0; 2 * q + 1 < len; q++) t[q] = __dadd_rn(t[2 * q], t[2 * q + 1]);
+    const double s = __dadd_rn(warp_tree32(t[0]), 0.0);
+    if (lane == 0) out[blockIdx.x] = s;
+  }
+}
+
+// The total of the nb CTA partials v[0..nb): contiguous pairwise tree over
+// nb zero-padded to a power of two P >= 256 (levels of the same tree as
+// reduce_finish's groups and final level); one CTA of 256 threads.
+__device__ double cta_total(const double* v, int nb) {
+  __shared__ double red[256];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int P = 256;
+  while (P < nb) P <<= 1;
+  const int c = P >> 8, i0 = threadIdx.x * c;
+  double s;
+  if (c <= 8) {
+    double t[8];
+#pragma unroll
+    for (int q = 0; q < 8; q++) t[q] = (q < c && i0 + q < nb) ? __ldcg(v + i0 + q) : 0.0;
+    for (int len = c; len > 1; len >>= 1)
+#pragma unroll
+      for (int q = 0; q < 4; q++)
+        if (2 * q + 1 < len) t[q] = __dadd_rn(t[2 * q], t[2 * q + 1]);
+    s = t[0];
+  } else {  // binary-counter merging of the span (pairwise for a power of two)
+    double st[32];
+    int sz[32];
+    int top = 0;
+    for (int q = 0; q < c; q++) {
+      double x = i0 + q < nb ? __ldcg(v + i0 + q) : 0.0;
+      int w = 1;
+      while (top > 0 && sz[top - 1] == w) {
+        x = __dadd_rn(st[top - 1], x);
+        w <<= 1;
+        top--;
+      }
+      st[top] = x;
+      sz[top] = w;
+      top++;
+    }
+    s = st[0];
+  }
+  red[threadIdx.x] = s;
+  __syncthreads();
+  double tot = 0.0;
+  if (warp == 0) {
+    double t[8];
+#pragma unroll
+    for (int q = 0; q < 8; q++) t[q] = red[lane * 8 + q];
+#pragma unroll
+    for (int len = 8; len > 1; len >>= 1)
+#pragma unroll
+      for (int q = 0; 2 * q + 1 < len; q++) t[q] = __dadd_rn(t[2 * q], t[2 * q + 1]);
+    tot = warp_tree32(t[0]);
+  }
+  return tot;  // valid in warp 0
+}
+
 
 __device__ __forceinline__ double precond_apply(const PcgArgs& a, int i) {
   if (a.precond == 0) return a.r[i];
@@ -681,7 +761,48 @@ __device__ __forceinline__ void rho_finish(PcgScalars* s, int first, double rho1
   }
 }
 
-// z = Prec(r), terms r_i z_i -> rho (first = 1: initial rho, p = z follows).
+// p.q: stop at maxit, breakdown if 0 or not finite, else alpha
+__device__ __forceinline__ void pq_finish(PcgScalars* s, double pq) {
+  if (s->k >= s->maxit) {
+    s->done = 1;
+    s->status = 1;
+    return;
+  }
+  if (pq == 0.0 || !finite_d(pq)) {
+    s->done = 1;
+    s->status = 2;
+    return;
+  }
+  s->alpha = __ddiv_rn(s->rho, pq);
+}
+
+// r.r: count the iteration, converged or not finite
+__device__ __forceinline__ void rr_finish(PcgScalars* s, double rr) {
+  s->k += 1;
+  double rn = __dsqrt_rn(rr);
+  if (!finite_d(rn)) {
+    s->done = 1;
+    s->status = 2;
+  } else if (rn <= __dmul_rn(s->rtol, s->bn)) {
+    s->done = 1;
+    s->status = 0;
+  }
+}
+
+// one CTA: the total of the partials the previous kernel stored, then its
+// scalar step (which: 0 rho, 1 p.q, 2 r.r)
+__global__ void k_pcg_fin(PcgArgs a, int which, int first) {
+  PcgScalars* s = a.s;
+  if (s->done) return;
+  const double tot = cta_total(a.ws.bsum, a.ws.nb);
+  if (threadIdx.x != 0) return;
+  if (which == 0) rho_finish(s, first, tot);
+  else if (which == 1) pq_finish(s, tot);
+  else rr_finish(s, tot);
+}
+
+// z = Prec(r), terms r_i z_i -> partials of rho (first = 1: initial rho, p =
+// z follows).
 // zonly: z of the rows up to kLongRow entries only, no inner product (the
 // long rows run beside it in k_pcg_prec_long, k_pcg_rz follows both)
 __global__ void k_pcg_prec(PcgArgs a, int first, int zonly) {
@@ -704,17 +825,16 @@ __global__ void k_pcg_prec(PcgArgs a, int first, int zonly) {
     term = __dmul_rn(a.r[i], z);
   }
   if (zonly) return;
-  PcgScalars* s = a.s;
-  reduce_finish(term, a.ws, [s, first](double rho1) { rho_finish(s, first, rho1); });
+  cta_partial(term, a.ws.bsum);
 }
 
-// terms r_i z_i -> rho, after k_pcg_prec (zonly) and k_pcg_prec_long
+// terms r_i z_i -> partials of rho, after k_pcg_prec (zonly) and
+// k_pcg_prec_long
 __global__ void k_pcg_rz(PcgArgs a, int first) {
   if (a.s->done) return;
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   const double term = i < a.n ? __dmul_rn(a.r[i], a.z[i]) : 0.0;
-  PcgScalars* s = a.s;
-  reduce_finish(term, a.ws, [s, first](double rho1) { rho_finish(s, first, rho1); });
+  cta_partial(term, a.ws.bsum);
 }
 
 // p = z (first) or p = fma(beta, p, z)
@@ -727,7 +847,7 @@ __global__ void k_pcg_dir(PcgArgs a, int first) {
   if (a.mixed) a.p32[i] = __double2float_rn(p);
 }
 
-// q = A p, terms p_i q_i -> alpha
+// q = A p, terms p_i q_i -> partials of p.q
 __global__ void k_pcg_spmv(PcgArgs a) {
   if (a.s->done) return;
   int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -737,23 +857,10 @@ __global__ void k_pcg_spmv(PcgArgs a) {
     a.q[i] = q;
     term = __dmul_rn(a.p[i], q);
   }
-  PcgScalars* s = a.s;
-  reduce_finish(term, a.ws, [s](double pq) {
-    if (s->k >= s->maxit) {
-      s->done = 1;
-      s->status = 1;
-      return;
-    }
-    if (pq == 0.0 || !finite_d(pq)) {
-      s->done = 1;
-      s->status = 2;
-      return;
-    }
-    s->alpha = __ddiv_rn(s->rho, pq);
-  });
+  cta_partial(term, a.ws.bsum);
 }
 
-// x += alpha p, r -= alpha q, terms r_i^2 -> convergence test
+// x += alpha p, r -= alpha q, terms r_i^2 -> partials of r.r
 __global__ void k_pcg_update(PcgArgs a) {
   if (a.s->done) return;
   int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -766,18 +873,7 @@ __global__ void k_pcg_update(PcgArgs a) {
     if (a.mixed) a.r32[i] = __double2float_rn(r);
     term = __dmul_rn(r, r);
   }
-  PcgScalars* s = a.s;
-  reduce_finish(term, a.ws, [s](double rr) {
-    s->k += 1;
-    double rn = __dsqrt_rn(rr);
-    if (!finite_d(rn)) {
-      s->done = 1;
-      s->status = 2;
-    } else if (rn <= __dmul_rn(s->rtol, s->bn)) {
-      s->done = 1;
-      s->status = 0;
-    }
-  });
+  cta_partial(term, a.ws.bsum);
 }
 
 // ---------------------------------------------------------------- Lanczos
@@ -878,11 +974,13 @@ static cudaError_t launch_pcg_prec(const PcgArgs& a, int first, const PcgFork& f
   int g = (a.n + 255) / 256;
   if (!a.nlong) {
     k_pcg_prec<<<g, 256, 0, st>>>(a, first, 0);
+    k_pcg_fin<<<1, 256, 0, st>>>(a, 0, first);
     return cudaGetLastError();
   }
   if (!f.st2) {
     k_pcg_prec_long<<<(a.nlong + 7) / 8, 256, 0, st>>>(a);
     k_pcg_prec<<<g, 256, 0, st>>>(a, first, 0);
+    k_pcg_fin<<<1, 256, 0, st>>>(a, 0, first);
     return cudaGetLastError();
   }
   cudaError_t e = cudaEventRecord(f.fork, st);
@@ -895,6 +993,7 @@ static cudaError_t launch_pcg_prec(const PcgArgs& a, int first, const PcgFork& f
   e = cudaStreamWaitEvent(st, f.join, 0);
   if (e) return e;
   k_pcg_rz<<<g, 256, 0, st>>>(a, first);
+  k_pcg_fin<<<1, 256, 0, st>>>(a, 0, first);
   return cudaGetLastError();
 }
 
@@ -910,7 +1009,9 @@ cudaError_t launch_pcg_init(const PcgArgs& a, const PcgFork& f, cudaStream_t st)
 cudaError_t launch_pcg_iter(const PcgArgs& a, const PcgFork& f, cudaStream_t st) {
   int g = (a.n + 255) / 256;
   k_pcg_spmv<<<g, 256, 0, st>>>(a);
+  k_pcg_fin<<<1, 256, 0, st>>>(a, 1, 0);
   k_pcg_update<<<g, 256, 0, st>>>(a);
+  k_pcg_fin<<<1, 256, 0, st>>>(a, 2, 0);
   cudaError_t e = launch_pcg_prec(a, 0, f, st);
   if (e) return e;
   k_pcg_dir<<<g, 256, 0, st>>>(a, 0);
