@@ -32,11 +32,12 @@ __device__ inline double block_tree_global(const double* v, int len, double* red
   return s;
 }
 
-// Per-phase cycle counts of the column pass, kept only in the library built
-// with SPAI_PHASE_CLOCKS (a profiling build; the product library has none of
-// this).  g_phase_clk[kind * 16 + phase] sums, over all warps, the clock64()
-// cycles a warp spent in that phase; kPhCols counts the columns and kPhTail
-// the cycles thread 0 of each CTA spent in the reduction tail.
+// Phase boundaries of the column work.  In the library built with
+// SPAI_PHASE_CLOCKS (a profiling build) they count cycles per phase:
+// g_phase_clk[kind * 16 + phase] sums, over all warps, the clock64() cycles a
+// warp spent in that phase; kPhCols counts the columns and kPhTail the cycles
+// thread 0 of each CTA spent in the reduction tail.  In the product library
+// some of them are CTA barriers of MR and LOMR passes (ColCtx::mark).
 enum : int {
   kPhLoad = 0, kPhUnion, kPhSelect, kPhStore, kPhSpgemm, kPhList, kPhFixsum, kPhTail, kPhCols,
   kPhWarp, kPhCount
@@ -72,10 +73,18 @@ struct ColCtx {
     ph_t0 = t;
   }
 #else
+  int nsync = 0;  // threads of the CTA's warps with a column in this round
   __device__ ColCtx(const PassParams& pp, char* w, int l, const DevScalars* s, int sg)
       : p(pp), ws(w), lane(l), overflow(0), bytes(0), rbytes(0), spg(0), nnzM(0), sc(s), seg(sg) {}
   __device__ __forceinline__ void ph_start() {}
-  __device__ __forceinline__ void mark(int) {}
+  // phase boundary: the round's warps pass the ends of the selections, the
+  // products and the sums together, so they run the same code at about the
+  // same time and the SM fetches it once for all of them (barriers at the
+  // other boundaries too measured slower)
+  __device__ __forceinline__ void mark(int k) {
+    constexpr int kSyncAt = (1 << kPhSelect) | (1 << kPhSpgemm) | (1 << kPhFixsum);
+    if (nsync > 32 && ((kSyncAt >> k) & 1)) asm volatile("bar.sync 1, %0;" ::"r"(nsync) : "memory");
+  }
 #endif
   template <typename T> __device__ T* at(int off) const { return (T*)(ws + off); }
 };
@@ -674,17 +683,28 @@ __global__ void __launch_bounds__(256, sizeof(VC) == 4 ? 4 : 3) colpass_kernel(c
 #ifdef SPAI_PHASE_CLOCKS
   const long long w_t0 = clock64();
 #endif
-  for (int cc = warp; cc < B; cc += p.NW) {
+  for (int base = 0; base < B; base += p.NW) {
+    const int cc = base + warp;
     long long j = j0 + cc;
+    // the round's warps with a column are the lowest nv (every warp of the
+    // CTA computes the same nv)
+    const long long nv = min((long long)p.NW, min((long long)(B - base), p.n - (j0 + base)));
+#ifndef SPAI_PHASE_CLOCKS
+    // MR and LOMR keep the round's warps together phase by phase: their
+    // kernels are larger than the SM's instruction cache, and warps spread
+    // over the code miss in it (measured: MR 67 -> 78 %, LOMR 54 -> 62 %
+    // hits); CG's smaller passes lose more to the waits than they gain
+    if (KIND == kMR || KIND == kLOMR) c.nsync = 32 * (int)max(nv, 0LL);
+#endif
     double pr[6] = {0, 0, 0, 0, 0, 0};
     c.ph_start();
-    if (j < p.n) {
+    if (warp < nv) {
       column_work<VS, VC, PI, KIND, HOT>(c, (int)j, pr);
 #ifdef SPAI_PHASE_CLOCKS
       c.ph[kPhCols]++;
 #endif
     }
-    if (lane == 0)
+    if (lane == 0 && cc < B)
       for (int q = 0; q < nq; q++) part[q * B + cc] = pr[q];
   }
 #ifdef SPAI_PHASE_CLOCKS
