@@ -652,7 +652,7 @@ __device__ inline void coefficients(const PassParams& p, DevScalars* sc, double*
 // One instantiation per pass kind keeps each kernel's code small: with all
 // kinds behind a runtime switch the instruction cache missed often.
 template <typename VS, typename VC, bool PI, int KIND, bool HOT = false>
-__global__ void __launch_bounds__(256, sizeof(VC) == 4 ? 4 : 3) colpass_kernel(const PassParams p) {
+__global__ void __launch_bounds__(sizeof(VC) == 4 ? 512 : 256, sizeof(VC) == 4 ? 2 : 3) colpass_kernel(const PassParams p) {
   extern __shared__ __align__(16) char smem[];
   const int seg = p.nseg ? p.seg_of_col[(long long)blockIdx.x * p.B] : -1;
   DevScalars* sc = seg >= 0 ? p.segsc + seg : p.sc;

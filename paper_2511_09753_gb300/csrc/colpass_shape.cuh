@@ -160,13 +160,17 @@ inline PassCfg make_cfg(int kind, int vc, int n, int CAP, int W, bool dia, int s
   const int nq = 6;
   const int extra_fixed = 8 * 1024;  // reduction scratch (1024 doubles)
   // defaults measured on GB300 (64^3 operator, cap 3, 50 iterations from
-  // M_0): 8-warp CTAs everywhere (smaller CTAs that pack more warps leave
-  // too little L1 for the gathers of A), LOMR with one column per warp,
-  // MR and the CG passes with eight
-  const int occ = occ_req > 0 ? occ_req : env_int("SPAI_COLPASS_OCC", kind == kLOMR ? 3 : 4);
+  // M_0): 8-warp CTAs for MR and CG (smaller CTAs that pack more warps leave
+  // too little L1 for the gathers of A), 16-warp CTAs for LOMR (FP32 values:
+  // its warps pass phase barriers together, and fewer, larger groups per SM
+  // share more of the instruction cache), LOMR with one column per warp, MR
+  // and the CG passes with eight
+  const int occ = occ_req > 0 ? occ_req
+                             : env_int("SPAI_COLPASS_OCC", kind == kLOMR ? (vc == 4 ? 2 : 3) : 4);
   const int cpw = cpw_req > 0 ? cpw_req : env_int("SPAI_COLPASS_CPW", kind == kLOMR ? 1 : 8);
   c.ok = false;
-  for (int NW = 8; NW >= 1; NW >>= 1) {
+  // up to 16 warps with FP32 values (the kernels' launch bound), else 8
+  for (int NW = vc == 4 ? 16 : 8; NW >= 1; NW >>= 1) {
     // B: columns per CTA, a power of two: cpw per warp, fewer when n is
     // small, more when needed to keep at most 65536 CTAs (two-level tree).
     int B = NW;
