@@ -511,6 +511,7 @@ __device__ void column_work(ColCtx<VS, VC>& c, int j, double* part) {
       fixsum<1>(part, lane, TermSq<VC>{Rv}, LR);
       return;
     }
+    if (L.hk == L.uk) hash_clear_all(ha, lane);  // the union and selection used its bytes
     int cq = spgemm<HOT>(p, ha, Pr, Pv, Lp, -1, Tr, Tv, lane, c.seg);  // table holds Q = A P
     c.mark(kPhSpgemm);
     c.spg++;

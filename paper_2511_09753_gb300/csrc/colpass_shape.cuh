@@ -65,16 +65,36 @@ inline WarpLayout make_layout(int kind, int vc, int CAP, int W, bool dia, bool p
     ru += align16(bytes);
     return at;
   };
-  L.hk = take(4 * H);
-  L.hv = take(vc * H);
-  L.ho = take(2 * H);
+  const bool cgb = kind == kCGB;
+  if (cgb) {
+    // CG pass B: table A, the union table, the tie rows and the histogram
+    // share one region.  A holds R = I - A M (when R is not read from the
+    // slab) until R is listed, then the union, then the selection use the
+    // bytes, and the pass clears A's keys before Q = A P.
+    const int a_bytes = align16(4 * H) + align16(vc * H) + align16(2 * H);
+    const int u_bytes = align16(4 * HU) + 2 * align16(vc * HU) + align16(2 * HU);
+    const int x = take(std::max(std::max(a_bytes, u_bytes), align16(4 * LIST) + 4 * 128));
+    L.hk = x;
+    L.hv = L.hk + align16(4 * H);
+    L.ho = L.hv + align16(vc * H);
+    L.uk = x;
+    L.ua = L.uk + align16(4 * HU);
+    L.ub = L.ua + align16(vc * HU);
+    L.uo = L.ub + align16(vc * HU);
+    L.tie = x;
+    L.hist = x + align16(4 * LIST);
+  } else {
+    L.hk = take(4 * H);
+    L.hv = take(vc * H);
+    L.ho = take(2 * H);
+  }
   L.gk = take(lomr ? 4 * H : 0);
   L.gv = take(lomr ? vc * H : 0);
   L.go = take(lomr ? 2 * H : 0);
   // the union table: in R's region when it fits, else with the tie scratch
   const int u_bytes = align16(4 * HU) + 2 * align16(vc * HU) + align16(2 * HU);
-  const int uat = in_r(u_bytes);
-  bool u_placed = false;
+  const int uat = cgb ? -1 : in_r(u_bytes);
+  bool u_placed = cgb;
   if (uat >= 0) {
     L.uk = uat;
     L.ua = L.uk + align16(4 * HU);
@@ -104,7 +124,7 @@ inline WarpLayout make_layout(int kind, int vc, int CAP, int W, bool dia, bool p
     }
   }
   // the union table (if not placed yet) and the tie scratch share one region
-  if (!in_b) {
+  if (!in_b && !cgb) {
     int base = o;
     int u = 0;
     if (!u_placed) {
@@ -134,7 +154,7 @@ inline WarpLayout make_layout(int kind, int vc, int CAP, int W, bool dia, bool p
     L.Tr = tr >= 0 && tv >= 0 ? tr : take(4 * TMAX);
     L.Tv = tr >= 0 && tv >= 0 ? tv : take(vc * TMAX);
   }
-  if (!in_b) L.hist = take(4 * 128);  // 256 packed 16-bit bins
+  if (!in_b && !cgb) L.hist = take(4 * 128);  // 256 packed 16-bit bins
   L.zr = take(pi ? 4 * LMAX : 0);
   L.zv = take(pi ? vc * LMAX : 0);
   L.bytes = o;

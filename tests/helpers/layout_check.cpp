@@ -7,6 +7,9 @@
 //   R list / union, S, T      (the update phase ends before R is formed;
 //                              T only with A in diagonal slots)
 //   LOMR table B / union, tie, histogram (table B is empty until A P)
+//   CG pass B's table A / union, tie, histogram; union / histogram (A's keys
+//                              are cleared before A P; the union is over
+//                              before the selection)
 // Prints the number of violations; exit status 1 if there is any.
 #include <cstdio>
 #include <string>
@@ -59,6 +62,9 @@ int main() {
                 if (upd && (is("R", "U") || is("R", "S"))) return true;
                 if (upd && dia && is("R", "T")) return true;
                 if (lomr && (is("B", "U") || is("B", "tie") || is("B", "hist"))) return true;
+                if (kind == kCGB && (is("A", "U") || is("A", "tie") || is("A", "hist") ||
+                                     is("U", "hist")))
+                  return true;
                 return false;
               };
               cases++;
