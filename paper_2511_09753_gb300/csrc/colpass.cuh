@@ -292,8 +292,7 @@ __device__ void column_work(ColCtx<VS, VC>& c, int j, double* part) {
 
   if constexpr (KIND == kRES) {
     int cnt = spgemm<HOT>(p, ha, Mr, Mv, Lm, j, Tr, Tv, lane, c.seg);
-    int LR = table_to_list(ha, cnt, j, Rr, Rv, lane);
-    hash_clear(ha, cnt, lane);
+    int LR = table_to_list<VC, true>(ha, cnt, j, Rr, Rv, lane);
     c.spg++;
     fixsum<1>(part, lane, TermSq<VC>{Rv}, LR);
     return;
@@ -312,8 +311,7 @@ __device__ void column_work(ColCtx<VS, VC>& c, int j, double* part) {
     c.nnzM += Lm;  // M_iter
     int cnt = spgemm<HOT>(p, ha, Mr, Mv, Lm, j, Tr, Tv, lane, c.seg);
     c.mark(kPhSpgemm);
-    int LR = table_to_list(ha, cnt, j, Rr, Rv, lane);
-    hash_clear(ha, cnt, lane);
+    int LR = table_to_list<VC, true>(ha, cnt, j, Rr, Rv, lane);
     c.mark(kPhList);
     c.spg++;
     if (!dir && !store) {
@@ -383,8 +381,7 @@ __device__ void column_work(ColCtx<VS, VC>& c, int j, double* part) {
     c.nnzM += Lm;  // M_iter
     int cr = spgemm<HOT>(p, ha, Mr, Mv, Lm, j, Tr, Tv, lane, c.seg);
     c.mark(kPhSpgemm);
-    int LR = table_to_list(ha, cr, j, Rr, Rv, lane);
-    hash_clear(ha, cr, lane);
+    int LR = table_to_list<VC, true>(ha, cr, j, Rr, Rv, lane);
     c.mark(kPhList);
     c.spg++;
     if (!dir && !store) {
@@ -464,8 +461,7 @@ __device__ void column_work(ColCtx<VS, VC>& c, int j, double* part) {
     }
     int cr = spgemm<HOT>(p, ha, Mr, Mv, Lm, j, Tr, Tv, lane, c.seg);
     c.mark(kPhSpgemm);
-    int LR = table_to_list(ha, cr, j, Rr, Rv, lane);
-    hash_clear(ha, cr, lane);
+    int LR = table_to_list<VC, true>(ha, cr, j, Rr, Rv, lane);
     c.mark(kPhList);
     c.spg++;
     if (rout) store_r(c, j, LR, Rr, Rv);
@@ -486,8 +482,7 @@ __device__ void column_work(ColCtx<VS, VC>& c, int j, double* part) {
       c.mark(kPhLoad);
     } else {
       int cr = spgemm<HOT>(p, ha, Mr, Mv, Lm, j, Tr, Tv, lane, c.seg);
-      LR = table_to_list(ha, cr, j, Rr, Rv, lane);
-      hash_clear(ha, cr, lane);
+      LR = table_to_list<VC, true>(ha, cr, j, Rr, Rv, lane);
       c.spg++;
     }
     if (!slab) {  // else P, loaded above, was chosen outside (global dropping)

@@ -138,27 +138,21 @@ struct Fix128 {
   long long hi;
 };
 
+// S += t at unit 2^(eb-1133), t truncated toward zero to that unit.  No
+// branches: the shifts are clamped (m < 2^53, so a right shift by 53 or more
+// leaves nothing), and a negative term is added as its two's complement.
 __device__ __forceinline__ void term_add(Fix128& S, const Term& t, int eb) {
   const unsigned long long m = t.m;
   const int sh = (t.e ? t.e : 1) - eb + 58;  // <= 58: the term fits in 111 bits
-  unsigned long long lo, hi;
-  if (sh >= 0) {
-    lo = m << sh;
-    hi = sh ? (m >> (64 - sh)) : 0ull;
-  } else {
-    lo = (sh > -64) ? (m >> (-sh)) : 0ull;
-    hi = 0ull;
-  }
-  if (t.neg) {
-    unsigned long long borrow = S.lo < lo ? 1ull : 0ull;
-    S.lo -= lo;
-    S.hi -= (long long)(hi + borrow);
-  } else {
-    unsigned long long s2 = S.lo + lo;
-    unsigned long long carry = s2 < lo ? 1ull : 0ull;
-    S.lo = s2;
-    S.hi += (long long)(hi + carry);
-  }
+  const int sl = max(sh, 0), sr = min(max(-sh, 0), 63);
+  const unsigned long long lo = (m << sl) >> sr;
+  const unsigned long long hi = (m >> 1) >> (63 - sl);  // m >> (64 - sl), 0 for sl = 0
+  const unsigned __int128 nm = (unsigned __int128)0 - (unsigned __int128)(unsigned)t.neg;
+  const unsigned __int128 v = ((((unsigned __int128)hi << 64) | lo) ^ nm) - nm;
+  const unsigned __int128 acc =
+      ((((unsigned __int128)(unsigned long long)S.hi) << 64) | S.lo) + v;
+  S.lo = (unsigned long long)acc;
+  S.hi = (long long)(unsigned long long)(acc >> 64);
 }
 
 // Warp sum of the 32 lanes' accumulators: each 128-bit two's-complement value
@@ -274,22 +268,18 @@ __device__ void fixsum(double* out, int lane, const F0& f0, int L0, const F1& f1
   e0 = __reduce_max_sync(kFull, e0);
   if (K > 1) e1 = __reduce_max_sync(kFull, e1);
   if (K > 2) e2 = __reduce_max_sync(kFull, e2);
+  // the cached terms (zero past a list's end) in one straight-line block, so
+  // the sums' carry chains interleave
   Fix128 S0 = {0ull, 0ll}, S1 = {0ull, 0ll}, S2 = {0ull, 0ll};
-  if (e0) {
-    if (lane < L0) term_add(S0, a0, e0);
-    if (lane + 32 < L0) term_add(S0, b0, e0);
-    for (int i = lane + 64; i < L0; i += 32) term_add(S0, f0(i), e0);
-  }
-  if (K > 1 && e1) {
-    if (lane < L1) term_add(S1, a1, e1);
-    if (lane + 32 < L1) term_add(S1, b1, e1);
-    for (int i = lane + 64; i < L1; i += 32) term_add(S1, f1(i), e1);
-  }
-  if (K > 2 && e2) {
-    if (lane < L2) term_add(S2, a2, e2);
-    if (lane + 32 < L2) term_add(S2, b2, e2);
-    for (int i = lane + 64; i < L2; i += 32) term_add(S2, f2(i), e2);
-  }
+  term_add(S0, a0, e0);
+  if (K > 1) term_add(S1, a1, e1);
+  if (K > 2) term_add(S2, a2, e2);
+  term_add(S0, b0, e0);
+  if (K > 1) term_add(S1, b1, e1);
+  if (K > 2) term_add(S2, b2, e2);
+  for (int i = lane + 64; i < L0; i += 32) term_add(S0, f0(i), e0);
+  if (K > 1) for (int i = lane + 64; i < L1; i += 32) term_add(S1, f1(i), e1);
+  if (K > 2) for (int i = lane + 64; i < L2; i += 32) term_add(S2, f2(i), e2);
   if (K == 1) {
     fix_allreduce(S0);
     out[0] = fix_to_double(S0, e0);
@@ -516,6 +506,14 @@ __device__ int warp_select(const int* sr, const V* sv, int L, int cap, int* dr, 
   K prefix = 0, pmask = 0;
   int need = cap;
   bool exact = false;
+  // lists of at most 64 entries (the usual case) keep their two keys per
+  // lane in registers for every digit pass
+  const bool small = L <= 64;
+  K k0 = 0, k1 = 0;
+  if (small) {
+    if (lane < L) k0 = sel_key(sv[lane], sr[lane], keep_row);
+    if (lane + 32 < L) k1 = sel_key(sv[lane + 32], sr[lane + 32], keep_row);
+  }
   // digits of 8 bits from the top of the key's 31 (63) significant bits, so
   // the first digit is the exponent field of an FP32 |v|; the last is shorter
   for (int hi = 8 * (int)sizeof(K) - 1; hi > 0; hi -= 8) {
@@ -523,17 +521,22 @@ __device__ int warp_select(const int* sr, const V* sv, int L, int cap, int* dr, 
     const unsigned dmask = (1u << (hi - shift)) - 1u;
     hist_clear(hist, lane);
     __syncwarp();
-    for (int base = 0; base < L; base += 32) {
-      int i = base + lane;
-      bool act = false;
-      unsigned dig = 0;
-      if (i < L) {
-        K k = absbits(sv[i]);
-        if (keep_row >= 0 && sr[i] == keep_row) k = ~(K)0 >> 1;
-        act = (k & pmask) == prefix;
-        dig = (unsigned)(k >> shift) & dmask;
+    if (small) {
+      hist_add(hist, lane < L && (k0 & pmask) == prefix, (unsigned)(k0 >> shift) & dmask);
+      hist_add(hist, lane + 32 < L && (k1 & pmask) == prefix, (unsigned)(k1 >> shift) & dmask);
+    } else {
+      for (int base = 0; base < L; base += 32) {
+        int i = base + lane;
+        bool act = false;
+        unsigned dig = 0;
+        if (i < L) {
+          K k = absbits(sv[i]);
+          if (keep_row >= 0 && sr[i] == keep_row) k = ~(K)0 >> 1;
+          act = (k & pmask) == prefix;
+          dig = (unsigned)(k >> shift) & dmask;
+        }
+        hist_add(hist, act, dig);
       }
-      hist_add(hist, act, dig);
     }
     __syncwarp();
     // the lane's 8 bins in two packed sums (their halves cannot carry: the
@@ -600,7 +603,7 @@ __device__ int warp_select(const int* sr, const V* sv, int L, int cap, int* dr, 
     if (i < L) {
       rr = sr[i];
       vv = sv[i];
-      K k = sel_key(vv, rr, keep_row) & pmask;
+      K k = (small ? (base ? k1 : k0) : sel_key(vv, rr, keep_row)) & pmask;
       keep = k > prefix;
       if (k == prefix) {
         if (exact) {
@@ -835,8 +838,9 @@ __device__ void sort_rows_small(int* r, V* v, int L, int* tr, V* tv, int lane) {
 // Move the table's rows to a list: value = acc (diag < 0) or the residual
 // 1 - acc on the diagonal / -acc elsewhere (diag >= 0); the transformed
 // value is also written back to the table so later lookups see R itself.
-// Exact zeros are left out of the list.
-template <typename VC>
+// Exact zeros are left out of the list.  CLEAR: the table is emptied on the
+// way instead (each lane clears the slots it read; nothing is written back).
+template <typename VC, bool CLEAR = false>
 __device__ int table_to_list(const HashT& h, int cnt, int diag, int* outr, VC* outv, int lane) {
   VC* hv = (VC*)h.val;
   int outn = 0;
@@ -848,10 +852,11 @@ __device__ int table_to_list(const HashT& h, int cnt, int diag, int* outr, VC* o
     if (i < cnt) {
       int s = h.occ[i];
       r = h.key[s];
+      if (CLEAR) h.key[s] = -1;
       VC acc = hv[s];
       if (diag >= 0) {
         val = (r == diag) ? (VC(1) - acc) : -acc;
-        hv[s] = val;
+        if (!CLEAR) hv[s] = val;
       } else {
         val = acc;
       }
