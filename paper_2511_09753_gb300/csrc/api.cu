@@ -120,6 +120,10 @@ struct spai_ctx {
   int* d_slong = nullptr;  // rows of S too long for the sliced ELL, and their count
   int* d_nlong = nullptr;
   int nlong = 0;
+  // with long rows: S's rows by length, longest first in each window of
+  // 1,024 rows (slot order of its sliced ELL), and the long rows by length
+  int* d_sperm = nullptr;
+  int* d_slongs = nullptr;
   int* d_cnt = nullptr;
   long long* d_scan = nullptr;
   int *d_tmpi = nullptr;
@@ -386,6 +390,8 @@ void free_all(spai_ctx* h) {
   dfree(h->d_ssval);
   dfree(h->d_slong);
   dfree(h->d_nlong);
+  dfree(h->d_sperm);
+  dfree(h->d_slongs);
   dfree(h->d_cnt);
   dfree(h->d_scan);
   dfree(h->d_tmpi);
@@ -545,9 +551,6 @@ int ensure_sym_sell(spai_ctx* h) {
     int rc = dalloc(&h->d_w32, (size_t)ns + 1);
     if (rc) return rc;
   }
-  long long tot = 0;
-  CK(launch_sell_build_i64(n, h->d_srp, h->d_sci, h->d_sv, h->d_w32, h->d_ssp, h->d_scan,
-                           &h->d_sscol, &h->d_ssval, &h->ss_cap, &tot, h->stream));
   if (!h->d_slong) {
     int rc = dalloc(&h->d_slong, (size_t)n);
     if (!rc) rc = dalloc(&h->d_nlong, 1);
@@ -556,7 +559,26 @@ int ensure_sym_sell(spai_ctx* h) {
   CK(launch_long_rows(n, h->d_srp, h->d_slong, h->d_nlong, h->stream));
   CK(cudaMemcpyAsync(&h->nlong, h->d_nlong, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
-  h->other_launches += 6;
+  h->other_launches += 1;
+  // with long rows the preconditioner product forms z apart from (r, z), so
+  // its slots can hold the rows in any order: longest first, so that the 32
+  // rows of a slice have like lengths and the slice's width wastes little
+  const int* perm = nullptr;
+  if (h->nlong) {
+    if (!h->d_sperm) {
+      int rc = dalloc(&h->d_sperm, (size_t)n);
+      if (!rc) rc = dalloc(&h->d_slongs, (size_t)n);
+      if (rc) return rc;
+    }
+    CK(launch_len_order(n, h->d_srp, h->d_sperm, h->stream));
+    CK(launch_sort_long(h->d_slong, h->nlong, h->d_srp, h->d_slongs, h->stream));
+    h->other_launches += 2;
+    perm = h->d_sperm;
+  }
+  long long tot = 0;
+  CK(launch_sell_build_i64(n, h->d_srp, h->d_sci, h->d_sv, h->d_w32, h->d_ssp, h->d_scan,
+                           &h->d_sscol, &h->d_ssval, &h->ss_cap, &tot, h->stream, perm));
+  h->other_launches += 5;
   h->ssell_valid = true;
   return SPAI_OK;
 }
@@ -1628,8 +1650,9 @@ int pcg_solve(spai_handle h, const double* b, double* x, int nrhs, double rtol, 
       a.sell.sptr = h->d_ssp;
       a.sell.col = h->d_sscol;
       a.sell.val = h->d_ssval;
-      a.longrows = h->d_slong;
+      a.longrows = h->nlong ? h->d_slongs : h->d_slong;
       a.nlong = h->nlong;
+      a.sperm = h->nlong ? h->d_sperm : nullptr;
     }
   }
   a.b = h->d_b;

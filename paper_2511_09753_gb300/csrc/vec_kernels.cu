@@ -152,6 +152,18 @@ __device__ __forceinline__ double sell_row_chain(const SellM& m, const long long
   return acc;
 }
 
+// The chain of a row of length len stored in slot i of a sliced ELL
+__device__ __forceinline__ double sell_slot_chain(const SellM& m, int len, const double* x, int i) {
+  const int s = i >> 5, lane = i & 31;
+  const long long b = m.sptr[s];
+  double acc = 0.0;
+  for (int t = 0; t < len; t++) {
+    long long e = b + 32LL * t + lane;
+    acc = __fma_rn(m.val[e], x[m.col[e]], acc);
+  }
+  return acc;
+}
+
 template <typename RP>
 __device__ __forceinline__ double row_chain_f32(const RP* rp, const int* ci, const float* v,
                                                 const float* x, int i) {
@@ -173,15 +185,17 @@ cudaError_t launch_to_f32(const double* in, float* out, long long count, cudaStr
 }
 
 // Rows longer than maxw are left out of the sliced ELL (stored as empty rows):
-// their products are formed from the CSR arrays by a whole warp.
+// their products are formed from the CSR arrays by a thread each.  perm
+// (optional): slot i of the sliced ELL holds row perm[i] instead of row i.
 template <typename RP>
-__global__ void k_sell_width(int n, const RP* rp, int* w32, int maxw) {
+__global__ void k_sell_width(int n, const RP* rp, int* w32, int maxw, const int* perm) {
   int s = blockIdx.x * blockDim.x + threadIdx.x;
   int ns = (n + 31) / 32;
   if (s >= ns) return;
   int w = 0;
   for (int i = 32 * s; i < min(n, 32 * s + 32); i++) {
-    const int len = (int)(rp[i + 1] - rp[i]);
+    const int row = perm ? perm[i] : i;
+    const int len = (int)(rp[row + 1] - rp[row]);
     if (len <= maxw) w = max(w, len);
   }
   w32[s] = 32 * w;
@@ -189,14 +203,16 @@ __global__ void k_sell_width(int n, const RP* rp, int* w32, int maxw) {
 
 template <typename RP>
 __global__ void k_sell_fill(int n, const RP* rp, const int* ci, const double* v,
-                            const long long* sptr, int* scol, double* sval, int maxw) {
+                            const long long* sptr, int* scol, double* sval, int maxw,
+                            const int* perm) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   int ns = (n + 31) / 32;
   if (i >= 32 * ns) return;
   const int s = i >> 5, lane = i & 31;
   const long long b = sptr[s];
   const int w = (int)((sptr[s + 1] - b) >> 5);
-  long long e0 = i < n ? (long long)rp[i] : 0, e1 = i < n ? (long long)rp[i + 1] : 0;
+  const int row = i < n ? (perm ? perm[i] : i) : 0;
+  long long e0 = i < n ? (long long)rp[row] : 0, e1 = i < n ? (long long)rp[row + 1] : 0;
   if (e1 - e0 > maxw) e1 = e0;
   for (int t = 0; t < w; t++) {
     long long e = e0 + t;
@@ -214,9 +230,10 @@ __global__ void k_sell_fill(int n, const RP* rp, const int* ci, const double* v,
 template <typename RP>
 static cudaError_t sell_build_t(int n, const RP* rp, const int* ci, const double* v, int* w32,
                                 long long* sptr, long long* scan_tmp, int** scol, double** sval,
-                                long long* cap, long long* total, cudaStream_t st, int maxw) {
+                                long long* cap, long long* total, cudaStream_t st, int maxw,
+                                const int* perm) {
   int ns = (n + 31) / 32;
-  k_sell_width<RP><<<(ns + 255) / 256, 256, 0, st>>>(n, rp, w32, maxw);
+  k_sell_width<RP><<<(ns + 255) / 256, 256, 0, st>>>(n, rp, w32, maxw, perm);
   cudaError_t e = launch_exclusive_scan(w32, sptr, ns, scan_tmp, st);
   if (e != cudaSuccess) return e;
   long long tot = 0;
@@ -233,7 +250,8 @@ static cudaError_t sell_build_t(int n, const RP* rp, const int* ci, const double
     if (e != cudaSuccess) return e;
     *cap = tot;
   }
-  k_sell_fill<RP><<<(32 * ns + 255) / 256, 256, 0, st>>>(n, rp, ci, v, sptr, *scol, *sval, maxw);
+  k_sell_fill<RP><<<(32 * ns + 255) / 256, 256, 0, st>>>(n, rp, ci, v, sptr, *scol, *sval, maxw,
+                                                         perm);
   *total = tot;
   return cudaGetLastError();
 }
@@ -242,14 +260,84 @@ cudaError_t launch_sell_build_i32(int n, const int* rp, const int* ci, const dou
                                   long long* sptr, long long* scan_tmp, int** scol, double** sval,
                                   long long* cap, long long* total, cudaStream_t st) {
   return sell_build_t<int>(n, rp, ci, v, w32, sptr, scan_tmp, scol, sval, cap, total, st,
-                           0x7fffffff);
+                           0x7fffffff, nullptr);
 }
 
 cudaError_t launch_sell_build_i64(int n, const long long* rp, const int* ci, const double* v,
                                   int* w32, long long* sptr, long long* scan_tmp, int** scol,
-                                  double** sval, long long* cap, long long* total, cudaStream_t st) {
+                                  double** sval, long long* cap, long long* total, cudaStream_t st,
+                                  const int* perm) {
   return sell_build_t<long long>(n, rp, ci, v, w32, sptr, scan_tmp, scol, sval, cap, total, st,
-                                 kLongRow);
+                                 kLongRow, perm);
+}
+
+// Rows of S ordered by length, longest first, inside each window of 1,024
+// consecutive rows (32 slices of the sliced ELL), so that a slice's rows
+// have like lengths while the operands a window gathers stay near each
+// other; rows longer than kLongRow (multiplied apart) count as empty.  The
+// order among rows of one length is arbitrary: each row's product is the
+// same chain wherever it sits.
+__global__ void __launch_bounds__(256) k_len_order(int n, const long long* rp, int* perm) {
+  __shared__ int cnt[kLongRow + 1];
+  const int w0 = blockIdx.x * 1024;
+  for (int b = threadIdx.x; b <= kLongRow; b += blockDim.x) cnt[b] = 0;
+  __syncthreads();
+  int len[4];
+#pragma unroll
+  for (int q = 0; q < 4; q++) {
+    const int i = w0 + q * 256 + threadIdx.x;
+    len[q] = -1;
+    if (i < n) {
+      const int l = (int)(rp[i + 1] - rp[i]);
+      len[q] = l <= kLongRow ? l : 0;
+      atomicAdd(&cnt[len[q]], 1);
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {  // counts -> first slot of each length, longest first
+    int at = w0;
+    for (int l = kLongRow; l >= 0; l--) {
+      const int c = cnt[l];
+      cnt[l] = at;
+      at += c;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < 4; q++)
+    if (len[q] >= 0) perm[atomicAdd(&cnt[len[q]], 1)] = w0 + q * 256 + threadIdx.x;
+}
+
+cudaError_t launch_len_order(int n, const long long* rp, int* perm, cudaStream_t st) {
+  k_len_order<<<(n + 1023) / 1024, 256, 0, st>>>(n, rp, perm);
+  return cudaGetLastError();
+}
+
+// The long rows in[0..nl) by length, longest first (ties: the smaller row),
+// by ranking in one CTA; more than kSortLongMax of them are copied as they
+// are (their order changes no result, only how the warps share them out).
+constexpr int kSortLongMax = 4096;
+__global__ void k_sort_long(const int* in, int nl, const long long* rp, int* out) {
+  for (int i = threadIdx.x; i < nl; i += blockDim.x) {
+    const int row = in[i];
+    if (nl > kSortLongMax) {
+      out[i] = row;
+      continue;
+    }
+    const long long len = rp[row + 1] - rp[row];
+    int rank = 0;
+    for (int k = 0; k < nl; k++) {
+      const int r2 = in[k];
+      const long long l2 = rp[r2 + 1] - rp[r2];
+      rank += (l2 > len) || (l2 == len && r2 < row);
+    }
+    out[rank] = row;
+  }
+}
+
+cudaError_t launch_sort_long(const int* in, int nl, const long long* rp, int* out, cudaStream_t st) {
+  k_sort_long<<<1, 1024, 0, st>>>(in, nl, rp, out);
+  return cudaGetLastError();
 }
 
 // ------------------------------------------------------------ set-up
@@ -689,14 +777,16 @@ __device__ __forceinline__ double precond_sell(const PcgArgs& a, int i) {
   return sell_row_chain(a.sell, a.mrp, a.r, i);
 }
 
-// z_i of the rows longer than kLongRow, a warp each: the lanes load 32
-// consecutive CSR entries and their operands at once; the chain itself --
-// the same fma chain over ascending column -- runs on the shuffled values
-__global__ void k_pcg_prec_long(PcgArgs a) {
+// z_i of the rows longer than kLongRow, a warp each, one warp per CTA (the
+// rows come longest first, so the longest chains start first and the warps
+// spread over all SMs instead of sharing a few SMs' FP64 pipes): the lanes
+// load 32 consecutive CSR entries and their operands at once; the chain
+// itself -- the same fma chain over ascending column -- runs on the shuffled
+// values
+__global__ void __launch_bounds__(32) k_pcg_prec_long(PcgArgs a) {
   if (a.s->done) return;
-  const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-  if (w >= a.nlong) return;
-  const int row = a.longrows[w];
+  const int lane = threadIdx.x;
+  const int row = a.longrows[blockIdx.x];
   const long long rb = a.mrp[row], re = a.mrp[row + 1];
   double acc = 0.0;
   for (long long base = rb; base < re; base += 32) {
@@ -811,8 +901,10 @@ __global__ void k_pcg_prec(PcgArgs a, int first, int zonly) {
   double term = 0.0;
   if (a.sell.sptr) {  // S in sliced ELL (FP64 products)
     if (i < a.n) {
-      if (zonly) {
-        if (a.mrp[i + 1] - a.mrp[i] <= kLongRow) a.z[i] = sell_row_chain(a.sell, a.mrp, a.r, i);
+      if (zonly) {  // slot i holds row sperm[i]
+        const int row = a.sperm ? a.sperm[i] : i;
+        const int len = (int)(a.mrp[row + 1] - a.mrp[row]);
+        if (len <= kLongRow) a.z[row] = sell_slot_chain(a.sell, len, a.r, i);
         return;
       }
       const double z = precond_sell(a, i);
@@ -978,15 +1070,16 @@ static cudaError_t launch_pcg_prec(const PcgArgs& a, int first, const PcgFork& f
     return cudaGetLastError();
   }
   if (!f.st2) {
-    k_pcg_prec_long<<<(a.nlong + 7) / 8, 256, 0, st>>>(a);
-    k_pcg_prec<<<g, 256, 0, st>>>(a, first, 0);
+    k_pcg_prec_long<<<a.nlong, 32, 0, st>>>(a);
+    k_pcg_prec<<<g, 256, 0, st>>>(a, first, 1);
+    k_pcg_rz<<<g, 256, 0, st>>>(a, first);
     k_pcg_fin<<<1, 256, 0, st>>>(a, 0, first);
     return cudaGetLastError();
   }
   cudaError_t e = cudaEventRecord(f.fork, st);
   if (!e) e = cudaStreamWaitEvent(f.st2, f.fork, 0);
   if (e) return e;
-  k_pcg_prec_long<<<(a.nlong + 7) / 8, 256, 0, f.st2>>>(a);
+  k_pcg_prec_long<<<a.nlong, 32, 0, f.st2>>>(a);
   e = cudaEventRecord(f.join, f.st2);
   if (e) return e;
   k_pcg_prec<<<g, 256, 0, st>>>(a, first, 1);

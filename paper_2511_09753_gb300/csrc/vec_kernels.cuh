@@ -40,6 +40,9 @@ struct PcgArgs {
   SellM sell;
   const int* longrows;
   int nlong;
+  // with long rows: slot i of `sell` holds row sperm[i] (rows by length,
+  // longest first), so the rows of a 32-row slice have like lengths
+  const int* sperm;
   const double* b;
   double *x, *r, *z, *p, *q;
   PcgScalars* s;
@@ -79,7 +82,13 @@ cudaError_t launch_sell_build_i32(int n, const int* rp, const int* ci, const dou
                                   long long* cap, long long* total, cudaStream_t st);
 cudaError_t launch_sell_build_i64(int n, const long long* rp, const int* ci, const double* v,
                                   int* w32, long long* sptr, long long* scan_tmp, int** scol,
-                                  double** sval, long long* cap, long long* total, cudaStream_t st);
+                                  double** sval, long long* cap, long long* total, cudaStream_t st,
+                                  const int* perm);
+// perm = the rows of the CSR rows rp ordered by length, longest first, in
+// each window of 1,024 rows (rows past the sliced-ELL limit count as empty)
+cudaError_t launch_len_order(int n, const long long* rp, int* perm, cudaStream_t st);
+// out = the long rows in[0..nl) by length, longest first
+cudaError_t launch_sort_long(const int* in, int nl, const long long* rp, int* out, cudaStream_t st);
 cudaError_t launch_to_f32(const double* in, float* out, long long count, cudaStream_t st);
 // rows of a CSR pattern longer than the sliced ELL's limit, compacted into out
 // (count in *nout, device)
