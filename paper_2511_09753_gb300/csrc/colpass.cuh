@@ -371,7 +371,9 @@ __device__ void column_work(ColCtx<VS, VC>& c, int j, double* part) {
       store_col(c, p.Prow, p.Pval, p.Plen, j, off, Lp, Pr, Pv);
       c.mark(kPhStore);
       CombAdd<VC> fa;
-      int Lt = warp_union(un, Mr, Mv, Lm, Sr, Sv, Ls, Tr, Tv, fa, lane);
+      // S (up to two caps of entries) looks up M (at most one): the union's
+      // table takes the shorter list, and m + s = s + m exactly
+      int Lt = warp_union(un, Sr, Sv, Ls, Mr, Mv, Lm, Tr, Tv, fa, lane);
       c.mark(kPhUnion);
       Lm = warp_select(Tr, Tv, Lt, cap, Mr, Mv, hist, tie, p.drop, ovf, lane, keep);
       c.mark(kPhSelect);

@@ -395,63 +395,91 @@ struct UnionT {
   int H;
 };
 
+// slot of row r, or -1 if absent
+__device__ __forceinline__ int hash_slot_of(const HashT& h, int r) {
+  int s = hslot(r, h.H);
+  for (;;) {
+    const int k = h.key[s];
+    if (k == r) return s;
+    if (k == -1) return -1;
+    s = (s + 1) & (h.H - 1);
+  }
+}
+
 // out = pattern union of A and B with value f(a or 0, b or 0); exact zeros
-// removed.  Returns the output length.
+// removed.  Returns the output length.  Rows are distinct within each list,
+// so only B goes into the table: A's rows look B up and go straight to the
+// output (a matched B slot is flagged), then B's unflagged rows follow.
 template <typename V, typename F>
 __device__ int warp_union(const UnionT& u, const int* ar, const V* av, int La, const int* br,
                           const V* bv, int Lb, int* outr, V* outv, F f, int lane) {
   HashT h;
   h.key = u.key;
-  h.val = u.va;
+  h.val = u.vb;
   h.occ = u.occ;
   h.H = u.H;
-  V* va = (V*)u.va;
+  V* hit = (V*)u.va;  // V(1) once an A row matched the slot
   V* vb = (V*)u.vb;
   hash_clear_all(h, lane);  // the table's bytes are shared with other scratch
   int cnt = 0;
-  for (int base = 0; base < La; base += 32) {
-    int i = base + lane;
-    bool isnew = false;
-    int s = -1;
-    if (i < La) {
-      s = hash_insert<V>(h, ar[i], &isnew);
-      va[s] = av[i];
-      vb[s] = V(0);
-    }
-    occ_append(h, cnt, isnew, s);
-  }
-  __syncwarp();
   for (int base = 0; base < Lb; base += 32) {
     int i = base + lane;
     bool isnew = false;
     int s = -1;
     if (i < Lb) {
       s = hash_insert<V>(h, br[i], &isnew);
-      if (isnew) va[s] = V(0);
       vb[s] = bv[i];
+      hit[s] = V(0);
     }
     occ_append(h, cnt, isnew, s);
   }
   __syncwarp();
   int outn = 0;
+  for (int base = 0; base < La; base += 32) {
+    int i = base + lane;
+    bool nz = false;
+    int r = 0;
+    V v = V(0);
+    if (i < La) {
+      r = ar[i];
+      const int s = hash_slot_of(h, r);
+      V y = V(0);
+      if (s >= 0) {
+        y = vb[s];
+        hit[s] = V(1);
+      }
+      v = f(av[i], y);
+      nz = v != V(0);
+    }
+    unsigned bm = __ballot_sync(kFull, nz);
+    if (nz) {
+      int pos = outn + __popc(bm & lanemask_lt());
+      outr[pos] = r;
+      outv[pos] = v;
+    }
+    outn += __popc(bm);
+  }
+  __syncwarp();
   for (int base = 0; base < cnt; base += 32) {
     int i = base + lane;
     bool nz = false;
     int r = 0;
     V v = V(0);
     if (i < cnt) {
-      int s = u.occ[i];
-      r = u.key[s];
-      v = f(va[s], vb[s]);
-      nz = v != V(0);
+      const int s = u.occ[i];
+      if (hit[s] == V(0)) {
+        r = u.key[s];
+        v = f(V(0), vb[s]);
+        nz = v != V(0);
+      }
     }
-    unsigned b = __ballot_sync(kFull, nz);
+    unsigned bm = __ballot_sync(kFull, nz);
     if (nz) {
-      int pos = outn + __popc(b & lanemask_lt());
+      int pos = outn + __popc(bm & lanemask_lt());
       outr[pos] = r;
       outv[pos] = v;
     }
-    outn += __popc(b);
+    outn += __popc(bm);
   }
   __syncwarp();
   return outn;
