@@ -140,6 +140,7 @@ struct spai_ctx {
          *d_q = nullptr;
   PcgScalars* d_ps = nullptr;
   double *d_vbsum = nullptr, *d_vgsum = nullptr;
+  double* d_vrrsum = nullptr;  // PCG: the CTA partials of (r, r)
   unsigned *d_vcnt1 = nullptr, *d_vcnt2 = nullptr;
   // PCG arithmetic (SPAI_FP64, or SPAI_MIXED: FP32-values products) and the
   // FP32 copies it uses: A's sliced-ELL values, M's and S's row values, the
@@ -408,6 +409,7 @@ void free_all(spai_ctx* h) {
   dfree(h->d_q);
   dfree(h->d_ps);
   dfree(h->d_vbsum);
+  dfree(h->d_vrrsum);
   dfree(h->d_vgsum);
   dfree(h->d_vcnt1);
   dfree(h->d_vcnt2);
@@ -1526,6 +1528,7 @@ static int ensure_pcg(spai_ctx* h) {
   rc = rc ? rc : dalloc(&h->d_q, n);
   rc = rc ? rc : dalloc(&h->d_ps, 1);
   rc = rc ? rc : dalloc(&h->d_vbsum, nb);
+  rc = rc ? rc : dalloc(&h->d_vrrsum, nb);
   rc = rc ? rc : dalloc(&h->d_vgsum, ng);
   rc = rc ? rc : dalloc(&h->d_vcnt1, ng);
   rc = rc ? rc : dalloc(&h->d_vcnt2, 1);
@@ -1672,6 +1675,7 @@ int pcg_solve(spai_handle h, const double* b, double* x, int nrhs, double rtol, 
     a.r32 = h->d_r32;
   }
   a.ws.bsum = h->d_vbsum;
+  a.rrsum = h->d_vrrsum;
   a.ws.gsum = h->d_vgsum;
   a.ws.cnt1 = h->d_vcnt1;
   a.ws.cnt2 = h->d_vcnt2;
@@ -1727,7 +1731,7 @@ int pcg_solve(spai_handle h, const double* b, double* x, int nrhs, double rtol, 
     } else {
       for (int c = 0; c < chunk; c++) CK(launch_pcg_iter(a, fk, st));
     }
-    h->pcg_launches += (5 + prec_launches) * chunk;
+    h->pcg_launches += (4 + prec_launches) * chunk;
     CK(cudaMemcpyAsync(&ps, h->d_ps, sizeof(ps), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     if (ps.done) break;

@@ -880,15 +880,24 @@ __device__ __forceinline__ void rr_finish(PcgScalars* s, double rr) {
 }
 
 // one CTA: the total of the partials the previous kernel stored, then its
-// scalar step (which: 0 rho, 1 p.q, 2 r.r)
+// scalar step (which: 0 rho, 1 p.q; 3: the (r, r) total of the update first
+// -- count the iteration, stop if converged -- then, if going on, rho)
 __global__ void k_pcg_fin(PcgArgs a, int which, int first) {
   PcgScalars* s = a.s;
   if (s->done) return;
+  if (which == 3) {
+    const double rr = cta_total(a.rrsum, a.ws.nb);
+    __syncthreads();  // cta_total's scratch is reused
+    const double rz = cta_total(a.ws.bsum, a.ws.nb);
+    if (threadIdx.x != 0) return;
+    rr_finish(s, rr);
+    if (!s->done) rho_finish(s, 0, rz);
+    return;
+  }
   const double tot = cta_total(a.ws.bsum, a.ws.nb);
   if (threadIdx.x != 0) return;
   if (which == 0) rho_finish(s, first, tot);
-  else if (which == 1) pq_finish(s, tot);
-  else rr_finish(s, tot);
+  else pq_finish(s, tot);
 }
 
 // z = Prec(r), terms r_i z_i -> partials of rho (first = 1: initial rho, p =
@@ -965,7 +974,7 @@ __global__ void k_pcg_update(PcgArgs a) {
     if (a.mixed) a.r32[i] = __double2float_rn(r);
     term = __dmul_rn(r, r);
   }
-  cta_partial(term, a.ws.bsum);
+  cta_partial(term, a.rrsum);
 }
 
 // ---------------------------------------------------------------- Lanczos
@@ -1061,19 +1070,19 @@ cudaError_t launch_lz_step(const LzArgs& a, int j, cudaStream_t st) {
 
 // z = Prec(r) and rho: with rows longer than kLongRow (and a second stream),
 // the long rows run on st2 beside the others on st, and k_pcg_rz joins them
-static cudaError_t launch_pcg_prec(const PcgArgs& a, int first, const PcgFork& f,
+static cudaError_t launch_pcg_prec(const PcgArgs& a, int first, int fin, const PcgFork& f,
                                    cudaStream_t st) {
   int g = (a.n + 255) / 256;
   if (!a.nlong) {
     k_pcg_prec<<<g, 256, 0, st>>>(a, first, 0);
-    k_pcg_fin<<<1, 256, 0, st>>>(a, 0, first);
+    k_pcg_fin<<<1, 256, 0, st>>>(a, fin, first);
     return cudaGetLastError();
   }
   if (!f.st2) {
     k_pcg_prec_long<<<a.nlong, 32, 0, st>>>(a);
     k_pcg_prec<<<g, 256, 0, st>>>(a, first, 1);
     k_pcg_rz<<<g, 256, 0, st>>>(a, first);
-    k_pcg_fin<<<1, 256, 0, st>>>(a, 0, first);
+    k_pcg_fin<<<1, 256, 0, st>>>(a, fin, first);
     return cudaGetLastError();
   }
   cudaError_t e = cudaEventRecord(f.fork, st);
@@ -1086,14 +1095,14 @@ static cudaError_t launch_pcg_prec(const PcgArgs& a, int first, const PcgFork& f
   e = cudaStreamWaitEvent(st, f.join, 0);
   if (e) return e;
   k_pcg_rz<<<g, 256, 0, st>>>(a, first);
-  k_pcg_fin<<<1, 256, 0, st>>>(a, 0, first);
+  k_pcg_fin<<<1, 256, 0, st>>>(a, fin, first);
   return cudaGetLastError();
 }
 
 cudaError_t launch_pcg_init(const PcgArgs& a, const PcgFork& f, cudaStream_t st) {
   int g = (a.n + 255) / 256;
   k_pcg_init<<<g, 256, 0, st>>>(a);
-  cudaError_t e = launch_pcg_prec(a, 1, f, st);
+  cudaError_t e = launch_pcg_prec(a, 1, 0, f, st);
   if (e) return e;
   k_pcg_dir<<<g, 256, 0, st>>>(a, 1);
   return cudaGetLastError();
@@ -1104,8 +1113,10 @@ cudaError_t launch_pcg_iter(const PcgArgs& a, const PcgFork& f, cudaStream_t st)
   k_pcg_spmv<<<g, 256, 0, st>>>(a);
   k_pcg_fin<<<1, 256, 0, st>>>(a, 1, 0);
   k_pcg_update<<<g, 256, 0, st>>>(a);
-  k_pcg_fin<<<1, 256, 0, st>>>(a, 2, 0);
-  cudaError_t e = launch_pcg_prec(a, 0, f, st);
+  // the preconditioner product runs before the update's (r, r) is totalled:
+  // its fin counts the iteration and stops on convergence before it forms
+  // rho, so a converged last iteration only forms a z that is not used
+  cudaError_t e = launch_pcg_prec(a, 0, 3, f, st);
   if (e) return e;
   k_pcg_dir<<<g, 256, 0, st>>>(a, 0);
   return cudaGetLastError();

@@ -47,6 +47,9 @@ struct PcgArgs {
   double *x, *r, *z, *p, *q;
   PcgScalars* s;
   RedWS ws;
+  // the CTA partials of (r, r), apart from ws.bsum: their total is taken
+  // with (r, z)'s, after the preconditioner product
+  double* rrsum;
   // mixed (FP32-values) products: A's sliced-ELL values and M's (or S's)
   // row values in FP32, and FP32 copies of p and r as their operands
   int mixed;
