@@ -73,7 +73,8 @@ struct ColCtx {
     ph_t0 = t;
   }
 #else
-  int nsync = 0;  // threads of the CTA's warps with a column in this round
+  int nsync = 0;  // threads of this warp's barrier group with a column in this round
+  int bar = 1;    // the group's named barrier
   __device__ ColCtx(const PassParams& pp, char* w, int l, const DevScalars* s, int sg)
       : p(pp), ws(w), lane(l), overflow(0), bytes(0), rbytes(0), spg(0), nnzM(0), sc(s), seg(sg) {}
   __device__ __forceinline__ void ph_start() {}
@@ -83,7 +84,8 @@ struct ColCtx {
   // other boundaries too measured slower)
   __device__ __forceinline__ void mark(int k) {
     constexpr int kSyncAt = (1 << kPhSelect) | (1 << kPhSpgemm) | (1 << kPhFixsum);
-    if (nsync > 32 && ((kSyncAt >> k) & 1)) asm volatile("bar.sync 1, %0;" ::"r"(nsync) : "memory");
+    if (nsync > 32 && ((kSyncAt >> k) & 1))
+      asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(nsync) : "memory");
   }
 #endif
   template <typename T> __device__ T* at(int off) const { return (T*)(ws + off); }
@@ -647,6 +649,9 @@ __device__ inline void coefficients(const PassParams& p, DevScalars* sc, double*
   }
 }
 
+// warps per phase-barrier group of the MR and LOMR passes
+constexpr int kBarWarps = 8;
+
 // One instantiation per pass kind keeps each kernel's code small: with all
 // kinds behind a runtime switch the instruction cache missed often.
 template <typename VS, typename VC, bool PI, int KIND, bool HOT = false>
@@ -692,7 +697,13 @@ __global__ void __launch_bounds__(sizeof(VC) == 4 ? 512 : 256, sizeof(VC) == 4 ?
     // kernels are larger than the SM's instruction cache, and warps spread
     // over the code miss in it (measured: MR 67 -> 78 %, LOMR 54 -> 62 %
     // hits); CG's smaller passes lose more to the waits than they gain
-    if (KIND == kMR || KIND == kLOMR) c.nsync = 32 * (int)max(nv, 0LL);
+    // (groups of kBarWarps warps, each on its own named barrier: fewer warps
+    // wait for the slowest of a group)
+    if (KIND == kMR || KIND == kLOMR) {
+      const int g0 = warp / kBarWarps * kBarWarps;
+      c.bar = 1 + warp / kBarWarps;
+      c.nsync = 32 * (int)max(0LL, min((long long)kBarWarps, nv - g0));
+    }
 #endif
     double pr[6] = {0, 0, 0, 0, 0, 0};
     c.ph_start();
