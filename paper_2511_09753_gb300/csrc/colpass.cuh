@@ -365,18 +365,17 @@ __device__ void column_work(ColCtx<VS, VC>& c, int j, double* part) {
     hb.occ = c.template at<uint16_t>(L.go);
     hb.H = L.H;
     if (upd) {
+      // S = delta Z + gamma P and T = M + S from one table (P_i = D(S),
+      // M_{i+1} = D(T))
       CombLin<VC> fl{c.sc->delta, c.sc->gamma};
-      int Ls = warp_union(un, Zr, Zv, Lz0, Pr, Pv, Lp, Sr, Sv, fl, lane);
+      CombAdd<VC> fa;
+      int Ls, Lt;
+      warp_union3(un, Zr, Zv, Lz0, Pr, Pv, Lp, Mr, Mv, Lm, Sr, Sv, &Ls, Tr, Tv, &Lt, fl, fa, lane);
       c.mark(kPhUnion);
       Lp = warp_select(Sr, Sv, Ls, cap, Pr, Pv, hist, tie, p.drop, ovf, lane, keep);
       c.mark(kPhSelect);
       store_col(c, p.Prow, p.Pval, p.Plen, j, off, Lp, Pr, Pv);
       c.mark(kPhStore);
-      CombAdd<VC> fa;
-      // S (up to two caps of entries) looks up M (at most one): the union's
-      // table takes the shorter list, and m + s = s + m exactly
-      int Lt = warp_union(un, Sr, Sv, Ls, Mr, Mv, Lm, Tr, Tv, fa, lane);
-      c.mark(kPhUnion);
       Lm = warp_select(Tr, Tv, Lt, cap, Mr, Mv, hist, tie, p.drop, ovf, lane, keep);
       c.mark(kPhSelect);
       store_col(c, p.Mrow, p.Mval, p.Mlen, j, off, Lm, Mr, Mv);

@@ -350,6 +350,18 @@ __device__ __forceinline__ V hash_find(const HashT& h, int r) {
   }
 }
 
+// finish the insertion of r whose first attempt, at its home slot, returned
+// got (-1: claimed there): probe on as hash_insert does; returns the slot
+__device__ __forceinline__ int hash_settle(const HashT& h, int r, int got, bool* isnew) {
+  int q = hslot(r, h.H);
+  while (got != -1 && got != r) {
+    q = (q + 1) & (h.H - 1);
+    got = atomicCAS(&h.key[q], -1, r);
+  }
+  *isnew = got == -1;
+  return q;
+}
+
 // append the slots that lanes inserted as new to the occupied list
 __device__ __forceinline__ void occ_append(const HashT& h, int& cnt, bool isnew, int slot) {
   unsigned b = __ballot_sync(kFull, isnew);
@@ -483,6 +495,120 @@ __device__ int warp_union(const UnionT& u, const int* ar, const V* av, int La, c
   }
   __syncwarp();
   return outn;
+}
+
+// LOMR's two combinations from one table: S = f(Z, P) (exact zeros removed)
+// and T = g(S, M) (exact zeros removed), the same values as
+// warp_union(Z, P, f) followed by warp_union(S list, M, g).  M and P enter
+// the table (a row of both has one slot); Z's rows look it up, and a slot a
+// Z row matched is marked by storing -2 - row as its key (lookups of other
+// rows probe past it, and the table is cleared before its next use); then
+// the unmarked slots give the rows of P or M that Z does not have.
+template <typename V, typename FS, typename FT>
+__device__ void warp_union3(const UnionT& u, const int* zr, const V* zv, int Lz, const int* pr,
+                            const V* pv, int Lp, const int* mr, const V* mv, int Lm, int* sr, V* sv,
+                            int* Ls, int* tr, V* tv, int* Lt, FS f, FT g, int lane) {
+  HashT h;
+  h.key = u.key;
+  h.val = u.vb;
+  h.occ = u.occ;
+  h.H = u.H;
+  V* hm = (V*)u.va;  // M's value of the slot, or 0
+  V* hp = (V*)u.vb;  // P's value of the slot, or 0
+  hash_clear_all(h, lane);
+  int cnt = 0;
+  for (int base = 0; base < Lm; base += 32) {
+    int i = base + lane;
+    bool isnew = false;
+    int q = -1;
+    if (i < Lm) {
+      q = hash_insert<V>(h, mr[i], &isnew);
+      hm[q] = mv[i];
+      hp[q] = V(0);
+    }
+    occ_append(h, cnt, isnew, q);
+  }
+  __syncwarp();
+  for (int base = 0; base < Lp; base += 32) {
+    int i = base + lane;
+    bool isnew = false;
+    int q = -1;
+    if (i < Lp) {
+      q = hash_insert<V>(h, pr[i], &isnew);
+      if (isnew) hm[q] = V(0);
+      hp[q] = pv[i];
+    }
+    occ_append(h, cnt, isnew, q);
+  }
+  __syncwarp();
+  int ns = 0, nt = 0;
+  for (int base = 0; base < Lz; base += 32) {
+    int i = base + lane;
+    bool s_nz = false, t_nz = false;
+    int r = 0;
+    V s = V(0), t = V(0);
+    if (i < Lz) {
+      r = zr[i];
+      const int q = hash_slot_of(h, r);
+      V p = V(0), m = V(0);
+      if (q >= 0) {
+        p = hp[q];
+        m = hm[q];
+        h.key[q] = -2 - r;
+      }
+      s = f(zv[i], p);
+      s_nz = s != V(0);
+      t = s_nz ? g(s, m) : m;  // a zero s is no row of the S list
+      t_nz = t != V(0);
+    }
+    unsigned bs = __ballot_sync(kFull, s_nz), bt = __ballot_sync(kFull, t_nz);
+    if (s_nz) {
+      const int at = ns + __popc(bs & lanemask_lt());
+      sr[at] = r;
+      sv[at] = s;
+    }
+    if (t_nz) {
+      const int at = nt + __popc(bt & lanemask_lt());
+      tr[at] = r;
+      tv[at] = t;
+    }
+    ns += __popc(bs);
+    nt += __popc(bt);
+  }
+  __syncwarp();
+  for (int base = 0; base < cnt; base += 32) {
+    int i = base + lane;
+    bool s_nz = false, t_nz = false;
+    int r = 0;
+    V s = V(0), t = V(0);
+    if (i < cnt) {
+      const int q = u.occ[i];
+      r = u.key[q];
+      if (r >= 0) {  // not matched by a Z row
+        const V p = hp[q], m = hm[q];
+        s = p != V(0) ? f(V(0), p) : V(0);
+        s_nz = s != V(0);
+        t = s_nz ? g(s, m) : m;
+        t_nz = t != V(0);
+      }
+    }
+    unsigned bs = __ballot_sync(kFull, s_nz), bt = __ballot_sync(kFull, t_nz);
+    if (s_nz) {
+      const int at = ns + __popc(bs & lanemask_lt());
+      sr[at] = r;
+      sv[at] = s;
+    }
+    if (t_nz) {
+      const int at = nt + __popc(bt & lanemask_lt());
+      tr[at] = r;
+      tv[at] = t;
+    }
+    ns += __popc(bs);
+    nt += __popc(bt);
+  }
+  __syncwarp();
+  *Ls = ns;
+  *Lt = nt;
 }
 
 // ------------------------------------------------------ 256-bin histograms
@@ -754,7 +880,18 @@ __device__ int spgemm_dia32(const PassParams& p, const HashT& h, const int* xr, 
       sl[s] = atomicCAS(&h.key[hslot(r, h.H)], -1, r);
     }
   }
+  // the diagonal row (R's "1 -"), claimed with the products' rows
+  const int gd = (diag >= 0 && lane == 0) ? atomicCAS(&h.key[hslot(diag, h.H)], -1, diag) : -2;
   int cnt = 0;
+  if (diag >= 0) {
+    bool isnew = false;
+    int slot = -1;
+    if (gd != -2) {
+      slot = hash_settle(h, diag, gd, &isnew);
+      if (isnew) hv[slot] = VC(0);
+    }
+    occ_append(h, cnt, isnew, slot);
+  }
 #pragma unroll
   for (int s = 7; s >= 0; s--) {
     if (s < D) {
@@ -783,13 +920,6 @@ __device__ int spgemm_dia32(const PassParams& p, const HashT& h, const int* xr, 
       if (sl[s] >= 0) hv[sl[s]] = vfma(a[s], x, hv[sl[s]]);
       __syncwarp();
     }
-  }
-  if (diag >= 0) {
-    bool isnew = false;
-    int slot = -1;
-    if (lane == 0) slot = hash_insert<VC>(h, diag, &isnew);
-    occ_append(h, cnt, isnew, slot);
-    __syncwarp();
   }
   return cnt;
 }
