@@ -14,6 +14,7 @@
 #include <algorithm>
 #include <cmath>
 #include <new>
+#include <thread>
 #include <vector>
 
 #include "spai.h"
@@ -595,6 +596,53 @@ void invalidate_rows(spai_ctx* h) {
 
 }  // namespace
 
+namespace {
+
+// The first failure of a check over rows [0, n), f(lo, hi) returning
+// {row, code} of its range's first failure or {hi, SPAI_OK}: ranges in
+// parallel (host_threads); of the ranges that failed, the one at the
+// smallest row wins, so the result is that of one scan in row order.
+struct RowFail {
+  int64_t row;
+  int code;
+};
+
+// Host threads for a pass over the rows of a matrix: up to 16 when it is
+// large (nnz >= 2^20), at least 1,024 rows each.
+unsigned host_threads(int64_t n, int64_t nnz) {
+  unsigned T = nnz >= (1LL << 20) ? std::min(16u, std::thread::hardware_concurrency()) : 1u;
+  if (T > (unsigned)(n / 1024)) T = (unsigned)std::max<int64_t>(1, n / 1024);
+  return std::max(T, 1u);
+}
+
+// f(t, lo, hi) for the T row ranges [n t / T, n (t + 1) / T), range 0 on the
+// calling thread; ranges without a thread (none could be started) run here.
+template <typename F>
+void for_ranges(int64_t n, unsigned T, const F& f) {
+  std::vector<std::thread> th;
+  try {
+    for (unsigned t = 1; t < T; t++)
+      th.emplace_back([&, t] { f(t, n * t / T, n * (t + 1) / T); });
+  } catch (...) {
+  }
+  for (unsigned t = (unsigned)th.size() + 1; t < T; t++) f(t, n * t / T, n * (t + 1) / T);
+  f(0u, (int64_t)0, n / T);
+  for (auto& x : th) x.join();
+}
+
+template <typename F>
+RowFail over_rows(int64_t n, int64_t nnz, const F& f) {
+  const unsigned T = host_threads(n, nnz);
+  if (T <= 1) return f(0, n);
+  std::vector<RowFail> r(T, RowFail{n, SPAI_OK});
+  for_ranges(n, T, [&](unsigned t, int64_t lo, int64_t hi) { r[t] = f(lo, hi); });
+  for (unsigned t = 0; t < T; t++)
+    if (r[t].code) return r[t];
+  return RowFail{n, SPAI_OK};
+}
+
+}  // namespace
+
 extern "C" {
 
 const char* spai_status_string(int code) {
@@ -623,34 +671,53 @@ int spai_validate_csr(int64_t n, int64_t nnz, const int32_t* rowptr, const int32
   if (n < 1 || nnz < 1 || !rowptr || !colind || !vals) return SPAI_ERR_ARG;
   if (n >= (1LL << 31) || nnz >= (1LL << 31)) return SPAI_ERR_UNSUPPORTED;
   if (rowptr[0] != 0 || rowptr[n] != nnz) return SPAI_ERR_CSR;
-  for (int64_t i = 0; i < n; i++) {
-    if (rowptr[i + 1] < rowptr[i]) return SPAI_ERR_CSR;
-    bool diag = false;
-    for (int64_t e = rowptr[i]; e < rowptr[i + 1]; e++) {
-      int32_t c = colind[e];
-      if (c < 0 || c >= n) return SPAI_ERR_CSR;
-      if (e > rowptr[i] && colind[e - 1] >= c) return SPAI_ERR_CSR;
-      if (!isfinite(vals[e])) return SPAI_ERR_NONFINITE;
-      if (c == i) {
-        if (!(vals[e] > 0.0)) return SPAI_ERR_NOT_SPD_DIAG;
-        diag = true;
-      }
+  // rows up to the first with a bad pointer (decreasing, or past nnz) have
+  // entries that can be read; the checks run over row ranges in parallel,
+  // and the failure at the smallest row is the one reported, as a scan in
+  // row order would find it
+  int64_t rows_ok = n;
+  for (int64_t i = 0; i < n; i++)
+    if (rowptr[i + 1] < rowptr[i] || rowptr[i + 1] > nnz) {
+      rows_ok = i;
+      break;
     }
-    if (!diag) return SPAI_ERR_NOT_SPD_DIAG;
-  }
-  if (check_symmetry) {
-    // rows are sorted, so scanning rows i in ascending order meets the
-    // entries (c, i) of each row c in its own order: a cursor per row
-    // points at the entry the next (i, c) must mirror
-    std::vector<int32_t> nxt(rowptr, rowptr + n);
-    for (int64_t i = 0; i < n; i++) {
+  const auto check = [&](int64_t lo, int64_t hi) -> RowFail {
+    for (int64_t i = lo; i < hi; i++) {
+      bool diag = false;
       for (int64_t e = rowptr[i]; e < rowptr[i + 1]; e++) {
-        const int32_t c = colind[e];
-        const int32_t q = nxt[c];
-        if (q >= rowptr[c + 1] || colind[q] != i || vals[q] != vals[e]) return SPAI_ERR_NOT_SYMMETRIC;
-        nxt[c] = q + 1;
+        int32_t c = colind[e];
+        if (c < 0 || c >= n) return {i, SPAI_ERR_CSR};
+        if (e > rowptr[i] && colind[e - 1] >= c) return {i, SPAI_ERR_CSR};
+        if (!isfinite(vals[e])) return {i, SPAI_ERR_NONFINITE};
+        if (c == i) {
+          if (!(vals[e] > 0.0)) return {i, SPAI_ERR_NOT_SPD_DIAG};
+          diag = true;
+        }
       }
+      if (!diag) return {i, SPAI_ERR_NOT_SPD_DIAG};
     }
+    return {hi, SPAI_OK};
+  };
+  RowFail f = over_rows(rows_ok, nnz, check);
+  if (f.code) return f.code;
+  if (rows_ok < n) return SPAI_ERR_CSR;
+  if (check_symmetry) {
+    // every off-diagonal entry (i, c) has its mirror (c, i), found by
+    // bisection in the sorted row c, with the same value
+    const auto mirror = [&](int64_t lo, int64_t hi) -> RowFail {
+      for (int64_t i = lo; i < hi; i++)
+        for (int64_t e = rowptr[i]; e < rowptr[i + 1]; e++) {
+          const int32_t c = colind[e];
+          if (c == i) continue;
+          const int32_t* b = colind + rowptr[c];
+          const int32_t* en = colind + rowptr[c + 1];
+          const int32_t* q = std::lower_bound(b, en, (int32_t)i);
+          if (q == en || *q != i || vals[q - colind] != vals[e]) return {i, SPAI_ERR_NOT_SYMMETRIC};
+        }
+      return {hi, SPAI_OK};
+    };
+    f = over_rows(n, nnz, mirror);
+    if (f.code) return f.code;
   }
   return SPAI_OK;
 }
@@ -716,9 +783,12 @@ int create_impl(spai_handle* out, int64_t n, int64_t nnz, const int32_t* rp, con
   // (launch_build_ell / launch_build_dia below); the host finds the diagonal
   // and the slot offsets
   std::vector<double> diag(n);
-  for (int64_t i = 0; i < n; i++)
-    for (int64_t e = rp[i]; e < rp[i + 1]; e++)
-      if (ci[e] == i) diag[i] = va[e];
+  const unsigned T = host_threads(n, nnz);
+  for_ranges(n, T, [&](unsigned, int64_t lo, int64_t hi) {
+    for (int64_t i = lo; i < hi; i++)
+      for (int64_t e = rp[i]; e < rp[i + 1]; e++)
+        if (ci[e] == i) diag[i] = va[e];
+  });
   // diagonal-slot layout when A has at most 32 distinct offsets col - row
   std::vector<int> seg_D, seg_doff;
   if (bd) {
@@ -763,26 +833,36 @@ int create_impl(spai_handle* out, int64_t n, int64_t nnz, const int32_t* rp, con
       seg_doff.clear();
     }
   } else {
-    std::vector<long long> offs;
-    std::vector<int> hint;  // index in offs of the t-th entry's offset in the previous row
-    bool ok = true;
-    for (int64_t i = 0; i < n && ok; i++)
-      for (int64_t e = rp[i]; e < rp[i + 1]; e++) {
-        const long long o = (long long)ci[e] - i;
-        const size_t t = (size_t)(e - rp[i]);
-        if (t < hint.size() && offs[hint[t]] == o) continue;
-        auto f = std::find(offs.begin(), offs.end(), o);
-        if (f == offs.end()) {
-          offs.push_back(o);
-          if (offs.size() > 32) {
-            ok = false;
-            break;
+    // the distinct offsets col - row of each row range (more than 32 in a
+    // range or in all: no diagonal slots), then their union
+    std::vector<std::vector<long long>> part(T);
+    for_ranges(n, T, [&](unsigned r, int64_t lo, int64_t hi) {
+      std::vector<long long>& offs = part[r];
+      std::vector<int> hint;  // index in offs of the t-th entry's offset in the previous row
+      bool rok = true;
+      for (int64_t i = lo; i < hi && rok; i++)
+        for (int64_t e = rp[i]; e < rp[i + 1]; e++) {
+          const long long o = (long long)ci[e] - i;
+          const size_t t = (size_t)(e - rp[i]);
+          if (t < hint.size() && offs[hint[t]] == o) continue;
+          auto f = std::find(offs.begin(), offs.end(), o);
+          if (f == offs.end()) {
+            offs.push_back(o);
+            if (offs.size() > 32) {
+              rok = false;
+              break;
+            }
+            f = offs.end() - 1;
           }
-          f = offs.end() - 1;
+          if (t >= hint.size()) hint.resize(t + 1, 0);
+          hint[t] = (int)(f - offs.begin());
         }
-        if (t >= hint.size()) hint.resize(t + 1, 0);
-        hint[t] = (int)(f - offs.begin());
-      }
+    });
+    std::vector<long long> offs;
+    for (auto& pr : part) offs.insert(offs.end(), pr.begin(), pr.end());
+    std::sort(offs.begin(), offs.end());
+    offs.erase(std::unique(offs.begin(), offs.end()), offs.end());
+    const bool ok = offs.size() <= 32;
     if (ok) {
       std::sort(offs.begin(), offs.end());
       h->dia = true;

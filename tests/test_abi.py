@@ -123,3 +123,35 @@ def test_create_batched_rejects_bad_input_before_any_device_call():
     with pytest.raises(spai.SpaiError) as e:
         spai.SpaiBatch([good], prec="fp64", cap_factor=0.0)
     assert e.value.code == -1
+
+
+def test_validate_csr_large_matrix_reports_the_first_failing_row():
+    """A matrix large enough for the row ranges to be checked on several host
+    threads (64^3, 1.8 M entries): of several faults, the one in the
+    smallest row decides the code, as a scan in row order would; a row
+    pointer that runs backwards or past nnz is a CSR error at its row."""
+    spai = _lib()
+    n, rp, ci, v = I.varcoef_3d_7pt(64)
+    rp = np.ascontiguousarray(rp, np.int32)
+    ci = np.ascontiguousarray(ci, np.int32)
+    v = np.ascontiguousarray(v, np.float64)
+    assert spai.validate_csr(n, rp, ci, v) == 0
+    a = v.copy(); a[1000] = np.nan
+    b = ci.copy(); b[1_500_000] = -5
+    assert spai.validate_csr(n, rp, b, a) == -5               # non-finite first
+    a = v.copy(); a[1_700_000] = np.inf
+    b = ci.copy(); b[100] = n + 3
+    assert spai.validate_csr(n, rp, b, a) == -2               # column out of range first
+    for e in (4, 900_001, len(v) - 2):                        # off-diagonal entries
+        assert ci[e] != np.searchsorted(rp, e, side="right") - 1
+        a = v.copy(); a[e] *= 1.0000001
+        assert spai.validate_csr(n, rp, ci, a) == -4
+        assert spai.validate_csr(n, rp, ci, a, check_symmetry=False) == 0
+    r = rp.copy(); r[200_000] = r[200_001] + 3                # backwards at row 199,999
+    a = v.copy(); a[10] = np.nan
+    assert spai.validate_csr(n, r, ci, a) == -5
+    assert spai.validate_csr(n, r, ci, v) == -2
+    d = v.copy()
+    last = n - 1
+    d[rp[last]:rp[last + 1]][ci[rp[last]:rp[last + 1]] == last] = 0.0
+    assert spai.validate_csr(n, rp, ci, d) == -3              # diagonal of the last row
