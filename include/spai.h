@@ -101,7 +101,10 @@ typedef struct {
  * indices in [0,n) strictly increasing per row, finite values, a positive
  * diagonal in every row and, if check_symmetry, exact symmetry.  Returns
  * SPAI_OK or SPAI_ERR_CSR / SPAI_ERR_NOT_SPD_DIAG / SPAI_ERR_NOT_SYMMETRIC /
- * SPAI_ERR_NONFINITE / SPAI_ERR_ARG. */
+ * SPAI_ERR_NONFINITE / SPAI_ERR_ARG: with several faults, the code of the
+ * one in the smallest row (symmetry is checked after the rest).  Matrices
+ * of 2^20 entries or more are checked over row ranges on up to 16 host
+ * threads (started and joined within the call). */
 int spai_validate_csr(int64_t n, int64_t nnz, const int32_t *rowptr, const int32_t *colind,
                       const double *vals, int check_symmetry);
 
